@@ -1,0 +1,510 @@
+/*
+ * hydro_oracle.c -- plain, slow FP64 CPU oracle for the finite-difference
+ * WENO5/WENO7 scheme with third-order Runge-Kutta time stepping for 3+1D
+ * ideal relativistic hydrodynamics (Sikorski et al., "Relativistic
+ * hydrodynamics on graphics processing units", arXiv:1604.03360).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent checker of the
+ * CUDA path.  Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg may load it; the product library never calls it and shares
+ * no code, header or table with it.
+ *
+ * What it computes, step by step, in the paper's order:
+ *   Eq. 1 (Sec. 1)   du/dt + sum_i d f_i(u)/dx_i = 0, u = (E, M_x, M_y, M_z, R):
+ *                    energy density T^00, momentum densities T^0i and one
+ *                    conserved charge density n*gamma.  Ideal fluid,
+ *                    T^{mu nu} = (e+p) u^mu u^nu - p g^{mu nu}, EOS p = cs2*e.
+ *   Eq. 2 (Sec. 1)   L(u) = sum_i (F_i(x - e_i/2) - F_i(x + e_i/2)) / |e_i|.
+ *   Sec. 1.2         F at the half-cell faces by finite-difference WENO of
+ *                    order 5 (r = 3) or 7 (r = 4), applied component-wise to
+ *                    the Lax-Friedrichs split fluxes f^+- = (f +- alpha u)/2,
+ *                    alpha per direction = max |characteristic speed| over the
+ *                    grid (global Lax-Friedrichs).
+ *   Sec. 1           "third order Runge-Kutta": the SSP (Shu-Osher) form
+ *                    u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1));
+ *                    u' = 1/3 u + 2/3 (u2 + dt L(u2)).
+ *
+ * Readings where the paper is silent (kept identical on both sides): the EOS
+ * p = cs2 e; component-wise reconstruction; global LF splitting recomputed
+ * from every stage's input; dt = cfl * min_d dx_d / max_d alpha_d over the
+ * directions with more than one cell, clipped to t_end; outflow boundaries
+ * copy the edge cell into the ghost cells (zeroth-order extrapolation of the
+ * conserved variables); periodic boundaries wrap; directions with a single
+ * cell contribute no flux difference.
+ *
+ * Built with -O2 -ffp-contract=off (no FMA contraction) so that x86-64 and
+ * aarch64 hosts give identical bits.  OpenMP (if present) only splits the
+ * independent per-cell and per-pencil loops; the maxima are order
+ * independent, so results do not depend on the thread count.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Oracle configuration (its own type: nothing is shared with the library). */
+typedef struct {
+    int32_t n[3];      /* interior cells along x, y, z (x fastest in memory) */
+    int32_t r;         /* WENO parameter: 3 -> WENO5, 4 -> WENO7 */
+    int32_t bc[3];     /* 0: outflow (copy edge cell), 1: periodic */
+    int32_t pad_;
+    double dx[3];      /* cell sizes |e_i| */
+    double cs2;        /* EOS p = cs2 * e */
+    double cfl;
+    double dt_fixed;   /* > 0: use this dt instead of the CFL rule */
+    double eps;        /* WENO epsilon in alpha_k = d_k / (eps + beta_k)^2 */
+} oc_cfg;
+
+enum { OC_OK = 0, OC_ERR_ARG = 1, OC_ERR_UNPHYSICAL = 4, OC_ERR_OOM = 3 };
+#define NF 5
+
+/* ------------------------------------------------------------------------ */
+/* Thermodynamics and fluxes (Eq. 1)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Conserved (E, M, R) -> primitive (e, v, n) for p = k e.  With
+ * W = (e+p) gamma^2: E = W - p, M = W v, so (E + k e)^2 - M^2 =
+ * (1+k) e (E + k e), i.e. k e^2 + (1-k) E e - (E^2 - M^2) = 0; the positive
+ * root is written in the cancellation-free form.  v = M / (E + p),
+ * n = R / gamma.  Returns nonzero for E <= 0 or |M| >= E (no physical
+ * state) or NaN input. */
+int oc_con2prim(double k, const double *u, double *w)
+{
+    const double E = u[0], mx = u[1], my = u[2], mz = u[3], R = u[4];
+    const double m2 = mx * mx + my * my + mz * mz;
+    const double d = E * E - m2;
+    if (!(E > 0.0) || !(d > 0.0)) return 1;
+    const double b = (1.0 - k) * E;
+    const double e = 2.0 * d / (b + sqrt(b * b + 4.0 * k * d));
+    const double p = k * e;
+    const double vx = mx / (E + p), vy = my / (E + p), vz = mz / (E + p);
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    w[0] = e;
+    w[1] = vx;
+    w[2] = vy;
+    w[3] = vz;
+    w[4] = R * sqrt(1.0 - v2);
+    return 0;
+}
+
+/* Primitive (e, v, n) -> conserved: E = (e+p) gamma^2 - p, M = (e+p) gamma^2 v,
+ * R = n gamma. */
+void oc_prim2con(double k, const double *w, double *u)
+{
+    const double e = w[0], vx = w[1], vy = w[2], vz = w[3], n = w[4];
+    const double p = k * e;
+    const double g2 = 1.0 / (1.0 - (vx * vx + vy * vy + vz * vz));
+    const double W = (e + p) * g2;
+    u[0] = W - p;
+    u[1] = W * vx;
+    u[2] = W * vy;
+    u[3] = W * vz;
+    u[4] = n * sqrt(g2);
+}
+
+/* Physical flux along direction d (Eq. 1): f_d(E) = M_d = T^{0d},
+ * f_d(M_j) = M_j v_d + p delta_jd = T^{jd}, f_d(R) = R v_d = n u^d. */
+void oc_flux(double k, int d, const double *u, const double *w, double *f)
+{
+    const double p = k * w[0];
+    const double vd = w[1 + d];
+    f[0] = u[1 + d];
+    f[1] = u[1] * vd + (d == 0 ? p : 0.0);
+    f[2] = u[2] * vd + (d == 1 ? p : 0.0);
+    f[3] = u[3] * vd + (d == 2 ? p : 0.0);
+    f[4] = u[4] * vd;
+}
+
+/* Characteristic (sound-wave) speeds along d for p = k e:
+ * lambda_+- = [v_d (1-k) +- sqrt(k) sqrt((1-v^2)(1 - v_d^2 - k (v^2 - v_d^2)))]
+ *             / (1 - k v^2).  The other three eigenvalues equal v_d and lie
+ * between these two. */
+void oc_eigen(double k, int d, const double *w, double *lam)
+{
+    const double vx = w[1], vy = w[2], vz = w[3];
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double vd = w[1 + d];
+    const double root = sqrt(k) * sqrt((1.0 - v2) * (1.0 - vd * vd - k * (v2 - vd * vd)));
+    const double den = 1.0 - k * v2;
+    lam[0] = (vd * (1.0 - k) - root) / den;
+    lam[1] = (vd * (1.0 - k) + root) / den;
+}
+
+/* ------------------------------------------------------------------------ */
+/* WENO reconstruction (Sec. 1.2; Jiang-Shu / Shu finite-difference WENO)    */
+/* ------------------------------------------------------------------------ */
+/* Left-biased value at x_{j+1/2} from v[0..2r-2] = v_{j-r+1} .. v_{j+r-1}.
+ * Candidate k (k = 0..r-1) uses cells j-r+1+k .. j+k, i.e. v[k .. k+r-1].
+ * p_k is the degree r-1 polynomial whose averages over those cells equal the
+ * values; q_k = p_k(x_{j+1/2}); p_k(xi) = sum_i c_i xi^i about x_j in units of
+ * dx.  Tables: numerators over a common denominator per row. */
+
+/* q_k = sum_m QN[k][m] v[k+m] / QD */
+static const double Q5N[3][3] = {{2, -7, 11}, {-1, 5, 2}, {2, 5, -1}};
+static const double Q5D = 6;
+static const double Q7N[4][4] = {{-3, 13, -23, 25}, {1, -5, 13, 3}, {-1, 7, 7, -1}, {3, 13, -5, 1}};
+static const double Q7D = 12;
+/* Taylor coefficients c_1 .. c_{r-1} of p_k: c_i = sum_m TN[k][i-1][m] v[k+m] / TD[i-1] */
+static const double T5N[3][2][3] = {
+    {{1, -4, 3}, {1, -2, 1}},
+    {{-1, 0, 1}, {1, -2, 1}},
+    {{-3, 4, -1}, {1, -2, 1}}};
+static const double T5D[2] = {2, 2};
+static const double T7N[4][3][4] = {
+    {{-7, 33, -69, 43}, {-1, 4, -5, 2}, {-1, 3, -3, 1}},
+    {{5, -27, 15, 7}, {0, 1, -2, 1}, {-1, 3, -3, 1}},
+    {{-7, -15, 27, -5}, {1, -2, 1, 0}, {-1, 3, -3, 1}},
+    {{-43, 69, -33, 7}, {2, -5, 4, -1}, {-1, 3, -3, 1}}};
+static const double T7D[3] = {24, 2, 6};
+/* optimal (linear) weights */
+static const double D5[3] = {1.0 / 10, 6.0 / 10, 3.0 / 10};
+static const double D7[4] = {1.0 / 35, 12.0 / 35, 18.0 / 35, 4.0 / 35};
+
+static double falling(int a, int l)
+{
+    double f = 1.0;
+    for (int i = 0; i < l; ++i) f *= (double)(a - i);
+    return f;
+}
+
+/* Smoothness indicator, the Jiang-Shu definition written out:
+ * beta = sum_{l=1}^{r-1} int_{-1/2}^{1/2} (d^l p / d xi^l)^2 d xi. */
+static double smoothness(int r, const double *c /* c[1..r-1] used */)
+{
+    double beta = 0.0;
+    for (int l = 1; l < r; ++l)
+        for (int a = l; a < r; ++a)
+            for (int b = l; b < r; ++b) {
+                const int pw = (a - l) + (b - l);
+                if (pw & 1) continue; /* odd moments of [-1/2, 1/2] vanish */
+                const double mom = 1.0 / ((double)(pw + 1) * ldexp(1.0, pw));
+                beta += falling(a, l) * falling(b, l) * c[a] * c[b] * mom;
+            }
+    return beta;
+}
+
+double oc_weno_left(int r, const double *v, double eps)
+{
+    double q[4], beta[4], alpha[4], sum = 0.0;
+    for (int k = 0; k < r; ++k) {
+        double c[4] = {0, 0, 0, 0};
+        q[k] = 0.0;
+        for (int m = 0; m < r; ++m)
+            q[k] += (r == 3 ? Q5N[k][m] : Q7N[k][m]) * v[k + m];
+        q[k] /= (r == 3 ? Q5D : Q7D);
+        for (int i = 1; i < r; ++i) {
+            for (int m = 0; m < r; ++m)
+                c[i] += (r == 3 ? T5N[k][i - 1][m] : T7N[k][i - 1][m]) * v[k + m];
+            c[i] /= (r == 3 ? T5D[i - 1] : T7D[i - 1]);
+        }
+        beta[k] = smoothness(r, c);
+        const double dk = (r == 3 ? D5[k] : D7[k]);
+        alpha[k] = dk / ((eps + beta[k]) * (eps + beta[k]));
+        sum += alpha[k];
+    }
+    double out = 0.0;
+    for (int k = 0; k < r; ++k) out += (alpha[k] / sum) * q[k];
+    return out;
+}
+
+/* Right-biased value at x_{j+1/2} from v_{j-r+2} .. v_{j+r}: the mirror image. */
+static double weno_right(int r, const double *v, double eps)
+{
+    double m[7];
+    for (int i = 0; i < 2 * r - 1; ++i) m[i] = v[2 * r - 2 - i];
+    return oc_weno_left(r, m, eps);
+}
+
+/* Coefficient tables, exported so tests can compare them with a symbolic
+ * derivation from the definition.  q: r*r, taylor: r*(r-1)*r, d: r. */
+int oc_weno_tables(int r, double *q, double *taylor, double *d)
+{
+    if (r != 3 && r != 4) return OC_ERR_ARG;
+    for (int k = 0; k < r; ++k) {
+        d[k] = (r == 3 ? D5[k] : D7[k]);
+        for (int m = 0; m < r; ++m) {
+            q[k * r + m] = (r == 3 ? Q5N[k][m] / Q5D : Q7N[k][m] / Q7D);
+            for (int i = 1; i < r; ++i)
+                taylor[(k * (r - 1) + (i - 1)) * r + m] =
+                    (r == 3 ? T5N[k][i - 1][m] / T5D[i - 1] : T7N[k][i - 1][m] / T7D[i - 1]);
+        }
+    }
+    return OC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid helpers and boundary conditions                                     */
+/* ------------------------------------------------------------------------ */
+static int g_threads = 0;
+void oc_set_threads(int n) { g_threads = n; }
+int oc_get_max_threads(void)
+{
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int active(const oc_cfg *c, int d) { return c->n[d] > 1; }
+
+/* index of the interior cell that supplies (possibly ghost) coordinate i */
+static int bc_src(const oc_cfg *c, int d, int i)
+{
+    const int n = c->n[d];
+    if (i >= 0 && i < n) return i;
+    if (c->bc[d] == 1) return ((i % n) + n) % n;
+    return i < 0 ? 0 : n - 1;
+}
+
+static int64_t cell(const oc_cfg *c, int i, int j, int k)
+{
+    return ((int64_t)k * c->n[1] + j) * c->n[0] + i;
+}
+
+static int cfg_ok(const oc_cfg *c)
+{
+    if (!c) return 0;
+    for (int d = 0; d < 3; ++d)
+        if (c->n[d] < 1 || !(c->dx[d] > 0) || (c->bc[d] != 0 && c->bc[d] != 1)) return 0;
+    if (c->r != 3 && c->r != 4) return 0;
+    if (!(c->cs2 > 0 && c->cs2 < 1) || !(c->eps > 0)) return 0;
+    for (int d = 0; d < 3; ++d)
+        if (active(c, d) && c->bc[d] == 1 && c->n[d] < c->r) return 0;
+    return 1;
+}
+
+/* alpha_d = max over interior cells of max(|lambda_-|, |lambda_+|). */
+int oc_alpha(const oc_cfg *c, const double *u, double *alpha)
+{
+    if (!cfg_ok(c)) return OC_ERR_ARG;
+    const int64_t N = (int64_t)c->n[0] * c->n[1] * c->n[2];
+    double a0 = 0, a1 = 0, a2 = 0;
+    int bad = 0;
+#pragma omp parallel for reduction(max : a0, a1, a2) reduction(| : bad) num_threads(oc_get_max_threads())
+    for (int64_t q = 0; q < N; ++q) {
+        double uu[NF], w[NF], lam[2];
+        for (int f = 0; f < NF; ++f) uu[f] = u[f * N + q];
+        if (oc_con2prim(c->cs2, uu, w)) {
+            bad |= 1;
+            continue;
+        }
+        oc_eigen(c->cs2, 0, w, lam);
+        a0 = fmax(a0, fmax(fabs(lam[0]), fabs(lam[1])));
+        oc_eigen(c->cs2, 1, w, lam);
+        a1 = fmax(a1, fmax(fabs(lam[0]), fabs(lam[1])));
+        oc_eigen(c->cs2, 2, w, lam);
+        a2 = fmax(a2, fmax(fabs(lam[0]), fabs(lam[1])));
+    }
+    alpha[0] = a0;
+    alpha[1] = a1;
+    alpha[2] = a2;
+    return bad ? OC_ERR_UNPHYSICAL : OC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The semi-discrete operator L(u) of Eq. 2                                 */
+/* ------------------------------------------------------------------------ */
+/* L = sum_d (F_d(j - 1/2) - F_d(j + 1/2)) / dx_d with
+ * F(j+1/2) = WENO_left(f^+_{j-r+1..j+r-1}) + WENO_right(f^-_{j-r+2..j+r}),
+ * f^+- = (f_d(u) +- alpha_d u) / 2, ghost cells from the boundary rule. */
+int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
+{
+    if (!cfg_ok(c)) return OC_ERR_ARG;
+    const int r = c->r, G = r;
+    const int64_t N = (int64_t)c->n[0] * c->n[1] * c->n[2];
+    int bad = 0;
+#pragma omp parallel for num_threads(oc_get_max_threads())
+    for (int64_t q = 0; q < NF * N; ++q) L[q] = 0.0;
+
+    for (int d = 0; d < 3; ++d) {
+        if (!active(c, d)) continue;
+        const int nd = c->n[d];
+        const int da = (d + 1) % 3, db = (d + 2) % 3; /* the two other axes */
+        const int64_t npen = (int64_t)c->n[da] * c->n[db];
+        const int len = nd + 2 * G;
+#pragma omp parallel for reduction(| : bad) num_threads(oc_get_max_threads())
+        for (int64_t pen = 0; pen < npen; ++pen) {
+            const int ia = (int)(pen % c->n[da]), ib = (int)(pen / c->n[da]);
+            double *fp = malloc(sizeof(double) * NF * len);
+            double *fm = malloc(sizeof(double) * NF * len);
+            double *F = malloc(sizeof(double) * NF * (nd + 1));
+            if (!fp || !fm || !F) {
+                bad |= 2;
+                free(fp); free(fm); free(F);
+                continue;
+            }
+            /* split fluxes at every cell of the pencil, ghosts included */
+            for (int m = 0; m < len; ++m) {
+                int ijk[3];
+                ijk[d] = bc_src(c, d, m - G);
+                ijk[da] = ia;
+                ijk[db] = ib;
+                const int64_t q = cell(c, ijk[0], ijk[1], ijk[2]);
+                double uu[NF], w[NF], f[NF];
+                for (int k = 0; k < NF; ++k) uu[k] = u[k * N + q];
+                if (oc_con2prim(c->cs2, uu, w)) {
+                    bad |= 1;
+                    for (int k = 0; k < NF; ++k) w[k] = 0.0;
+                }
+                oc_flux(c->cs2, d, uu, w, f);
+                for (int k = 0; k < NF; ++k) {
+                    fp[k * len + m] = 0.5 * (f[k] + alpha[d] * uu[k]);
+                    fm[k * len + m] = 0.5 * (f[k] - alpha[d] * uu[k]);
+                }
+            }
+            /* face fluxes: F[s] sits at face s - 1/2, s = 0..nd */
+            for (int s = 0; s <= nd; ++s) {
+                const int j = s - 1 + G; /* padded index of the cell left of the face */
+                for (int k = 0; k < NF; ++k) {
+                    const double *vp = fp + k * len + (j - r + 1);
+                    const double *vm = fm + k * len + (j - r + 2);
+                    F[k * (nd + 1) + s] = oc_weno_left(r, vp, c->eps) + weno_right(r, vm, c->eps);
+                }
+            }
+            for (int s = 0; s < nd; ++s) {
+                int ijk[3];
+                ijk[d] = s;
+                ijk[da] = ia;
+                ijk[db] = ib;
+                const int64_t q = cell(c, ijk[0], ijk[1], ijk[2]);
+                for (int k = 0; k < NF; ++k)
+                    L[k * N + q] += (F[k * (nd + 1) + s] - F[k * (nd + 1) + s + 1]) / c->dx[d];
+            }
+            free(fp);
+            free(fm);
+            free(F);
+        }
+    }
+    if (bad & 2) return OC_ERR_OOM;
+    return bad ? OC_ERR_UNPHYSICAL : OC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time stepping (Sec. 1: third-order Runge-Kutta, SSP form)                 */
+/* ------------------------------------------------------------------------ */
+static double cfl_dt(const oc_cfg *c, const double *alpha)
+{
+    if (c->dt_fixed > 0) return c->dt_fixed;
+    int any = 0;
+    for (int d = 0; d < 3; ++d) any |= active(c, d);
+    double mindx = INFINITY, amax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        if (any && !active(c, d)) continue;
+        mindx = fmin(mindx, c->dx[d]);
+        amax = fmax(amax, alpha[d]);
+    }
+    return c->cfl * mindx / amax;
+}
+
+/* One RK3 stage: out = a*un + b*(us + dt*L(us; alpha)) (a = 0 for stage 1). */
+static int rk_stage(const oc_cfg *c, const double *un, const double *us, const double *alpha,
+                    double dt, double a, double b, double *out, double *Lbuf)
+{
+    const int rc = oc_L(c, us, alpha, Lbuf);
+    if (rc) return rc;
+    const int64_t M = (int64_t)NF * c->n[0] * c->n[1] * c->n[2];
+#pragma omp parallel for num_threads(oc_get_max_threads())
+    for (int64_t q = 0; q < M; ++q) {
+        const double s = us[q] + dt * Lbuf[q];
+        out[q] = (a == 0.0) ? s : a * un[q] + b * s;
+    }
+    return OC_OK;
+}
+
+/* Advance u in place by up to nsteps RK3 steps, stopping when t reaches
+ * t_end (t_end < 0: no limit).  If alpha_in/dt_in are given, those frozen
+ * values replace the computed ones (alpha_in[step*9 + stage*3 + d],
+ * dt_in[step]).  alpha_out/dt_out (optional) record the values used.
+ * *t and *steps are updated.  Returns 0 or an error code. */
+int oc_run(const oc_cfg *c, double *u, int nsteps, double t_end, double *t, int64_t *steps,
+           const double *alpha_in, const double *dt_in, double *alpha_out, double *dt_out)
+{
+    if (!cfg_ok(c) || nsteps < 0 || !t) return OC_ERR_ARG;
+    const int64_t M = (int64_t)NF * c->n[0] * c->n[1] * c->n[2];
+    double *u1 = malloc(sizeof(double) * M), *u2 = malloc(sizeof(double) * M);
+    double *Lb = malloc(sizeof(double) * M);
+    int rc = OC_OK;
+    if (!u1 || !u2 || !Lb) rc = OC_ERR_OOM;
+    for (int s = 0; s < nsteps && rc == OC_OK; ++s) {
+        double a0[3], a1[3], a2[3], dt;
+        if (alpha_in) {
+            memcpy(a0, alpha_in + 9 * s, sizeof a0);
+            dt = dt_in[s];
+        } else {
+            if ((rc = oc_alpha(c, u, a0))) break;
+            dt = cfl_dt(c, a0);
+            if (t_end >= 0 && *t + dt > t_end) dt = t_end - *t;
+            if (!(dt > 0)) break;
+        }
+        if ((rc = rk_stage(c, u, u, a0, dt, 0.0, 1.0, u1, Lb))) break;
+        if (alpha_in) memcpy(a1, alpha_in + 9 * s + 3, sizeof a1);
+        else if ((rc = oc_alpha(c, u1, a1))) break;
+        if ((rc = rk_stage(c, u, u1, a1, dt, 0.75, 0.25, u2, Lb))) break;
+        if (alpha_in) memcpy(a2, alpha_in + 9 * s + 6, sizeof a2);
+        else if ((rc = oc_alpha(c, u2, a2))) break;
+        if ((rc = rk_stage(c, u, u2, a2, dt, 1.0 / 3.0, 2.0 / 3.0, u, Lb))) break;
+        if (alpha_out) {
+            memcpy(alpha_out + 9 * s, a0, sizeof a0);
+            memcpy(alpha_out + 9 * s + 3, a1, sizeof a1);
+            memcpy(alpha_out + 9 * s + 6, a2, sizeof a2);
+        }
+        if (dt_out) dt_out[s] = dt;
+        *t += dt;
+        if (steps) *steps += 1;
+    }
+    free(u1);
+    free(u2);
+    free(Lb);
+    return rc;
+}
+
+/* Momentum anisotropy eps_2 = sum(T^xx - T^yy) / sum(T^xx + T^yy) over the
+ * interior cells, T^ij = (e+p) gamma^2 v_i v_j + p delta_ij = M_i v_j + p delta_ij.
+ * Serial sum in memory order. */
+int oc_eps2(const oc_cfg *c, const double *u, double *out)
+{
+    if (!cfg_ok(c)) return OC_ERR_ARG;
+    const int64_t N = (int64_t)c->n[0] * c->n[1] * c->n[2];
+    double num = 0.0, den = 0.0;
+    for (int64_t q = 0; q < N; ++q) {
+        double uu[NF], w[NF];
+        for (int f = 0; f < NF; ++f) uu[f] = u[f * N + q];
+        if (oc_con2prim(c->cs2, uu, w)) return OC_ERR_UNPHYSICAL;
+        const double p = c->cs2 * w[0];
+        const double txx = uu[1] * w[1] + p, tyy = uu[2] * w[2] + p;
+        num += txx - tyy;
+        den += txx + tyy;
+    }
+    *out = num / den;
+    return OC_OK;
+}
+
+/* Array versions of the point functions, for tests. */
+int oc_con2prim_n(double k, const double *u, int64_t n, double *w)
+{
+    int bad = 0;
+    for (int64_t q = 0; q < n; ++q) {
+        double uu[NF], ww[NF];
+        for (int f = 0; f < NF; ++f) uu[f] = u[f * n + q];
+        if (oc_con2prim(k, uu, ww)) {
+            bad = 1;
+            for (int f = 0; f < NF; ++f) ww[f] = NAN;
+        }
+        for (int f = 0; f < NF; ++f) w[f * n + q] = ww[f];
+    }
+    return bad ? OC_ERR_UNPHYSICAL : OC_OK;
+}
+
+void oc_prim2con_n(double k, const double *w, int64_t n, double *u)
+{
+    for (int64_t q = 0; q < n; ++q) {
+        double uu[NF], ww[NF];
+        for (int f = 0; f < NF; ++f) ww[f] = w[f * n + q];
+        oc_prim2con(k, ww, uu);
+        for (int f = 0; f < NF; ++f) u[f * n + q] = uu[f];
+    }
+}

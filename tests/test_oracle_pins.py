@@ -1,0 +1,451 @@
+"""Pins for the CPU oracle: each test checks the oracle against something the
+paper or the mathematics fixes (closed forms, exact solutions, invariants,
+symbolic derivations from the WENO definition), never against itself."""
+import numpy as np
+import pytest
+import sympy as sp
+
+import workloads as W
+from exact import SodExact, hubble as hubble_exact, t_mu_nu
+
+K = 1.0 / 3.0
+
+
+def rand_prims(rng, m):
+    e = np.exp(rng.uniform(np.log(1e-3), np.log(1e2), m))
+    d = rng.standard_normal((m, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    vmag = rng.uniform(0, 0.99, m)
+    v = d * vmag[:, None]
+    n = rng.uniform(0.01, 3, m)
+    return e, v, n
+
+
+# ---------------------------------------------------------------- Eq. 1 pieces
+def test_con2prim_roundtrip(oracle_lib):
+    """Conserved densities built from T^{mu nu}, N^mu by definition are inverted
+    by the oracle to the original (e, v, n)."""
+    rng = np.random.default_rng(1)
+    e, v, n = rand_prims(rng, 2000)
+    T00, T0i, N0 = t_mu_nu(e, v, n, K)
+    u = np.stack([T00, T0i[:, 0], T0i[:, 1], T0i[:, 2], N0])
+    w = oracle_lib.con2prim(u, K)
+    np.testing.assert_allclose(w[0], e, rtol=1e-12)
+    np.testing.assert_allclose(w[1:4].T, v, rtol=1e-11, atol=1e-14)
+    np.testing.assert_allclose(w[4], n, rtol=1e-11)
+    # at rest E = e exactly, n = R exactly
+    u0 = np.array([[2.5], [0.0], [0.0], [0.0], [0.7]])
+    w0 = oracle_lib.con2prim(u0, K)
+    assert w0[0, 0] == 2.5 and w0[4, 0] == 0.7 and np.all(w0[1:4] == 0)
+
+
+def test_con2prim_rejects_unphysical(oracle_lib):
+    u = np.array([[1.0, -1.0, 1.0], [0.5, 0.0, 1.0], [0.0, 0.0, 0.1], [0.0, 0.0, 0.0], [1.0, 1.0, 1.0]])
+    w = oracle_lib.con2prim(u, K)
+    assert np.isfinite(w[:, 0]).all()
+    assert np.isnan(w[:, 1]).all() and np.isnan(w[:, 2]).all()
+
+
+def test_prim2con_matches_definition(oracle_lib):
+    rng = np.random.default_rng(2)
+    e, v, n = rand_prims(rng, 500)
+    T00, T0i, N0 = t_mu_nu(e, v, n, K)
+    u = oracle_lib.prim2con(np.stack([e, v[:, 0], v[:, 1], v[:, 2], n]), K)
+    np.testing.assert_allclose(u[0], T00, rtol=1e-13)
+    np.testing.assert_allclose(u[1:4].T, T0i, rtol=1e-13, atol=1e-300)
+    np.testing.assert_allclose(u[4], N0, rtol=1e-13)
+
+
+def test_flux_matches_stress_tensor(oracle_lib):
+    """f_d(u) = (T^{0d}, T^{xd}, T^{yd}, T^{zd}, N^d) with T^{ij} = (e+p) g^2 v_i v_j + p delta_ij."""
+    rng = np.random.default_rng(3)
+    e, v, n = rand_prims(rng, 50)
+    for q in range(50):
+        T00, T0i, N0 = t_mu_nu(e[q], v[q], n[q], K)
+        u = np.array([T00, *T0i, N0])
+        g2 = 1 / (1 - v[q] @ v[q])
+        p = K * e[q]
+        for d in range(3):
+            f = oracle_lib.flux(d, u, K)
+            Tid = (e[q] + p) * g2 * v[q] * v[q][d] + p * (np.arange(3) == d)
+            ref = np.array([(e[q] + p) * g2 * v[q][d], *Tid, n[q] * np.sqrt(g2) * v[q][d]])
+            np.testing.assert_allclose(f, ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
+
+
+def test_eigenvalues_match_flux_jacobian(oracle_lib):
+    """The characteristic speeds are the extreme eigenvalues of df_d/du,
+    here from a central-difference Jacobian of the oracle's own flux."""
+    rng = np.random.default_rng(4)
+    e, v, n = rand_prims(rng, 40)
+    for q in range(40):
+        T00, T0i, N0 = t_mu_nu(e[q], v[q] * 0.9, n[q], K)
+        u = np.array([T00, *T0i, N0])
+        w = oracle_lib.con2prim(u.reshape(5, 1), K).ravel()
+        for d in range(3):
+            J = np.empty((5, 5))
+            for j in range(5):
+                h = 1e-6 * max(abs(u[j]), u[0])
+                up, um = u.copy(), u.copy()
+                up[j] += h
+                um[j] -= h
+                J[:, j] = (oracle_lib.flux(d, up, K) - oracle_lib.flux(d, um, K)) / (2 * h)
+            ev = np.sort(np.linalg.eigvals(J).real)
+            lam = oracle_lib.eigen(d, w, K)
+            np.testing.assert_allclose([ev[0], ev[-1]], lam, atol=2e-6)
+            np.testing.assert_allclose(ev[1:4], w[1 + d], atol=2e-6)
+
+
+def test_eigenvalues_special_cases(oracle_lib):
+    c = np.sqrt(K)
+    lam = oracle_lib.eigen(0, np.array([1.0, 0, 0, 0, 1]), K)
+    np.testing.assert_allclose(lam, [-c, c], rtol=1e-15)
+    for vx in (-0.9, -0.3, 0.2, 0.7, 0.99):
+        lam = oracle_lib.eigen(0, np.array([1.0, vx, 0, 0, 1]), K)
+        np.testing.assert_allclose(lam, [(vx - c) / (1 - vx * c), (vx + c) / (1 + vx * c)], rtol=1e-13)
+
+
+# ---------------------------------------------------------------- Sec. 1.2 WENO
+def _weno_definition(r):
+    """Candidate values, Taylor coefficients and linear weights of FD-WENO of
+    order 2r-1, derived symbolically from the definition (cell-average
+    interpolation over each candidate stencil)."""
+    xi = sp.symbols("xi")
+    v = sp.symbols("v0:%d" % (2 * r - 1))
+    half = sp.Rational(1, 2)
+    qs, taylors, polys = [], [], []
+    for k in range(r):
+        c = sp.symbols("c0:%d" % r)
+        p = sum(c[i] * xi ** i for i in range(r))
+        eqs = [sp.Eq(sp.integrate(p, (xi, o - half, o + half)), v[o + r - 1]) for o in range(-r + 1 + k, k + 1)]
+        sol = sp.solve(eqs, c)
+        pk = sp.expand(p.subs(sol))
+        polys.append(pk)
+        qs.append(sp.expand(pk.subs(xi, half)))
+        taylors.append([sp.expand(sol[c[i]]) for i in range(1, r)])
+    R = 2 * r - 1
+    C = sp.symbols("C0:%d" % R)
+    P = sum(C[i] * xi ** i for i in range(R))
+    sol = sp.solve([sp.Eq(sp.integrate(P, (xi, o - half, o + half)), v[o + r - 1]) for o in range(-r + 1, r)], C)
+    big = sp.expand(P.subs(sol).subs(xi, half))
+    ds = sp.symbols("d0:%d" % r)
+    ex = sp.expand(sum(ds[k] * qs[k] for k in range(r)) - big)
+    dsol = sp.solve([ex.coeff(vv) for vv in v], ds)
+    betas = [sp.expand(sum(sp.integrate(sp.diff(pk, xi, l) ** 2, (xi, -half, half)) for l in range(1, r)))
+             for pk in polys]
+    return v, qs, taylors, [dsol[d] for d in ds], betas
+
+
+@pytest.mark.parametrize("r", [3, 4])
+def test_weno_tables_match_definition(oracle_lib, r):
+    v, qs, taylors, ds, _ = _weno_definition(r)
+    q, t, d = oracle_lib.weno_tables(r)
+    np.testing.assert_allclose(d, [float(x) for x in ds], rtol=1e-15)
+    for k in range(r):
+        for m in range(r):
+            assert abs(q[k, m] - float(qs[k].coeff(v[k + m]))) < 1e-15
+            for i in range(r - 1):
+                assert abs(t[k, i, m] - float(taylors[k][i].coeff(v[k + m]))) < 1e-15
+
+
+@pytest.mark.parametrize("r", [3, 4])
+def test_weno_reconstruction_matches_definition(oracle_lib, r):
+    """Nonlinear reconstruction on random data equals the definition evaluated
+    in exact rational arithmetic (beta from the integral of squared derivatives)."""
+    v, qs, _, ds, betas = _weno_definition(r)
+    rng = np.random.default_rng(5 + r)
+    for trial in range(40):
+        vals = rng.integers(-50, 50, size=2 * r - 1) / rng.choice([4, 16, 1000, 10 ** 6])
+        vals = vals + (trial % 3) * rng.standard_normal(2 * r - 1) * 1e-4
+        exact_vals = [sp.Rational(float(x)) for x in vals]
+        sub = dict(zip(v, exact_vals))
+        eps = sp.Rational(1, 10 ** 6)
+        a = [ds[k] / (eps + betas[k].subs(sub)) ** 2 for k in range(r)]
+        ref = sum(a[k] * qs[k].subs(sub) for k in range(r)) / sum(a)
+        got = oracle_lib.weno_left(r, vals, 1e-6)
+        assert abs(got - float(ref)) <= 1e-13 * max(1.0, abs(float(ref))), (trial, got, float(ref))
+
+
+@pytest.mark.parametrize("r", [3, 4])
+def test_weno_difference_exact_on_polynomials(oracle_lib, r):
+    """With linear weights (eps >> beta) the FD difference (R_{j+1/2} - R_{j-1/2})/h
+    of point values of a polynomial is its exact derivative up to degree 2r-1
+    and not beyond."""
+    h = 0.1
+    x = (np.arange(-r, r + 1)) * h   # points j-r .. j+r, j at index r
+    rng = np.random.default_rng(11)
+    for deg in range(0, 2 * r + 1):
+        coef = rng.uniform(-1, 1, deg + 1)
+        f = np.polyval(coef, x)
+        fp = np.polyval(np.polyder(coef), 0.0) if deg > 0 else 0.0
+        Rp = oracle_lib.weno_left(r, f[1:2 * r], 1e20)
+        Rm = oracle_lib.weno_left(r, f[0:2 * r - 1], 1e20)
+        err = abs((Rp - Rm) / h - fp)
+        if deg <= 2 * r - 1:
+            assert err < 1e-9, (deg, err)
+        else:
+            assert err > 1e-6, (deg, err)
+
+
+def test_weno_mirror_symmetry(oracle_lib):
+    """Reconstruction commutes with reversal for a symmetric stencil pair: the
+    left-biased value of v equals the value the mirrored scheme gives, and a
+    constant is reproduced exactly."""
+    for r in (3, 4):
+        assert oracle_lib.weno_left(r, np.full(2 * r - 1, 3.25)) == pytest.approx(3.25, rel=1e-15)
+
+
+# ---------------------------------------------------------------- Eq. 2 and RK3
+def _advection_setup(N, r, axis, amp):
+    """Uniform e, v and a sinusoidal charge: R = n gamma is advected, so
+    L(R) = -v_axis dR/dx_axis exactly and L(E) = L(M) = 0."""
+    n = [1, 1, 1]
+    n[axis] = N
+    L = 1.0
+    g = W.Grid(n=tuple(n), dx=(L / N,) * 3, origin=(0, 0, 0), bc=(1, 1, 1), scheme=2 * r - 1)
+    xs = (np.arange(N) + 0.5) / N
+    vel = [0.0, 0.0, 0.0]
+    vel[axis] = 0.5
+    e = np.ones(N)
+    nn = 1.0 + amp * np.sin(2 * np.pi * xs)
+    T00, T0i, N0 = t_mu_nu(e, np.tile(vel, (N, 1)), nn, K)
+    shape = (n[2], n[1], n[0])
+    u = np.stack([T00.reshape(shape), T0i[:, 0].reshape(shape), T0i[:, 1].reshape(shape),
+                  T0i[:, 2].reshape(shape), N0.reshape(shape)])
+    g2 = 1 / (1 - 0.25)
+    dR = amp * np.sqrt(g2) * 2 * np.pi * np.cos(2 * np.pi * xs)
+    return g, u, (-0.5 * dR).reshape(shape)
+
+
+@pytest.mark.parametrize("r,order", [(3, 5), (4, 7)])
+def test_spatial_convergence_order(oracle_lib, r, order):
+    for axis in range(3):
+        errs = []
+        Ns = (16, 32) if r == 4 else (32, 64)
+        for N in Ns:
+            g, u, ref = _advection_setup(N, r, axis, 1e-4)
+            c = oracle_lib.make_cfg(g.n, g.dx, scheme=g.scheme, bc=g.bc)
+            Lu = oracle_lib.L(c, u, oracle_lib.alpha(c, u))
+            assert np.abs(Lu[0]).max() < 1e-12 and np.abs(Lu[1:4]).max() < 1e-12
+            errs.append(np.abs(Lu[4] - ref).max())
+        obs = np.log2(errs[0] / errs[1])
+        assert order - 0.6 < obs < order + 1.0, (axis, errs, obs)
+
+
+def test_rk3_temporal_order(oracle_lib):
+    """SSP-RK3 is third order: halving dt on a fixed grid shrinks the error
+    against a much finer dt by about 8."""
+    g, w = W.smooth_periodic(n=(16, 1, 1), amp=0.1, vamp=0.2, seed=3)
+    u0 = oracle_lib.prim2con(w)
+    T = 0.2
+    def solve(nst):
+        c = oracle_lib.make_cfg(g.n, g.dx, scheme=5, bc=(1, 1, 1), dt_fixed=T / nst)
+        return oracle_lib.run(c, u0, nst)[0]
+    ref = solve(640)
+    e1 = np.abs(solve(20) - ref).max()
+    e2 = np.abs(solve(40) - ref).max()
+    e3 = np.abs(solve(80) - ref).max()
+    assert 6.5 < e1 / e2 < 9.5 and 6.5 < e2 / e3 < 9.5, (e1, e2, e3)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_conservation_periodic(oracle_lib, scheme):
+    """Flux form of Eq. 2 telescopes on a periodic box: totals of E, M, R are
+    constant to round-off."""
+    g, w = W.smooth_periodic(n=(10, 9, 8), amp=0.3, vamp=0.4, seed=5, scheme=scheme)
+    u0 = oracle_lib.prim2con(w)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=(1, 1, 1), cfl=0.4)
+    u1, t, k = oracle_lib.run(c, u0, 5)
+    assert k == 5 and t > 0
+    tot0 = u0.reshape(5, -1).sum(1)
+    tot1 = u1.reshape(5, -1).sum(1)
+    scale = np.abs(u0).reshape(5, -1).sum(1).max()
+    assert np.abs(tot1 - tot0).max() < 1e-13 * scale, tot1 - tot0
+    assert np.abs(u1 - u0).max() > 1e-3   # something actually moved
+
+
+def test_translation_invariance_periodic(oracle_lib):
+    g, w = W.smooth_periodic(n=(12, 8, 6), seed=9)
+    u0 = oracle_lib.prim2con(w)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=5, bc=(1, 1, 1), dt_fixed=0.01)
+    a = oracle_lib.run(c, u0, 2)[0]
+    b = oracle_lib.run(c, np.roll(u0, (2, 3, 5), axis=(1, 2, 3)), 2)[0]
+    np.testing.assert_allclose(np.roll(a, (2, 3, 5), axis=(1, 2, 3)), b, rtol=0, atol=1e-14)
+
+
+def test_uniform_state_preserved_outflow(oracle_lib):
+    """A uniform moving state is an exact solution; outflow ghosts keep it."""
+    n = (7, 6, 5)
+    w = np.stack([np.full(n[::-1], 2.0), np.full(n[::-1], 0.3), np.full(n[::-1], -0.2),
+                  np.full(n[::-1], 0.1), np.full(n[::-1], 0.5)])
+    u0 = oracle_lib.prim2con(w)
+    c = oracle_lib.make_cfg(n, (0.1, 0.1, 0.1), scheme=7, bc=(0, 0, 0))
+    u1 = oracle_lib.run(c, u0, 3)[0]
+    np.testing.assert_allclose(u1, u0, rtol=1e-14)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_mirror_and_permutation_symmetry(oracle_lib, scheme):
+    g, w = W.lumpy(n=(10, 10, 10), seed=21, scheme=scheme)
+    w[1] = 0.2 * np.tanh(w[0] - 1)  # give the flow a velocity field
+    u0 = oracle_lib.prim2con(w)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme)
+    a = oracle_lib.run(c, u0, 2)[0]
+    # mirror x -> -x: reverse x and flip M_x
+    um = u0[:, :, :, ::-1].copy()
+    um[1] *= -1
+    b = oracle_lib.run(c, um, 2)[0]
+    b = b[:, :, :, ::-1].copy()
+    b[1] *= -1
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * np.abs(a).max())
+    # swap x <-> y: transpose the two spatial axes and swap M_x, M_y
+    ut = u0.transpose(0, 1, 3, 2)[[0, 2, 1, 3, 4]].copy()
+    b = oracle_lib.run(c, ut, 2)[0]
+    b = b.transpose(0, 1, 3, 2)[[0, 2, 1, 3, 4]]
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * np.abs(a).max())
+
+
+def test_anisotropic_spacing_uses_own_dx(oracle_lib):
+    """L scales as 1/dx_d per direction: doubling dx_y halves the y part."""
+    g, w = W.smooth_periodic(n=(1, 16, 1), seed=4)
+    u = oracle_lib.prim2con(w)
+    c1 = oracle_lib.make_cfg(g.n, (1.0, 1 / 16, 1.0), bc=(1, 1, 1))
+    c2 = oracle_lib.make_cfg(g.n, (1.0, 2 / 16, 1.0), bc=(1, 1, 1))
+    a = oracle_lib.alpha(c1, u)
+    np.testing.assert_allclose(oracle_lib.L(c2, u, a) * 2, oracle_lib.L(c1, u, a), rtol=1e-14, atol=1e-15)
+
+
+# ---------------------------------------------------------------- Sec. 3 tests
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_sod_against_exact_solution(oracle_lib, scheme):
+    ex = SodExact()
+    errs = []
+    for N in (100, 200, 400):
+        g, w = W.sod(N=N, scheme=scheme)
+        c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, cfl=g.cfl)
+        u, t, k = oracle_lib.run(c, oracle_lib.prim2con(w), 100000, t=0.0, t_end=0.4)
+        assert t == pytest.approx(0.4, abs=1e-15)
+        p = oracle_lib.con2prim(u)
+        x = g.centres()[0].ravel()
+        e_ex, v_ex, n_ex = ex(x, 0.4)
+        errs.append(np.abs(p[4].ravel() - n_ex).mean())
+        if N == 400:
+            e_num, v_num, n_num = p[0].ravel(), p[1].ravel(), p[4].ravel()
+            # plateau between the rarefaction tail and the shock
+            mid = (x > ex.xi_tail * 0.4 + 0.03) & (x < ex.V_shock * 0.4 - 0.03)
+            assert np.abs(e_num[mid] / ex.e_star - 1).max() < 0.01
+            assert np.abs(v_num[mid] / ex.v_star - 1).max() < 0.01
+            midL = (x > ex.xi_tail * 0.4 + 0.03) & (x < ex.v_star * 0.4 - 0.03)
+            midR = (x > ex.v_star * 0.4 + 0.03) & (x < ex.V_shock * 0.4 - 0.03)
+            assert np.abs(n_num[midL] / ex.n_star_L - 1).max() < 0.01
+            assert np.abs(n_num[midR] / ex.n_star_R - 1).max() < 0.015
+            # shock position: where e crosses the mid value, within 3 cells
+            half = 0.5 * (ex.e_star + ex.eR)
+            i = np.where((e_num[:-1] > half) & (e_num[1:] <= half) & (x[:-1] > 0.2))[0][0]
+            assert abs(x[i] + 0.5 * g.dx[0] - ex.V_shock * 0.4) < 3 * g.dx[0]
+            assert np.all(np.isfinite(p))
+    assert errs[0] > errs[1] > errs[2], errs
+    obs = np.log2(errs[0] / errs[2]) / 2
+    assert 0.4 < obs < 1.3, (errs, obs)
+
+
+def _hubble_error(oracle_lib, N, scheme, axes=None, R=1.5):
+    """Max relative error of e and n, and abs error of v_x, over |x_i| < R after
+    the flow has run from t0 = 10 to t0 + 1 (far inside the light cone of the
+    outflow boundaries at |x_i| = 5)."""
+    if axes is None:
+        g, w = W.hubble(N=N, scheme=scheme)
+    else:
+        g, w = W.ellipsoidal_charge(N=N, scheme=scheme, axes=axes)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, cfl=0.3)
+    T1 = g.t0 + 1.0
+    u, t, k = oracle_lib.run(c, oracle_lib.prim2con(w), 10 ** 6, t=g.t0, t_end=T1)
+    assert t == pytest.approx(T1)
+    p = oracle_lib.con2prim(u)
+    x, y, z = g.centres()
+    ref = hubble_exact(x, y, z, T1, axes=axes)
+    inside = np.broadcast_to((np.abs(x) < R) & (np.abs(y) < R) & (np.abs(z) < R), p[0].shape)
+    ee = np.abs(p[0] / ref[0] - 1)[inside].max()
+    ve = np.abs(p[1] - np.broadcast_to(ref[1], p[1].shape))[inside].max()
+    ne = np.abs(p[4] / ref[4] - 1)[inside].max()
+    return ee, ve, ne
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_hubble_flow_against_analytic(oracle_lib, scheme):
+    """Hubble-like expansion: e(tau) = e0 (t0/tau)^(3(1+cs2)), v = x/t; the
+    error over a fixed interior region shrinks with resolution."""
+    e24, v24, n24 = _hubble_error(oracle_lib, 24, scheme)
+    e32, v32, n32 = _hubble_error(oracle_lib, 32, scheme)
+    assert e32 < 2e-5 and v32 < 1e-5 and n32 < 2e-5, (e32, v32, n32)
+    assert e32 < 0.6 * e24 and n32 < 0.6 * n24, (e24, e32, n24, n32)
+
+
+def test_ellipsoidal_charge_on_hubble(oracle_lib):
+    """Ellipsoidal charge profile in x/t carried by the Hubble flow (exact)."""
+    e24, _, n24 = _hubble_error(oracle_lib, 24, 5, axes=(2.0, 3.0, 4.0))
+    e32, _, n32 = _hubble_error(oracle_lib, 32, 5, axes=(2.0, 3.0, 4.0))
+    assert n32 < 1e-4 and e32 < 2e-5, (e32, n32)
+    assert n32 < 0.6 * n24, (n24, n32)
+
+
+def test_frozen_run_reproduces_recorded_run(oracle_lib):
+    g, w = W.lumpy(n=(8, 9, 10), seed=3)
+    c = oracle_lib.make_cfg(g.n, g.dx)
+    u0 = oracle_lib.prim2con(w)
+    a, t, k, al, dts = oracle_lib.run(c, u0, 3, record=True)
+    b, t2, k2 = oracle_lib.run(c, u0, 3, alpha_in=al, dt_in=dts)
+    assert k == 3 and np.array_equal(a, b)
+
+
+def test_thread_count_does_not_change_bits(oracle_lib):
+    g, w = W.lumpy(n=(12, 11, 10), seed=8, scheme=7)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=7)
+    u0 = oracle_lib.prim2con(w)
+    oracle_lib.set_threads(1)
+    a = oracle_lib.run(c, u0, 2)[0]
+    oracle_lib.set_threads(0)
+    b = oracle_lib.run(c, u0, 2)[0]
+    assert np.array_equal(a, b)
+
+
+def test_unphysical_state_is_reported(oracle_lib):
+    g, w = W.lumpy(n=(6, 6, 6), seed=1)
+    u0 = oracle_lib.prim2con(w)
+    u0[1, 2, 3, 4] = 2 * u0[0, 2, 3, 4]   # |M| > E
+    c = oracle_lib.make_cfg(g.n, g.dx)
+    with pytest.raises(FloatingPointError):
+        oracle_lib.run(c, u0, 1)
+
+
+@pytest.mark.parametrize("scheme,bc,mode", [(5, 0, "edge"), (7, 0, "edge"), (5, 1, "wrap"), (7, 1, "wrap")])
+def test_boundary_rule_equals_explicit_padding(oracle_lib, scheme, bc, mode):
+    """Outflow = zeroth-order extrapolation (ghost = edge cell), periodic = wrap:
+    L on N cells equals L of the explicitly padded (N + 2G) domain at the
+    original cells, whatever rule that larger domain uses at its own edges."""
+    G = (scheme + 1) // 2
+    g, w = W.lumpy(n=(9, 8, 7), seed=31, scheme=scheme)
+    w[1] = 0.3 * np.tanh(w[0] - 2)
+    w[3] = -0.2 * np.tanh(w[0] - 1)
+    u = oracle_lib.prim2con(w)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=(bc, bc, bc))
+    a = oracle_lib.alpha(c, u)
+    Lu = oracle_lib.L(c, u, a)
+    up = np.pad(u, ((0, 0), (G, G), (G, G), (G, G)), mode=mode)
+    cp = oracle_lib.make_cfg(tuple(k + 2 * G for k in g.n), g.dx, scheme=scheme, bc=(1 - bc,) * 3)
+    assert np.array_equal(oracle_lib.alpha(cp, up), a)
+    Lp = oracle_lib.L(cp, up, a)[:, G:-G, G:-G, G:-G]
+    assert np.array_equal(Lp, Lu)
+
+
+def test_cfl_rule_and_final_time(oracle_lib):
+    """dt = cfl * min_d dx_d / max_d alpha_d over directions with more than one
+    cell; the last step is shortened to land on t_end."""
+    g, w = W.lumpy(n=(10, 12, 1), seed=2)
+    c = oracle_lib.make_cfg(g.n, (0.1, 0.07, 5.0), cfl=0.35)
+    u0 = oracle_lib.prim2con(w)
+    a0 = oracle_lib.alpha(c, u0)
+    _, t, k, al, dts = oracle_lib.run(c, u0, 1, record=True)
+    assert dts[0] == 0.35 * 0.07 / max(a0[0], a0[1])
+    assert np.array_equal(al[0, 0], a0)
+    _, t, k = oracle_lib.run(c, u0, 1000, t=0.0, t_end=2.5 * dts[0])
+    assert k == 3 and t == 2.5 * dts[0]

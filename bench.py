@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark: FP64 WENO5/WENO7 + SSP-RK3 cell-updates/s on one GB300.
+
+Workload (headline): 3+1D ellipsoidal flow on a 256^3 grid, WENO7, FP64,
+synthetic seeded data shaped like the paper's Sec. 3 test (Gaussian ellipsoid
+e0 = 20, a, b, c = 2, 3, 4, linear axis-scaled velocity, n ~ e, p = e/3).
+A "step" is one full RK3 step (three fused stage kernels + two 1-thread
+bookkeeping kernels).  A cell-update is one interior cell advanced by one RK3
+step.  The state (3.6 GB of FP64 fields) is far larger than L2 (129 MB), so
+no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): every rank runs an
+independent replica of the grid (the single-grid path does not shard); value =
+all ranks' cell-updates / max-over-ranks time.
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FP64 work of one interior cell and one RK3 stage, counted on the
+# kernel's own formulation (FMA = 2 flops, add/mul/reciprocal/sqrt = 1):
+# 15 face-field reconstructions pairs (2 x 61 / 2 x 136 flops + 6 to combine),
+# flux differences 40, RK combine 20 (mean of 10/25/25), split fluxes 75,
+# primitive recovery 22, speeds 34.
+FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
+                        7: 15 * (2 * 136 + 6) + 40 + 20 + 75 + 22 + 34}
+# Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
+# stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
+HBM_BYTES_PER_CELL_UPDATE = 320
+SMS = 152
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.p = None
+        self.lines = []
+
+    def __enter__(self):
+        ids = []
+        try:
+            import torch
+            u = getattr(torch.cuda.get_device_properties(self.idx), "uuid", None)
+            if u is not None:
+                s = str(u)
+                ids.append(s if s.startswith("GPU-") else "GPU-" + s)
+        except Exception:
+            pass
+        ids.append(str(self.idx))
+        for i in ids:
+            try:
+                chk = subprocess.run(["nvidia-smi", "-i", i, "--query-gpu=clocks.sm", "--format=csv,noheader"],
+                                     capture_output=True, text=True, timeout=20)
+                if chk.returncode == 0:
+                    self.p = subprocess.Popen(["nvidia-smi", "-i", i, "--query-gpu=" + self.Q,
+                                               "--format=csv,noheader,nounits", "-lms", "200"],
+                                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                    break
+            except Exception:
+                continue
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=10)
+            except Exception:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(scheme, N=256):
+    import workloads as W
+    return W.ellipsoidal(N=N, scheme=scheme)
+
+
+def cpu_sample(scheme, N=256, sub=128):
+    """Central sub^3 block of the N^3 workload (same dx), outflow edges."""
+    g, w = workload(scheme, N)
+    lo = (N - sub) // 2
+    ws = np.ascontiguousarray(w[:, lo:lo + sub, lo:lo + sub, lo:lo + sub])
+    import workloads as W
+    gs = W.Grid(n=(sub, sub, sub), dx=g.dx, origin=tuple(o + lo * d for o, d in zip(g.origin, g.dx)),
+                bc=(0, 0, 0), scheme=scheme, cfl=g.cfl, name="ellipsoidal-subblock")
+    return gs, ws
+
+
+def time_oracle(scheme, steps, sub):
+    import oracle
+    oracle.build()
+    gs, ws = cpu_sample(scheme, sub=sub)
+    c = oracle.make_cfg(gs.n, gs.dx, scheme=scheme, cfl=gs.cfl)
+    u0 = oracle.prim2con(ws)
+    t0 = time.perf_counter()
+    oracle.run(c, u0, steps)
+    dt = time.perf_counter() - t0
+    return gs.cells * steps / dt, dt, oracle.max_threads()
+
+
+def reference_arm(args):
+    """The oracle (plain FP64 C, OpenMP over the host cores) on a bounded
+    sample of the same workload: each step = one RK3 step of the central
+    48^3 block of the 256^3 grid."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sub = 48
+    import oracle
+    oracle.build()
+    gs, ws = cpu_sample(args.scheme, sub=sub)
+    c = oracle.make_cfg(gs.n, gs.dx, scheme=args.scheme, cfl=gs.cfl)
+    u = oracle.prim2con(ws)
+    for _ in range(args.warmup):
+        u = oracle.run(c, u, 1)[0]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = oracle.run(c, u, 1)[0]
+    dt = time.perf_counter() - t0
+    v = gs.cells * args.steps / dt
+    line = {"impl": "reference", "metric": "FP64 WENO%d cell-updates/s (256^3 ellipsoidal)" % args.scheme,
+            "value": v, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ellipsoidal-256^3-WENO%d (oracle sample: central %d^3 block per step)"
+                       % (args.scheme, sub)},
+            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "central %d^3 block of the 256^3 workload, %d RK3 steps" % (sub, args.steps)},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scheme", type=int, default=7, choices=[5, 7])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the WENO5 and e2e extras")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_1604_03360_gb300 import Hydro
+    from paper_1604_03360_gb300 import build as B
+    B.build()
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    g, w = workload(args.scheme)
+    cells = g.cells
+    h = Hydro.from_grid(g, stream=stream)
+    w_dev = torch.from_numpy(w).to(dev)
+    h.set_primitive(w_dev)
+    h.step(args.warmup)
+    torch.cuda.synchronize()
+    h.sync()
+
+    # ---- timed region: K steps, per-kernel CUDA events on the launching stream
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        kms = h.profile_step(args.steps)
+        e1.record(stream)
+        barrier()
+    el = e0.elapsed_time(e1) / 1e3
+    h.sync()
+    t_all = torch.tensor([el], device=dev)
+    if pg is not None:
+        pg.all_reduce(t_all, op=pg.ReduceOp.MAX)
+    tmax = float(t_all.item())
+    value = world * cells * args.steps / tmax
+    stage_ms = float(kms[1:4].sum()) / (3 * args.steps)
+    flops = FLOPS_PER_CELL_STAGE[args.scheme] * cells
+    achieved = flops / (stage_ms * 1e-3) / 1e12
+    peaks = load_peaks()
+    from paper_1604_03360_gb300 import measure_fp64_peak
+    fp64_peak = 2.0 * measure_fp64_peak(stream) / 1e12   # TFLOP/s, FMA = 2 flops
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_achieved = HBM_BYTES_PER_CELL_UPDATE * (cells * args.steps / el) / 1e9
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_extra:
+        u_host = torch.empty((5,) + w.shape[1:], dtype=torch.float64).pin_memory()
+        h.get_state(u_host)
+        out_host = torch.empty_like(u_host).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h.set_state(u_host)
+            h.step(1)
+            h.get_state(out_host)
+        barrier()
+        te = time.perf_counter() - t0
+        t_e = torch.tensor([te], device=dev)
+        if pg is not None:
+            pg.all_reduce(t_e, op=pg.ReduceOp.MAX)
+        nbytes = 5 * cells * 8
+        e2e = {"value": world * cells * args.steps / float(t_e.item()), "unit": "cell-updates/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    extra = {}
+    if not args.no_extra and args.scheme == 7:
+        g5, w5 = workload(5)
+        h5 = Hydro.from_grid(g5, stream=stream)
+        h5.set_primitive(torch.from_numpy(w5).to(dev))
+        h5.step(2)
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        k5 = h5.profile_step(args.steps)
+        a1.record(stream)
+        barrier()
+        el5 = a0.elapsed_time(a1) / 1e3
+        st5 = float(k5[1:4].sum()) / (3 * args.steps)
+        extra["weno5_256"] = {"value": cells * args.steps / el5, "unit": "cell-updates/s",
+                              "ms_per_step": 1e3 * el5 / args.steps, "stage_kernel_ms": st5,
+                              "fp64_tflops": FLOPS_PER_CELL_STAGE[5] * cells / (st5 * 1e-3) / 1e12,
+                              "fp64_frac": FLOPS_PER_CELL_STAGE[5] * cells / (st5 * 1e-3) / 1e12 / fp64_peak,
+                              "hbm_frac": HBM_BYTES_PER_CELL_UPDATE * cells * args.steps / el5 / 1e9 / hbm_peak}
+        h5.close()
+    h.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, secs, cores = time_oracle(args.scheme, 1, 128 if args.scheme == 5 else 96)
+        cpu = {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+               "sample": "1 RK3 step of the central %d^3 block of the 256^3 workload (%.1f s)"
+               % (128 if args.scheme == 5 else 96, secs)}
+
+    if rank == 0:
+        line = {
+            "metric": "FP64 WENO%d cell-updates/s at 256^3 (ellipsoidal flow); %%HBM peak" % args.scheme,
+            "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ellipsoidal-256^3-WENO%d" % args.scheme, "grid": [256, 256, 256],
+                       "steps_per_timing": args.steps, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state 3.6 GB >> 129 MB L2: no flush needed"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak, "traffic": None,
+                         "kernel": "stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,
+                         "peak_source": "FP64 FMA probe kernel measured in this run (hydro_measure_fp64_peak); "
+                                        "MEASURED_PEAKS.json has no FP64 figure; nominal 152 SM x 2 DFMA/clk x "
+                                        "2 flop x 2.07 GHz = 1.259"},
+            "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak, "frac": hbm_achieved / hbm_peak,
+                    "bytes_per_cell_update": HBM_BYTES_PER_CELL_UPDATE, "peak_source": "MEASURED_PEAKS.json"},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "gpu_launches": 5 * args.steps + 1,
+            "kernel_ms_per_step": {"step_begin": kms[0] / args.steps, "stage1": kms[1] / args.steps,
+                                   "stage2": kms[2] / args.steps, "stage3": kms[3] / args.steps,
+                                   "step_end": kms[4] / args.steps},
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

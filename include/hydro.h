@@ -1,0 +1,155 @@
+/*
+ * hydro.h -- C ABI of the GB300 (sm_103a) FP64 WENO5/WENO7 + RK3 solver for
+ * 3+1D ideal relativistic hydrodynamics, after Sikorski et al.,
+ * "Relativistic hydrodynamics on graphics processing units" (arXiv:1604.03360).
+ *
+ * The operation (paper, Sec. 1):
+ *   Eq. 1   du/dt + sum_i d f_i(u)/dx_i = 0 with u = (E, M_x, M_y, M_z, R):
+ *           energy density T^00, momentum densities T^0i and the conserved
+ *           charge density n*gamma of an ideal fluid with p = cs2 * e.
+ *   Eq. 2   L(u) = sum_i (F_i(x - e_i/2) - F_i(x + e_i/2)) / |e_i| on a
+ *           Cartesian grid; F at the half-cell faces from finite-difference
+ *           WENO of order 5 or 7 (Sec. 1.2) on Lax-Friedrichs split fluxes.
+ *   Sec. 1  third-order Runge-Kutta in time (SSP / Shu-Osher form).
+ * Readings where the paper is silent: component-wise WENO on f^+- =
+ * (f +- alpha_d u)/2 with alpha_d the largest characteristic speed over the
+ * grid (recomputed from every stage's input); epsilon = weno_eps in
+ * omega_k ~ d_k / (eps + beta_k)^2; dt = cfl * min_d dx_d / max_d alpha_d over
+ * directions with more than one cell, clipped so that t lands on t_end;
+ * outflow = copy of the edge cell into the ghost cells; periodic = wrap;
+ * directions with one cell contribute no flux difference.
+ *
+ * Conventions for every entry point:
+ *   - Fields are FP64 structure-of-arrays: field f (0..4) of a state starts at
+ *     ptr + f * field_stride and holds nz*ny*nx values, x fastest.
+ *     field_stride >= nx*ny*nz (elements, not bytes).
+ *   - mem = HYDRO_MEM_HOST: ptr is host memory (pageable or pinned);
+ *     mem = HYDRO_MEM_DEVICE: ptr is device memory on the handle's device.
+ *     The caller keeps ownership of every pointer it passes.
+ *   - All work is ordered on the CUDA stream given at creation (NULL = the
+ *     legacy default stream).  Calls that return data to the host synchronise
+ *     that stream; all others are asynchronous.
+ *   - Every call returns a hydro_status; no C++ exception crosses the ABI and
+ *     no kernel traps.  Device-side problems (an unphysical state such as
+ *     E <= 0 or |M| >= E, or a NaN) are recorded on the device and reported
+ *     by the next synchronising call (hydro_get_state, hydro_sync), which
+ *     then returns HYDRO_ERR_UNPHYSICAL.  hydro_last_error() describes the
+ *     most recent failure of a handle.
+ *   - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HYDRO_OK = 0,
+    HYDRO_ERR_INVALID_ARG = 1,
+    HYDRO_ERR_CUDA = 2,
+    HYDRO_ERR_OOM = 3,
+    HYDRO_ERR_UNPHYSICAL = 4,
+    HYDRO_ERR_TIMEOUT = 5,
+    HYDRO_ERR_STATE = 6
+} hydro_status;
+
+typedef enum { HYDRO_WENO5 = 5, HYDRO_WENO7 = 7 } hydro_scheme;
+typedef enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1 } hydro_bc;
+typedef enum { HYDRO_MEM_HOST = 0, HYDRO_MEM_DEVICE = 1 } hydro_mem;
+
+/* Problem definition (Eq. 2 grid, Sec. 1.2 scheme, boundary rule). */
+typedef struct {
+    int32_t n[3];       /* interior cells nx, ny, nz (>= 1; a direction with
+                           n = 1 is inactive; a periodic active direction
+                           needs n >= 4 for WENO7, >= 3 for WENO5) */
+    int32_t scheme;     /* HYDRO_WENO5 or HYDRO_WENO7 */
+    int32_t bc[3];      /* hydro_bc per direction */
+    int32_t reserved;   /* must be 0 */
+    double dx[3];       /* cell sizes |e_i| > 0 */
+    double origin[3];   /* lower corner of the box (informational) */
+    double cs2;         /* EOS p = cs2 * e, 0 < cs2 < 1 (1/3 in the paper's tests) */
+    double cfl;         /* dt = cfl * min dx / max alpha when dt_fixed <= 0 */
+    double dt_fixed;    /* > 0: constant time step */
+    double weno_eps;    /* WENO epsilon, > 0 (1e-6) */
+} hydro_config;
+
+typedef struct hydro_s hydro_t;
+
+/* Create a solver for one grid.  The library allocates and owns all device
+ * buffers (three conserved states, three primitive scratch states and a small
+ * control block, about 27 doubles per cell).  stream: a cudaStream_t (may be
+ * NULL).  Errors: INVALID_ARG for a bad config or NULL out, OOM, CUDA. */
+hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out);
+
+/* Release every resource of h (NULL is a no-op). */
+hydro_status hydro_destroy(hydro_t* h);
+
+/* Load the conserved state u = (E, M_x, M_y, M_z, R) (Eq. 1) at time t and
+ * reset the step counter.  Also recovers the primitives and the characteristic
+ * speeds of the new state on the device.  Asynchronous. */
+hydro_status hydro_set_state(hydro_t* h, const double* u, int64_t field_stride, int32_t mem, double t);
+
+/* Load primitives (e, v_x, v_y, v_z, n) and convert them to the conserved
+ * state on the device: E = (e+p) g^2 - p, M = (e+p) g^2 v, R = n g, with
+ * g^2 = 1/(1 - v^2), p = cs2 e.  Requires |v| < 1, e > 0. */
+hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stride, int32_t mem, double t);
+
+/* Advance by up to nsteps RK3 steps (Sec. 1).  If t_end >= 0 the last step is
+ * shortened so that t lands on t_end and later steps do nothing.  Each step is
+ * one replay of a captured CUDA graph: a 1-thread step-begin kernel (dt from
+ * the current characteristic speeds), three fused stage kernels (Eq. 2 + RK
+ * combine + speeds of the new state) and a 1-thread step-end kernel.
+ * Asynchronous; no host synchronisation. */
+hydro_status hydro_step(hydro_t* h, int32_t nsteps, double t_end);
+
+/* Copy the current conserved state out (synchronises the stream).  t and
+ * step (either may be NULL) receive the simulation time and the number of
+ * steps taken since the last set_state.  Returns HYDRO_ERR_UNPHYSICAL if a
+ * kernel met an unphysical state since the last set_state (the state is still
+ * copied). */
+hydro_status hydro_get_state(hydro_t* h, double* u, int64_t field_stride, int32_t mem, double* t, int64_t* step);
+
+/* Copy the primitives (e, v_x, v_y, v_z, n) of the current state out
+ * (synchronises the stream). */
+hydro_status hydro_get_primitive(hydro_t* h, double* w, int64_t field_stride, int32_t mem);
+
+/* Synchronise the stream and report deferred device errors. */
+hydro_status hydro_sync(hydro_t* h);
+
+/* Largest characteristic speed per direction of the current state (alpha_d
+ * of the global Lax-Friedrichs splitting) and the last time step taken.
+ * Synchronises. */
+hydro_status hydro_get_speeds(hydro_t* h, double alpha[3], double* last_dt);
+
+/* Text of the last error of h (never NULL; "" if none).  Valid until the next
+ * call on h.  hydro_last_error(NULL) describes the last failed hydro_create. */
+const char* hydro_last_error(hydro_t* h);
+
+/* Advance like hydro_step, but launch the five kernels of every step directly
+ * (no graph) with CUDA events between them on the handle's stream, and
+ * return in kernel_ms[5] the summed device time of: step-begin, stage 1,
+ * stage 2, stage 3, step-end.  Synchronises once per step.  For measurement
+ * only; the numerical result equals hydro_step's bit for bit. */
+hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double kernel_ms[5]);
+
+/* Device pointer of the current conserved state (5 fields, stride
+ * hydro_field_stride()) for zero-copy readers; owned by h. */
+const double* hydro_state_device_ptr(hydro_t* h);
+int64_t hydro_field_stride(hydro_t* h);
+
+/* Measurement helper, not part of the paper's method: times a kernel of
+ * independent FP64 FMA chains on every SM (on `stream`, synchronising it) and
+ * returns the FP64 FMA issue rate in FMA/s -- the roofline denominator of the
+ * FP64-bound stage kernel.  Allocates and frees a small scratch buffer. */
+hydro_status hydro_measure_fp64_peak(void* stream, double* fma_per_second);
+
+/* Library version string. */
+const char* hydro_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYDRO_H */

@@ -1,0 +1,223 @@
+"""ctypes binding of the C ABI in include/hydro.h.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  There is no CPU fallback -- if libhydro.so is missing or fails to
+load, every entry point raises.  PyTorch supplies device memory and streams.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhydro.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_UNPHYSICAL, ERR_TIMEOUT, ERR_STATE = range(7)
+MEM_HOST, MEM_DEVICE = 0, 1
+WENO5, WENO7 = 5, 7
+BC_OUTFLOW, BC_PERIODIC = 0, 1
+
+_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNPHYSICAL", 5: "TIMEOUT", 6: "STATE"}
+
+
+class HydroError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hydro error %s (%d): %s" % (_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class HydroConfig(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 3),
+        ("scheme", ctypes.c_int32),
+        ("bc", ctypes.c_int32 * 3),
+        ("reserved", ctypes.c_int32),
+        ("dx", ctypes.c_double * 3),
+        ("origin", ctypes.c_double * 3),
+        ("cs2", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("dt_fixed", ctypes.c_double),
+        ("weno_eps", ctypes.c_double),
+    ]
+
+
+def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
+                origin=(0.0, 0.0, 0.0)):
+    c = HydroConfig()
+    for i in range(3):
+        c.n[i] = int(n[i])
+        c.bc[i] = int(bc[i])
+        c.dx[i] = float(dx[i])
+        c.origin[i] = float(origin[i])
+    c.scheme = int(scheme)
+    c.reserved = 0
+    c.cs2 = float(cs2)
+    c.cfl = float(cfl)
+    c.dt_fixed = float(dt_fixed)
+    c.weno_eps = float(eps)
+    return c
+
+
+_lib = None
+
+
+def lib():
+    """Load libhydro.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libhydro.so is not built (run paper_1604_03360_gb300/build.py); "
+                           "there is no fallback implementation")
+    L = ctypes.CDLL(LIB_PATH)
+    P, vp, i32, i64, d = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "hydro_create": ([P(HydroConfig), vp, P(vp)], i32),
+        "hydro_destroy": ([vp], i32),
+        "hydro_set_state": ([vp, vp, i64, i32, d], i32),
+        "hydro_set_primitive": ([vp, vp, i64, i32, d], i32),
+        "hydro_step": ([vp, i32, d], i32),
+        "hydro_get_state": ([vp, vp, i64, i32, P(d), P(i64)], i32),
+        "hydro_get_primitive": ([vp, vp, i64, i32], i32),
+        "hydro_sync": ([vp], i32),
+        "hydro_get_speeds": ([vp, P(d), P(d)], i32),
+        "hydro_profile_step": ([vp, i32, d, P(d)], i32),
+        "hydro_last_error": ([vp], ctypes.c_char_p),
+        "hydro_state_device_ptr": ([vp], vp),
+        "hydro_field_stride": ([vp], i64),
+        "hydro_version": ([], ctypes.c_char_p),
+        "hydro_measure_fp64_peak": ([vp, P(d)], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def as_buffer(x, writable=False):
+    """(pointer, field_stride, mem) of a (5, ...) float64 array or tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("need a C-contiguous float64 numpy array")
+        if writable and not x.flags["WRITEABLE"]:
+            raise ValueError("array is read-only")
+        return ctypes.c_void_p(x.ctypes.data), x[0].size, MEM_HOST
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("need a numpy array or a torch tensor")
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise ValueError("need a contiguous float64 tensor")
+    return ctypes.c_void_p(x.data_ptr()), x[0].numel(), (MEM_DEVICE if x.is_cuda else MEM_HOST)
+
+
+def measure_fp64_peak(stream=None):
+    """FP64 FMA/s of the current device (measured by a probe kernel)."""
+    L = lib()
+    r = ctypes.c_double()
+    rc = L.hydro_measure_fp64_peak(_stream_handle(stream), ctypes.byref(r))
+    if rc:
+        raise HydroError(rc, "FP64 peak probe failed")
+    return r.value
+
+
+class Hydro:
+    """One grid of the FP64 WENO5/WENO7 + SSP-RK3 solver (hydro_t)."""
+
+    def __init__(self, n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
+                 origin=(0.0, 0.0, 0.0), stream=None):
+        self._L = lib()
+        self.cfg = make_config(n, dx, scheme, bc, cs2, cfl, dt_fixed, eps, origin)
+        self.n = tuple(int(k) for k in n)
+        self.shape = (5, self.n[2], self.n[1], self.n[0])
+        h = ctypes.c_void_p()
+        rc = self._L.hydro_create(ctypes.byref(self.cfg), _stream_handle(stream), ctypes.byref(h))
+        if rc:
+            raise HydroError(rc, self._L.hydro_last_error(None).decode())
+        self._h = h
+        self.t = 0.0
+        self.steps = 0
+
+    @classmethod
+    def from_grid(cls, g, stream=None):
+        """Create from a workloads.Grid description."""
+        return cls(g.n, g.dx, scheme=g.scheme, bc=g.bc, cs2=g.cs2, cfl=g.cfl, eps=g.eps, origin=g.origin,
+                   stream=stream)
+
+    def _check(self, rc):
+        if rc:
+            raise HydroError(rc, self._L.hydro_last_error(self._h).decode())
+
+    def set_state(self, u, t=0.0):
+        p, fs, mem = as_buffer(u)
+        self._check(self._L.hydro_set_state(self._h, p, fs, mem, float(t)))
+        self.t, self.steps = float(t), 0
+
+    def set_primitive(self, w, t=0.0):
+        p, fs, mem = as_buffer(w)
+        self._check(self._L.hydro_set_primitive(self._h, p, fs, mem, float(t)))
+        self.t, self.steps = float(t), 0
+
+    def step(self, nsteps=1, t_end=-1.0):
+        self._check(self._L.hydro_step(self._h, int(nsteps), float(t_end)))
+
+    def profile_step(self, nsteps=1, t_end=-1.0):
+        """Per-kernel device ms (step-begin, stage 1..3, step-end) summed over nsteps."""
+        ms = (ctypes.c_double * 5)()
+        self._check(self._L.hydro_profile_step(self._h, int(nsteps), float(t_end), ms))
+        return np.array(ms[:])
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, fs, mem = as_buffer(out, writable=True)
+        t = ctypes.c_double()
+        k = ctypes.c_int64()
+        self._check(self._L.hydro_get_state(self._h, p, fs, mem, ctypes.byref(t), ctypes.byref(k)))
+        self.t, self.steps = t.value, k.value
+        return out
+
+    def get_primitive(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, fs, mem = as_buffer(out, writable=True)
+        self._check(self._L.hydro_get_primitive(self._h, p, fs, mem))
+        return out
+
+    def sync(self):
+        self._check(self._L.hydro_sync(self._h))
+
+    def speeds(self):
+        a = (ctypes.c_double * 3)()
+        dt = ctypes.c_double()
+        self._check(self._L.hydro_get_speeds(self._h, a, ctypes.byref(dt)))
+        return np.array(a[:]), dt.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.hydro_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

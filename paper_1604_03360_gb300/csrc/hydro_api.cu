@@ -1,0 +1,351 @@
+// hydro_api.cu -- the C ABI of include/hydro.h for one grid: buffers, the
+// device control block, the captured per-step CUDA graph and the copies.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "hydro_common.cuh"
+
+using namespace hydro;
+
+struct hydro_s {
+    hydro_config cfg;
+    int R = 3;
+    int dev = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;   // caller's stream
+    cudaStream_t cap = nullptr;      // private stream used only for graph capture
+    long long ncell = 0, fs = 0;
+    double* buf = nullptr;
+    double* U[3] = {nullptr, nullptr, nullptr};
+    double* W[3] = {nullptr, nullptr, nullptr};
+    Ctl* ctl = nullptr;
+    Ctl* hctl = nullptr;             // pinned mirror for read-back
+    cudaGraphExec_t exec = nullptr;
+    StageLaunch L{};
+    int zc = 0;
+    bool have_state = false;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static hydro_status fail(hydro_t* h, hydro_status s, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+static hydro_status cuda_fail(hydro_t* h, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? HYDRO_ERR_OOM : HYDRO_ERR_CUDA, m);
+}
+
+#define CK(h, call, where)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, where); \
+    } while (0)
+
+static StageArgs stage_args(hydro_t* h, int stage)
+{
+    StageArgs a{};
+    const int in = stage - 1;                       // U0 -> U1 -> U2 -> U0
+    a.u_in = h->U[in];
+    a.w_in = h->W[in];
+    a.u_n = h->U[0];
+    a.u_out = stage == 3 ? h->U[0] : h->U[stage];
+    a.w_out = stage == 3 ? h->W[0] : h->W[stage];
+    a.fs = h->fs;
+    a.nx = h->cfg.n[0];
+    a.ny = h->cfg.n[1];
+    a.nz = h->cfg.n[2];
+    a.zc = h->zc;
+    for (int d = 0; d < 3; ++d) {
+        a.bc[d] = h->cfg.bc[d];
+        a.act[d] = h->cfg.n[d] > 1;
+        a.hdx[d] = 0.5 / h->cfg.dx[d];
+    }
+    a.cs2 = h->cfg.cs2;
+    a.eps_s = h->cfg.weno_eps * (h->R == 3 ? SchemeConst<3>::eps_scale : SchemeConst<4>::eps_scale);
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    a.ca = ca[in];
+    a.cb = cb[in];
+    a.alpha_in = stage == 1 ? h->ctl->a_cur : (stage == 2 ? h->ctl->a_s1 : h->ctl->a_s2);
+    a.alpha_out = stage == 1 ? h->ctl->a_s1 : (stage == 2 ? h->ctl->a_s2 : h->ctl->a_next);
+    a.dt = &h->ctl->dt;
+    a.status = &h->ctl->status;
+    a.bad_cell = &h->ctl->bad_cell;
+    return a;
+}
+
+static cudaError_t enqueue_step(hydro_t* h, cudaStream_t s)
+{
+    const dim3 grid((h->cfg.n[0] + h->L.tx - 1) / h->L.tx, (h->cfg.n[1] + h->L.ty - 1) / h->L.ty,
+                    (h->cfg.n[2] + h->zc - 1) / h->zc);
+    step_begin_kernel<<<1, 1, 0, s>>>(h->ctl, step_params(h->cfg));
+    for (int st = 1; st <= 3; ++st) {
+        const StageArgs a = stage_args(h, st);
+        h->L.fn<<<grid, h->L.tx * h->L.ty, h->L.smem, s>>>(a);
+    }
+    step_end_kernel<<<1, 1, 0, s>>>(h->ctl);
+    return cudaGetLastError();
+}
+
+static hydro_status build_graph(hydro_t* h)
+{
+    if (h->exec) return HYDRO_OK;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "capture begin");
+    cudaError_t e1 = enqueue_step(h, h->cap);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e1 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, e1, "capture step");
+    }
+    CK(h, e2, "capture end");
+    cudaError_t e3 = cudaGraphInstantiate(&h->exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e3, "graph instantiate");
+    return HYDRO_OK;
+}
+
+static int blocks_for(long long n) { long long b = (n + 255) / 256; return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b)); }
+
+extern "C" {
+
+const char* hydro_version(void) { return "hydro-gb300 1.0 (sm_103a, FP64 WENO5/7 + SSP-RK3)"; }
+
+hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
+{
+    if (!out) return fail(nullptr, HYDRO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    const std::string why = check_config(cfg);
+    if (!why.empty()) return fail(nullptr, HYDRO_ERR_INVALID_ARG, why);
+    hydro_t* h = new (std::nothrow) hydro_t();
+    if (!h) return fail(nullptr, HYDRO_ERR_OOM, "host allocation failed");
+    h->cfg = *cfg;
+    h->R = cfg->scheme == HYDRO_WENO5 ? 3 : 4;
+    h->stream = (cudaStream_t)stream;
+    cudaError_t e;
+    auto bail = [&](hydro_status s) {
+        g_create_err = h->err;
+        hydro_destroy(h);
+        return s;
+    };
+    if ((e = cudaGetDevice(&h->dev)) != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
+    if ((e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "device attribute"));
+    if ((e = stage_launch_info(h->R, &h->L)) != cudaSuccess) return bail(cuda_fail(h, e, "stage kernel setup"));
+    h->ncell = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
+    h->fs = (h->ncell + 31) / 32 * 32;   // 256-byte aligned fields
+    h->zc = pick_zc(cfg->n[0], cfg->n[1], cfg->n[2], h->L, h->sms);
+    const size_t bytes = sizeof(double) * (size_t)h->fs * 27;
+    if ((e = cudaMalloc(&h->buf, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "state buffers"));
+    for (int i = 0; i < 3; ++i) {
+        h->U[i] = h->buf + (size_t)h->fs * 5 * i;
+        h->W[i] = h->buf + (size_t)h->fs * (15 + 4 * i);
+    }
+    if ((e = cudaMemsetAsync(h->buf, 0, bytes, h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+    if ((e = cudaMalloc(&h->ctl, sizeof(Ctl))) != cudaSuccess) return bail(cuda_fail(h, e, "control block"));
+    if ((e = cudaMallocHost(&h->hctl, sizeof(Ctl))) != cudaSuccess) return bail(cuda_fail(h, e, "pinned control"));
+    if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "capture stream"));
+    reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 0.0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(h, e, "reset"));
+    hydro_status s = build_graph(h);
+    if (s != HYDRO_OK) return bail(s);
+    *out = h;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_destroy(hydro_t* h)
+{
+    if (!h) return HYDRO_OK;
+    if (h->stream || h->buf) cudaStreamSynchronize(h->stream);
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->buf) cudaFree(h->buf);
+    if (h->ctl) cudaFree(h->ctl);
+    if (h->hctl) cudaFreeHost(h->hctl);
+    delete h;
+    return HYDRO_OK;
+}
+
+const char* hydro_last_error(hydro_t* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+static hydro_status copy_fields(hydro_t* h, double* dst, long long dstride, const double* src, long long sstride,
+                                int nf, cudaMemcpyKind kind)
+{
+    for (int f = 0; f < nf; ++f)
+        CK(h, cudaMemcpyAsync(dst + f * dstride, src + f * sstride, sizeof(double) * h->ncell, kind, h->stream),
+           "copy");
+    return HYDRO_OK;
+}
+
+static hydro_status check_io(hydro_t* h, const void* p, int64_t stride, int32_t mem)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (!p) return fail(h, HYDRO_ERR_INVALID_ARG, "NULL data pointer");
+    if (stride < h->ncell) return fail(h, HYDRO_ERR_INVALID_ARG, "field_stride smaller than the cell count");
+    if (mem != HYDRO_MEM_HOST && mem != HYDRO_MEM_DEVICE) return fail(h, HYDRO_ERR_INVALID_ARG, "mem must be 0 or 1");
+    return HYDRO_OK;
+}
+
+static hydro_status after_load(hydro_t* h, double t)
+{
+    reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
+    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl);
+    CK(h, cudaGetLastError(), "prepare");
+    h->have_state = true;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_set_state(hydro_t* h, const double* u, int64_t field_stride, int32_t mem, double t)
+{
+    hydro_status s = check_io(h, u, field_stride, mem);
+    if (s) return s;
+    s = copy_fields(h, h->U[0], h->fs, u, field_stride, 5,
+                    mem == HYDRO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
+    if (s) return s;
+    return after_load(h, t);
+}
+
+hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stride, int32_t mem, double t)
+{
+    hydro_status s = check_io(h, w, field_stride, mem);
+    if (s) return s;
+    const double* src = w;
+    long long ss = field_stride;
+    if (mem == HYDRO_MEM_HOST) {   // stage through U1 (scratch between steps)
+        s = copy_fields(h, h->U[1], h->fs, w, field_stride, 5, cudaMemcpyHostToDevice);
+        if (s) return s;
+        src = h->U[1];
+        ss = h->fs;
+    }
+    reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
+    prim2con_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(src, ss, h->U[0], h->fs, h->ncell, h->cfg.cs2, h->ctl);
+    CK(h, cudaGetLastError(), "prim2con");
+    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl);
+    CK(h, cudaGetLastError(), "prepare");
+    h->have_state = true;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_step(hydro_t* h, int32_t nsteps, double t_end)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (nsteps < 0) return fail(h, HYDRO_ERR_INVALID_ARG, "nsteps < 0");
+    if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
+    set_t_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t_end);
+    CK(h, cudaGetLastError(), "set t_end");
+    for (int i = 0; i < nsteps; ++i) CK(h, cudaGraphLaunch(h->exec, h->stream), "graph launch");
+    return HYDRO_OK;
+}
+
+hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double kernel_ms[5])
+{
+    if (!h || !kernel_ms) return HYDRO_ERR_INVALID_ARG;
+    if (nsteps < 0) return fail(h, HYDRO_ERR_INVALID_ARG, "nsteps < 0");
+    if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
+    for (int i = 0; i < 5; ++i) kernel_ms[i] = 0.0;
+    cudaEvent_t ev[6];
+    for (int i = 0; i < 6; ++i) CK(h, cudaEventCreate(&ev[i]), "event create");
+    hydro_status st = HYDRO_OK;
+    set_t_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t_end);
+    const dim3 grid((h->cfg.n[0] + h->L.tx - 1) / h->L.tx, (h->cfg.n[1] + h->L.ty - 1) / h->L.ty,
+                    (h->cfg.n[2] + h->zc - 1) / h->zc);
+    for (int s = 0; s < nsteps && st == HYDRO_OK; ++s) {
+        cudaEventRecord(ev[0], h->stream);
+        step_begin_kernel<<<1, 1, 0, h->stream>>>(h->ctl, step_params(h->cfg));
+        cudaEventRecord(ev[1], h->stream);
+        for (int k = 1; k <= 3; ++k) {
+            const StageArgs a = stage_args(h, k);
+            h->L.fn<<<grid, h->L.tx * h->L.ty, h->L.smem, h->stream>>>(a);
+            cudaEventRecord(ev[1 + k], h->stream);
+        }
+        step_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl);
+        cudaEventRecord(ev[5], h->stream);
+        cudaError_t e = cudaEventSynchronize(ev[5]);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            st = cuda_fail(h, e, "profiled step");
+            break;
+        }
+        for (int i = 0; i < 5; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            kernel_ms[i] += ms;
+        }
+    }
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+    return st;
+}
+
+static hydro_status read_ctl(hydro_t* h)
+{
+    CK(h, cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream), "read control");
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+    if (h->hctl->status) {
+        char b[160];
+        snprintf(b, sizeof b, "unphysical state (E <= 0, |M| >= E or NaN) first seen at cell %lld",
+                 (long long)h->hctl->bad_cell);
+        return fail(h, HYDRO_ERR_UNPHYSICAL, b);
+    }
+    return HYDRO_OK;
+}
+
+hydro_status hydro_sync(hydro_t* h)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    return read_ctl(h);
+}
+
+hydro_status hydro_get_state(hydro_t* h, double* u, int64_t field_stride, int32_t mem, double* t, int64_t* step)
+{
+    hydro_status s = check_io(h, u, field_stride, mem);
+    if (s) return s;
+    s = copy_fields(h, u, field_stride, h->U[0], h->fs, 5,
+                    mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+    if (s) return s;
+    s = read_ctl(h);
+    if (t) *t = h->hctl->t;
+    if (step) *step = h->hctl->step;
+    return s;
+}
+
+hydro_status hydro_get_primitive(hydro_t* h, double* w, int64_t field_stride, int32_t mem)
+{
+    hydro_status s = check_io(h, w, field_stride, mem);
+    if (s) return s;
+    state_to_prim_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->fs, h->U[1], h->fs, h->ncell,
+                                                                      h->cfg.cs2);
+    CK(h, cudaGetLastError(), "state_to_prim");
+    s = copy_fields(h, w, field_stride, h->U[1], h->fs, 5,
+                    mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+    if (s) return s;
+    return read_ctl(h);
+}
+
+hydro_status hydro_get_speeds(hydro_t* h, double alpha[3], double* last_dt)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    hydro_status s = read_ctl(h);
+    if (alpha)
+        for (int d = 0; d < 3; ++d) {
+            unsigned long long b = h->hctl->a_cur[d];
+            double v;
+            memcpy(&v, &b, sizeof v);
+            alpha[d] = v;
+        }
+    if (last_dt) *last_dt = h->hctl->last_dt;
+    return s;
+}
+
+const double* hydro_state_device_ptr(hydro_t* h) { return h ? h->U[0] : nullptr; }
+int64_t hydro_field_stride(hydro_t* h) { return h ? h->fs : 0; }
+
+}  // extern "C"

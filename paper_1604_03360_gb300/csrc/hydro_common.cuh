@@ -1,0 +1,103 @@
+// hydro_common.cuh -- host/device pieces shared by the library's translation
+// units: the device control block, small bookkeeping kernels and launch
+// helpers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+
+#include "../../include/hydro.h"
+#include "stage_kernel.cuh"
+
+namespace hydro {
+
+// Device-resident control block of one grid (or one event of a batch).
+// Speeds are stored as IEEE bit patterns so atomicMax on them is exact.
+struct Ctl {
+    unsigned long long a_cur[3];   // speeds of the current state u^n
+    unsigned long long a_s1[3];    // speeds of the stage-1 output
+    unsigned long long a_s2[3];    // speeds of the stage-2 output
+    unsigned long long a_next[3];  // speeds of the stage-3 output
+    double dt;                     // step being taken (0: nothing to do)
+    double t;                      // simulation time
+    double t_end;                  // < 0: unlimited
+    double last_dt;
+    long long step;
+    long long bad_cell;
+    int status;
+    int pad_;
+};
+
+struct StepParams {
+    double cfl, dt_fixed, mindx;
+    int actmask;                   // bit d: axis d takes part in dt
+};
+
+// dt from the speeds of u^n, clipped to t_end; zero the accumulation slots.
+__global__ void step_begin_kernel(Ctl* c, StepParams sp);
+// commit the step: speeds of u^{n+1} become current, advance t.
+__global__ void step_end_kernel(Ctl* c);
+__global__ void set_t_end_kernel(Ctl* c, double t_end);
+__global__ void reset_ctl_kernel(Ctl* c, double t);
+// primitives and speeds of a state (after set_state)
+__global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c);
+// primitives (e, v, n) -> conserved
+__global__ void prim2con_kernel(const double* wp, long long ws, double* u, long long fs, long long n, double cs2,
+                                Ctl* c);
+// conserved -> (e, v, n)
+__global__ void state_to_prim_kernel(const double* u, long long fs, double* out, long long os, long long n,
+                                     double cs2);
+
+inline StepParams step_params(const hydro_config& cfg)
+{
+    StepParams sp;
+    sp.cfl = cfg.cfl;
+    sp.dt_fixed = cfg.dt_fixed;
+    int mask = 0;
+    for (int d = 0; d < 3; ++d)
+        if (cfg.n[d] > 1) mask |= 1 << d;
+    if (!mask) mask = 7;
+    double m = INFINITY;
+    for (int d = 0; d < 3; ++d)
+        if (mask & (1 << d)) m = fmin(m, cfg.dx[d]);
+    sp.mindx = m;
+    sp.actmask = mask;
+    return sp;
+}
+
+// validate a config; returns an empty string when it is usable
+std::string check_config(const hydro_config* c);
+
+// stage kernel dispatch for a scheme (R = 3 or 4)
+struct StageLaunch {
+    void (*fn)(StageArgs);
+    size_t smem;
+    int tx, ty;
+    int ctas_per_sm;
+};
+cudaError_t stage_launch_info(int R, StageLaunch* out);
+
+inline int pick_zc(int nx, int ny, int nz, const StageLaunch& L, int sms)
+{
+    const long long tiles = (long long)((nx + L.tx - 1) / L.tx) * ((ny + L.ty - 1) / L.ty);
+    const long long conc = (long long)sms * (L.ctas_per_sm > 0 ? L.ctas_per_sm : 1);
+    static const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+    int best = nz;
+    double best_cost = 1e300;
+    for (int zc : cand) {
+        if (zc > nz && zc != cand[0]) break;
+        const int z = zc < nz ? zc : nz;
+        const long long ctas = tiles * ((nz + z - 1) / z);
+        const long long waves = (ctas + conc - 1) / conc;
+        const double cost = (double)waves * (z + 1.5);   // 1.5 planes: chunk prologue
+        if (cost < best_cost * 0.999) {
+            best_cost = cost;
+            best = z;
+        }
+    }
+    return best;
+}
+
+}  // namespace hydro

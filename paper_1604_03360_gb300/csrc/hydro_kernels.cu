@@ -1,0 +1,161 @@
+// hydro_kernels.cu -- the stage kernel instantiations and the bookkeeping
+// kernels of the step driver.
+#include "hydro_common.cuh"
+
+namespace hydro {
+
+__global__ void step_begin_kernel(Ctl* c, StepParams sp)
+{
+    double amax = 0.0;
+    for (int d = 0; d < 3; ++d)
+        if (sp.actmask & (1 << d)) amax = fmax(amax, __longlong_as_double((long long)c->a_cur[d]));
+    double dt = sp.dt_fixed > 0.0 ? sp.dt_fixed : sp.cfl * sp.mindx / amax;
+    if (c->t_end >= 0.0 && c->t + dt > c->t_end) dt = c->t_end - c->t;
+    if (!(dt > 0.0)) dt = 0.0;
+    c->dt = dt;
+    for (int d = 0; d < 3; ++d) {
+        c->a_s1[d] = 0ull;
+        c->a_s2[d] = 0ull;
+        c->a_next[d] = 0ull;
+    }
+}
+
+__global__ void step_end_kernel(Ctl* c)
+{
+    if (c->dt > 0.0) {
+        for (int d = 0; d < 3; ++d) c->a_cur[d] = c->a_next[d];
+        c->t += c->dt;
+        c->last_dt = c->dt;
+        c->step += 1;
+    }
+}
+
+__global__ void set_t_end_kernel(Ctl* c, double t_end) { c->t_end = t_end; }
+
+__global__ void reset_ctl_kernel(Ctl* c, double t)
+{
+    for (int d = 0; d < 3; ++d) {
+        c->a_cur[d] = c->a_s1[d] = c->a_s2[d] = c->a_next[d] = 0ull;
+    }
+    c->dt = 0.0;
+    c->t = t;
+    c->t_end = -1.0;
+    c->last_dt = 0.0;
+    c->step = 0;
+    c->bad_cell = -1;
+    c->status = 0;
+}
+
+__global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c)
+{
+    unsigned long long am[3] = {0ull, 0ull, 0ull};
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        double pr, vx, vy, vz, e;
+        if (con2prim(cs2, u[q], u[fs + q], u[2 * fs + q], u[3 * fs + q], pr, vx, vy, vz, e)) {
+            w[q] = pr;
+            w[fs + q] = vx;
+            w[2 * fs + q] = vy;
+            w[3 * fs + q] = vz;
+            double sp[3];
+            max_speeds(cs2, vx, vy, vz, sp);
+            for (int d = 0; d < 3; ++d) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(sp[d]);
+                am[d] = b > am[d] ? b : am[d];
+            }
+        } else {
+            for (int k = 0; k < 4; ++k) w[k * fs + q] = 0.0;
+            if (atomicCAS(&c->status, 0, (int)HYDRO_ERR_UNPHYSICAL) == 0) c->bad_cell = q;
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        unsigned long long v = am[d];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, v, o);
+            v = x > v ? x : v;
+        }
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(&c->a_cur[d], v);
+    }
+}
+
+__global__ void prim2con_kernel(const double* wp, long long ws, double* u, long long fs, long long n, double cs2,
+                                Ctl* c)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const double e = wp[q], vx = wp[ws + q], vy = wp[2 * ws + q], vz = wp[3 * ws + q], nn = wp[4 * ws + q];
+        const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+        if (!(e > 0.0) || !(v2 < 1.0)) {
+            if (atomicCAS(&c->status, 0, (int)HYDRO_ERR_UNPHYSICAL) == 0) c->bad_cell = q;
+        }
+        const double p = cs2 * e;
+        const double g2 = 1.0 / (1.0 - v2);
+        const double W = (e + p) * g2;
+        u[q] = W - p;
+        u[fs + q] = W * vx;
+        u[2 * fs + q] = W * vy;
+        u[3 * fs + q] = W * vz;
+        u[4 * fs + q] = nn * sqrt(g2);
+    }
+}
+
+__global__ void state_to_prim_kernel(const double* u, long long fs, double* out, long long os, long long n,
+                                     double cs2)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        double pr, vx, vy, vz, e;
+        if (con2prim(cs2, u[q], u[fs + q], u[2 * fs + q], u[3 * fs + q], pr, vx, vy, vz, e)) {
+            const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+            out[q] = e;
+            out[os + q] = vx;
+            out[2 * os + q] = vy;
+            out[3 * os + q] = vz;
+            out[4 * os + q] = u[4 * fs + q] * sqrt(1.0 - v2);
+        } else {
+            for (int k = 0; k < 5; ++k) out[k * os + q] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+    }
+}
+
+template <int R>
+static cudaError_t info_for(StageLaunch* out)
+{
+    constexpr int TX = 16, TY = 8;
+    out->fn = stage_kernel<R, TX, TY>;
+    out->smem = StageSmem<R, TX, TY>::bytes;
+    out->tx = TX;
+    out->ty = TY;
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)out->smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_kernel<R, TX, TY>, TX * TY,
+                                                         out->smem);
+}
+
+cudaError_t stage_launch_info(int R, StageLaunch* out)
+{
+    if (R == 3) return info_for<3>(out);
+    if (R == 4) return info_for<4>(out);
+    return cudaErrorInvalidValue;
+}
+
+std::string check_config(const hydro_config* c)
+{
+    if (!c) return "config is NULL";
+    if (c->scheme != HYDRO_WENO5 && c->scheme != HYDRO_WENO7) return "scheme must be 5 or 7";
+    const int G = c->scheme == HYDRO_WENO5 ? 3 : 4;
+    for (int d = 0; d < 3; ++d) {
+        if (c->n[d] < 1) return "grid size must be >= 1";
+        if (!(c->dx[d] > 0.0) || !std::isfinite(c->dx[d])) return "dx must be positive and finite";
+        if (c->bc[d] != HYDRO_BC_OUTFLOW && c->bc[d] != HYDRO_BC_PERIODIC) return "bc must be 0 (outflow) or 1 (periodic)";
+        if (c->n[d] > 1 && c->bc[d] == HYDRO_BC_PERIODIC && c->n[d] < G) return "periodic axis shorter than the stencil";
+    }
+    if ((long long)c->n[0] * c->n[1] > (1LL << 40) || c->n[0] > (1 << 28) || c->n[1] > 65535 * 8 ||
+        c->n[2] > (1 << 28))
+        return "grid too large";
+    if (!(c->cs2 > 0.0 && c->cs2 < 1.0)) return "cs2 must lie in (0, 1)";
+    if (!(c->weno_eps > 0.0)) return "weno_eps must be positive";
+    if (!(c->dt_fixed > 0.0) && !(c->cfl > 0.0)) return "need cfl > 0 or dt_fixed > 0";
+    if (c->reserved != 0) return "reserved must be 0";
+    return std::string();
+}
+
+}  // namespace hydro

@@ -1,0 +1,174 @@
+// hydro_math.cuh -- FP64 device arithmetic of the relativistic hydro scheme
+// (Sikorski et al., arXiv:1604.03360): conserved->primitive recovery for
+// p = cs2 e, the fluxes of Eq. 1, the characteristic speeds used by the
+// Lax-Friedrichs splitting, and finite-difference WENO5 / WENO7 (Sec. 1.2).
+//
+// GB300 design notes.  On this part the FP64 pipe issues ~2 FMA per clock per
+// SM while FP32/INT issue ~60x more, so every FP64 instruction counts:
+//  * reconstructions return a fraction N/D (one reciprocal per face instead of
+//    one division per weight);
+//  * the Lax-Friedrichs split works on g = f +- alpha u = 2 f^{+-} and the
+//    smoothness indicators are rescaled by powers of two (or 9 for WENO7)
+//    with epsilon rescaled to match -- exact rescalings that leave the
+//    nonlinear weights unchanged;
+//  * reciprocals take the MUFU seed (rcp.approx.ftz.f64, on the SFU pipe) and
+//    one cubically convergent Newton correction on the FP64 pipe.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hydro {
+
+// 1/x for finite, normal, positive or negative x.  Seed r0 from the MUFU
+// approximation, then the series (Newton-Raphson of order three) correction
+// r = r0 (1 + e + e^2), e = 1 - x r0, whose relative error is e^3 (Muller et
+// al., Handbook of Floating-Point Arithmetic, Newton-Raphson division).  The
+// result is within about one ulp of 1/x; it is not correctly rounded.
+__device__ __forceinline__ double rcp(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    const double e = fma(-x, r, 1.0);
+    const double t = fma(e, e, e);
+    return fma(r, t, r);
+}
+
+// Conserved -> primitive for p = k e (positive root of
+// k e^2 + (1-k) E e - (E^2 - M^2) = 0 in cancellation-free form).
+// Returns false for E <= 0, |M| >= E or NaN.  Outputs p, v and e.
+__device__ __forceinline__ bool con2prim(double k, double E, double mx, double my, double mz,
+                                         double& p, double& vx, double& vy, double& vz, double& e)
+{
+    const double m2 = fma(mx, mx, fma(my, my, mz * mz));
+    const double d = fma(E, E, -m2);
+    if (!(E > 0.0) || !(d > 0.0)) return false;
+    const double b = (1.0 - k) * E;
+    const double s = sqrt(fma(b, b, 4.0 * k * d));
+    e = (2.0 * d) * rcp(b + s);
+    p = k * e;
+    const double ih = rcp(E + p);
+    vx = mx * ih;
+    vy = my * ih;
+    vz = mz * ih;
+    return true;
+}
+
+// max(|lambda_+|, |lambda_-|) along each axis for p = k e, where
+// lambda_+- = (v_d (1-k) +- sqrt(k (1-v^2)(1 - k v^2 - (1-k) v_d^2))) / (1 - k v^2);
+// with a positive denominator and a non-negative root the larger magnitude is
+// (|v_d| (1-k) + root) / (1 - k v^2).
+__device__ __forceinline__ void max_speeds(double k, double vx, double vy, double vz, double out[3])
+{
+    const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+    const double one_kv2 = fma(-k, v2, 1.0);
+    const double kq = k * (1.0 - v2);
+    const double iden = rcp(one_kv2);
+    const double omk = 1.0 - k;
+    const double v[3] = {vx, vy, vz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double rad = kq * fma(-omk * v[d], v[d], one_kv2);
+        out[d] = fma(fabs(v[d]), omk, sqrt(rad)) * iden;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FD-WENO reconstruction (Jiang-Shu smoothness indicators, Sec. 1.2).
+// weno_left: value at x_{j+1/2} from v[0..S-1] = v_{j-r+1} .. v_{j+r-1}.
+// Result = N / D.  Candidate k uses v[k..k+r-1].
+// ---------------------------------------------------------------------------
+
+// r = 3.  With inputs g = 2 f the indicator b_k = 13/3 (2nd diff)^2 +
+// (1st-derivative form)^2 equals 16 beta_k(f); eps_s must be 16 eps.
+// N and D are the weight-normalised sums multiplied by 10 prod_k (eps+beta_k)^2.
+__device__ __forceinline__ void weno5(double a, double b, double c, double d, double e, double eps_s,
+                                      double& N, double& D)
+{
+    const double s0 = fma(-2.0, b, a) + c;
+    const double s1 = fma(-2.0, c, b) + d;
+    const double s2 = fma(-2.0, d, c) + e;
+    const double t0 = fma(3.0, c, fma(-4.0, b, a));
+    const double t1 = d - b;
+    const double t2 = fma(-3.0, c, fma(4.0, d, -e));
+    const double k13 = 13.0 / 3.0;
+    const double b0 = eps_s + fma(k13 * s0, s0, t0 * t0);
+    const double b1 = eps_s + fma(k13 * s1, s1, t1 * t1);
+    const double b2 = eps_s + fma(k13 * s2, s2, t2 * t2);
+    const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2;
+    const double P0 = w1 * w2, P1 = w0 * w2, P2 = w0 * w1;
+    // 10 d_k q_k: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6, q1 = (-b+5c+2d)/6, q2 = (2c+5d-e)/6
+    const double n0 = fma(11.0 / 6.0, c, fma(-7.0 / 6.0, b, a * (1.0 / 3.0)));
+    const double n1 = fma(2.0, d, fma(5.0, c, -b));
+    const double n2 = fma(-0.5, e, fma(2.5, d, c));
+    N = fma(n0, P0, fma(n1, P1, n2 * P2));
+    D = fma(3.0, P2, fma(6.0, P1, P0));
+}
+
+// r = 4 (Balsara-Shu weights from the same definition).  For the cubic
+// candidate p_k(xi) = sum c_i xi^i about x_j, beta = (c1 + c3/4)^2 +
+// 13/3 c2^2 + 781/20 c3^2.  With A = 6 (c1 + c3/4), B = 2 c2, C = 6 c3
+// (integer-coefficient forms) and inputs g = 2 f:
+// b_k = A^2 + 39 B^2 + 781/20 C^2 = 144 beta_k(f); eps_s must be 144 eps.
+// N and D are multiplied by 35 prod_k (eps+beta_k)^2.
+__device__ __forceinline__ void weno7(const double* v, double eps_s, double& N, double& D)
+{
+    const double v0 = v[0], v1 = v[1], v2 = v[2], v3 = v[3], v4 = v[4], v5 = v[5], v6 = v[6];
+    const double A0 = fma(-2.0, v0, fma(9.0, v1, fma(-18.0, v2, 11.0 * v3)));
+    const double A1 = fma(2.0, v4, fma(3.0, v3, fma(-6.0, v2, v1)));
+    const double A2 = fma(-2.0, v2, fma(-3.0, v3, fma(6.0, v4, -v5)));
+    const double A3 = fma(-11.0, v3, fma(18.0, v4, fma(-9.0, v5, 2.0 * v6)));
+    const double B0 = fma(2.0, v3, fma(-5.0, v2, fma(4.0, v1, -v0)));
+    const double B1 = fma(-2.0, v3, v2) + v4;   // candidates 1 and 2 share the
+    const double B2 = B1;                         // central 2nd difference at j
+    const double B3 = fma(2.0, v3, fma(-5.0, v4, fma(4.0, v5, -v6)));
+    const double C0 = (v3 - v0) + 3.0 * (v1 - v2);
+    const double C1 = (v4 - v1) + 3.0 * (v2 - v3);
+    const double C2 = (v5 - v2) + 3.0 * (v3 - v4);
+    const double C3 = (v6 - v3) + 3.0 * (v4 - v5);
+    const double kc = 781.0 / 20.0;
+    const double b0 = eps_s + fma(A0, A0, fma(39.0 * B0, B0, kc * C0 * C0));
+    const double b1 = eps_s + fma(A1, A1, fma(39.0 * B1, B1, kc * C1 * C1));
+    const double b2 = eps_s + fma(A2, A2, fma(39.0 * B2, B2, kc * C2 * C2));
+    const double b3 = eps_s + fma(A3, A3, fma(39.0 * B3, B3, kc * C3 * C3));
+    const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2, w3 = b3 * b3;
+    const double p01 = w0 * w1, p23 = w2 * w3;
+    const double P0 = w1 * p23, P1 = w0 * p23, P2 = p01 * w3, P3 = p01 * w2;
+    // 35 d_k q_k, d = (1, 12, 18, 4)/35
+    const double n0 = fma(25.0 / 12.0, v3, fma(-23.0 / 12.0, v2, fma(13.0 / 12.0, v1, -0.25 * v0)));
+    const double n1 = fma(3.0, v4, fma(13.0, v3, fma(-5.0, v2, v1)));
+    const double n2 = fma(10.5, v3 + v4, -1.5 * (v2 + v5));
+    const double n3 = fma(13.0 / 3.0, v4, fma(-5.0 / 3.0, v5, fma(1.0 / 3.0, v6, v3)));
+    N = fma(n0, P0, fma(n1, P1, fma(n2, P2, n3 * P3)));
+    D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
+}
+
+template <int R>
+__device__ __forceinline__ void weno_left(const double* v, double eps_s, double& N, double& D)
+{
+    if constexpr (R == 3) weno5(v[0], v[1], v[2], v[3], v[4], eps_s, N, D);
+    else weno7(v, eps_s, N, D);
+}
+
+// Right-biased value at x_{j-1/2} of the stencil centred on j: the mirror image.
+template <int R>
+__device__ __forceinline__ void weno_right(const double* v, double eps_s, double& N, double& D)
+{
+    if constexpr (R == 3) {
+        weno5(v[4], v[3], v[2], v[1], v[0], eps_s, N, D);
+    } else {
+        const double m[7] = {v[6], v[5], v[4], v[3], v[2], v[1], v[0]};
+        weno7(m, eps_s, N, D);
+    }
+}
+
+// Face value N+/D+ + N-/D- with one reciprocal.
+__device__ __forceinline__ double face_sum(double Np, double Dp, double Nm, double Dm)
+{
+    return fma(Np, Dm, Nm * Dp) * rcp(Dp * Dm);
+}
+
+template <int R> struct SchemeConst;
+template <> struct SchemeConst<3> { static constexpr double eps_scale = 16.0; };
+template <> struct SchemeConst<4> { static constexpr double eps_scale = 144.0; };
+
+}  // namespace hydro

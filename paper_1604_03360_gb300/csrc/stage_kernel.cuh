@@ -1,0 +1,304 @@
+// stage_kernel.cuh -- one fused RK3 stage of the FD-WENO scheme
+// (arXiv:1604.03360, Eq. 2 + Sec. 1.2 + the RK3 of Sec. 1) for sm_103a.
+//
+// One launch computes, for every interior cell,
+//   L(u_s) = sum_d (F_d(j-1/2) - F_d(j+1/2)) / dx_d        (Eq. 2)
+//   u_out  = ca * u_n + cb * (u_s + dt L(u_s))              (SSP-RK3 stage)
+// then recovers the primitives of u_out (stored for the next stage) and
+// reduces the largest characteristic speed per axis of u_out (the Lax-
+// Friedrichs alpha of the next stage) with warp shuffles + one atomicMax per
+// warp on the IEEE bit pattern (exact, order independent).
+//
+// Work decomposition: a CTA owns a TX x TY column tile and a chunk of z
+// planes and sweeps along z.  Per plane:
+//   1. each thread appends the split z-fluxes g = f_z +- alpha_z u of its own
+//      column at plane p+G to a private ring (shared memory, 2G-1 planes) and
+//      reconstructs the z-face p+1/2 from it (no barrier needed);
+//   2. the CTA stages split x-fluxes of the tile rows plus G halo cells each
+//      side, and split y-fluxes of the tile columns plus halo, in shared
+//      memory (ghost cells come from the boundary rule by index mapping);
+//   3. the CTA reconstructs all (TX+1) x TY x-faces and TX x (TY+1) y-faces,
+//      one (face, field) item per thread at a time;
+//   4. each thread combines the six face fluxes of its cell and finishes.
+// Primitive variables (p, v) of the stage input come from the previous
+// stage's epilogue, so no cell is recovered twice in a stage.
+#pragma once
+#include "hydro_math.cuh"
+
+namespace hydro {
+
+struct StageArgs {
+    const double* u_in;     // 5 fields: stage input u_s (stencil reads)
+    const double* w_in;     // 4 fields: p, v_x, v_y, v_z of u_s
+    const double* u_n;      // 5 fields: step-start state (ca != 0 only)
+    double* u_out;          // 5 fields (may alias u_n: each thread reads then writes its own cell)
+    double* w_out;          // 4 fields
+    long long fs;           // field stride
+    int nx, ny, nz;
+    int zc;                 // z planes per CTA
+    int bc[3];              // 0 outflow, 1 periodic
+    int act[3];             // direction has more than one cell
+    double hdx[3];          // 0.5 / dx_d (the 1/2 of the LF split folded in)
+    double cs2;
+    double eps_s;           // rescaled WENO epsilon
+    double ca, cb;          // RK stage coefficients
+    const unsigned long long* alpha_in;  // 3 speeds (IEEE bits) used for the split
+    const double* dt;       // time step (device); <= 0: the stage does nothing
+    unsigned long long* alpha_out;       // 3 speeds of u_out (atomicMax target)
+    int* status;            // first error code
+    long long* bad_cell;    // linear index of the first unphysical cell
+};
+
+__device__ __forceinline__ int bc_map(int i, int n, int bc)
+{
+    if (i >= 0 && i < n) return i;
+    if (bc == 1) {
+        i %= n;
+        return i < 0 ? i + n : i;
+    }
+    return i < 0 ? 0 : n - 1;
+}
+
+template <int R, int TX, int TY>
+struct StageSmem {
+    static constexpr int G = R, S = 2 * R - 1, NT = TX * TY, NRING = 2 * R - 1;
+    static constexpr int GXW = TX + 2 * G, GYH = TY + 2 * G;
+    static constexpr int RING = NRING * 10 * NT;
+    static constexpr int GX = 10 * TY * GXW;
+    static constexpr int GY = 10 * GYH * TX;
+    static constexpr int FX = 5 * TY * (TX + 1);
+    static constexpr int FY = 5 * (TY + 1) * TX;
+    static constexpr size_t bytes = sizeof(double) * (size_t)(RING + GX + GY + FX + FY);
+};
+
+// split fluxes g+- = f_d(u) +- alpha u (= 2 f^{+-}) of one cell along axis d
+__device__ __forceinline__ void split_flux(int d, const double u[5], const double w[4], double alpha,
+                                           double gp[5], double gm[5])
+{
+    const double p = w[0], vd = w[1 + d];
+    double f[5];
+    f[0] = u[1 + d];
+    f[1] = u[1] * vd;
+    f[2] = u[2] * vd;
+    f[3] = u[3] * vd;
+    f[4] = u[4] * vd;
+    f[1 + d] += p;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        gp[k] = fma(alpha, u[k], f[k]);
+        gm[k] = fma(-alpha, u[k], f[k]);
+    }
+}
+
+template <int R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, (R == 3 ? 2 : 1)) stage_kernel(const StageArgs a)
+{
+    using SM = StageSmem<R, TX, TY>;
+    constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING;
+    constexpr int GXW = SM::GXW, GYH = SM::GYH;
+    extern __shared__ __align__(16) double smem[];
+    double* ring = smem;
+    double* gx = ring + SM::RING;
+    double* gy = gx + SM::GX;
+    double* Fx = gy + SM::GY;
+    double* Fy = Fx + SM::FX;
+
+    const double dt = *a.dt;
+    if (!(dt > 0.0)) return;
+    double al[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) al[d] = __longlong_as_double((long long)a.alpha_in[d]);
+
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int zb = blockIdx.z * a.zc, ze = min(zb + a.zc, a.nz);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool own = (x < nx) && (y < ny);
+    const int xs = bc_map(x, nx, a.bc[0]), ys = bc_map(y, ny, a.bc[1]);
+    const long long fs = a.fs, plane = (long long)nx * ny;
+    const bool zact = a.act[2] != 0;
+
+    auto load = [&](long long q, double u[5], double w[4]) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) u[k] = __ldg(a.u_in + k * fs + q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = __ldg(a.w_in + k * fs + q);
+    };
+    auto slot_of = [&](int m) { return (m + 4 * NRING) % NRING; };
+    auto ingest = [&](int m) {
+        const long long q = (long long)bc_map(m, nz, a.bc[2]) * plane + (long long)ys * nx + xs;
+        double u[5], w[4], gp[5], gm[5];
+        load(q, u, w);
+        split_flux(2, u, w, al[2], gp, gm);
+        double* r = ring + slot_of(m) * 10 * NT + tid;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            r[k * NT] = gp[k];
+            r[(5 + k) * NT] = gm[k];
+        }
+    };
+    // N/D of the left-biased (+) and right-biased (-) reconstructions of the
+    // z-stencil centred on plane m, field k
+    auto recon_z = [&](int m, int k, double& Np, double& Dp, double& Nm, double& Dm) {
+        double vp[S], vm[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            const double* r = ring + slot_of(m - G + 1 + i) * 10 * NT + tid;
+            vp[i] = r[k * NT];
+            vm[i] = r[(5 + k) * NT];
+        }
+        weno_left<R>(vp, a.eps_s, Np, Dp);
+        weno_right<R>(vm, a.eps_s, Nm, Dm);
+    };
+
+    double hNp[5], hDp[5], Fzm[5], Fzp[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) { hNp[k] = 0.0; hDp[k] = 1.0; Fzm[k] = 0.0; Fzp[k] = 0.0; }
+    if (zact) {
+        for (int m = zb - G; m <= zb + G - 2; ++m) ingest(m);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double Nm, Dm;
+            recon_z(zb - 1, k, hNp[k], hDp[k], Nm, Dm);
+        }
+        ingest(zb + G - 1);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double Np, Dp, Nm, Dm;
+            recon_z(zb, k, Np, Dp, Nm, Dm);
+            Fzm[k] = face_sum(hNp[k], hDp[k], Nm, Dm);
+            hNp[k] = Np;
+            hDp[k] = Dp;
+        }
+    }
+
+    unsigned long long amax[3] = {0ull, 0ull, 0ull};
+    const int nfx = a.act[0] ? 5 * TY * (TX + 1) : 0;
+    const int nfy = a.act[1] ? 5 * (TY + 1) * TX : 0;
+    const int ngx = a.act[0] ? TY * GXW : 0;
+    const int ngy = a.act[1] ? GYH * TX : 0;
+
+    for (int p = zb; p < ze; ++p) {
+        // 1. z: ingest plane p+G, face p+1/2 = R+(p) + R-(p+1)
+        if (zact) {
+            ingest(p + G);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                double Np, Dp, Nm, Dm;
+                recon_z(p + 1, k, Np, Dp, Nm, Dm);
+                Fzp[k] = face_sum(hNp[k], hDp[k], Nm, Dm);
+                hNp[k] = Np;
+                hDp[k] = Dp;
+            }
+        }
+        // 2. split x- and y-fluxes of plane p (tile + halo) into shared memory
+        const long long qz = (long long)bc_map(p, nz, a.bc[2]) * plane;
+        for (int it = tid; it < ngx + ngy; it += NT) {
+            double u[5], w[4], gp[5], gm[5];
+            if (it < ngx) {
+                const int row = it / GXW, col = it % GXW;
+                const int xx = bc_map(x0 - G + col, nx, a.bc[0]), yy = bc_map(y0 + row, ny, a.bc[1]);
+                load(qz + (long long)yy * nx + xx, u, w);
+                split_flux(0, u, w, al[0], gp, gm);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    gx[(k * TY + row) * GXW + col] = gp[k];
+                    gx[((5 + k) * TY + row) * GXW + col] = gm[k];
+                }
+            } else {
+                const int j = it - ngx, row = j / TX, col = j % TX;
+                const int xx = bc_map(x0 + col, nx, a.bc[0]), yy = bc_map(y0 - G + row, ny, a.bc[1]);
+                load(qz + (long long)yy * nx + xx, u, w);
+                split_flux(1, u, w, al[1], gp, gm);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    gy[(k * GYH + row) * TX + col] = gp[k];
+                    gy[((5 + k) * GYH + row) * TX + col] = gm[k];
+                }
+            }
+        }
+        __syncthreads();
+        // 3. x- and y-faces, one (face, field) per item
+        for (int it = tid; it < nfx + nfy; it += NT) {
+            double vp[S], vm[S], Np, Dp, Nm, Dm;
+            if (it < nfx) {
+                const int k = it / (TY * (TX + 1)), rr = it % (TY * (TX + 1));
+                const int row = rr / (TX + 1), f = rr % (TX + 1);   // face f - 1/2 of the tile
+                const double* gpr = gx + (k * TY + row) * GXW;
+                const double* gmr = gx + ((5 + k) * TY + row) * GXW;
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    vp[i] = gpr[f + i];
+                    vm[i] = gmr[f + 1 + i];
+                }
+                weno_left<R>(vp, a.eps_s, Np, Dp);
+                weno_right<R>(vm, a.eps_s, Nm, Dm);
+                Fx[(k * TY + row) * (TX + 1) + f] = face_sum(Np, Dp, Nm, Dm);
+            } else {
+                const int j = it - nfx;
+                const int k = j / ((TY + 1) * TX), rr = j % ((TY + 1) * TX);
+                const int f = rr / TX, col = rr % TX;                 // face f - 1/2 along y
+                const double* gpc = gy + (k * GYH) * TX + col;
+                const double* gmc = gy + ((5 + k) * GYH) * TX + col;
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    vp[i] = gpc[(f + i) * TX];
+                    vm[i] = gmc[(f + 1 + i) * TX];
+                }
+                weno_left<R>(vp, a.eps_s, Np, Dp);
+                weno_right<R>(vm, a.eps_s, Nm, Dm);
+                Fy[(k * (TY + 1) + f) * TX + col] = face_sum(Np, Dp, Nm, Dm);
+            }
+        }
+        __syncthreads();
+        // 4. combine, RK update, primitives and speeds of the new state
+        if (own) {
+            const long long q = (long long)p * plane + (long long)y * nx + x;
+            double un[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                double L = 0.0;
+                if (a.act[0]) L = a.hdx[0] * (Fx[(k * TY + ty) * (TX + 1) + tx] - Fx[(k * TY + ty) * (TX + 1) + tx + 1]);
+                if (a.act[1]) L = fma(a.hdx[1], Fy[(k * (TY + 1) + ty) * TX + tx] - Fy[(k * (TY + 1) + ty + 1) * TX + tx], L);
+                if (zact) L = fma(a.hdx[2], Fzm[k] - Fzp[k], L);
+                const double s = fma(dt, L, __ldg(a.u_in + k * fs + q));
+                un[k] = (a.ca == 0.0) ? s : fma(a.ca, a.u_n[k * fs + q], a.cb * s);
+                a.u_out[k * fs + q] = un[k];
+            }
+            double pr, vx, vy, vz, e;
+            if (con2prim(a.cs2, un[0], un[1], un[2], un[3], pr, vx, vy, vz, e)) {
+                a.w_out[q] = pr;
+                a.w_out[fs + q] = vx;
+                a.w_out[2 * fs + q] = vy;
+                a.w_out[3 * fs + q] = vz;
+                double sp[3];
+                max_speeds(a.cs2, vx, vy, vz, sp);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const unsigned long long b = (unsigned long long)__double_as_longlong(sp[d]);
+                    amax[d] = b > amax[d] ? b : amax[d];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a.w_out[k * fs + q] = 0.0;
+                if (atomicCAS(a.status, 0, 4) == 0) *a.bad_cell = q;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Fzm[k] = Fzp[k];
+    }
+    // speeds: warp max, one atomic per warp and axis
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        unsigned long long v = amax[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
+        }
+        if ((tid & 31) == 0 && v) atomicMax(a.alpha_out + d, v);
+    }
+}
+
+}  // namespace hydro

@@ -1,0 +1,69 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports
+every function include/hydro.h declares, and rejects bad arguments before any
+device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_1604_03360_gb300.build as B
+    B.build()
+    import paper_1604_03360_gb300 as H
+    return H.lib()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(hydro_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version(L):
+    assert b"sm_103a" in L.hydro_version()
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("scheme", 6, b"scheme"), ("cs2", 1.0, b"cs2"), ("weno_eps", 0.0, b"weno_eps"),
+    ("reserved", 1, b"reserved"),
+])
+def test_invalid_config_rejected(L, field, value, msg):
+    import paper_1604_03360_gb300 as H
+    c = H.make_config((8, 8, 8), (0.1, 0.1, 0.1))
+    setattr(c, field, value)
+    h = ctypes.c_void_p()
+    assert L.hydro_create(ctypes.byref(c), None, ctypes.byref(h)) == H._binding.ERR_INVALID_ARG
+    assert msg in L.hydro_last_error(None)
+
+
+def test_invalid_grid_rejected(L):
+    import paper_1604_03360_gb300 as H
+    for n, dx, bc in [((0, 4, 4), (1, 1, 1), (0, 0, 0)), ((8, 8, 8), (1, -1, 1), (0, 0, 0)),
+                      ((8, 2, 8), (1, 1, 1), (0, 1, 0)), ((8, 8, 8), (1, 1, 1), (0, 2, 0))]:
+        c = H.make_config(n, dx, bc=bc)
+        h = ctypes.c_void_p()
+        assert L.hydro_create(ctypes.byref(c), None, ctypes.byref(h)) == H._binding.ERR_INVALID_ARG
+    assert L.hydro_create(None, None, ctypes.byref(ctypes.c_void_p())) == H._binding.ERR_INVALID_ARG
+
+
+def test_null_handle_calls_fail_cleanly(L):
+    assert L.hydro_step(None, 1, -1.0) == 1
+    assert L.hydro_sync(None) == 1
+    assert L.hydro_destroy(None) == 0
+    assert L.hydro_field_stride(None) == 0

@@ -1,0 +1,183 @@
+"""GPU (C-ABI) vs CPU oracle parity: element-wise, per field, within the
+spec tolerance of 1e-11 (normwise relative error per field)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from parity import TOL, assert_parity, field_errors, oracle_cfg, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_03360_gb300.build as B
+    B.build()
+    oracle.build()
+
+
+def with_flow(g, w, scale=0.3):
+    """Add a smooth velocity field to data generated at rest."""
+    x, y, z = g.centres()
+    sh = w[0].shape
+    w[1] = np.broadcast_to(scale * np.tanh(x / 3.0) * np.ones_like(y), sh)
+    w[2] = np.broadcast_to(-0.5 * scale * np.tanh((y - 0.5) / 2.0) * np.ones_like(z), sh)
+    w[3] = np.broadcast_to(0.4 * scale * np.sin(z / 2.0) * np.ones_like(x), sh)
+    return w
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_sod_full_config(scheme):
+    """1+1D Sod tube, N = 400, CFL 0.4, to t = 0.4 (Sec. 3, Fig. 1 setup)."""
+    g, w = W.sod(N=400, scheme=scheme)
+    assert_parity(g, w, 100000, t0=0.0, t_end=0.4)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+@pytest.mark.parametrize("dims", [(37, 29, 21), (16, 8, 40), (53, 11, 9)])
+def test_ragged_lumpy_flow(scheme, dims):
+    """Uneven grid spanning several 16 x 8 tiles and z chunks with ragged tails."""
+    g, w = W.lumpy(n=dims, seed=sum(dims), scheme=scheme)
+    w = with_flow(g, w)
+    assert_parity(g, w, 6)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_periodic_smooth(scheme):
+    g, w = W.smooth_periodic(n=(19, 13, 11), amp=0.3, vamp=0.5, seed=4, scheme=scheme)
+    g.cfl = 0.4
+    assert_parity(g, w, 8)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 40), (1, 40, 1), (40, 1, 1), (23, 17, 1), (1, 19, 23), (21, 1, 18),
+                                  (1, 1, 1), (2, 2, 2)])
+def test_degenerate_dimensions(dims):
+    g, w = W.lumpy(n=dims, seed=5, scheme=5)
+    w = with_flow(g, w)
+    assert_parity(g, w, 5)
+
+
+def test_mixed_boundaries():
+    g, w = W.smooth_periodic(n=(24, 17, 12), seed=8, scheme=7)
+    g.bc = (1, 0, 1)
+    assert_parity(g, w, 5)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_hubble_exact_init(scheme):
+    g, w = W.hubble(N=40, scheme=scheme)
+    assert_parity(g, w, 10, t0=g.t0)
+
+
+@pytest.mark.parametrize("scheme", [7, 5])
+def test_ellipsoidal_reduced_long_run(scheme):
+    """Ellipsoidal flow (Sec. 3, Fig. 2 setup) at 48^3 for the full 200 steps.
+    The CFL number is scaled by 48/256 so that the time step, and hence the
+    physical time reached after 200 steps (t ~ 5.8), match the 256^3 run; at
+    CFL 0.3 a coarse grid would run 5x longer, past the point where the
+    near-vacuum corners (|v| -> 1) turn unphysical."""
+    g, w = W.ellipsoidal(N=48, scheme=scheme)
+    g.cfl = 0.3 * 48 / 256
+    assert_parity(g, w, 200)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_hubble_full_size_128(scheme):
+    """Hubble-like flow at the full 128^3 grid (exact-init, t0 = 10)."""
+    g, w = W.hubble(N=128, scheme=scheme)
+    assert_parity(g, w, 2, t0=g.t0)
+
+
+def test_ellipsoidal_full_size_256_weno7():
+    """The benchmark workload itself: 256^3 ellipsoidal flow, WENO7, two steps
+    in the launch configuration the benchmark times."""
+    g, w = W.ellipsoidal(N=256, scheme=7)
+    assert_parity(g, w, 2)
+
+
+def test_ellipsoidal_full_config_200_steps_stays_physical():
+    """All 200 steps of the 256^3 WENO7 configuration: no unphysical state,
+    the time reached matches the CFL rule, total energy only leaves through
+    the outflow boundaries (it cannot grow)."""
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.ellipsoidal(N=256, scheme=7)
+    with Hydro.from_grid(g) as h:
+        h.set_primitive(w)
+        e0 = h.get_state()[0].sum()
+        h.step(200)
+        u = h.get_state()
+        assert h.steps == 200 and 5.0 < h.t < 6.5, (h.steps, h.t)
+    assert np.isfinite(u).all()
+    assert u[0].sum() <= e0 * (1 + 1e-12)
+    M = np.sqrt(u[1] ** 2 + u[2] ** 2 + u[3] ** 2)
+    assert (u[0] > M).all()
+
+
+def test_t_end_stops_stepping():
+    g, w = W.sod(N=120, scheme=5)
+    ref, tr, kr = run_oracle(g, w, 100000, 0.0, 0.1)
+    got, tg, kg = run_gpu(g, w, kr + 25, 0.0, 0.1)
+    assert kg == kr and tg == pytest.approx(0.1, abs=1e-15)
+    assert np.all(field_errors(got, ref) <= TOL)
+
+
+def test_set_state_and_set_primitive_agree():
+    g, w = W.lumpy(n=(20, 18, 16), seed=2)
+    w = with_flow(g, w)
+    u0 = oracle.prim2con(w)
+    a, _, _ = run_gpu(g, w, 3, use_primitive=True)
+    b, _, _ = run_gpu(g, w, 3, use_primitive=False, u0=u0)
+    assert np.all(field_errors(a, b) <= 1e-13)
+
+
+def test_bitwise_deterministic():
+    g, w = W.ellipsoidal(N=36, scheme=7)
+    a, _, _ = run_gpu(g, w, 5)
+    b, _, _ = run_gpu(g, w, 5)
+    assert np.array_equal(a, b)
+
+
+def test_primitives_and_speeds():
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=(17, 15, 13), seed=12)
+    w = with_flow(g, w)
+    u0 = oracle.prim2con(w)
+    with Hydro.from_grid(g) as h:
+        h.set_state(u0)
+        p = h.get_primitive()
+        a, _ = h.speeds()
+    np.testing.assert_allclose(p, oracle.con2prim(u0), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(a, oracle.alpha(oracle_cfg(g), u0), rtol=1e-14)
+
+
+def test_device_tensors_roundtrip():
+    import torch
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=(24, 20, 16), seed=13)
+    u0 = oracle.prim2con(w)
+    dev = torch.from_numpy(u0).cuda()
+    with Hydro.from_grid(g) as h:
+        h.set_state(dev)
+        h.step(2)
+        out = torch.empty_like(dev)
+        h.get_state(out)
+        host = h.get_state()
+    assert np.array_equal(out.cpu().numpy(), host)
+    ref = oracle.run(oracle_cfg(g), u0, 2)[0]
+    assert np.all(field_errors(host, ref) <= TOL)
+
+
+def test_unphysical_state_reported():
+    from paper_1604_03360_gb300 import Hydro, HydroError
+    g, w = W.lumpy(n=(10, 10, 10), seed=3)
+    u0 = oracle.prim2con(w)
+    u0[1, 4, 5, 6] = 3.0 * u0[0, 4, 5, 6]
+    with Hydro.from_grid(g) as h:
+        h.set_state(u0)
+        with pytest.raises(HydroError) as ei:
+            h.sync()
+        assert ei.value.code == 4

@@ -188,6 +188,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scheme", type=int, default=7, choices=[5, 7])
+    ap.add_argument("--grid", type=int, default=256, help="cells per axis (256: the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the WENO5 and e2e extras")
     args = ap.parse_args()
@@ -213,7 +214,7 @@ def main():
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    g, w = workload(args.scheme)
+    g, w = workload(args.scheme, args.grid)
     cells = g.cells
     h = Hydro.from_grid(g, stream=stream)
     w_dev = torch.from_numpy(w).to(dev)
@@ -269,7 +270,7 @@ def main():
 
     extra = {}
     if not args.no_extra and args.scheme == 7:
-        g5, w5 = workload(5)
+        g5, w5 = workload(5, args.grid)
         h5 = Hydro.from_grid(g5, stream=stream)
         h5.set_primitive(torch.from_numpy(w5).to(dev))
         h5.step(2)
@@ -298,13 +299,13 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "FP64 WENO%d cell-updates/s at 256^3 (ellipsoidal flow); %%HBM peak" % args.scheme,
+            "metric": "FP64 WENO%d cell-updates/s at %d^3 (ellipsoidal flow); %%HBM peak" % (args.scheme, args.grid),
             "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ellipsoidal-256^3-WENO%d" % args.scheme, "grid": [256, 256, 256],
+            "config": {"workload": "ellipsoidal-%d^3-WENO%d" % (args.grid, args.scheme), "grid": [args.grid] * 3,
                        "steps_per_timing": args.steps, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "state 3.6 GB >> 129 MB L2: no flush needed"},
+                       "l2": "state %.2f GB > 129 MB L2: no flush needed" % (27 * 8 * cells / 1e9)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp64_peak, "traffic": None,
                          "kernel": "stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,

@@ -146,6 +146,40 @@ int64_t hydro_field_stride(hydro_t* h);
  * FP64-bound stage kernel.  Allocates and frees a small scratch buffer. */
 hydro_status hydro_measure_fp64_peak(void* stream, double* fma_per_second);
 
+/* ---- Stepping without device allocation -------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot call cudaMalloc -- for example a host application whose device
+ * memory belongs to its own pool allocator, or a loop with a fixed footprint
+ * that must not pay cudaMalloc's implicit synchronisation.  It advances the
+ * conserved state by up to nsteps RK3 steps exactly like hydro_step (same
+ * kernels, same result), but keeps all intermediate data in one static
+ * device array of the library (HYDRO_NOALLOC_MAX_CELLS * 176 bytes + 256
+ * bytes, about 23 MB) that every GPU which loads the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   cfg          grid and scheme, as for hydro_create.
+ *   u_in, u_out  device pointers: 5 fields (E, M_x, M_y, M_z, R) with stride
+ *                field_stride; u_out receives the result (u_out == u_in is
+ *                allowed: the update is then in place).  Owned by the caller.
+ *   field_stride cell count <= field_stride <= HYDRO_NOALLOC_MAX_CELLS, else
+ *                HYDRO_ERR_INVALID_ARG with a message saying so.
+ *   t0, t_end    start time; t_end < 0 for no limit (as in hydro_step).
+ *   stream       cudaStream_t for all work (NULL: legacy default stream).
+ *   t_out        NULL: fully asynchronous, device errors are not reported.
+ *                Non-NULL: the call synchronises the stream, stores the final
+ *                time and returns HYDRO_ERR_UNPHYSICAL if a stage met an
+ *                unphysical state.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and configures the kernels, with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array and it keeps the previous call's contents (each call resets what
+ * it reads): calls whose GPU work overlaps race on it and must be serialised.
+ * hydro_noalloc_last_error() describes the calling thread's last failure. */
+#define HYDRO_NOALLOC_MAX_CELLS 131072
+hydro_status hydro_step_noalloc(const hydro_config* cfg, const double* u_in, double* u_out, int64_t field_stride,
+                                double t0, int32_t nsteps, double t_end, void* stream, double* t_out);
+const char* hydro_noalloc_last_error(void);
+
 /* Library version string. */
 const char* hydro_version(void);
 

@@ -181,6 +181,83 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def lumpy_on_device(g, seed, dev, width=0.5):
+    """The seeded lumpy event (workloads.lumpy_params) evaluated on the GPU
+    with torch as separable Gaussians: e = 0.1 + sum A gx(x) gy(y) gz(z), v = 0, n = e."""
+    import torch
+    import workloads as W
+    centres, amps = W.lumpy_params(seed)
+    ax = [torch.tensor(g.origin[d] + (np.arange(g.n[d]) + 0.5) * g.dx[d], device=dev) for d in range(3)]
+    e = torch.full((g.n[2], g.n[1], g.n[0]), 0.1, dtype=torch.float64, device=dev)
+    for c, A in zip(centres, amps):
+        gx = torch.exp(-(ax[0] - c[0]) ** 2 / (2 * width * width))
+        gy = torch.exp(-(ax[1] - c[1]) ** 2 / (2 * width * width))
+        gz = torch.exp(-(ax[2] - c[2]) ** 2 / (2 * width * width))
+        e += float(A) * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    z = torch.zeros_like(e)
+    return torch.stack([e, z, z, z, e]).contiguous()
+
+
+def batched_vs_looped(dev, stream, barrier, steps, warmup, events=256):
+    """configs: 256 seeded lumpy events, per-axis sizes U{48..160}, WENO5, 100
+    RK3 steps each.  Times `steps` steps of (a) the batched path (one
+    persistent launch per stage over all events, graph-replayed) and (b) a loop
+    of the single-grid path over the same events; events/s counts events
+    finishing all 100 steps."""
+    import torch
+    import workloads as W
+    from paper_1604_03360_gb300 import Hydro, HydroBatch
+    sizes = W.batch_sizes(events)
+    grids = [W.batch_grid(i, sizes) for i in range(events)]
+    cells = sum(g.cells for g in grids)
+    out = {"workload": "%d lumpy events, per-axis sizes U{48..160}, WENO5, 100 RK3 steps" % events,
+           "events": events, "cells": cells, "steps_timed": steps}
+    b = HydroBatch(grids, stream=stream)
+    for i, g in enumerate(grids):
+        b.set_primitive(i, lumpy_on_device(g, 1604 + i, dev))
+    tune_ms = b.autotune()
+    b.step(warmup)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kms = b.profile_step(steps)
+    e1.record(stream)
+    barrier()
+    b.sync()
+    tb = e0.elapsed_time(e1) / 1e3 / steps
+    out["batched"] = {"ms_per_step": 1e3 * tb, "events_per_s": events / (100 * tb), "cell_updates_per_s": cells / tb,
+                      "launch": list(b.launch()), "autotune_stage1_ms": tune_ms,
+                      "persistent_stage_ms": float(kms[1:4].sum()) / (3 * steps), "gpu_launches_per_step": 5}
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    hs = []
+    for i, g in enumerate(grids):
+        h = Hydro.from_grid(g, stream=stream)
+        h.set_primitive(lumpy_on_device(g, 1604 + i, dev))
+        hs.append(h)
+    for _ in range(warmup):
+        for h in hs:
+            h.step(1)
+    barrier()
+    e0.record(stream)
+    for _ in range(steps):
+        for h in hs:
+            h.step(1)
+    e1.record(stream)
+    barrier()
+    for h in hs:
+        h.sync()
+    tl = e0.elapsed_time(e1) / 1e3 / steps
+    out["looped"] = {"ms_per_step": 1e3 * tl, "events_per_s": events / (100 * tl), "cell_updates_per_s": cells / tl,
+                     "gpu_launches_per_step": 5 * events}
+    out["batched_over_looped"] = tl / tb
+    for h in hs:
+        h.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,6 +268,8 @@ def main():
     ap.add_argument("--grid", type=int, default=256, help="cells per axis (256: the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the WENO5 and e2e extras")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-looped ensemble")
+    ap.add_argument("--batch-events", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -219,6 +298,8 @@ def main():
     h = Hydro.from_grid(g, stream=stream)
     w_dev = torch.from_numpy(w).to(dev)
     h.set_primitive(w_dev)
+    tuned_ms = h.autotune()
+    launch = h.launch()
     h.step(args.warmup)
     torch.cuda.synchronize()
     h.sync()
@@ -273,7 +354,8 @@ def main():
         g5, w5 = workload(5, args.grid)
         h5 = Hydro.from_grid(g5, stream=stream)
         h5.set_primitive(torch.from_numpy(w5).to(dev))
-        h5.step(2)
+        h5.autotune()
+        h5.step(3)
         barrier()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
@@ -282,13 +364,15 @@ def main():
         barrier()
         el5 = a0.elapsed_time(a1) / 1e3
         st5 = float(k5[1:4].sum()) / (3 * args.steps)
-        extra["weno5_256"] = {"value": cells * args.steps / el5, "unit": "cell-updates/s",
+        extra["weno5_256"] = {"value": cells * args.steps / el5, "unit": "cell-updates/s", "launch": h5.launch(),
                               "ms_per_step": 1e3 * el5 / args.steps, "stage_kernel_ms": st5,
                               "fp64_tflops": FLOPS_PER_CELL_STAGE[5] * cells / (st5 * 1e-3) / 1e12,
                               "fp64_frac": FLOPS_PER_CELL_STAGE[5] * cells / (st5 * 1e-3) / 1e12 / fp64_peak,
                               "hbm_frac": HBM_BYTES_PER_CELL_UPDATE * cells * args.steps / el5 / 1e9 / hbm_peak}
         h5.close()
     h.close()
+    if not args.no_extra and not args.no_batch:
+        extra["batched_vs_looped"] = batched_vs_looped(dev, stream, barrier, 3, 3, args.batch_events)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -305,7 +389,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "ellipsoidal-%d^3-WENO%d" % (args.grid, args.scheme), "grid": [args.grid] * 3,
                        "steps_per_timing": args.steps, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "state %.2f GB > 129 MB L2: no flush needed" % (27 * 8 * cells / 1e9)},
+                       "l2": "state %.2f GB > 129 MB L2: no flush needed" % (27 * 8 * cells / 1e9),
+                       "launch": {"variant": launch[0], "tile": [launch[1], launch[2]], "z_chunk": launch[3],
+                                  "autotune_stage_ms": tuned_ms}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp64_peak, "traffic": None,
                          "kernel": "stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,

@@ -135,6 +135,24 @@ const char* hydro_last_error(hydro_t* h);
  * only; the numerical result equals hydro_step's bit for bit. */
 hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double kernel_ms[5]);
 
+/* Launch configuration of the stage kernel.  Several CTA tile shapes are
+ * compiled per scheme (variant 0 is the default); the z-chunk (planes per CTA)
+ * sets how many CTAs share a column.  hydro_set_launch forces a variant
+ * (0 <= variant < hydro_launch_variants(scheme)) and z-chunk (zc <= 0: the
+ * built-in wave-count heuristic), rebuilding the step graph.  Results do not
+ * depend on the choice beyond FMA-level rounding of the same formulas. */
+int32_t hydro_launch_variants(int32_t scheme);
+hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc);
+hydro_status hydro_get_launch(hydro_t* h, int32_t* variant, int32_t* tile_x, int32_t* tile_y, int32_t* zc);
+
+/* Autotuner: with a state loaded, time one stage launch for every compiled
+ * tile shape and a few z-chunks around the heuristic choice on this grid, keep
+ * the fastest and rebuild the step graph (synchronises; the loaded state is
+ * left unchanged).  If the environment variable HYDRO_TUNE_CACHE names a file,
+ * the choice is looked up there first (key: scheme and grid size) and stored
+ * there after tuning.  best_ms (may be NULL) receives the chosen stage time. */
+hydro_status hydro_autotune(hydro_t* h, double* best_ms);
+
 /* Device pointer of the current conserved state (5 fields, stride
  * hydro_field_stride()) for zero-copy readers; owned by h. */
 const double* hydro_state_device_ptr(hydro_t* h);
@@ -145,6 +163,42 @@ int64_t hydro_field_stride(hydro_t* h);
  * returns the FP64 FMA issue rate in FMA/s -- the roofline denominator of the
  * FP64-bound stage kernel.  Allocates and frees a small scratch buffer. */
 hydro_status hydro_measure_fp64_peak(void* stream, double* fma_per_second);
+
+/* ---- Event-by-event ensembles ------------------------------------------
+ * Many independent grids ("events", possibly of different sizes and cell
+ * spacings, one scheme for all) advanced together; the paper motivates GPU
+ * hydro with event-by-event studies (Sec. 1).  Each RK3 stage of ALL events is
+ * one persistent launch of sms x (CTAs per SM) CTAs that pop (event, tile,
+ * z chunk) items from a precomputed work-list with one atomicAdd each and run
+ * the same per-item stage code as hydro_step, so every event's result equals
+ * its single-grid result.  Each event keeps its own speeds, dt and time; a
+ * step is one replay of a captured CUDA graph.  Events are indexed 0..n-1 in
+ * the order of cfgs.  Semantics of set/get/step/sync as for a single grid
+ * (t_end is not supported: steps are always taken). */
+typedef struct hydro_batch_s hydro_batch_t;
+hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void* stream, hydro_batch_t** out);
+hydro_status hydro_batch_destroy(hydro_batch_t* b);
+hydro_status hydro_batch_set_state(hydro_batch_t* b, int32_t event, const double* u, int64_t field_stride, int32_t mem,
+                                   double t);
+hydro_status hydro_batch_set_primitive(hydro_batch_t* b, int32_t event, const double* w, int64_t field_stride,
+                                       int32_t mem, double t);
+hydro_status hydro_batch_step(hydro_batch_t* b, int32_t nsteps);
+hydro_status hydro_batch_get_state(hydro_batch_t* b, int32_t event, double* u, int64_t field_stride, int32_t mem,
+                                   double* t, int64_t* step);
+hydro_status hydro_batch_sync(hydro_batch_t* b);
+int32_t hydro_batch_size(hydro_batch_t* b);
+const char* hydro_batch_last_error(hydro_batch_t* b);
+/* As hydro_profile_step, for the whole batch (kernel_ms: step-begin, the three
+ * persistent stages, step-end). */
+hydro_status hydro_batch_profile_step(hydro_batch_t* b, int32_t nsteps, double kernel_ms[5]);
+/* Tile shape / z chunk of the persistent kernel (variants as for a single
+ * grid); n_items is the work-list length.  hydro_batch_autotune times a
+ * stage-1 launch per candidate (states, speeds and times are unchanged) and
+ * keeps the fastest. */
+hydro_status hydro_batch_set_launch(hydro_batch_t* b, int32_t variant, int32_t zc);
+hydro_status hydro_batch_get_launch(hydro_batch_t* b, int32_t* variant, int32_t* tile_x, int32_t* tile_y, int32_t* zc,
+                                    int32_t* n_items);
+hydro_status hydro_batch_autotune(hydro_batch_t* b, double* best_ms);
 
 /* ---- Stepping without device allocation -------------------------------
  * The paper has no counterpart of this entry point; it exists for callers

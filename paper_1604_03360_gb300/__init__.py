@@ -5,8 +5,8 @@ The hot path runs in hand-written sm_103a CUDA kernels behind the C ABI of
 include/hydro.h (libhydro.so, built in-tree by build.py).  This package is the
 thin Python binding over that ABI.
 """
-from ._binding import (BC_OUTFLOW, BC_PERIODIC, MEM_DEVICE, MEM_HOST, WENO5, WENO7, Hydro, HydroConfig,
+from ._binding import (BC_OUTFLOW, BC_PERIODIC, MEM_DEVICE, MEM_HOST, WENO5, WENO7, Hydro, HydroBatch, HydroConfig,
                        HydroError, LIB_PATH, as_buffer, lib, make_config, measure_fp64_peak)
 
-__all__ = ["Hydro", "HydroConfig", "HydroError", "lib", "make_config", "measure_fp64_peak", "as_buffer", "LIB_PATH",
+__all__ = ["Hydro", "HydroBatch", "HydroConfig", "HydroError", "lib", "make_config", "measure_fp64_peak", "as_buffer", "LIB_PATH",
            "WENO5", "WENO7", "BC_OUTFLOW", "BC_PERIODIC", "MEM_HOST", "MEM_DEVICE"]

@@ -83,10 +83,27 @@ def lib():
         "hydro_get_speeds": ([vp, P(d), P(d)], i32),
         "hydro_profile_step": ([vp, i32, d, P(d)], i32),
         "hydro_last_error": ([vp], ctypes.c_char_p),
+        "hydro_launch_variants": ([i32], i32),
+        "hydro_set_launch": ([vp, i32, i32], i32),
+        "hydro_get_launch": ([vp, P(i32), P(i32), P(i32), P(i32)], i32),
+        "hydro_autotune": ([vp, P(d)], i32),
         "hydro_state_device_ptr": ([vp], vp),
         "hydro_field_stride": ([vp], i64),
         "hydro_version": ([], ctypes.c_char_p),
         "hydro_measure_fp64_peak": ([vp, P(d)], i32),
+        "hydro_batch_create": ([vp, i32, vp, P(vp)], i32),
+        "hydro_batch_destroy": ([vp], i32),
+        "hydro_batch_set_state": ([vp, i32, vp, i64, i32, d], i32),
+        "hydro_batch_set_primitive": ([vp, i32, vp, i64, i32, d], i32),
+        "hydro_batch_step": ([vp, i32], i32),
+        "hydro_batch_get_state": ([vp, i32, vp, i64, i32, P(d), P(i64)], i32),
+        "hydro_batch_sync": ([vp], i32),
+        "hydro_batch_size": ([vp], i32),
+        "hydro_batch_last_error": ([vp], ctypes.c_char_p),
+        "hydro_batch_profile_step": ([vp, i32, P(d)], i32),
+        "hydro_batch_set_launch": ([vp, i32, i32], i32),
+        "hydro_batch_get_launch": ([vp, P(i32), P(i32), P(i32), P(i32), P(i32)], i32),
+        "hydro_batch_autotune": ([vp, P(d)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -179,6 +196,21 @@ class Hydro:
         self._check(self._L.hydro_profile_step(self._h, int(nsteps), float(t_end), ms))
         return np.array(ms[:])
 
+    def autotune(self):
+        """Time the compiled tile shapes / z-chunks on this grid; keep the fastest."""
+        ms = ctypes.c_double()
+        self._check(self._L.hydro_autotune(self._h, ctypes.byref(ms)))
+        return ms.value
+
+    def set_launch(self, variant, zc=0):
+        self._check(self._L.hydro_set_launch(self._h, int(variant), int(zc)))
+
+    def launch(self):
+        """(variant, tile_x, tile_y, z_chunk) of the stage kernel."""
+        v = [ctypes.c_int32() for _ in range(4)]
+        self._check(self._L.hydro_get_launch(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
     def get_state(self, out=None):
         if out is None:
             out = np.empty(self.shape)
@@ -208,6 +240,93 @@ class Hydro:
     def close(self):
         if getattr(self, "_h", None):
             self._L.hydro_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class HydroBatch:
+    """An event-by-event ensemble of independent grids (hydro_batch_t): one
+    persistent launch per RK3 stage walks a work-list of all events' tiles."""
+
+    def __init__(self, grids, stream=None):
+        """grids: sequence of workloads.Grid (or objects with n, dx, scheme, bc,
+        cs2, cfl, eps, origin)."""
+        self._L = lib()
+        self.grids = list(grids)
+        arr = (HydroConfig * len(self.grids))()
+        for i, g in enumerate(self.grids):
+            arr[i] = make_config(g.n, g.dx, g.scheme, g.bc, g.cs2, g.cfl, 0.0, g.eps, g.origin)
+        h = ctypes.c_void_p()
+        rc = self._L.hydro_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.grids), _stream_handle(stream),
+                                        ctypes.byref(h))
+        if rc:
+            raise HydroError(rc, self._L.hydro_batch_last_error(None).decode())
+        self._h = h
+        self.shapes = [(5, g.n[2], g.n[1], g.n[0]) for g in self.grids]
+
+    def __len__(self):
+        return len(self.grids)
+
+    def _check(self, rc):
+        if rc:
+            raise HydroError(rc, self._L.hydro_batch_last_error(self._h).decode())
+
+    def set_state(self, e, u, t=0.0):
+        p, fs, mem = as_buffer(u)
+        self._check(self._L.hydro_batch_set_state(self._h, int(e), p, fs, mem, float(t)))
+
+    def set_primitive(self, e, w, t=0.0):
+        p, fs, mem = as_buffer(w)
+        self._check(self._L.hydro_batch_set_primitive(self._h, int(e), p, fs, mem, float(t)))
+
+    def step(self, nsteps=1):
+        self._check(self._L.hydro_batch_step(self._h, int(nsteps)))
+
+    def get_state(self, e, out=None):
+        if out is None:
+            out = np.empty(self.shapes[e])
+        p, fs, mem = as_buffer(out, writable=True)
+        t = ctypes.c_double()
+        k = ctypes.c_int64()
+        self._check(self._L.hydro_batch_get_state(self._h, int(e), p, fs, mem, ctypes.byref(t), ctypes.byref(k)))
+        return out, t.value, k.value
+
+    def sync(self):
+        self._check(self._L.hydro_batch_sync(self._h))
+
+    def profile_step(self, nsteps=1):
+        ms = (ctypes.c_double * 5)()
+        self._check(self._L.hydro_batch_profile_step(self._h, int(nsteps), ms))
+        return np.array(ms[:])
+
+    def autotune(self):
+        ms = ctypes.c_double()
+        self._check(self._L.hydro_batch_autotune(self._h, ctypes.byref(ms)))
+        return ms.value
+
+    def set_launch(self, variant, zc=0):
+        self._check(self._L.hydro_batch_set_launch(self._h, int(variant), int(zc)))
+
+    def launch(self):
+        """(variant, tile_x, tile_y, z_chunk, work items)."""
+        v = [ctypes.c_int32() for _ in range(5)]
+        self._check(self._L.hydro_batch_get_launch(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.hydro_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,6 +1,7 @@
 // hydro_api.cu -- the C ABI of include/hydro.h for one grid: buffers, the
 // device control block, the captured per-step CUDA graph and the copies.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -24,6 +25,7 @@ struct hydro_s {
     Ctl* hctl = nullptr;             // pinned mirror for read-back
     cudaGraphExec_t exec = nullptr;
     StageLaunch L{};
+    int variant = 0;
     int zc = 0;
     bool have_state = false;
     std::string err;
@@ -283,6 +285,157 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
     }
     for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
     return st;
+}
+
+__global__ void set_dt_kernel(Ctl* c, double dt) { c->dt = dt; }
+
+static hydro_status apply_launch(hydro_t* h, int variant, int zc)
+{
+    StageLaunch L{};
+    cudaError_t e = stage_launch_variant(h->R, variant, &L);
+    if (e == cudaErrorInvalidValue) return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
+    CK(h, e, "stage kernel setup");
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+    if (h->exec) {
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+    }
+    h->L = L;
+    h->variant = variant;
+    h->zc = zc > 0 ? (zc < h->cfg.n[2] ? zc : h->cfg.n[2]) : pick_zc(h->cfg.n[0], h->cfg.n[1], h->cfg.n[2], L, h->sms);
+    return build_graph(h);
+}
+
+static std::string tune_key(const hydro_t* h)
+{
+    char b[96];
+    snprintf(b, sizeof b, "%d %d %d %d", h->R, h->cfg.n[0], h->cfg.n[1], h->cfg.n[2]);
+    return b;
+}
+
+static bool tune_cache_lookup(const hydro_t* h, int* variant, int* zc)
+{
+    const char* path = getenv("HYDRO_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    const std::string key = tune_key(h);
+    char line[256];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        int R, nx, ny, nz, v, z;
+        if (sscanf(line, "%d %d %d %d %d %d", &R, &nx, &ny, &nz, &v, &z) == 6) {
+            char k[96];
+            snprintf(k, sizeof k, "%d %d %d %d", R, nx, ny, nz);
+            if (key == k) {
+                *variant = v;
+                *zc = z;
+                found = true;   // the last matching line wins
+            }
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void tune_cache_store(const hydro_t* h, int variant, int zc)
+{
+    const char* path = getenv("HYDRO_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d\n", tune_key(h).c_str(), variant, zc);
+    fclose(f);
+}
+
+extern "C" int32_t hydro_launch_variants(int32_t scheme)
+{
+    if (scheme == HYDRO_WENO5) return 3;
+    if (scheme == HYDRO_WENO7) return 2;
+    return 0;
+}
+
+extern "C" hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (variant < 0 || variant >= hydro_launch_variants(h->cfg.scheme))
+        return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
+    return apply_launch(h, variant, zc);
+}
+
+extern "C" hydro_status hydro_get_launch(hydro_t* h, int32_t* variant, int32_t* tile_x, int32_t* tile_y, int32_t* zc)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (variant) *variant = h->variant;
+    if (tile_x) *tile_x = h->L.tx;
+    if (tile_y) *tile_y = h->L.ty;
+    if (zc) *zc = h->zc;
+    return HYDRO_OK;
+}
+
+extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
+    int cv = 0, cz = 0;
+    if (tune_cache_lookup(h, &cv, &cz) && cv >= 0 && cv < hydro_launch_variants(h->cfg.scheme)) {
+        if (best_ms) *best_ms = -1.0;
+        return apply_launch(h, cv, cz);
+    }
+    static const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+    const int ncand = (int)(sizeof cand / sizeof cand[0]);
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0), "event");
+    CK(h, cudaEventCreate(&e1), "event");
+    double best = 1e300;
+    int bv = h->variant, bz = h->zc;
+    hydro_status st = HYDRO_OK;
+    // a positive dt makes the stage kernel run; it only writes stage-1 scratch
+    set_dt_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 1e-300);
+    for (int v = 0; v < hydro_launch_variants(h->cfg.scheme) && st == HYDRO_OK; ++v) {
+        StageLaunch L{};
+        if (stage_launch_variant(h->R, v, &L) != cudaSuccess) continue;
+        const int z0 = pick_zc(h->cfg.n[0], h->cfg.n[1], h->cfg.n[2], L, h->sms);
+        int i0 = 0;
+        while (i0 < ncand - 1 && cand[i0] < z0) ++i0;
+        for (int di = -1; di <= 1; ++di) {
+            const int i = i0 + di;
+            if (i < 0 || i >= ncand) continue;
+            int zc = cand[i] < h->cfg.n[2] ? cand[i] : h->cfg.n[2];
+            if (di != 0 && zc == z0) continue;
+            if (di == 0) zc = z0;
+            h->L = L;
+            h->zc = zc;
+            const StageArgs a = stage_args(h, 1);
+            const dim3 grid((h->cfg.n[0] + L.tx - 1) / L.tx, (h->cfg.n[1] + L.ty - 1) / L.ty,
+                            (h->cfg.n[2] + zc - 1) / zc);
+            L.fn<<<grid, L.tx * L.ty, L.smem, h->stream>>>(a);   // warm-up
+            cudaEventRecord(e0, h->stream);
+            L.fn<<<grid, L.tx * L.ty, L.smem, h->stream>>>(a);
+            cudaEventRecord(e1, h->stream);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                st = cuda_fail(h, e, "autotune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bv = v;
+                bz = zc;
+            }
+            if (zc == h->cfg.n[2]) break;
+        }
+    }
+    set_dt_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 0.0);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HYDRO_OK) return st;
+    if (best_ms) *best_ms = best;
+    tune_cache_store(h, bv, bz);
+    return apply_launch(h, bv, bz);
 }
 
 static hydro_status read_ctl(hydro_t* h)

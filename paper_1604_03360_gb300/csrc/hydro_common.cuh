@@ -70,14 +70,19 @@ inline StepParams step_params(const hydro_config& cfg)
 // validate a config; returns an empty string when it is usable
 std::string check_config(const hydro_config* c);
 
-// stage kernel dispatch for a scheme (R = 3 or 4)
+// stage kernel dispatch for a scheme (R = 3 or 4) and a tile shape
 struct StageLaunch {
     void (*fn)(StageArgs);
     size_t smem;
     int tx, ty;
     int ctas_per_sm;
 };
-cudaError_t stage_launch_info(int R, StageLaunch* out);
+// tile shapes compiled for each scheme; index 0 is the default
+constexpr int kTileVariants = 3;
+// fills *out for variant v (0 <= v < kTileVariants); returns
+// cudaErrorInvalidValue for a variant that does not exist for this scheme
+cudaError_t stage_launch_variant(int R, int v, StageLaunch* out);
+inline cudaError_t stage_launch_info(int R, StageLaunch* out) { return stage_launch_variant(R, 0, out); }
 
 inline int pick_zc(int nx, int ny, int nz, const StageLaunch& L, int sms)
 {

@@ -115,10 +115,9 @@ __global__ void state_to_prim_kernel(const double* u, long long fs, double* out,
     }
 }
 
-template <int R>
+template <int R, int TX, int TY>
 static cudaError_t info_for(StageLaunch* out)
 {
-    constexpr int TX = 16, TY = 8;
     out->fn = stage_kernel<R, TX, TY>;
     out->smem = StageSmem<R, TX, TY>::bytes;
     out->tx = TX;
@@ -130,10 +129,19 @@ static cudaError_t info_for(StageLaunch* out)
                                                          out->smem);
 }
 
-cudaError_t stage_launch_info(int R, StageLaunch* out)
+// WENO5: 16x16 (1 CTA of 8 warps per SM), 16x8 (2 CTAs of 4 warps), 32x8.
+// WENO7: 16x16 (8 warps, 221 KB shared memory), 16x8 (4 warps).
+cudaError_t stage_launch_variant(int R, int v, StageLaunch* out)
 {
-    if (R == 3) return info_for<3>(out);
-    if (R == 4) return info_for<4>(out);
+    if (R == 3) {
+        if (v == 0) return info_for<3, 16, 16>(out);
+        if (v == 1) return info_for<3, 16, 8>(out);
+        if (v == 2) return info_for<3, 32, 8>(out);
+    }
+    if (R == 4) {
+        if (v == 0) return info_for<4, 16, 16>(out);
+        if (v == 1) return info_for<4, 16, 8>(out);
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -90,13 +90,14 @@ __device__ __forceinline__ void split_flux(int d, const double u[5], const doubl
     }
 }
 
+// One work item: column tile (tile_x, tile_y) of TX x TY cells and z chunk chunk_z of the
+// grid described by a.  All threads of the CTA call it with the same item.
 template <int R, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (R == 3 ? 2 : 1)) stage_kernel(const StageArgs a)
+__device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
 {
     using SM = StageSmem<R, TX, TY>;
     constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING;
     constexpr int GXW = SM::GXW, GYH = SM::GYH;
-    extern __shared__ __align__(16) double smem[];
     double* ring = smem;
     double* gx = ring + SM::RING;
     double* gy = gx + SM::GX;
@@ -110,8 +111,8 @@ __global__ void __launch_bounds__(TX * TY, (R == 3 ? 2 : 1)) stage_kernel(const 
     for (int d = 0; d < 3; ++d) al[d] = __longlong_as_double((long long)a.alpha_in[d]);
 
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int zb = blockIdx.z * a.zc, ze = min(zb + a.zc, a.nz);
+    const int x0 = tile_x * TX, y0 = tile_y * TY;
+    const int zb = chunk_z * a.zc, ze = min(zb + a.zc, a.nz);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = (x < nx) && (y < ny);
@@ -299,6 +300,13 @@ __global__ void __launch_bounds__(TX * TY, (R == 3 ? 2 : 1)) stage_kernel(const 
         }
         if ((tid & 31) == 0 && v) atomicMax(a.alpha_out + d, v);
     }
+}
+
+template <int R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) stage_kernel(const StageArgs a)
+{
+    extern __shared__ __align__(16) double smem[];
+    stage_tile<R, TX, TY>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 }  // namespace hydro

@@ -181,3 +181,38 @@ def test_unphysical_state_reported():
         with pytest.raises(HydroError) as ei:
             h.sync()
         assert ei.value.code == 4
+
+
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (7, 0), (7, 1)])
+def test_every_launch_variant(scheme, variant):
+    """Every compiled CTA tile shape, with a short z chunk so several chunks
+    meet inside the grid, matches the oracle."""
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=(37, 29, 21), seed=77, scheme=scheme)
+    w = with_flow(g, w)
+    u0 = oracle.prim2con(w)
+    ref = oracle.run(oracle_cfg(g), u0, 4)[0]
+    with Hydro.from_grid(g) as h:
+        h.set_launch(variant, 8)
+        assert h.launch()[0] == variant and h.launch()[3] == 8
+        h.set_state(u0)
+        h.step(4)
+        got = h.get_state()
+    assert np.all(field_errors(got, ref) <= TOL)
+
+
+def test_autotune_keeps_results(tmp_path, monkeypatch):
+    from paper_1604_03360_gb300 import Hydro
+    monkeypatch.setenv("HYDRO_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    g, w = W.ellipsoidal(N=40, scheme=7)
+    u0 = oracle.prim2con(w)
+    ref = oracle.run(oracle_cfg(g), u0, 3)[0]
+    for attempt in range(2):          # second pass reads the cache
+        with Hydro.from_grid(g) as h:
+            h.set_state(u0)
+            ms = h.autotune()
+            assert (ms > 0) if attempt == 0 else (ms == -1.0)
+            h.step(3)
+            got = h.get_state()
+        assert np.all(field_errors(got, ref) <= TOL)
+    assert (tmp_path / "tune.txt").read_text().strip()

@@ -116,20 +116,28 @@ def ellipsoidal(N=256, scheme=7, box=12.0, e0=20.0, axes=(2.0, 3.0, 4.0), v_corn
     return g, _stack(g, e, x / (t0 * a[0] ** 2), y / (t0 * a[1] ** 2), z / (t0 * a[2] ** 2), e / e0)
 
 
-def lumpy(n=(96, 96, 96), seed=1604, box=6.0, blobs=20, width=0.5, radius=4.0, mu=1.0,
-          sigma=0.5, scheme=5, nsteps=50, cfl=0.3):
-    """e = 0.1 + sum of `blobs` Gaussians of width `width`, centres uniform in a
-    ball of radius `radius`, amplitudes lognormal(mu, sigma); v = 0; n = e.
-    Box [-box, box] per axis with dx_d = 2 box / n_d (uneven boxes allowed)."""
+def lumpy_params(seed=1604, blobs=20, radius=4.0, mu=1.0, sigma=0.5):
+    """Seeded hot-spot parameters: centres uniform in a ball of radius
+    `radius` (direction from 3 normals, radius r U^(1/3)), amplitudes
+    lognormal(mu, sigma)."""
     rng = np.random.default_rng(seed)
     dirs = rng.standard_normal((blobs, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
     rad = radius * rng.random(blobs) ** (1.0 / 3.0)
     centres = dirs * rad[:, None]
     amps = rng.lognormal(mean=mu, sigma=sigma, size=blobs)
+    return centres, amps
+
+
+def lumpy(n=(96, 96, 96), seed=1604, box=6.0, blobs=20, width=0.5, radius=4.0, mu=1.0,
+          sigma=0.5, scheme=5, nsteps=50, cfl=0.3):
+    """e = 0.1 + sum of `blobs` Gaussians of width `width` (parameters from
+    lumpy_params); v = 0; n = e.  Box [-box, box] per axis with
+    dx_d = 2 box / n_d (uneven boxes allowed)."""
+    centres, amps = lumpy_params(seed, blobs, radius, mu, sigma)
     dx = tuple(2.0 * box / int(k) for k in n)
     g = Grid(n=tuple(int(k) for k in n), dx=dx, origin=(-box,) * 3, bc=(0, 0, 0), scheme=scheme,
-             cfl=cfl, nsteps=nsteps, name="lumpy", extra=dict(seed=seed))
+             cfl=cfl, nsteps=nsteps, name="lumpy", extra=dict(seed=seed, width=width))
     x, y, z = g.centres()
     e = np.full((g.n[2], g.n[1], g.n[0]), 0.1)
     for c, A in zip(centres, amps):
@@ -149,6 +157,13 @@ def batch_sizes(events=256, seed=1604, lo=48, hi=160):
 def batch_event(i, sizes, seed=1604, scheme=5, nsteps=100):
     """Event i of the event-by-event ensemble: lumpy data, seed seed + i."""
     return lumpy(n=sizes[i], seed=seed + i, scheme=scheme, nsteps=nsteps)
+
+
+def batch_grid(i, sizes, scheme=5, box=6.0, nsteps=100, cfl=0.3):
+    """Grid of event i (the data comes from batch_event or lumpy_params)."""
+    n = sizes[i]
+    return Grid(n=tuple(int(k) for k in n), dx=tuple(2.0 * box / int(k) for k in n), origin=(-box,) * 3,
+                bc=(0, 0, 0), scheme=scheme, cfl=cfl, nsteps=nsteps, name="lumpy-event")
 
 
 def smooth_periodic(n=(12, 12, 12), seed=7, amp=0.2, vamp=0.3, scheme=5, length=1.0):

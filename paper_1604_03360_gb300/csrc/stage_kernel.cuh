@@ -153,10 +153,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         weno_right<R>(vm, a.eps_s, Nm, Dm);
     };
 
+    // columns outside the grid (ragged tiles) have no z-faces to compute: their
+    // ring is private and nobody reads it
+    const bool zwork = zact && own;
     double hNp[5], hDp[5], Fzm[5], Fzp[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) { hNp[k] = 0.0; hDp[k] = 1.0; Fzm[k] = 0.0; Fzp[k] = 0.0; }
-    if (zact) {
+    if (zwork) {
         for (int m = zb - G; m <= zb + G - 2; ++m) ingest(m);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -175,14 +178,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 
     unsigned long long amax[3] = {0ull, 0ull, 0ull};
-    const int nfx = a.act[0] ? 5 * TY * (TX + 1) : 0;
-    const int nfy = a.act[1] ? 5 * (TY + 1) * TX : 0;
-    const int ngx = a.act[0] ? TY * GXW : 0;
-    const int ngy = a.act[1] ? GYH * TX : 0;
+    // only the rows / columns of the tile inside the grid (plus halo) do work
+    const int ncol = min(TX, nx - x0), nrow = min(TY, ny - y0);
+    const int wx = ncol + 2 * G, hy = nrow + 2 * G;      // staged extents
+    const int nfx = a.act[0] ? 5 * nrow * (ncol + 1) : 0;
+    const int nfy = a.act[1] ? 5 * (nrow + 1) * ncol : 0;
+    const int ngx = a.act[0] ? nrow * wx : 0;
+    const int ngy = a.act[1] ? hy * ncol : 0;
 
     for (int p = zb; p < ze; ++p) {
         // 1. z: ingest plane p+G, face p+1/2 = R+(p) + R-(p+1)
-        if (zact) {
+        if (zwork) {
             ingest(p + G);
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -198,7 +204,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         for (int it = tid; it < ngx + ngy; it += NT) {
             double u[5], w[4], gp[5], gm[5];
             if (it < ngx) {
-                const int row = it / GXW, col = it % GXW;
+                const int row = it / wx, col = it % wx;
                 const int xx = bc_map(x0 - G + col, nx, a.bc[0]), yy = bc_map(y0 + row, ny, a.bc[1]);
                 load(qz + (long long)yy * nx + xx, u, w);
                 split_flux(0, u, w, al[0], gp, gm);
@@ -208,7 +214,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                     gx[((5 + k) * TY + row) * GXW + col] = gm[k];
                 }
             } else {
-                const int j = it - ngx, row = j / TX, col = j % TX;
+                const int j = it - ngx, row = j / ncol, col = j % ncol;
                 const int xx = bc_map(x0 + col, nx, a.bc[0]), yy = bc_map(y0 - G + row, ny, a.bc[1]);
                 load(qz + (long long)yy * nx + xx, u, w);
                 split_flux(1, u, w, al[1], gp, gm);
@@ -224,8 +230,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         for (int it = tid; it < nfx + nfy; it += NT) {
             double vp[S], vm[S], Np, Dp, Nm, Dm;
             if (it < nfx) {
-                const int k = it / (TY * (TX + 1)), rr = it % (TY * (TX + 1));
-                const int row = rr / (TX + 1), f = rr % (TX + 1);   // face f - 1/2 of the tile
+                const int k = it / (nrow * (ncol + 1)), rr = it % (nrow * (ncol + 1));
+                const int row = rr / (ncol + 1), f = rr % (ncol + 1);   // face f - 1/2 of the tile
                 const double* gpr = gx + (k * TY + row) * GXW;
                 const double* gmr = gx + ((5 + k) * TY + row) * GXW;
 #pragma unroll
@@ -238,8 +244,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 Fx[(k * TY + row) * (TX + 1) + f] = face_sum(Np, Dp, Nm, Dm);
             } else {
                 const int j = it - nfx;
-                const int k = j / ((TY + 1) * TX), rr = j % ((TY + 1) * TX);
-                const int f = rr / TX, col = rr % TX;                 // face f - 1/2 along y
+                const int k = j / ((nrow + 1) * ncol), rr = j % ((nrow + 1) * ncol);
+                const int f = rr / ncol, col = rr % ncol;             // face f - 1/2 along y
                 const double* gpc = gy + (k * GYH) * TX + col;
                 const double* gmc = gy + ((5 + k) * GYH) * TX + col;
 #pragma unroll

@@ -164,6 +164,36 @@ int64_t hydro_field_stride(hydro_t* h);
  * FP64-bound stage kernel.  Allocates and frees a small scratch buffer. */
 hydro_status hydro_measure_fp64_peak(void* stream, double* fma_per_second);
 
+/* ---- Reverse mode (adjoint) --------------------------------------------
+ * Gradients of a final-state observable with respect to the initial state.
+ * The Lax-Friedrichs speeds and time steps are frozen at their forward values
+ * (they are maxima over the grid and not differentiable); the WENO weights
+ * (epsilon > 0) are smooth, so every other ingredient is differentiated
+ * exactly.  The paper's scheme (Sec. 1, Eq. 2, Sec. 1.2) is the function
+ * being differentiated; the adjoint itself is not in the paper.
+ *
+ * hydro_forward_record: advance the current state by nsteps RK3 steps (no
+ *   t_end), recording each step's speeds and dt and checkpointing the state
+ *   every ckpt_every steps (device workspace owned by h, about
+ *   (57 + 5 * (ceil(nsteps/ckpt_every) + ckpt_every)) doubles per cell).
+ *   Asynchronous.
+ * hydro_adjoint: grad_u0 = (d u_N / d u_0)^T lambda_final for the recorded
+ *   run: segment by segment, the step-start states are recomputed from the
+ *   checkpoint with frozen stages, then each step's three stage adjoints run
+ *   in reverse.  lambda_final and grad_u0: 5 fields with field_stride, in
+ *   `mem`.  Synchronises.  HYDRO_ERR_STATE if nothing was recorded.
+ * hydro_recorded_steps: number of recorded steps and (either may be NULL)
+ *   the speeds alpha[n][stage][axis] (9 per step) and dt[n].  Synchronises.
+ * hydro_eps2: momentum anisotropy eps_2 = sum(T^xx - T^yy) / sum(T^xx + T^yy)
+ *   of state u (NULL: the current state) and, if grad != NULL, its gradient
+ *   with respect to the conserved fields (5 fields, R component zero).
+ *   Synchronises. */
+hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t ckpt_every);
+hydro_status hydro_adjoint(hydro_t* h, const double* lambda_final, double* grad_u0, int64_t field_stride, int32_t mem);
+hydro_status hydro_recorded_steps(hydro_t* h, int32_t* nsteps, double* alpha, double* dt);
+hydro_status hydro_eps2(hydro_t* h, const double* u, int64_t field_stride, int32_t mem, double* eps2, double* grad,
+                        int64_t grad_stride, int32_t grad_mem);
+
 /* ---- Event-by-event ensembles ------------------------------------------
  * Many independent grids ("events", possibly of different sizes and cell
  * spacings, one scheme for all) advanced together; the paper motivates GPU

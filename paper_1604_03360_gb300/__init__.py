@@ -8,5 +8,7 @@ thin Python binding over that ABI.
 from ._binding import (BC_OUTFLOW, BC_PERIODIC, MEM_DEVICE, MEM_HOST, WENO5, WENO7, Hydro, HydroBatch, HydroConfig,
                        HydroError, LIB_PATH, as_buffer, lib, make_config, measure_fp64_peak)
 
-__all__ = ["Hydro", "HydroBatch", "HydroConfig", "HydroError", "lib", "make_config", "measure_fp64_peak", "as_buffer", "LIB_PATH",
+from . import autograd  # noqa: E402  (torch.autograd.Function wrappers of the adjoint)
+
+__all__ = ["autograd", "Hydro", "HydroBatch", "HydroConfig", "HydroError", "lib", "make_config", "measure_fp64_peak", "as_buffer", "LIB_PATH",
            "WENO5", "WENO7", "BC_OUTFLOW", "BC_PERIODIC", "MEM_HOST", "MEM_DEVICE"]

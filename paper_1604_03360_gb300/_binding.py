@@ -91,6 +91,10 @@ def lib():
         "hydro_field_stride": ([vp], i64),
         "hydro_version": ([], ctypes.c_char_p),
         "hydro_measure_fp64_peak": ([vp, P(d)], i32),
+        "hydro_forward_record": ([vp, i32, i32], i32),
+        "hydro_adjoint": ([vp, vp, vp, i64, i32], i32),
+        "hydro_recorded_steps": ([vp, P(i32), vp, vp], i32),
+        "hydro_eps2": ([vp, vp, i64, i32, P(d), vp, i64, i32], i32),
         "hydro_batch_create": ([vp, i32, vp, P(vp)], i32),
         "hydro_batch_destroy": ([vp], i32),
         "hydro_batch_set_state": ([vp, i32, vp, i64, i32, d], i32),
@@ -171,7 +175,7 @@ class Hydro:
     def from_grid(cls, g, stream=None):
         """Create from a workloads.Grid description."""
         return cls(g.n, g.dx, scheme=g.scheme, bc=g.bc, cs2=g.cs2, cfl=g.cfl, eps=g.eps, origin=g.origin,
-                   stream=stream)
+                   dt_fixed=getattr(g, "dt_fixed", 0.0), stream=stream)
 
     def _check(self, rc):
         if rc:
@@ -210,6 +214,44 @@ class Hydro:
         v = [ctypes.c_int32() for _ in range(4)]
         self._check(self._L.hydro_get_launch(self._h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def forward_record(self, nsteps, ckpt_every=10):
+        """Advance nsteps steps, recording speeds/dt and checkpoints for adjoint()."""
+        self._check(self._L.hydro_forward_record(self._h, int(nsteps), int(ckpt_every)))
+
+    def adjoint(self, lam, out=None):
+        """(d u_N / d u_0)^T lam for the recorded run (frozen speeds and dt)."""
+        if out is None:
+            out = np.empty(self.shape) if isinstance(lam, np.ndarray) else lam.new_empty(lam.shape)
+        pl, fs, mem = as_buffer(lam)
+        po, fo, memo = as_buffer(out, writable=True)
+        if fs != fo or mem != memo:
+            raise ValueError("lam and out must have the same layout and memory kind")
+        self._check(self._L.hydro_adjoint(self._h, pl, po, fs, mem))
+        return out
+
+    def recorded_steps(self):
+        n = ctypes.c_int32()
+        self._check(self._L.hydro_recorded_steps(self._h, ctypes.byref(n), None, None))
+        al = np.empty((max(n.value, 1), 3, 3))
+        dt = np.empty(max(n.value, 1))
+        self._check(self._L.hydro_recorded_steps(self._h, ctypes.byref(n), ctypes.c_void_p(al.ctypes.data),
+                                                 ctypes.c_void_p(dt.ctypes.data)))
+        return al[:n.value], dt[:n.value]
+
+    def eps2(self, u=None, grad=None):
+        """eps_2 of u (default: the current state); fills grad (same layout) if given."""
+        e = ctypes.c_double()
+        if u is not None:
+            pu, fu, mu = as_buffer(u)
+        else:
+            pu, fu, mu = None, 0, 0
+        if grad is not None:
+            pg, fg, mg = as_buffer(grad, writable=True)
+        else:
+            pg, fg, mg = None, 0, 0
+        self._check(self._L.hydro_eps2(self._h, pu, fu, mu, ctypes.byref(e), pg, fg, mg))
+        return e.value
 
     def get_state(self, out=None):
         if out is None:
@@ -266,7 +308,8 @@ class HydroBatch:
         self.grids = list(grids)
         arr = (HydroConfig * len(self.grids))()
         for i, g in enumerate(self.grids):
-            arr[i] = make_config(g.n, g.dx, g.scheme, g.bc, g.cs2, g.cfl, 0.0, g.eps, g.origin)
+            arr[i] = make_config(g.n, g.dx, g.scheme, g.bc, g.cs2, g.cfl, getattr(g, "dt_fixed", 0.0), g.eps,
+                                 g.origin)
         h = ctypes.c_void_p()
         rc = self._L.hydro_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.grids), _stream_handle(stream),
                                         ctypes.byref(h))

@@ -1,0 +1,722 @@
+// hydro_adjoint.cu -- reverse mode (vector-Jacobian product) of N steps of the
+// WENO + SSP-RK3 scheme, with the Lax-Friedrichs speeds and the time steps
+// frozen at their forward values (their maxima are not differentiable), and
+// the momentum-anisotropy observable eps_2 with its gradient.
+//
+// Forward with recording: every step stores its speeds (stage inputs) and dt;
+// the state is checkpointed every `ckpt_every` steps.  Backward, segment by
+// segment from the last: recompute the segment's step-start states from its
+// checkpoint with frozen stages, then for each step (last first) rebuild the
+// stage-1 and stage-2 states and run the three stage adjoints in reverse:
+//   u_out = ca u_n + cb (u_s + dt L(u_s))  =>
+//   lam_s = cb lam_out + J_L(u_s)^T (cb dt lam_out),  lam_n += ca lam_out.
+// J_L^T mu is a sum over axes.  Per axis, one thread per (pencil, field)
+// sweeps the pencil's faces with a register window: face adjoint
+// F~bar_{j+1/2} = hdx (mu_{j+1} - mu_j), reverse-mode WENO of both biased
+// reconstructions into the split-flux adjoints gbar+-, ghost-cell
+// contributions folded back onto their source cells by the boundary rule (no
+// atomics anywhere); then a cell kernel applies
+//   ubar += J_f(u)^T (gbar+ + gbar-) + alpha (gbar+ - gbar-).
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hydro_common.cuh"
+
+namespace hydro {
+
+// ---------------------------------------------------------------- WENO VJPs
+// Linear forms of the scaled reconstructions (same definitions as weno5 /
+// weno7 in hydro_math.cuh): b_k = eps_s + c1 L1_k^2 + c2 L2_k^2 (+ c3 L3_k^2),
+// w_k = b_k^2, N = sum n_k prod_{m!=k} w_m, D = sum dc_k prod_{m!=k} w_m,
+// value = N / D.  vb += Rbar * d(N/D)/dv.
+template <int R>
+struct WenoForms;
+
+template <>
+struct WenoForms<3> {
+    static constexpr int S = 5, NL = 2;
+    __device__ static double L(int l, int k, int i)
+    {
+        // l = 0: first-derivative form t_k; l = 1: second difference s_k
+        const double t[3][5] = {{1, -4, 3, 0, 0}, {0, -1, 0, 1, 0}, {0, 0, -3, 4, -1}};
+        const double s[3][5] = {{1, -2, 1, 0, 0}, {0, 1, -2, 1, 0}, {0, 0, 1, -2, 1}};
+        return l == 0 ? t[k][i] : s[k][i];
+    }
+    __device__ static double n(int k, int i)
+    {
+        const double c[3][5] = {{1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0, 0}, {0, -1, 5, 2, 0}, {0, 0, 1, 2.5, -0.5}};
+        return c[k][i];
+    }
+    __device__ static double c(int l) { return l == 0 ? 1.0 : 13.0 / 3.0; }
+    __device__ static double dc(int k) { return k == 0 ? 1.0 : (k == 1 ? 6.0 : 3.0); }
+};
+
+template <>
+struct WenoForms<4> {
+    static constexpr int S = 7, NL = 3;
+    __device__ static double L(int l, int k, int i)
+    {
+        const double A[4][7] = {{-2, 9, -18, 11, 0, 0, 0}, {0, 1, -6, 3, 2, 0, 0}, {0, 0, -2, -3, 6, -1, 0},
+                                {0, 0, 0, -11, 18, -9, 2}};
+        const double B[4][7] = {{-1, 4, -5, 2, 0, 0, 0}, {0, 0, 1, -2, 1, 0, 0}, {0, 0, 1, -2, 1, 0, 0},
+                                {0, 0, 0, 2, -5, 4, -1}};
+        const double C[4][7] = {{-1, 3, -3, 1, 0, 0, 0}, {0, -1, 3, -3, 1, 0, 0}, {0, 0, -1, 3, -3, 1, 0},
+                                {0, 0, 0, -1, 3, -3, 1}};
+        return l == 0 ? A[k][i] : (l == 1 ? B[k][i] : C[k][i]);
+    }
+    __device__ static double n(int k, int i)
+    {
+        const double c[4][7] = {{-0.25, 13.0 / 12.0, -23.0 / 12.0, 25.0 / 12.0, 0, 0, 0},
+                                {0, 1, -5, 13, 3, 0, 0},
+                                {0, 0, -1.5, 10.5, 10.5, -1.5, 0},
+                                {0, 0, 0, 1, 13.0 / 3.0, -5.0 / 3.0, 1.0 / 3.0}};
+        return c[k][i];
+    }
+    __device__ static double c(int l) { return l == 0 ? 1.0 : (l == 1 ? 39.0 : 781.0 / 20.0); }
+    __device__ static double dc(int k) { return k == 0 ? 1.0 : (k == 1 ? 12.0 : (k == 2 ? 18.0 : 4.0)); }
+};
+
+template <int R>
+__device__ __forceinline__ void weno_left_vjp(const double* v, double eps_s, double Rbar, double* vb)
+{
+    using F = WenoForms<R>;
+    constexpr int S = F::S, NL = F::NL;
+    double Lf[NL][R], nk[R], b[R], w[R], P[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        double bk = eps_s;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            double x = 0.0;
+#pragma unroll
+            for (int i = 0; i < S; ++i)
+                if (F::L(l, k, i) != 0.0) x = fma(F::L(l, k, i), v[i], x);
+            Lf[l][k] = x;
+            bk = fma(F::c(l) * x, x, bk);
+        }
+        double y = 0.0;
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+            if (F::n(k, i) != 0.0) y = fma(F::n(k, i), v[i], y);
+        nk[k] = y;
+        b[k] = bk;
+        w[k] = bk * bk;
+    }
+    double N = 0.0, D = 0.0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        double p = 1.0;
+#pragma unroll
+        for (int m = 0; m < R; ++m)
+            if (m != k) p *= w[m];
+        P[k] = p;
+        N = fma(nk[k], p, N);
+        D = fma(F::dc(k), p, D);
+    }
+    const double iD = rcp(D);
+    const double Nb = Rbar * iD;
+    const double Db = -Nb * N * iD;
+    double Pb[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) Pb[k] = fma(Nb, nk[k], Db * F::dc(k));
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        double wb = 0.0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (k == m) continue;
+            double p = 1.0;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (j != k && j != m) p *= w[j];
+            wb = fma(Pb[k], p, wb);
+        }
+        const double bb = 2.0 * b[m] * wb;
+        const double nb = Nb * P[m];
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            double g = F::n(m, i) * nb;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) g = fma(F::L(l, m, i) * 2.0 * F::c(l) * Lf[l][m], bb, g);
+            vb[i] += g;
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void weno_right_vjp(const double* v, double eps_s, double Rbar, double* vb)
+{
+    constexpr int S = 2 * R - 1;
+    double m[S], mb[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        m[i] = v[S - 1 - i];
+        mb[i] = 0.0;
+    }
+    weno_left_vjp<R>(m, eps_s, Rbar, mb);
+#pragma unroll
+    for (int i = 0; i < S; ++i) vb[S - 1 - i] += mb[i];
+}
+
+// ------------------------------------------------------------ adjoint kernels
+struct AdjPencilArgs {
+    const double* u;                    // stage input state (5 fields)
+    const double* w;                    // its p, v_x, v_y, v_z
+    const double* lam;                  // adjoint of the stage output (5 fields)
+    double* gp;                         // out: adjoint of g+ along axis d (5 fields)
+    double* gm;                         // out: adjoint of g- along axis d (5 fields)
+    const unsigned long long* rec;      // step record: speeds [3 stages][3 axes], dt
+    long long fs;
+    int n[3], bc[3];
+    int d, stage;
+    double hdx, cb, eps_s;
+};
+
+template <int R>
+__global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
+{
+    constexpr int G = R, Wn = 2 * R;
+    const int d = a.d, nd = a.n[d];
+    const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+    const long long npen = (long long)a.n[da] * a.n[db];
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= npen * 5) return;
+    const int k = (int)(tid / npen);
+    const long long pen = tid % npen;
+    const long long st[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
+    const long long base = (pen % a.n[da]) * st[da] + (pen / a.n[da]) * st[db];
+    const long long stp = st[d];
+    const long long fs = a.fs;
+    const double alpha = __longlong_as_double((long long)a.rec[3 * (a.stage - 1) + d]);
+    const double dt = __longlong_as_double((long long)a.rec[9]);
+    const double sc = a.cb * dt * a.hdx;
+
+    auto gval = [&](int m, double& gpv, double& gmv) {
+        const long long q = base + (long long)bc_map(m, nd, a.bc[d]) * stp;
+        const double uk = a.u[k * fs + q];
+        const double vd = a.w[(1 + d) * fs + q];
+        double f;
+        if (k == 0) f = a.u[(1 + d) * fs + q];
+        else f = uk * vd + (k == 1 + d ? a.w[q] : 0.0);
+        gpv = fma(alpha, uk, f);
+        gmv = fma(-alpha, uk, f);
+    };
+    double gpw[Wn], gmw[Wn], ap[Wn], am[Wn], lo_p[G], lo_m[G], hi_p[G], hi_m[G];
+#pragma unroll
+    for (int i = 0; i < Wn; ++i) {
+        gval(-G + i, gpw[i], gmw[i]);
+        ap[i] = am[i] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i) lo_p[i] = lo_m[i] = hi_p[i] = hi_m[i] = 0.0;
+    auto emit = [&](int m, double vp, double vm) {
+        if (m >= 0 && m < nd) {
+            const long long q = base + (long long)m * stp;
+            a.gp[k * fs + q] = vp;
+            a.gm[k * fs + q] = vm;
+        } else if (m < 0) {
+#pragma unroll
+            for (int i = 0; i < G; ++i)
+                if (m == i - G) { lo_p[i] += vp; lo_m[i] += vm; }
+        } else {
+#pragma unroll
+            for (int i = 0; i < G; ++i)
+                if (m == nd + i) { hi_p[i] += vp; hi_m[i] += vm; }
+        }
+    };
+    double lamL = 0.0;
+    for (int j = -1; j <= nd - 1; ++j) {
+        const double lamR = (j + 1 < nd) ? a.lam[k * fs + base + (long long)(j + 1) * stp] : 0.0;
+        const double Fb = sc * (lamR - lamL);
+        lamL = lamR;
+        weno_left_vjp<R>(gpw, a.eps_s, Fb, ap);           // cells j-G+1 .. j+G-1
+        weno_right_vjp<R>(gmw + 1, a.eps_s, Fb, am + 1);  // cells j-G+2 .. j+G
+        emit(j - G + 1, ap[0], am[0]);
+#pragma unroll
+        for (int i = 0; i < Wn - 1; ++i) {
+            gpw[i] = gpw[i + 1];
+            gmw[i] = gmw[i + 1];
+            ap[i] = ap[i + 1];
+            am[i] = am[i + 1];
+        }
+        if (j + 1 <= nd - 1) gval(j + G + 1, gpw[Wn - 1], gmw[Wn - 1]);
+        ap[Wn - 1] = am[Wn - 1] = 0.0;
+    }
+    // cells nd-G+1 .. nd+G-1 are complete
+#pragma unroll
+    for (int i = 0; i < Wn - 1; ++i) emit(nd - G + 1 + i, ap[i], am[i]);
+    // ghost cells fold back onto their source cells
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        const long long ql = base + (long long)bc_map(i - G, nd, a.bc[d]) * stp;
+        a.gp[k * fs + ql] += lo_p[i];
+        a.gm[k * fs + ql] += lo_m[i];
+        const long long qh = base + (long long)bc_map(nd + i, nd, a.bc[d]) * stp;
+        a.gp[k * fs + qh] += hi_p[i];
+        a.gm[k * fs + qh] += hi_m[i];
+    }
+}
+
+// V += J_f(u)^T (gp + gm) + alpha (gp - gm) for axis d
+__global__ void adj_flux_kernel(const double* u, const double* w, const double* gp, const double* gm, double* V,
+                                const unsigned long long* rec, int stage, int d, long long fs, long long ncell,
+                                double cs2)
+{
+    const double alpha = __longlong_as_double((long long)rec[3 * (stage - 1) + d]);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+         q += (long long)gridDim.x * blockDim.x) {
+        double s[5], t[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            const double a = gp[f * fs + q], b = gm[f * fs + q];
+            s[f] = a + b;
+            t[f] = a - b;
+        }
+        const double E = u[q], M[3] = {u[fs + q], u[2 * fs + q], u[3 * fs + q]}, Rr = u[4 * fs + q];
+        const double p = w[q], v[3] = {w[fs + q], w[2 * fs + q], w[3 * fs + q]};
+        const double h = E + p, ih = 1.0 / h;
+        const double Q = fma(2.0, p, (1.0 - cs2) * E);
+        const double iQ = 1.0 / Q;
+        const double pE = (2.0 * cs2 * E - (1.0 - cs2) * p) * iQ;
+        double pM[3];
+        for (int j = 0; j < 3; ++j) pM[j] = -2.0 * cs2 * M[j] * iQ;
+        const double vd = v[d];
+        const double S = s[1] * M[0] + s[2] * M[1] + s[3] * M[2] + s[4] * Rr;
+        const double vdE = -vd * (1.0 + pE) * ih;
+        double ub[5];
+        ub[0] = S * vdE + s[1 + d] * pE;
+        for (int j = 0; j < 3; ++j) {
+            const double vdM = ((j == d ? 1.0 : 0.0) - vd * pM[j]) * ih;
+            ub[1 + j] = (j == d ? s[0] : 0.0) + s[1 + j] * vd + S * vdM + s[1 + d] * pM[j];
+        }
+        ub[4] = s[4] * vd;
+#pragma unroll
+        for (int f = 0; f < 5; ++f) V[f * fs + q] += fma(alpha, t[f], ub[f]);
+    }
+}
+
+// lam_s = cb lam + V (+ acc); acc = (reset ? 0 : acc) + ca lam
+__global__ void adj_combine_kernel(const double* lam, const double* V, double* out, double* acc, double ca, double cb,
+                                   int add_acc, int reset_acc, long long fs, long long ncell)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+         q += (long long)gridDim.x * blockDim.x)
+        for (int f = 0; f < 5; ++f) {
+            const long long i = f * fs + q;
+            const double l = lam[i];
+            double o = fma(cb, l, V[i]);
+            if (add_acc) o += acc[i];
+            out[i] = o;
+            if (!add_acc) acc[i] = reset_acc ? ca * l : fma(ca, l, acc[i]);
+        }
+}
+
+__global__ void record_kernel(const Ctl* c, unsigned long long* rec)
+{
+    for (int d = 0; d < 3; ++d) {
+        rec[d] = c->a_cur[d];
+        rec[3 + d] = c->a_s1[d];
+        rec[6 + d] = c->a_s2[d];
+    }
+    rec[9] = (unsigned long long)__double_as_longlong(c->dt);
+}
+
+// ------------------------------------------------------------ eps_2
+__global__ void eps2_partial_kernel(const double* u, long long fs, long long ncell, double cs2, double* part)
+{
+    double num = 0.0, den = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+         q += (long long)gridDim.x * blockDim.x) {
+        double p, vx, vy, vz, e;
+        if (!con2prim(cs2, u[q], u[fs + q], u[2 * fs + q], u[3 * fs + q], p, vx, vy, vz, e)) {
+            num = den = __longlong_as_double(0x7ff8000000000000LL);
+            continue;
+        }
+        const double txx = fma(u[fs + q], vx, p), tyy = fma(u[2 * fs + q], vy, p);
+        num += txx - tyy;
+        den += txx + tyy;
+    }
+    __shared__ double sn[256], sd[256];
+    sn[threadIdx.x] = num;
+    sd[threadIdx.x] = den;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sn[threadIdx.x] += sn[threadIdx.x + o];
+            sd[threadIdx.x] += sd[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sn[0];
+        part[2 * blockIdx.x + 1] = sd[0];
+    }
+}
+
+__global__ void eps2_final_kernel(double* part, int nblocks)
+{
+    double n = 0.0, d = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        n += part[2 * b];
+        d += part[2 * b + 1];
+    }
+    part[0] = n;
+    part[1] = d;
+    part[2] = n / d;
+}
+
+// d eps_2 / d u at every cell (eps_2 = num/den): (dnum - eps2 dden) / den
+__global__ void eps2_grad_kernel(const double* u, long long fs, long long ncell, double cs2, const double* sums,
+                                 double* g, long long gs)
+{
+    const double den = sums[1], eps = sums[2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+         q += (long long)gridDim.x * blockDim.x) {
+        double p, vx, vy, vz, e;
+        const double E = u[q], Mx = u[fs + q], My = u[2 * fs + q], Mz = u[3 * fs + q];
+        con2prim(cs2, E, Mx, My, Mz, p, vx, vy, vz, e);
+        const double h = E + p, ih = 1.0 / h;
+        const double Q = fma(2.0, p, (1.0 - cs2) * E), iQ = 1.0 / Q;
+        const double pE = (2.0 * cs2 * E - (1.0 - cs2) * p) * iQ;
+        const double M[3] = {Mx, My, Mz};
+        double pM[3];
+        for (int j = 0; j < 3; ++j) pM[j] = -2.0 * cs2 * M[j] * iQ;
+        // a = Mx vx, b = My vy, derivatives wrt (E, Mx, My, Mz)
+        const double vxE = -vx * (1.0 + pE) * ih, vyE = -vy * (1.0 + pE) * ih;
+        double ga[4], gb[4], gpp[4];
+        ga[0] = Mx * vxE;
+        gb[0] = My * vyE;
+        gpp[0] = pE;
+        for (int j = 0; j < 3; ++j) {
+            const double vxM = ((j == 0 ? 1.0 : 0.0) - vx * pM[j]) * ih;
+            const double vyM = ((j == 1 ? 1.0 : 0.0) - vy * pM[j]) * ih;
+            ga[1 + j] = (j == 0 ? vx : 0.0) + Mx * vxM;
+            gb[1 + j] = (j == 1 ? vy : 0.0) + My * vyM;
+            gpp[1 + j] = pM[j];
+        }
+        for (int c = 0; c < 4; ++c) {
+            const double dn = ga[c] - gb[c];
+            const double dd = ga[c] + gb[c] + 2.0 * gpp[c];
+            g[c * gs + q] = (dn - eps * dd) / den;
+        }
+        g[4 * gs + q] = 0.0;
+    }
+}
+
+}  // namespace hydro
+
+// ------------------------------------------------------------------ host side
+using namespace hydro;
+
+static hydro_status afail(hydro_t* h, cudaError_t e, const char* where)
+{
+    return hydro_handle_fail(h, e == cudaErrorMemoryAllocation ? HYDRO_ERR_OOM : HYDRO_ERR_CUDA,
+                             std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define ACK(h, call, where)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return afail((h), e_, where);  \
+    } while (0)
+
+static int cells_blocks(long long n) { long long b = (n + 255) / 256; return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b)); }
+
+static StageArgs frozen_stage(const HandleView& v, AdjointWork* w, double** U, double** W, int stage, int step)
+{
+    StageArgs a{};
+    const int in = stage - 1;
+    a.u_in = U[in];
+    a.w_in = W[in];
+    a.u_n = U[0];
+    a.u_out = stage == 3 ? U[0] : U[stage];
+    a.w_out = stage == 3 ? W[0] : W[stage];
+    a.fs = w->fs;
+    a.nx = v.cfg.n[0];
+    a.ny = v.cfg.n[1];
+    a.nz = v.cfg.n[2];
+    a.zc = v.zc;
+    for (int d = 0; d < 3; ++d) {
+        a.bc[d] = v.cfg.bc[d];
+        a.act[d] = v.cfg.n[d] > 1;
+        a.hdx[d] = 0.5 / v.cfg.dx[d];
+    }
+    a.cs2 = v.cfg.cs2;
+    a.eps_s = v.cfg.weno_eps * (v.R == 3 ? SchemeConst<3>::eps_scale : SchemeConst<4>::eps_scale);
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    a.ca = ca[in];
+    a.cb = cb[in];
+    a.alpha_in = w->rec + 10 * (long long)step + 3 * in;
+    a.dt = reinterpret_cast<const double*>(w->rec + 10 * (long long)step + 9);
+    a.alpha_out = w->ctl->a_next;
+    a.status = &v.ctl->status;
+    a.bad_cell = &v.ctl->bad_cell;
+    return a;
+}
+
+static dim3 stage_grid(const HandleView& v)
+{
+    return dim3((v.cfg.n[0] + v.L.tx - 1) / v.L.tx, (v.cfg.n[1] + v.L.ty - 1) / v.L.ty, (v.cfg.n[2] + v.zc - 1) / v.zc);
+}
+
+extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t ckpt_every)
+{
+    HandleView v;
+    hydro_status s = hydro_handle_view(h, &v);
+    if (s) return s;
+    if (!v.loaded) return hydro_handle_fail(h, HYDRO_ERR_STATE, "no state loaded");
+    if (nsteps < 1 || ckpt_every < 1) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
+    AdjointWork* w = hydro_handle_adjoint(h, true);
+    if (!w) return hydro_handle_fail(h, HYDRO_ERR_OOM, "host allocation failed");
+    // (re)allocate the workspace for this length
+    cudaStreamSynchronize(v.stream);
+    cudaFree(w->buf);
+    cudaFree(w->rec);
+    cudaFree(w->ctl);
+    w->buf = nullptr;
+    w->rec = nullptr;
+    w->ctl = nullptr;
+    w->nsteps = nsteps;
+    w->ckpt = ckpt_every;
+    w->nckpt = (nsteps + ckpt_every - 1) / ckpt_every;
+    w->fs = v.fs;
+    const long long fs = v.fs;
+    const long long nfields = 27 + 5 * 4 + 10 + 5LL * w->nckpt + 5LL * ckpt_every;
+    ACK(h, cudaMalloc(&w->buf, sizeof(double) * (size_t)(fs * nfields)), "adjoint workspace");
+    ACK(h, cudaMalloc(&w->rec, sizeof(unsigned long long) * 10 * (size_t)nsteps), "step record");
+    ACK(h, cudaMalloc(&w->ctl, sizeof(Ctl)), "scratch control");
+    double* p = w->buf;
+    for (int i = 0; i < 3; ++i) {
+        w->AU[i] = p;
+        p += 5 * fs;
+    }
+    for (int i = 0; i < 3; ++i) {
+        w->AW[i] = p;
+        p += 4 * fs;
+    }
+    w->LAM = p; p += 5 * fs;
+    w->OUT = p; p += 5 * fs;
+    w->ACC = p; p += 5 * fs;
+    w->V = p; p += 5 * fs;
+    w->GP = p; p += 5 * fs;
+    w->GM = p; p += 5 * fs;
+    w->CK = p; p += 5 * fs * w->nckpt;
+    w->SEG = p;
+    // forward steps on the handle's own state, recording speeds and dt; the
+    // stage-1/2 outputs go to the workspace
+    double* U[3];
+    double* Wp[3];
+    set_t_end_kernel<<<1, 1, 0, v.stream>>>(v.ctl, -1.0);
+    // U0/W0 are the handle's; stage outputs go to the workspace's AU1/AU2
+    U[0] = v.U0;
+    U[1] = w->AU[1];
+    U[2] = w->AU[2];
+    Wp[0] = v.W0;
+    Wp[1] = w->AW[1];
+    Wp[2] = w->AW[2];
+    const dim3 grid = stage_grid(v);
+    for (int n = 0; n < nsteps; ++n) {
+        if (n % ckpt_every == 0)
+            ACK(h, cudaMemcpyAsync(w->CK + 5 * fs * (n / ckpt_every), v.U0, sizeof(double) * 5 * fs,
+                                   cudaMemcpyDeviceToDevice, v.stream), "checkpoint");
+        step_begin_kernel<<<1, 1, 0, v.stream>>>(v.ctl, step_params(v.cfg));
+        for (int st = 1; st <= 3; ++st) {
+            StageArgs a{};
+            const int in = st - 1;
+            a.u_in = U[in];
+            a.w_in = Wp[in];
+            a.u_n = U[0];
+            a.u_out = st == 3 ? U[0] : U[st];
+            a.w_out = st == 3 ? Wp[0] : Wp[st];
+            a.fs = fs;
+            a.nx = v.cfg.n[0];
+            a.ny = v.cfg.n[1];
+            a.nz = v.cfg.n[2];
+            a.zc = v.zc;
+            for (int d = 0; d < 3; ++d) {
+                a.bc[d] = v.cfg.bc[d];
+                a.act[d] = v.cfg.n[d] > 1;
+                a.hdx[d] = 0.5 / v.cfg.dx[d];
+            }
+            a.cs2 = v.cfg.cs2;
+            a.eps_s = v.cfg.weno_eps * (v.R == 3 ? SchemeConst<3>::eps_scale : SchemeConst<4>::eps_scale);
+            static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+            a.ca = ca[in];
+            a.cb = cb[in];
+            a.alpha_in = st == 1 ? v.ctl->a_cur : (st == 2 ? v.ctl->a_s1 : v.ctl->a_s2);
+            a.alpha_out = st == 1 ? v.ctl->a_s1 : (st == 2 ? v.ctl->a_s2 : v.ctl->a_next);
+            a.dt = &v.ctl->dt;
+            a.status = &v.ctl->status;
+            a.bad_cell = &v.ctl->bad_cell;
+            v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
+        }
+        record_kernel<<<1, 1, 0, v.stream>>>(v.ctl, w->rec + 10 * (long long)n);
+        step_end_kernel<<<1, 1, 0, v.stream>>>(v.ctl);
+    }
+    ACK(h, cudaGetLastError(), "recorded forward");
+    return HYDRO_OK;
+}
+
+static hydro_status stage_adjoint(hydro_t* h, const HandleView& v, AdjointWork* w, const double* u, const double* ww,
+                                  int stage, int step, const double* lam, double* out, int add_acc, int reset_acc)
+{
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const long long fs = w->fs, nc = v.ncell;
+    ACK(h, cudaMemsetAsync(w->V, 0, sizeof(double) * 5 * fs, v.stream), "zero V");
+    const unsigned long long* rec = w->rec + 10 * (long long)step;
+    for (int d = 0; d < 3; ++d) {
+        if (v.cfg.n[d] <= 1) continue;
+        AdjPencilArgs a{};
+        a.u = u;
+        a.w = ww;
+        a.lam = lam;
+        a.gp = w->GP;
+        a.gm = w->GM;
+        a.rec = rec;
+        a.fs = fs;
+        for (int i = 0; i < 3; ++i) {
+            a.n[i] = v.cfg.n[i];
+            a.bc[i] = v.cfg.bc[i];
+        }
+        a.d = d;
+        a.stage = stage;
+        a.hdx = 0.5 / v.cfg.dx[d];
+        a.cb = cb[stage - 1];
+        a.eps_s = v.cfg.weno_eps * (v.R == 3 ? SchemeConst<3>::eps_scale : SchemeConst<4>::eps_scale);
+        const long long threads = 5LL * (nc / v.cfg.n[d]);
+        const int blocks = (int)((threads + 127) / 128);
+        if (v.R == 3) adj_pencil_kernel<3><<<blocks, 128, 0, v.stream>>>(a);
+        else adj_pencil_kernel<4><<<blocks, 128, 0, v.stream>>>(a);
+        adj_flux_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(u, ww, w->GP, w->GM, w->V, rec, stage, d, fs, nc,
+                                                                 v.cfg.cs2);
+    }
+    adj_combine_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(lam, w->V, out, w->ACC, ca[stage - 1], cb[stage - 1],
+                                                               add_acc, reset_acc, fs, nc);
+    ACK(h, cudaGetLastError(), "stage adjoint");
+    return HYDRO_OK;
+}
+
+extern "C" hydro_status hydro_adjoint(hydro_t* h, const double* lambda_final, double* grad_u0, int64_t field_stride,
+                                      int32_t mem)
+{
+    HandleView v;
+    hydro_status s = hydro_handle_view(h, &v);
+    if (s) return s;
+    AdjointWork* w = hydro_handle_adjoint(h, false);
+    if (!w || !w->buf) return hydro_handle_fail(h, HYDRO_ERR_STATE, "no recorded forward run (call hydro_forward_record)");
+    if (!lambda_final || !grad_u0) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "NULL pointer");
+    if (field_stride < v.ncell) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "field_stride smaller than the cell count");
+    if (mem != HYDRO_MEM_HOST && mem != HYDRO_MEM_DEVICE) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "mem must be 0 or 1");
+    const long long fs = w->fs, nc = v.ncell;
+    const cudaMemcpyKind kin = mem == HYDRO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kout = mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    for (int f = 0; f < 5; ++f)
+        ACK(h, cudaMemcpyAsync(w->LAM + f * fs, lambda_final + f * field_stride, sizeof(double) * nc, kin, v.stream),
+            "load lambda");
+    const dim3 grid = stage_grid(v);
+    const int N = w->nsteps, C = w->ckpt;
+    for (int seg = w->nckpt - 1; seg >= 0; --seg) {
+        const int s0 = seg * C, s1 = (s0 + C < N) ? s0 + C : N;
+        // step-start states of the segment, recomputed with frozen stages
+        ACK(h, cudaMemcpyAsync(w->AU[0], w->CK + 5 * fs * seg, sizeof(double) * 5 * fs, cudaMemcpyDeviceToDevice,
+                               v.stream), "restore");
+        for (int n = s0; n < s1; ++n) {
+            ACK(h, cudaMemcpyAsync(w->SEG + 5 * fs * (n - s0), w->AU[0], sizeof(double) * 5 * fs,
+                                   cudaMemcpyDeviceToDevice, v.stream), "segment");
+            if (n == s1 - 1) break;
+            prepare_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(w->AU[0], w->AW[0], fs, nc, v.cfg.cs2, w->ctl);
+            for (int st = 1; st <= 3; ++st) {
+                const StageArgs a = frozen_stage(v, w, w->AU, w->AW, st, n);
+                v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
+            }
+        }
+        for (int n = s1 - 1; n >= s0; --n) {
+            ACK(h, cudaMemcpyAsync(w->AU[0], w->SEG + 5 * fs * (n - s0), sizeof(double) * 5 * fs,
+                                   cudaMemcpyDeviceToDevice, v.stream), "segment state");
+            prepare_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(w->AU[0], w->AW[0], fs, nc, v.cfg.cs2, w->ctl);
+            for (int st = 1; st <= 2; ++st) {
+                const StageArgs a = frozen_stage(v, w, w->AU, w->AW, st, n);
+                v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
+            }
+            // stage 3 (input u2): lam_u2 = 2/3 lam + J^T(2/3 dt lam); acc = 1/3 lam
+            if ((s = stage_adjoint(h, v, w, w->AU[2], w->AW[2], 3, n, w->LAM, w->OUT, 0, 1))) return s;
+            // stage 2 (input u1): lam_u1 = 1/4 lam_u2 + J^T(1/4 dt lam_u2); acc += 3/4 lam_u2
+            if ((s = stage_adjoint(h, v, w, w->AU[1], w->AW[1], 2, n, w->OUT, w->LAM, 0, 0))) return s;
+            // stage 1 (input u^n): lam_n = acc + lam_u1 + J^T(dt lam_u1)
+            if ((s = stage_adjoint(h, v, w, w->AU[0], w->AW[0], 1, n, w->LAM, w->OUT, 1, 0))) return s;
+            double* t = w->LAM;
+            w->LAM = w->OUT;
+            w->OUT = t;
+        }
+    }
+    for (int f = 0; f < 5; ++f)
+        ACK(h, cudaMemcpyAsync(grad_u0 + f * field_stride, w->LAM + f * fs, sizeof(double) * nc, kout, v.stream),
+            "store gradient");
+    ACK(h, cudaStreamSynchronize(v.stream), "synchronize");
+    return HYDRO_OK;
+}
+
+extern "C" hydro_status hydro_recorded_steps(hydro_t* h, int32_t* nsteps, double* alpha, double* dt)
+{
+    HandleView v;
+    hydro_status s = hydro_handle_view(h, &v);
+    if (s) return s;
+    AdjointWork* w = hydro_handle_adjoint(h, false);
+    if (!w || !w->rec) return hydro_handle_fail(h, HYDRO_ERR_STATE, "no recorded forward run");
+    if (nsteps) *nsteps = w->nsteps;
+    if (alpha || dt) {
+        std::vector<unsigned long long> r(10 * (size_t)w->nsteps);
+        ACK(h, cudaMemcpyAsync(r.data(), w->rec, sizeof(unsigned long long) * r.size(), cudaMemcpyDeviceToHost, v.stream),
+            "read record");
+        ACK(h, cudaStreamSynchronize(v.stream), "synchronize");
+        for (int n = 0; n < w->nsteps; ++n) {
+            for (int i = 0; i < 9; ++i)
+                if (alpha) memcpy(alpha + 9 * n + i, &r[10 * n + i], sizeof(double));
+            if (dt) memcpy(dt + n, &r[10 * n + 9], sizeof(double));
+        }
+    }
+    return HYDRO_OK;
+}
+
+extern "C" hydro_status hydro_eps2(hydro_t* h, const double* u, int64_t field_stride, int32_t mem, double* eps2,
+                                   double* grad, int64_t grad_stride, int32_t grad_mem)
+{
+    HandleView v;
+    hydro_status s = hydro_handle_view(h, &v);
+    if (s) return s;
+    if (!eps2) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "eps2 is NULL");
+    const long long fs = v.fs, nc = v.ncell;
+    if (u && field_stride < nc) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "field_stride smaller than the cell count");
+    if (grad && grad_stride < nc) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "grad_stride smaller than the cell count");
+    if (!u && !v.loaded) return hydro_handle_fail(h, HYDRO_ERR_STATE, "no state loaded");
+    // scratch: one state, the gradient and the block partial sums (stream-ordered)
+    double* scratch = nullptr;
+    const int nb = 152 * 8;
+    ACK(h, cudaMallocAsync(&scratch, sizeof(double) * (size_t)(10 * fs + 2 * nb + 8), v.stream), "eps2 scratch");
+    const double* src = v.U0;
+    if (u) {
+        const cudaMemcpyKind k = mem == HYDRO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        for (int f = 0; f < 5; ++f)
+            ACK(h, cudaMemcpyAsync(scratch + f * fs, u + f * field_stride, sizeof(double) * nc, k, v.stream), "copy");
+        src = scratch;
+    }
+    double* part = scratch + 10 * fs;
+    eps2_partial_kernel<<<nb, 256, 0, v.stream>>>(src, fs, nc, v.cfg.cs2, part);
+    eps2_final_kernel<<<1, 1, 0, v.stream>>>(part, nb);
+    double sums[3];
+    ACK(h, cudaMemcpyAsync(sums, part, sizeof sums, cudaMemcpyDeviceToHost, v.stream), "read eps2");
+    if (grad) {
+        double* g = scratch + 5 * fs;
+        eps2_grad_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(src, fs, nc, v.cfg.cs2, part, g, fs);
+        const cudaMemcpyKind k = grad_mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        for (int f = 0; f < 5; ++f)
+            ACK(h, cudaMemcpyAsync(grad + f * grad_stride, g + f * fs, sizeof(double) * nc, k, v.stream), "copy grad");
+    }
+    ACK(h, cudaFreeAsync(scratch, v.stream), "free");
+    ACK(h, cudaStreamSynchronize(v.stream), "synchronize");
+    *eps2 = sums[2];
+    if (!(sums[2] == sums[2])) return hydro_handle_fail(h, HYDRO_ERR_UNPHYSICAL, "eps2 of an unphysical state");
+    return HYDRO_OK;
+}

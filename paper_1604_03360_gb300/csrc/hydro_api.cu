@@ -28,6 +28,7 @@ struct hydro_s {
     int variant = 0;
     int zc = 0;
     bool have_state = false;
+    AdjointWork* adj = nullptr;      // reverse-mode workspace (hydro_adjoint.cu)
     std::string err;
 };
 
@@ -115,6 +116,34 @@ static hydro_status build_graph(hydro_t* h)
     return HYDRO_OK;
 }
 
+namespace hydro {
+hydro_status hydro_handle_view(hydro_t* h, HandleView* v)
+{
+    if (!h || !v) return HYDRO_ERR_INVALID_ARG;
+    v->loaded = h->have_state;
+    v->cfg = h->cfg;
+    v->R = h->R;
+    v->stream = h->stream;
+    v->ncell = h->ncell;
+    v->fs = h->fs;
+    v->U0 = h->U[0];
+    v->W0 = h->W[0];
+    v->ctl = h->ctl;
+    v->L = h->L;
+    v->zc = h->zc;
+    return HYDRO_OK;
+}
+
+AdjointWork* hydro_handle_adjoint(hydro_t* h, bool create)
+{
+    if (!h) return nullptr;
+    if (!h->adj && create) h->adj = new (std::nothrow) AdjointWork();
+    return h->adj;
+}
+
+hydro_status hydro_handle_fail(hydro_t* h, hydro_status s, const std::string& m) { return fail(h, s, m); }
+}  // namespace hydro
+
 static int blocks_for(long long n) { long long b = (n + 255) / 256; return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b)); }
 
 extern "C" {
@@ -173,6 +202,12 @@ hydro_status hydro_destroy(hydro_t* h)
     if (h->buf) cudaFree(h->buf);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);
+    if (h->adj) {
+        cudaFree(h->adj->buf);
+        cudaFree(h->adj->rec);
+        cudaFree(h->adj->ctl);
+        delete h->adj;
+    }
     delete h;
     return HYDRO_OK;
 }

@@ -105,4 +105,31 @@ inline int pick_zc(int nx, int ny, int nz, const StageLaunch& L, int sms)
     return best;
 }
 
+// The adjoint workspace lives beside the handle; hydro_api.cu owns the handle.
+struct AdjointWork {
+    int nsteps = 0, ckpt = 0, nckpt = 0;
+    long long fs = 0;
+    double* buf = nullptr;                 // all states below
+    double *AU[3], *AW[3], *LAM, *OUT, *ACC, *V, *GP, *GM, *CK, *SEG;
+    unsigned long long* rec = nullptr;     // nsteps x 10
+    Ctl* ctl = nullptr;                    // scratch control block (speed sinks)
+};
+
+// Interface to the handle (defined in hydro_api.cu).
+struct HandleView {
+    bool loaded;
+    hydro_config cfg;
+    int R;
+    cudaStream_t stream;
+    long long ncell, fs;
+    double *U0, *W0;
+    Ctl* ctl;
+    StageLaunch L;
+    int zc;
+};
+hydro_status hydro_handle_view(hydro_t* h, HandleView* v);
+AdjointWork* hydro_handle_adjoint(hydro_t* h, bool create);
+hydro_status hydro_handle_fail(hydro_t* h, hydro_status s, const std::string& m);
+
+
 }  // namespace hydro

@@ -110,3 +110,25 @@ def test_batch_requires_every_event_loaded():
         with pytest.raises(HydroError) as ei:
             b.step(1)
         assert ei.value.code == 6
+
+
+def test_batch_ensemble_time_step_keeps_events_physical():
+    """Eight events of the event-by-event configuration spanning the size
+    range, 100 steps with the ensemble time step: all stay physical, reach
+    t = 2.25, and one of them matches the oracle after the full run."""
+    from paper_1604_03360_gb300 import HydroBatch
+    sizes = [(48, 48, 48), (160, 160, 160), (48, 160, 96), (130, 57, 75), (64, 64, 160), (100, 100, 100),
+             (150, 49, 120), (77, 88, 99)]
+    ev = [W.batch_event(i, sizes) for i in range(len(sizes))]
+    with HydroBatch([g for g, _ in ev]) as b:
+        for i, (g, w) in enumerate(ev):
+            b.set_primitive(i, w)
+        b.step(100)
+        b.sync()
+        out = [b.get_state(i) for i in range(len(ev))]
+    for u, t, k in out:
+        assert k == 100 and abs(t - 100 * W.BATCH_DT) < 1e-12
+        assert np.isfinite(u).all()
+    g0, w0 = ev[0]
+    ref = oracle.run(oracle_cfg(g0), oracle.prim2con(w0), 100)[0]
+    assert np.all(field_errors(out[0][0], ref) <= TOL)

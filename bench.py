@@ -34,6 +34,10 @@ sys.path.insert(0, ROOT)
 # primitive recovery 22, speeds 34.
 FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
                         7: 15 * (2 * 136 + 6) + 40 + 20 + 75 + 22 + 34}
+# DRAM traffic of one WENO7 stage launch measured by ncu on the 128^3 case
+# (profiles/stage_kernel_weno7_128.md): 268 MB / 2.10 M cells; it scales with
+# the cell count.  None for WENO5 (not captured for the current kernel).
+NCU_DRAM_BYTES_PER_CELL_STAGE = {7: 268.1e6 / 128 ** 3}
 # Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
 # stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
 HBM_BYTES_PER_CELL_UPDATE = 320
@@ -258,6 +262,48 @@ def batched_vs_looped(dev, stream, barrier, steps, warmup, events=256):
     return out
 
 
+def adjoint_96(dev, stream, barrier):
+    """Adjoint configuration: 96^3 lumpy event (seed 1604), WENO5, 50 RK3 steps
+    with a checkpoint every 10; gradient of eps_2 with respect to the initial
+    state.  Times the recorded forward and the reverse sweep."""
+    import torch
+    import workloads as W
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=(96, 96, 96), seed=1604)
+    h = Hydro.from_grid(g, stream=stream)
+    wd = torch.from_numpy(w).to(dev)
+    h.set_primitive(wd)
+    h.autotune()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    lam = torch.empty_like(wd)
+    grad = torch.empty_like(wd)
+    uN = torch.empty_like(wd)
+    out = {}
+    for rep in range(2):                       # first pass warms up
+        h.set_primitive(wd)
+        barrier()
+        ev[0].record(stream)
+        h.forward_record(50, 10)
+        ev[1].record(stream)
+        h.get_state(uN)
+        eps = h.eps2(uN, lam)
+        barrier()
+        ev[1].synchronize()
+        t_fwd = ev[0].elapsed_time(ev[1])
+        ev[0].record(stream)
+        h.adjoint(lam, grad)
+        ev[2].record(stream)
+        barrier()
+        t_adj = ev[0].elapsed_time(ev[2])
+        out = {"workload": "96^3 lumpy (seed 1604), WENO5, 50 RK3 steps, checkpoint every 10, d eps_2 / d u_0",
+               "eps2": eps, "forward_record_ms": t_fwd, "adjoint_ms": t_adj,
+               "adjoint_over_forward": t_adj / t_fwd,
+               "cell_updates_per_s_forward": g.cells * 50 / (t_fwd * 1e-3),
+               "gradient_norm": float(grad[0].norm())}
+    h.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,6 +419,8 @@ def main():
     h.close()
     if not args.no_extra and not args.no_batch:
         extra["batched_vs_looped"] = batched_vs_looped(dev, stream, barrier, 3, 3, args.batch_events)
+    if not args.no_extra:
+        extra["adjoint_96"] = adjoint_96(dev, stream, barrier)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -393,7 +441,10 @@ def main():
                        "launch": {"variant": launch[0], "tile": [launch[1], launch[2]], "z_chunk": launch[3],
                                   "autotune_stage_ms": tuned_ms}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp64_peak, "traffic": None,
+                         "frac": achieved / fp64_peak,
+                         "traffic": (NCU_DRAM_BYTES_PER_CELL_STAGE[args.scheme] * cells
+                                     if args.scheme in NCU_DRAM_BYTES_PER_CELL_STAGE else None),
+                         "traffic_source": "ncu dram__bytes_read+write of the 128^3 stage launch, scaled by cells",
                          "kernel": "stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,
                          "peak_source": "FP64 FMA probe kernel measured in this run (hydro_measure_fp64_peak); "
                                         "MEASURED_PEAKS.json has no FP64 figure; nominal 152 SM x 2 DFMA/clk x "

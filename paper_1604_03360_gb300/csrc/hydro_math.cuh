@@ -81,23 +81,25 @@ __device__ __forceinline__ void max_speeds(double k, double vx, double vy, doubl
 // r = 3.  With inputs g = 2 f the indicator b_k = 13/3 (2nd diff)^2 +
 // (1st-derivative form)^2 equals 16 beta_k(f); eps_s must be 16 eps.
 // N and D are the weight-normalised sums multiplied by 10 prod_k (eps+beta_k)^2.
+// All linear forms are built from the differences d_i = v_{i+1} - v_i:
+// 2nd differences s_k = d_{k+1} - d_k, first-derivative forms
+// t0 = 3 d1 - d0, t1 = d1 + d2, t2 = 3 d2 - d3 (same values as the
+// Jiang-Shu forms a - 4b + 3c, d - b, -3c + 4d - e).
 __device__ __forceinline__ void weno5(double a, double b, double c, double d, double e, double eps_s,
                                       double& N, double& D)
 {
-    const double s0 = fma(-2.0, b, a) + c;
-    const double s1 = fma(-2.0, c, b) + d;
-    const double s2 = fma(-2.0, d, c) + e;
-    const double t0 = fma(3.0, c, fma(-4.0, b, a));
-    const double t1 = d - b;
-    const double t2 = fma(-3.0, c, fma(4.0, d, -e));
+    const double d0 = b - a, d1 = c - b, d2 = d - c, d3 = e - d;
+    const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2;
+    const double t0 = fma(3.0, d1, -d0), t1 = d1 + d2, t2 = fma(3.0, d2, -d3);
     const double k13 = 13.0 / 3.0;
-    const double b0 = eps_s + fma(k13 * s0, s0, t0 * t0);
-    const double b1 = eps_s + fma(k13 * s1, s1, t1 * t1);
-    const double b2 = eps_s + fma(k13 * s2, s2, t2 * t2);
+    const double b0 = fma(k13 * s0, s0, fma(t0, t0, eps_s));
+    const double b1 = fma(k13 * s1, s1, fma(t1, t1, eps_s));
+    const double b2 = fma(k13 * s2, s2, fma(t2, t2, eps_s));
     const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2;
     const double P0 = w1 * w2, P1 = w0 * w2, P2 = w0 * w1;
-    // 10 d_k q_k: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6, q1 = (-b+5c+2d)/6, q2 = (2c+5d-e)/6
-    const double n0 = fma(11.0 / 6.0, c, fma(-7.0 / 6.0, b, a * (1.0 / 3.0)));
+    // 10 d_k q_k: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6 = c - d0/3 + 5 d1/6,
+    // q1 = (-b+5c+2d)/6, q2 = (2c+5d-e)/6
+    const double n0 = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, c));
     const double n1 = fma(2.0, d, fma(5.0, c, -b));
     const double n2 = fma(-0.5, e, fma(2.5, d, c));
     N = fma(n0, P0, fma(n1, P1, n2 * P2));
@@ -110,31 +112,33 @@ __device__ __forceinline__ void weno5(double a, double b, double c, double d, do
 // (integer-coefficient forms) and inputs g = 2 f:
 // b_k = A^2 + 39 B^2 + 781/20 C^2 = 144 beta_k(f); eps_s must be 144 eps.
 // N and D are multiplied by 35 prod_k (eps+beta_k)^2.
+// In the difference basis d_i = v_{i+1} - v_i, e_i = d_{i+1} - d_i:
+// C_k = e_{k+1} - e_k (third differences); B0 = 2 e1 - e0, B1 = B2 = e2,
+// B3 = 2 e3 - e4; A0 = 2 d0 - 7 d1 + 11 d2, A1 = -d1 + 5 d2 + 2 d3,
+// A2 = 2 d2 + 5 d3 - d4, A3 = 11 d3 - 7 d4 + 2 d5 (identical values to the
+// forms written on the cell values).
 __device__ __forceinline__ void weno7(const double* v, double eps_s, double& N, double& D)
 {
     const double v0 = v[0], v1 = v[1], v2 = v[2], v3 = v[3], v4 = v[4], v5 = v[5], v6 = v[6];
-    const double A0 = fma(-2.0, v0, fma(9.0, v1, fma(-18.0, v2, 11.0 * v3)));
-    const double A1 = fma(2.0, v4, fma(3.0, v3, fma(-6.0, v2, v1)));
-    const double A2 = fma(-2.0, v2, fma(-3.0, v3, fma(6.0, v4, -v5)));
-    const double A3 = fma(-11.0, v3, fma(18.0, v4, fma(-9.0, v5, 2.0 * v6)));
-    const double B0 = fma(2.0, v3, fma(-5.0, v2, fma(4.0, v1, -v0)));
-    const double B1 = fma(-2.0, v3, v2) + v4;   // candidates 1 and 2 share the
-    const double B2 = B1;                         // central 2nd difference at j
-    const double B3 = fma(2.0, v3, fma(-5.0, v4, fma(4.0, v5, -v6)));
-    const double C0 = (v3 - v0) + 3.0 * (v1 - v2);
-    const double C1 = (v4 - v1) + 3.0 * (v2 - v3);
-    const double C2 = (v5 - v2) + 3.0 * (v3 - v4);
-    const double C3 = (v6 - v3) + 3.0 * (v4 - v5);
+    const double d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3, d4 = v5 - v4, d5 = v6 - v5;
+    const double e0 = d1 - d0, e1 = d2 - d1, e2 = d3 - d2, e3 = d4 - d3, e4 = d5 - d4;
+    const double C0 = e1 - e0, C1 = e2 - e1, C2 = e3 - e2, C3 = e4 - e3;
+    const double B0 = fma(2.0, e1, -e0), B12 = e2, B3 = fma(2.0, e3, -e4);
+    const double A0 = fma(11.0, d2, fma(-7.0, d1, 2.0 * d0));
+    const double A1 = fma(2.0, d3, fma(5.0, d2, -d1));
+    const double A2 = fma(5.0, d3, fma(2.0, d2, -d4));
+    const double A3 = fma(2.0, d5, fma(-7.0, d4, 11.0 * d3));
     const double kc = 781.0 / 20.0;
-    const double b0 = eps_s + fma(A0, A0, fma(39.0 * B0, B0, kc * C0 * C0));
-    const double b1 = eps_s + fma(A1, A1, fma(39.0 * B1, B1, kc * C1 * C1));
-    const double b2 = eps_s + fma(A2, A2, fma(39.0 * B2, B2, kc * C2 * C2));
-    const double b3 = eps_s + fma(A3, A3, fma(39.0 * B3, B3, kc * C3 * C3));
+    const double b39 = 39.0 * B12;
+    const double b0 = fma(A0, A0, fma(39.0 * B0, B0, fma(kc * C0, C0, eps_s)));
+    const double b1 = fma(A1, A1, fma(b39, B12, fma(kc * C1, C1, eps_s)));
+    const double b2 = fma(A2, A2, fma(b39, B12, fma(kc * C2, C2, eps_s)));
+    const double b3 = fma(A3, A3, fma(39.0 * B3, B3, fma(kc * C3, C3, eps_s)));
     const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2, w3 = b3 * b3;
     const double p01 = w0 * w1, p23 = w2 * w3;
     const double P0 = w1 * p23, P1 = w0 * p23, P2 = p01 * w3, P3 = p01 * w2;
-    // 35 d_k q_k, d = (1, 12, 18, 4)/35
-    const double n0 = fma(25.0 / 12.0, v3, fma(-23.0 / 12.0, v2, fma(13.0 / 12.0, v1, -0.25 * v0)));
+    // 35 d_k q_k, d = (1, 12, 18, 4)/35; q0 = v3 + d0/4 - 5 d1/6 + 13 d2/12
+    const double n0 = fma(13.0 / 12.0, d2, fma(-5.0 / 6.0, d1, fma(0.25, d0, v3)));
     const double n1 = fma(3.0, v4, fma(13.0, v3, fma(-5.0, v2, v1)));
     const double n2 = fma(10.5, v3 + v4, -1.5 * (v2 + v5));
     const double n3 = fma(13.0 / 3.0, v4, fma(-5.0 / 3.0, v5, fma(1.0 / 3.0, v6, v3)));

@@ -1,8 +1,11 @@
 // hydro_api.cu -- the C ABI of include/hydro.h for one grid: buffers, the
 // device control block, the captured per-step CUDA graph and the copies.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
+#include <vector>
 #include <new>
 #include <string>
 
@@ -385,8 +388,8 @@ static void tune_cache_store(const hydro_t* h, int variant, int zc)
 
 extern "C" int32_t hydro_launch_variants(int32_t scheme)
 {
-    if (scheme == HYDRO_WENO5) return 3;
-    if (scheme == HYDRO_WENO7) return 2;
+    if (scheme == HYDRO_WENO5) return 4;
+    if (scheme == HYDRO_WENO7) return 3;
     return 0;
 }
 
@@ -417,33 +420,43 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
         if (best_ms) *best_ms = -1.0;
         return apply_launch(h, cv, cz);
     }
-    static const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
-    const int ncand = (int)(sizeof cand / sizeof cand[0]);
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0), "event");
     CK(h, cudaEventCreate(&e1), "event");
     double best = 1e300;
     int bv = h->variant, bz = h->zc;
     hydro_status st = HYDRO_OK;
+    const int nz = h->cfg.n[2];
     // a positive dt makes the stage kernel run; it only writes stage-1 scratch
     set_dt_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 1e-300);
     for (int v = 0; v < hydro_launch_variants(h->cfg.scheme) && st == HYDRO_OK; ++v) {
         StageLaunch L{};
         if (stage_launch_variant(h->R, v, &L) != cudaSuccess) continue;
-        const int z0 = pick_zc(h->cfg.n[0], h->cfg.n[1], h->cfg.n[2], L, h->sms);
-        int i0 = 0;
-        while (i0 < ncand - 1 && cand[i0] < z0) ++i0;
-        for (int di = -1; di <= 1; ++di) {
-            const int i = i0 + di;
-            if (i < 0 || i >= ncand) continue;
-            int zc = cand[i] < h->cfg.n[2] ? cand[i] : h->cfg.n[2];
-            if (di != 0 && zc == z0) continue;
-            if (di == 0) zc = z0;
+        // z chunks: balanced splits ceil(nz/k) and a fixed ladder; time the five
+        // the wave-count model likes best
+        std::vector<int> zs;
+        for (int k = 1; k <= 64; ++k) zs.push_back((nz + k - 1) / k);
+        for (int z : {8, 12, 16, 24, 32, 48, 64}) zs.push_back(z);
+        std::vector<std::pair<double, int>> scored;
+        const long long tiles = (long long)((h->cfg.n[0] + L.tx - 1) / L.tx) * ((h->cfg.n[1] + L.ty - 1) / L.ty);
+        const long long conc = (long long)h->sms * (L.ctas_per_sm > 0 ? L.ctas_per_sm : 1);
+        for (int z : zs) {
+            if (z < 1 || z > nz || (z < 8 && nz >= 8)) continue;
+            bool dup = false;
+            for (auto& q : scored) dup |= (q.second == z);
+            if (dup) continue;
+            const long long ctas = tiles * ((nz + z - 1) / z);
+            const double cost = (double)((ctas + conc - 1) / conc) * (z + 1.5);
+            scored.push_back({cost, z});
+        }
+        std::sort(scored.begin(), scored.end());
+        if (scored.size() > 5) scored.resize(5);
+        for (auto& cz : scored) {
+            const int zc = cz.second;
             h->L = L;
             h->zc = zc;
             const StageArgs a = stage_args(h, 1);
-            const dim3 grid((h->cfg.n[0] + L.tx - 1) / L.tx, (h->cfg.n[1] + L.ty - 1) / L.ty,
-                            (h->cfg.n[2] + zc - 1) / zc);
+            const dim3 grid((h->cfg.n[0] + L.tx - 1) / L.tx, (h->cfg.n[1] + L.ty - 1) / L.ty, (nz + zc - 1) / zc);
             L.fn<<<grid, L.tx * L.ty, L.smem, h->stream>>>(a);   // warm-up
             cudaEventRecord(e0, h->stream);
             L.fn<<<grid, L.tx * L.ty, L.smem, h->stream>>>(a);
@@ -461,7 +474,6 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
                 bv = v;
                 bz = zc;
             }
-            if (zc == h->cfg.n[2]) break;
         }
     }
     set_dt_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 0.0);

@@ -71,7 +71,7 @@ __device__ __forceinline__ StageArgs batch_stage_args(const BatchEvent& E, int s
     return a;
 }
 
-template <int R, int TX, int TY>
+template <int R, int TX, int TY, int ILP = 1>
 __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) batch_stage_kernel(const BatchArgs b)
 {
     extern __shared__ __align__(16) double smem[];
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) b
         if (it >= b.n_items) break;
         const int4 w = b.items[it];
         const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
-        stage_tile<R, TX, TY>(a, w.y, w.z, w.w, smem);
+        stage_tile<R, TX, TY, ILP>(a, w.y, w.z, w.w, smem);
     }
 }
 
@@ -124,18 +124,18 @@ struct BatchLaunch {
     int tx, ty, ctas_per_sm;
 };
 
-template <int R, int TX, int TY>
+template <int R, int TX, int TY, int ILP = 1>
 static cudaError_t batch_info_for(BatchLaunch* out)
 {
-    out->fn = batch_stage_kernel<R, TX, TY>;
+    out->fn = batch_stage_kernel<R, TX, TY, ILP>;
     out->smem = StageSmem<R, TX, TY>::bytes;
     out->tx = TX;
     out->ty = TY;
-    cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)out->smem);
+    cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<R, TX, TY, ILP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, batch_stage_kernel<R, TX, TY>, TX * TY,
-                                                         out->smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, batch_stage_kernel<R, TX, TY, ILP>,
+                                                         TX * TY, out->smem);
 }
 
 // same tile shapes as the single-grid kernel (variant numbering matches)
@@ -145,10 +145,12 @@ static cudaError_t batch_launch_variant(int R, int v, BatchLaunch* out)
         if (v == 0) return batch_info_for<3, 16, 16>(out);
         if (v == 1) return batch_info_for<3, 16, 8>(out);
         if (v == 2) return batch_info_for<3, 32, 8>(out);
+        if (v == 3) return batch_info_for<3, 16, 16, 2>(out);
     }
     if (R == 4) {
         if (v == 0) return batch_info_for<4, 16, 16>(out);
         if (v == 1) return batch_info_for<4, 16, 8>(out);
+        if (v == 2) return batch_info_for<4, 16, 16, 2>(out);
     }
     return cudaErrorInvalidValue;
 }

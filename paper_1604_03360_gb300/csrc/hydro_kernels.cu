@@ -115,32 +115,36 @@ __global__ void state_to_prim_kernel(const double* u, long long fs, double* out,
     }
 }
 
-template <int R, int TX, int TY>
+template <int R, int TX, int TY, int ILP = 1>
 static cudaError_t info_for(StageLaunch* out)
 {
-    out->fn = stage_kernel<R, TX, TY>;
+    out->fn = stage_kernel<R, TX, TY, ILP>;
     out->smem = StageSmem<R, TX, TY>::bytes;
     out->tx = TX;
     out->ty = TY;
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY, ILP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)out->smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_kernel<R, TX, TY>, TX * TY,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_kernel<R, TX, TY, ILP>, TX * TY,
                                                          out->smem);
 }
 
-// WENO5: 16x16 (1 CTA of 8 warps per SM), 16x8 (2 CTAs of 4 warps), 32x8.
-// WENO7: 16x16 (8 warps, 221 KB shared memory), 16x8 (4 warps).
+// WENO5: 16x16 (1 CTA of 8 warps per SM), 16x8 (2 CTAs of 4 warps), 32x8,
+//        16x16 with two face items per iteration.
+// WENO7: 16x16 (8 warps, 221 KB shared memory), 16x8 (4 warps), 16x16 with two
+//        face items per iteration.
 cudaError_t stage_launch_variant(int R, int v, StageLaunch* out)
 {
     if (R == 3) {
         if (v == 0) return info_for<3, 16, 16>(out);
         if (v == 1) return info_for<3, 16, 8>(out);
         if (v == 2) return info_for<3, 32, 8>(out);
+        if (v == 3) return info_for<3, 16, 16, 2>(out);
     }
     if (R == 4) {
         if (v == 0) return info_for<4, 16, 16>(out);
         if (v == 1) return info_for<4, 16, 8>(out);
+        if (v == 2) return info_for<4, 16, 16, 2>(out);
     }
     return cudaErrorInvalidValue;
 }

@@ -92,7 +92,7 @@ __device__ __forceinline__ void split_flux(int d, const double u[5], const doubl
 
 // One work item: column tile (tile_x, tile_y) of TX x TY cells and z chunk chunk_z of the
 // grid described by a.  All threads of the CTA call it with the same item.
-template <int R, int TX, int TY>
+template <int R, int TX, int TY, int ILP = 1>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
 {
     using SM = StageSmem<R, TX, TY>;
@@ -226,37 +226,60 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             }
         }
         __syncthreads();
-        // 3. x- and y-faces, one (face, field) per item
-        for (int it = tid; it < nfx + nfy; it += NT) {
-            double vp[S], vm[S], Np, Dp, Nm, Dm;
+        // 3. x- and y-faces, one (face, field) item per thread at a time (ILP
+        //    items per iteration); every item is a stencil of S values with a
+        //    stride in the staged arrays, so x and y items run the same code
+        auto locate = [&](int it, const double*& pp, const double*& pm, int& st, double*& out) {
             if (it < nfx) {
                 const int k = it / (nrow * (ncol + 1)), rr = it % (nrow * (ncol + 1));
                 const int row = rr / (ncol + 1), f = rr % (ncol + 1);   // face f - 1/2 of the tile
-                const double* gpr = gx + (k * TY + row) * GXW;
-                const double* gmr = gx + ((5 + k) * TY + row) * GXW;
-#pragma unroll
-                for (int i = 0; i < S; ++i) {
-                    vp[i] = gpr[f + i];
-                    vm[i] = gmr[f + 1 + i];
-                }
-                weno_left<R>(vp, a.eps_s, Np, Dp);
-                weno_right<R>(vm, a.eps_s, Nm, Dm);
-                Fx[(k * TY + row) * (TX + 1) + f] = face_sum(Np, Dp, Nm, Dm);
+                pp = gx + (k * TY + row) * GXW + f;
+                pm = gx + ((5 + k) * TY + row) * GXW + f + 1;
+                st = 1;
+                out = Fx + (k * TY + row) * (TX + 1) + f;
             } else {
                 const int j = it - nfx;
                 const int k = j / ((nrow + 1) * ncol), rr = j % ((nrow + 1) * ncol);
                 const int f = rr / ncol, col = rr % ncol;             // face f - 1/2 along y
-                const double* gpc = gy + (k * GYH) * TX + col;
-                const double* gmc = gy + ((5 + k) * GYH) * TX + col;
-#pragma unroll
-                for (int i = 0; i < S; ++i) {
-                    vp[i] = gpc[(f + i) * TX];
-                    vm[i] = gmc[(f + 1 + i) * TX];
-                }
-                weno_left<R>(vp, a.eps_s, Np, Dp);
-                weno_right<R>(vm, a.eps_s, Nm, Dm);
-                Fy[(k * (TY + 1) + f) * TX + col] = face_sum(Np, Dp, Nm, Dm);
+                pp = gy + (k * GYH + f) * TX + col;
+                pm = gy + ((5 + k) * GYH + f + 1) * TX + col;
+                st = TX;
+                out = Fy + (k * (TY + 1) + f) * TX + col;
             }
+        };
+        const int nitems = nfx + nfy;
+        for (int it0 = tid; it0 < nitems; it0 += ILP * NT) {
+            double vp[ILP][S], vm[ILP][S], F[ILP];
+            double* out[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                const int it = it0 + u * NT;
+                const double* pp;
+                const double* pm;
+                int st;
+                out[u] = nullptr;
+                if (it < nitems) {
+                    locate(it, pp, pm, st, out[u]);
+#pragma unroll
+                    for (int i = 0; i < S; ++i) {
+                        vp[u][i] = pp[i * st];
+                        vm[u][i] = pm[i * st];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < S; ++i) vp[u][i] = vm[u][i] = 0.0;   // result discarded
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                double Np, Dp, Nm, Dm;
+                weno_left<R>(vp[u], a.eps_s, Np, Dp);
+                weno_right<R>(vm[u], a.eps_s, Nm, Dm);
+                F[u] = face_sum(Np, Dp, Nm, Dm);
+            }
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (out[u]) *out[u] = F[u];
         }
         __syncthreads();
         // 4. combine, RK update, primitives and speeds of the new state
@@ -308,11 +331,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 }
 
-template <int R, int TX, int TY>
+template <int R, int TX, int TY, int ILP = 1>
 __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) stage_kernel(const StageArgs a)
 {
     extern __shared__ __align__(16) double smem[];
-    stage_tile<R, TX, TY>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    stage_tile<R, TX, TY, ILP>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 }  // namespace hydro

@@ -183,7 +183,7 @@ def test_unphysical_state_reported():
         assert ei.value.code == 4
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (7, 0), (7, 1)])
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (7, 0), (7, 1), (7, 2)])
 def test_every_launch_variant(scheme, variant):
     """Every compiled CTA tile shape, with a short z chunk so several chunks
     meet inside the grid, matches the oracle."""

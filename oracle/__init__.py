@@ -46,7 +46,7 @@ class Cfg(ctypes.Structure):
         ("n", ctypes.c_int32 * 3),
         ("r", ctypes.c_int32),
         ("bc", ctypes.c_int32 * 3),
-        ("pad_", ctypes.c_int32),
+        ("split", ctypes.c_int32),
         ("dx", ctypes.c_double * 3),
         ("cs2", ctypes.c_double),
         ("cfl", ctypes.c_double),
@@ -100,8 +100,9 @@ def max_threads():
     return lib().oc_get_max_threads()
 
 
-def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0, eps=1e-6):
-    """n = (nx, ny, nz); scheme 5 (WENO5) or 7 (WENO7); bc 0 outflow / 1 periodic."""
+def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0, eps=1e-6, split=0):
+    """n = (nx, ny, nz); scheme 5 (WENO5) or 7 (WENO7); bc 0 outflow / 1 periodic;
+    split 0 global / 1 local Lax-Friedrichs."""
     c = Cfg()
     for i in range(3):
         c.n[i] = int(n[i])
@@ -112,6 +113,7 @@ def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0
     c.cfl = float(cfl)
     c.dt_fixed = float(dt_fixed)
     c.eps = float(eps)
+    c.split = int(split)
     return c
 
 

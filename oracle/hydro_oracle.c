@@ -31,6 +31,10 @@
  * copy the edge cell into the ghost cells (zeroth-order extrapolation of the
  * conserved variables); periodic boundaries wrap; directions with a single
  * cell contribute no flux difference.
+ * Local Lax-Friedrichs variant (split = 1): the face j+1/2 along d uses
+ * alpha = max over the 2r cells j-r+1 .. j+r (the union of both biased
+ * stencils) of max(|lambda_-|, |lambda_+|) along d; the time step still uses
+ * the global speeds.
  *
  * Built with -O2 -ffp-contract=off (no FMA contraction) so that x86-64 and
  * aarch64 hosts give identical bits.  OpenMP (if present) only splits the
@@ -50,7 +54,7 @@ typedef struct {
     int32_t n[3];      /* interior cells along x, y, z (x fastest in memory) */
     int32_t r;         /* WENO parameter: 3 -> WENO5, 4 -> WENO7 */
     int32_t bc[3];     /* 0: outflow (copy edge cell), 1: periodic */
-    int32_t pad_;
+    int32_t split;     /* 0: global Lax-Friedrichs, 1: local Lax-Friedrichs */
     double dx[3];      /* cell sizes |e_i| */
     double cs2;        /* EOS p = cs2 * e */
     double cfl;
@@ -271,6 +275,7 @@ static int cfg_ok(const oc_cfg *c)
     for (int d = 0; d < 3; ++d)
         if (c->n[d] < 1 || !(c->dx[d] > 0) || (c->bc[d] != 0 && c->bc[d] != 1)) return 0;
     if (c->r != 3 && c->r != 4) return 0;
+    if (c->split != 0 && c->split != 1) return 0;
     if (!(c->cs2 > 0 && c->cs2 < 1) || !(c->eps > 0)) return 0;
     for (int d = 0; d < 3; ++d)
         if (active(c, d) && c->bc[d] == 1 && c->n[d] < c->r) return 0;
@@ -332,9 +337,12 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
             double *fp = malloc(sizeof(double) * NF * len);
             double *fm = malloc(sizeof(double) * NF * len);
             double *F = malloc(sizeof(double) * NF * (nd + 1));
-            if (!fp || !fm || !F) {
+            double *fr = malloc(sizeof(double) * NF * len);    /* physical flux (local LF) */
+            double *ur = malloc(sizeof(double) * NF * len);    /* state (local LF) */
+            double *sp = malloc(sizeof(double) * len);         /* max |lambda| along d (local LF) */
+            if (!fp || !fm || !F || !fr || !ur || !sp) {
                 bad |= 2;
-                free(fp); free(fm); free(F);
+                free(fp); free(fm); free(F); free(fr); free(ur); free(sp);
                 continue;
             }
             /* split fluxes at every cell of the pencil, ghosts included */
@@ -354,11 +362,31 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
                 for (int k = 0; k < NF; ++k) {
                     fp[k * len + m] = 0.5 * (f[k] + alpha[d] * uu[k]);
                     fm[k * len + m] = 0.5 * (f[k] - alpha[d] * uu[k]);
+                    fr[k * len + m] = f[k];
+                    ur[k * len + m] = uu[k];
                 }
+                double lam[2];
+                oc_eigen(c->cs2, d, w, lam);
+                sp[m] = fmax(fabs(lam[0]), fabs(lam[1]));
             }
             /* face fluxes: F[s] sits at face s - 1/2, s = 0..nd */
             for (int s = 0; s <= nd; ++s) {
                 const int j = s - 1 + G; /* padded index of the cell left of the face */
+                if (c->split == 1) {
+                    /* local LF: split again with this face's own alpha */
+                    double af = 0.0;
+                    for (int m = j - r + 1; m <= j + r; ++m) af = fmax(af, sp[m]);
+                    for (int k = 0; k < NF; ++k) {
+                        double vp[7], vm[7];
+                        for (int i = 0; i < 2 * r - 1; ++i) {
+                            const int a = j - r + 1 + i, b = j - r + 2 + i;
+                            vp[i] = 0.5 * (fr[k * len + a] + af * ur[k * len + a]);
+                            vm[i] = 0.5 * (fr[k * len + b] - af * ur[k * len + b]);
+                        }
+                        F[k * (nd + 1) + s] = oc_weno_left(r, vp, c->eps) + weno_right(r, vm, c->eps);
+                    }
+                    continue;
+                }
                 for (int k = 0; k < NF; ++k) {
                     const double *vp = fp + k * len + (j - r + 1);
                     const double *vm = fm + k * len + (j - r + 2);
@@ -377,6 +405,9 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
             free(fp);
             free(fm);
             free(F);
+            free(fr);
+            free(ur);
+            free(sp);
         }
     }
     if (bad & 2) return OC_ERR_OOM;

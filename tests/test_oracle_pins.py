@@ -449,3 +449,68 @@ def test_cfl_rule_and_final_time(oracle_lib):
     assert np.array_equal(al[0, 0], a0)
     _, t, k = oracle_lib.run(c, u0, 1000, t=0.0, t_end=2.5 * dts[0])
     assert k == 3 and t == 2.5 * dts[0]
+
+
+# ---------------------------------------------------------------- local Lax-Friedrichs
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_local_lf_equals_global_for_uniform_speeds(oracle_lib, scheme):
+    """With uniform e and v (only the passive charge varies) every face sees
+    the same speed, so local and global splitting give identical bits."""
+    r = (scheme + 1) // 2
+    g, u, _ = _advection_setup(24, r, 1, 0.3)
+    cg = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=g.bc, split=0)
+    cl = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=g.bc, split=1)
+    a = oracle_lib.alpha(cg, u)
+    assert np.array_equal(oracle_lib.L(cg, u, a), oracle_lib.L(cl, u, a))
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_local_lf_is_local(oracle_lib, scheme):
+    """L at cell i depends only on cells i-r .. i+r under local splitting:
+    raising the speed at cell i+r+1 changes L_i under global splitting but
+    leaves it bit-identical under local splitting."""
+    r = (scheme + 1) // 2
+    N = 30
+    g, w = W.smooth_periodic(n=(N, 1, 1), seed=12, scheme=scheme, vamp=0.3)
+    g.bc = (0, 0, 0)
+    u0 = oracle_lib.prim2con(w)
+    i = 8
+    w2 = w.copy()
+    w2[1, 0, 0, i + r + 1] = 0.95          # much faster cell just outside the window
+    u1 = oracle_lib.prim2con(w2)
+    for split, same in ((1, True), (0, False)):
+        c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, split=split)
+        L0 = oracle_lib.L(c, u0, oracle_lib.alpha(c, u0))
+        L1 = oracle_lib.L(c, u1, oracle_lib.alpha(c, u1))
+        assert np.array_equal(L0[:, 0, 0, i], L1[:, 0, 0, i]) == same, split
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_local_lf_conserves_and_follows_boundary_rule(oracle_lib, scheme):
+    g, w = W.smooth_periodic(n=(10, 9, 8), amp=0.3, vamp=0.4, seed=5, scheme=scheme)
+    u0 = oracle_lib.prim2con(w)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=(1, 1, 1), cfl=0.4, split=1)
+    u1 = oracle_lib.run(c, u0, 4)[0]
+    scale = np.abs(u0).reshape(5, -1).sum(1).max()
+    assert np.abs(u1.reshape(5, -1).sum(1) - u0.reshape(5, -1).sum(1)).max() < 1e-13 * scale
+    G = (scheme + 1) // 2
+    a = oracle_lib.alpha(c, u0)
+    up = np.pad(u0, ((0, 0), (G, G), (G, G), (G, G)), mode="wrap")
+    cp = oracle_lib.make_cfg(tuple(k + 2 * G for k in g.n), g.dx, scheme=scheme, bc=(0, 0, 0), split=1)
+    assert np.array_equal(oracle_lib.L(cp, up, a)[:, G:-G, G:-G, G:-G], oracle_lib.L(c, u0, a))
+
+
+def test_local_lf_sod_at_least_as_accurate(oracle_lib):
+    ex = SodExact()
+    errs = {}
+    for split in (0, 1):
+        g, w = W.sod(N=200, scheme=5)
+        c = oracle_lib.make_cfg(g.n, g.dx, scheme=5, cfl=g.cfl, split=split)
+        u, t, k = oracle_lib.run(c, oracle_lib.prim2con(w), 100000, t_end=0.4)
+        p = oracle_lib.con2prim(u)
+        x = g.centres()[0].ravel()
+        e_ex, v_ex, n_ex = ex(x, 0.4)
+        errs[split] = np.abs(p[0].ravel() - e_ex).mean()
+        mid = (x > ex.xi_tail * 0.4 + 0.04) & (x < ex.V_shock * 0.4 - 0.04)
+        assert np.abs(p[0].ravel()[mid] / ex.e_star - 1).max() < 0.01
+    assert errs[1] <= errs[0] * 1.001, errs

@@ -417,6 +417,28 @@ def main():
                               "hbm_frac": HBM_BYTES_PER_CELL_UPDATE * cells * args.steps / el5 / 1e9 / hbm_peak}
         h5.close()
     h.close()
+    if not args.no_extra:
+        # local Lax-Friedrichs splitting, same workload and scheme
+        gl, wl = workload(args.scheme, args.grid)
+        gl.split = 1
+        hl = Hydro.from_grid(gl, stream=stream)
+        hl.set_primitive(torch.from_numpy(wl).to(dev))
+        hl.autotune()
+        hl.step(3)
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        kl = hl.profile_step(3)
+        a1.record(stream)
+        barrier()
+        hl.sync()
+        ell = a0.elapsed_time(a1) / 1e3
+        extra["local_lf_256"] = {"value": cells * 3 / ell, "unit": "cell-updates/s", "steps": 3,
+                                 "ms_per_step": 1e3 * ell / 3, "launch": hl.launch(),
+                                 "stage_kernel_ms": float(kl[1:4].sum()) / 9,
+                                 "fp64_frac_global_lf_count": FLOPS_PER_CELL_STAGE[args.scheme] * cells
+                                 / (float(kl[1:4].sum()) / 9 * 1e-3) / 1e12 / fp64_peak}
+        hl.close()
     if not args.no_extra and not args.no_batch:
         extra["batched_vs_looped"] = batched_vs_looped(dev, stream, barrier, 3, 3, args.batch_events)
     if not args.no_extra:

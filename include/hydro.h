@@ -67,7 +67,13 @@ typedef struct {
                            needs n >= 4 for WENO7, >= 3 for WENO5) */
     int32_t scheme;     /* HYDRO_WENO5 or HYDRO_WENO7 */
     int32_t bc[3];      /* hydro_bc per direction */
-    int32_t reserved;   /* must be 0 */
+    int32_t split;      /* flux splitting: 0 = global Lax-Friedrichs (alpha_d
+                           = max speed over the grid), 1 = local Lax-Friedrichs
+                           (each face j+1/2 uses the max speed over the 2r
+                           cells of its two stencils); dt uses the global
+                           speeds either way.  Local LF is not supported by
+                           hydro_forward_record/hydro_adjoint or
+                           hydro_step_noalloc (HYDRO_ERR_INVALID_ARG) */
     double dx[3];       /* cell sizes |e_i| > 0 */
     double origin[3];   /* lower corner of the box (informational) */
     double cs2;         /* EOS p = cs2 * e, 0 < cs2 < 1 (1/3 in the paper's tests) */
@@ -138,10 +144,10 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
 /* Launch configuration of the stage kernel.  Several CTA tile shapes are
  * compiled per scheme (variant 0 is the default); the z-chunk (planes per CTA)
  * sets how many CTAs share a column.  hydro_set_launch forces a variant
- * (0 <= variant < hydro_launch_variants(scheme)) and z-chunk (zc <= 0: the
+ * (0 <= variant < hydro_launch_variants(scheme, split)) and z-chunk (zc <= 0: the
  * built-in wave-count heuristic), rebuilding the step graph.  Results do not
  * depend on the choice beyond FMA-level rounding of the same formulas. */
-int32_t hydro_launch_variants(int32_t scheme);
+int32_t hydro_launch_variants(int32_t scheme, int32_t split);
 hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc);
 hydro_status hydro_get_launch(hydro_t* h, int32_t* variant, int32_t* tile_x, int32_t* tile_y, int32_t* zc);
 

@@ -24,6 +24,7 @@ struct hydro_s {
     double* buf = nullptr;
     double* U[3] = {nullptr, nullptr, nullptr};
     double* W[3] = {nullptr, nullptr, nullptr};
+    double* S[3] = {nullptr, nullptr, nullptr};   // per-axis speeds (local LF only)
     Ctl* ctl = nullptr;
     Ctl* hctl = nullptr;             // pinned mirror for read-back
     cudaGraphExec_t exec = nullptr;
@@ -85,6 +86,8 @@ static StageArgs stage_args(hydro_t* h, int stage)
     a.dt = &h->ctl->dt;
     a.status = &h->ctl->status;
     a.bad_cell = &h->ctl->bad_cell;
+    a.s_in = h->S[in];
+    a.s_out = stage == 3 ? h->S[0] : h->S[stage];
     return a;
 }
 
@@ -173,15 +176,18 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
     if ((e = cudaGetDevice(&h->dev)) != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
     if ((e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev)) != cudaSuccess)
         return bail(cuda_fail(h, e, "device attribute"));
-    if ((e = stage_launch_info(h->R, &h->L)) != cudaSuccess) return bail(cuda_fail(h, e, "stage kernel setup"));
+    if ((e = stage_launch_variant(h->R, cfg->split, 0, &h->L)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "stage kernel setup"));
     h->ncell = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
     h->fs = (h->ncell + 31) / 32 * 32;   // 256-byte aligned fields
     h->zc = pick_zc(cfg->n[0], cfg->n[1], cfg->n[2], h->L, h->sms);
-    const size_t bytes = sizeof(double) * (size_t)h->fs * 27;
+    const int nfields = cfg->split ? 36 : 27;
+    const size_t bytes = sizeof(double) * (size_t)h->fs * nfields;
     if ((e = cudaMalloc(&h->buf, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "state buffers"));
     for (int i = 0; i < 3; ++i) {
         h->U[i] = h->buf + (size_t)h->fs * 5 * i;
         h->W[i] = h->buf + (size_t)h->fs * (15 + 4 * i);
+        if (cfg->split) h->S[i] = h->buf + (size_t)h->fs * (27 + 3 * i);
     }
     if ((e = cudaMemsetAsync(h->buf, 0, bytes, h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
     if ((e = cudaMalloc(&h->ctl, sizeof(Ctl))) != cudaSuccess) return bail(cuda_fail(h, e, "control block"));
@@ -238,7 +244,8 @@ static hydro_status check_io(hydro_t* h, const void* p, int64_t stride, int32_t 
 static hydro_status after_load(hydro_t* h, double t)
 {
     reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
-    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl);
+    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl,
+                                                                 h->S[0]);
     CK(h, cudaGetLastError(), "prepare");
     h->have_state = true;
     return HYDRO_OK;
@@ -269,7 +276,8 @@ hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stri
     reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
     prim2con_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(src, ss, h->U[0], h->fs, h->ncell, h->cfg.cs2, h->ctl);
     CK(h, cudaGetLastError(), "prim2con");
-    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl);
+    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl,
+                                                                 h->S[0]);
     CK(h, cudaGetLastError(), "prepare");
     h->have_state = true;
     return HYDRO_OK;
@@ -330,7 +338,7 @@ __global__ void set_dt_kernel(Ctl* c, double dt) { c->dt = dt; }
 static hydro_status apply_launch(hydro_t* h, int variant, int zc)
 {
     StageLaunch L{};
-    cudaError_t e = stage_launch_variant(h->R, variant, &L);
+    cudaError_t e = stage_launch_variant(h->R, h->cfg.split, variant, &L);
     if (e == cudaErrorInvalidValue) return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     CK(h, e, "stage kernel setup");
     CK(h, cudaStreamSynchronize(h->stream), "synchronize");
@@ -386,17 +394,17 @@ static void tune_cache_store(const hydro_t* h, int variant, int zc)
     fclose(f);
 }
 
-extern "C" int32_t hydro_launch_variants(int32_t scheme)
+extern "C" int32_t hydro_launch_variants(int32_t scheme, int32_t split)
 {
-    if (scheme == HYDRO_WENO5) return 4;
-    if (scheme == HYDRO_WENO7) return 3;
+    if (split != 0 && split != 1) return 0;
+    if (scheme == HYDRO_WENO5 || scheme == HYDRO_WENO7) return launch_variant_count(scheme == HYDRO_WENO5 ? 3 : 4, split);
     return 0;
 }
 
 extern "C" hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc)
 {
     if (!h) return HYDRO_ERR_INVALID_ARG;
-    if (variant < 0 || variant >= hydro_launch_variants(h->cfg.scheme))
+    if (variant < 0 || variant >= hydro_launch_variants(h->cfg.scheme, h->cfg.split))
         return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     return apply_launch(h, variant, zc);
 }
@@ -416,7 +424,7 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
     if (!h) return HYDRO_ERR_INVALID_ARG;
     if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
     int cv = 0, cz = 0;
-    if (tune_cache_lookup(h, &cv, &cz) && cv >= 0 && cv < hydro_launch_variants(h->cfg.scheme)) {
+    if (tune_cache_lookup(h, &cv, &cz) && cv >= 0 && cv < hydro_launch_variants(h->cfg.scheme, h->cfg.split)) {
         if (best_ms) *best_ms = -1.0;
         return apply_launch(h, cv, cz);
     }
@@ -429,9 +437,9 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
     const int nz = h->cfg.n[2];
     // a positive dt makes the stage kernel run; it only writes stage-1 scratch
     set_dt_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 1e-300);
-    for (int v = 0; v < hydro_launch_variants(h->cfg.scheme) && st == HYDRO_OK; ++v) {
+    for (int v = 0; v < hydro_launch_variants(h->cfg.scheme, h->cfg.split) && st == HYDRO_OK; ++v) {
         StageLaunch L{};
-        if (stage_launch_variant(h->R, v, &L) != cudaSuccess) continue;
+        if (stage_launch_variant(h->R, h->cfg.split, v, &L) != cudaSuccess) continue;
         // z chunks: balanced splits ceil(nz/k) and a fixed ladder; time the five
         // the wave-count model likes best
         std::vector<int> zs;

@@ -23,6 +23,7 @@ namespace hydro {
 struct BatchEvent {
     double* U[3];
     double* W[3];
+    double* S[3];             // per-axis speeds (local LF only)
     long long fs, ncell;
     int n[3], bc[3], act[3];
     double hdx[3];
@@ -68,10 +69,12 @@ __device__ __forceinline__ StageArgs batch_stage_args(const BatchEvent& E, int s
     a.dt = &E.ctl->dt;
     a.status = &E.ctl->status;
     a.bad_cell = &E.ctl->bad_cell;
+    a.s_in = E.S[in];
+    a.s_out = stage == 3 ? E.S[0] : E.S[stage];
     return a;
 }
 
-template <int R, int TX, int TY, int ILP = 1>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
 __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) batch_stage_kernel(const BatchArgs b)
 {
     extern __shared__ __align__(16) double smem[];
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) b
         if (it >= b.n_items) break;
         const int4 w = b.items[it];
         const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
-        stage_tile<R, TX, TY, ILP>(a, w.y, w.z, w.w, smem);
+        stage_tile<R, TX, TY, ILP, LLF>(a, w.y, w.z, w.w, smem);
     }
 }
 
@@ -124,23 +127,29 @@ struct BatchLaunch {
     int tx, ty, ctas_per_sm;
 };
 
-template <int R, int TX, int TY, int ILP = 1>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
 static cudaError_t batch_info_for(BatchLaunch* out)
 {
-    out->fn = batch_stage_kernel<R, TX, TY, ILP>;
-    out->smem = StageSmem<R, TX, TY>::bytes;
+    out->fn = batch_stage_kernel<R, TX, TY, ILP, LLF>;
+    out->smem = StageSmem<R, TX, TY, LLF>::bytes;
     out->tx = TX;
     out->ty = TY;
-    cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<R, TX, TY, ILP>,
+    cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<R, TX, TY, ILP, LLF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, batch_stage_kernel<R, TX, TY, ILP>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, batch_stage_kernel<R, TX, TY, ILP, LLF>,
                                                          TX * TY, out->smem);
 }
 
 // same tile shapes as the single-grid kernel (variant numbering matches)
-static cudaError_t batch_launch_variant(int R, int v, BatchLaunch* out)
+static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* out)
 {
+    if (split == 1) {
+        if (R == 3 && v == 0) return batch_info_for<3, 16, 16, 1, true>(out);
+        if (R == 3 && v == 1) return batch_info_for<3, 16, 8, 1, true>(out);
+        if (R == 4 && v == 0) return batch_info_for<4, 16, 8, 1, true>(out);
+        return cudaErrorInvalidValue;
+    }
     if (R == 3) {
         if (v == 0) return batch_info_for<3, 16, 16>(out);
         if (v == 1) return batch_info_for<3, 16, 8>(out);
@@ -288,7 +297,7 @@ static int batch_default_zc(const hydro_batch_t* b)
 static hydro_status apply_batch_launch(hydro_batch_t* b, int variant, int zc)
 {
     BatchLaunch L{};
-    cudaError_t e = batch_launch_variant(b->R, variant, &L);
+    cudaError_t e = batch_launch_variant(b->R, b->cfg[0].split, variant, &L);
     if (e == cudaErrorInvalidValue) return bfail(b, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     BCK(b, e, "batch kernel setup");
     BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
@@ -326,8 +335,8 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
     for (int e = 0; e < n_events; ++e) {
         const std::string why = check_config(&cfgs[e]);
         if (!why.empty()) return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "event " + std::to_string(e) + ": " + why);
-        if (cfgs[e].scheme != cfgs[0].scheme)
-            return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "all events of a batch must use the same scheme");
+        if (cfgs[e].scheme != cfgs[0].scheme || cfgs[e].split != cfgs[0].split)
+            return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "all events of a batch must use the same scheme and splitting");
     }
     hydro_batch_t* b = new (std::nothrow) hydro_batch_t();
     if (!b) return bfail(nullptr, HYDRO_ERR_OOM, "host allocation failed");
@@ -351,7 +360,7 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
         const long long nc = (long long)cfgs[i].n[0] * cfgs[i].n[1] * cfgs[i].n[2];
         b->ev[i].ncell = nc;
         b->ev[i].fs = (nc + 31) / 32 * 32;
-        total += 27 * b->ev[i].fs;
+        total += (cfgs[0].split ? 36 : 27) * b->ev[i].fs;
     }
     if ((e = cudaMalloc(&b->buf, sizeof(double) * (size_t)total)) != cudaSuccess) return bail(bcuda(b, e, "event buffers"));
     if ((e = cudaMalloc(&b->ctl, sizeof(Ctl) * n_events)) != cudaSuccess) return bail(bcuda(b, e, "control blocks"));
@@ -365,8 +374,9 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
         for (int k = 0; k < 3; ++k) {
             E.U[k] = b->buf + off + E.fs * 5 * k;
             E.W[k] = b->buf + off + E.fs * (15 + 4 * k);
+            E.S[k] = c.split ? b->buf + off + E.fs * (27 + 3 * k) : nullptr;
         }
-        off += 27 * E.fs;
+        off += (c.split ? 36 : 27) * E.fs;
         for (int d = 0; d < 3; ++d) {
             E.n[d] = c.n[d];
             E.bc[d] = c.bc[d];
@@ -416,7 +426,7 @@ hydro_status hydro_batch_set_state(hydro_batch_t* b, int32_t e, const double* u,
     for (int f = 0; f < 5; ++f)
         BCK(b, cudaMemcpyAsync(E.U[0] + f * E.fs, u + f * field_stride, sizeof(double) * E.ncell, k, b->stream), "copy");
     reset_ctl_kernel<<<1, 1, 0, b->stream>>>(E.ctl, t);
-    prepare_kernel<<<bblocks(E.ncell), 256, 0, b->stream>>>(E.U[0], E.W[0], E.fs, E.ncell, E.cs2, E.ctl);
+    prepare_kernel<<<bblocks(E.ncell), 256, 0, b->stream>>>(E.U[0], E.W[0], E.fs, E.ncell, E.cs2, E.ctl, E.S[0]);
     BCK(b, cudaGetLastError(), "prepare");
     b->loaded[e] = 1;
     return HYDRO_OK;
@@ -439,7 +449,7 @@ hydro_status hydro_batch_set_primitive(hydro_batch_t* b, int32_t e, const double
     }
     reset_ctl_kernel<<<1, 1, 0, b->stream>>>(E.ctl, t);
     prim2con_kernel<<<bblocks(E.ncell), 256, 0, b->stream>>>(src, ss, E.U[0], E.fs, E.ncell, E.cs2, E.ctl);
-    prepare_kernel<<<bblocks(E.ncell), 256, 0, b->stream>>>(E.U[0], E.W[0], E.fs, E.ncell, E.cs2, E.ctl);
+    prepare_kernel<<<bblocks(E.ncell), 256, 0, b->stream>>>(E.U[0], E.W[0], E.fs, E.ncell, E.cs2, E.ctl, E.S[0]);
     BCK(b, cudaGetLastError(), "prim2con");
     b->loaded[e] = 1;
     return HYDRO_OK;
@@ -528,7 +538,7 @@ int32_t hydro_batch_size(hydro_batch_t* b) { return b ? b->n_events : 0; }
 hydro_status hydro_batch_set_launch(hydro_batch_t* b, int32_t variant, int32_t zc)
 {
     if (!b) return HYDRO_ERR_INVALID_ARG;
-    if (variant < 0 || variant >= hydro_launch_variants(b->cfg[0].scheme))
+    if (variant < 0 || variant >= hydro_launch_variants(b->cfg[0].scheme, b->cfg[0].split))
         return bfail(b, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     return apply_batch_launch(b, variant, zc);
 }
@@ -560,7 +570,7 @@ hydro_status hydro_batch_autotune(hydro_batch_t* b, double* best_ms)
     BCK(b, cudaEventCreate(&e0), "event");
     BCK(b, cudaEventCreate(&e1), "event");
     const int eb = (b->n_events + 127) / 128;
-    for (int v = 0; v < hydro_launch_variants(b->cfg[0].scheme) && s == HYDRO_OK; ++v)
+    for (int v = 0; v < hydro_launch_variants(b->cfg[0].scheme, b->cfg[0].split) && s == HYDRO_OK; ++v)
         for (int zc : zcs) {
             s = apply_batch_launch(b, v, zc);
             if (s) break;

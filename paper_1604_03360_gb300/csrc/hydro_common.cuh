@@ -42,7 +42,9 @@ __global__ void step_end_kernel(Ctl* c);
 __global__ void set_t_end_kernel(Ctl* c, double t_end);
 __global__ void reset_ctl_kernel(Ctl* c, double t);
 // primitives and speeds of a state (after set_state)
-__global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c);
+// (and, if s != nullptr, the per-axis speeds of every cell: 3 fields)
+__global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c,
+                               double* s = nullptr);
 // primitives (e, v, n) -> conserved
 __global__ void prim2con_kernel(const double* wp, long long ws, double* u, long long fs, long long n, double cs2,
                                 Ctl* c);
@@ -77,12 +79,12 @@ struct StageLaunch {
     int tx, ty;
     int ctas_per_sm;
 };
-// tile shapes compiled for each scheme; index 0 is the default
-constexpr int kTileVariants = 3;
-// fills *out for variant v (0 <= v < kTileVariants); returns
-// cudaErrorInvalidValue for a variant that does not exist for this scheme
-cudaError_t stage_launch_variant(int R, int v, StageLaunch* out);
-inline cudaError_t stage_launch_info(int R, StageLaunch* out) { return stage_launch_variant(R, 0, out); }
+// Tile shapes compiled per scheme and splitting (index 0 is the default);
+// stage_launch_variant returns cudaErrorInvalidValue for a variant that does
+// not exist.  split: 0 global, 1 local Lax-Friedrichs.
+int launch_variant_count(int R, int split);
+cudaError_t stage_launch_variant(int R, int split, int v, StageLaunch* out);
+inline cudaError_t stage_launch_info(int R, StageLaunch* out) { return stage_launch_variant(R, 0, 0, out); }
 
 inline int pick_zc(int nx, int ny, int nz, const StageLaunch& L, int sms)
 {

@@ -46,7 +46,7 @@ __global__ void reset_ctl_kernel(Ctl* c, double t)
     c->status = 0;
 }
 
-__global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c)
+__global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c, double* s)
 {
     unsigned long long am[3] = {0ull, 0ull, 0ull};
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -61,9 +61,12 @@ __global__ void prepare_kernel(const double* u, double* w, long long fs, long lo
             for (int d = 0; d < 3; ++d) {
                 const unsigned long long b = (unsigned long long)__double_as_longlong(sp[d]);
                 am[d] = b > am[d] ? b : am[d];
+                if (s) s[d * fs + q] = sp[d];
             }
         } else {
             for (int k = 0; k < 4; ++k) w[k * fs + q] = 0.0;
+            if (s)
+                for (int d = 0; d < 3; ++d) s[d * fs + q] = 0.0;
             if (atomicCAS(&c->status, 0, (int)HYDRO_ERR_UNPHYSICAL) == 0) c->bad_cell = q;
         }
     }
@@ -115,26 +118,40 @@ __global__ void state_to_prim_kernel(const double* u, long long fs, double* out,
     }
 }
 
-template <int R, int TX, int TY, int ILP = 1>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
 static cudaError_t info_for(StageLaunch* out)
 {
-    out->fn = stage_kernel<R, TX, TY, ILP>;
-    out->smem = StageSmem<R, TX, TY>::bytes;
+    out->fn = stage_kernel<R, TX, TY, ILP, LLF>;
+    out->smem = StageSmem<R, TX, TY, LLF>::bytes;
     out->tx = TX;
     out->ty = TY;
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY, ILP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)out->smem);
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY, ILP, LLF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_kernel<R, TX, TY, ILP>, TX * TY,
-                                                         out->smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_kernel<R, TX, TY, ILP, LLF>,
+                                                         TX * TY, out->smem);
 }
 
 // WENO5: 16x16 (1 CTA of 8 warps per SM), 16x8 (2 CTAs of 4 warps), 32x8,
 //        16x16 with two face items per iteration.
 // WENO7: 16x16 (8 warps, 221 KB shared memory), 16x8 (4 warps), 16x16 with two
 //        face items per iteration.
-cudaError_t stage_launch_variant(int R, int v, StageLaunch* out)
+// Local LF (raw staging, 2G-plane ring): WENO5 16x16 and 16x8; WENO7 16x8
+// (16x16 would need 247 KB of shared memory).
+int launch_variant_count(int R, int split)
 {
+    if (split == 1) return R == 3 ? 2 : 1;
+    return R == 3 ? 4 : 3;
+}
+
+cudaError_t stage_launch_variant(int R, int split, int v, StageLaunch* out)
+{
+    if (split == 1) {
+        if (R == 3 && v == 0) return info_for<3, 16, 16, 1, true>(out);
+        if (R == 3 && v == 1) return info_for<3, 16, 8, 1, true>(out);
+        if (R == 4 && v == 0) return info_for<4, 16, 8, 1, true>(out);
+        return cudaErrorInvalidValue;
+    }
     if (R == 3) {
         if (v == 0) return info_for<3, 16, 16>(out);
         if (v == 1) return info_for<3, 16, 8>(out);
@@ -166,7 +183,7 @@ std::string check_config(const hydro_config* c)
     if (!(c->cs2 > 0.0 && c->cs2 < 1.0)) return "cs2 must lie in (0, 1)";
     if (!(c->weno_eps > 0.0)) return "weno_eps must be positive";
     if (!(c->dt_fixed > 0.0) && !(c->cfl > 0.0)) return "need cfl > 0 or dt_fixed > 0";
-    if (c->reserved != 0) return "reserved must be 0";
+    if (c->split != 0 && c->split != 1) return "split must be 0 (global) or 1 (local Lax-Friedrichs)";
     return std::string();
 }
 

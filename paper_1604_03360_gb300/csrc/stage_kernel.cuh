@@ -22,6 +22,12 @@
 //   4. each thread combines the six face fluxes of its cell and finishes.
 // Primitive variables (p, v) of the stage input come from the previous
 // stage's epilogue, so no cell is recovered twice in a stage.
+//
+// Local Lax-Friedrichs variant (LLF): each face splits with its own speed,
+// the largest |lambda| over the 2G cells of its two stencils, so cells are
+// staged raw -- flux f, state u and that cell's speed s (kept from the
+// previous stage's epilogue) -- and every face forms g+- = f +- alpha_face u
+// itself.  The z ring then holds 2G planes and each z face is computed whole.
 #pragma once
 #include "hydro_math.cuh"
 
@@ -47,6 +53,8 @@ struct StageArgs {
     unsigned long long* alpha_out;       // 3 speeds of u_out (atomicMax target)
     int* status;            // first error code
     long long* bad_cell;    // linear index of the first unphysical cell
+    const double* s_in;     // local LF only: 3 fields, max |lambda| per axis of u_s
+    double* s_out;          // local LF only: 3 fields, the same for u_out
 };
 
 __device__ __forceinline__ int bc_map(int i, int n, int bc)
@@ -59,13 +67,15 @@ __device__ __forceinline__ int bc_map(int i, int n, int bc)
     return i < 0 ? 0 : n - 1;
 }
 
-template <int R, int TX, int TY>
+template <int R, int TX, int TY, bool LLF = false>
 struct StageSmem {
-    static constexpr int G = R, S = 2 * R - 1, NT = TX * TY, NRING = 2 * R - 1;
+    static constexpr int G = R, S = 2 * R - 1, NT = TX * TY;
+    static constexpr int NV = LLF ? 11 : 10;                 // staged values per cell
+    static constexpr int NRING = LLF ? 2 * R : 2 * R - 1;    // z planes kept per column
     static constexpr int GXW = TX + 2 * G, GYH = TY + 2 * G;
-    static constexpr int RING = NRING * 10 * NT;
-    static constexpr int GX = 10 * TY * GXW;
-    static constexpr int GY = 10 * GYH * TX;
+    static constexpr int RING = NRING * NV * NT;
+    static constexpr int GX = NV * TY * GXW;
+    static constexpr int GY = NV * GYH * TX;
     static constexpr int FX = 5 * TY * (TX + 1);
     static constexpr int FY = 5 * (TY + 1) * TX;
     static constexpr size_t bytes = sizeof(double) * (size_t)(RING + GX + GY + FX + FY);
@@ -90,13 +100,56 @@ __device__ __forceinline__ void split_flux(int d, const double u[5], const doubl
     }
 }
 
+// physical flux f_d(u) of one cell along axis d
+__device__ __forceinline__ void raw_flux(int d, const double u[5], const double w[4], double f[5])
+{
+    const double vd = w[1 + d];
+    f[0] = u[1 + d];
+    f[1] = u[1] * vd;
+    f[2] = u[2] * vd;
+    f[3] = u[3] * vd;
+    f[4] = u[4] * vd;
+    f[1 + d] += w[0];
+}
+
+// Local-LF face value (scaled by 2) from raw stencil data of one field over the
+// 2G cells j-G+1 .. j+G of face j+1/2 (element stride st): alpha_face = max s,
+// g+ = f + alpha u on the first 2G-1 cells, g- = f - alpha u on the last 2G-1.
+template <int R>
+__device__ __forceinline__ double llf_face(const double* f, const double* u, const double* s, int st, double eps_s)
+{
+    constexpr int W = 2 * R, S = 2 * R - 1;
+    unsigned long long ab = (unsigned long long)__double_as_longlong(s[0]);
+#pragma unroll
+    for (int i = 1; i < W; ++i) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(s[i * st]);
+        ab = b > ab ? b : ab;   // speeds are >= 0: integer order = value order
+    }
+    const double a = __longlong_as_double((long long)ab);
+    double fv[W], uv[W], vp[S], vm[S];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        fv[i] = f[i * st];
+        uv[i] = u[i * st];
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        vp[i] = fma(a, uv[i], fv[i]);
+        vm[i] = fma(-a, uv[i + 1], fv[i + 1]);
+    }
+    double Np, Dp, Nm, Dm;
+    weno_left<R>(vp, eps_s, Np, Dp);
+    weno_right<R>(vm, eps_s, Nm, Dm);
+    return face_sum(Np, Dp, Nm, Dm);
+}
+
 // One work item: column tile (tile_x, tile_y) of TX x TY cells and z chunk chunk_z of the
 // grid described by a.  All threads of the CTA call it with the same item.
-template <int R, int TX, int TY, int ILP = 1>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
 {
-    using SM = StageSmem<R, TX, TY>;
-    constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING;
+    using SM = StageSmem<R, TX, TY, LLF>;
+    constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING, NV = SM::NV;
     constexpr int GXW = SM::GXW, GYH = SM::GYH;
     double* ring = smem;
     double* gx = ring + SM::RING;
@@ -127,17 +180,40 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         for (int k = 0; k < 4; ++k) w[k] = __ldg(a.w_in + k * fs + q);
     };
     auto slot_of = [&](int m) { return (m + 4 * NRING) % NRING; };
+    // ring slot layout: global LF g+ (5), g- (5); local LF f (5), u (5), s_z
     auto ingest = [&](int m) {
         const long long q = (long long)bc_map(m, nz, a.bc[2]) * plane + (long long)ys * nx + xs;
         double u[5], w[4], gp[5], gm[5];
         load(q, u, w);
-        split_flux(2, u, w, al[2], gp, gm);
-        double* r = ring + slot_of(m) * 10 * NT + tid;
+        double* r = ring + slot_of(m) * NV * NT + tid;
+        if constexpr (LLF) {
+            raw_flux(2, u, w, gp);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            r[k * NT] = gp[k];
-            r[(5 + k) * NT] = gm[k];
+            for (int k = 0; k < 5; ++k) {
+                r[k * NT] = gp[k];
+                r[(5 + k) * NT] = u[k];
+            }
+            r[10 * NT] = __ldg(a.s_in + 2 * fs + q);
+        } else {
+            split_flux(2, u, w, al[2], gp, gm);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                r[k * NT] = gp[k];
+                r[(5 + k) * NT] = gm[k];
+            }
         }
+    };
+    // local LF: the whole z face m+1/2 of field k from planes m-G+1 .. m+G
+    auto face_z_llf = [&](int m, int k) {
+        double fv[2 * G], uv[2 * G], sv[2 * G];
+#pragma unroll
+        for (int i = 0; i < 2 * G; ++i) {
+            const double* r = ring + slot_of(m - G + 1 + i) * NV * NT + tid;
+            fv[i] = r[k * NT];
+            uv[i] = r[(5 + k) * NT];
+            sv[i] = r[10 * NT];
+        }
+        return llf_face<R>(fv, uv, sv, 1, a.eps_s);
     };
     // N/D of the left-biased (+) and right-biased (-) reconstructions of the
     // z-stencil centred on plane m, field k
@@ -145,7 +221,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         double vp[S], vm[S];
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            const double* r = ring + slot_of(m - G + 1 + i) * 10 * NT + tid;
+            const double* r = ring + slot_of(m - G + 1 + i) * NV * NT + tid;
             vp[i] = r[k * NT];
             vm[i] = r[(5 + k) * NT];
         }
@@ -159,7 +235,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     double hNp[5], hDp[5], Fzm[5], Fzp[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) { hNp[k] = 0.0; hDp[k] = 1.0; Fzm[k] = 0.0; Fzp[k] = 0.0; }
-    if (zwork) {
+    if (zwork && LLF) {
+        for (int m = zb - G; m <= zb + G - 1; ++m) ingest(m);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Fzm[k] = face_z_llf(zb - 1, k);
+    } else if (zwork) {
         for (int m = zb - G; m <= zb + G - 2; ++m) ingest(m);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -188,7 +268,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 
     for (int p = zb; p < ze; ++p) {
         // 1. z: ingest plane p+G, face p+1/2 = R+(p) + R-(p+1)
-        if (zwork) {
+        if (zwork && LLF) {
+            ingest(p + G);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Fzp[k] = face_z_llf(p, k);
+        } else if (zwork) {
             ingest(p + G);
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -206,22 +290,44 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             if (it < ngx) {
                 const int row = it / wx, col = it % wx;
                 const int xx = bc_map(x0 - G + col, nx, a.bc[0]), yy = bc_map(y0 + row, ny, a.bc[1]);
-                load(qz + (long long)yy * nx + xx, u, w);
-                split_flux(0, u, w, al[0], gp, gm);
+                const long long q = qz + (long long)yy * nx + xx;
+                load(q, u, w);
+                if constexpr (LLF) {
+                    raw_flux(0, u, w, gp);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    gx[(k * TY + row) * GXW + col] = gp[k];
-                    gx[((5 + k) * TY + row) * GXW + col] = gm[k];
+                    for (int k = 0; k < 5; ++k) {
+                        gx[(k * TY + row) * GXW + col] = gp[k];
+                        gx[((5 + k) * TY + row) * GXW + col] = u[k];
+                    }
+                    gx[(10 * TY + row) * GXW + col] = __ldg(a.s_in + q);
+                } else {
+                    split_flux(0, u, w, al[0], gp, gm);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        gx[(k * TY + row) * GXW + col] = gp[k];
+                        gx[((5 + k) * TY + row) * GXW + col] = gm[k];
+                    }
                 }
             } else {
                 const int j = it - ngx, row = j / ncol, col = j % ncol;
                 const int xx = bc_map(x0 + col, nx, a.bc[0]), yy = bc_map(y0 - G + row, ny, a.bc[1]);
-                load(qz + (long long)yy * nx + xx, u, w);
-                split_flux(1, u, w, al[1], gp, gm);
+                const long long q = qz + (long long)yy * nx + xx;
+                load(q, u, w);
+                if constexpr (LLF) {
+                    raw_flux(1, u, w, gp);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    gy[(k * GYH + row) * TX + col] = gp[k];
-                    gy[((5 + k) * GYH + row) * TX + col] = gm[k];
+                    for (int k = 0; k < 5; ++k) {
+                        gy[(k * GYH + row) * TX + col] = gp[k];
+                        gy[((5 + k) * GYH + row) * TX + col] = u[k];
+                    }
+                    gy[(10 * GYH + row) * TX + col] = __ldg(a.s_in + fs + q);
+                } else {
+                    split_flux(1, u, w, al[1], gp, gm);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        gy[(k * GYH + row) * TX + col] = gp[k];
+                        gy[((5 + k) * GYH + row) * TX + col] = gm[k];
+                    }
                 }
             }
         }
@@ -248,6 +354,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             }
         };
         const int nitems = nfx + nfy;
+        if constexpr (LLF) {
+            // local LF: window of 2G raw cells starting at the same place as g+
+            for (int it = tid; it < nitems; it += NT) {
+                const double* pp;
+                const double* pm;
+                int st;
+                double* out;
+                locate(it, pp, pm, st, out);
+                // pp points at f_k of the window start; u_k and s sit 5 and 10-k
+                // field blocks further in the same staged array
+                const int fb = (it < nfx) ? TY * GXW : GYH * TX;      // one field block
+                const int k = (it < nfx) ? it / (nrow * (ncol + 1)) : (it - nfx) / ((nrow + 1) * ncol);
+                *out = llf_face<R>(pp, pp + 5 * fb, pp + (10 - k) * fb, st, a.eps_s);
+            }
+        } else
         for (int it0 = tid; it0 < nitems; it0 += ILP * NT) {
             double vp[ILP][S], vm[ILP][S], F[ILP];
             double* out[ILP];
@@ -308,10 +429,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 for (int d = 0; d < 3; ++d) {
                     const unsigned long long b = (unsigned long long)__double_as_longlong(sp[d]);
                     amax[d] = b > amax[d] ? b : amax[d];
+                    if constexpr (LLF) a.s_out[d * fs + q] = sp[d];
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) a.w_out[k * fs + q] = 0.0;
+                if constexpr (LLF)
+                    for (int d = 0; d < 3; ++d) a.s_out[d * fs + q] = 0.0;
                 if (atomicCAS(a.status, 0, 4) == 0) *a.bad_cell = q;
             }
         }
@@ -331,11 +455,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 }
 
-template <int R, int TX, int TY, int ILP = 1>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
 __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) stage_kernel(const StageArgs a)
 {
     extern __shared__ __align__(16) double smem[];
-    stage_tile<R, TX, TY, ILP>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    stage_tile<R, TX, TY, ILP, LLF>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 }  // namespace hydro

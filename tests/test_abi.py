@@ -41,7 +41,7 @@ def test_version(L):
 
 @pytest.mark.parametrize("field,value,msg", [
     ("scheme", 6, b"scheme"), ("cs2", 1.0, b"cs2"), ("weno_eps", 0.0, b"weno_eps"),
-    ("reserved", 1, b"reserved"),
+    ("split", 2, b"split"),
 ])
 def test_invalid_config_rejected(L, field, value, msg):
     import paper_1604_03360_gb300 as H

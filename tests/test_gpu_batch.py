@@ -132,3 +132,18 @@ def test_batch_ensemble_time_step_keeps_events_physical():
     g0, w0 = ev[0]
     ref = oracle.run(oracle_cfg(g0), oracle.prim2con(w0), 100)[0]
     assert np.all(field_errors(out[0][0], ref) <= TOL)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_batch_local_lf(scheme):
+    from paper_1604_03360_gb300 import HydroBatch
+    ev = make_events(SIZES[:4], scheme=scheme, seed=1010)
+    for g, _ in ev:
+        g.split = 1
+    with HydroBatch([g for g, _ in ev]) as b:
+        for i, (g, w) in enumerate(ev):
+            b.set_primitive(i, w)
+        b.step(3)
+        for i, (g, w) in enumerate(ev):
+            ref = oracle.run(oracle_cfg(g), oracle.prim2con(w), 3)[0]
+            assert np.all(field_errors(b.get_state(i)[0], ref) <= TOL), i

@@ -216,3 +216,58 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
             got = h.get_state()
         assert np.all(field_errors(got, ref) <= TOL)
     assert (tmp_path / "tune.txt").read_text().strip()
+
+
+# ---------------------------------------------------------------- local Lax-Friedrichs
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_local_lf_sod(scheme):
+    g, w = W.sod(N=400, scheme=scheme)
+    g.split = 1
+    assert_parity(g, w, 100000, t0=0.0, t_end=0.4)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+@pytest.mark.parametrize("dims", [(37, 29, 21), (23, 17, 1), (1, 19, 23)])
+def test_local_lf_ragged(scheme, dims):
+    g, w = W.lumpy(n=dims, seed=5 + sum(dims), scheme=scheme)
+    w = with_flow(g, w)
+    g.split = 1
+    assert_parity(g, w, 6)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_local_lf_periodic_and_ellipsoidal(scheme):
+    g, w = W.smooth_periodic(n=(19, 13, 11), amp=0.3, vamp=0.5, seed=4, scheme=scheme)
+    g.split = 1
+    assert_parity(g, w, 8)
+    g, w = W.ellipsoidal(N=40, scheme=scheme)
+    g.split = 1
+    g.cfl = 0.3 * 40 / 256
+    assert_parity(g, w, 40)
+
+
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (7, 0)])
+def test_local_lf_every_launch_variant(scheme, variant):
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=(37, 29, 21), seed=78, scheme=scheme)
+    w = with_flow(g, w)
+    g.split = 1
+    u0 = oracle.prim2con(w)
+    ref = oracle.run(oracle_cfg(g), u0, 4)[0]
+    with Hydro.from_grid(g) as h:
+        h.set_launch(variant, 8)
+        h.set_state(u0)
+        h.step(4)
+        got = h.get_state()
+    assert np.all(field_errors(got, ref) <= TOL)
+
+
+def test_local_lf_rejected_where_unsupported():
+    from paper_1604_03360_gb300 import Hydro, HydroError
+    g, w = W.lumpy(n=(12, 11, 10), seed=2)
+    g.split = 1
+    with Hydro.from_grid(g) as h:
+        h.set_primitive(w)
+        with pytest.raises(HydroError) as ei:
+            h.forward_record(2, 1)
+        assert ei.value.code == 1 and "global Lax-Friedrichs" in str(ei.value)

@@ -33,6 +33,7 @@ class Grid:
     scheme: int = 5
     cfl: float = 0.3
     dt_fixed: float = 0.0       # > 0: constant time step instead of the CFL rule
+    split: int = 0              # 0 global, 1 local Lax-Friedrichs splitting
     cs2: float = CS2
     eps: float = 1e-6
     t0: float = 0.0

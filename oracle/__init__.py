@@ -47,6 +47,8 @@ class Cfg(ctypes.Structure):
         ("r", ctypes.c_int32),
         ("bc", ctypes.c_int32 * 3),
         ("split", ctypes.c_int32),
+        ("nq", ctypes.c_int32),
+        ("pad2_", ctypes.c_int32),
         ("dx", ctypes.c_double * 3),
         ("cs2", ctypes.c_double),
         ("cfl", ctypes.c_double),
@@ -74,8 +76,8 @@ def lib():
         L.oc_L.argtypes = [P(Cfg), vp, vp, vp]
         L.oc_run.argtypes = [P(Cfg), vp, ctypes.c_int, d, P(d), P(ctypes.c_int64), vp, vp, vp, vp]
         L.oc_eps2.argtypes = [P(Cfg), vp, P(d)]
-        L.oc_con2prim_n.argtypes = [d, vp, ctypes.c_int64, vp]
-        L.oc_prim2con_n.argtypes = [d, vp, ctypes.c_int64, vp]
+        L.oc_con2prim_n.argtypes = [d, ctypes.c_int, vp, ctypes.c_int64, vp]
+        L.oc_prim2con_n.argtypes = [d, ctypes.c_int, vp, ctypes.c_int64, vp]
         L.oc_set_threads.argtypes = [ctypes.c_int]
         L.oc_get_max_threads.restype = ctypes.c_int
         _lib = L
@@ -100,9 +102,10 @@ def max_threads():
     return lib().oc_get_max_threads()
 
 
-def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0, eps=1e-6, split=0):
+def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0, eps=1e-6, split=0, nq=1):
     """n = (nx, ny, nz); scheme 5 (WENO5) or 7 (WENO7); bc 0 outflow / 1 periodic;
-    split 0 global / 1 local Lax-Friedrichs."""
+    split 0 global / 1 local Lax-Friedrichs; nq conserved charges (state has
+    4 + nq fields)."""
     c = Cfg()
     for i in range(3):
         c.n[i] = int(n[i])
@@ -114,26 +117,28 @@ def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0
     c.dt_fixed = float(dt_fixed)
     c.eps = float(eps)
     c.split = int(split)
+    c.nq = int(nq)
     return c
 
 
 def _shape(c):
-    return (5, c.n[2], c.n[1], c.n[0])
+    return (4 + max(1, c.nq), c.n[2], c.n[1], c.n[0])
 
 
 def con2prim(u, cs2=1.0 / 3.0):
-    """u: (5, ...) conserved -> (5, ...) primitives (e, vx, vy, vz, n); NaN where unphysical."""
+    """u: (4+q, ...) conserved (E, M, R_1..R_q) -> primitives (e, vx, vy, vz,
+    n_1..n_q); NaN where unphysical."""
     u = _c(u)
     w = np.empty_like(u)
     n = u[0].size
-    lib().oc_con2prim_n(cs2, _ptr(u), n, _ptr(w))
+    lib().oc_con2prim_n(cs2, u.shape[0], _ptr(u), n, _ptr(w))
     return w
 
 
 def prim2con(w, cs2=1.0 / 3.0):
     w = _c(w)
     u = np.empty_like(w)
-    lib().oc_prim2con_n(cs2, _ptr(w), w[0].size, _ptr(u))
+    lib().oc_prim2con_n(cs2, w.shape[0], _ptr(w), w[0].size, _ptr(u))
     return u
 
 

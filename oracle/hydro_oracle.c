@@ -31,6 +31,9 @@
  * copy the edge cell into the ghost cells (zeroth-order extrapolation of the
  * conserved variables); periodic boundaries wrap; directions with a single
  * cell contribute no flux difference.
+ * Several conserved charges (nq > 1): the state is (E, M, R_1..R_nq); every
+ * charge is a passive density advected like R (flux R_k v_d, n_k = R_k / gamma),
+ * since p = cs2 e does not depend on them.
  * Local Lax-Friedrichs variant (split = 1): the face j+1/2 along d uses
  * alpha = max over the 2r cells j-r+1 .. j+r (the union of both biased
  * stencils) of max(|lambda_-|, |lambda_+|) along d; the time step still uses
@@ -55,6 +58,8 @@ typedef struct {
     int32_t r;         /* WENO parameter: 3 -> WENO5, 4 -> WENO7 */
     int32_t bc[3];     /* 0: outflow (copy edge cell), 1: periodic */
     int32_t split;     /* 0: global Lax-Friedrichs, 1: local Lax-Friedrichs */
+    int32_t nq;        /* conserved charge densities R_1..R_nq (0 or 1: one) */
+    int32_t pad_;
     double dx[3];      /* cell sizes |e_i| */
     double cs2;        /* EOS p = cs2 * e */
     double cfl;
@@ -63,7 +68,8 @@ typedef struct {
 } oc_cfg;
 
 enum { OC_OK = 0, OC_ERR_ARG = 1, OC_ERR_UNPHYSICAL = 4, OC_ERR_OOM = 3 };
-#define NF 5
+#define MAXF 8   /* E, M_x, M_y, M_z and up to four charges */
+static int nfields(const void *cfg);
 
 /* ------------------------------------------------------------------------ */
 /* Thermodynamics and fluxes (Eq. 1)                                        */
@@ -111,7 +117,7 @@ void oc_prim2con(double k, const double *w, double *u)
 
 /* Physical flux along direction d (Eq. 1): f_d(E) = M_d = T^{0d},
  * f_d(M_j) = M_j v_d + p delta_jd = T^{jd}, f_d(R) = R v_d = n u^d. */
-void oc_flux(double k, int d, const double *u, const double *w, double *f)
+void oc_flux_n(double k, int d, int nf, const double *u, const double *w, double *f)
 {
     const double p = k * w[0];
     const double vd = w[1 + d];
@@ -119,8 +125,10 @@ void oc_flux(double k, int d, const double *u, const double *w, double *f)
     f[1] = u[1] * vd + (d == 0 ? p : 0.0);
     f[2] = u[2] * vd + (d == 1 ? p : 0.0);
     f[3] = u[3] * vd + (d == 2 ? p : 0.0);
-    f[4] = u[4] * vd;
+    for (int q = 4; q < nf; ++q) f[q] = u[q] * vd;   /* charges: R_q v_d */
 }
+
+void oc_flux(double k, int d, const double *u, const double *w, double *f) { oc_flux_n(k, d, 5, u, w, f); }
 
 /* Characteristic (sound-wave) speeds along d for p = k e:
  * lambda_+- = [v_d (1-k) +- sqrt(k) sqrt((1-v^2)(1 - v_d^2 - k (v^2 - v_d^2)))]
@@ -254,6 +262,11 @@ int oc_get_max_threads(void)
 }
 
 static int active(const oc_cfg *c, int d) { return c->n[d] > 1; }
+static int nfields(const void *cfg)
+{
+    const oc_cfg *c = (const oc_cfg *)cfg;
+    return 4 + (c->nq > 1 ? c->nq : 1);
+}
 
 /* index of the interior cell that supplies (possibly ghost) coordinate i */
 static int bc_src(const oc_cfg *c, int d, int i)
@@ -276,6 +289,7 @@ static int cfg_ok(const oc_cfg *c)
         if (c->n[d] < 1 || !(c->dx[d] > 0) || (c->bc[d] != 0 && c->bc[d] != 1)) return 0;
     if (c->r != 3 && c->r != 4) return 0;
     if (c->split != 0 && c->split != 1) return 0;
+    if (c->nq < 0 || c->nq > MAXF - 4) return 0;
     if (!(c->cs2 > 0 && c->cs2 < 1) || !(c->eps > 0)) return 0;
     for (int d = 0; d < 3; ++d)
         if (active(c, d) && c->bc[d] == 1 && c->n[d] < c->r) return 0;
@@ -291,8 +305,8 @@ int oc_alpha(const oc_cfg *c, const double *u, double *alpha)
     int bad = 0;
 #pragma omp parallel for reduction(max : a0, a1, a2) reduction(| : bad) num_threads(oc_get_max_threads())
     for (int64_t q = 0; q < N; ++q) {
-        double uu[NF], w[NF], lam[2];
-        for (int f = 0; f < NF; ++f) uu[f] = u[f * N + q];
+        double uu[MAXF], w[MAXF], lam[2];
+        for (int f = 0; f < 5; ++f) uu[f] = u[f * N + q];
         if (oc_con2prim(c->cs2, uu, w)) {
             bad |= 1;
             continue;
@@ -320,6 +334,7 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
 {
     if (!cfg_ok(c)) return OC_ERR_ARG;
     const int r = c->r, G = r;
+    const int NF = nfields(c);
     const int64_t N = (int64_t)c->n[0] * c->n[1] * c->n[2];
     int bad = 0;
 #pragma omp parallel for num_threads(oc_get_max_threads())
@@ -352,13 +367,13 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
                 ijk[da] = ia;
                 ijk[db] = ib;
                 const int64_t q = cell(c, ijk[0], ijk[1], ijk[2]);
-                double uu[NF], w[NF], f[NF];
+                double uu[MAXF], w[MAXF], f[MAXF];
                 for (int k = 0; k < NF; ++k) uu[k] = u[k * N + q];
                 if (oc_con2prim(c->cs2, uu, w)) {
                     bad |= 1;
-                    for (int k = 0; k < NF; ++k) w[k] = 0.0;
+                    for (int k = 0; k < 5; ++k) w[k] = 0.0;
                 }
-                oc_flux(c->cs2, d, uu, w, f);
+                oc_flux_n(c->cs2, d, NF, uu, w, f);
                 for (int k = 0; k < NF; ++k) {
                     fp[k * len + m] = 0.5 * (f[k] + alpha[d] * uu[k]);
                     fm[k * len + m] = 0.5 * (f[k] - alpha[d] * uu[k]);
@@ -437,7 +452,7 @@ static int rk_stage(const oc_cfg *c, const double *un, const double *us, const d
 {
     const int rc = oc_L(c, us, alpha, Lbuf);
     if (rc) return rc;
-    const int64_t M = (int64_t)NF * c->n[0] * c->n[1] * c->n[2];
+    const int64_t M = (int64_t)nfields(c) * c->n[0] * c->n[1] * c->n[2];
 #pragma omp parallel for num_threads(oc_get_max_threads())
     for (int64_t q = 0; q < M; ++q) {
         const double s = us[q] + dt * Lbuf[q];
@@ -455,7 +470,7 @@ int oc_run(const oc_cfg *c, double *u, int nsteps, double t_end, double *t, int6
            const double *alpha_in, const double *dt_in, double *alpha_out, double *dt_out)
 {
     if (!cfg_ok(c) || nsteps < 0 || !t) return OC_ERR_ARG;
-    const int64_t M = (int64_t)NF * c->n[0] * c->n[1] * c->n[2];
+    const int64_t M = (int64_t)nfields(c) * c->n[0] * c->n[1] * c->n[2];
     double *u1 = malloc(sizeof(double) * M), *u2 = malloc(sizeof(double) * M);
     double *Lb = malloc(sizeof(double) * M);
     int rc = OC_OK;
@@ -502,8 +517,8 @@ int oc_eps2(const oc_cfg *c, const double *u, double *out)
     const int64_t N = (int64_t)c->n[0] * c->n[1] * c->n[2];
     double num = 0.0, den = 0.0;
     for (int64_t q = 0; q < N; ++q) {
-        double uu[NF], w[NF];
-        for (int f = 0; f < NF; ++f) uu[f] = u[f * N + q];
+        double uu[MAXF], w[MAXF];
+        for (int f = 0; f < 5; ++f) uu[f] = u[f * N + q];
         if (oc_con2prim(c->cs2, uu, w)) return OC_ERR_UNPHYSICAL;
         const double p = c->cs2 * w[0];
         const double txx = uu[1] * w[1] + p, tyy = uu[2] * w[2] + p;
@@ -515,27 +530,34 @@ int oc_eps2(const oc_cfg *c, const double *u, double *out)
 }
 
 /* Array versions of the point functions, for tests. */
-int oc_con2prim_n(double k, const double *u, int64_t n, double *w)
+/* (E, M, R_1..R_q) <-> (e, v, n_1..n_q) for nf = 4 + q fields of n cells. */
+int oc_con2prim_n(double k, int nf, const double *u, int64_t n, double *w)
 {
     int bad = 0;
+    if (nf < 5 || nf > MAXF) return OC_ERR_ARG;
     for (int64_t q = 0; q < n; ++q) {
-        double uu[NF], ww[NF];
-        for (int f = 0; f < NF; ++f) uu[f] = u[f * n + q];
+        double uu[MAXF], ww[MAXF];
+        for (int f = 0; f < nf; ++f) uu[f] = u[f * n + q];
         if (oc_con2prim(k, uu, ww)) {
             bad = 1;
-            for (int f = 0; f < NF; ++f) ww[f] = NAN;
+            for (int f = 0; f < nf; ++f) ww[f] = NAN;
+        } else {
+            const double v2 = ww[1] * ww[1] + ww[2] * ww[2] + ww[3] * ww[3];
+            for (int f = 5; f < nf; ++f) ww[f] = uu[f] * sqrt(1.0 - v2);
         }
-        for (int f = 0; f < NF; ++f) w[f * n + q] = ww[f];
+        for (int f = 0; f < nf; ++f) w[f * n + q] = ww[f];
     }
     return bad ? OC_ERR_UNPHYSICAL : OC_OK;
 }
 
-void oc_prim2con_n(double k, const double *w, int64_t n, double *u)
+void oc_prim2con_n(double k, int nf, const double *w, int64_t n, double *u)
 {
     for (int64_t q = 0; q < n; ++q) {
-        double uu[NF], ww[NF];
-        for (int f = 0; f < NF; ++f) ww[f] = w[f * n + q];
+        double uu[MAXF], ww[MAXF];
+        for (int f = 0; f < nf; ++f) ww[f] = w[f * n + q];
         oc_prim2con(k, ww, uu);
-        for (int f = 0; f < NF; ++f) u[f * n + q] = uu[f];
+        const double g = 1.0 / sqrt(1.0 - (ww[1] * ww[1] + ww[2] * ww[2] + ww[3] * ww[3]));
+        for (int f = 5; f < nf; ++f) uu[f] = ww[f] * g;
+        for (int f = 0; f < nf; ++f) u[f * n + q] = uu[f];
     }
 }

@@ -514,3 +514,45 @@ def test_local_lf_sod_at_least_as_accurate(oracle_lib):
         mid = (x > ex.xi_tail * 0.4 + 0.04) & (x < ex.V_shock * 0.4 - 0.04)
         assert np.abs(p[0].ravel()[mid] / ex.e_star - 1).max() < 0.01
     assert errs[1] <= errs[0] * 1.001, errs
+
+
+# ---------------------------------------------------------------- several charges
+@pytest.mark.parametrize("scheme,split", [(5, 0), (7, 1)])
+def test_extra_charges_are_passive_and_independent(oracle_lib, scheme, split):
+    """With nq charges the first five fields evolve exactly as with one, and
+    charge k evolves exactly as charge 1 would if it were the only one (p = cs2 e
+    does not depend on charges; each is advected component-wise like R)."""
+    g, w = W.lumpy(n=(9, 8, 7), seed=14, scheme=scheme)
+    w[1] = 0.3 * np.tanh(w[0] - 1.0)
+    w3 = W.with_charges(g, w, 3)
+    c3 = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, split=split, nq=3)
+    c1 = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, split=split, nq=1)
+    u3 = oracle_lib.prim2con(w3)
+    assert u3.shape[0] == 7
+    a3, t3, k3 = oracle_lib.run(c3, u3, 3)
+    a1, t1, k1 = oracle_lib.run(c1, u3[:5].copy(), 3)
+    assert t3 == t1 and np.array_equal(a3[:5], a1)
+    for j in (5, 6):
+        uj = u3[:5].copy()
+        uj[4] = u3[j]
+        assert np.array_equal(oracle_lib.run(c1, uj, 3)[0][4], a3[j])
+
+
+def test_extra_charge_conversions_roundtrip(oracle_lib):
+    g, w = W.lumpy(n=(6, 5, 4), seed=3)
+    w[2] = 0.4 * np.tanh(w[0] - 1.0)
+    w4 = W.with_charges(g, w, 4)
+    u = oracle_lib.prim2con(w4)
+    gam = 1.0 / np.sqrt(1.0 - (w4[1] ** 2 + w4[2] ** 2 + w4[3] ** 2))
+    np.testing.assert_allclose(u[5:], w4[5:] * gam, rtol=1e-14)
+    np.testing.assert_allclose(oracle_lib.con2prim(u), w4, rtol=1e-12, atol=1e-15)
+
+
+def test_extra_charges_conserved_periodic(oracle_lib):
+    g, w = W.smooth_periodic(n=(10, 9, 8), seed=6)
+    w3 = W.with_charges(g, w, 3)
+    c = oracle_lib.make_cfg(g.n, g.dx, bc=(1, 1, 1), nq=3)
+    u0 = oracle_lib.prim2con(w3)
+    u1 = oracle_lib.run(c, u0, 4)[0]
+    tot0, tot1 = u0.reshape(7, -1).sum(1), u1.reshape(7, -1).sum(1)
+    assert np.abs(tot1 - tot0).max() < 1e-13 * np.abs(u0).reshape(7, -1).sum(1).max()

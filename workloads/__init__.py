@@ -147,6 +147,16 @@ def lumpy(n=(96, 96, 96), seed=1604, box=6.0, blobs=20, width=0.5, radius=4.0, m
     return g, _stack(g, e, 0.0, 0.0, 0.0, e)
 
 
+def with_charges(g, w, nq=3):
+    """Append nq - 1 further charge densities to primitive data w (shape
+    (5, ...)): n_2 = n^2 / max n, n_3 = 1 + sin of the x coordinate, n_4 = 0.5.
+    Returns data of shape (4 + nq, ...)."""
+    x, _, _ = g.centres()
+    n1 = w[4]
+    extra = [n1 * n1 / n1.max(), np.broadcast_to(1.0 + 0.5 * np.sin(x), n1.shape), np.full(n1.shape, 0.5)]
+    return np.concatenate([w, np.stack(extra[:nq - 1])]) if nq > 1 else w
+
+
 def batch_sizes(events=256, seed=1604, lo=48, hi=160):
     """Per-event grid sizes (nx, ny, nz), each drawn uniformly from [lo, hi]."""
     out = []

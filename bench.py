@@ -439,6 +439,27 @@ def main():
                                  "fp64_frac_global_lf_count": FLOPS_PER_CELL_STAGE[args.scheme] * cells
                                  / (float(kl[1:4].sum()) / 9 * 1e-3) / 1e12 / fp64_peak}
         hl.close()
+    if not args.no_extra:
+        # three conserved charges (state of 7 fields), same workload and scheme
+        import workloads as W
+        gq, wq = workload(args.scheme, args.grid)
+        gq.nq = 3
+        hq = Hydro.from_grid(gq, stream=stream)
+        hq.set_primitive(torch.from_numpy(W.with_charges(gq, wq, 3)).to(dev))
+        hq.autotune()
+        hq.step(3)
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        kq = hq.profile_step(3)
+        a1.record(stream)
+        barrier()
+        hq.sync()
+        elq = a0.elapsed_time(a1) / 1e3
+        extra["charges3_256"] = {"value": cells * 3 / elq, "unit": "cell-updates/s", "steps": 3, "fields": 7,
+                                 "ms_per_step": 1e3 * elq / 3, "launch": hq.launch(),
+                                 "stage_kernel_ms": float(kq[1:4].sum()) / 9}
+        hq.close()
     if not args.no_extra and not args.no_batch:
         extra["batched_vs_looped"] = batched_vs_looped(dev, stream, barrier, 3, 3, args.batch_events)
     if not args.no_extra:

@@ -20,7 +20,8 @@
  * directions with one cell contribute no flux difference.
  *
  * Conventions for every entry point:
- *   - Fields are FP64 structure-of-arrays: field f (0..4) of a state starts at
+ *   - Fields are FP64 structure-of-arrays: field f (0..4, or 0..3+nq with
+ *     several charges) of a state starts at
  *     ptr + f * field_stride and holds nz*ny*nx values, x fastest.
  *     field_stride >= nx*ny*nz (elements, not bytes).
  *   - mem = HYDRO_MEM_HOST: ptr is host memory (pageable or pinned);
@@ -74,6 +75,13 @@ typedef struct {
                            speeds either way.  Local LF is not supported by
                            hydro_forward_record/hydro_adjoint or
                            hydro_step_noalloc (HYDRO_ERR_INVALID_ARG) */
+    int32_t nq;         /* conserved charge densities: 0 or 1 = one (R), up to
+                           3 (R_1, R_2, R_3; "charge densities" in Sec. 1).
+                           Each is passive (p = cs2 e) and advected like R; a
+                           state then has 4 + nq fields (E, M_x, M_y, M_z,
+                           R_1..R_nq) and primitives (e, v, n_1..n_nq).  nq > 1
+                           is supported by the single-grid path only */
+    int32_t reserved2;  /* must be 0 */
     double dx[3];       /* cell sizes |e_i| > 0 */
     double origin[3];   /* lower corner of the box (informational) */
     double cs2;         /* EOS p = cs2 * e, 0 < cs2 < 1 (1/3 in the paper's tests) */
@@ -144,10 +152,10 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
 /* Launch configuration of the stage kernel.  Several CTA tile shapes are
  * compiled per scheme (variant 0 is the default); the z-chunk (planes per CTA)
  * sets how many CTAs share a column.  hydro_set_launch forces a variant
- * (0 <= variant < hydro_launch_variants(scheme, split)) and z-chunk (zc <= 0: the
+ * (0 <= variant < hydro_launch_variants(scheme, split, nq)) and z-chunk (zc <= 0: the
  * built-in wave-count heuristic), rebuilding the step graph.  Results do not
  * depend on the choice beyond FMA-level rounding of the same formulas. */
-int32_t hydro_launch_variants(int32_t scheme, int32_t split);
+int32_t hydro_launch_variants(int32_t scheme, int32_t split, int32_t nq);
 hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc);
 hydro_status hydro_get_launch(hydro_t* h, int32_t* variant, int32_t* tile_x, int32_t* tile_y, int32_t* zc);
 

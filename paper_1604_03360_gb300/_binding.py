@@ -32,6 +32,8 @@ class HydroConfig(ctypes.Structure):
         ("scheme", ctypes.c_int32),
         ("bc", ctypes.c_int32 * 3),
         ("split", ctypes.c_int32),
+        ("nq", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
         ("dx", ctypes.c_double * 3),
         ("origin", ctypes.c_double * 3),
         ("cs2", ctypes.c_double),
@@ -42,7 +44,7 @@ class HydroConfig(ctypes.Structure):
 
 
 def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
-                origin=(0.0, 0.0, 0.0), split=0):
+                origin=(0.0, 0.0, 0.0), split=0, nq=1):
     c = HydroConfig()
     for i in range(3):
         c.n[i] = int(n[i])
@@ -51,6 +53,8 @@ def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=
         c.origin[i] = float(origin[i])
     c.scheme = int(scheme)
     c.split = int(split)
+    c.nq = int(nq)
+    c.reserved2 = 0
     c.cs2 = float(cs2)
     c.cfl = float(cfl)
     c.dt_fixed = float(dt_fixed)
@@ -83,7 +87,7 @@ def lib():
         "hydro_get_speeds": ([vp, P(d), P(d)], i32),
         "hydro_profile_step": ([vp, i32, d, P(d)], i32),
         "hydro_last_error": ([vp], ctypes.c_char_p),
-        "hydro_launch_variants": ([i32, i32], i32),
+        "hydro_launch_variants": ([i32, i32, i32], i32),
         "hydro_set_launch": ([vp, i32, i32], i32),
         "hydro_get_launch": ([vp, P(i32), P(i32), P(i32), P(i32)], i32),
         "hydro_autotune": ([vp, P(d)], i32),
@@ -158,11 +162,11 @@ class Hydro:
     """One grid of the FP64 WENO5/WENO7 + SSP-RK3 solver (hydro_t)."""
 
     def __init__(self, n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
-                 origin=(0.0, 0.0, 0.0), split=0, stream=None):
+                 origin=(0.0, 0.0, 0.0), split=0, nq=1, stream=None):
         self._L = lib()
-        self.cfg = make_config(n, dx, scheme, bc, cs2, cfl, dt_fixed, eps, origin, split)
+        self.cfg = make_config(n, dx, scheme, bc, cs2, cfl, dt_fixed, eps, origin, split, nq)
         self.n = tuple(int(k) for k in n)
-        self.shape = (5, self.n[2], self.n[1], self.n[0])
+        self.shape = (4 + max(1, int(nq)), self.n[2], self.n[1], self.n[0])
         h = ctypes.c_void_p()
         rc = self._L.hydro_create(ctypes.byref(self.cfg), _stream_handle(stream), ctypes.byref(h))
         if rc:
@@ -175,7 +179,8 @@ class Hydro:
     def from_grid(cls, g, stream=None):
         """Create from a workloads.Grid description."""
         return cls(g.n, g.dx, scheme=g.scheme, bc=g.bc, cs2=g.cs2, cfl=g.cfl, eps=g.eps, origin=g.origin,
-                   dt_fixed=getattr(g, "dt_fixed", 0.0), split=getattr(g, "split", 0), stream=stream)
+                   dt_fixed=getattr(g, "dt_fixed", 0.0), split=getattr(g, "split", 0), nq=getattr(g, "nq", 1),
+                   stream=stream)
 
     def _check(self, rc):
         if rc:
@@ -309,7 +314,7 @@ class HydroBatch:
         arr = (HydroConfig * len(self.grids))()
         for i, g in enumerate(self.grids):
             arr[i] = make_config(g.n, g.dx, g.scheme, g.bc, g.cs2, g.cfl, getattr(g, "dt_fixed", 0.0), g.eps,
-                                 g.origin, getattr(g, "split", 0))
+                                 g.origin, getattr(g, "split", 0), getattr(g, "nq", 1))
         h = ctypes.c_void_p()
         rc = self._L.hydro_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.grids), _stream_handle(stream),
                                         ctypes.byref(h))

@@ -31,6 +31,7 @@ struct hydro_s {
     StageLaunch L{};
     int variant = 0;
     int zc = 0;
+    int nf = 5;                      // state fields: E, M, and nq >= 1 charges
     bool have_state = false;
     AdjointWork* adj = nullptr;      // reverse-mode workspace (hydro_adjoint.cu)
     std::string err;
@@ -176,18 +177,21 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
     if ((e = cudaGetDevice(&h->dev)) != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
     if ((e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev)) != cudaSuccess)
         return bail(cuda_fail(h, e, "device attribute"));
-    if ((e = stage_launch_variant(h->R, cfg->split, 0, &h->L)) != cudaSuccess)
+    h->nf = state_fields(*cfg);
+    if ((e = stage_launch_variant(h->R, cfg->split, cfg->nq, 0, &h->L)) != cudaSuccess)
         return bail(cuda_fail(h, e, "stage kernel setup"));
     h->ncell = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
     h->fs = (h->ncell + 31) / 32 * 32;   // 256-byte aligned fields
     h->zc = pick_zc(cfg->n[0], cfg->n[1], cfg->n[2], h->L, h->sms);
-    const int nfields = cfg->split ? 36 : 27;
+    // U0..U2 (nf fields each), W0..W2 (4 each), speeds S0..S2 (3 each, local LF)
+    const int nf = h->nf;
+    const int nfields = 3 * nf + 12 + (cfg->split ? 9 : 0);
     const size_t bytes = sizeof(double) * (size_t)h->fs * nfields;
     if ((e = cudaMalloc(&h->buf, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "state buffers"));
     for (int i = 0; i < 3; ++i) {
-        h->U[i] = h->buf + (size_t)h->fs * 5 * i;
-        h->W[i] = h->buf + (size_t)h->fs * (15 + 4 * i);
-        if (cfg->split) h->S[i] = h->buf + (size_t)h->fs * (27 + 3 * i);
+        h->U[i] = h->buf + (size_t)h->fs * nf * i;
+        h->W[i] = h->buf + (size_t)h->fs * (3 * nf + 4 * i);
+        if (cfg->split) h->S[i] = h->buf + (size_t)h->fs * (3 * nf + 12 + 3 * i);
     }
     if ((e = cudaMemsetAsync(h->buf, 0, bytes, h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
     if ((e = cudaMalloc(&h->ctl, sizeof(Ctl))) != cudaSuccess) return bail(cuda_fail(h, e, "control block"));
@@ -255,7 +259,7 @@ hydro_status hydro_set_state(hydro_t* h, const double* u, int64_t field_stride, 
 {
     hydro_status s = check_io(h, u, field_stride, mem);
     if (s) return s;
-    s = copy_fields(h, h->U[0], h->fs, u, field_stride, 5,
+    s = copy_fields(h, h->U[0], h->fs, u, field_stride, h->nf,
                     mem == HYDRO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
     if (s) return s;
     return after_load(h, t);
@@ -268,13 +272,14 @@ hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stri
     const double* src = w;
     long long ss = field_stride;
     if (mem == HYDRO_MEM_HOST) {   // stage through U1 (scratch between steps)
-        s = copy_fields(h, h->U[1], h->fs, w, field_stride, 5, cudaMemcpyHostToDevice);
+        s = copy_fields(h, h->U[1], h->fs, w, field_stride, h->nf, cudaMemcpyHostToDevice);
         if (s) return s;
         src = h->U[1];
         ss = h->fs;
     }
     reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
-    prim2con_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(src, ss, h->U[0], h->fs, h->ncell, h->cfg.cs2, h->ctl);
+    prim2con_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(src, ss, h->U[0], h->fs, h->ncell, h->cfg.cs2, h->ctl,
+                                                                  h->nf);
     CK(h, cudaGetLastError(), "prim2con");
     prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl,
                                                                  h->S[0]);
@@ -338,7 +343,7 @@ __global__ void set_dt_kernel(Ctl* c, double dt) { c->dt = dt; }
 static hydro_status apply_launch(hydro_t* h, int variant, int zc)
 {
     StageLaunch L{};
-    cudaError_t e = stage_launch_variant(h->R, h->cfg.split, variant, &L);
+    cudaError_t e = stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, variant, &L);
     if (e == cudaErrorInvalidValue) return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     CK(h, e, "stage kernel setup");
     CK(h, cudaStreamSynchronize(h->stream), "synchronize");
@@ -394,17 +399,19 @@ static void tune_cache_store(const hydro_t* h, int variant, int zc)
     fclose(f);
 }
 
-extern "C" int32_t hydro_launch_variants(int32_t scheme, int32_t split)
+extern "C" int32_t hydro_launch_variants(int32_t scheme, int32_t split, int32_t nq)
 {
     if (split != 0 && split != 1) return 0;
-    if (scheme == HYDRO_WENO5 || scheme == HYDRO_WENO7) return launch_variant_count(scheme == HYDRO_WENO5 ? 3 : 4, split);
+    if (nq < 0 || nq > 3) return 0;
+    if (scheme == HYDRO_WENO5 || scheme == HYDRO_WENO7)
+        return launch_variant_count(scheme == HYDRO_WENO5 ? 3 : 4, split, nq);
     return 0;
 }
 
 extern "C" hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc)
 {
     if (!h) return HYDRO_ERR_INVALID_ARG;
-    if (variant < 0 || variant >= hydro_launch_variants(h->cfg.scheme, h->cfg.split))
+    if (variant < 0 || variant >= hydro_launch_variants(h->cfg.scheme, h->cfg.split, h->cfg.nq))
         return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     return apply_launch(h, variant, zc);
 }
@@ -424,7 +431,7 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
     if (!h) return HYDRO_ERR_INVALID_ARG;
     if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
     int cv = 0, cz = 0;
-    if (tune_cache_lookup(h, &cv, &cz) && cv >= 0 && cv < hydro_launch_variants(h->cfg.scheme, h->cfg.split)) {
+    if (tune_cache_lookup(h, &cv, &cz) && cv >= 0 && cv < hydro_launch_variants(h->cfg.scheme, h->cfg.split, h->cfg.nq)) {
         if (best_ms) *best_ms = -1.0;
         return apply_launch(h, cv, cz);
     }
@@ -437,9 +444,9 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
     const int nz = h->cfg.n[2];
     // a positive dt makes the stage kernel run; it only writes stage-1 scratch
     set_dt_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 1e-300);
-    for (int v = 0; v < hydro_launch_variants(h->cfg.scheme, h->cfg.split) && st == HYDRO_OK; ++v) {
+    for (int v = 0; v < hydro_launch_variants(h->cfg.scheme, h->cfg.split, h->cfg.nq) && st == HYDRO_OK; ++v) {
         StageLaunch L{};
-        if (stage_launch_variant(h->R, h->cfg.split, v, &L) != cudaSuccess) continue;
+        if (stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, v, &L) != cudaSuccess) continue;
         // z chunks: balanced splits ceil(nz/k) and a fixed ladder; time the five
         // the wave-count model likes best
         std::vector<int> zs;
@@ -516,7 +523,7 @@ hydro_status hydro_get_state(hydro_t* h, double* u, int64_t field_stride, int32_
 {
     hydro_status s = check_io(h, u, field_stride, mem);
     if (s) return s;
-    s = copy_fields(h, u, field_stride, h->U[0], h->fs, 5,
+    s = copy_fields(h, u, field_stride, h->U[0], h->fs, h->nf,
                     mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
     if (s) return s;
     s = read_ctl(h);
@@ -530,9 +537,9 @@ hydro_status hydro_get_primitive(hydro_t* h, double* w, int64_t field_stride, in
     hydro_status s = check_io(h, w, field_stride, mem);
     if (s) return s;
     state_to_prim_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->fs, h->U[1], h->fs, h->ncell,
-                                                                      h->cfg.cs2);
+                                                                      h->cfg.cs2, h->nf);
     CK(h, cudaGetLastError(), "state_to_prim");
-    s = copy_fields(h, w, field_stride, h->U[1], h->fs, 5,
+    s = copy_fields(h, w, field_stride, h->U[1], h->fs, h->nf,
                     mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
     if (s) return s;
     return read_ctl(h);

@@ -335,6 +335,8 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
     for (int e = 0; e < n_events; ++e) {
         const std::string why = check_config(&cfgs[e]);
         if (!why.empty()) return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "event " + std::to_string(e) + ": " + why);
+        if (cfgs[e].nq > 1)
+            return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path supports one charge (nq <= 1)");
         if (cfgs[e].scheme != cfgs[0].scheme || cfgs[e].split != cfgs[0].split)
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "all events of a batch must use the same scheme and splitting");
     }
@@ -448,7 +450,7 @@ hydro_status hydro_batch_set_primitive(hydro_batch_t* b, int32_t e, const double
         ss = E.fs;
     }
     reset_ctl_kernel<<<1, 1, 0, b->stream>>>(E.ctl, t);
-    prim2con_kernel<<<bblocks(E.ncell), 256, 0, b->stream>>>(src, ss, E.U[0], E.fs, E.ncell, E.cs2, E.ctl);
+    prim2con_kernel<<<bblocks(E.ncell), 256, 0, b->stream>>>(src, ss, E.U[0], E.fs, E.ncell, E.cs2, E.ctl, 5);
     prepare_kernel<<<bblocks(E.ncell), 256, 0, b->stream>>>(E.U[0], E.W[0], E.fs, E.ncell, E.cs2, E.ctl, E.S[0]);
     BCK(b, cudaGetLastError(), "prim2con");
     b->loaded[e] = 1;
@@ -538,7 +540,7 @@ int32_t hydro_batch_size(hydro_batch_t* b) { return b ? b->n_events : 0; }
 hydro_status hydro_batch_set_launch(hydro_batch_t* b, int32_t variant, int32_t zc)
 {
     if (!b) return HYDRO_ERR_INVALID_ARG;
-    if (variant < 0 || variant >= hydro_launch_variants(b->cfg[0].scheme, b->cfg[0].split))
+    if (variant < 0 || variant >= hydro_launch_variants(b->cfg[0].scheme, b->cfg[0].split, 1))
         return bfail(b, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     return apply_batch_launch(b, variant, zc);
 }
@@ -570,7 +572,7 @@ hydro_status hydro_batch_autotune(hydro_batch_t* b, double* best_ms)
     BCK(b, cudaEventCreate(&e0), "event");
     BCK(b, cudaEventCreate(&e1), "event");
     const int eb = (b->n_events + 127) / 128;
-    for (int v = 0; v < hydro_launch_variants(b->cfg[0].scheme, b->cfg[0].split) && s == HYDRO_OK; ++v)
+    for (int v = 0; v < hydro_launch_variants(b->cfg[0].scheme, b->cfg[0].split, 1) && s == HYDRO_OK; ++v)
         for (int zc : zcs) {
             s = apply_batch_launch(b, v, zc);
             if (s) break;

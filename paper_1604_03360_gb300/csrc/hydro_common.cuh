@@ -47,10 +47,10 @@ __global__ void prepare_kernel(const double* u, double* w, long long fs, long lo
                                double* s = nullptr);
 // primitives (e, v, n) -> conserved
 __global__ void prim2con_kernel(const double* wp, long long ws, double* u, long long fs, long long n, double cs2,
-                                Ctl* c);
+                                Ctl* c, int nf);
 // conserved -> (e, v, n)
 __global__ void state_to_prim_kernel(const double* u, long long fs, double* out, long long os, long long n,
-                                     double cs2);
+                                     double cs2, int nf);
 
 inline StepParams step_params(const hydro_config& cfg)
 {
@@ -82,9 +82,11 @@ struct StageLaunch {
 // Tile shapes compiled per scheme and splitting (index 0 is the default);
 // stage_launch_variant returns cudaErrorInvalidValue for a variant that does
 // not exist.  split: 0 global, 1 local Lax-Friedrichs.
-int launch_variant_count(int R, int split);
-cudaError_t stage_launch_variant(int R, int split, int v, StageLaunch* out);
-inline cudaError_t stage_launch_info(int R, StageLaunch* out) { return stage_launch_variant(R, 0, 0, out); }
+// nq: number of charges (state fields = 4 + nq).
+int launch_variant_count(int R, int split, int nq);
+cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out);
+inline cudaError_t stage_launch_info(int R, StageLaunch* out) { return stage_launch_variant(R, 0, 1, 0, out); }
+inline int state_fields(const hydro_config& c) { return 4 + (c.nq > 1 ? c.nq : 1); }
 
 inline int pick_zc(int nx, int ny, int nz, const StageLaunch& L, int sms)
 {

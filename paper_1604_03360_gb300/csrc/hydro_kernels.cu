@@ -81,7 +81,7 @@ __global__ void prepare_kernel(const double* u, double* w, long long fs, long lo
 }
 
 __global__ void prim2con_kernel(const double* wp, long long ws, double* u, long long fs, long long n, double cs2,
-                                Ctl* c)
+                                Ctl* c, int nf)
 {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const double e = wp[q], vx = wp[ws + q], vy = wp[2 * ws + q], vz = wp[3 * ws + q], nn = wp[4 * ws + q];
@@ -97,11 +97,12 @@ __global__ void prim2con_kernel(const double* wp, long long ws, double* u, long 
         u[2 * fs + q] = W * vy;
         u[3 * fs + q] = W * vz;
         u[4 * fs + q] = nn * sqrt(g2);
+        for (int k = 5; k < nf; ++k) u[k * fs + q] = wp[k * ws + q] * sqrt(g2);   // further charges
     }
 }
 
 __global__ void state_to_prim_kernel(const double* u, long long fs, double* out, long long os, long long n,
-                                     double cs2)
+                                     double cs2, int nf)
 {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         double pr, vx, vy, vz, e;
@@ -111,24 +112,24 @@ __global__ void state_to_prim_kernel(const double* u, long long fs, double* out,
             out[os + q] = vx;
             out[2 * os + q] = vy;
             out[3 * os + q] = vz;
-            out[4 * os + q] = u[4 * fs + q] * sqrt(1.0 - v2);
+            for (int k = 4; k < nf; ++k) out[k * os + q] = u[k * fs + q] * sqrt(1.0 - v2);
         } else {
-            for (int k = 0; k < 5; ++k) out[k * os + q] = __longlong_as_double(0x7ff8000000000000LL);
+            for (int k = 0; k < nf; ++k) out[k * os + q] = __longlong_as_double(0x7ff8000000000000LL);
         }
     }
 }
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5>
 static cudaError_t info_for(StageLaunch* out)
 {
-    out->fn = stage_kernel<R, TX, TY, ILP, LLF>;
-    out->smem = StageSmem<R, TX, TY, LLF>::bytes;
+    out->fn = stage_kernel<R, TX, TY, ILP, LLF, NF>;
+    out->smem = StageSmem<R, TX, TY, LLF, NF>::bytes;
     out->tx = TX;
     out->ty = TY;
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY, ILP, LLF>,
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY, ILP, LLF, NF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_kernel<R, TX, TY, ILP, LLF>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_kernel<R, TX, TY, ILP, LLF, NF>,
                                                          TX * TY, out->smem);
 }
 
@@ -138,14 +139,29 @@ static cudaError_t info_for(StageLaunch* out)
 //        face items per iteration.
 // Local LF (raw staging, 2G-plane ring): WENO5 16x16 and 16x8; WENO7 16x8
 // (16x16 would need 247 KB of shared memory).
-int launch_variant_count(int R, int split)
+// Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
+int launch_variant_count(int R, int split, int nq)
 {
+    if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 2 : 1;
     return R == 3 ? 4 : 3;
 }
 
-cudaError_t stage_launch_variant(int R, int split, int v, StageLaunch* out)
+template <int NF>
+static cudaError_t charges_variant(int R, int split, StageLaunch* out)
 {
+    if (R == 3) return split ? info_for<3, 16, 8, 1, true, NF>(out) : info_for<3, 16, 8, 1, false, NF>(out);
+    return split ? info_for<4, 16, 8, 1, true, NF>(out) : info_for<4, 16, 8, 1, false, NF>(out);
+}
+
+cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out)
+{
+    if (nq > 1) {
+        if (v != 0) return cudaErrorInvalidValue;
+        if (nq == 2) return charges_variant<6>(R, split, out);
+        if (nq == 3) return charges_variant<7>(R, split, out);
+        return cudaErrorInvalidValue;
+    }
     if (split == 1) {
         if (R == 3 && v == 0) return info_for<3, 16, 16, 1, true>(out);
         if (R == 3 && v == 1) return info_for<3, 16, 8, 1, true>(out);
@@ -184,6 +200,8 @@ std::string check_config(const hydro_config* c)
     if (!(c->weno_eps > 0.0)) return "weno_eps must be positive";
     if (!(c->dt_fixed > 0.0) && !(c->cfl > 0.0)) return "need cfl > 0 or dt_fixed > 0";
     if (c->split != 0 && c->split != 1) return "split must be 0 (global) or 1 (local Lax-Friedrichs)";
+    if (c->nq < 0 || c->nq > 3) return "nq (number of charges) must be 0..3";
+    if (c->reserved2 != 0) return "reserved2 must be 0";
     return std::string();
 }
 

@@ -67,48 +67,47 @@ __device__ __forceinline__ int bc_map(int i, int n, int bc)
     return i < 0 ? 0 : n - 1;
 }
 
-template <int R, int TX, int TY, bool LLF = false>
+template <int R, int TX, int TY, bool LLF = false, int NF = 5>
 struct StageSmem {
     static constexpr int G = R, S = 2 * R - 1, NT = TX * TY;
-    static constexpr int NV = LLF ? 11 : 10;                 // staged values per cell
+    static constexpr int NV = LLF ? 2 * NF + 1 : 2 * NF;     // staged values per cell
     static constexpr int NRING = LLF ? 2 * R : 2 * R - 1;    // z planes kept per column
     static constexpr int GXW = TX + 2 * G, GYH = TY + 2 * G;
     static constexpr int RING = NRING * NV * NT;
     static constexpr int GX = NV * TY * GXW;
     static constexpr int GY = NV * GYH * TX;
-    static constexpr int FX = 5 * TY * (TX + 1);
-    static constexpr int FY = 5 * (TY + 1) * TX;
+    static constexpr int FX = NF * TY * (TX + 1);
+    static constexpr int FY = NF * (TY + 1) * TX;
     static constexpr size_t bytes = sizeof(double) * (size_t)(RING + GX + GY + FX + FY);
 };
 
 // split fluxes g+- = f_d(u) +- alpha u (= 2 f^{+-}) of one cell along axis d
-__device__ __forceinline__ void split_flux(int d, const double u[5], const double w[4], double alpha,
-                                           double gp[5], double gm[5])
+// (fields E, M_x, M_y, M_z, then the NF - 4 charges, each with flux R v_d)
+template <int NF>
+__device__ __forceinline__ void split_flux(int d, const double* u, const double w[4], double alpha, double* gp,
+                                           double* gm)
 {
     const double p = w[0], vd = w[1 + d];
-    double f[5];
+    double f[NF];
     f[0] = u[1 + d];
-    f[1] = u[1] * vd;
-    f[2] = u[2] * vd;
-    f[3] = u[3] * vd;
-    f[4] = u[4] * vd;
+#pragma unroll
+    for (int k = 1; k < NF; ++k) f[k] = u[k] * vd;
     f[1 + d] += p;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < NF; ++k) {
         gp[k] = fma(alpha, u[k], f[k]);
         gm[k] = fma(-alpha, u[k], f[k]);
     }
 }
 
 // physical flux f_d(u) of one cell along axis d
-__device__ __forceinline__ void raw_flux(int d, const double u[5], const double w[4], double f[5])
+template <int NF>
+__device__ __forceinline__ void raw_flux(int d, const double* u, const double w[4], double* f)
 {
     const double vd = w[1 + d];
     f[0] = u[1 + d];
-    f[1] = u[1] * vd;
-    f[2] = u[2] * vd;
-    f[3] = u[3] * vd;
-    f[4] = u[4] * vd;
+#pragma unroll
+    for (int k = 1; k < NF; ++k) f[k] = u[k] * vd;
     f[1 + d] += w[0];
 }
 
@@ -145,10 +144,10 @@ __device__ __forceinline__ double llf_face(const double* f, const double* u, con
 
 // One work item: column tile (tile_x, tile_y) of TX x TY cells and z chunk chunk_z of the
 // grid described by a.  All threads of the CTA call it with the same item.
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
 {
-    using SM = StageSmem<R, TX, TY, LLF>;
+    using SM = StageSmem<R, TX, TY, LLF, NF>;
     constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING, NV = SM::NV;
     constexpr int GXW = SM::GXW, GYH = SM::GYH;
     double* ring = smem;
@@ -173,9 +172,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     const long long fs = a.fs, plane = (long long)nx * ny;
     const bool zact = a.act[2] != 0;
 
-    auto load = [&](long long q, double u[5], double w[4]) {
+    auto load = [&](long long q, double* u, double w[4]) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) u[k] = __ldg(a.u_in + k * fs + q);
+        for (int k = 0; k < NF; ++k) u[k] = __ldg(a.u_in + k * fs + q);
 #pragma unroll
         for (int k = 0; k < 4; ++k) w[k] = __ldg(a.w_in + k * fs + q);
     };
@@ -183,23 +182,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     // ring slot layout: global LF g+ (5), g- (5); local LF f (5), u (5), s_z
     auto ingest = [&](int m) {
         const long long q = (long long)bc_map(m, nz, a.bc[2]) * plane + (long long)ys * nx + xs;
-        double u[5], w[4], gp[5], gm[5];
+        double u[NF], w[4], gp[NF], gm[NF];
         load(q, u, w);
         double* r = ring + slot_of(m) * NV * NT + tid;
         if constexpr (LLF) {
-            raw_flux(2, u, w, gp);
+            raw_flux<NF>(2, u, w, gp);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
+            for (int k = 0; k < NF; ++k) {
                 r[k * NT] = gp[k];
-                r[(5 + k) * NT] = u[k];
+                r[(NF + k) * NT] = u[k];
             }
-            r[10 * NT] = __ldg(a.s_in + 2 * fs + q);
+            r[2 * NF * NT] = __ldg(a.s_in + 2 * fs + q);
         } else {
-            split_flux(2, u, w, al[2], gp, gm);
+            split_flux<NF>(2, u, w, al[2], gp, gm);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
+            for (int k = 0; k < NF; ++k) {
                 r[k * NT] = gp[k];
-                r[(5 + k) * NT] = gm[k];
+                r[(NF + k) * NT] = gm[k];
             }
         }
     };
@@ -210,8 +209,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         for (int i = 0; i < 2 * G; ++i) {
             const double* r = ring + slot_of(m - G + 1 + i) * NV * NT + tid;
             fv[i] = r[k * NT];
-            uv[i] = r[(5 + k) * NT];
-            sv[i] = r[10 * NT];
+            uv[i] = r[(NF + k) * NT];
+            sv[i] = r[2 * NF * NT];
         }
         return llf_face<R>(fv, uv, sv, 1, a.eps_s);
     };
@@ -223,7 +222,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         for (int i = 0; i < S; ++i) {
             const double* r = ring + slot_of(m - G + 1 + i) * NV * NT + tid;
             vp[i] = r[k * NT];
-            vm[i] = r[(5 + k) * NT];
+            vm[i] = r[(NF + k) * NT];
         }
         weno_left<R>(vp, a.eps_s, Np, Dp);
         weno_right<R>(vm, a.eps_s, Nm, Dm);
@@ -232,23 +231,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     // columns outside the grid (ragged tiles) have no z-faces to compute: their
     // ring is private and nobody reads it
     const bool zwork = zact && own;
-    double hNp[5], hDp[5], Fzm[5], Fzp[5];
+    double hNp[NF], hDp[NF], Fzm[NF], Fzp[NF];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) { hNp[k] = 0.0; hDp[k] = 1.0; Fzm[k] = 0.0; Fzp[k] = 0.0; }
+    for (int k = 0; k < NF; ++k) { hNp[k] = 0.0; hDp[k] = 1.0; Fzm[k] = 0.0; Fzp[k] = 0.0; }
     if (zwork && LLF) {
         for (int m = zb - G; m <= zb + G - 1; ++m) ingest(m);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) Fzm[k] = face_z_llf(zb - 1, k);
+        for (int k = 0; k < NF; ++k) Fzm[k] = face_z_llf(zb - 1, k);
     } else if (zwork) {
         for (int m = zb - G; m <= zb + G - 2; ++m) ingest(m);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < NF; ++k) {
             double Nm, Dm;
             recon_z(zb - 1, k, hNp[k], hDp[k], Nm, Dm);
         }
         ingest(zb + G - 1);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < NF; ++k) {
             double Np, Dp, Nm, Dm;
             recon_z(zb, k, Np, Dp, Nm, Dm);
             Fzm[k] = face_sum(hNp[k], hDp[k], Nm, Dm);
@@ -261,8 +260,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     // only the rows / columns of the tile inside the grid (plus halo) do work
     const int ncol = min(TX, nx - x0), nrow = min(TY, ny - y0);
     const int wx = ncol + 2 * G, hy = nrow + 2 * G;      // staged extents
-    const int nfx = a.act[0] ? 5 * nrow * (ncol + 1) : 0;
-    const int nfy = a.act[1] ? 5 * (nrow + 1) * ncol : 0;
+    const int nfx = a.act[0] ? NF * nrow * (ncol + 1) : 0;
+    const int nfy = a.act[1] ? NF * (nrow + 1) * ncol : 0;
     const int ngx = a.act[0] ? nrow * wx : 0;
     const int ngy = a.act[1] ? hy * ncol : 0;
 
@@ -271,11 +270,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         if (zwork && LLF) {
             ingest(p + G);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) Fzp[k] = face_z_llf(p, k);
+            for (int k = 0; k < NF; ++k) Fzp[k] = face_z_llf(p, k);
         } else if (zwork) {
             ingest(p + G);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
+            for (int k = 0; k < NF; ++k) {
                 double Np, Dp, Nm, Dm;
                 recon_z(p + 1, k, Np, Dp, Nm, Dm);
                 Fzp[k] = face_sum(hNp[k], hDp[k], Nm, Dm);
@@ -286,26 +285,26 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         // 2. split x- and y-fluxes of plane p (tile + halo) into shared memory
         const long long qz = (long long)bc_map(p, nz, a.bc[2]) * plane;
         for (int it = tid; it < ngx + ngy; it += NT) {
-            double u[5], w[4], gp[5], gm[5];
+            double u[NF], w[4], gp[NF], gm[NF];
             if (it < ngx) {
                 const int row = it / wx, col = it % wx;
                 const int xx = bc_map(x0 - G + col, nx, a.bc[0]), yy = bc_map(y0 + row, ny, a.bc[1]);
                 const long long q = qz + (long long)yy * nx + xx;
                 load(q, u, w);
                 if constexpr (LLF) {
-                    raw_flux(0, u, w, gp);
+                    raw_flux<NF>(0, u, w, gp);
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
+                    for (int k = 0; k < NF; ++k) {
                         gx[(k * TY + row) * GXW + col] = gp[k];
-                        gx[((5 + k) * TY + row) * GXW + col] = u[k];
+                        gx[((NF + k) * TY + row) * GXW + col] = u[k];
                     }
-                    gx[(10 * TY + row) * GXW + col] = __ldg(a.s_in + q);
+                    gx[(2 * NF * TY + row) * GXW + col] = __ldg(a.s_in + q);
                 } else {
-                    split_flux(0, u, w, al[0], gp, gm);
+                    split_flux<NF>(0, u, w, al[0], gp, gm);
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
+                    for (int k = 0; k < NF; ++k) {
                         gx[(k * TY + row) * GXW + col] = gp[k];
-                        gx[((5 + k) * TY + row) * GXW + col] = gm[k];
+                        gx[((NF + k) * TY + row) * GXW + col] = gm[k];
                     }
                 }
             } else {
@@ -314,19 +313,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 const long long q = qz + (long long)yy * nx + xx;
                 load(q, u, w);
                 if constexpr (LLF) {
-                    raw_flux(1, u, w, gp);
+                    raw_flux<NF>(1, u, w, gp);
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
+                    for (int k = 0; k < NF; ++k) {
                         gy[(k * GYH + row) * TX + col] = gp[k];
-                        gy[((5 + k) * GYH + row) * TX + col] = u[k];
+                        gy[((NF + k) * GYH + row) * TX + col] = u[k];
                     }
-                    gy[(10 * GYH + row) * TX + col] = __ldg(a.s_in + fs + q);
+                    gy[(2 * NF * GYH + row) * TX + col] = __ldg(a.s_in + fs + q);
                 } else {
-                    split_flux(1, u, w, al[1], gp, gm);
+                    split_flux<NF>(1, u, w, al[1], gp, gm);
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
+                    for (int k = 0; k < NF; ++k) {
                         gy[(k * GYH + row) * TX + col] = gp[k];
-                        gy[((5 + k) * GYH + row) * TX + col] = gm[k];
+                        gy[((NF + k) * GYH + row) * TX + col] = gm[k];
                     }
                 }
             }
@@ -340,7 +339,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 const int k = it / (nrow * (ncol + 1)), rr = it % (nrow * (ncol + 1));
                 const int row = rr / (ncol + 1), f = rr % (ncol + 1);   // face f - 1/2 of the tile
                 pp = gx + (k * TY + row) * GXW + f;
-                pm = gx + ((5 + k) * TY + row) * GXW + f + 1;
+                pm = gx + ((NF + k) * TY + row) * GXW + f + 1;
                 st = 1;
                 out = Fx + (k * TY + row) * (TX + 1) + f;
             } else {
@@ -348,7 +347,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 const int k = j / ((nrow + 1) * ncol), rr = j % ((nrow + 1) * ncol);
                 const int f = rr / ncol, col = rr % ncol;             // face f - 1/2 along y
                 pp = gy + (k * GYH + f) * TX + col;
-                pm = gy + ((5 + k) * GYH + f + 1) * TX + col;
+                pm = gy + ((NF + k) * GYH + f + 1) * TX + col;
                 st = TX;
                 out = Fy + (k * (TY + 1) + f) * TX + col;
             }
@@ -366,7 +365,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 // field blocks further in the same staged array
                 const int fb = (it < nfx) ? TY * GXW : GYH * TX;      // one field block
                 const int k = (it < nfx) ? it / (nrow * (ncol + 1)) : (it - nfx) / ((nrow + 1) * ncol);
-                *out = llf_face<R>(pp, pp + 5 * fb, pp + (10 - k) * fb, st, a.eps_s);
+                *out = llf_face<R>(pp, pp + NF * fb, pp + (2 * NF - k) * fb, st, a.eps_s);
             }
         } else
         for (int it0 = tid; it0 < nitems; it0 += ILP * NT) {
@@ -406,9 +405,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         // 4. combine, RK update, primitives and speeds of the new state
         if (own) {
             const long long q = (long long)p * plane + (long long)y * nx + x;
-            double un[5];
+            double un[NF];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
+            for (int k = 0; k < NF; ++k) {
                 double L = 0.0;
                 if (a.act[0]) L = a.hdx[0] * (Fx[(k * TY + ty) * (TX + 1) + tx] - Fx[(k * TY + ty) * (TX + 1) + tx + 1]);
                 if (a.act[1]) L = fma(a.hdx[1], Fy[(k * (TY + 1) + ty) * TX + tx] - Fy[(k * (TY + 1) + ty + 1) * TX + tx], L);
@@ -440,7 +439,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             }
         }
 #pragma unroll
-        for (int k = 0; k < 5; ++k) Fzm[k] = Fzp[k];
+        for (int k = 0; k < NF; ++k) Fzm[k] = Fzp[k];
     }
     // speeds: warp max, one atomic per warp and axis
 #pragma unroll
@@ -455,11 +454,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 }
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
-__global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) stage_kernel(const StageArgs a)
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5>
+__global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 && NF == 5 ? 2 : 1)) stage_kernel(const StageArgs a)
 {
     extern __shared__ __align__(16) double smem[];
-    stage_tile<R, TX, TY, ILP, LLF>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    stage_tile<R, TX, TY, ILP, LLF, NF>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 }  // namespace hydro

@@ -271,3 +271,49 @@ def test_local_lf_rejected_where_unsupported():
         with pytest.raises(HydroError) as ei:
             h.forward_record(2, 1)
         assert ei.value.code == 1 and "global Lax-Friedrichs" in str(ei.value)
+
+
+# ---------------------------------------------------------------- several charges
+@pytest.mark.parametrize("scheme,split,nq", [(5, 0, 2), (7, 0, 3), (5, 1, 3), (7, 1, 2)])
+def test_several_charges_match_oracle(scheme, split, nq):
+    g, w = W.lumpy(n=(37, 29, 21), seed=90 + nq, scheme=scheme)
+    w = with_flow(g, w)
+    g.split, g.nq = split, nq
+    assert_parity(g, W.with_charges(g, w, nq), 6)
+
+
+def test_extra_charges_evolve_like_the_single_charge():
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=(30, 26, 22), seed=61, scheme=5)
+    w = with_flow(g, w)
+    w3 = W.with_charges(g, w, 3)
+    g.nq = 3
+    with Hydro.from_grid(g) as h:
+        h.set_primitive(w3)
+        h.step(5)
+        u3 = h.get_state()
+        p3 = h.get_primitive()
+    assert u3.shape[0] == 7
+    g.nq = 1
+    for j in (4, 5, 6):
+        wj = w3[:5].copy()
+        wj[4] = w3[j]
+        with Hydro.from_grid(g) as h:
+            h.set_primitive(wj)
+            h.step(5)
+            u1 = h.get_state()
+        assert np.abs(u1[4] - u3[j]).max() <= 1e-14 * np.abs(u1[4]).max()
+        assert np.all(field_errors(u3[:4], u1[:4]) <= 1e-14)
+    np.testing.assert_allclose(p3, oracle.con2prim(u3), rtol=1e-12, atol=1e-14)
+
+
+def test_several_charges_rejected_where_unsupported():
+    from paper_1604_03360_gb300 import Hydro, HydroBatch, HydroError
+    g, w = W.lumpy(n=(12, 11, 10), seed=2)
+    g.nq = 2
+    with pytest.raises(HydroError):
+        HydroBatch([g, g])
+    with Hydro.from_grid(g) as h:
+        h.set_primitive(W.with_charges(g, w, 2))
+        with pytest.raises(HydroError):
+            h.forward_record(2, 1)

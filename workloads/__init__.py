@@ -34,6 +34,7 @@ class Grid:
     cfl: float = 0.3
     dt_fixed: float = 0.0       # > 0: constant time step instead of the CFL rule
     split: int = 0              # 0 global, 1 local Lax-Friedrichs splitting
+    nq: int = 1                 # conserved charge densities (state fields 4 + nq)
     cs2: float = CS2
     eps: float = 1e-6
     t0: float = 0.0

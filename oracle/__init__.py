@@ -48,6 +48,8 @@ class Cfg(ctypes.Structure):
         ("bc", ctypes.c_int32 * 3),
         ("split", ctypes.c_int32),
         ("nq", ctypes.c_int32),
+        ("limiter", ctypes.c_int32),
+        ("musta_k", ctypes.c_int32),
         ("pad2_", ctypes.c_int32),
         ("dx", ctypes.c_double * 3),
         ("cs2", ctypes.c_double),
@@ -79,6 +81,8 @@ def lib():
         L.oc_con2prim_n.argtypes = [d, ctypes.c_int, vp, ctypes.c_int64, vp]
         L.oc_prim2con_n.argtypes = [d, ctypes.c_int, vp, ctypes.c_int64, vp]
         L.oc_set_threads.argtypes = [ctypes.c_int]
+        L.oc_limiter.argtypes = [ctypes.c_int, d, d]
+        L.oc_limiter.restype = d
         L.oc_get_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -102,23 +106,32 @@ def max_threads():
     return lib().oc_get_max_threads()
 
 
-def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0, eps=1e-6, split=0, nq=1):
-    """n = (nx, ny, nz); scheme 5 (WENO5) or 7 (WENO7); bc 0 outflow / 1 periodic;
-    split 0 global / 1 local Lax-Friedrichs; nq conserved charges (state has
-    4 + nq fields)."""
+def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0, eps=1e-6, split=0, nq=1,
+             limiter=0, musta_k=2):
+    """n = (nx, ny, nz); scheme 5 (WENO5), 7 (WENO7) or 2 (MUSTA-FORCE + MUSCL);
+    bc 0 outflow / 1 periodic; split 0 global / 1 local Lax-Friedrichs; nq
+    conserved charges (state has 4 + nq fields); limiter 0 minmod, 1 MC,
+    2 van Leer, 3 superbee; musta_k MUSTA stages."""
     c = Cfg()
     for i in range(3):
         c.n[i] = int(n[i])
         c.dx[i] = float(dx[i])
         c.bc[i] = int(bc[i])
-    c.r = {5: 3, 7: 4}[int(scheme)]
+    c.r = {5: 3, 7: 4, 2: 1}[int(scheme)]
     c.cs2 = float(cs2)
     c.cfl = float(cfl)
     c.dt_fixed = float(dt_fixed)
     c.eps = float(eps)
     c.split = int(split)
     c.nq = int(nq)
+    c.limiter = int(limiter)
+    c.musta_k = int(musta_k)
     return c
+
+
+def limiter(kind, a, b):
+    """MUSCL slope limiter of the oracle (0 minmod, 1 MC, 2 van Leer, 3 superbee)."""
+    return lib().oc_limiter(int(kind), float(a), float(b))
 
 
 def _shape(c):

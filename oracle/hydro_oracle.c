@@ -34,6 +34,16 @@
  * Several conserved charges (nq > 1): the state is (E, M, R_1..R_nq); every
  * charge is a passive density advected like R (flux R_k v_d, n_k = R_k / gamma),
  * since p = cs2 e does not depend on them.
+ * MUSTA-FORCE + MUSCL (r = 1, Sec. 1.1, second order): the state is
+ * reconstructed linearly in each cell, component-wise on the conserved
+ * variables, with the slope limited by `limiter` (u_L = u_j + s_j/2,
+ * u_R = u_{j+1} - s_{j+1}/2; an unphysical reconstructed state falls back to
+ * the cell average).  The face flux is MUSTA: musta_k stages of the centred
+ * FORCE flux F = (F_LF + F_LW)/2 on the local states, with the local ratio
+ * dt/dx = 0.9 / S, S = max |lambda| over the two local states; between
+ * stages the local states are advanced as a predictor (u_L -= r (F - f_L),
+ * u_R -= r (f_R - F)).  If the Lax-Wendroff state is unphysical the stage
+ * flux is F_LF; if a predicted state is unphysical the iteration stops.
  * Local Lax-Friedrichs variant (split = 1): the face j+1/2 along d uses
  * alpha = max over the 2r cells j-r+1 .. j+r (the union of both biased
  * stencils) of max(|lambda_-|, |lambda_+|) along d; the time step still uses
@@ -59,6 +69,8 @@ typedef struct {
     int32_t bc[3];     /* 0: outflow (copy edge cell), 1: periodic */
     int32_t split;     /* 0: global Lax-Friedrichs, 1: local Lax-Friedrichs */
     int32_t nq;        /* conserved charge densities R_1..R_nq (0 or 1: one) */
+    int32_t limiter;   /* MUSCL slope limiter: 0 minmod, 1 MC, 2 van Leer, 3 superbee */
+    int32_t musta_k;   /* MUSTA stages (>= 1; 1 is plain FORCE) */
     int32_t pad_;
     double dx[3];      /* cell sizes |e_i| */
     double cs2;        /* EOS p = cs2 * e */
@@ -69,6 +81,7 @@ typedef struct {
 
 enum { OC_OK = 0, OC_ERR_ARG = 1, OC_ERR_UNPHYSICAL = 4, OC_ERR_OOM = 3 };
 #define MAXF 8   /* E, M_x, M_y, M_z and up to four charges */
+#define NFMAX_M 8
 static int nfields(const void *cfg);
 
 /* ------------------------------------------------------------------------ */
@@ -287,12 +300,13 @@ static int cfg_ok(const oc_cfg *c)
     if (!c) return 0;
     for (int d = 0; d < 3; ++d)
         if (c->n[d] < 1 || !(c->dx[d] > 0) || (c->bc[d] != 0 && c->bc[d] != 1)) return 0;
-    if (c->r != 3 && c->r != 4) return 0;
+    if (c->r != 1 && c->r != 3 && c->r != 4) return 0;
+    if (c->r == 1 && (c->limiter < 0 || c->limiter > 3 || c->musta_k < 1 || c->split != 0 || c->nq > 1)) return 0;
     if (c->split != 0 && c->split != 1) return 0;
     if (c->nq < 0 || c->nq > MAXF - 4) return 0;
     if (!(c->cs2 > 0 && c->cs2 < 1) || !(c->eps > 0)) return 0;
     for (int d = 0; d < 3; ++d)
-        if (active(c, d) && c->bc[d] == 1 && c->n[d] < c->r) return 0;
+        if (active(c, d) && c->bc[d] == 1 && c->n[d] < (c->r == 1 ? 2 : c->r)) return 0;
     return 1;
 }
 
@@ -325,6 +339,79 @@ int oc_alpha(const oc_cfg *c, const double *u, double *alpha)
 }
 
 /* ------------------------------------------------------------------------ */
+/* MUSCL + MUSTA-FORCE (Sec. 1.1)                                            */
+/* ------------------------------------------------------------------------ */
+static double minmod2(double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+/* limited slope from the backward and forward differences a, b */
+double oc_limiter(int kind, double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    switch (kind) {
+    case 0: /* minmod */
+        return minmod2(a, b);
+    case 1: /* monotonized central: minmod(2a, (a+b)/2, 2b) */
+        return minmod2(minmod2(2.0 * a, 0.5 * (a + b)), 2.0 * b);
+    case 2: /* van Leer: harmonic mean */
+        return 2.0 * a * b / (a + b);
+    default: { /* superbee: maxmod(minmod(2a, b), minmod(a, 2b)) */
+        const double s1 = minmod2(2.0 * a, b), s2 = minmod2(a, 2.0 * b);
+        return fabs(s1) > fabs(s2) ? s1 : s2;
+    }
+    }
+}
+
+static double max_speed(const oc_cfg *c, int d, const double *w)
+{
+    double lam[2];
+    oc_eigen(c->cs2, d, w, lam);
+    return fmax(fabs(lam[0]), fabs(lam[1]));
+}
+
+/* MUSTA-FORCE flux along d between local states uL, uR (5 values each).
+ * Returns nonzero if the initial local states are unphysical. */
+static int musta_force(const oc_cfg *c, int d, const double *uL0, const double *uR0, double *F)
+{
+    double uL[NFMAX_M], uR[NFMAX_M], wL[NFMAX_M], wR[NFMAX_M], fL[NFMAX_M], fR[NFMAX_M];
+    memcpy(uL, uL0, sizeof(double) * 5);
+    memcpy(uR, uR0, sizeof(double) * 5);
+    if (oc_con2prim(c->cs2, uL, wL) || oc_con2prim(c->cs2, uR, wR)) return 1;
+    for (int l = 1; l <= c->musta_k; ++l) {
+        oc_flux_n(c->cs2, d, 5, uL, wL, fL);
+        oc_flux_n(c->cs2, d, 5, uR, wR, fR);
+        const double S = fmax(max_speed(c, d, wL), max_speed(c, d, wR));
+        const double r = 0.9 / S;               /* local dt / dx */
+        double uLW[NFMAX_M], wLW[NFMAX_M], fLW[NFMAX_M], Flf[NFMAX_M];
+        for (int k = 0; k < 5; ++k) {
+            Flf[k] = 0.5 * (fL[k] + fR[k]) - 0.5 / r * (uR[k] - uL[k]);
+            uLW[k] = 0.5 * (uL[k] + uR[k]) - 0.5 * r * (fR[k] - fL[k]);
+        }
+        if (oc_con2prim(c->cs2, uLW, wLW)) {
+            for (int k = 0; k < 5; ++k) F[k] = Flf[k];
+        } else {
+            oc_flux_n(c->cs2, d, 5, uLW, wLW, fLW);
+            for (int k = 0; k < 5; ++k) F[k] = 0.5 * (Flf[k] + fLW[k]);
+        }
+        if (l == c->musta_k) break;
+        double nL[NFMAX_M], nR[NFMAX_M], vL[NFMAX_M], vR[NFMAX_M];
+        for (int k = 0; k < 5; ++k) {
+            nL[k] = uL[k] - r * (F[k] - fL[k]);
+            nR[k] = uR[k] - r * (fR[k] - F[k]);
+        }
+        if (oc_con2prim(c->cs2, nL, vL) || oc_con2prim(c->cs2, nR, vR)) break;
+        memcpy(uL, nL, sizeof uL);
+        memcpy(uR, nR, sizeof uR);
+        memcpy(wL, vL, sizeof wL);
+        memcpy(wR, vR, sizeof wR);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The semi-discrete operator L(u) of Eq. 2                                 */
 /* ------------------------------------------------------------------------ */
 /* L = sum_d (F_d(j - 1/2) - F_d(j + 1/2)) / dx_d with
@@ -333,7 +420,7 @@ int oc_alpha(const oc_cfg *c, const double *u, double *alpha)
 int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
 {
     if (!cfg_ok(c)) return OC_ERR_ARG;
-    const int r = c->r, G = r;
+    const int r = c->r, G = (r == 1 ? 2 : r);
     const int NF = nfields(c);
     const int64_t N = (int64_t)c->n[0] * c->n[1] * c->n[2];
     int bad = 0;
@@ -387,6 +474,27 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
             /* face fluxes: F[s] sits at face s - 1/2, s = 0..nd */
             for (int s = 0; s <= nd; ++s) {
                 const int j = s - 1 + G; /* padded index of the cell left of the face */
+                if (r == 1) {
+                    /* MUSCL states at the face from cells j-1 .. j+2, then MUSTA-FORCE */
+                    double uL[NFMAX_M], uR[NFMAX_M], u0[NFMAX_M], u1[NFMAX_M], wtmp[NFMAX_M], Ff[NFMAX_M];
+                    for (int k = 0; k < 5; ++k) {
+                        const double *v = ur + k * len;
+                        const double sl = oc_limiter(c->limiter, v[j] - v[j - 1], v[j + 1] - v[j]);
+                        const double sr = oc_limiter(c->limiter, v[j + 1] - v[j], v[j + 2] - v[j + 1]);
+                        u0[k] = v[j];
+                        u1[k] = v[j + 1];
+                        uL[k] = v[j] + 0.5 * sl;
+                        uR[k] = v[j + 1] - 0.5 * sr;
+                    }
+                    if (oc_con2prim(c->cs2, uL, wtmp)) memcpy(uL, u0, sizeof uL);
+                    if (oc_con2prim(c->cs2, uR, wtmp)) memcpy(uR, u1, sizeof uR);
+                    if (musta_force(c, d, uL, uR, Ff)) {
+                        bad |= 1;
+                        for (int k = 0; k < 5; ++k) Ff[k] = 0.0;
+                    }
+                    for (int k = 0; k < NF; ++k) F[k * (nd + 1) + s] = Ff[k];
+                    continue;
+                }
                 if (c->split == 1) {
                     /* local LF: split again with this face's own alpha */
                     double af = 0.0;

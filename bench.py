@@ -262,6 +262,49 @@ def batched_vs_looped(dev, stream, barrier, steps, warmup, events=256):
     return out
 
 
+def musta_force_256(dev, stream, barrier, grid, with_cpu):
+    """The paper's second scheme (Sec. 1.1): MUSCL (minmod) + 2-stage
+    MUSTA-FORCE on the same ellipsoidal workload; and, for the paper's only
+    published comparison (the GPU program ~200x faster than a single-threaded
+    CPU program for MUSTA-FORCE, Sec. 2), the oracle's MUSTA-FORCE on ONE host
+    thread over a bounded 48^3 central block."""
+    import torch
+    from paper_1604_03360_gb300 import Hydro
+    g, w = workload(5, grid)
+    g.scheme, g.limiter, g.musta_stages = 2, 0, 2
+    h = Hydro.from_grid(g, stream=stream)
+    h.set_primitive(torch.from_numpy(w).to(dev))
+    h.autotune()
+    h.step(3)
+    barrier()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    km = h.profile_step(3)
+    a1.record(stream)
+    barrier()
+    h.sync()
+    el = a0.elapsed_time(a1) / 1e3
+    out = {"value": g.cells * 3 / el, "unit": "cell-updates/s", "steps": 3, "limiter": "minmod",
+           "musta_stages": 2, "ms_per_step": 1e3 * el / 3, "launch": h.launch(),
+           "stage_kernel_ms": float(km[1:4].sum()) / 9}
+    h.close()
+    if with_cpu:
+        import oracle
+        oracle.build()
+        gs, ws = cpu_sample(5, grid, 48)
+        c = oracle.make_cfg(gs.n, gs.dx, scheme=2, cfl=gs.cfl, limiter=0, musta_k=2)
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.run(c, oracle.prim2con(ws), 1)
+        dt1 = time.perf_counter() - t0
+        oracle.set_threads(0)
+        v1 = gs.cells / dt1
+        out["single_thread_oracle"] = {"value": v1, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                                       "sample": "1 RK3 step of the central 48^3 block (%.1f s)" % dt1}
+        out["gpu_over_single_thread_cpu"] = out["value"] / v1
+    return out
+
+
 def adjoint_96(dev, stream, barrier):
     """Adjoint configuration: 96^3 lumpy event (seed 1604), WENO5, 50 RK3 steps
     with a checkpoint every 10; gradient of eps_2 with respect to the initial
@@ -460,6 +503,8 @@ def main():
                                  "ms_per_step": 1e3 * elq / 3, "launch": hq.launch(),
                                  "stage_kernel_ms": float(kq[1:4].sum()) / 9}
         hq.close()
+    if not args.no_extra:
+        extra["musta_force_256"] = musta_force_256(dev, stream, barrier, args.grid, rank == 0 and not args.no_cpu_baseline)
     if not args.no_extra and not args.no_batch:
         extra["batched_vs_looped"] = batched_vs_looped(dev, stream, barrier, 3, 3, args.batch_events)
     if not args.no_extra:

@@ -57,7 +57,11 @@ typedef enum {
     HYDRO_ERR_STATE = 6
 } hydro_status;
 
-typedef enum { HYDRO_WENO5 = 5, HYDRO_WENO7 = 7 } hydro_scheme;
+/* WENO5 / WENO7: finite-difference WENO of Sec. 1.2 (the hot path).
+ * MUSTA_FORCE: the second-order scheme of Sec. 1.1 -- MUSCL linear
+ * reconstruction with a slope limiter and the multi-stage (MUSTA) centred
+ * FORCE flux; see hydro_config.limiter / musta_stages. */
+typedef enum { HYDRO_MUSTA_FORCE = 2, HYDRO_WENO5 = 5, HYDRO_WENO7 = 7 } hydro_scheme;
 typedef enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1 } hydro_bc;
 typedef enum { HYDRO_MEM_HOST = 0, HYDRO_MEM_DEVICE = 1 } hydro_mem;
 
@@ -66,7 +70,7 @@ typedef struct {
     int32_t n[3];       /* interior cells nx, ny, nz (>= 1; a direction with
                            n = 1 is inactive; a periodic active direction
                            needs n >= 4 for WENO7, >= 3 for WENO5) */
-    int32_t scheme;     /* HYDRO_WENO5 or HYDRO_WENO7 */
+    int32_t scheme;     /* HYDRO_WENO5, HYDRO_WENO7 or HYDRO_MUSTA_FORCE */
     int32_t bc[3];      /* hydro_bc per direction */
     int32_t split;      /* flux splitting: 0 = global Lax-Friedrichs (alpha_d
                            = max speed over the grid), 1 = local Lax-Friedrichs
@@ -81,7 +85,17 @@ typedef struct {
                            state then has 4 + nq fields (E, M_x, M_y, M_z,
                            R_1..R_nq) and primitives (e, v, n_1..n_nq).  nq > 1
                            is supported by the single-grid path only */
-    int32_t reserved2;  /* must be 0 */
+    int32_t limiter;    /* MUSTA-FORCE: MUSCL slope limiter on the conserved
+                           variables, component-wise: 0 minmod, 1 monotonized
+                           central, 2 van Leer, 3 superbee.  A reconstructed
+                           state with E <= 0 or |M| >= E falls back to the
+                           cell value.  Ignored by WENO */
+    int32_t musta_stages; /* MUSTA-FORCE: stages K of the centred FORCE flux on
+                           the local states (0 = default 2; 1 = plain FORCE),
+                           local ratio dt/dx = 0.9 / max|lambda| of the local
+                           states.  Ignored by WENO.  MUSTA-FORCE runs on the
+                           single-grid path with split = 0, nq <= 1 */
+    int32_t reserved3;  /* must be 0 */
     double dx[3];       /* cell sizes |e_i| > 0 */
     double origin[3];   /* lower corner of the box (informational) */
     double cs2;         /* EOS p = cs2 * e, 0 < cs2 < 1 (1/3 in the paper's tests) */

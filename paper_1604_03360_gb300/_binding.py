@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libhydro.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_UNPHYSICAL, ERR_TIMEOUT, ERR_STATE = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
-WENO5, WENO7 = 5, 7
+WENO5, WENO7, MUSTA_FORCE = 5, 7, 2
 BC_OUTFLOW, BC_PERIODIC = 0, 1
 
 _NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNPHYSICAL", 5: "TIMEOUT", 6: "STATE"}
@@ -33,7 +33,9 @@ class HydroConfig(ctypes.Structure):
         ("bc", ctypes.c_int32 * 3),
         ("split", ctypes.c_int32),
         ("nq", ctypes.c_int32),
-        ("reserved2", ctypes.c_int32),
+        ("limiter", ctypes.c_int32),
+        ("musta_stages", ctypes.c_int32),
+        ("reserved3", ctypes.c_int32),
         ("dx", ctypes.c_double * 3),
         ("origin", ctypes.c_double * 3),
         ("cs2", ctypes.c_double),
@@ -44,7 +46,7 @@ class HydroConfig(ctypes.Structure):
 
 
 def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
-                origin=(0.0, 0.0, 0.0), split=0, nq=1):
+                origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2):
     c = HydroConfig()
     for i in range(3):
         c.n[i] = int(n[i])
@@ -54,7 +56,9 @@ def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=
     c.scheme = int(scheme)
     c.split = int(split)
     c.nq = int(nq)
-    c.reserved2 = 0
+    c.limiter = int(limiter)
+    c.musta_stages = int(musta_stages)
+    c.reserved3 = 0
     c.cs2 = float(cs2)
     c.cfl = float(cfl)
     c.dt_fixed = float(dt_fixed)
@@ -162,9 +166,9 @@ class Hydro:
     """One grid of the FP64 WENO5/WENO7 + SSP-RK3 solver (hydro_t)."""
 
     def __init__(self, n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
-                 origin=(0.0, 0.0, 0.0), split=0, nq=1, stream=None):
+                 origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2, stream=None):
         self._L = lib()
-        self.cfg = make_config(n, dx, scheme, bc, cs2, cfl, dt_fixed, eps, origin, split, nq)
+        self.cfg = make_config(n, dx, scheme, bc, cs2, cfl, dt_fixed, eps, origin, split, nq, limiter, musta_stages)
         self.n = tuple(int(k) for k in n)
         self.shape = (4 + max(1, int(nq)), self.n[2], self.n[1], self.n[0])
         h = ctypes.c_void_p()
@@ -180,7 +184,7 @@ class Hydro:
         """Create from a workloads.Grid description."""
         return cls(g.n, g.dx, scheme=g.scheme, bc=g.bc, cs2=g.cs2, cfl=g.cfl, eps=g.eps, origin=g.origin,
                    dt_fixed=getattr(g, "dt_fixed", 0.0), split=getattr(g, "split", 0), nq=getattr(g, "nq", 1),
-                   stream=stream)
+                   limiter=getattr(g, "limiter", 0), musta_stages=getattr(g, "musta_stages", 2), stream=stream)
 
     def _check(self, rc):
         if rc:

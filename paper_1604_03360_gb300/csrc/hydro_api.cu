@@ -89,6 +89,8 @@ static StageArgs stage_args(hydro_t* h, int stage)
     a.bad_cell = &h->ctl->bad_cell;
     a.s_in = h->S[in];
     a.s_out = stage == 3 ? h->S[0] : h->S[stage];
+    a.limiter = h->cfg.limiter;
+    a.musta_k = musta_stages_of(h->cfg);
     return a;
 }
 
@@ -166,7 +168,7 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
     hydro_t* h = new (std::nothrow) hydro_t();
     if (!h) return fail(nullptr, HYDRO_ERR_OOM, "host allocation failed");
     h->cfg = *cfg;
-    h->R = cfg->scheme == HYDRO_WENO5 ? 3 : 4;
+    h->R = scheme_R(cfg->scheme);
     h->stream = (cudaStream_t)stream;
     cudaError_t e;
     auto bail = [&](hydro_status s) {
@@ -360,7 +362,8 @@ static hydro_status apply_launch(hydro_t* h, int variant, int zc)
 static std::string tune_key(const hydro_t* h)
 {
     char b[96];
-    snprintf(b, sizeof b, "%d %d %d %d", h->R, h->cfg.n[0], h->cfg.n[1], h->cfg.n[2]);
+    snprintf(b, sizeof b, "%d %d %d %d", h->R * 10 + h->cfg.split + 100 * h->cfg.nq, h->cfg.n[0], h->cfg.n[1],
+             h->cfg.n[2]);
     return b;
 }
 
@@ -403,8 +406,8 @@ extern "C" int32_t hydro_launch_variants(int32_t scheme, int32_t split, int32_t 
 {
     if (split != 0 && split != 1) return 0;
     if (nq < 0 || nq > 3) return 0;
-    if (scheme == HYDRO_WENO5 || scheme == HYDRO_WENO7)
-        return launch_variant_count(scheme == HYDRO_WENO5 ? 3 : 4, split, nq);
+    if (scheme == HYDRO_WENO5 || scheme == HYDRO_WENO7 || scheme == HYDRO_MUSTA_FORCE)
+        return launch_variant_count(scheme_R(scheme), split, nq);
     return 0;
 }
 

@@ -335,6 +335,8 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
     for (int e = 0; e < n_events; ++e) {
         const std::string why = check_config(&cfgs[e]);
         if (!why.empty()) return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "event " + std::to_string(e) + ": " + why);
+        if (cfgs[e].scheme == HYDRO_MUSTA_FORCE)
+            return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path runs the WENO schemes only");
         if (cfgs[e].nq > 1)
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path supports one charge (nq <= 1)");
         if (cfgs[e].scheme != cfgs[0].scheme || cfgs[e].split != cfgs[0].split)

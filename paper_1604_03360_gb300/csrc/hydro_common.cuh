@@ -87,6 +87,9 @@ int launch_variant_count(int R, int split, int nq);
 cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out);
 inline cudaError_t stage_launch_info(int R, StageLaunch* out) { return stage_launch_variant(R, 0, 1, 0, out); }
 inline int state_fields(const hydro_config& c) { return 4 + (c.nq > 1 ? c.nq : 1); }
+// internal scheme code: 3 WENO5, 4 WENO7, 2 MUSTA-FORCE (the ghost width)
+inline int scheme_R(int scheme) { return scheme == HYDRO_WENO5 ? 3 : (scheme == HYDRO_WENO7 ? 4 : 2); }
+inline int musta_stages_of(const hydro_config& c) { return c.musta_stages > 0 ? c.musta_stages : 2; }
 
 inline int pick_zc(int nx, int ny, int nz, const StageLaunch& L, int sms)
 {

@@ -1,6 +1,7 @@
 // hydro_kernels.cu -- the stage kernel instantiations and the bookkeeping
 // kernels of the step driver.
 #include "hydro_common.cuh"
+#include "musta_kernel.cuh"
 
 namespace hydro {
 
@@ -142,6 +143,7 @@ static cudaError_t info_for(StageLaunch* out)
 // Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
 int launch_variant_count(int R, int split, int nq)
 {
+    if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 2 : 1;
     return R == 3 ? 4 : 3;
@@ -154,8 +156,29 @@ static cudaError_t charges_variant(int R, int split, StageLaunch* out)
     return split ? info_for<4, 16, 8, 1, true, NF>(out) : info_for<4, 16, 8, 1, false, NF>(out);
 }
 
+template <int TX, int TY>
+static cudaError_t musta_info_for(StageLaunch* out)
+{
+    out->fn = musta_stage_kernel<TX, TY>;
+    out->smem = MustaSmem<TX, TY>::bytes;
+    out->tx = TX;
+    out->ty = TY;
+    cudaError_t e = cudaFuncSetAttribute(musta_stage_kernel<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)out->smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, musta_stage_kernel<TX, TY>, TX * TY,
+                                                         out->smem);
+}
+
+// R == 2 denotes MUSTA-FORCE + MUSCL (two ghost cells): 16x16 and 16x8 tiles.
 cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out)
 {
+    if (R == 2) {
+        if (split != 0 || nq > 1) return cudaErrorInvalidValue;
+        if (v == 0) return musta_info_for<16, 16>(out);
+        if (v == 1) return musta_info_for<16, 8>(out);
+        return cudaErrorInvalidValue;
+    }
     if (nq > 1) {
         if (v != 0) return cudaErrorInvalidValue;
         if (nq == 2) return charges_variant<6>(R, split, out);
@@ -185,8 +208,15 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
 std::string check_config(const hydro_config* c)
 {
     if (!c) return "config is NULL";
-    if (c->scheme != HYDRO_WENO5 && c->scheme != HYDRO_WENO7) return "scheme must be 5 or 7";
-    const int G = c->scheme == HYDRO_WENO5 ? 3 : 4;
+    if (c->scheme != HYDRO_WENO5 && c->scheme != HYDRO_WENO7 && c->scheme != HYDRO_MUSTA_FORCE)
+        return "scheme must be 5, 7 (WENO) or 2 (MUSTA-FORCE)";
+    const int G = c->scheme == HYDRO_WENO5 ? 3 : (c->scheme == HYDRO_WENO7 ? 4 : 2);
+    if (c->scheme == HYDRO_MUSTA_FORCE) {
+        if (c->limiter < 0 || c->limiter > 3) return "limiter must be 0 (minmod), 1 (MC), 2 (van Leer) or 3 (superbee)";
+        if (c->musta_stages < 0 || c->musta_stages > 8) return "musta_stages must be 0 (default 2) .. 8";
+        if (c->split != 0) return "MUSTA-FORCE has no flux splitting (split must be 0)";
+        if (c->nq > 1) return "MUSTA-FORCE supports one charge (nq <= 1)";
+    }
     for (int d = 0; d < 3; ++d) {
         if (c->n[d] < 1) return "grid size must be >= 1";
         if (!(c->dx[d] > 0.0) || !std::isfinite(c->dx[d])) return "dx must be positive and finite";
@@ -201,7 +231,7 @@ std::string check_config(const hydro_config* c)
     if (!(c->dt_fixed > 0.0) && !(c->cfl > 0.0)) return "need cfl > 0 or dt_fixed > 0";
     if (c->split != 0 && c->split != 1) return "split must be 0 (global) or 1 (local Lax-Friedrichs)";
     if (c->nq < 0 || c->nq > 3) return "nq (number of charges) must be 0..3";
-    if (c->reserved2 != 0) return "reserved2 must be 0";
+    if (c->reserved3 != 0) return "reserved3 must be 0";
     return std::string();
 }
 

@@ -95,6 +95,7 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, const double
     if (!why.empty()) return fail(HYDRO_ERR_INVALID_ARG, why);
     if (cfg->split != 0) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc supports global splitting only");
     if (cfg->nq > 1) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc supports one charge (nq <= 1)");
+    if (cfg->scheme == HYDRO_MUSTA_FORCE) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc runs the WENO schemes only");
     if (!u_in || !u_out) return fail(HYDRO_ERR_INVALID_ARG, "NULL state pointer");
     if (nsteps < 0) return fail(HYDRO_ERR_INVALID_ARG, "nsteps < 0");
     const long long ncell = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];

@@ -55,6 +55,8 @@ struct StageArgs {
     long long* bad_cell;    // linear index of the first unphysical cell
     const double* s_in;     // local LF only: 3 fields, max |lambda| per axis of u_s
     double* s_out;          // local LF only: 3 fields, the same for u_out
+    int limiter;            // MUSTA-FORCE only: MUSCL slope limiter (0 minmod, 1 MC, 2 van Leer, 3 superbee)
+    int musta_k;            // MUSTA-FORCE only: number of MUSTA stages
 };
 
 __device__ __forceinline__ int bc_map(int i, int n, int bc)

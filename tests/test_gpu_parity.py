@@ -317,3 +317,55 @@ def test_several_charges_rejected_where_unsupported():
         h.set_primitive(W.with_charges(g, w, 2))
         with pytest.raises(HydroError):
             h.forward_record(2, 1)
+
+
+# ---------------------------------------------------------------- MUSTA-FORCE + MUSCL
+@pytest.mark.parametrize("limiter,stages", [(0, 2), (1, 1), (2, 3), (3, 2)])
+def test_musta_sod(limiter, stages):
+    g, w = W.sod(N=400, scheme=5)
+    g.scheme, g.limiter, g.musta_stages = 2, limiter, stages
+    assert_parity(g, w, 100000, t0=0.0, t_end=0.4)
+
+
+@pytest.mark.parametrize("dims", [(37, 29, 21), (23, 17, 1), (1, 19, 23), (16, 16, 40)])
+def test_musta_ragged_and_degenerate(dims):
+    g, w = W.lumpy(n=dims, seed=7 + sum(dims), scheme=5)
+    w = with_flow(g, w)
+    g.scheme, g.limiter = 2, 1
+    assert_parity(g, w, 6)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_musta_periodic_and_variants(variant):
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.smooth_periodic(n=(19, 13, 11), amp=0.3, vamp=0.5, seed=4, scheme=5)
+    g.scheme, g.limiter = 2, 2
+    u0 = oracle.prim2con(w)
+    ref = oracle.run(oracle_cfg(g), u0, 8)[0]
+    with Hydro.from_grid(g) as h:
+        h.set_launch(variant, 6)
+        h.set_state(u0)
+        h.step(8)
+        got = h.get_state()
+    assert np.all(field_errors(got, ref) <= TOL)
+
+
+def test_musta_ellipsoidal():
+    g, w = W.ellipsoidal(N=40, scheme=5)
+    g.scheme, g.cfl = 2, 0.3 * 40 / 256
+    assert_parity(g, w, 40)
+
+
+def test_musta_rejected_where_unsupported():
+    from paper_1604_03360_gb300 import Hydro, HydroBatch, HydroError
+    g, w = W.lumpy(n=(12, 11, 10), seed=2)
+    g.scheme = 2
+    with pytest.raises(HydroError):
+        HydroBatch([g])
+    with Hydro.from_grid(g) as h:
+        h.set_primitive(w)
+        with pytest.raises(HydroError):
+            h.forward_record(2, 1)
+    g.split = 1
+    with pytest.raises(HydroError):
+        Hydro.from_grid(g)

@@ -35,6 +35,8 @@ class Grid:
     dt_fixed: float = 0.0       # > 0: constant time step instead of the CFL rule
     split: int = 0              # 0 global, 1 local Lax-Friedrichs splitting
     nq: int = 1                 # conserved charge densities (state fields 4 + nq)
+    limiter: int = 0            # MUSTA-FORCE: 0 minmod, 1 MC, 2 van Leer, 3 superbee
+    musta_stages: int = 2       # MUSTA-FORCE: stages of the FORCE flux
     cs2: float = CS2
     eps: float = 1e-6
     t0: float = 0.0

@@ -305,6 +305,48 @@ def musta_force_256(dev, stream, barrier, grid, with_cpu):
     return out
 
 
+def slabs_256(dev, stream, barrier, scheme, grid, variant, nslabs=4, steps=3, warmup=2):
+    """The benchmark grid cut into z-slabs on this one GPU (halo handles,
+    ghost planes exchanged device to device and speeds max-reduced between
+    RK stages): throughput against the whole grid, and whether the final
+    state is bit-identical to the whole grid's after the same steps."""
+    import torch
+    from paper_1604_03360_gb300 import Hydro
+    from paper_1604_03360_gb300.domain import LocalExchange, SlabDomain, split_grid
+    g, w = workload(scheme, grid)
+    wd = torch.from_numpy(w).to(dev)
+    slabs, bounds = split_grid(g, nslabs, stream=stream)
+    for s, (z0, z1) in zip(slabs, bounds):
+        s.set_launch(variant)
+        s.set_primitive(wd[:, z0:z1].contiguous())
+    dom = SlabDomain(LocalExchange(slabs, g.bc[2], device=dev))
+    dom.loaded()
+    dom.step(warmup)
+    barrier()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    dom.step(steps)
+    a1.record(stream)
+    barrier()
+    el = a0.elapsed_time(a1) / 1e3
+    got = torch.cat([s.get_state(torch.empty((5, z1 - z0) + w.shape[2:], dtype=torch.float64, device=dev))
+                     for s, (z0, z1) in zip(slabs, bounds)], dim=1)
+    for s in slabs:
+        s.close()
+    h = Hydro.from_grid(g, stream=stream)
+    h.set_launch(variant)
+    h.set_primitive(wd)
+    h.step(warmup + steps)
+    ref = h.get_state(torch.empty_like(wd))
+    h.close()
+    barrier()
+    G = {5: 3, 7: 4}[scheme]
+    return {"value": g.cells * steps / el, "unit": "cell-updates/s", "slabs": nslabs, "steps": steps,
+            "ms_per_step": 1e3 * el / steps, "bounds": bounds,
+            "ghost_block_bytes": 9 * G * grid * grid * 8, "ghost_copies_per_stage": 4 * nslabs - 2,
+            "bit_identical_to_whole_grid": bool(torch.equal(got, ref))}
+
+
 def adjoint_96(dev, stream, barrier):
     """Adjoint configuration: 96^3 lumpy event (seed 1604), WENO5, 50 RK3 steps
     with a checkpoint every 10; gradient of eps_2 with respect to the initial
@@ -509,6 +551,8 @@ def main():
         extra["batched_vs_looped"] = batched_vs_looped(dev, stream, barrier, 3, 3, args.batch_events)
     if not args.no_extra:
         extra["adjoint_96"] = adjoint_96(dev, stream, barrier)
+    if not args.no_extra:
+        extra["slabs4_%d" % args.grid] = slabs_256(dev, stream, barrier, args.scheme, args.grid, launch[0])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -62,7 +62,13 @@ typedef enum {
  * reconstruction with a slope limiter and the multi-stage (MUSTA) centred
  * FORCE flux; see hydro_config.limiter / musta_stages. */
 typedef enum { HYDRO_MUSTA_FORCE = 2, HYDRO_WENO5 = 5, HYDRO_WENO7 = 7 } hydro_scheme;
-typedef enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1 } hydro_bc;
+/* HYDRO_BC_HALO (z only): the grid is one z-slab of a larger grid.  The
+ * handle stores G = r planes (WENO5 3, WENO7 4, MUSTA-FORCE 2) of ghost cells
+ * below and above its nz interior planes, and its stage kernels read them as
+ * they are; the caller fills them before every RK stage (hydro_halo_*) and
+ * drives the step one stage at a time (hydro_stage).  See the slab-domain
+ * entry points below. */
+typedef enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1, HYDRO_BC_HALO = 2 } hydro_bc;
 typedef enum { HYDRO_MEM_HOST = 0, HYDRO_MEM_DEVICE = 1 } hydro_mem;
 
 /* Problem definition (Eq. 2 grid, Sec. 1.2 scheme, boundary rule). */
@@ -185,6 +191,56 @@ hydro_status hydro_autotune(hydro_t* h, double* best_ms);
  * hydro_field_stride()) for zero-copy readers; owned by h. */
 const double* hydro_state_device_ptr(hydro_t* h);
 int64_t hydro_field_stride(hydro_t* h);
+
+/* ---- z-slab domain decomposition ----------------------------------------
+ * L(u) of Eq. 3 at a cell depends on the r (= G) neighbouring cells along
+ * each axis (Sec. 1, after Eq. 3), and the global Lax-Friedrichs speeds of
+ * Sec. 1.2 are maxima over the whole grid.  A grid split into z-slabs, each
+ * a handle with bc[2] = HYDRO_BC_HALO holding nz >= G interior planes,
+ * therefore advances exactly like the whole grid if, before each RK stage,
+ * every slab's G ghost planes on each side hold the neighbouring slab's
+ * planes of that stage's input (or the boundary rule's values at the ends of
+ * the grid), and every speed slot is the maximum over all slabs.  A step is
+ *     hydro_stage(h, 0, t_end)            dt from speed slot 0 (must already
+ *                                         be the global max), clear slots 1-3
+ *     for s in 1, 2, 3:
+ *         fill ghost planes of level s-1  (hydro_halo_pack / _unpack /
+ *                                          _fill_outflow)
+ *         hydro_stage(h, s, t_end)        RK stage s; local max speeds of its
+ *                                         output into slot s
+ *         max-reduce slot s over slabs    (hydro_speed_slot read, reduce, write)
+ *     hydro_stage(h, 4, t_end)            commit: slot 3 becomes slot 0, t += dt
+ * After hydro_set_state/_set_primitive slot 0 holds the slab's own speeds
+ * and must be max-reduced before the first step.  Levels: 0 = u^n (also the
+ * stage-3 output), 1 and 2 = the stage-1 and stage-2 outputs.  Every call is
+ * stream-ordered on the handle's stream and returns without synchronising
+ * unless a host buffer is involved.  hydro_step/_profile_step, the adjoint
+ * and hydro_autotune reject halo handles. */
+
+/* Doubles in one side's ghost block: (nf + 4 [+ 3 with local LF]) fields x
+ * G planes x nx x ny, laid out field by field, each field's planes in
+ * ascending z (the layout of hydro_halo_pack's output). */
+int64_t hydro_halo_doubles(hydro_t* h);
+/* Copy the G interior planes next to `side` (0 = low z, 1 = high z) of every
+ * field of `level` into buf (hydro_halo_doubles() doubles, host or device per
+ * mem, owned by the caller; a host copy synchronises the stream). */
+hydro_status hydro_halo_pack(hydro_t* h, int32_t level, int32_t side, double* buf, int32_t mem);
+/* Copy buf (layout of hydro_halo_pack) into the G ghost planes on `side` of
+ * `level`: the low ghost planes take the lower neighbour's high pack, the
+ * high ghost planes the upper neighbour's low pack. */
+hydro_status hydro_halo_unpack(hydro_t* h, int32_t level, int32_t side, const double* buf, int32_t mem);
+/* Outflow boundary at the end of the grid: every ghost plane on `side` of
+ * `level` becomes a copy of the nearest interior plane (the zero-gradient
+ * rule of the whole-grid kernels). */
+hydro_status hydro_halo_fill_outflow(hydro_t* h, int32_t level, int32_t side);
+/* One part of a step on a halo handle: which = 0 step begin (dt, clipped to
+ * t_end when t_end >= 0), 1..3 RK stage, 4 step commit.  Any other value or
+ * a handle without HYDRO_BC_HALO -> HYDRO_ERR_INVALID_ARG. */
+hydro_status hydro_stage(hydro_t* h, int32_t which, double t_end);
+/* Read (io = 0) or write (io = 1) speed slot `slot` (0 = speeds of u^n,
+ * 1..3 = of the stage-s output): 3 non-negative doubles (max |lambda| along
+ * x, y, z), host or device per mem.  A host read synchronises the stream. */
+hydro_status hydro_speed_slot(hydro_t* h, int32_t slot, int32_t io, double* speeds, int32_t mem);
 
 /* Measurement helper, not part of the paper's method: times a kernel of
  * independent FP64 FMA chains on every SM (on `stream`, synchronising it) and

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libhydro.so")
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_UNPHYSICAL, ERR_TIMEOUT, ERR_STATE = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
 WENO5, WENO7, MUSTA_FORCE = 5, 7, 2
-BC_OUTFLOW, BC_PERIODIC = 0, 1
+BC_OUTFLOW, BC_PERIODIC, BC_HALO = 0, 1, 2
 
 _NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNPHYSICAL", 5: "TIMEOUT", 6: "STATE"}
 
@@ -116,6 +116,12 @@ def lib():
         "hydro_batch_set_launch": ([vp, i32, i32], i32),
         "hydro_batch_get_launch": ([vp, P(i32), P(i32), P(i32), P(i32), P(i32)], i32),
         "hydro_batch_autotune": ([vp, P(d)], i32),
+        "hydro_halo_doubles": ([vp], i64),
+        "hydro_halo_pack": ([vp, i32, i32, vp, i32], i32),
+        "hydro_halo_unpack": ([vp, i32, i32, vp, i32], i32),
+        "hydro_halo_fill_outflow": ([vp, i32, i32], i32),
+        "hydro_stage": ([vp, i32, d], i32),
+        "hydro_speed_slot": ([vp, i32, i32, vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -150,6 +156,20 @@ def as_buffer(x, writable=False):
     if x.dtype != torch.float64 or not x.is_contiguous():
         raise ValueError("need a contiguous float64 tensor")
     return ctypes.c_void_p(x.data_ptr()), x[0].numel(), (MEM_DEVICE if x.is_cuda else MEM_HOST)
+
+
+def _flat_buffer(x, n, writable=False):
+    """(pointer, mem) of a contiguous float64 buffer of at least n doubles."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.size < n:
+            raise ValueError("need a C-contiguous float64 array of %d doubles" % n)
+        if writable and not x.flags["WRITEABLE"]:
+            raise ValueError("array is read-only")
+        return ctypes.c_void_p(x.ctypes.data), MEM_HOST
+    import torch
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.float64 or not x.is_contiguous() or x.numel() < n:
+        raise ValueError("need a contiguous float64 tensor of %d doubles" % n)
+    return ctypes.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST)
 
 
 def measure_fp64_peak(stream=None):
@@ -281,6 +301,38 @@ class Hydro:
 
     def sync(self):
         self._check(self._L.hydro_sync(self._h))
+
+    # -- z-slab (bc[2] = BC_HALO) handles: one RK stage at a time ---------
+
+    def halo_doubles(self):
+        """Doubles in one side's ghost block (0 for a whole grid)."""
+        return int(self._L.hydro_halo_doubles(self._h))
+
+    def halo_pack(self, level, side, buf):
+        """Interior planes next to `side` of RK level `level` -> buf (1-D float64)."""
+        p, mem = _flat_buffer(buf, self.halo_doubles(), writable=True)
+        self._check(self._L.hydro_halo_pack(self._h, int(level), int(side), p, mem))
+        return buf
+
+    def halo_unpack(self, level, side, buf):
+        """buf (a neighbour's pack) -> ghost planes on `side` of level `level`."""
+        p, mem = _flat_buffer(buf, self.halo_doubles())
+        self._check(self._L.hydro_halo_unpack(self._h, int(level), int(side), p, mem))
+
+    def halo_fill_outflow(self, level, side):
+        self._check(self._L.hydro_halo_fill_outflow(self._h, int(level), int(side)))
+
+    def stage(self, which, t_end=-1.0):
+        """0 step begin, 1..3 RK stage, 4 step commit."""
+        self._check(self._L.hydro_stage(self._h, int(which), float(t_end)))
+
+    def speed_slot(self, slot, buf=None, write=False):
+        """Read (or, write=True, overwrite) speed slot 0..3 through a 3-double buffer."""
+        if buf is None:
+            buf = np.zeros(3)
+        p, mem = _flat_buffer(buf, 3, writable=not write)
+        self._check(self._L.hydro_speed_slot(self._h, int(slot), 1 if write else 0, p, mem))
+        return buf
 
     def speeds(self):
         a = (ctypes.c_double * 3)()

@@ -438,6 +438,8 @@ static StageArgs frozen_stage(const HandleView& v, AdjointWork* w, double** U, d
     a.ny = v.cfg.n[1];
     a.nz = v.cfg.n[2];
     a.zc = v.zc;
+    a.zlo = 0;
+    a.zhi = v.cfg.n[2];
     for (int d = 0; d < 3; ++d) {
         a.bc[d] = v.cfg.bc[d];
         a.act[d] = v.cfg.n[d] > 1;
@@ -472,6 +474,8 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     if (v.cfg.nq > 1) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint supports one charge (nq <= 1)");
     if (v.cfg.scheme == HYDRO_MUSTA_FORCE)
         return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint differentiates the WENO schemes only");
+    if (v.cfg.bc[2] == HYDRO_BC_HALO)
+        return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint runs on whole grids (no z halo)");
     if (nsteps < 1 || ckpt_every < 1) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
     AdjointWork* w = hydro_handle_adjoint(h, true);
     if (!w) return hydro_handle_fail(h, HYDRO_ERR_OOM, "host allocation failed");
@@ -540,6 +544,8 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
             a.ny = v.cfg.n[1];
             a.nz = v.cfg.n[2];
             a.zc = v.zc;
+            a.zlo = 0;
+            a.zhi = v.cfg.n[2];
             for (int d = 0; d < 3; ++d) {
                 a.bc[d] = v.cfg.bc[d];
                 a.act[d] = v.cfg.n[d] > 1;

@@ -32,6 +32,11 @@ struct hydro_s {
     int variant = 0;
     int zc = 0;
     int nf = 5;                      // state fields: E, M, and nq >= 1 charges
+    // z halo storage (bc[2] == HYDRO_BC_HALO, a slab of a larger grid): nz_alloc
+    // stored planes, interior [zlo, zhi), interior data starts `off` doubles
+    // into every field; otherwise nz_alloc = n[2], zlo = 0, off = 0
+    int nz_alloc = 0, zlo = 0, zhi = 0, G = 3;
+    long long off = 0;
     bool have_state = false;
     AdjointWork* adj = nullptr;      // reverse-mode workspace (hydro_adjoint.cu)
     std::string err;
@@ -70,11 +75,13 @@ static StageArgs stage_args(hydro_t* h, int stage)
     a.fs = h->fs;
     a.nx = h->cfg.n[0];
     a.ny = h->cfg.n[1];
-    a.nz = h->cfg.n[2];
+    a.nz = h->nz_alloc;
     a.zc = h->zc;
+    a.zlo = h->zlo;
+    a.zhi = h->zhi;
     for (int d = 0; d < 3; ++d) {
         a.bc[d] = h->cfg.bc[d];
-        a.act[d] = h->cfg.n[d] > 1;
+        a.act[d] = axis_active(h->cfg, d);
         a.hdx[d] = 0.5 / h->cfg.dx[d];
     }
     a.cs2 = h->cfg.cs2;
@@ -97,7 +104,7 @@ static StageArgs stage_args(hydro_t* h, int stage)
 static cudaError_t enqueue_step(hydro_t* h, cudaStream_t s)
 {
     const dim3 grid((h->cfg.n[0] + h->L.tx - 1) / h->L.tx, (h->cfg.n[1] + h->L.ty - 1) / h->L.ty,
-                    (h->cfg.n[2] + h->zc - 1) / h->zc);
+                    (h->zhi - h->zlo + h->zc - 1) / h->zc);
     step_begin_kernel<<<1, 1, 0, s>>>(h->ctl, step_params(h->cfg));
     for (int st = 1; st <= 3; ++st) {
         const StageArgs a = stage_args(h, st);
@@ -135,8 +142,8 @@ hydro_status hydro_handle_view(hydro_t* h, HandleView* v)
     v->stream = h->stream;
     v->ncell = h->ncell;
     v->fs = h->fs;
-    v->U0 = h->U[0];
-    v->W0 = h->W[0];
+    v->U0 = h->U[0] + h->off;
+    v->W0 = h->W[0] + h->off;
     v->ctl = h->ctl;
     v->L = h->L;
     v->zc = h->zc;
@@ -182,8 +189,15 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
     h->nf = state_fields(*cfg);
     if ((e = stage_launch_variant(h->R, cfg->split, cfg->nq, 0, &h->L)) != cudaSuccess)
         return bail(cuda_fail(h, e, "stage kernel setup"));
+    h->G = h->R;
     h->ncell = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
-    h->fs = (h->ncell + 31) / 32 * 32;   // 256-byte aligned fields
+    const bool halo = cfg->bc[2] == HYDRO_BC_HALO;
+    h->nz_alloc = cfg->n[2] + (halo ? 2 * h->G : 0);
+    h->zlo = halo ? h->G : 0;
+    h->zhi = h->zlo + cfg->n[2];
+    h->off = (long long)h->zlo * cfg->n[0] * cfg->n[1];
+    const long long nalloc = (long long)cfg->n[0] * cfg->n[1] * h->nz_alloc;
+    h->fs = (nalloc + 31) / 32 * 32;   // 256-byte aligned fields
     h->zc = pick_zc(cfg->n[0], cfg->n[1], cfg->n[2], h->L, h->sms);
     // U0..U2 (nf fields each), W0..W2 (4 each), speeds S0..S2 (3 each, local LF)
     const int nf = h->nf;
@@ -250,8 +264,8 @@ static hydro_status check_io(hydro_t* h, const void* p, int64_t stride, int32_t 
 static hydro_status after_load(hydro_t* h, double t)
 {
     reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
-    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl,
-                                                                 h->S[0]);
+    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0] + h->off, h->W[0] + h->off, h->fs, h->ncell,
+                                                                 h->cfg.cs2, h->ctl, h->S[0] ? h->S[0] + h->off : nullptr);
     CK(h, cudaGetLastError(), "prepare");
     h->have_state = true;
     return HYDRO_OK;
@@ -261,7 +275,7 @@ hydro_status hydro_set_state(hydro_t* h, const double* u, int64_t field_stride, 
 {
     hydro_status s = check_io(h, u, field_stride, mem);
     if (s) return s;
-    s = copy_fields(h, h->U[0], h->fs, u, field_stride, h->nf,
+    s = copy_fields(h, h->U[0] + h->off, h->fs, u, field_stride, h->nf,
                     mem == HYDRO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
     if (s) return s;
     return after_load(h, t);
@@ -274,17 +288,17 @@ hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stri
     const double* src = w;
     long long ss = field_stride;
     if (mem == HYDRO_MEM_HOST) {   // stage through U1 (scratch between steps)
-        s = copy_fields(h, h->U[1], h->fs, w, field_stride, h->nf, cudaMemcpyHostToDevice);
+        s = copy_fields(h, h->U[1] + h->off, h->fs, w, field_stride, h->nf, cudaMemcpyHostToDevice);
         if (s) return s;
-        src = h->U[1];
+        src = h->U[1] + h->off;
         ss = h->fs;
     }
     reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
-    prim2con_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(src, ss, h->U[0], h->fs, h->ncell, h->cfg.cs2, h->ctl,
-                                                                  h->nf);
+    prim2con_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(src, ss, h->U[0] + h->off, h->fs, h->ncell, h->cfg.cs2,
+                                                                  h->ctl, h->nf);
     CK(h, cudaGetLastError(), "prim2con");
-    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->W[0], h->fs, h->ncell, h->cfg.cs2, h->ctl,
-                                                                 h->S[0]);
+    prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0] + h->off, h->W[0] + h->off, h->fs, h->ncell,
+                                                                 h->cfg.cs2, h->ctl, h->S[0] ? h->S[0] + h->off : nullptr);
     CK(h, cudaGetLastError(), "prepare");
     h->have_state = true;
     return HYDRO_OK;
@@ -293,6 +307,7 @@ hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stri
 hydro_status hydro_step(hydro_t* h, int32_t nsteps, double t_end)
 {
     if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (h->cfg.bc[2] == HYDRO_BC_HALO) return fail(h, HYDRO_ERR_INVALID_ARG, "a halo slab steps through hydro_stage");
     if (nsteps < 0) return fail(h, HYDRO_ERR_INVALID_ARG, "nsteps < 0");
     if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
     set_t_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t_end);
@@ -304,6 +319,7 @@ hydro_status hydro_step(hydro_t* h, int32_t nsteps, double t_end)
 hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double kernel_ms[5])
 {
     if (!h || !kernel_ms) return HYDRO_ERR_INVALID_ARG;
+    if (h->cfg.bc[2] == HYDRO_BC_HALO) return fail(h, HYDRO_ERR_INVALID_ARG, "a halo slab steps through hydro_stage");
     if (nsteps < 0) return fail(h, HYDRO_ERR_INVALID_ARG, "nsteps < 0");
     if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
     for (int i = 0; i < 5; ++i) kernel_ms[i] = 0.0;
@@ -312,7 +328,7 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
     hydro_status st = HYDRO_OK;
     set_t_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t_end);
     const dim3 grid((h->cfg.n[0] + h->L.tx - 1) / h->L.tx, (h->cfg.n[1] + h->L.ty - 1) / h->L.ty,
-                    (h->cfg.n[2] + h->zc - 1) / h->zc);
+                    (h->zhi - h->zlo + h->zc - 1) / h->zc);
     for (int s = 0; s < nsteps && st == HYDRO_OK; ++s) {
         cudaEventRecord(ev[0], h->stream);
         step_begin_kernel<<<1, 1, 0, h->stream>>>(h->ctl, step_params(h->cfg));
@@ -338,6 +354,119 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
     }
     for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
     return st;
+}
+
+// ---- z-slab domain decomposition ---------------------------------------
+
+static bool is_halo(const hydro_t* h) { return h->cfg.bc[2] == HYDRO_BC_HALO; }
+
+// the exchanged fields of one level, in pack order: u (nf), w (4), speeds (3, local LF)
+static int level_fields(hydro_t* h, int level, double* f[16])
+{
+    int n = 0;
+    for (int k = 0; k < h->nf; ++k) f[n++] = h->U[level] + (size_t)h->fs * k;
+    for (int k = 0; k < 4; ++k) f[n++] = h->W[level] + (size_t)h->fs * k;
+    if (h->cfg.split)
+        for (int k = 0; k < 3; ++k) f[n++] = h->S[level] + (size_t)h->fs * k;
+    return n;
+}
+
+int64_t hydro_halo_doubles(hydro_t* h)
+{
+    if (!h || !is_halo(h)) return 0;
+    double* f[16];
+    return (int64_t)level_fields(h, 0, f) * h->G * h->cfg.n[0] * h->cfg.n[1];
+}
+
+static hydro_status halo_args(hydro_t* h, int level, int side, int mem, const void* buf)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (!is_halo(h)) return fail(h, HYDRO_ERR_INVALID_ARG, "not a halo (bc[2] = HYDRO_BC_HALO) handle");
+    if (level < 0 || level > 2 || side < 0 || side > 1) return fail(h, HYDRO_ERR_INVALID_ARG, "level must be 0..2, side 0..1");
+    if (mem != HYDRO_MEM_HOST && mem != HYDRO_MEM_DEVICE) return fail(h, HYDRO_ERR_INVALID_ARG, "bad mem");
+    if (!buf) return fail(h, HYDRO_ERR_INVALID_ARG, "buffer is NULL");
+    return HYDRO_OK;
+}
+
+// pack: interior planes next to `side` -> buf; unpack: buf -> ghost planes on `side`
+static hydro_status halo_copy(hydro_t* h, int level, int side, double* out, const double* in, int mem, bool pack)
+{
+    const long long plane = (long long)h->cfg.n[0] * h->cfg.n[1], blk = (long long)h->G * plane;
+    const int z0 = pack ? (side ? h->zhi - h->G : h->zlo) : (side ? h->zhi : 0);
+    double* f[16];
+    const int n = level_fields(h, level, f);
+    const cudaMemcpyKind kind = mem == HYDRO_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                        : (pack ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    for (int k = 0; k < n; ++k) {
+        double* dst = pack ? out + k * blk : f[k] + z0 * plane;
+        const double* src = pack ? f[k] + z0 * plane : in + k * blk;
+        CK(h, cudaMemcpyAsync(dst, src, sizeof(double) * blk, kind, h->stream), "halo copy");
+    }
+    if (mem == HYDRO_MEM_HOST) CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return HYDRO_OK;
+}
+
+hydro_status hydro_halo_pack(hydro_t* h, int32_t level, int32_t side, double* buf, int32_t mem)
+{
+    hydro_status s = halo_args(h, level, side, mem, buf);
+    return s ? s : halo_copy(h, level, side, buf, nullptr, mem, true);
+}
+
+hydro_status hydro_halo_unpack(hydro_t* h, int32_t level, int32_t side, const double* buf, int32_t mem)
+{
+    hydro_status s = halo_args(h, level, side, mem, buf);
+    return s ? s : halo_copy(h, level, side, nullptr, buf, mem, false);
+}
+
+hydro_status hydro_halo_fill_outflow(hydro_t* h, int32_t level, int32_t side)
+{
+    hydro_status s = halo_args(h, level, side, HYDRO_MEM_DEVICE, h);
+    if (s) return s;
+    FieldList fl{};
+    fl.n = level_fields(h, level, fl.f);
+    const long long plane = (long long)h->cfg.n[0] * h->cfg.n[1];
+    const long long src = (long long)(side ? h->zhi - 1 : h->zlo) * plane;
+    const long long dst = (long long)(side ? h->zhi : 0) * plane;
+    halo_replicate_kernel<<<blocks_for((long long)fl.n * h->G * plane), 256, 0, h->stream>>>(fl, plane, src, dst, h->G);
+    CK(h, cudaGetLastError(), "halo fill");
+    return HYDRO_OK;
+}
+
+hydro_status hydro_stage(hydro_t* h, int32_t which, double t_end)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (!is_halo(h)) return fail(h, HYDRO_ERR_INVALID_ARG, "hydro_stage drives halo (bc[2] = HYDRO_BC_HALO) handles only");
+    if (which < 0 || which > 4) return fail(h, HYDRO_ERR_INVALID_ARG, "which must be 0..4");
+    if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
+    if (which == 0) {
+        set_t_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t_end);
+        step_begin_kernel<<<1, 1, 0, h->stream>>>(h->ctl, step_params(h->cfg));
+    } else if (which == 4) {
+        step_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl);
+    } else {
+        const dim3 grid((h->cfg.n[0] + h->L.tx - 1) / h->L.tx, (h->cfg.n[1] + h->L.ty - 1) / h->L.ty,
+                        (h->zhi - h->zlo + h->zc - 1) / h->zc);
+        const StageArgs a = stage_args(h, which);
+        h->L.fn<<<grid, h->L.tx * h->L.ty, h->L.smem, h->stream>>>(a);
+    }
+    CK(h, cudaGetLastError(), "stage launch");
+    return HYDRO_OK;
+}
+
+hydro_status hydro_speed_slot(hydro_t* h, int32_t slot, int32_t io, double* speeds, int32_t mem)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (slot < 0 || slot > 3 || (io != 0 && io != 1) || !speeds ||
+        (mem != HYDRO_MEM_HOST && mem != HYDRO_MEM_DEVICE))
+        return fail(h, HYDRO_ERR_INVALID_ARG, "bad speed-slot arguments");
+    unsigned long long* p = slot == 0 ? h->ctl->a_cur : slot == 1 ? h->ctl->a_s1 : slot == 2 ? h->ctl->a_s2 : h->ctl->a_next;
+    // the slot holds the IEEE bits of non-negative doubles (ordered like the values)
+    const cudaMemcpyKind kind = mem == HYDRO_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                        : (io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    if (io) CK(h, cudaMemcpyAsync(p, speeds, 3 * sizeof(double), kind, h->stream), "speed slot write");
+    else CK(h, cudaMemcpyAsync(speeds, p, 3 * sizeof(double), kind, h->stream), "speed slot read");
+    if (mem == HYDRO_MEM_HOST) CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return HYDRO_OK;
 }
 
 __global__ void set_dt_kernel(Ctl* c, double dt) { c->dt = dt; }
@@ -432,6 +561,7 @@ extern "C" hydro_status hydro_get_launch(hydro_t* h, int32_t* variant, int32_t* 
 extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
 {
     if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (h->cfg.bc[2] == HYDRO_BC_HALO) return fail(h, HYDRO_ERR_INVALID_ARG, "hydro_autotune runs whole grids (no z halo)");
     if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
     int cv = 0, cz = 0;
     if (tune_cache_lookup(h, &cv, &cz) && cv >= 0 && cv < hydro_launch_variants(h->cfg.scheme, h->cfg.split, h->cfg.nq)) {
@@ -526,7 +656,7 @@ hydro_status hydro_get_state(hydro_t* h, double* u, int64_t field_stride, int32_
 {
     hydro_status s = check_io(h, u, field_stride, mem);
     if (s) return s;
-    s = copy_fields(h, u, field_stride, h->U[0], h->fs, h->nf,
+    s = copy_fields(h, u, field_stride, h->U[0] + h->off, h->fs, h->nf,
                     mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
     if (s) return s;
     s = read_ctl(h);
@@ -539,10 +669,10 @@ hydro_status hydro_get_primitive(hydro_t* h, double* w, int64_t field_stride, in
 {
     hydro_status s = check_io(h, w, field_stride, mem);
     if (s) return s;
-    state_to_prim_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0], h->fs, h->U[1], h->fs, h->ncell,
-                                                                      h->cfg.cs2, h->nf);
+    state_to_prim_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0] + h->off, h->fs, h->U[1] + h->off,
+                                                                      h->fs, h->ncell, h->cfg.cs2, h->nf);
     CK(h, cudaGetLastError(), "state_to_prim");
-    s = copy_fields(h, w, field_stride, h->U[1], h->fs, h->nf,
+    s = copy_fields(h, w, field_stride, h->U[1] + h->off, h->fs, h->nf,
                     mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
     if (s) return s;
     return read_ctl(h);
@@ -563,7 +693,7 @@ hydro_status hydro_get_speeds(hydro_t* h, double alpha[3], double* last_dt)
     return s;
 }
 
-const double* hydro_state_device_ptr(hydro_t* h) { return h ? h->U[0] : nullptr; }
+const double* hydro_state_device_ptr(hydro_t* h) { return h ? h->U[0] + h->off : nullptr; }
 int64_t hydro_field_stride(hydro_t* h) { return h ? h->fs : 0; }
 
 }  // extern "C"

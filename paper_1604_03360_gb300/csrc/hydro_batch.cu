@@ -55,6 +55,8 @@ __device__ __forceinline__ StageArgs batch_stage_args(const BatchEvent& E, int s
     a.ny = E.n[1];
     a.nz = E.n[2];
     a.zc = zc;
+    a.zlo = 0;
+    a.zhi = E.n[2];
     for (int d = 0; d < 3; ++d) {
         a.bc[d] = E.bc[d];
         a.act[d] = E.act[d];
@@ -335,6 +337,8 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
     for (int e = 0; e < n_events; ++e) {
         const std::string why = check_config(&cfgs[e]);
         if (!why.empty()) return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "event " + std::to_string(e) + ": " + why);
+        if (cfgs[e].bc[2] == HYDRO_BC_HALO)
+            return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "batch events are whole grids (no z halo)");
         if (cfgs[e].scheme == HYDRO_MUSTA_FORCE)
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path runs the WENO schemes only");
         if (cfgs[e].nq > 1)

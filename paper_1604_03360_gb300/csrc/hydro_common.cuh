@@ -40,6 +40,14 @@ __global__ void step_begin_kernel(Ctl* c, StepParams sp);
 // commit the step: speeds of u^{n+1} become current, advance t.
 __global__ void step_end_kernel(Ctl* c);
 __global__ void set_t_end_kernel(Ctl* c, double t_end);
+// ghost planes of a z-slab (outflow end of the grid): for every listed field,
+// planes dst .. dst + G - 1 (offsets in doubles / plane) become copies of the
+// plane at offset src
+struct FieldList {
+    double* f[16];
+    int n;
+};
+__global__ void halo_replicate_kernel(FieldList fl, long long plane, long long src, long long dst, int G);
 __global__ void reset_ctl_kernel(Ctl* c, double t);
 // primitives and speeds of a state (after set_state)
 // (and, if s != nullptr, the per-axis speeds of every cell: 3 fields)
@@ -52,6 +60,13 @@ __global__ void prim2con_kernel(const double* wp, long long ws, double* u, long 
 __global__ void state_to_prim_kernel(const double* u, long long fs, double* out, long long os, long long n,
                                      double cs2, int nf);
 
+// an axis takes part in the scheme if it has more than one cell; a z axis
+// with stored halos (a slab of a larger grid) always does
+inline bool axis_active(const hydro_config& cfg, int d)
+{
+    return cfg.n[d] > 1 || (d == 2 && cfg.bc[2] == HYDRO_BC_HALO);
+}
+
 inline StepParams step_params(const hydro_config& cfg)
 {
     StepParams sp;
@@ -59,7 +74,7 @@ inline StepParams step_params(const hydro_config& cfg)
     sp.dt_fixed = cfg.dt_fixed;
     int mask = 0;
     for (int d = 0; d < 3; ++d)
-        if (cfg.n[d] > 1) mask |= 1 << d;
+        if (axis_active(cfg, d)) mask |= 1 << d;
     if (!mask) mask = 7;
     double m = INFINITY;
     for (int d = 0; d < 3; ++d)

@@ -33,6 +33,16 @@ __global__ void step_end_kernel(Ctl* c)
 
 __global__ void set_t_end_kernel(Ctl* c, double t_end) { c->t_end = t_end; }
 
+__global__ void halo_replicate_kernel(FieldList fl, long long plane, long long src, long long dst, int G)
+{
+    const long long tot = (long long)fl.n * G * plane;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const long long c = i % plane, r = i / plane;
+        const int g = (int)(r % G), f = (int)(r / G);
+        fl.f[f][dst + g * plane + c] = fl.f[f][src + c];
+    }
+}
+
 __global__ void reset_ctl_kernel(Ctl* c, double t)
 {
     for (int d = 0; d < 3; ++d) {
@@ -220,9 +230,11 @@ std::string check_config(const hydro_config* c)
     for (int d = 0; d < 3; ++d) {
         if (c->n[d] < 1) return "grid size must be >= 1";
         if (!(c->dx[d] > 0.0) || !std::isfinite(c->dx[d])) return "dx must be positive and finite";
-        if (c->bc[d] != HYDRO_BC_OUTFLOW && c->bc[d] != HYDRO_BC_PERIODIC) return "bc must be 0 (outflow) or 1 (periodic)";
+        if (c->bc[d] != HYDRO_BC_OUTFLOW && c->bc[d] != HYDRO_BC_PERIODIC && !(d == 2 && c->bc[d] == HYDRO_BC_HALO))
+            return "bc must be 0 (outflow) or 1 (periodic); 2 (halo) on z only";
         if (c->n[d] > 1 && c->bc[d] == HYDRO_BC_PERIODIC && c->n[d] < G) return "periodic axis shorter than the stencil";
     }
+    if (c->bc[2] == HYDRO_BC_HALO && c->n[2] < G) return "a halo slab needs nz >= the stencil half-width r";
     if ((long long)c->n[0] * c->n[1] > (1LL << 40) || c->n[0] > (1 << 28) || c->n[1] > 65535 * 8 ||
         c->n[2] > (1 << 28))
         return "grid too large";

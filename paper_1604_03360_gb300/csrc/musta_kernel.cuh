@@ -158,7 +158,7 @@ __device__ __forceinline__ void musta_tile(const StageArgs& a, int tile_x, int t
     if (!(dt > 0.0)) return;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
-    const int zb = chunk_z * a.zc, ze = min(zb + a.zc, a.nz);
+    const int zb = a.zlo + chunk_z * a.zc, ze = min(zb + a.zc, a.zhi);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = (x < nx) && (y < ny);

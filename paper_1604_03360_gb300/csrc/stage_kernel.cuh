@@ -57,11 +57,16 @@ struct StageArgs {
     double* s_out;          // local LF only: 3 fields, the same for u_out
     int limiter;            // MUSTA-FORCE only: MUSCL slope limiter (0 minmod, 1 MC, 2 van Leer, 3 superbee)
     int musta_k;            // MUSTA-FORCE only: number of MUSTA stages
+    int zlo, zhi;           // planes computed: [zlo, zhi) of the nz stored (0, nz unless z halos are stored)
 };
 
+// boundary rule 0 outflow (copy edge cell), 1 periodic; 2 (z only) halo: the
+// ghost planes are stored with the grid and filled from outside, so every
+// index read is already inside the stored array
 __device__ __forceinline__ int bc_map(int i, int n, int bc)
 {
     if (i >= 0 && i < n) return i;
+    if (bc == 2) return i;
     if (bc == 1) {
         i %= n;
         return i < 0 ? i + n : i;
@@ -166,7 +171,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
-    const int zb = chunk_z * a.zc, ze = min(zb + a.zc, a.nz);
+    const int zb = a.zlo + chunk_z * a.zc, ze = min(zb + a.zc, a.zhi);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = (x < nx) && (y < ny);

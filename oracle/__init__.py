@@ -50,7 +50,7 @@ class Cfg(ctypes.Structure):
         ("nq", ctypes.c_int32),
         ("limiter", ctypes.c_int32),
         ("musta_k", ctypes.c_int32),
-        ("pad2_", ctypes.c_int32),
+        ("charw", ctypes.c_int32),
         ("dx", ctypes.c_double * 3),
         ("cs2", ctypes.c_double),
         ("cfl", ctypes.c_double),
@@ -70,6 +70,7 @@ def lib():
         L.oc_con2prim.argtypes = [d, vp, vp]
         L.oc_prim2con.argtypes = [d, vp, vp]
         L.oc_flux.argtypes = [d, ctypes.c_int, vp, vp, vp]
+        L.oc_flux_n.argtypes = [d, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         L.oc_eigen.argtypes = [d, ctypes.c_int, vp, vp]
         L.oc_weno_left.argtypes = [ctypes.c_int, vp, d]
         L.oc_weno_left.restype = d
@@ -83,6 +84,9 @@ def lib():
         L.oc_set_threads.argtypes = [ctypes.c_int]
         L.oc_limiter.argtypes = [ctypes.c_int, d, d]
         L.oc_limiter.restype = d
+        L.oc_char_basis.argtypes = [d, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        L.oc_invert.argtypes = [ctypes.c_int, vp, vp]
+        L.oc_invert.restype = ctypes.c_int
         L.oc_get_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -107,11 +111,12 @@ def max_threads():
 
 
 def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0, eps=1e-6, split=0, nq=1,
-             limiter=0, musta_k=2):
+             limiter=0, musta_k=2, charw=0):
     """n = (nx, ny, nz); scheme 5 (WENO5), 7 (WENO7) or 2 (MUSTA-FORCE + MUSCL);
     bc 0 outflow / 1 periodic; split 0 global / 1 local Lax-Friedrichs; nq
     conserved charges (state has 4 + nq fields); limiter 0 minmod, 1 MC,
-    2 van Leer, 3 superbee; musta_k MUSTA stages."""
+    2 van Leer, 3 superbee; musta_k MUSTA stages; charw 0 component-wise,
+    1 characteristic-wise WENO."""
     c = Cfg()
     for i in range(3):
         c.n[i] = int(n[i])
@@ -126,6 +131,7 @@ def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0
     c.nq = int(nq)
     c.limiter = int(limiter)
     c.musta_k = int(musta_k)
+    c.charw = int(charw)
     return c
 
 
@@ -156,14 +162,14 @@ def prim2con(w, cs2=1.0 / 3.0):
 
 
 def flux(d, u, cs2=1.0 / 3.0):
-    """Physical flux f_d(u) of one cell (u: 5 conserved values)."""
-    u = _c(u)
-    w = np.empty(5)
+    """Physical flux f_d(u) of one cell (u: 4 + q conserved values, q >= 1)."""
+    u = _c(u).reshape(-1)
+    w = np.empty(max(8, u.size))
     rc = lib().oc_con2prim(cs2, _ptr(u), _ptr(w))
     if rc:
         raise ValueError("unphysical state")
-    f = np.empty(5)
-    lib().oc_flux(cs2, int(d), _ptr(u), _ptr(w), _ptr(f))
+    f = np.empty(u.size)
+    lib().oc_flux_n(cs2, int(d), u.size, _ptr(u), _ptr(w), _ptr(f))
     return f
 
 
@@ -173,6 +179,27 @@ def eigen(d, w, cs2=1.0 / 3.0):
     lam = np.empty(2)
     lib().oc_eigen(cs2, int(d), _ptr(w), _ptr(lam))
     return lam
+
+
+def char_basis(d, w, cs2=1.0 / 3.0):
+    """(R, lam): right eigenvectors of df_d/du (columns; sound -, sound +,
+    shear t1, shear t2, charges) at primitives w = (e, vx, vy, vz, n_1..n_q),
+    and their eigenvalues."""
+    w = _c(w)
+    nf = w.size
+    Rm = np.empty((nf, nf))
+    lam = np.empty(nf)
+    lib().oc_char_basis(cs2, int(d), nf, _ptr(w), _ptr(Rm), _ptr(lam))
+    return Rm, lam
+
+
+def invert(A):
+    """Inverse by the oracle's Gauss-Jordan elimination (partial pivoting)."""
+    A = _c(A)
+    out = np.empty_like(A)
+    if lib().oc_invert(A.shape[0], _ptr(A), _ptr(out)):
+        raise ValueError("singular matrix")
+    return out
 
 
 def weno_left(r, v, eps=1e-6):

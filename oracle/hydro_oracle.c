@@ -44,6 +44,15 @@
  * stages the local states are advanced as a predictor (u_L -= r (F - f_L),
  * u_R -= r (f_R - F)).  If the Lax-Wendroff state is unphysical the stage
  * flux is F_LF; if a predicted state is unphysical the iteration stops.
+ * Characteristic-wise variant (charw = 1, with global LF): at the face
+ * j+1/2 along d the split fluxes of both stencils are projected on the
+ * characteristic fields of the face state -- the primitives of the mean of
+ * the conserved states of cells j and j+1 -- with the left eigenvectors
+ * L = R^-1 of df_d/du there; every field is reconstructed as above and the
+ * face flux is R times the reconstructed fields.  R (oc_char_basis) is
+ * derived in closed form, each column the change of u for a unit change of
+ * e (sound waves), of one transverse velocity (shear waves) or of one
+ * charge density; L comes from Gauss-Jordan elimination (oc_invert).
  * Local Lax-Friedrichs variant (split = 1): the face j+1/2 along d uses
  * alpha = max over the 2r cells j-r+1 .. j+r (the union of both biased
  * stencils) of max(|lambda_-|, |lambda_+|) along d; the time step still uses
@@ -71,7 +80,7 @@ typedef struct {
     int32_t nq;        /* conserved charge densities R_1..R_nq (0 or 1: one) */
     int32_t limiter;   /* MUSCL slope limiter: 0 minmod, 1 MC, 2 van Leer, 3 superbee */
     int32_t musta_k;   /* MUSTA stages (>= 1; 1 is plain FORCE) */
-    int32_t pad_;
+    int32_t charw;     /* WENO on: 0 the components of u, 1 the characteristic fields */
     double dx[3];      /* cell sizes |e_i| */
     double cs2;        /* EOS p = cs2 * e */
     double cfl;
@@ -156,6 +165,91 @@ void oc_eigen(double k, int d, const double *w, double *lam)
     const double den = 1.0 - k * v2;
     lam[0] = (vd * (1.0 - k) - root) / den;
     lam[1] = (vd * (1.0 - k) + root) / den;
+}
+
+/* Right eigenvectors of the flux Jacobian A_d = df_d/du at the primitive
+ * state w = (e, v, n_1..n_q), as the columns of Rm (nf x nf, row-major,
+ * rows E, M_x, M_y, M_z, R_1..R_q).  Each column is the change of u that
+ * belongs to a unit change of one primitive quantity along one wave family,
+ * derived from dF = lambda dU for T^{mu nu} of an ideal fluid with p = k e
+ * (h = (1+k) e, K = h gamma^2, Q = d(K) = gamma^2 dh + 2 h gamma^4 v.dv):
+ *   col 0, 1  sound waves lambda_-, lambda_+ (oc_eigen), de = 1:
+ *             dv_d = k (1 - lambda v_d) / (K (lambda - v_d)),
+ *             dv_t = -lambda k v_t / (K (lambda - v_d)) (t != d),
+ *             dE = Q - k, dM_i = Q v_i + K dv_i, dR_q = R_q dv_d / (lambda - v_d);
+ *   col 2, 3  shear waves along t1 = (d+1)%3, t2 = (d+2)%3, lambda = v_d,
+ *             dv_t = 1 (de = dv_d = 0, dn = 0): Q = 2 h gamma^4 v_t,
+ *             dE = Q, dM_i = Q v_i + K delta_it, dR_q = n_q gamma^3 v_t;
+ *   col 4+q   charge q, lambda = v_d, dn_q = 1: dR_q = gamma, all else 0.
+ * lam (optional) receives the eigenvalue of every column.  The normalisation
+ * (unit primitive change) fixes the scale of the characteristic fields. */
+void oc_char_basis(double k, int d, int nf, const double *w, double *Rm, double *lam)
+{
+    const double e = w[0], v[3] = {w[1], w[2], w[3]};
+    const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const double g2 = 1.0 / (1.0 - v2), gam = sqrt(g2);
+    const double h = (1.0 + k) * e, K = h * g2;
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    double ls[2];
+    oc_eigen(k, d, w, ls);
+    for (int i = 0; i < nf * nf; ++i) Rm[i] = 0.0;
+    for (int s = 0; s < 2; ++s) {                 /* sound waves */
+        const double l = ls[s];
+        double dv[3];
+        dv[d] = k * (1.0 - l * v[d]) / (K * (l - v[d]));
+        dv[t1] = -l * k * v[t1] / (K * (l - v[d]));
+        dv[t2] = -l * k * v[t2] / (K * (l - v[d]));
+        const double vdv = v[0] * dv[0] + v[1] * dv[1] + v[2] * dv[2];
+        const double Q = g2 * (1.0 + k) + 2.0 * h * g2 * g2 * vdv;
+        Rm[0 * nf + s] = Q - k;
+        for (int i = 0; i < 3; ++i) Rm[(1 + i) * nf + s] = Q * v[i] + K * dv[i];
+        for (int q = 4; q < nf; ++q) Rm[q * nf + s] = w[q] * gam * dv[d] / (l - v[d]);
+    }
+    const int ts[2] = {t1, t2};
+    for (int s = 0; s < 2; ++s) {                 /* shear waves */
+        const int t = ts[s];
+        const double Q = 2.0 * h * g2 * g2 * v[t];
+        Rm[0 * nf + 2 + s] = Q;
+        for (int i = 0; i < 3; ++i) Rm[(1 + i) * nf + 2 + s] = Q * v[i] + (i == t ? K : 0.0);
+        for (int q = 4; q < nf; ++q) Rm[q * nf + 2 + s] = w[q] * gam * g2 * v[t];
+    }
+    for (int q = 4; q < nf; ++q) Rm[q * nf + q] = gam;   /* charges */
+    if (lam) {
+        lam[0] = ls[0];
+        lam[1] = ls[1];
+        for (int c = 2; c < nf; ++c) lam[c] = v[d];
+    }
+}
+
+/* Inverse of the nf x nf matrix A (row-major) by Gauss-Jordan elimination
+ * with partial pivoting.  Returns nonzero if a pivot vanishes. */
+int oc_invert(int nf, const double *A, double *Ainv)
+{
+    double M[MAXF][2 * MAXF];
+    for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < 2 * nf; ++j) M[i][j] = j < nf ? A[i * nf + j] : (j - nf == i ? 1.0 : 0.0);
+    for (int c = 0; c < nf; ++c) {
+        int piv = c;
+        for (int i = c + 1; i < nf; ++i)
+            if (fabs(M[i][c]) > fabs(M[piv][c])) piv = i;
+        if (!(fabs(M[piv][c]) > 0.0)) return 1;
+        if (piv != c)
+            for (int j = 0; j < 2 * nf; ++j) {
+                const double t = M[c][j];
+                M[c][j] = M[piv][j];
+                M[piv][j] = t;
+            }
+        const double pv = M[c][c];
+        for (int j = 0; j < 2 * nf; ++j) M[c][j] /= pv;
+        for (int i = 0; i < nf; ++i) {
+            if (i == c) continue;
+            const double f = M[i][c];
+            for (int j = 0; j < 2 * nf; ++j) M[i][j] -= f * M[c][j];
+        }
+    }
+    for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < nf; ++j) Ainv[i * nf + j] = M[i][nf + j];
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -303,6 +397,7 @@ static int cfg_ok(const oc_cfg *c)
     if (c->r != 1 && c->r != 3 && c->r != 4) return 0;
     if (c->r == 1 && (c->limiter < 0 || c->limiter > 3 || c->musta_k < 1 || c->split != 0 || c->nq > 1)) return 0;
     if (c->split != 0 && c->split != 1) return 0;
+    if (c->charw != 0 && (c->charw != 1 || c->r == 1)) return 0;
     if (c->nq < 0 || c->nq > MAXF - 4) return 0;
     if (!(c->cs2 > 0 && c->cs2 < 1) || !(c->eps > 0)) return 0;
     for (int d = 0; d < 3; ++d)
@@ -507,6 +602,40 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
                             vm[i] = 0.5 * (fr[k * len + b] - af * ur[k * len + b]);
                         }
                         F[k * (nd + 1) + s] = oc_weno_left(r, vp, c->eps) + weno_right(r, vm, c->eps);
+                    }
+                    continue;
+                }
+                if (c->charw == 1) {
+                    /* characteristic fields at the face state: the mean of the
+                     * conserved states of the two cells beside the face */
+                    double ub[MAXF], wb[MAXF], Rm[MAXF * MAXF], Lm[MAXF * MAXF], Fc[MAXF];
+                    for (int k = 0; k < NF; ++k) ub[k] = 0.5 * (ur[k * len + j] + ur[k * len + j + 1]);
+                    if (oc_con2prim(c->cs2, ub, wb)) {
+                        bad |= 1;
+                        continue;
+                    }
+                    for (int q = 5; q < NF; ++q) wb[q] = ub[q] * sqrt(1.0 - (wb[1] * wb[1] + wb[2] * wb[2] + wb[3] * wb[3]));
+                    oc_char_basis(c->cs2, d, NF, wb, Rm, NULL);
+                    if (oc_invert(NF, Rm, Lm)) {
+                        bad |= 1;
+                        continue;
+                    }
+                    for (int ch = 0; ch < NF; ++ch) {
+                        double vp[7], vm[7];
+                        for (int i = 0; i < 2 * r - 1; ++i) {
+                            vp[i] = 0.0;
+                            vm[i] = 0.0;
+                            for (int k = 0; k < NF; ++k) {
+                                vp[i] += Lm[ch * NF + k] * fp[k * len + j - r + 1 + i];
+                                vm[i] += Lm[ch * NF + k] * fm[k * len + j - r + 2 + i];
+                            }
+                        }
+                        Fc[ch] = oc_weno_left(r, vp, c->eps) + weno_right(r, vm, c->eps);
+                    }
+                    for (int k = 0; k < NF; ++k) {
+                        double acc = 0.0;
+                        for (int ch = 0; ch < NF; ++ch) acc += Rm[k * NF + ch] * Fc[ch];
+                        F[k * (nd + 1) + s] = acc;
                     }
                     continue;
                 }

@@ -640,3 +640,132 @@ def test_musta_sod_and_weno_is_sharper(oracle_lib, limiter):
                 ew = np.abs(oracle_lib.con2prim(uw)[0].ravel() - e_ex)[shock].sum()
                 assert ew < em, (scheme, ew, em)
     assert errs[0] > errs[1] > errs[2], errs
+
+
+# ---------------------------------------------------------------- characteristic-wise WENO
+def _fd_jacobian_action(oracle_lib, d, u, r, h=1e-6):
+    """(f_d(u + h r) - f_d(u - h r)) / 2h: the flux Jacobian applied to r,
+    by central differences of the flux of Eq. 1."""
+    return (oracle_lib.flux(d, u + h * r) - oracle_lib.flux(d, u - h * r)) / (2 * h)
+
+
+@pytest.mark.parametrize("nq", [1, 2, 3])
+def test_char_basis_is_the_eigenbasis(oracle_lib, nq):
+    """Each column r_c of the right-eigenvector matrix satisfies A_d r_c =
+    lambda_c r_c for the Jacobian of the flux (checked by finite differences),
+    with its declared normalisation (a unit change of e, v_t or n_q, checked
+    by finite differences of the primitive recovery); the sound speeds equal
+    oc_eigen's; the oracle's inverse is the left-eigenvector matrix."""
+    rng = np.random.default_rng(40 + nq)
+    _, v, _ = rand_prims(rng, 12)
+    for i in range(12):
+        vv = v[i] * min(1.0, 0.9 / max(np.linalg.norm(v[i]), 1e-300))   # |v| <= 0.9
+        w = np.concatenate([[rng.uniform(0.3, 3.0)], vv, rng.uniform(0.2, 2.0, nq)])
+        nf = 4 + nq
+        u = oracle_lib.prim2con(w.reshape(nf, 1, 1, 1).copy()).reshape(nf)
+        for d in range(3):
+            Rm, lam = oracle_lib.char_basis(d, w)
+            np.testing.assert_array_equal(lam[:2], oracle_lib.eigen(d, w[:5]))
+            assert np.all(lam[2:] == w[1 + d])
+            for c in range(nf):
+                Ar = _fd_jacobian_action(oracle_lib, d, u, Rm[:, c])
+                assert np.abs(Ar - lam[c] * Rm[:, c]).max() < 1e-8 * np.abs(Rm[:, c]).max(), (d, c)
+                wp = oracle_lib.con2prim((u + 1e-6 * Rm[:, c]).reshape(nf, 1, 1, 1).copy()).reshape(nf)
+                wm = oracle_lib.con2prim((u - 1e-6 * Rm[:, c]).reshape(nf, 1, 1, 1).copy()).reshape(nf)
+                dw = (wp - wm) / 2e-6
+                want = np.zeros(nf)
+                if c < 2:
+                    want[0] = 1.0                       # sound: unit change of e
+                    dw[1:], want[1:] = 0.0, 0.0         # (v, n follow from the wave)
+                elif c < 4:
+                    want[1 + (d + c - 1) % 3] = 1.0     # shear: unit change of v_t
+                else:
+                    want[c] = 1.0                       # charge q: unit change of n_q
+                assert np.abs(dw - want).max() < 1e-7, (d, c, dw)
+            Lm = oracle_lib.invert(Rm)
+            np.testing.assert_allclose(Lm, np.linalg.inv(Rm), rtol=1e-10, atol=1e-12 * np.abs(Lm).max())
+            assert np.abs(Lm @ Rm - np.eye(nf)).max() < 1e-11
+
+
+def test_char_basis_at_rest(oracle_lib):
+    """At v = 0 the waves decouple: sound (dE, dM_d) = (1, -+c_s) with
+    dR = n / h, shear dM_t = h = (1 + c_s^2) e, charges dR_q = 1."""
+    e, n = 2.5, 0.7
+    h, cs = (1 + K) * e, np.sqrt(K)
+    for d in range(3):
+        Rm, lam = oracle_lib.char_basis(d, np.array([e, 0, 0, 0, n]))
+        want = np.zeros((5, 5))
+        want[0, 0] = want[0, 1] = 1.0
+        want[1 + d, 0], want[1 + d, 1] = -cs, cs
+        want[4, 0] = want[4, 1] = n / h
+        want[1 + (d + 1) % 3, 2] = h
+        want[1 + (d + 2) % 3, 3] = h
+        want[4, 4] = 1.0
+        np.testing.assert_allclose(Rm, want, rtol=1e-15, atol=1e-15)
+        np.testing.assert_allclose(lam, [-cs, cs, 0, 0, 0], atol=1e-16)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_charwise_with_linear_weights_is_componentwise(oracle_lib, scheme):
+    """With the linear WENO weights (epsilon so large that every
+    omega_k = d_k) the reconstruction is linear, so projecting on the
+    characteristic fields and back changes nothing: characteristic- and
+    component-wise L agree to round-off.  Pins the stencil alignment of the
+    projection and that the back-projection inverts it."""
+    g, w = W.smooth_periodic(n=(9, 8, 7), amp=0.3, vamp=0.5, seed=21, scheme=scheme)
+    u = oracle_lib.prim2con(w)
+    c0 = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=(1, 1, 1), eps=1e30)
+    c1 = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=(1, 1, 1), eps=1e30, charw=1)
+    a = oracle_lib.alpha(c0, u)
+    L0, L1 = oracle_lib.L(c0, u, a), oracle_lib.L(c1, u, a)
+    assert np.abs(L1 - L0).max() < 1e-11 * np.abs(L0).max()
+    c2 = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=(1, 1, 1), charw=1)
+    assert np.abs(oracle_lib.L(c2, u, a) - L0).max() > 1e-9 * np.abs(L0).max()   # nonlinear weights do differ
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_charwise_conserves_and_follows_boundary_rule(oracle_lib, scheme):
+    g, w = W.smooth_periodic(n=(10, 9, 8), amp=0.3, vamp=0.4, seed=5, scheme=scheme)
+    u0 = oracle_lib.prim2con(w)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, bc=(1, 1, 1), cfl=0.4, charw=1)
+    u1, t, k = oracle_lib.run(c, u0, 4)
+    scale = np.abs(u0).reshape(5, -1).sum(1).max()
+    assert k == 4 and np.abs(u1.reshape(5, -1).sum(1) - u0.reshape(5, -1).sum(1)).max() < 1e-13 * scale
+    G = (scheme + 1) // 2
+    gl, wl = W.lumpy(n=(9, 8, 7), seed=31, scheme=scheme)
+    wl[1] = 0.3 * np.tanh(wl[0] - 2)
+    ul = oracle_lib.prim2con(wl)
+    for bc, mode in ((0, "edge"), (1, "wrap")):
+        cb = oracle_lib.make_cfg(gl.n, gl.dx, scheme=scheme, bc=(bc,) * 3, charw=1)
+        a = oracle_lib.alpha(cb, ul)
+        up = np.pad(ul, ((0, 0), (G, G), (G, G), (G, G)), mode=mode)
+        cp = oracle_lib.make_cfg(tuple(k + 2 * G for k in gl.n), gl.dx, scheme=scheme, bc=(1 - bc,) * 3, charw=1)
+        assert np.array_equal(oracle_lib.L(cp, up, a)[:, G:-G, G:-G, G:-G], oracle_lib.L(cb, ul, a))
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_charwise_sod_has_fewer_oscillations(oracle_lib, scheme):
+    """Sod tube: characteristic-wise WENO keeps the plateaus and the L1 error
+    of the component-wise scheme (within 3%) but removes most of its spurious
+    oscillations -- the excess total variation of e, v and n over the exact
+    solution falls at least threefold, and the velocity overshoot at least
+    twofold."""
+    ex = SodExact()
+    g, w = W.sod(N=400, scheme=scheme)
+    x = g.centres()[0].ravel()
+    e_ex, v_ex, n_ex = ex(x, 0.4)
+    tv = lambda a: np.abs(np.diff(a)).sum()   # noqa: E731
+    out = {}
+    for cw in (0, 1):
+        c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, cfl=g.cfl, charw=cw)
+        u, t, k = oracle_lib.run(c, oracle_lib.prim2con(w), 100000, t_end=0.4)
+        assert t == pytest.approx(0.4, abs=1e-15)
+        p = oracle_lib.con2prim(u)
+        e, v, n = p[0].ravel(), p[1].ravel(), p[4].ravel()
+        out[cw] = dict(l1=np.abs(e - e_ex).mean(), tv=[tv(e) - tv(e_ex), tv(v) - tv(v_ex), tv(n) - tv(n_ex)],
+                       over=v.max() - ex.v_star)
+        mid = (x > ex.xi_tail * 0.4 + 0.03) & (x < ex.V_shock * 0.4 - 0.03)
+        assert np.abs(e[mid] / ex.e_star - 1).max() < 0.01
+    assert out[1]["l1"] < 1.03 * out[0]["l1"], out
+    assert all(a * 3 < b for a, b in zip(out[1]["tv"], out[0]["tv"])), out
+    assert 2 * out[1]["over"] < out[0]["over"], out

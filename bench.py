@@ -525,6 +525,27 @@ def main():
                                  / (float(kl[1:4].sum()) / 9 * 1e-3) / 1e12 / fp64_peak}
         hl.close()
     if not args.no_extra:
+        # characteristic-wise WENO (global LF), same workload and scheme
+        gc, wc = workload(args.scheme, args.grid)
+        gc.charwise = 1
+        hc = Hydro.from_grid(gc, stream=stream)
+        hc.set_primitive(torch.from_numpy(wc).to(dev))
+        hc.autotune()
+        hc.step(3)
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        kc = hc.profile_step(3)
+        a1.record(stream)
+        barrier()
+        hc.sync()
+        elc = a0.elapsed_time(a1) / 1e3
+        extra["charwise_%d" % args.grid] = {"value": cells * 3 / elc, "unit": "cell-updates/s", "steps": 3,
+                                            "ms_per_step": 1e3 * elc / 3, "launch": hc.launch(),
+                                            "stage_kernel_ms": float(kc[1:4].sum()) / 9,
+                                            "over_componentwise": (float(kc[1:4].sum()) / 9) / stage_ms}
+        hc.close()
+    if not args.no_extra:
         # three conserved charges (state of 7 fields), same workload and scheme
         import workloads as W
         gq, wq = workload(args.scheme, args.grid)

@@ -101,7 +101,15 @@ typedef struct {
                            local ratio dt/dx = 0.9 / max|lambda| of the local
                            states.  Ignored by WENO.  MUSTA-FORCE runs on the
                            single-grid path with split = 0, nq <= 1 */
-    int32_t reserved3;  /* must be 0 */
+    int32_t charwise;   /* WENO reconstruction: 0 = component-wise (on each
+                           field of the split fluxes), 1 = characteristic-wise:
+                           at each face the split fluxes are projected on the
+                           characteristic fields of df_d/du at the mean of the
+                           two neighbouring states, reconstructed there and
+                           mapped back (Sec. 1.2 leaves this choice open).
+                           1 needs WENO with split = 0; it runs on the
+                           single-grid and z-slab paths, not the adjoint, the
+                           batch or hydro_step_noalloc */
     double dx[3];       /* cell sizes |e_i| > 0 */
     double origin[3];   /* lower corner of the box (informational) */
     double cs2;         /* EOS p = cs2 * e, 0 < cs2 < 1 (1/3 in the paper's tests) */
@@ -176,6 +184,9 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
  * built-in wave-count heuristic), rebuilding the step graph.  Results do not
  * depend on the choice beyond FMA-level rounding of the same formulas. */
 int32_t hydro_launch_variants(int32_t scheme, int32_t split, int32_t nq);
+/* The same count for a full configuration (characteristic-wise WENO has its
+ * own tile shapes); 0 for an invalid configuration. */
+int32_t hydro_launch_variants_cfg(const hydro_config* cfg);
 hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc);
 hydro_status hydro_get_launch(hydro_t* h, int32_t* variant, int32_t* tile_x, int32_t* tile_y, int32_t* zc);
 

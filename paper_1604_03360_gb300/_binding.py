@@ -35,7 +35,7 @@ class HydroConfig(ctypes.Structure):
         ("nq", ctypes.c_int32),
         ("limiter", ctypes.c_int32),
         ("musta_stages", ctypes.c_int32),
-        ("reserved3", ctypes.c_int32),
+        ("charwise", ctypes.c_int32),
         ("dx", ctypes.c_double * 3),
         ("origin", ctypes.c_double * 3),
         ("cs2", ctypes.c_double),
@@ -46,7 +46,7 @@ class HydroConfig(ctypes.Structure):
 
 
 def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
-                origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2):
+                origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2, charwise=0):
     c = HydroConfig()
     for i in range(3):
         c.n[i] = int(n[i])
@@ -58,7 +58,7 @@ def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=
     c.nq = int(nq)
     c.limiter = int(limiter)
     c.musta_stages = int(musta_stages)
-    c.reserved3 = 0
+    c.charwise = int(charwise)
     c.cs2 = float(cs2)
     c.cfl = float(cfl)
     c.dt_fixed = float(dt_fixed)
@@ -92,6 +92,7 @@ def lib():
         "hydro_profile_step": ([vp, i32, d, P(d)], i32),
         "hydro_last_error": ([vp], ctypes.c_char_p),
         "hydro_launch_variants": ([i32, i32, i32], i32),
+        "hydro_launch_variants_cfg": ([P(HydroConfig)], i32),
         "hydro_set_launch": ([vp, i32, i32], i32),
         "hydro_get_launch": ([vp, P(i32), P(i32), P(i32), P(i32)], i32),
         "hydro_autotune": ([vp, P(d)], i32),
@@ -186,9 +187,10 @@ class Hydro:
     """One grid of the FP64 WENO5/WENO7 + SSP-RK3 solver (hydro_t)."""
 
     def __init__(self, n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
-                 origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2, stream=None):
+                 origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2, charwise=0, stream=None):
         self._L = lib()
-        self.cfg = make_config(n, dx, scheme, bc, cs2, cfl, dt_fixed, eps, origin, split, nq, limiter, musta_stages)
+        self.cfg = make_config(n, dx, scheme, bc, cs2, cfl, dt_fixed, eps, origin, split, nq, limiter, musta_stages,
+                               charwise)
         self.n = tuple(int(k) for k in n)
         self.shape = (4 + max(1, int(nq)), self.n[2], self.n[1], self.n[0])
         h = ctypes.c_void_p()
@@ -204,7 +206,8 @@ class Hydro:
         """Create from a workloads.Grid description."""
         return cls(g.n, g.dx, scheme=g.scheme, bc=g.bc, cs2=g.cs2, cfl=g.cfl, eps=g.eps, origin=g.origin,
                    dt_fixed=getattr(g, "dt_fixed", 0.0), split=getattr(g, "split", 0), nq=getattr(g, "nq", 1),
-                   limiter=getattr(g, "limiter", 0), musta_stages=getattr(g, "musta_stages", 2), stream=stream)
+                   limiter=getattr(g, "limiter", 0), musta_stages=getattr(g, "musta_stages", 2),
+                   charwise=getattr(g, "charwise", 0), stream=stream)
 
     def _check(self, rc):
         if rc:
@@ -370,7 +373,8 @@ class HydroBatch:
         arr = (HydroConfig * len(self.grids))()
         for i, g in enumerate(self.grids):
             arr[i] = make_config(g.n, g.dx, g.scheme, g.bc, g.cs2, g.cfl, getattr(g, "dt_fixed", 0.0), g.eps,
-                                 g.origin, getattr(g, "split", 0), getattr(g, "nq", 1))
+                                 g.origin, getattr(g, "split", 0), getattr(g, "nq", 1), getattr(g, "limiter", 0),
+                                 getattr(g, "musta_stages", 2), getattr(g, "charwise", 0))
         h = ctypes.c_void_p()
         rc = self._L.hydro_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.grids), _stream_handle(stream),
                                         ctypes.byref(h))

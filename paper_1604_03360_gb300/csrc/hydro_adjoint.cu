@@ -472,6 +472,8 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     if (v.cfg.split != 0)
         return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint needs global Lax-Friedrichs splitting (split = 0)");
     if (v.cfg.nq > 1) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint supports one charge (nq <= 1)");
+    if (v.cfg.charwise)
+        return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint differentiates component-wise WENO only");
     if (v.cfg.scheme == HYDRO_MUSTA_FORCE)
         return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint differentiates the WENO schemes only");
     if (v.cfg.bc[2] == HYDRO_BC_HALO)

@@ -187,7 +187,7 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
     if ((e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev)) != cudaSuccess)
         return bail(cuda_fail(h, e, "device attribute"));
     h->nf = state_fields(*cfg);
-    if ((e = stage_launch_variant(h->R, cfg->split, cfg->nq, 0, &h->L)) != cudaSuccess)
+    if ((e = stage_launch_variant(h->R, cfg->split, cfg->nq, 0, &h->L, cfg->charwise)) != cudaSuccess)
         return bail(cuda_fail(h, e, "stage kernel setup"));
     h->G = h->R;
     h->ncell = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
@@ -474,7 +474,7 @@ __global__ void set_dt_kernel(Ctl* c, double dt) { c->dt = dt; }
 static hydro_status apply_launch(hydro_t* h, int variant, int zc)
 {
     StageLaunch L{};
-    cudaError_t e = stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, variant, &L);
+    cudaError_t e = stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, variant, &L, h->cfg.charwise);
     if (e == cudaErrorInvalidValue) return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     CK(h, e, "stage kernel setup");
     CK(h, cudaStreamSynchronize(h->stream), "synchronize");
@@ -491,8 +491,8 @@ static hydro_status apply_launch(hydro_t* h, int variant, int zc)
 static std::string tune_key(const hydro_t* h)
 {
     char b[96];
-    snprintf(b, sizeof b, "%d %d %d %d", h->R * 10 + h->cfg.split + 100 * h->cfg.nq, h->cfg.n[0], h->cfg.n[1],
-             h->cfg.n[2]);
+    snprintf(b, sizeof b, "%d %d %d %d", h->R * 10 + h->cfg.split + 100 * h->cfg.nq + 1000 * h->cfg.charwise,
+             h->cfg.n[0], h->cfg.n[1], h->cfg.n[2]);
     return b;
 }
 
@@ -540,10 +540,16 @@ extern "C" int32_t hydro_launch_variants(int32_t scheme, int32_t split, int32_t 
     return 0;
 }
 
+extern "C" int32_t hydro_launch_variants_cfg(const hydro_config* cfg)
+{
+    if (!check_config(cfg).empty()) return 0;
+    return launch_variant_count(scheme_R(cfg->scheme), cfg->split, cfg->nq, cfg->charwise);
+}
+
 extern "C" hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc)
 {
     if (!h) return HYDRO_ERR_INVALID_ARG;
-    if (variant < 0 || variant >= hydro_launch_variants(h->cfg.scheme, h->cfg.split, h->cfg.nq))
+    if (variant < 0 || variant >= hydro_launch_variants_cfg(&h->cfg))
         return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     return apply_launch(h, variant, zc);
 }
@@ -564,7 +570,7 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
     if (h->cfg.bc[2] == HYDRO_BC_HALO) return fail(h, HYDRO_ERR_INVALID_ARG, "hydro_autotune runs whole grids (no z halo)");
     if (!h->have_state) return fail(h, HYDRO_ERR_STATE, "no state loaded");
     int cv = 0, cz = 0;
-    if (tune_cache_lookup(h, &cv, &cz) && cv >= 0 && cv < hydro_launch_variants(h->cfg.scheme, h->cfg.split, h->cfg.nq)) {
+    if (tune_cache_lookup(h, &cv, &cz) && cv >= 0 && cv < hydro_launch_variants_cfg(&h->cfg)) {
         if (best_ms) *best_ms = -1.0;
         return apply_launch(h, cv, cz);
     }
@@ -577,9 +583,9 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
     const int nz = h->cfg.n[2];
     // a positive dt makes the stage kernel run; it only writes stage-1 scratch
     set_dt_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 1e-300);
-    for (int v = 0; v < hydro_launch_variants(h->cfg.scheme, h->cfg.split, h->cfg.nq) && st == HYDRO_OK; ++v) {
+    for (int v = 0; v < hydro_launch_variants_cfg(&h->cfg) && st == HYDRO_OK; ++v) {
         StageLaunch L{};
-        if (stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, v, &L) != cudaSuccess) continue;
+        if (stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, v, &L, h->cfg.charwise) != cudaSuccess) continue;
         // z chunks: balanced splits ceil(nz/k) and a fixed ladder; time the five
         // the wave-count model likes best
         std::vector<int> zs;

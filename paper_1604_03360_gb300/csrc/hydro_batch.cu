@@ -343,6 +343,8 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path runs the WENO schemes only");
         if (cfgs[e].nq > 1)
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path supports one charge (nq <= 1)");
+        if (cfgs[e].charwise)
+            return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path runs component-wise WENO only");
         if (cfgs[e].scheme != cfgs[0].scheme || cfgs[e].split != cfgs[0].split)
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "all events of a batch must use the same scheme and splitting");
     }

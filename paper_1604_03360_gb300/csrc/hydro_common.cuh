@@ -98,8 +98,11 @@ struct StageLaunch {
 // stage_launch_variant returns cudaErrorInvalidValue for a variant that does
 // not exist.  split: 0 global, 1 local Lax-Friedrichs.
 // nq: number of charges (state fields = 4 + nq).
-int launch_variant_count(int R, int split, int nq);
-cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out);
+// charw: characteristic-wise reconstruction (hydro_char.cu; split must be 0).
+int launch_variant_count(int R, int split, int nq, int charw = 0);
+cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out, int charw = 0);
+int char_variant_count(int R, int nq);
+cudaError_t char_launch_variant(int R, int nq, int v, StageLaunch* out);
 inline cudaError_t stage_launch_info(int R, StageLaunch* out) { return stage_launch_variant(R, 0, 1, 0, out); }
 inline int state_fields(const hydro_config& c) { return 4 + (c.nq > 1 ? c.nq : 1); }
 // internal scheme code: 3 WENO5, 4 WENO7, 2 MUSTA-FORCE (the ghost width)

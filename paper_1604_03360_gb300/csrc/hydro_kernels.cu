@@ -151,8 +151,9 @@ static cudaError_t info_for(StageLaunch* out)
 // Local LF (raw staging, 2G-plane ring): WENO5 16x16 and 16x8; WENO7 16x8
 // (16x16 would need 247 KB of shared memory).
 // Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
-int launch_variant_count(int R, int split, int nq)
+int launch_variant_count(int R, int split, int nq, int charw)
 {
+    if (charw) return (R == 3 || R == 4) && split == 0 ? char_variant_count(R, nq) : 0;
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 2 : 1;
@@ -181,8 +182,9 @@ static cudaError_t musta_info_for(StageLaunch* out)
 }
 
 // R == 2 denotes MUSTA-FORCE + MUSCL (two ghost cells): 16x16 and 16x8 tiles.
-cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out)
+cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out, int charw)
 {
+    if (charw) return split == 0 ? char_launch_variant(R, nq, v, out) : cudaErrorInvalidValue;
     if (R == 2) {
         if (split != 0 || nq > 1) return cudaErrorInvalidValue;
         if (v == 0) return musta_info_for<16, 16>(out);
@@ -243,7 +245,9 @@ std::string check_config(const hydro_config* c)
     if (!(c->dt_fixed > 0.0) && !(c->cfl > 0.0)) return "need cfl > 0 or dt_fixed > 0";
     if (c->split != 0 && c->split != 1) return "split must be 0 (global) or 1 (local Lax-Friedrichs)";
     if (c->nq < 0 || c->nq > 3) return "nq (number of charges) must be 0..3";
-    if (c->reserved3 != 0) return "reserved3 must be 0";
+    if (c->charwise != 0 && c->charwise != 1) return "charwise must be 0 (component-wise) or 1 (characteristic-wise)";
+    if (c->charwise && (c->scheme == HYDRO_MUSTA_FORCE || c->split != 0))
+        return "characteristic-wise reconstruction needs WENO with global Lax-Friedrichs splitting (split = 0)";
     return std::string();
 }
 

@@ -28,7 +28,14 @@
 // staged raw -- flux f, state u and that cell's speed s (kept from the
 // previous stage's epilogue) -- and every face forms g+- = f +- alpha_face u
 // itself.  The z ring then holds 2G planes and each z face is computed whole.
+//
+// Characteristic-wise variant (CHW, global LF): cells are staged as in the
+// component-wise scheme (g+ and g-), but every face is one work item that
+// projects its 2G-cell window on the characteristic fields of the face state
+// (char_weno.cuh), reconstructs them and maps the result back, all fields at
+// once.  The z ring holds 2G planes, as for local LF.
 #pragma once
+#include "char_weno.cuh"
 #include "hydro_math.cuh"
 
 namespace hydro {
@@ -74,11 +81,11 @@ __device__ __forceinline__ int bc_map(int i, int n, int bc)
     return i < 0 ? 0 : n - 1;
 }
 
-template <int R, int TX, int TY, bool LLF = false, int NF = 5>
+template <int R, int TX, int TY, bool LLF = false, int NF = 5, bool CHW = false>
 struct StageSmem {
     static constexpr int G = R, S = 2 * R - 1, NT = TX * TY;
     static constexpr int NV = LLF ? 2 * NF + 1 : 2 * NF;     // staged values per cell
-    static constexpr int NRING = LLF ? 2 * R : 2 * R - 1;    // z planes kept per column
+    static constexpr int NRING = (LLF || CHW) ? 2 * R : 2 * R - 1;    // z planes kept per column
     static constexpr int GXW = TX + 2 * G, GYH = TY + 2 * G;
     static constexpr int RING = NRING * NV * NT;
     static constexpr int GX = NV * TY * GXW;
@@ -151,10 +158,11 @@ __device__ __forceinline__ double llf_face(const double* f, const double* u, con
 
 // One work item: column tile (tile_x, tile_y) of TX x TY cells and z chunk chunk_z of the
 // grid described by a.  All threads of the CTA call it with the same item.
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
 {
-    using SM = StageSmem<R, TX, TY, LLF, NF>;
+    static_assert(!(LLF && CHW), "characteristic-wise WENO uses the global Lax-Friedrichs split");
+    using SM = StageSmem<R, TX, TY, LLF, NF, CHW>;
     constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING, NV = SM::NV;
     constexpr int GXW = SM::GXW, GYH = SM::GYH;
     double* ring = smem;
@@ -235,6 +243,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         weno_right<R>(vm, a.eps_s, Nm, Dm);
     };
 
+    // characteristic-wise: the whole z face m+1/2 from planes m-G+1 .. m+G
+    int foz[NF];
+#pragma unroll
+    for (int m = 0; m < NF; ++m) foz[m] = rot_field(m, 2) * NT;
+    auto face_z_chw = [&](int m, double* Fz) {
+        double Fr[NF];
+        auto cell = [&](int i) { return (const double*)(ring + slot_of(m - G + 1 + i) * NV * NT + tid); };
+        const bool ok = char_face<R, NF>(cell, foz, NF * NT, al[2], a.cs2, a.eps_s, Fr);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) Fz[rot_field(k, 2)] = Fr[k];
+        return ok;
+    };
+    bool face_ok = true;
+
     // columns outside the grid (ragged tiles) have no z-faces to compute: their
     // ring is private and nobody reads it
     const bool zwork = zact && own;
@@ -245,6 +267,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         for (int m = zb - G; m <= zb + G - 1; ++m) ingest(m);
 #pragma unroll
         for (int k = 0; k < NF; ++k) Fzm[k] = face_z_llf(zb - 1, k);
+    } else if (zwork && CHW) {
+        for (int m = zb - G; m <= zb + G - 1; ++m) ingest(m);
+        face_ok &= face_z_chw(zb - 1, Fzm);
     } else if (zwork) {
         for (int m = zb - G; m <= zb + G - 2; ++m) ingest(m);
 #pragma unroll
@@ -278,6 +303,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             ingest(p + G);
 #pragma unroll
             for (int k = 0; k < NF; ++k) Fzp[k] = face_z_llf(p, k);
+        } else if (zwork && CHW) {
+            ingest(p + G);
+            face_ok &= face_z_chw(p, Fzp);
         } else if (zwork) {
             ingest(p + G);
 #pragma unroll
@@ -360,7 +388,36 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             }
         };
         const int nitems = nfx + nfy;
-        if constexpr (LLF) {
+        if constexpr (CHW) {
+            // characteristic-wise: one face (all fields) per item
+            const int nx_f = a.act[0] ? nrow * (ncol + 1) : 0;
+            const int ny_f = a.act[1] ? (nrow + 1) * ncol : 0;
+            for (int it = tid; it < nx_f + ny_f; it += NT) {
+                double Fr[NF];
+                int fo[NF];
+                bool ok;
+                if (it < nx_f) {
+                    const int row = it / (ncol + 1), f = it % (ncol + 1);
+                    const double* base = gx + row * GXW + f;
+#pragma unroll
+                    for (int m = 0; m < NF; ++m) fo[m] = rot_field(m, 0) * (TY * GXW);
+                    auto cell = [&](int i) { return base + i; };
+                    ok = char_face<R, NF>(cell, fo, NF * TY * GXW, al[0], a.cs2, a.eps_s, Fr);
+#pragma unroll
+                    for (int m = 0; m < NF; ++m) Fx[(rot_field(m, 0) * TY + row) * (TX + 1) + f] = Fr[m];
+                } else {
+                    const int j = it - nx_f, f = j / ncol, col = j % ncol;
+                    const double* base = gy + f * TX + col;
+#pragma unroll
+                    for (int m = 0; m < NF; ++m) fo[m] = rot_field(m, 1) * (GYH * TX);
+                    auto cell = [&](int i) { return base + i * TX; };
+                    ok = char_face<R, NF>(cell, fo, NF * GYH * TX, al[1], a.cs2, a.eps_s, Fr);
+#pragma unroll
+                    for (int m = 0; m < NF; ++m) Fy[(rot_field(m, 1) * (TY + 1) + f) * TX + col] = Fr[m];
+                }
+                face_ok &= ok;
+            }
+        } else if constexpr (LLF) {
             // local LF: window of 2G raw cells starting at the same place as g+
             for (int it = tid; it < nitems; it += NT) {
                 const double* pp;
@@ -448,6 +505,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 #pragma unroll
         for (int k = 0; k < NF; ++k) Fzm[k] = Fzp[k];
     }
+    if constexpr (CHW) {
+        // a face state that is not physical (only possible next to an
+        // unphysical cell): report it like one
+        if (!face_ok && atomicCAS(a.status, 0, 4) == 0) *a.bad_cell = (long long)zb * plane + (long long)ys * nx + xs;
+    }
     // speeds: warp max, one atomic per warp and axis
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -461,11 +523,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 }
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5>
-__global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 && NF == 5 ? 2 : 1)) stage_kernel(const StageArgs a)
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false>
+__global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 && NF == 5 && !CHW ? 2 : 1))
+    stage_kernel(const StageArgs a)
 {
     extern __shared__ __align__(16) double smem[];
-    stage_tile<R, TX, TY, ILP, LLF, NF>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    stage_tile<R, TX, TY, ILP, LLF, NF, CHW>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 }  // namespace hydro

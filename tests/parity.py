@@ -21,7 +21,8 @@ def oracle_cfg(g, dt_fixed=None):
     dt = getattr(g, "dt_fixed", 0.0) if dt_fixed is None else dt_fixed
     return oracle.make_cfg(g.n, g.dx, cs2=g.cs2, scheme=g.scheme, bc=g.bc, cfl=g.cfl, dt_fixed=dt, eps=g.eps,
                            split=getattr(g, "split", 0), nq=getattr(g, "nq", 1),
-                           limiter=getattr(g, "limiter", 0), musta_k=getattr(g, "musta_stages", 2))
+                           limiter=getattr(g, "limiter", 0), musta_k=getattr(g, "musta_stages", 2),
+                           charw=getattr(g, "charwise", 0))
 
 
 def run_oracle(g, w, nsteps, t0=0.0, t_end=-1.0):

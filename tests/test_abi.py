@@ -41,7 +41,7 @@ def test_version(L):
 
 @pytest.mark.parametrize("field,value,msg", [
     ("scheme", 6, b"scheme"), ("cs2", 1.0, b"cs2"), ("weno_eps", 0.0, b"weno_eps"),
-    ("split", 2, b"split"),
+    ("split", 2, b"split"), ("charwise", 2, b"charwise"),
 ])
 def test_invalid_config_rejected(L, field, value, msg):
     import paper_1604_03360_gb300 as H
@@ -67,3 +67,26 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.hydro_sync(None) == 1
     assert L.hydro_destroy(None) == 0
     assert L.hydro_field_stride(None) == 0
+
+
+def test_charwise_needs_weno_with_global_splitting(L):
+    import paper_1604_03360_gb300 as H
+    for kw in (dict(split=1), dict(scheme=2)):
+        c = H.make_config((8, 8, 8), (0.1, 0.1, 0.1), charwise=1, **kw)
+        h = ctypes.c_void_p()
+        assert L.hydro_create(ctypes.byref(c), None, ctypes.byref(h)) == H._binding.ERR_INVALID_ARG
+        assert b"characteristic" in L.hydro_last_error(None)
+    for scheme, nq, n in ((5, 1, 2), (7, 1, 1), (5, 3, 1), (7, 2, 1)):
+        c = H.make_config((8, 8, 8), (0.1, 0.1, 0.1), scheme=scheme, nq=nq, charwise=1)
+        assert L.hydro_launch_variants_cfg(ctypes.byref(c)) == n
+
+
+def test_halo_slab_needs_g_planes(L):
+    import paper_1604_03360_gb300 as H
+    for scheme, nz in ((5, 2), (7, 3), (2, 1)):
+        c = H.make_config((8, 8, nz), (0.1, 0.1, 0.1), scheme=scheme, bc=(0, 0, H.BC_HALO))
+        h = ctypes.c_void_p()
+        assert L.hydro_create(ctypes.byref(c), None, ctypes.byref(h)) == H._binding.ERR_INVALID_ARG
+        assert b"halo" in L.hydro_last_error(None)
+    c = H.make_config((8, 8, 8), (0.1, 0.1, 0.1), bc=(H.BC_HALO, 0, 0))
+    assert L.hydro_create(ctypes.byref(c), None, ctypes.byref(ctypes.c_void_p())) == H._binding.ERR_INVALID_ARG

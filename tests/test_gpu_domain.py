@@ -109,3 +109,11 @@ def test_halo_handle_rejects_whole_grid_calls():
     finally:
         for s in slabs:
             s.close()
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_charwise_slabs(scheme):
+    g, w = W.lumpy(n=(17, 15, 22), seed=19, scheme=scheme)
+    w = with_flow(g, w)
+    g.charwise = 1
+    check(g, w, 3, 4, device="cuda")

@@ -369,3 +369,67 @@ def test_musta_rejected_where_unsupported():
     g.split = 1
     with pytest.raises(HydroError):
         Hydro.from_grid(g)
+
+
+# ---------------------------------------------------------------- characteristic-wise WENO
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_charwise_sod(scheme):
+    g, w = W.sod(N=400, scheme=scheme)
+    g.charwise = 1
+    assert_parity(g, w, 100000, t0=0.0, t_end=0.4)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+@pytest.mark.parametrize("dims", [(37, 29, 21), (23, 17, 1), (1, 19, 23), (1, 1, 40)])
+def test_charwise_ragged_and_degenerate(scheme, dims):
+    g, w = W.lumpy(n=dims, seed=17 + sum(dims), scheme=scheme)
+    w = with_flow(g, w)
+    g.charwise = 1
+    assert_parity(g, w, 6)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_charwise_periodic_and_ellipsoidal(scheme):
+    g, w = W.smooth_periodic(n=(19, 13, 11), amp=0.3, vamp=0.5, seed=4, scheme=scheme)
+    g.charwise = 1
+    assert_parity(g, w, 8)
+    g, w = W.ellipsoidal(N=40, scheme=scheme)
+    g.charwise = 1
+    g.cfl = 0.3 * 40 / 256
+    assert_parity(g, w, 40)
+
+
+@pytest.mark.parametrize("scheme,nq", [(5, 2), (7, 3)])
+def test_charwise_several_charges(scheme, nq):
+    g, w = W.lumpy(n=(37, 29, 21), seed=40 + nq, scheme=scheme)
+    w = with_flow(g, w)
+    g.charwise, g.nq = 1, nq
+    assert_parity(g, W.with_charges(g, w, nq), 6)
+
+
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (7, 0)])
+def test_charwise_every_launch_variant(scheme, variant):
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=(37, 29, 21), seed=79, scheme=scheme)
+    w = with_flow(g, w)
+    g.charwise = 1
+    u0 = oracle.prim2con(w)
+    ref = oracle.run(oracle_cfg(g), u0, 4)[0]
+    with Hydro.from_grid(g) as h:
+        h.set_launch(variant, 8)
+        h.set_state(u0)
+        h.step(4)
+        got = h.get_state()
+    assert np.all(field_errors(got, ref) <= TOL)
+
+
+def test_charwise_rejected_where_unsupported():
+    from paper_1604_03360_gb300 import Hydro, HydroBatch, HydroError
+    g, w = W.lumpy(n=(12, 11, 10), seed=2)
+    g.charwise = 1
+    with pytest.raises(HydroError):
+        HydroBatch([g])
+    with Hydro.from_grid(g) as h:
+        h.set_primitive(w)
+        with pytest.raises(HydroError):
+            h.forward_record(2, 1)

@@ -283,12 +283,15 @@ def test_uniform_state_preserved_outflow(oracle_lib):
     np.testing.assert_allclose(u1, u0, rtol=1e-14)
 
 
-@pytest.mark.parametrize("scheme", [5, 7])
-def test_mirror_and_permutation_symmetry(oracle_lib, scheme):
+@pytest.mark.parametrize("scheme,charw", [(5, 0), (7, 0), (5, 1), (7, 1)])
+def test_mirror_and_permutation_symmetry(oracle_lib, scheme, charw):
+    """Mirror x -> -x and the swap x <-> y commute with a run (for the
+    characteristic-wise scheme this also fixes the face state to be symmetric
+    in the two cells beside the face)."""
     g, w = W.lumpy(n=(10, 10, 10), seed=21, scheme=scheme)
     w[1] = 0.2 * np.tanh(w[0] - 1)  # give the flow a velocity field
     u0 = oracle_lib.prim2con(w)
-    c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme)
+    c = oracle_lib.make_cfg(g.n, g.dx, scheme=scheme, charw=charw)
     a = oracle_lib.run(c, u0, 2)[0]
     # mirror x -> -x: reverse x and flip M_x
     um = u0[:, :, :, ::-1].copy()

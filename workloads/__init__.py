@@ -37,6 +37,7 @@ class Grid:
     nq: int = 1                 # conserved charge densities (state fields 4 + nq)
     limiter: int = 0            # MUSTA-FORCE: 0 minmod, 1 MC, 2 van Leer, 3 superbee
     musta_stages: int = 2       # MUSTA-FORCE: stages of the FORCE flux
+    charwise: int = 0           # WENO on 0 the components, 1 the characteristic fields
     cs2: float = CS2
     eps: float = 1e-6
     t0: float = 0.0

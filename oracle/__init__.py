@@ -56,6 +56,7 @@ class Cfg(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("dt_fixed", ctypes.c_double),
         ("eps", ctypes.c_double),
+        ("mass", ctypes.c_double),
     ]
 
 
@@ -79,8 +80,15 @@ def lib():
         L.oc_L.argtypes = [P(Cfg), vp, vp, vp]
         L.oc_run.argtypes = [P(Cfg), vp, ctypes.c_int, d, P(d), P(ctypes.c_int64), vp, vp, vp, vp]
         L.oc_eps2.argtypes = [P(Cfg), vp, P(d)]
-        L.oc_con2prim_n.argtypes = [d, ctypes.c_int, vp, ctypes.c_int64, vp]
-        L.oc_prim2con_n.argtypes = [d, ctypes.c_int, vp, ctypes.c_int64, vp]
+        L.oc_con2prim_n.argtypes = [d, d, ctypes.c_int, vp, ctypes.c_int64, vp]
+        L.oc_prim2con_n.argtypes = [d, d, ctypes.c_int, vp, ctypes.c_int64, vp]
+        L.oc_con2prim_gas.argtypes = [d, d, vp, vp]
+        L.oc_con2prim_eos.argtypes = [d, d, vp, vp]
+        L.oc_flux_eos.argtypes = [d, d, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        L.oc_sound2.argtypes = [d, d, vp]
+        L.oc_sound2.restype = d
+        L.oc_eos_p.argtypes = [d, d, vp]
+        L.oc_eos_p.restype = d
         L.oc_set_threads.argtypes = [ctypes.c_int]
         L.oc_limiter.argtypes = [ctypes.c_int, d, d]
         L.oc_limiter.restype = d
@@ -111,12 +119,13 @@ def max_threads():
 
 
 def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0, eps=1e-6, split=0, nq=1,
-             limiter=0, musta_k=2, charw=0):
+             limiter=0, musta_k=2, charw=0, mass=0.0):
     """n = (nx, ny, nz); scheme 5 (WENO5), 7 (WENO7) or 2 (MUSTA-FORCE + MUSCL);
     bc 0 outflow / 1 periodic; split 0 global / 1 local Lax-Friedrichs; nq
     conserved charges (state has 4 + nq fields); limiter 0 minmod, 1 MC,
     2 van Leer, 3 superbee; musta_k MUSTA stages; charw 0 component-wise,
-    1 characteristic-wise WENO."""
+    1 characteristic-wise WENO; mass m of the EOS p = cs2 (e - m n_1)
+    (0: p = cs2 e)."""
     c = Cfg()
     for i in range(3):
         c.n[i] = int(n[i])
@@ -132,6 +141,7 @@ def make_cfg(n, dx, cs2=1.0 / 3.0, scheme=5, bc=(0, 0, 0), cfl=0.3, dt_fixed=0.0
     c.limiter = int(limiter)
     c.musta_k = int(musta_k)
     c.charw = int(charw)
+    c.mass = float(mass)
     return c
 
 
@@ -144,32 +154,49 @@ def _shape(c):
     return (4 + max(1, c.nq), c.n[2], c.n[1], c.n[0])
 
 
-def con2prim(u, cs2=1.0 / 3.0):
+def con2prim(u, cs2=1.0 / 3.0, mass=0.0):
     """u: (4+q, ...) conserved (E, M, R_1..R_q) -> primitives (e, vx, vy, vz,
-    n_1..n_q); NaN where unphysical."""
+    n_1..n_q) for the EOS p = cs2 (e - mass n_1); NaN where unphysical."""
     u = _c(u)
     w = np.empty_like(u)
     n = u[0].size
-    lib().oc_con2prim_n(cs2, u.shape[0], _ptr(u), n, _ptr(w))
+    lib().oc_con2prim_n(cs2, mass, u.shape[0], _ptr(u), n, _ptr(w))
     return w
 
 
-def prim2con(w, cs2=1.0 / 3.0):
+def prim2con(w, cs2=1.0 / 3.0, mass=0.0):
     w = _c(w)
     u = np.empty_like(w)
-    lib().oc_prim2con_n(cs2, w.shape[0], _ptr(w), w[0].size, _ptr(u))
+    lib().oc_prim2con_n(cs2, mass, w.shape[0], _ptr(w), w[0].size, _ptr(u))
     return u
 
 
-def flux(d, u, cs2=1.0 / 3.0):
+def con2prim_gas(u, cs2, mass):
+    """One cell (5 values) by the iterative recovery, whatever the mass
+    (also m = 0); None if no physical state exists."""
+    u = _c(u).reshape(-1)
+    w = np.empty(5)
+    return None if lib().oc_con2prim_gas(cs2, mass, _ptr(u), _ptr(w)) else w
+
+
+def sound2(w, cs2=1.0 / 3.0, mass=0.0):
+    """Squared sound speed of primitives w (e, vx, vy, vz, n_1)."""
+    return lib().oc_sound2(cs2, mass, _ptr(_c(w).reshape(-1)))
+
+
+def pressure(w, cs2=1.0 / 3.0, mass=0.0):
+    return lib().oc_eos_p(cs2, mass, _ptr(_c(w).reshape(-1)))
+
+
+def flux(d, u, cs2=1.0 / 3.0, mass=0.0):
     """Physical flux f_d(u) of one cell (u: 4 + q conserved values, q >= 1)."""
     u = _c(u).reshape(-1)
     w = np.empty(max(8, u.size))
-    rc = lib().oc_con2prim(cs2, _ptr(u), _ptr(w))
+    rc = lib().oc_con2prim_eos(cs2, mass, _ptr(u), _ptr(w))
     if rc:
         raise ValueError("unphysical state")
     f = np.empty(u.size)
-    lib().oc_flux_n(cs2, int(d), u.size, _ptr(u), _ptr(w), _ptr(f))
+    lib().oc_flux_eos(cs2, mass, int(d), u.size, _ptr(u), _ptr(w), _ptr(f))
     return f
 
 

@@ -31,6 +31,12 @@
  * copy the edge cell into the ghost cells (zeroth-order extrapolation of the
  * conserved variables); periodic boundaries wrap; directions with a single
  * cell contribute no flux difference.
+ * General EOS (mass m > 0): p = cs2 (e - m n_1), the ideal gas of adiabatic
+ * index 1 + cs2 whose rest mass is m per unit of the first charge (m = 0 is
+ * p = cs2 e).  The first charge then enters the pressure; the primitive
+ * recovery solves for p by bracketed Newton iteration, and the Lax-Friedrichs
+ * speeds use c_s^2 = (1 + cs2) p / (e + p).  WENO (component-wise, global or
+ * local LF) only.
  * Several conserved charges (nq > 1): the state is (E, M, R_1..R_nq); every
  * charge is a passive density advected like R (flux R_k v_d, n_k = R_k / gamma),
  * since p = cs2 e does not depend on them.
@@ -86,6 +92,7 @@ typedef struct {
     double cfl;
     double dt_fixed;   /* > 0: use this dt instead of the CFL rule */
     double eps;        /* WENO epsilon in alpha_k = d_k / (eps + beta_k)^2 */
+    double mass;       /* EOS p = cs2 (e - mass n_1); 0: p = cs2 e */
 } oc_cfg;
 
 enum { OC_OK = 0, OC_ERR_ARG = 1, OC_ERR_UNPHYSICAL = 4, OC_ERR_OOM = 3 };
@@ -165,6 +172,101 @@ void oc_eigen(double k, int d, const double *w, double *lam)
     const double den = 1.0 - k * v2;
     lam[0] = (vd * (1.0 - k) - root) / den;
     lam[1] = (vd * (1.0 - k) + root) / den;
+}
+
+/* ------------------------------------------------------------------------ */
+/* General equation of state p(e, n) = k (e - m n_1)                         */
+/* ------------------------------------------------------------------------ */
+/* The ideal gas with adiabatic index 1 + k whose rest mass is m per unit of
+ * the first charge: n_1 m is the rest-mass density, e - m n_1 the internal
+ * energy density.  m = 0 is the EOS p = k e above.  Sound speed squared
+ * c_s^2 = dp/de + n/(e+p) dp/dn = k (e + p - m n) / (e + p) = (1 + k) p / (e + p). */
+double oc_eos_p(double k, double m, const double *w) { return m == 0.0 ? k * w[0] : k * (w[0] - m * w[4]); }
+
+double oc_sound2(double k, double m, const double *w)
+{
+    if (m == 0.0) return k;
+    const double p = oc_eos_p(k, m, w);
+    return (1.0 + k) * p / (w[0] + p);
+}
+
+/* Conserved -> primitive for m >= 0 by bracketed Newton iteration on the
+ * pressure: with v = M / (E + p), e = E - M.v, n = R sqrt(1 - v^2),
+ * f(p) = k (e - m n) - p is decreasing (f' = v^2 c_s^2 - 1 < 0); f(0) > 0
+ * is required (positive internal energy) and f <= 0 at the pressure of the
+ * m = 0 state (an upper bracket).  Iterates until the Newton update is below
+ * 1e-15 p (at most 200 steps).  Returns nonzero if no physical state exists. */
+int oc_con2prim_gas(double k, double m, const double *u, double *w)
+{
+    const double E = u[0], R = u[4];
+    const double M2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+    const double dd = E * E - M2;
+    if (!(E > 0.0) || !(dd > 0.0) || !(R >= 0.0)) return 1;
+    const double b = (1.0 - k) * E;
+    const double hi0 = k * (2.0 * dd / (b + sqrt(b * b + 4.0 * k * dd)));   /* pressure if m = 0 */
+    double lo = 0.0, hi = hi0;
+    /* f and f' at p */
+    double p = hi, f = 0.0, fp = -1.0;
+    {
+        const double v2 = M2 / (E * E);
+        const double f0 = k * ((E - M2 / E) - m * R * sqrt(1.0 - v2));
+        if (!(f0 > 0.0)) return 1;
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double h = E + p, v2 = M2 / (h * h);
+        const double e = E - M2 / h, n = R * sqrt(1.0 - v2);
+        f = k * (e - m * n) - p;
+        const double cs2 = (1.0 + k) * p / (e + p);
+        fp = v2 * cs2 - 1.0;
+        if (f > 0.0) lo = p;
+        else hi = p;
+        double pn = p - f / fp;
+        if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
+        const double dp = fabs(pn - p);
+        p = pn;
+        if (dp <= 1e-15 * p) break;
+    }
+    if (!(p > 0.0)) return 1;
+    const double h = E + p;
+    w[0] = E - M2 / h;
+    w[1] = u[1] / h;
+    w[2] = u[2] / h;
+    w[3] = u[3] / h;
+    w[4] = R * sqrt(1.0 - (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
+    return 0;
+}
+
+int oc_con2prim_eos(double k, double m, const double *u, double *w)
+{
+    return m == 0.0 ? oc_con2prim(k, u, w) : oc_con2prim_gas(k, m, u, w);
+}
+
+/* Primitive -> conserved for the general EOS (same definitions as oc_prim2con). */
+void oc_prim2con_eos(double k, double m, const double *w, double *u)
+{
+    if (m == 0.0) {
+        oc_prim2con(k, w, u);
+        return;
+    }
+    const double e = w[0], vx = w[1], vy = w[2], vz = w[3], n = w[4];
+    const double p = oc_eos_p(k, m, w);
+    const double g2 = 1.0 / (1.0 - (vx * vx + vy * vy + vz * vz));
+    const double W = (e + p) * g2;
+    u[0] = W - p;
+    u[1] = W * vx;
+    u[2] = W * vy;
+    u[3] = W * vz;
+    u[4] = n * sqrt(g2);
+}
+
+/* Flux of Eq. 1 with p from the general EOS (oc_flux_n for m = 0). */
+void oc_flux_eos(double k, double m, int d, int nf, const double *u, const double *w, double *f)
+{
+    const double p = oc_eos_p(k, m, w);
+    const double vd = w[1 + d];
+    f[0] = u[1 + d];
+    for (int j = 0; j < 3; ++j) f[1 + j] = u[1 + j] * vd + (d == j ? p : 0.0);
+    for (int q = 4; q < nf; ++q) f[q] = u[q] * vd;
 }
 
 /* Right eigenvectors of the flux Jacobian A_d = df_d/du at the primitive
@@ -398,6 +500,7 @@ static int cfg_ok(const oc_cfg *c)
     if (c->r == 1 && (c->limiter < 0 || c->limiter > 3 || c->musta_k < 1 || c->split != 0 || c->nq > 1)) return 0;
     if (c->split != 0 && c->split != 1) return 0;
     if (c->charw != 0 && (c->charw != 1 || c->r == 1)) return 0;
+    if (!(c->mass >= 0.0) || (c->mass > 0.0 && (c->r == 1 || c->charw))) return 0;
     if (c->nq < 0 || c->nq > MAXF - 4) return 0;
     if (!(c->cs2 > 0 && c->cs2 < 1) || !(c->eps > 0)) return 0;
     for (int d = 0; d < 3; ++d)
@@ -416,15 +519,16 @@ int oc_alpha(const oc_cfg *c, const double *u, double *alpha)
     for (int64_t q = 0; q < N; ++q) {
         double uu[MAXF], w[MAXF], lam[2];
         for (int f = 0; f < 5; ++f) uu[f] = u[f * N + q];
-        if (oc_con2prim(c->cs2, uu, w)) {
+        if (oc_con2prim_eos(c->cs2, c->mass, uu, w)) {
             bad |= 1;
             continue;
         }
-        oc_eigen(c->cs2, 0, w, lam);
+        const double cs2 = oc_sound2(c->cs2, c->mass, w);
+        oc_eigen(cs2, 0, w, lam);
         a0 = fmax(a0, fmax(fabs(lam[0]), fabs(lam[1])));
-        oc_eigen(c->cs2, 1, w, lam);
+        oc_eigen(cs2, 1, w, lam);
         a1 = fmax(a1, fmax(fabs(lam[0]), fabs(lam[1])));
-        oc_eigen(c->cs2, 2, w, lam);
+        oc_eigen(cs2, 2, w, lam);
         a2 = fmax(a2, fmax(fabs(lam[0]), fabs(lam[1])));
     }
     alpha[0] = a0;
@@ -551,11 +655,11 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
                 const int64_t q = cell(c, ijk[0], ijk[1], ijk[2]);
                 double uu[MAXF], w[MAXF], f[MAXF];
                 for (int k = 0; k < NF; ++k) uu[k] = u[k * N + q];
-                if (oc_con2prim(c->cs2, uu, w)) {
+                if (oc_con2prim_eos(c->cs2, c->mass, uu, w)) {
                     bad |= 1;
                     for (int k = 0; k < 5; ++k) w[k] = 0.0;
                 }
-                oc_flux_n(c->cs2, d, NF, uu, w, f);
+                oc_flux_eos(c->cs2, c->mass, d, NF, uu, w, f);
                 for (int k = 0; k < NF; ++k) {
                     fp[k * len + m] = 0.5 * (f[k] + alpha[d] * uu[k]);
                     fm[k * len + m] = 0.5 * (f[k] - alpha[d] * uu[k]);
@@ -563,7 +667,7 @@ int oc_L(const oc_cfg *c, const double *u, const double *alpha, double *L)
                     ur[k * len + m] = uu[k];
                 }
                 double lam[2];
-                oc_eigen(c->cs2, d, w, lam);
+                oc_eigen(oc_sound2(c->cs2, c->mass, w), d, w, lam);
                 sp[m] = fmax(fabs(lam[0]), fabs(lam[1]));
             }
             /* face fluxes: F[s] sits at face s - 1/2, s = 0..nd */
@@ -756,8 +860,8 @@ int oc_eps2(const oc_cfg *c, const double *u, double *out)
     for (int64_t q = 0; q < N; ++q) {
         double uu[MAXF], w[MAXF];
         for (int f = 0; f < 5; ++f) uu[f] = u[f * N + q];
-        if (oc_con2prim(c->cs2, uu, w)) return OC_ERR_UNPHYSICAL;
-        const double p = c->cs2 * w[0];
+        if (oc_con2prim_eos(c->cs2, c->mass, uu, w)) return OC_ERR_UNPHYSICAL;
+        const double p = oc_eos_p(c->cs2, c->mass, w);
         const double txx = uu[1] * w[1] + p, tyy = uu[2] * w[2] + p;
         num += txx - tyy;
         den += txx + tyy;
@@ -768,14 +872,14 @@ int oc_eps2(const oc_cfg *c, const double *u, double *out)
 
 /* Array versions of the point functions, for tests. */
 /* (E, M, R_1..R_q) <-> (e, v, n_1..n_q) for nf = 4 + q fields of n cells. */
-int oc_con2prim_n(double k, int nf, const double *u, int64_t n, double *w)
+int oc_con2prim_n(double k, double m, int nf, const double *u, int64_t n, double *w)
 {
     int bad = 0;
     if (nf < 5 || nf > MAXF) return OC_ERR_ARG;
     for (int64_t q = 0; q < n; ++q) {
         double uu[MAXF], ww[MAXF];
         for (int f = 0; f < nf; ++f) uu[f] = u[f * n + q];
-        if (oc_con2prim(k, uu, ww)) {
+        if (oc_con2prim_eos(k, m, uu, ww)) {
             bad = 1;
             for (int f = 0; f < nf; ++f) ww[f] = NAN;
         } else {
@@ -787,12 +891,12 @@ int oc_con2prim_n(double k, int nf, const double *u, int64_t n, double *w)
     return bad ? OC_ERR_UNPHYSICAL : OC_OK;
 }
 
-void oc_prim2con_n(double k, int nf, const double *w, int64_t n, double *u)
+void oc_prim2con_n(double k, double m, int nf, const double *w, int64_t n, double *u)
 {
     for (int64_t q = 0; q < n; ++q) {
         double uu[MAXF], ww[MAXF];
         for (int f = 0; f < nf; ++f) ww[f] = w[f * n + q];
-        oc_prim2con(k, ww, uu);
+        oc_prim2con_eos(k, m, ww, uu);
         const double g = 1.0 / sqrt(1.0 - (ww[1] * ww[1] + ww[2] * ww[2] + ww[3] * ww[3]));
         for (int f = 5; f < nf; ++f) uu[f] = ww[f] * g;
         for (int f = 0; f < nf; ++f) u[f * n + q] = uu[f];

@@ -6,7 +6,7 @@ import pytest
 import sympy as sp
 
 import workloads as W
-from exact import SodExact, hubble as hubble_exact, t_mu_nu
+from exact import GasRiemannExact, SodExact, hubble as hubble_exact, t_mu_nu, t_mu_nu_p
 
 K = 1.0 / 3.0
 
@@ -772,3 +772,162 @@ def test_charwise_sod_has_fewer_oscillations(oracle_lib, scheme):
     assert out[1]["l1"] < 1.03 * out[0]["l1"], out
     assert all(a * 3 < b for a, b in zip(out[1]["tv"], out[0]["tv"])), out
     assert 2 * out[1]["over"] < out[0]["over"], out
+
+
+# ---------------------------------------------------------------- general EOS p = k (e - m n)
+def _gas_states(rng, m, k, count):
+    """Random states of the ideal gas with rest mass: n, internal energy
+    e - m n > 0 over four decades, |v| < 0.99."""
+    _, v, n = rand_prims(rng, count)
+    eint = np.exp(rng.uniform(np.log(1e-2), np.log(1e2), count)) * np.maximum(m * n, 1e-3)
+    e = m * n + eint
+    return e, k * eint, v, n
+
+
+@pytest.mark.parametrize("k,m", [(2.0 / 3.0, 1.0), (0.4, 0.3), (1.0 / 3.0, 3.0)])
+def test_gas_con2prim_roundtrip(oracle_lib, k, m):
+    """Conserved densities built from T^{mu nu}, N^mu with p = k (e - m n) by
+    definition are inverted to the original (e, v, n)."""
+    rng = np.random.default_rng(int(100 * k + 10 * m))
+    e, p, v, n = _gas_states(rng, m, k, 2000)
+    T00, T0i, N0 = t_mu_nu_p(e, p, v, n)
+    u = np.stack([T00, T0i[:, 0], T0i[:, 1], T0i[:, 2], N0])
+    w = oracle_lib.con2prim(u, k, m)
+    np.testing.assert_allclose(w[0], e, rtol=1e-10)
+    np.testing.assert_allclose(w[1:4].T, v, rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(w[4], n, rtol=1e-10)
+    np.testing.assert_allclose(oracle_lib.prim2con(w, k, m), u, rtol=1e-10, atol=1e-13 * np.abs(u).max())
+
+
+def test_gas_recovery_at_zero_mass_is_the_closed_form(oracle_lib):
+    rng = np.random.default_rng(7)
+    e, v, n = rand_prims(rng, 300)
+    T00, T0i, N0 = t_mu_nu(e, v, n, K)
+    u = np.stack([T00, T0i[:, 0], T0i[:, 1], T0i[:, 2], N0])
+    w = oracle_lib.con2prim(u, K)
+    for q in range(300):
+        wg = oracle_lib.con2prim_gas(u[:, q].copy(), K, 0.0)
+        np.testing.assert_allclose(wg, w[:, q], rtol=1e-13, atol=1e-15)
+
+
+def test_gas_rejects_negative_internal_energy(oracle_lib):
+    """A state whose recovered internal energy would be negative (e < m n)
+    has no physical pressure."""
+    for v in (0.0, 0.5, 0.9):
+        T00, T0i, N0 = t_mu_nu_p(1.0, 0.0, np.array([v, 0, 0]), 1.2)   # e = 1 < m n = 1.2
+        assert oracle_lib.con2prim_gas(np.array([T00, *T0i, N0]), 2.0 / 3.0, 1.0) is None
+
+
+@pytest.mark.parametrize("k,m", [(2.0 / 3.0, 1.0), (0.4, 2.0)])
+def test_gas_sound_speed_from_flux_jacobian(oracle_lib, k, m):
+    """With the general EOS the extreme eigenvalues of a central-difference
+    Jacobian of the flux (through the iterative recovery) are lambda_+- with
+    c_s^2 = (1 + k) p / (e + p); the other three equal v_d."""
+    rng = np.random.default_rng(5)
+    e, p, v, n = _gas_states(rng, m, k, 30)
+    for q in range(30):
+        T00, T0i, N0 = t_mu_nu_p(e[q], p[q], v[q] * 0.9, n[q])
+        u = np.array([T00, *T0i, N0])
+        w = oracle_lib.con2prim(u.reshape(5, 1), k, m).ravel()
+        cs2 = oracle_lib.sound2(w, k, m)
+        assert cs2 == pytest.approx((1 + k) * p[q] / (e[q] + p[q]), rel=1e-10)
+        for d in range(3):
+            J = np.empty((5, 5))
+            for j in range(5):
+                h = 1e-6 * max(abs(u[j]), u[0])
+                up, um = u.copy(), u.copy()
+                up[j] += h
+                um[j] -= h
+                J[:, j] = (oracle_lib.flux(d, up, k, m) - oracle_lib.flux(d, um, k, m)) / (2 * h)
+            ev = np.sort(np.linalg.eigvals(J).real)
+            np.testing.assert_allclose([ev[0], ev[-1]], oracle_lib.eigen(d, w, cs2), atol=1e-5)
+            np.testing.assert_allclose(ev[1:4], w[1 + d], atol=1e-5)
+
+
+def test_gas_riemann_exact_solution_is_consistent():
+    ex = GasRiemannExact()
+    assert max(abs(r) for r in ex.jump_residuals()) < 1e-12
+    assert ex.pR < ex.p_star < ex.pL and 0 < ex.v_star < ex.V_shock < 1
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_gas_shock_tube_against_exact_solution(oracle_lib, scheme):
+    """Ideal-gas shock tube (k = 2/3, m = 1): the L1 errors of n, p, v fall
+    with N; at N = 400 the plateaus of p, v and n on both sides of the
+    contact are within 2 % of the exact solution and the shock is within 3
+    cells of its exact position."""
+    ex = GasRiemannExact()
+    errs = []
+    for N in (100, 200, 400):
+        g, w = W.gas_sod(N=N, scheme=scheme)
+        c = oracle_lib.make_cfg(g.n, g.dx, cs2=g.cs2, scheme=scheme, cfl=g.cfl, mass=g.mass)
+        u, t, k = oracle_lib.run(c, oracle_lib.prim2con(w, g.cs2, g.mass), 100000, t_end=0.4)
+        assert t == pytest.approx(0.4, abs=1e-15)
+        pr = oracle_lib.con2prim(u, g.cs2, g.mass)
+        x = g.centres()[0].ravel()
+        e_ex, v_ex, n_ex, p_ex = ex(x, 0.4)
+        n, v = pr[4].ravel(), pr[1].ravel()
+        p = g.cs2 * (pr[0].ravel() - g.mass * n)
+        errs.append([np.abs(n - n_ex).mean(), np.abs(p - p_ex).mean(), np.abs(v - v_ex).mean()])
+        if N == 400:
+            mid = (x > ex.xi_tail * 0.4 + 0.03) & (x < ex.V_shock * 0.4 - 0.03)
+            midL = (x > ex.xi_tail * 0.4 + 0.03) & (x < ex.v_star * 0.4 - 0.03)
+            midR = (x > ex.v_star * 0.4 + 0.03) & (x < ex.V_shock * 0.4 - 0.03)
+            assert np.abs(p[mid] / ex.p_star - 1).max() < 0.02
+            assert np.abs(v[mid] / ex.v_star - 1).max() < 0.02
+            assert np.abs(n[midL] / ex.n_star_L - 1).max() < 0.02
+            assert np.abs(n[midR] / ex.n_star_R - 1).max() < 0.02
+            half = 0.5 * (ex.p_star + ex.pR)
+            i = np.where((p[:-1] > half) & (p[1:] <= half) & (x[:-1] > 0.1))[0][0]
+            assert abs(x[i] + 0.5 * g.dx[0] - ex.V_shock * 0.4) < 3 * g.dx[0]
+    errs = np.array(errs)
+    assert np.all(errs[1:] < 0.75 * errs[:-1]), errs
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_gas_conserves_and_follows_boundary_rule(oracle_lib, scheme):
+    k, m = 2.0 / 3.0, 1.0
+    g, w = W.smooth_periodic(n=(10, 9, 8), amp=0.3, vamp=0.4, seed=5, scheme=scheme)
+    w[0] = w[0] + m * w[4]          # keep the internal energy positive
+    u0 = oracle_lib.prim2con(w, k, m)
+    c = oracle_lib.make_cfg(g.n, g.dx, cs2=k, scheme=scheme, bc=(1, 1, 1), cfl=0.4, mass=m)
+    u1, t, kk = oracle_lib.run(c, u0, 4)
+    scale = np.abs(u0).reshape(5, -1).sum(1).max()
+    assert kk == 4 and np.abs(u1.reshape(5, -1).sum(1) - u0.reshape(5, -1).sum(1)).max() < 1e-13 * scale
+    G = (scheme + 1) // 2
+    gl, wl = W.lumpy(n=(9, 8, 7), seed=31, scheme=scheme)
+    wl[1] = 0.3 * np.tanh(wl[0] - 2)
+    wl[0] = wl[0] + m * wl[4]
+    ul = oracle_lib.prim2con(wl, k, m)
+    for bc, mode in ((0, "edge"), (1, "wrap")):
+        cb = oracle_lib.make_cfg(gl.n, gl.dx, cs2=k, scheme=scheme, bc=(bc,) * 3, mass=m)
+        a = oracle_lib.alpha(cb, ul)
+        up = np.pad(ul, ((0, 0), (G, G), (G, G), (G, G)), mode=mode)
+        cp = oracle_lib.make_cfg(tuple(q + 2 * G for q in gl.n), gl.dx, cs2=k, scheme=scheme, bc=(1 - bc,) * 3, mass=m)
+        assert np.array_equal(oracle_lib.L(cp, up, a)[:, G:-G, G:-G, G:-G], oracle_lib.L(cb, ul, a))
+
+
+def test_gas_alpha_is_the_largest_jacobian_eigenvalue(oracle_lib):
+    """alpha_d of the Lax-Friedrichs split with the general EOS equals the
+    largest |eigenvalue| of central-difference flux Jacobians over the grid."""
+    k, m = 2.0 / 3.0, 1.0
+    g, w = W.lumpy(n=(4, 3, 3), seed=8, scheme=5)
+    w[1] = 0.6 * np.tanh(w[0] - 1)
+    w[2] = -0.3
+    w[0] = w[0] + m * w[4]
+    u = oracle_lib.prim2con(w, k, m)
+    c = oracle_lib.make_cfg(g.n, g.dx, cs2=k, mass=m)
+    a = oracle_lib.alpha(c, u)
+    ref = np.zeros(3)
+    for q in range(u[0].size):
+        uq = u.reshape(5, -1)[:, q].copy()
+        for d in range(3):
+            J = np.empty((5, 5))
+            for j in range(5):
+                h = 1e-6 * max(abs(uq[j]), uq[0])
+                up, um = uq.copy(), uq.copy()
+                up[j] += h
+                um[j] -= h
+                J[:, j] = (oracle_lib.flux(d, up, k, m) - oracle_lib.flux(d, um, k, m)) / (2 * h)
+            ref[d] = max(ref[d], np.abs(np.linalg.eigvals(J)).max())
+    np.testing.assert_allclose(a, ref, rtol=1e-5)

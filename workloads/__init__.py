@@ -38,6 +38,7 @@ class Grid:
     limiter: int = 0            # MUSTA-FORCE: 0 minmod, 1 MC, 2 van Leer, 3 superbee
     musta_stages: int = 2       # MUSTA-FORCE: stages of the FORCE flux
     charwise: int = 0           # WENO on 0 the components, 1 the characteristic fields
+    mass: float = 0.0           # EOS p = cs2 (e - mass n_1); 0: p = cs2 e
     cs2: float = CS2
     eps: float = 1e-6
     t0: float = 0.0
@@ -77,6 +78,19 @@ def sod(N=400, scheme=5):
     e = np.where(left, 1.0, 0.1)
     n = np.where(left, 1.0, 0.125)
     return g, _stack(g, e, 0.0, 0.0, 0.0, n)
+
+
+def gas_sod(N=400, scheme=5, k=2.0 / 3.0, m=1.0):
+    """Shock tube for the ideal gas p = k (e - m n) (adiabatic index 1 + k):
+    left (n=1, p=1), right (n=0.125, p=0.1), both at rest, split at x = 0 on
+    [-1, 1], outflow boundaries, CFL 0.4, run to t = 0.4; e = m n + p / k."""
+    g = Grid(n=(N, 1, 1), dx=(2.0 / N, 2.0 / N, 2.0 / N), origin=(-1.0, -1.0 / N, -1.0 / N),
+             bc=(0, 0, 0), scheme=scheme, cfl=0.4, cs2=k, mass=m, t_end=0.4, nsteps=100000, name="gas_sod")
+    x, _, _ = g.centres()
+    left = x < 0
+    n = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    return g, _stack(g, m * n + p / k, 0.0, 0.0, 0.0, n)
 
 
 def hubble(N=128, scheme=5, box=5.0, t0=10.0, e0=10.0, n0=1.0, nsteps=100, cfl=0.3):

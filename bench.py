@@ -549,6 +549,28 @@ def main():
                                             "over_componentwise": (float(kc[1:4].sum()) / 9) / stage_ms}
         hc.close()
     if not args.no_extra:
+        # general EOS p = cs2 (e - m n_1) with m = 1 (iterative primitive recovery), same workload
+        gg, wg = workload(args.scheme, args.grid)
+        gg.mass = 1.0
+        hg = Hydro.from_grid(gg, stream=stream)
+        hg.set_primitive(torch.from_numpy(wg).to(dev))
+        hg.autotune()
+        hg.step(3)
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        kg = hg.profile_step(3)
+        a1.record(stream)
+        barrier()
+        hg.sync()
+        elg = a0.elapsed_time(a1) / 1e3
+        extra["gas_eos_%d" % args.grid] = {"value": cells * 3 / elg, "unit": "cell-updates/s", "steps": 3,
+                                           "eos": "p = cs2 (e - m n), cs2 = 1/3, m = 1",
+                                           "ms_per_step": 1e3 * elg / 3, "launch": hg.launch(),
+                                           "stage_kernel_ms": float(kg[1:4].sum()) / 9,
+                                           "over_default_eos": (float(kg[1:4].sum()) / 9) / stage_ms}
+        hg.close()
+    if not args.no_extra:
         # three conserved charges (state of 7 fields), same workload and scheme
         import workloads as W
         gq, wq = workload(args.scheme, args.grid)

@@ -11,7 +11,9 @@
  *           Cartesian grid; F at the half-cell faces from finite-difference
  *           WENO of order 5 or 7 (Sec. 1.2) on Lax-Friedrichs split fluxes.
  *   Sec. 1  third-order Runge-Kutta in time (SSP / Shu-Osher form).
- * Readings where the paper is silent: component-wise WENO on f^+- =
+ * Readings where the paper is silent (each switchable in hydro_config: local
+ * Lax-Friedrichs, characteristic-wise WENO, several charges, the general EOS
+ * p = cs2 (e - eos_mass n_1)): component-wise WENO on f^+- =
  * (f +- alpha_d u)/2 with alpha_d the largest characteristic speed over the
  * grid (recomputed from every stage's input); epsilon = weno_eps in
  * omega_k ~ d_k / (eps + beta_k)^2; dt = cfl * min_d dx_d / max_d alpha_d over
@@ -116,6 +118,15 @@ typedef struct {
     double cfl;         /* dt = cfl * min dx / max alpha when dt_fixed <= 0 */
     double dt_fixed;    /* > 0: constant time step */
     double weno_eps;    /* WENO epsilon, > 0 (1e-6) */
+    double eos_mass;    /* equation of state p = cs2 (e - eos_mass n_1): 0 (the
+                           default) is p = cs2 e; > 0 is the ideal gas of
+                           adiabatic index 1 + cs2 whose rest mass is eos_mass
+                           per unit of the first charge (Sec. 1 leaves the EOS
+                           open).  The first charge then enters the pressure, the
+                           primitive recovery iterates (bracketed Newton on p)
+                           and states with e <= eos_mass n_1 are unphysical.
+                           > 0 needs component-wise WENO (either splitting) and
+                           runs on the single-grid and z-slab paths only */
 } hydro_config;
 
 typedef struct hydro_s hydro_t;

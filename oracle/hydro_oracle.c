@@ -194,8 +194,10 @@ double oc_sound2(double k, double m, const double *w)
  * pressure: with v = M / (E + p), e = E - M.v, n = R sqrt(1 - v^2),
  * f(p) = k (e - m n) - p is decreasing (f' = v^2 c_s^2 - 1 < 0); f(0) > 0
  * is required (positive internal energy) and f <= 0 at the pressure of the
- * m = 0 state (an upper bracket).  Iterates until the Newton update is below
- * 1e-15 p (at most 200 steps).  Returns nonzero if no physical state exists. */
+ * m = 0 state (an upper bracket).  A Newton step that leaves the bracket is
+ * replaced by bisection.  Stops at f = 0, when the update no longer changes
+ * p, or when it is below 1e-15 p (at most 200 steps).  Returns nonzero if no
+ * physical state exists. */
 int oc_con2prim_gas(double k, double m, const double *u, double *w)
 {
     const double E = u[0], R = u[4];
@@ -216,11 +218,13 @@ int oc_con2prim_gas(double k, double m, const double *u, double *w)
         const double h = E + p, v2 = M2 / (h * h);
         const double e = E - M2 / h, n = R * sqrt(1.0 - v2);
         f = k * (e - m * n) - p;
+        if (f == 0.0) break;                      /* p is the root */
         const double cs2 = (1.0 + k) * p / (e + p);
         fp = v2 * cs2 - 1.0;
         if (f > 0.0) lo = p;
         else hi = p;
         double pn = p - f / fp;
+        if (pn == p) break;                       /* the update is below the rounding of p */
         if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
         const double dp = fabs(pn - p);
         p = pn;

@@ -42,11 +42,12 @@ class HydroConfig(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("dt_fixed", ctypes.c_double),
         ("weno_eps", ctypes.c_double),
+        ("eos_mass", ctypes.c_double),
     ]
 
 
 def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
-                origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2, charwise=0):
+                origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2, charwise=0, eos_mass=0.0):
     c = HydroConfig()
     for i in range(3):
         c.n[i] = int(n[i])
@@ -63,6 +64,7 @@ def make_config(n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=
     c.cfl = float(cfl)
     c.dt_fixed = float(dt_fixed)
     c.weno_eps = float(eps)
+    c.eos_mass = float(eos_mass)
     return c
 
 
@@ -187,10 +189,11 @@ class Hydro:
     """One grid of the FP64 WENO5/WENO7 + SSP-RK3 solver (hydro_t)."""
 
     def __init__(self, n, dx, scheme=5, bc=(0, 0, 0), cs2=1.0 / 3.0, cfl=0.3, dt_fixed=0.0, eps=1e-6,
-                 origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2, charwise=0, stream=None):
+                 origin=(0.0, 0.0, 0.0), split=0, nq=1, limiter=0, musta_stages=2, charwise=0, eos_mass=0.0,
+                 stream=None):
         self._L = lib()
         self.cfg = make_config(n, dx, scheme, bc, cs2, cfl, dt_fixed, eps, origin, split, nq, limiter, musta_stages,
-                               charwise)
+                               charwise, eos_mass)
         self.n = tuple(int(k) for k in n)
         self.shape = (4 + max(1, int(nq)), self.n[2], self.n[1], self.n[0])
         h = ctypes.c_void_p()
@@ -207,7 +210,7 @@ class Hydro:
         return cls(g.n, g.dx, scheme=g.scheme, bc=g.bc, cs2=g.cs2, cfl=g.cfl, eps=g.eps, origin=g.origin,
                    dt_fixed=getattr(g, "dt_fixed", 0.0), split=getattr(g, "split", 0), nq=getattr(g, "nq", 1),
                    limiter=getattr(g, "limiter", 0), musta_stages=getattr(g, "musta_stages", 2),
-                   charwise=getattr(g, "charwise", 0), stream=stream)
+                   charwise=getattr(g, "charwise", 0), eos_mass=getattr(g, "mass", 0.0), stream=stream)
 
     def _check(self, rc):
         if rc:
@@ -374,7 +377,7 @@ class HydroBatch:
         for i, g in enumerate(self.grids):
             arr[i] = make_config(g.n, g.dx, g.scheme, g.bc, g.cs2, g.cfl, getattr(g, "dt_fixed", 0.0), g.eps,
                                  g.origin, getattr(g, "split", 0), getattr(g, "nq", 1), getattr(g, "limiter", 0),
-                                 getattr(g, "musta_stages", 2), getattr(g, "charwise", 0))
+                                 getattr(g, "musta_stages", 2), getattr(g, "charwise", 0), getattr(g, "mass", 0.0))
         h = ctypes.c_void_p()
         rc = self._L.hydro_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.grids), _stream_handle(stream),
                                         ctypes.byref(h))

@@ -23,7 +23,10 @@
 // About 26 FP64 operations per projected vector (NF = 5) and 30 for the
 // back-projection, with 9 reciprocals and 3 square roots of setup per face.
 // Fields are handled in the face's own frame: (E, M_d, M_t1, M_t2, R...),
-// t1 = (d+1)%3, t2 = (d+2)%3; the caller maps them to memory offsets.
+// t1 = (d+1)%3, t2 = (d+2)%3; the caller maps them to memory.  Staged x/y
+// faces read g+- from shared memory and recover the face state as
+// (g+ - g-) / (2 alpha); z faces read a per-column ring of (u, p, v_z) and
+// form g+- and the face state from it.
 #pragma once
 #include "hydro_math.cuh"
 
@@ -37,26 +40,15 @@ __device__ __forceinline__ int rot_field(int k, int d)
     return 1 + (a >= 3 ? a - 3 : a);
 }
 
-// Characteristic-wise face flux (scaled like g: 2 F).  cell(i) points at field
-// 0 of g+ of window cell i (i = 0 .. 2r-1, cell j-r+1+i); field m of g+ sits
-// at +fo[m], of g- at +fo[m] + gmo.  fo[] must hold the memory offsets of the
-// rotated fields (rot_field).  Returns false (F = 0) if the face state is not
-// physical.
-template <int R, int NF, class Cell>
-__device__ __forceinline__ bool char_face(Cell cell, const int* fo, int gmo, double alpha, double k, double eps_s,
-                                          double* F)
+// Characteristic-wise face flux (scaled like g: 2 F).  gval(i, m, s) returns
+// rotated field m of the split flux g+ (s = 0) or g- (s = 1) of window cell i
+// (i = 0 .. 2r-1, cell j-r+1+i); ub holds the rotated face state, the mean of
+// the conserved states of window cells r-1 and r.  Returns false (F = 0) if
+// the face state is not physical.
+template <int R, int NF, class GV>
+__device__ __forceinline__ bool char_face(GV gval, const double* ub, double k, double eps_s, double* F)
 {
-    constexpr int G = R, S = 2 * R - 1, NQ = NF - 4;
-    // 1. face state: mean of cells G-1 and G, u = (g+ - g-) / (2 alpha)
-    double ub[NF];
-    {
-        const double* c0 = cell(G - 1);
-        const double* c1 = cell(G);
-        const double q = 0.25 * rcp(alpha);
-#pragma unroll
-        for (int m = 0; m < NF; ++m)
-            ub[m] = ((c0[fo[m]] - c0[fo[m] + gmo]) + (c1[fo[m]] - c1[fo[m] + gmo])) * q;
-    }
+    constexpr int S = 2 * R - 1, NQ = NF - 4;
     double pr, vn, v1, v2, e;
     if (!con2prim(k, ub[0], ub[1], ub[2], ub[3], pr, vn, v1, v2, e)) {
 #pragma unroll
@@ -104,9 +96,9 @@ __device__ __forceinline__ bool char_face(Cell cell, const int* fo, int gmo, dou
     const double aN = m2 * ub[1], a1 = m2 * ub[2], a2 = m2 * ub[3];
     const double iEp = rcp(fma(k, e, ub[0]));
 
-    // characteristic fields of one split-flux vector g (memory pointer)
-    auto project = [&](const double* p, double* c) {
-        const double gE = p[fo[0]], gN = p[fo[1]], g1 = p[fo[2]], g2v = p[fo[3]];
+    // characteristic fields of the split-flux vector g+ (s = 0) or g- (s = 1) of cell i
+    auto project = [&](int i, int s, double* c) {
+        const double gE = gval(i, 0, s), gN = gval(i, 1, s), g1 = gval(i, 2, s), g2v = gval(i, 3, s);
         const double de = fma(aE, gE, fma(aN, gN, fma(a1, g1, a2 * g2v)));
         const double t = fma(k, de, gE);
         const double dvn = fma(-vn, t, gN) * iEp;
@@ -122,7 +114,7 @@ __device__ __forceinline__ bool char_face(Cell cell, const int* fo, int gmo, dou
             const double vdv = fma(vn, dvn, fma(v1, dv1, v2 * dv2));
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const double dn = fma(p[fo[4 + q]], ig, -nq[q] * g2 * vdv);
+                const double dn = fma(gval(i, 4 + q, s), ig, -nq[q] * g2 * vdv);
                 c[4 + q] = fma(-Nw[1][q], cp, fma(-Nw[0][q], cm, dn));
             }
         }
@@ -135,7 +127,7 @@ __device__ __forceinline__ bool char_face(Cell cell, const int* fo, int gmo, dou
 #pragma unroll
         for (int i = 0; i < S; ++i) {
             double c[NF];
-            project(cell(i), c);
+            project(i, 0, c);
 #pragma unroll
             for (int m = 0; m < NF; ++m) v[m][i] = c[m];
         }
@@ -147,7 +139,7 @@ __device__ __forceinline__ bool char_face(Cell cell, const int* fo, int gmo, dou
 #pragma unroll
         for (int i = 0; i < S; ++i) {
             double c[NF];
-            project(cell(i + 1) + gmo, c);
+            project(i + 1, 1, c);
 #pragma unroll
             for (int m = 0; m < NF; ++m) v[m][i] = c[m];
         }

@@ -474,6 +474,8 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     if (v.cfg.nq > 1) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint supports one charge (nq <= 1)");
     if (v.cfg.charwise)
         return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint differentiates component-wise WENO only");
+    if (v.cfg.eos_mass != 0.0)
+        return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint differentiates the EOS p = cs2 e only");
     if (v.cfg.scheme == HYDRO_MUSTA_FORCE)
         return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "the adjoint differentiates the WENO schemes only");
     if (v.cfg.bc[2] == HYDRO_BC_HALO)
@@ -700,6 +702,7 @@ extern "C" hydro_status hydro_eps2(hydro_t* h, const double* u, int64_t field_st
     hydro_status s = hydro_handle_view(h, &v);
     if (s) return s;
     if (!eps2) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "eps2 is NULL");
+    if (v.cfg.eos_mass != 0.0) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "eps_2 is implemented for p = cs2 e only");
     const long long fs = v.fs, nc = v.ncell;
     if (u && field_stride < nc) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "field_stride smaller than the cell count");
     if (grad && grad_stride < nc) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "grad_stride smaller than the cell count");

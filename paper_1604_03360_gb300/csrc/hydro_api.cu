@@ -98,6 +98,7 @@ static StageArgs stage_args(hydro_t* h, int stage)
     a.s_out = stage == 3 ? h->S[0] : h->S[stage];
     a.limiter = h->cfg.limiter;
     a.musta_k = musta_stages_of(h->cfg);
+    a.eos_m = h->cfg.eos_mass;
     return a;
 }
 
@@ -265,7 +266,8 @@ static hydro_status after_load(hydro_t* h, double t)
 {
     reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
     prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0] + h->off, h->W[0] + h->off, h->fs, h->ncell,
-                                                                 h->cfg.cs2, h->ctl, h->S[0] ? h->S[0] + h->off : nullptr);
+                                                                 h->cfg.cs2, h->ctl, h->S[0] ? h->S[0] + h->off : nullptr,
+                                                                 h->cfg.eos_mass);
     CK(h, cudaGetLastError(), "prepare");
     h->have_state = true;
     return HYDRO_OK;
@@ -295,10 +297,11 @@ hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stri
     }
     reset_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t);
     prim2con_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(src, ss, h->U[0] + h->off, h->fs, h->ncell, h->cfg.cs2,
-                                                                  h->ctl, h->nf);
+                                                                  h->ctl, h->nf, h->cfg.eos_mass);
     CK(h, cudaGetLastError(), "prim2con");
     prepare_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0] + h->off, h->W[0] + h->off, h->fs, h->ncell,
-                                                                 h->cfg.cs2, h->ctl, h->S[0] ? h->S[0] + h->off : nullptr);
+                                                                 h->cfg.cs2, h->ctl, h->S[0] ? h->S[0] + h->off : nullptr,
+                                                                 h->cfg.eos_mass);
     CK(h, cudaGetLastError(), "prepare");
     h->have_state = true;
     return HYDRO_OK;
@@ -676,7 +679,8 @@ hydro_status hydro_get_primitive(hydro_t* h, double* w, int64_t field_stride, in
     hydro_status s = check_io(h, w, field_stride, mem);
     if (s) return s;
     state_to_prim_kernel<<<blocks_for(h->ncell), 256, 0, h->stream>>>(h->U[0] + h->off, h->fs, h->U[1] + h->off,
-                                                                      h->fs, h->ncell, h->cfg.cs2, h->nf);
+                                                                      h->fs, h->ncell, h->cfg.cs2, h->nf,
+                                                                      h->cfg.eos_mass);
     CK(h, cudaGetLastError(), "state_to_prim");
     s = copy_fields(h, w, field_stride, h->U[1] + h->off, h->fs, h->nf,
                     mem == HYDRO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);

@@ -43,7 +43,7 @@ struct BatchArgs {
 
 __device__ __forceinline__ StageArgs batch_stage_args(const BatchEvent& E, int stage, int zc)
 {
-    StageArgs a;
+    StageArgs a{};
     const int in = stage - 1;
     a.u_in = E.U[in];
     a.w_in = E.W[in];
@@ -345,6 +345,8 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path supports one charge (nq <= 1)");
         if (cfgs[e].charwise)
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path runs component-wise WENO only");
+        if (cfgs[e].eos_mass != 0.0)
+            return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "the batched path runs the EOS p = cs2 e only (eos_mass = 0)");
         if (cfgs[e].scheme != cfgs[0].scheme || cfgs[e].split != cfgs[0].split)
             return bfail(nullptr, HYDRO_ERR_INVALID_ARG, "all events of a batch must use the same scheme and splitting");
     }

@@ -51,14 +51,26 @@ __global__ void halo_replicate_kernel(FieldList fl, long long plane, long long s
 __global__ void reset_ctl_kernel(Ctl* c, double t);
 // primitives and speeds of a state (after set_state)
 // (and, if s != nullptr, the per-axis speeds of every cell: 3 fields)
+// eos_m: mass of the EOS p = cs2 (e - eos_m n_1) (0: p = cs2 e)
 __global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c,
-                               double* s = nullptr);
+                               double* s = nullptr, double eos_m = 0.0);
 // primitives (e, v, n) -> conserved
 __global__ void prim2con_kernel(const double* wp, long long ws, double* u, long long fs, long long n, double cs2,
-                                Ctl* c, int nf);
+                                Ctl* c, int nf, double eos_m = 0.0);
 // conserved -> (e, v, n)
 __global__ void state_to_prim_kernel(const double* u, long long fs, double* out, long long os, long long n,
-                                     double cs2, int nf);
+                                     double cs2, int nf, double eos_m = 0.0);
+// conserved -> (p, v, e) and the squared sound speed for either EOS
+__device__ __forceinline__ bool recover(double cs2, double eos_m, const double* u, long long fs, long long q,
+                                        double& p, double& vx, double& vy, double& vz, double& e, double& ks)
+{
+    ks = cs2;
+    if (eos_m == 0.0) return con2prim(cs2, u[q], u[fs + q], u[2 * fs + q], u[3 * fs + q], p, vx, vy, vz, e);
+    if (!con2prim_gas(cs2, eos_m, u[q], u[fs + q], u[2 * fs + q], u[3 * fs + q], u[4 * fs + q], p, vx, vy, vz, e))
+        return false;
+    ks = sound2_gas(cs2, p, e);
+    return true;
+}
 
 // an axis takes part in the scheme if it has more than one cell; a z axis
 // with stored halos (a slab of a larger grid) always does

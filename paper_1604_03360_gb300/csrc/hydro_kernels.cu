@@ -57,18 +57,19 @@ __global__ void reset_ctl_kernel(Ctl* c, double t)
     c->status = 0;
 }
 
-__global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c, double* s)
+__global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c, double* s,
+                               double eos_m)
 {
     unsigned long long am[3] = {0ull, 0ull, 0ull};
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        double pr, vx, vy, vz, e;
-        if (con2prim(cs2, u[q], u[fs + q], u[2 * fs + q], u[3 * fs + q], pr, vx, vy, vz, e)) {
+        double pr, vx, vy, vz, e, ks;
+        if (recover(cs2, eos_m, u, fs, q, pr, vx, vy, vz, e, ks)) {
             w[q] = pr;
             w[fs + q] = vx;
             w[2 * fs + q] = vy;
             w[3 * fs + q] = vz;
             double sp[3];
-            max_speeds(cs2, vx, vy, vz, sp);
+            max_speeds(ks, vx, vy, vz, sp);
             for (int d = 0; d < 3; ++d) {
                 const unsigned long long b = (unsigned long long)__double_as_longlong(sp[d]);
                 am[d] = b > am[d] ? b : am[d];
@@ -92,15 +93,15 @@ __global__ void prepare_kernel(const double* u, double* w, long long fs, long lo
 }
 
 __global__ void prim2con_kernel(const double* wp, long long ws, double* u, long long fs, long long n, double cs2,
-                                Ctl* c, int nf)
+                                Ctl* c, int nf, double eos_m)
 {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const double e = wp[q], vx = wp[ws + q], vy = wp[2 * ws + q], vz = wp[3 * ws + q], nn = wp[4 * ws + q];
         const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
-        if (!(e > 0.0) || !(v2 < 1.0)) {
+        if (!(e > 0.0) || !(v2 < 1.0) || (eos_m != 0.0 && !(e > eos_m * nn && nn >= 0.0))) {
             if (atomicCAS(&c->status, 0, (int)HYDRO_ERR_UNPHYSICAL) == 0) c->bad_cell = q;
         }
-        const double p = cs2 * e;
+        const double p = eos_m == 0.0 ? cs2 * e : cs2 * (e - eos_m * nn);
         const double g2 = 1.0 / (1.0 - v2);
         const double W = (e + p) * g2;
         u[q] = W - p;
@@ -113,11 +114,11 @@ __global__ void prim2con_kernel(const double* wp, long long ws, double* u, long 
 }
 
 __global__ void state_to_prim_kernel(const double* u, long long fs, double* out, long long os, long long n,
-                                     double cs2, int nf)
+                                     double cs2, int nf, double eos_m)
 {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        double pr, vx, vy, vz, e;
-        if (con2prim(cs2, u[q], u[fs + q], u[2 * fs + q], u[3 * fs + q], pr, vx, vy, vz, e)) {
+        double pr, vx, vy, vz, e, ks;
+        if (recover(cs2, eos_m, u, fs, q, pr, vx, vy, vz, e, ks)) {
             const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
             out[q] = e;
             out[os + q] = vx;
@@ -246,6 +247,9 @@ std::string check_config(const hydro_config* c)
     if (c->split != 0 && c->split != 1) return "split must be 0 (global) or 1 (local Lax-Friedrichs)";
     if (c->nq < 0 || c->nq > 3) return "nq (number of charges) must be 0..3";
     if (c->charwise != 0 && c->charwise != 1) return "charwise must be 0 (component-wise) or 1 (characteristic-wise)";
+    if (!(c->eos_mass >= 0.0) || !std::isfinite(c->eos_mass)) return "eos_mass must be >= 0 and finite";
+    if (c->eos_mass > 0.0 && (c->scheme == HYDRO_MUSTA_FORCE || c->charwise))
+        return "the general EOS (eos_mass > 0) runs component-wise WENO only";
     if (c->charwise && (c->scheme == HYDRO_MUSTA_FORCE || c->split != 0))
         return "characteristic-wise reconstruction needs WENO with global Lax-Friedrichs splitting (split = 0)";
     return std::string();

@@ -53,6 +53,56 @@ __device__ __forceinline__ bool con2prim(double k, double E, double mx, double m
     return true;
 }
 
+// Conserved -> primitive for the general EOS p = k (e - m n), m > 0 (n = R /
+// gamma, the first charge).  The pressure solves f(p) = k (e(p) - m n(p)) - p
+// = 0 with v = M / (E + p), e = E - M.v, n = R sqrt(1 - v^2); f is decreasing
+// (f' = v^2 c_s^2 - 1), f(0) > 0 is required (positive internal energy) and the
+// p = k e pressure brackets the root from above.  Newton steps that leave the
+// bracket are replaced by bisection; stops at f = 0, when the update no longer
+// changes p, or when it is below 1e-15 p (at most 100 steps).  Returns false
+// when no physical state exists.
+static __device__ __noinline__ bool con2prim_gas(double k, double m, double E, double mx, double my, double mz, double R,
+                                          double& p, double& vx, double& vy, double& vz, double& e)
+{
+    const double M2 = fma(mx, mx, fma(my, my, mz * mz));
+    const double d = fma(E, E, -M2);
+    if (!(E > 0.0) || !(d > 0.0) || !(R >= 0.0)) return false;
+    const double iE = rcp(E);
+    const double v20 = M2 * iE * iE;
+    if (!(k * fma(-m * R, sqrt(1.0 - v20), fma(-M2, iE, E)) > 0.0)) return false;   // f(0) > 0
+    const double b = (1.0 - k) * E;
+    double hi = k * ((2.0 * d) * rcp(b + sqrt(fma(b, b, 4.0 * k * d))));
+    double lo = 0.0, x = hi;
+    for (int it = 0; it < 100; ++it) {
+        const double ih = rcp(E + x);
+        const double v2 = M2 * ih * ih;
+        const double ee = fma(-M2, ih, E);
+        const double n = R * sqrt(1.0 - v2);
+        const double f = fma(k, fma(-m, n, ee), -x);
+        if (f == 0.0) break;                      // x is the root
+        const double fp = fma(v2 * (1.0 + k) * x, rcp(ee + x), -1.0);
+        if (f > 0.0) lo = x;
+        else hi = x;
+        double xn = fma(-f, rcp(fp), x);
+        if (xn == x) break;                       // the update is below the rounding of x
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        const double dx = fabs(xn - x);
+        x = xn;
+        if (dx <= 1e-15 * x) break;
+    }
+    if (!(x > 0.0)) return false;
+    const double ih = rcp(E + x);
+    p = x;
+    e = fma(-M2, ih, E);
+    vx = mx * ih;
+    vy = my * ih;
+    vz = mz * ih;
+    return true;
+}
+
+// squared sound speed of the general EOS: (1 + k) p / (e + p)
+__device__ __forceinline__ double sound2_gas(double k, double p, double e) { return (1.0 + k) * p * rcp(e + p); }
+
 // max(|lambda_+|, |lambda_-|) along each axis for p = k e, where
 // lambda_+- = (v_d (1-k) +- sqrt(k (1-v^2)(1 - k v^2 - (1-k) v_d^2))) / (1 - k v^2);
 // with a positive denominator and a non-negative root the larger magnitude is

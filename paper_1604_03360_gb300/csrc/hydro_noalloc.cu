@@ -96,6 +96,7 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, const double
     if (cfg->split != 0) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc supports global splitting only");
     if (cfg->nq > 1) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc supports one charge (nq <= 1)");
     if (cfg->charwise) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc runs component-wise WENO only");
+    if (cfg->eos_mass != 0.0) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc runs the EOS p = cs2 e only");
     if (cfg->bc[2] == HYDRO_BC_HALO) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc runs whole grids (no z halo)");
     if (cfg->scheme == HYDRO_MUSTA_FORCE) return fail(HYDRO_ERR_INVALID_ARG, "hydro_step_noalloc runs the WENO schemes only");
     if (!u_in || !u_out) return fail(HYDRO_ERR_INVALID_ARG, "NULL state pointer");

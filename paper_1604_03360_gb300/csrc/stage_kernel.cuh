@@ -29,11 +29,12 @@
 // previous stage's epilogue) -- and every face forms g+- = f +- alpha_face u
 // itself.  The z ring then holds 2G planes and each z face is computed whole.
 //
-// Characteristic-wise variant (CHW, global LF): cells are staged as in the
+// Characteristic-wise variant (CHW, global LF): x/y cells are staged as in the
 // component-wise scheme (g+ and g-), but every face is one work item that
 // projects its 2G-cell window on the characteristic fields of the face state
 // (char_weno.cuh), reconstructs them and maps the result back, all fields at
-// once.  The z ring holds 2G planes, as for local LF.
+// once.  The z ring holds 2G planes of (u, p, v_z), from which the z faces
+// form g+- themselves.
 #pragma once
 #include "char_weno.cuh"
 #include "hydro_math.cuh"
@@ -65,6 +66,7 @@ struct StageArgs {
     int limiter;            // MUSTA-FORCE only: MUSCL slope limiter (0 minmod, 1 MC, 2 van Leer, 3 superbee)
     int musta_k;            // MUSTA-FORCE only: number of MUSTA stages
     int zlo, zhi;           // planes computed: [zlo, zhi) of the nz stored (0, nz unless z halos are stored)
+    double eos_m;           // EOS p = cs2 (e - eos_m n_1); 0: p = cs2 e
 };
 
 // boundary rule 0 outflow (copy edge cell), 1 periodic; 2 (z only) halo: the
@@ -87,7 +89,10 @@ struct StageSmem {
     static constexpr int NV = LLF ? 2 * NF + 1 : 2 * NF;     // staged values per cell
     static constexpr int NRING = (LLF || CHW) ? 2 * R : 2 * R - 1;    // z planes kept per column
     static constexpr int GXW = TX + 2 * G, GYH = TY + 2 * G;
-    static constexpr int RING = NRING * NV * NT;
+    // z ring values per cell: characteristic-wise keeps (u, p, v_z) and forms
+    // g+- when a face reads them (a smaller ring: two CTAs per SM at 16 x 8)
+    static constexpr int NVR = CHW ? NF + 2 : NV;
+    static constexpr int RING = NRING * NVR * NT;
     static constexpr int GX = NV * TY * GXW;
     static constexpr int GY = NV * GYH * TX;
     static constexpr int FX = NF * TY * (TX + 1);
@@ -163,7 +168,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 {
     static_assert(!(LLF && CHW), "characteristic-wise WENO uses the global Lax-Friedrichs split");
     using SM = StageSmem<R, TX, TY, LLF, NF, CHW>;
-    constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING, NV = SM::NV;
+    constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING, NVR = SM::NVR;
     constexpr int GXW = SM::GXW, GYH = SM::GYH;
     double* ring = smem;
     double* gx = ring + SM::RING;
@@ -199,8 +204,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         const long long q = (long long)bc_map(m, nz, a.bc[2]) * plane + (long long)ys * nx + xs;
         double u[NF], w[4], gp[NF], gm[NF];
         load(q, u, w);
-        double* r = ring + slot_of(m) * NV * NT + tid;
-        if constexpr (LLF) {
+        double* r = ring + slot_of(m) * NVR * NT + tid;
+        if constexpr (CHW) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) r[k * NT] = u[k];
+            r[NF * NT] = w[0];
+            r[(NF + 1) * NT] = w[3];
+        } else if constexpr (LLF) {
             raw_flux<NF>(2, u, w, gp);
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
@@ -222,7 +232,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         double fv[2 * G], uv[2 * G], sv[2 * G];
 #pragma unroll
         for (int i = 0; i < 2 * G; ++i) {
-            const double* r = ring + slot_of(m - G + 1 + i) * NV * NT + tid;
+            const double* r = ring + slot_of(m - G + 1 + i) * NVR * NT + tid;
             fv[i] = r[k * NT];
             uv[i] = r[(NF + k) * NT];
             sv[i] = r[2 * NF * NT];
@@ -235,7 +245,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         double vp[S], vm[S];
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            const double* r = ring + slot_of(m - G + 1 + i) * NV * NT + tid;
+            const double* r = ring + slot_of(m - G + 1 + i) * NVR * NT + tid;
             vp[i] = r[k * NT];
             vm[i] = r[(NF + k) * NT];
         }
@@ -243,14 +253,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         weno_right<R>(vm, a.eps_s, Nm, Dm);
     };
 
-    // characteristic-wise: the whole z face m+1/2 from planes m-G+1 .. m+G
-    int foz[NF];
-#pragma unroll
-    for (int m = 0; m < NF; ++m) foz[m] = rot_field(m, 2) * NT;
+    // characteristic-wise: the whole z face m+1/2 from planes m-G+1 .. m+G,
+    // g+- = f_z +- alpha u formed from the ring's (u, p, v_z)
     auto face_z_chw = [&](int m, double* Fz) {
-        double Fr[NF];
-        auto cell = [&](int i) { return (const double*)(ring + slot_of(m - G + 1 + i) * NV * NT + tid); };
-        const bool ok = char_face<R, NF>(cell, foz, NF * NT, al[2], a.cs2, a.eps_s, Fr);
+        double Fr[NF], ub[NF];
+        auto rp = [&](int i) { return (const double*)(ring + slot_of(m - G + 1 + i) * NVR * NT + tid); };
+        const double az = al[2];
+        auto gval = [&](int i, int f, int s) {
+            // volatile: reload per use rather than keep the window in registers
+            const volatile double* r = rp(i);
+            const double uf = r[rot_field(f, 2) * NT], vz = r[(NF + 1) * NT];
+            const double fl = f == 0 ? r[rot_field(1, 2) * NT] : (f == 1 ? fma(uf, vz, r[NF * NT]) : uf * vz);
+            return s == 0 ? fma(az, uf, fl) : fma(-az, uf, fl);
+        };
+#pragma unroll
+        for (int f = 0; f < NF; ++f) ub[f] = 0.5 * (rp(G - 1)[rot_field(f, 2) * NT] + rp(G)[rot_field(f, 2) * NT]);
+        const bool ok = char_face<R, NF>(gval, ub, a.cs2, a.eps_s, Fr);
 #pragma unroll
         for (int k = 0; k < NF; ++k) Fz[rot_field(k, 2)] = Fr[k];
         return ok;
@@ -401,8 +419,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                     const double* base = gx + row * GXW + f;
 #pragma unroll
                     for (int m = 0; m < NF; ++m) fo[m] = rot_field(m, 0) * (TY * GXW);
-                    auto cell = [&](int i) { return base + i; };
-                    ok = char_face<R, NF>(cell, fo, NF * TY * GXW, al[0], a.cs2, a.eps_s, Fr);
+                    constexpr int gmo = NF * TY * GXW;
+                    auto gval = [&](int i, int m, int s) { return base[i + fo[m] + s * gmo]; };
+                    double ub[NF];
+                    const double q = 0.25 * rcp(al[0]);
+#pragma unroll
+                    for (int m = 0; m < NF; ++m)
+                        ub[m] = ((gval(G - 1, m, 0) - gval(G - 1, m, 1)) + (gval(G, m, 0) - gval(G, m, 1))) * q;
+                    ok = char_face<R, NF>(gval, ub, a.cs2, a.eps_s, Fr);
 #pragma unroll
                     for (int m = 0; m < NF; ++m) Fx[(rot_field(m, 0) * TY + row) * (TX + 1) + f] = Fr[m];
                 } else {
@@ -410,8 +434,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                     const double* base = gy + f * TX + col;
 #pragma unroll
                     for (int m = 0; m < NF; ++m) fo[m] = rot_field(m, 1) * (GYH * TX);
-                    auto cell = [&](int i) { return base + i * TX; };
-                    ok = char_face<R, NF>(cell, fo, NF * GYH * TX, al[1], a.cs2, a.eps_s, Fr);
+                    constexpr int gmo = NF * GYH * TX;
+                    auto gval = [&](int i, int m, int s) { return base[i * TX + fo[m] + s * gmo]; };
+                    double ub[NF];
+                    const double q = 0.25 * rcp(al[1]);
+#pragma unroll
+                    for (int m = 0; m < NF; ++m)
+                        ub[m] = ((gval(G - 1, m, 0) - gval(G - 1, m, 1)) + (gval(G, m, 0) - gval(G, m, 1))) * q;
+                    ok = char_face<R, NF>(gval, ub, a.cs2, a.eps_s, Fr);
 #pragma unroll
                     for (int m = 0; m < NF; ++m) Fy[(rot_field(m, 1) * (TY + 1) + f) * TX + col] = Fr[m];
                 }
@@ -480,14 +510,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 un[k] = (a.ca == 0.0) ? s : fma(a.ca, a.u_n[k * fs + q], a.cb * s);
                 a.u_out[k * fs + q] = un[k];
             }
-            double pr, vx, vy, vz, e;
-            if (con2prim(a.cs2, un[0], un[1], un[2], un[3], pr, vx, vy, vz, e)) {
+            double pr, vx, vy, vz, e, ks = a.cs2;
+            bool okp;
+            if (a.eos_m == 0.0) {
+                okp = con2prim(a.cs2, un[0], un[1], un[2], un[3], pr, vx, vy, vz, e);
+            } else {
+                okp = con2prim_gas(a.cs2, a.eos_m, un[0], un[1], un[2], un[3], un[4], pr, vx, vy, vz, e);
+                if (okp) ks = sound2_gas(a.cs2, pr, e);
+            }
+            if (okp) {
                 a.w_out[q] = pr;
                 a.w_out[fs + q] = vx;
                 a.w_out[2 * fs + q] = vy;
                 a.w_out[3 * fs + q] = vz;
                 double sp[3];
-                max_speeds(a.cs2, vx, vy, vz, sp);
+                max_speeds(ks, vx, vy, vz, sp);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     const unsigned long long b = (unsigned long long)__double_as_longlong(sp[d]);

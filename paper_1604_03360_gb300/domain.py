@@ -50,7 +50,8 @@ def make_slab(g, z0, z1, stream=None):
     return Hydro((g.n[0], g.n[1], z1 - z0), g.dx, scheme=g.scheme, bc=(g.bc[0], g.bc[1], BC_HALO), cs2=g.cs2,
                  cfl=g.cfl, eps=g.eps, origin=origin, dt_fixed=getattr(g, "dt_fixed", 0.0),
                  split=getattr(g, "split", 0), nq=getattr(g, "nq", 1), limiter=getattr(g, "limiter", 0),
-                 musta_stages=getattr(g, "musta_stages", 2), charwise=getattr(g, "charwise", 0), stream=stream)
+                 musta_stages=getattr(g, "musta_stages", 2), charwise=getattr(g, "charwise", 0),
+                 eos_mass=getattr(g, "mass", 0.0), stream=stream)
 
 
 def _zeros(n, device):

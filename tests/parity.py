@@ -22,12 +22,12 @@ def oracle_cfg(g, dt_fixed=None):
     return oracle.make_cfg(g.n, g.dx, cs2=g.cs2, scheme=g.scheme, bc=g.bc, cfl=g.cfl, dt_fixed=dt, eps=g.eps,
                            split=getattr(g, "split", 0), nq=getattr(g, "nq", 1),
                            limiter=getattr(g, "limiter", 0), musta_k=getattr(g, "musta_stages", 2),
-                           charw=getattr(g, "charwise", 0))
+                           charw=getattr(g, "charwise", 0), mass=getattr(g, "mass", 0.0))
 
 
 def run_oracle(g, w, nsteps, t0=0.0, t_end=-1.0):
     c = oracle_cfg(g)
-    u0 = oracle.prim2con(w, g.cs2)
+    u0 = oracle.prim2con(w, g.cs2, getattr(g, "mass", 0.0))
     return oracle.run(c, u0, nsteps, t=t0, t_end=t_end)
 
 
@@ -45,7 +45,7 @@ def run_gpu(g, w, nsteps, t0=0.0, t_end=-1.0, use_primitive=True, u0=None):
 
 def assert_parity(g, w, nsteps, t0=0.0, t_end=-1.0, tol=TOL, use_primitive=True):
     ref, tr, kr = run_oracle(g, w, nsteps, t0, t_end)
-    u0 = oracle.prim2con(w, g.cs2)
+    u0 = oracle.prim2con(w, g.cs2, getattr(g, "mass", 0.0))
     got, tg, kg = run_gpu(g, w, nsteps, t0, t_end, use_primitive=use_primitive, u0=u0)
     assert kg == kr, (kg, kr)
     assert abs(tg - tr) <= 1e-13 * max(1.0, abs(tr)), (tg, tr)

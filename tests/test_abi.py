@@ -41,7 +41,7 @@ def test_version(L):
 
 @pytest.mark.parametrize("field,value,msg", [
     ("scheme", 6, b"scheme"), ("cs2", 1.0, b"cs2"), ("weno_eps", 0.0, b"weno_eps"),
-    ("split", 2, b"split"), ("charwise", 2, b"charwise"),
+    ("split", 2, b"split"), ("charwise", 2, b"charwise"), ("eos_mass", -1.0, b"eos_mass"),
 ])
 def test_invalid_config_rejected(L, field, value, msg):
     import paper_1604_03360_gb300 as H

@@ -117,3 +117,11 @@ def test_charwise_slabs(scheme):
     w = with_flow(g, w)
     g.charwise = 1
     check(g, w, 3, 4, device="cuda")
+
+
+def test_gas_eos_slabs():
+    g, w = W.lumpy(n=(17, 15, 22), seed=23, scheme=5)
+    w = with_flow(g, w)
+    w[0] = w[0] + w[4]
+    g.cs2, g.mass = 2.0 / 3.0, 1.0
+    check(g, w, 3, 4, device="cuda")

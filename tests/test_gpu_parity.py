@@ -433,3 +433,67 @@ def test_charwise_rejected_where_unsupported():
         h.set_primitive(w)
         with pytest.raises(HydroError):
             h.forward_record(2, 1)
+
+
+# ---------------------------------------------------------------- general EOS p = cs2 (e - m n)
+@pytest.mark.parametrize("scheme,split", [(5, 0), (7, 0), (5, 1)])
+def test_gas_shock_tube(scheme, split):
+    g, w = W.gas_sod(N=400, scheme=scheme)
+    g.split = split
+    assert_parity(g, w, 100000, t0=0.0, t_end=0.4)
+
+
+def _gas_lumpy(dims, seed, scheme, m=1.0):
+    g, w = W.lumpy(n=dims, seed=seed, scheme=scheme)
+    w = with_flow(g, w)
+    w[0] = w[0] + m * w[4]            # internal energy e - m n stays positive
+    g.cs2, g.mass = 2.0 / 3.0, m
+    return g, w
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+@pytest.mark.parametrize("dims", [(37, 29, 21), (23, 17, 1), (1, 1, 40)])
+def test_gas_ragged_and_degenerate(scheme, dims):
+    g, w = _gas_lumpy(dims, 7 + sum(dims), scheme)
+    assert_parity(g, w, 6)
+
+
+def test_gas_periodic_local_lf_and_charges():
+    g, w = W.smooth_periodic(n=(19, 13, 11), amp=0.3, vamp=0.5, seed=4, scheme=7)
+    w[0] = w[0] + 0.5 * w[4]
+    g.cs2, g.mass, g.split = 0.4, 0.5, 1
+    assert_parity(g, w, 8)
+    g, w = _gas_lumpy((30, 22, 18), 3, 5)
+    g.nq = 3
+    assert_parity(g, W.with_charges(g, w, 3), 5)
+
+
+def test_gas_primitives_read_back():
+    from paper_1604_03360_gb300 import Hydro
+    g, w = _gas_lumpy((20, 18, 16), 12, 5)
+    with Hydro.from_grid(g) as h:
+        h.set_primitive(w)
+        h.step(3)
+        u = h.get_state()
+        p = h.get_primitive()
+    ref = oracle.con2prim(u, g.cs2, g.mass)
+    assert np.abs(p - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_gas_rejected_where_unsupported():
+    from paper_1604_03360_gb300 import Hydro, HydroBatch, HydroError
+    g, w = _gas_lumpy((12, 11, 10), 2, 5)
+    with pytest.raises(HydroError):
+        HydroBatch([g])
+    with Hydro.from_grid(g) as h:
+        h.set_primitive(w)
+        with pytest.raises(HydroError):
+            h.forward_record(2, 1)
+        with pytest.raises(HydroError):
+            h.eps2()
+    for kw in (dict(scheme=2), dict(charwise=1)):
+        for k, v in kw.items():
+            setattr(g, k, v)
+        with pytest.raises(HydroError):
+            Hydro.from_grid(g)
+        g.scheme, g.charwise = 5, 0

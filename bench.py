@@ -153,6 +153,10 @@ def time_oracle(scheme, steps, sub):
     return gs.cells * steps / dt, dt, oracle.max_threads()
 
 
+def headline_metric(scheme, grid):
+    return "FP64 WENO%d cell-updates/s at %d^3 (ellipsoidal flow); %%HBM peak" % (scheme, grid)
+
+
 def reference_arm(args):
     """The oracle (plain FP64 C, OpenMP over the host cores) on a bounded
     sample of the same workload: each step = one RK3 step of the central
@@ -163,7 +167,7 @@ def reference_arm(args):
     sub = 48
     import oracle
     oracle.build()
-    gs, ws = cpu_sample(args.scheme, sub=sub)
+    gs, ws = cpu_sample(args.scheme, N=args.grid, sub=min(sub, args.grid))
     c = oracle.make_cfg(gs.n, gs.dx, scheme=args.scheme, cfl=gs.cfl)
     u = oracle.prim2con(ws)
     for _ in range(args.warmup):
@@ -173,14 +177,15 @@ def reference_arm(args):
         u = oracle.run(c, u, 1)[0]
     dt = time.perf_counter() - t0
     v = gs.cells * args.steps / dt
-    line = {"impl": "reference", "metric": "FP64 WENO%d cell-updates/s (256^3 ellipsoidal)" % args.scheme,
+    line = {"impl": "reference", "metric": headline_metric(args.scheme, args.grid),
             "value": v, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ellipsoidal-256^3-WENO%d (oracle sample: central %d^3 block per step)"
-                       % (args.scheme, sub)},
+            "config": {"workload": "ellipsoidal-%d^3-WENO%d" % (args.grid, args.scheme), "grid": [args.grid] * 3,
+                       "steps_per_timing": args.steps, "parallelism": "single"},
             "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": "central %d^3 block of the 256^3 workload, %d RK3 steps" % (sub, args.steps)},
+                             "sample": "central %d^3 block of the %d^3 workload, %d RK3 steps"
+                                       % (min(sub, args.grid), args.grid, args.steps)},
             "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -609,7 +614,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "FP64 WENO%d cell-updates/s at %d^3 (ellipsoidal flow); %%HBM peak" % (args.scheme, args.grid),
+            "metric": headline_metric(args.scheme, args.grid),
             "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

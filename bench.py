@@ -408,9 +408,20 @@ def main():
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--charwise", action="store_true",
                     help="headline run with characteristic-wise WENO (profiling; the metric stays component-wise)")
+    ap.add_argument("--only", choices=["adjoint"], default=None,
+                    help="run one extra measurement alone and print it (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.only == "adjoint":
+        import torch
+        from paper_1604_03360_gb300 import build as B
+        B.build()
+        torch.cuda.set_device(0)
+        stream = torch.cuda.current_stream()
+        print(json.dumps({"adjoint_96": adjoint_96(torch.device("cuda", 0), stream, torch.cuda.synchronize)}),
+              flush=True)
+        return
 
     import torch
     from paper_1604_03360_gb300 import Hydro

@@ -10,13 +10,13 @@
 // stage-1 and stage-2 states and run the three stage adjoints in reverse:
 //   u_out = ca u_n + cb (u_s + dt L(u_s))  =>
 //   lam_s = cb lam_out + J_L(u_s)^T (cb dt lam_out),  lam_n += ca lam_out.
-// J_L^T mu is a sum over axes.  Per axis, one thread per (pencil, field)
-// sweeps the pencil's faces with a register window: face adjoint
+// J_L^T mu is a sum over axes.  One launch covers every axis: one thread per
+// (axis, field, pencil) sweeps the pencil's faces with a register window: face adjoint
 // F~bar_{j+1/2} = hdx (mu_{j+1} - mu_j), reverse-mode WENO of both biased
 // reconstructions into the split-flux adjoints gbar+-, ghost-cell
 // contributions folded back onto their source cells by the boundary rule (no
-// atomics anywhere); then a cell kernel applies
-//   ubar += J_f(u)^T (gbar+ + gbar-) + alpha (gbar+ - gbar-).
+// atomics anywhere); then one cell kernel applies, summed over the axes,
+//   ubar = sum_d J_f_d(u)^T (gbar+_d + gbar-_d) + alpha_d (gbar+_d - gbar-_d).
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -166,33 +166,47 @@ struct AdjPencilArgs {
     const double* u;                    // stage input state (5 fields)
     const double* w;                    // its p, v_x, v_y, v_z
     const double* lam;                  // adjoint of the stage output (5 fields)
-    double* gp;                         // out: adjoint of g+ along axis d (5 fields)
-    double* gm;                         // out: adjoint of g- along axis d (5 fields)
+    double* gp;                         // out: adjoint of g+, 5 fields per axis, axis d at gp + 5 d fs
+    double* gm;                         // out: adjoint of g-, same layout
     const unsigned long long* rec;      // step record: speeds [3 stages][3 axes], dt
     long long fs;
     int n[3], bc[3];
-    int d, stage;
-    double hdx, cb, eps_s;
+    int act[3];                         // axes with more than one cell
+    int stage;
+    double hdx[3], cb, eps_s;
 };
 
 template <int R>
 __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
 {
     constexpr int G = R, Wn = 2 * R;
-    const int d = a.d, nd = a.n[d];
+    // thread -> (axis, field, pencil): the active axes' ranges follow one another
+    long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int d = -1;
+    for (int dd = 0; dd < 3; ++dd) {
+        if (!a.act[dd]) continue;
+        const long long cnt = 5LL * a.n[dd == 0 ? 1 : 0] * a.n[dd == 2 ? 1 : 2];
+        if (tid < cnt) {
+            d = dd;
+            break;
+        }
+        tid -= cnt;
+    }
+    if (d < 0) return;
+    const int nd = a.n[d];
     const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
     const long long npen = (long long)a.n[da] * a.n[db];
-    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= npen * 5) return;
     const int k = (int)(tid / npen);
     const long long pen = tid % npen;
+    double* const gpo = a.gp + 5LL * d * a.fs;
+    double* const gmo = a.gm + 5LL * d * a.fs;
     const long long st[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
     const long long base = (pen % a.n[da]) * st[da] + (pen / a.n[da]) * st[db];
     const long long stp = st[d];
     const long long fs = a.fs;
     const double alpha = __longlong_as_double((long long)a.rec[3 * (a.stage - 1) + d]);
     const double dt = __longlong_as_double((long long)a.rec[9]);
-    const double sc = a.cb * dt * a.hdx;
+    const double sc = a.cb * dt * a.hdx[d];
 
     auto gval = [&](int m, double& gpv, double& gmv) {
         const long long q = base + (long long)bc_map(m, nd, a.bc[d]) * stp;
@@ -215,8 +229,8 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
     auto emit = [&](int m, double vp, double vm) {
         if (m >= 0 && m < nd) {
             const long long q = base + (long long)m * stp;
-            a.gp[k * fs + q] = vp;
-            a.gm[k * fs + q] = vm;
+            gpo[k * fs + q] = vp;
+            gmo[k * fs + q] = vm;
         } else if (m < 0) {
 #pragma unroll
             for (int i = 0; i < G; ++i)
@@ -252,29 +266,22 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         const long long ql = base + (long long)bc_map(i - G, nd, a.bc[d]) * stp;
-        a.gp[k * fs + ql] += lo_p[i];
-        a.gm[k * fs + ql] += lo_m[i];
+        gpo[k * fs + ql] += lo_p[i];
+        gmo[k * fs + ql] += lo_m[i];
         const long long qh = base + (long long)bc_map(nd + i, nd, a.bc[d]) * stp;
-        a.gp[k * fs + qh] += hi_p[i];
-        a.gm[k * fs + qh] += hi_m[i];
+        gpo[k * fs + qh] += hi_p[i];
+        gmo[k * fs + qh] += hi_m[i];
     }
 }
 
-// V += J_f(u)^T (gp + gm) + alpha (gp - gm) for axis d
+// V = sum over the active axes d of J_f_d(u)^T (gp_d + gm_d) + alpha_d (gp_d - gm_d)
+// (gp_d, gm_d: 5 fields each at gp + 5 d fs); actmask bit d: axis d is active
 __global__ void adj_flux_kernel(const double* u, const double* w, const double* gp, const double* gm, double* V,
-                                const unsigned long long* rec, int stage, int d, long long fs, long long ncell,
+                                const unsigned long long* rec, int stage, int actmask, long long fs, long long ncell,
                                 double cs2)
 {
-    const double alpha = __longlong_as_double((long long)rec[3 * (stage - 1) + d]);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
          q += (long long)gridDim.x * blockDim.x) {
-        double s[5], t[5];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) {
-            const double a = gp[f * fs + q], b = gm[f * fs + q];
-            s[f] = a + b;
-            t[f] = a - b;
-        }
         const double E = u[q], M[3] = {u[fs + q], u[2 * fs + q], u[3 * fs + q]}, Rr = u[4 * fs + q];
         const double p = w[q], v[3] = {w[fs + q], w[2 * fs + q], w[3 * fs + q]};
         const double h = E + p, ih = 1.0 / h;
@@ -283,18 +290,34 @@ __global__ void adj_flux_kernel(const double* u, const double* w, const double* 
         const double pE = (2.0 * cs2 * E - (1.0 - cs2) * p) * iQ;
         double pM[3];
         for (int j = 0; j < 3; ++j) pM[j] = -2.0 * cs2 * M[j] * iQ;
-        const double vd = v[d];
-        const double S = s[1] * M[0] + s[2] * M[1] + s[3] * M[2] + s[4] * Rr;
-        const double vdE = -vd * (1.0 + pE) * ih;
-        double ub[5];
-        ub[0] = S * vdE + s[1 + d] * pE;
-        for (int j = 0; j < 3; ++j) {
-            const double vdM = ((j == d ? 1.0 : 0.0) - vd * pM[j]) * ih;
-            ub[1 + j] = (j == d ? s[0] : 0.0) + s[1 + j] * vd + S * vdM + s[1 + d] * pM[j];
-        }
-        ub[4] = s[4] * vd;
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int d = 0; d < 3; ++d) {
+            if (!(actmask & (1 << d))) continue;
+            const double alpha = __longlong_as_double((long long)rec[3 * (stage - 1) + d]);
+            const double* gpd = gp + 5LL * d * fs;
+            const double* gmd = gm + 5LL * d * fs;
+            double s[5], t[5];
 #pragma unroll
-        for (int f = 0; f < 5; ++f) V[f * fs + q] += fma(alpha, t[f], ub[f]);
+            for (int f = 0; f < 5; ++f) {
+                const double a = gpd[f * fs + q], b = gmd[f * fs + q];
+                s[f] = a + b;
+                t[f] = a - b;
+            }
+            const double vd = v[d];
+            const double S = s[1] * M[0] + s[2] * M[1] + s[3] * M[2] + s[4] * Rr;
+            const double vdE = -vd * (1.0 + pE) * ih;
+            double ub[5];
+            ub[0] = S * vdE + s[1 + d] * pE;
+            for (int j = 0; j < 3; ++j) {
+                const double vdM = ((j == d ? 1.0 : 0.0) - vd * pM[j]) * ih;
+                ub[1 + j] = (j == d ? s[0] : 0.0) + s[1 + j] * vd + S * vdM + s[1 + d] * pM[j];
+            }
+            ub[4] = s[4] * vd;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) acc[f] += fma(alpha, t[f], ub[f]);
+        }
+#pragma unroll
+        for (int f = 0; f < 5; ++f) V[f * fs + q] = acc[f];
     }
 }
 
@@ -496,7 +519,7 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     w->nckpt = (nsteps + ckpt_every - 1) / ckpt_every;
     w->fs = v.fs;
     const long long fs = v.fs;
-    const long long nfields = 27 + 5 * 4 + 10 + 5LL * w->nckpt + 5LL * ckpt_every;
+    const long long nfields = 27 + 5 * 4 + 30 + 5LL * w->nckpt + 5LL * ckpt_every;
     ACK(h, cudaMalloc(&w->buf, sizeof(double) * (size_t)(fs * nfields)), "adjoint workspace");
     ACK(h, cudaMalloc(&w->rec, sizeof(unsigned long long) * 10 * (size_t)nsteps), "step record");
     ACK(h, cudaMalloc(&w->ctl, sizeof(Ctl)), "scratch control");
@@ -513,8 +536,8 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     w->OUT = p; p += 5 * fs;
     w->ACC = p; p += 5 * fs;
     w->V = p; p += 5 * fs;
-    w->GP = p; p += 5 * fs;
-    w->GM = p; p += 5 * fs;
+    w->GP = p; p += 15 * fs;   // 5 fields per axis
+    w->GM = p; p += 15 * fs;
     w->CK = p; p += 5 * fs * w->nckpt;
     w->SEG = p;
     // forward steps on the handle's own state, recording speeds and dt; the
@@ -579,34 +602,37 @@ static hydro_status stage_adjoint(hydro_t* h, const HandleView& v, AdjointWork* 
 {
     static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     const long long fs = w->fs, nc = v.ncell;
-    ACK(h, cudaMemsetAsync(w->V, 0, sizeof(double) * 5 * fs, v.stream), "zero V");
     const unsigned long long* rec = w->rec + 10 * (long long)step;
+    AdjPencilArgs a{};
+    a.u = u;
+    a.w = ww;
+    a.lam = lam;
+    a.gp = w->GP;
+    a.gm = w->GM;
+    a.rec = rec;
+    a.fs = fs;
+    long long threads = 0;
+    int actmask = 0;
     for (int d = 0; d < 3; ++d) {
-        if (v.cfg.n[d] <= 1) continue;
-        AdjPencilArgs a{};
-        a.u = u;
-        a.w = ww;
-        a.lam = lam;
-        a.gp = w->GP;
-        a.gm = w->GM;
-        a.rec = rec;
-        a.fs = fs;
-        for (int i = 0; i < 3; ++i) {
-            a.n[i] = v.cfg.n[i];
-            a.bc[i] = v.cfg.bc[i];
+        a.n[d] = v.cfg.n[d];
+        a.bc[d] = v.cfg.bc[d];
+        a.act[d] = v.cfg.n[d] > 1;
+        a.hdx[d] = 0.5 / v.cfg.dx[d];
+        if (a.act[d]) {
+            threads += 5LL * (nc / v.cfg.n[d]);
+            actmask |= 1 << d;
         }
-        a.d = d;
-        a.stage = stage;
-        a.hdx = 0.5 / v.cfg.dx[d];
-        a.cb = cb[stage - 1];
-        a.eps_s = v.cfg.weno_eps * (v.R == 3 ? SchemeConst<3>::eps_scale : SchemeConst<4>::eps_scale);
-        const long long threads = 5LL * (nc / v.cfg.n[d]);
+    }
+    a.stage = stage;
+    a.cb = cb[stage - 1];
+    a.eps_s = v.cfg.weno_eps * (v.R == 3 ? SchemeConst<3>::eps_scale : SchemeConst<4>::eps_scale);
+    if (threads > 0) {
         const int blocks = (int)((threads + 127) / 128);
         if (v.R == 3) adj_pencil_kernel<3><<<blocks, 128, 0, v.stream>>>(a);
         else adj_pencil_kernel<4><<<blocks, 128, 0, v.stream>>>(a);
-        adj_flux_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(u, ww, w->GP, w->GM, w->V, rec, stage, d, fs, nc,
-                                                                 v.cfg.cs2);
     }
+    adj_flux_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(u, ww, w->GP, w->GM, w->V, rec, stage, actmask, fs, nc,
+                                                             v.cfg.cs2);
     adj_combine_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(lam, w->V, out, w->ACC, ca[stage - 1], cb[stage - 1],
                                                                add_acc, reset_acc, fs, nc);
     ACK(h, cudaGetLastError(), "stage adjoint");

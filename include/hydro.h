@@ -281,7 +281,8 @@ hydro_status hydro_measure_fp64_peak(void* stream, double* fma_per_second);
  * hydro_forward_record: advance the current state by nsteps RK3 steps (no
  *   t_end), recording each step's speeds and dt and checkpointing the state
  *   every ckpt_every steps (device workspace owned by h, about
- *   (57 + 5 * (ceil(nsteps/ckpt_every) + ckpt_every)) doubles per cell).
+ *   77 + 5 * ceil(nsteps/ckpt_every) + 27 * ckpt_every doubles per cell:
+ *   the reverse sweep keeps every stage input of one segment).
  *   Asynchronous.
  * hydro_adjoint: grad_u0 = (d u_N / d u_0)^T lambda_final for the recorded
  *   run: segment by segment, the step-start states are recomputed from the

@@ -5,9 +5,10 @@
 //
 // Forward with recording: every step stores its speeds (stage inputs) and dt;
 // the state is checkpointed every `ckpt_every` steps.  Backward, segment by
-// segment from the last: recompute the segment's step-start states from its
-// checkpoint with frozen stages, then for each step (last first) rebuild the
-// stage-1 and stage-2 states and run the three stage adjoints in reverse:
+// segment from the last: recompute the segment from its checkpoint with
+// frozen stages, keeping every stage input (u and its primitives) of every
+// step of the segment, then for each step (last first) run the three stage
+// adjoints in reverse:
 //   u_out = ca u_n + cb (u_s + dt L(u_s))  =>
 //   lam_s = cb lam_out + J_L(u_s)^T (cb dt lam_out),  lam_n += ca lam_out.
 // J_L^T mu is a sum over axes.  One launch covers every axis: one thread per
@@ -447,15 +448,18 @@ static hydro_status afail(hydro_t* h, cudaError_t e, const char* where)
 
 static int cells_blocks(long long n) { long long b = (n + 255) / 256; return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b)); }
 
-static StageArgs frozen_stage(const HandleView& v, AdjointWork* w, double** U, double** W, int stage, int step)
+// RK stage `stage` of step `step` with the recorded speeds and dt: input
+// (u_in, w_in), step-start state u_n, output (u_out, w_out)
+static StageArgs frozen_stage_at(const HandleView& v, AdjointWork* w, const double* u_in, const double* w_in,
+                                 const double* u_n, double* u_out, double* w_out, int stage, int step)
 {
     StageArgs a{};
     const int in = stage - 1;
-    a.u_in = U[in];
-    a.w_in = W[in];
-    a.u_n = U[0];
-    a.u_out = stage == 3 ? U[0] : U[stage];
-    a.w_out = stage == 3 ? W[0] : W[stage];
+    a.u_in = u_in;
+    a.w_in = w_in;
+    a.u_n = u_n;
+    a.u_out = u_out;
+    a.w_out = w_out;
     a.fs = w->fs;
     a.nx = v.cfg.n[0];
     a.ny = v.cfg.n[1];
@@ -480,6 +484,11 @@ static StageArgs frozen_stage(const HandleView& v, AdjointWork* w, double** U, d
     a.bad_cell = &v.ctl->bad_cell;
     return a;
 }
+
+// segment storage: step i of the segment keeps its three stage inputs, each
+// the 5 conserved fields followed by the 4 primitive fields (27 fields a step)
+static double* seg_u(AdjointWork* w, int i, int k) { return w->SEG + w->fs * (27LL * i + 9LL * k); }
+static double* seg_w(AdjointWork* w, int i, int k) { return w->SEG + w->fs * (27LL * i + 9LL * k + 5); }
 
 static dim3 stage_grid(const HandleView& v)
 {
@@ -519,7 +528,7 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     w->nckpt = (nsteps + ckpt_every - 1) / ckpt_every;
     w->fs = v.fs;
     const long long fs = v.fs;
-    const long long nfields = 27 + 5 * 4 + 30 + 5LL * w->nckpt + 5LL * ckpt_every;
+    const long long nfields = 27 + 5 * 4 + 30 + 5LL * w->nckpt + 27LL * ckpt_every;
     ACK(h, cudaMalloc(&w->buf, sizeof(double) * (size_t)(fs * nfields)), "adjoint workspace");
     ACK(h, cudaMalloc(&w->rec, sizeof(unsigned long long) * 10 * (size_t)nsteps), "step record");
     ACK(h, cudaMalloc(&w->ctl, sizeof(Ctl)), "scratch control");
@@ -660,33 +669,29 @@ extern "C" hydro_status hydro_adjoint(hydro_t* h, const double* lambda_final, do
     const int N = w->nsteps, C = w->ckpt;
     for (int seg = w->nckpt - 1; seg >= 0; --seg) {
         const int s0 = seg * C, s1 = (s0 + C < N) ? s0 + C : N;
-        // step-start states of the segment, recomputed with frozen stages
-        ACK(h, cudaMemcpyAsync(w->AU[0], w->CK + 5 * fs * seg, sizeof(double) * 5 * fs, cudaMemcpyDeviceToDevice,
+        // the segment recomputed from its checkpoint with frozen stages; every
+        // stage input is kept (the last step's third stage is not needed)
+        ACK(h, cudaMemcpyAsync(seg_u(w, 0, 0), w->CK + 5 * fs * seg, sizeof(double) * 5 * fs, cudaMemcpyDeviceToDevice,
                                v.stream), "restore");
+        prepare_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(seg_u(w, 0, 0), seg_w(w, 0, 0), fs, nc, v.cfg.cs2, w->ctl);
         for (int n = s0; n < s1; ++n) {
-            ACK(h, cudaMemcpyAsync(w->SEG + 5 * fs * (n - s0), w->AU[0], sizeof(double) * 5 * fs,
-                                   cudaMemcpyDeviceToDevice, v.stream), "segment");
-            if (n == s1 - 1) break;
-            prepare_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(w->AU[0], w->AW[0], fs, nc, v.cfg.cs2, w->ctl);
+            const int i = n - s0;
             for (int st = 1; st <= 3; ++st) {
-                const StageArgs a = frozen_stage(v, w, w->AU, w->AW, st, n);
+                if (st == 3 && n == s1 - 1) break;
+                const StageArgs a = frozen_stage_at(v, w, seg_u(w, i, st - 1), seg_w(w, i, st - 1), seg_u(w, i, 0),
+                                                    st < 3 ? seg_u(w, i, st) : seg_u(w, i + 1, 0),
+                                                    st < 3 ? seg_w(w, i, st) : seg_w(w, i + 1, 0), st, n);
                 v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
             }
         }
         for (int n = s1 - 1; n >= s0; --n) {
-            ACK(h, cudaMemcpyAsync(w->AU[0], w->SEG + 5 * fs * (n - s0), sizeof(double) * 5 * fs,
-                                   cudaMemcpyDeviceToDevice, v.stream), "segment state");
-            prepare_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(w->AU[0], w->AW[0], fs, nc, v.cfg.cs2, w->ctl);
-            for (int st = 1; st <= 2; ++st) {
-                const StageArgs a = frozen_stage(v, w, w->AU, w->AW, st, n);
-                v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
-            }
+            const int i = n - s0;
             // stage 3 (input u2): lam_u2 = 2/3 lam + J^T(2/3 dt lam); acc = 1/3 lam
-            if ((s = stage_adjoint(h, v, w, w->AU[2], w->AW[2], 3, n, w->LAM, w->OUT, 0, 1))) return s;
+            if ((s = stage_adjoint(h, v, w, seg_u(w, i, 2), seg_w(w, i, 2), 3, n, w->LAM, w->OUT, 0, 1))) return s;
             // stage 2 (input u1): lam_u1 = 1/4 lam_u2 + J^T(1/4 dt lam_u2); acc += 3/4 lam_u2
-            if ((s = stage_adjoint(h, v, w, w->AU[1], w->AW[1], 2, n, w->OUT, w->LAM, 0, 0))) return s;
+            if ((s = stage_adjoint(h, v, w, seg_u(w, i, 1), seg_w(w, i, 1), 2, n, w->OUT, w->LAM, 0, 0))) return s;
             // stage 1 (input u^n): lam_n = acc + lam_u1 + J^T(dt lam_u1)
-            if ((s = stage_adjoint(h, v, w, w->AU[0], w->AW[0], 1, n, w->LAM, w->OUT, 1, 0))) return s;
+            if ((s = stage_adjoint(h, v, w, seg_u(w, i, 0), seg_w(w, i, 0), 1, n, w->LAM, w->OUT, 1, 0))) return s;
             double* t = w->LAM;
             w->LAM = w->OUT;
             w->OUT = t;

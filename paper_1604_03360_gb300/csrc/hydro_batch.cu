@@ -133,7 +133,7 @@ template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
 static cudaError_t batch_info_for(BatchLaunch* out)
 {
     out->fn = batch_stage_kernel<R, TX, TY, ILP, LLF>;
-    out->smem = StageSmem<R, TX, TY, LLF>::bytes;
+    out->smem = StageSmem<R, TX, TY, LLF, 5, false, ILP == kPencilSweep>::bytes;
     out->tx = TX;
     out->ty = TY;
     cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<R, TX, TY, ILP, LLF>,
@@ -157,11 +157,15 @@ static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* ou
         if (v == 1) return batch_info_for<3, 16, 8>(out);
         if (v == 2) return batch_info_for<3, 32, 8>(out);
         if (v == 3) return batch_info_for<3, 16, 16, 2>(out);
+        if (v == 4) return batch_info_for<3, 16, 16, kPencilSweep>(out);
+        if (v == 5) return batch_info_for<3, 16, 8, kPencilSweep>(out);
     }
     if (R == 4) {
         if (v == 0) return batch_info_for<4, 16, 16>(out);
         if (v == 1) return batch_info_for<4, 16, 8>(out);
         if (v == 2) return batch_info_for<4, 16, 16, 2>(out);
+        if (v == 3) return batch_info_for<4, 16, 16, kPencilSweep>(out);
+        if (v == 4) return batch_info_for<4, 16, 8, kPencilSweep>(out);
     }
     return cudaErrorInvalidValue;
 }

@@ -135,7 +135,7 @@ template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5>
 static cudaError_t info_for(StageLaunch* out)
 {
     out->fn = stage_kernel<R, TX, TY, ILP, LLF, NF>;
-    out->smem = StageSmem<R, TX, TY, LLF, NF>::bytes;
+    out->smem = StageSmem<R, TX, TY, LLF, NF, false, ILP == kPencilSweep>::bytes;
     out->tx = TX;
     out->ty = TY;
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY, ILP, LLF, NF>,
@@ -146,9 +146,10 @@ static cudaError_t info_for(StageLaunch* out)
 }
 
 // WENO5: 16x16 (1 CTA of 8 warps per SM), 16x8 (2 CTAs of 4 warps), 32x8,
-//        16x16 with two face items per iteration.
+//        16x16 with two face items per iteration, pencil sweeps on 16x16 and
+//        16x8.
 // WENO7: 16x16 (8 warps, 221 KB shared memory), 16x8 (4 warps), 16x16 with two
-//        face items per iteration.
+//        face items per iteration, pencil sweeps on 16x16 and 16x8.
 // Local LF (raw staging, 2G-plane ring): WENO5 16x16 and 16x8; WENO7 16x8
 // (16x16 would need 247 KB of shared memory).
 // Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
@@ -158,7 +159,7 @@ int launch_variant_count(int R, int split, int nq, int charw)
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 2 : 1;
-    return R == 3 ? 4 : 3;
+    return R == 3 ? 6 : 5;
 }
 
 template <int NF>
@@ -209,11 +210,15 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 1) return info_for<3, 16, 8>(out);
         if (v == 2) return info_for<3, 32, 8>(out);
         if (v == 3) return info_for<3, 16, 16, 2>(out);
+        if (v == 4) return info_for<3, 16, 16, kPencilSweep>(out);
+        if (v == 5) return info_for<3, 16, 8, kPencilSweep>(out);
     }
     if (R == 4) {
         if (v == 0) return info_for<4, 16, 16>(out);
         if (v == 1) return info_for<4, 16, 8>(out);
         if (v == 2) return info_for<4, 16, 16, 2>(out);
+        if (v == 3) return info_for<4, 16, 16, kPencilSweep>(out);
+        if (v == 4) return info_for<4, 16, 8, kPencilSweep>(out);
     }
     return cudaErrorInvalidValue;
 }

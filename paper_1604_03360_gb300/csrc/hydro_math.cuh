@@ -135,25 +135,89 @@ __device__ __forceinline__ void max_speeds(double k, double vx, double vy, doubl
 // 2nd differences s_k = d_{k+1} - d_k, first-derivative forms
 // t0 = 3 d1 - d0, t1 = d1 + d2, t2 = 3 d2 - d3 (same values as the
 // Jiang-Shu forms a - 4b + 3c, d - b, -3c + 4d - e).
-__device__ __forceinline__ void weno5(double a, double b, double c, double d, double e, double eps_s,
-                                      double& N, double& D)
+//
+// The differences of a window do not depend on the face it serves, so a sweep
+// along a pencil carries them from one face to the next (Diff5 / Diff7): the
+// window v_{j-r+1} .. v_{j+r-1} of face j+1/2 shares all but one difference
+// of each order with the window of face j+3/2.  weno5 / weno7 compute them
+// afresh; the *_slide functions update them for a window moved by one cell,
+// with the same operations on the same operands, so a sweep gives the same
+// bits as fresh windows.
+struct Diff5 {
+    double d[4];     // d_i = v_{i+1} - v_i
+    double s[3];     // s_k = d_{k+1} - d_k
+    double ks[3];    // 13/3 s_k
+};
+
+__device__ __forceinline__ void weno5_diffs(const double* v, Diff5& q)
 {
-    const double d0 = b - a, d1 = c - b, d2 = d - c, d3 = e - d;
-    const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q.d[i] = v[i + 1] - v[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        q.s[k] = q.d[k + 1] - q.d[k];
+        q.ks[k] = (13.0 / 3.0) * q.s[k];
+    }
+}
+
+// window moved one cell up the array (v is the new window): the new cell
+// enters at v[4]
+__device__ __forceinline__ void weno5_slide(const double* v, Diff5& q)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q.d[i] = q.d[i + 1];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        q.s[k] = q.s[k + 1];
+        q.ks[k] = q.ks[k + 1];
+    }
+    q.d[3] = v[4] - v[3];
+    q.s[2] = q.d[3] - q.d[2];
+    q.ks[2] = (13.0 / 3.0) * q.s[2];
+}
+
+// mirrored window moved one cell (m is the new mirrored window): the new
+// cell enters at m[0]
+__device__ __forceinline__ void weno5_slide_mirror(const double* m, Diff5& q)
+{
+#pragma unroll
+    for (int i = 3; i > 0; --i) q.d[i] = q.d[i - 1];
+#pragma unroll
+    for (int k = 2; k > 0; --k) {
+        q.s[k] = q.s[k - 1];
+        q.ks[k] = q.ks[k - 1];
+    }
+    q.d[0] = m[1] - m[0];
+    q.s[0] = q.d[1] - q.d[0];
+    q.ks[0] = (13.0 / 3.0) * q.s[0];
+}
+
+__device__ __forceinline__ void weno5_core(const double* v, const Diff5& q, double eps_s, double& N, double& D)
+{
+    const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3];
     const double t0 = fma(3.0, d1, -d0), t1 = d1 + d2, t2 = fma(3.0, d2, -d3);
-    const double k13 = 13.0 / 3.0;
-    const double b0 = fma(k13 * s0, s0, fma(t0, t0, eps_s));
-    const double b1 = fma(k13 * s1, s1, fma(t1, t1, eps_s));
-    const double b2 = fma(k13 * s2, s2, fma(t2, t2, eps_s));
+    const double b0 = fma(q.ks[0], q.s[0], fma(t0, t0, eps_s));
+    const double b1 = fma(q.ks[1], q.s[1], fma(t1, t1, eps_s));
+    const double b2 = fma(q.ks[2], q.s[2], fma(t2, t2, eps_s));
     const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2;
     const double P0 = w1 * w2, P1 = w0 * w2, P2 = w0 * w1;
     // 10 d_k q_k: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6 = c - d0/3 + 5 d1/6,
     // q1 = (-b+5c+2d)/6, q2 = (2c+5d-e)/6
+    const double b = v[1], c = v[2], d = v[3], e = v[4];
     const double n0 = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, c));
     const double n1 = fma(2.0, d, fma(5.0, c, -b));
     const double n2 = fma(-0.5, e, fma(2.5, d, c));
     N = fma(n0, P0, fma(n1, P1, n2 * P2));
     D = fma(3.0, P2, fma(6.0, P1, P0));
+}
+
+__device__ __forceinline__ void weno5(double a, double b, double c, double d, double e, double eps_s,
+                                      double& N, double& D)
+{
+    const double v[5] = {a, b, c, d, e};
+    Diff5 q;
+    weno5_diffs(v, q);
+    weno5_core(v, q, eps_s, N, D);
 }
 
 // r = 4 (Balsara-Shu weights from the same definition).  For the cubic
@@ -166,34 +230,86 @@ __device__ __forceinline__ void weno5(double a, double b, double c, double d, do
 // C_k = e_{k+1} - e_k (third differences); B0 = 2 e1 - e0, B1 = B2 = e2,
 // B3 = 2 e3 - e4; A0 = 2 d0 - 7 d1 + 11 d2, A1 = -d1 + 5 d2 + 2 d3,
 // A2 = 2 d2 + 5 d3 - d4, A3 = 11 d3 - 7 d4 + 2 d5 (identical values to the
-// forms written on the cell values).
-__device__ __forceinline__ void weno7(const double* v, double eps_s, double& N, double& D)
+// forms written on the cell values).  The term 781/20 C_k^2 + eps depends on
+// the cells of stencil k only, so it is carried with the differences.
+struct Diff7 {
+    double d[6];     // d_i = v_{i+1} - v_i
+    double e[5];     // e_i = d_{i+1} - d_i
+    double ct[4];    // 781/20 C_k^2 + eps_s, C_k = e_{k+1} - e_k
+};
+
+__device__ __forceinline__ double w7_cterm(double C, double eps_s) { return fma((781.0 / 20.0) * C, C, eps_s); }
+
+__device__ __forceinline__ void weno7_diffs(const double* v, double eps_s, Diff7& q)
 {
-    const double v0 = v[0], v1 = v[1], v2 = v[2], v3 = v[3], v4 = v[4], v5 = v[5], v6 = v[6];
-    const double d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3, d4 = v5 - v4, d5 = v6 - v5;
-    const double e0 = d1 - d0, e1 = d2 - d1, e2 = d3 - d2, e3 = d4 - d3, e4 = d5 - d4;
-    const double C0 = e1 - e0, C1 = e2 - e1, C2 = e3 - e2, C3 = e4 - e3;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q.d[i] = v[i + 1] - v[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) q.e[i] = q.d[i + 1] - q.d[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q.ct[k] = w7_cterm(q.e[k + 1] - q.e[k], eps_s);
+}
+
+// window moved one cell up the array: the new cell enters at v[6]
+__device__ __forceinline__ void weno7_slide(const double* v, double eps_s, Diff7& q)
+{
+#pragma unroll
+    for (int i = 0; i < 5; ++i) q.d[i] = q.d[i + 1];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q.e[i] = q.e[i + 1];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) q.ct[k] = q.ct[k + 1];
+    q.d[5] = v[6] - v[5];
+    q.e[4] = q.d[5] - q.d[4];
+    q.ct[3] = w7_cterm(q.e[4] - q.e[3], eps_s);
+}
+
+// mirrored window moved one cell: the new cell enters at m[0]
+__device__ __forceinline__ void weno7_slide_mirror(const double* m, double eps_s, Diff7& q)
+{
+#pragma unroll
+    for (int i = 5; i > 0; --i) q.d[i] = q.d[i - 1];
+#pragma unroll
+    for (int i = 4; i > 0; --i) q.e[i] = q.e[i - 1];
+#pragma unroll
+    for (int k = 3; k > 0; --k) q.ct[k] = q.ct[k - 1];
+    q.d[0] = m[1] - m[0];
+    q.e[0] = q.d[1] - q.d[0];
+    q.ct[0] = w7_cterm(q.e[1] - q.e[0], eps_s);
+}
+
+__device__ __forceinline__ void weno7_core(const double* v, const Diff7& q, double& N, double& D)
+{
+    const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3], d4 = q.d[4], d5 = q.d[5];
+    const double e0 = q.e[0], e1 = q.e[1], e2 = q.e[2], e3 = q.e[3], e4 = q.e[4];
     const double B0 = fma(2.0, e1, -e0), B12 = e2, B3 = fma(2.0, e3, -e4);
     const double A0 = fma(11.0, d2, fma(-7.0, d1, 2.0 * d0));
     const double A1 = fma(2.0, d3, fma(5.0, d2, -d1));
     const double A2 = fma(5.0, d3, fma(2.0, d2, -d4));
     const double A3 = fma(2.0, d5, fma(-7.0, d4, 11.0 * d3));
-    const double kc = 781.0 / 20.0;
     const double b39 = 39.0 * B12;
-    const double b0 = fma(A0, A0, fma(39.0 * B0, B0, fma(kc * C0, C0, eps_s)));
-    const double b1 = fma(A1, A1, fma(b39, B12, fma(kc * C1, C1, eps_s)));
-    const double b2 = fma(A2, A2, fma(b39, B12, fma(kc * C2, C2, eps_s)));
-    const double b3 = fma(A3, A3, fma(39.0 * B3, B3, fma(kc * C3, C3, eps_s)));
+    const double b0 = fma(A0, A0, fma(39.0 * B0, B0, q.ct[0]));
+    const double b1 = fma(A1, A1, fma(b39, B12, q.ct[1]));
+    const double b2 = fma(A2, A2, fma(b39, B12, q.ct[2]));
+    const double b3 = fma(A3, A3, fma(39.0 * B3, B3, q.ct[3]));
     const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2, w3 = b3 * b3;
     const double p01 = w0 * w1, p23 = w2 * w3;
     const double P0 = w1 * p23, P1 = w0 * p23, P2 = p01 * w3, P3 = p01 * w2;
     // 35 d_k q_k, d = (1, 12, 18, 4)/35; q0 = v3 + d0/4 - 5 d1/6 + 13 d2/12
+    const double v1 = v[1], v2 = v[2], v3 = v[3], v4 = v[4], v5 = v[5], v6 = v[6];
     const double n0 = fma(13.0 / 12.0, d2, fma(-5.0 / 6.0, d1, fma(0.25, d0, v3)));
     const double n1 = fma(3.0, v4, fma(13.0, v3, fma(-5.0, v2, v1)));
     const double n2 = fma(10.5, v3 + v4, -1.5 * (v2 + v5));
     const double n3 = fma(13.0 / 3.0, v4, fma(-5.0 / 3.0, v5, fma(1.0 / 3.0, v6, v3)));
     N = fma(n0, P0, fma(n1, P1, fma(n2, P2, n3 * P3)));
     D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
+}
+
+__device__ __forceinline__ void weno7(const double* v, double eps_s, double& N, double& D)
+{
+    Diff7 q;
+    weno7_diffs(v, eps_s, q);
+    weno7_core(v, q, N, D);
 }
 
 template <int R>

@@ -83,12 +83,14 @@ __device__ __forceinline__ int bc_map(int i, int n, int bc)
     return i < 0 ? 0 : n - 1;
 }
 
-template <int R, int TX, int TY, bool LLF = false, int NF = 5, bool CHW = false>
+template <int R, int TX, int TY, bool LLF = false, int NF = 5, bool CHW = false, bool SWP = false>
 struct StageSmem {
     static constexpr int G = R, S = 2 * R - 1, NT = TX * TY;
     static constexpr int NV = LLF ? 2 * NF + 1 : 2 * NF;     // staged values per cell
     static constexpr int NRING = (LLF || CHW) ? 2 * R : 2 * R - 1;    // z planes kept per column
-    static constexpr int GXW = TX + 2 * G, GYH = TY + 2 * G;
+    // x rows of the staged split fluxes; the pencil sweep reads one row per
+    // lane, so its pitch is odd (no shared-memory bank conflicts)
+    static constexpr int GXW = TX + 2 * G + ((SWP && (TX + 2 * G) % 2 == 0) ? 1 : 0), GYH = TY + 2 * G;
     // z ring values per cell: characteristic-wise keeps (u, p, v_z) and forms
     // g+- when a face reads them (a smaller ring: two CTAs per SM at 16 x 8)
     static constexpr int NVR = CHW ? NF + 2 : NV;
@@ -163,11 +165,51 @@ __device__ __forceinline__ double llf_face(const double* f, const double* u, con
 
 // One work item: column tile (tile_x, tile_y) of TX x TY cells and z chunk chunk_z of the
 // grid described by a.  All threads of the CTA call it with the same item.
+// Face work of step 3 (component-wise, global LF): ILP = 1 or 2 takes one or
+// two independent (face, field) items per thread and iteration; ILP =
+// kPencilSweep has every lane sweep a run of consecutive faces of one pencil
+// (axis, field, row or column), carrying the stencil differences from face to
+// face (Diff5 / Diff7).
+constexpr int kPencilSweep = 0;
+
+template <int R> struct DiffOf;
+template <> struct DiffOf<3> { using T = Diff5; };
+template <> struct DiffOf<4> { using T = Diff7; };
+
+template <int R>
+__device__ __forceinline__ void diffs_fresh(const double* v, double eps_s, typename DiffOf<R>::T& q)
+{
+    if constexpr (R == 3) weno5_diffs(v, q);
+    else weno7_diffs(v, eps_s, q);
+}
+template <int R>
+__device__ __forceinline__ void diffs_slide(const double* v, double eps_s, typename DiffOf<R>::T& q)
+{
+    if constexpr (R == 3) weno5_slide(v, q);
+    else weno7_slide(v, eps_s, q);
+}
+template <int R>
+__device__ __forceinline__ void diffs_slide_mirror(const double* m, double eps_s, typename DiffOf<R>::T& q)
+{
+    if constexpr (R == 3) weno5_slide_mirror(m, q);
+    else weno7_slide_mirror(m, eps_s, q);
+}
+template <int R>
+__device__ __forceinline__ void weno_core(const double* v, const typename DiffOf<R>::T& q, double eps_s, double& N,
+                                          double& D)
+{
+    if constexpr (R == 3) weno5_core(v, q, eps_s, N, D);
+    else weno7_core(v, q, N, D);
+}
+
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
 {
     static_assert(!(LLF && CHW), "characteristic-wise WENO uses the global Lax-Friedrichs split");
-    using SM = StageSmem<R, TX, TY, LLF, NF, CHW>;
+    constexpr bool SWP = (ILP == kPencilSweep);
+    static_assert(!(SWP && (LLF || CHW)), "the pencil sweep serves the component-wise global-LF scheme");
+    static_assert((TX * TY) % 32 == 0, "whole warps");
+    using SM = StageSmem<R, TX, TY, LLF, NF, CHW, SWP>;
     constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING, NVR = SM::NVR;
     constexpr int GXW = SM::GXW, GYH = SM::GYH;
     double* ring = smem;
@@ -315,6 +357,27 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     const int ngx = a.act[0] ? nrow * wx : 0;
     const int ngy = a.act[1] ? hy * ncol : 0;
 
+    // Pencil-sweep schedule (SWP): pencils x (field, row) then y (field,
+    // column), 32 per group, one per lane.  A group takes as many steps as its
+    // longest pencil has faces; the (group, face) steps are dealt out to the
+    // warps in contiguous runs, so every lane of a warp starts a new window at
+    // the same step and the sweep never diverges.
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = NT / 32;
+    const int npx = a.act[0] ? NF * nrow : 0, npy = a.act[1] ? NF * ncol : 0, npen = npx + npy;
+    auto pen_faces = [&](int P) { return P < npx ? ncol + 1 : nrow + 1; };
+    auto group_len = [&](int g) { return max(pen_faces(32 * g), pen_faces(min(32 * g + 31, npen - 1))); };
+    int sw_g0 = 0, sw_f0 = 0, sw_u0 = 0, sw_u1 = 0;
+    if constexpr (SWP) {
+        const int ngrp = (npen + 31) / 32;
+        int units = 0;
+        for (int g = 0; g < ngrp; ++g) units += group_len(g);
+        sw_u0 = units * warp / NW;
+        sw_u1 = units * (warp + 1) / NW;
+        sw_f0 = sw_u0;
+        while (sw_g0 < ngrp && sw_f0 >= group_len(sw_g0)) sw_f0 -= group_len(sw_g0++);
+    }
+
     for (int p = zb; p < ze; ++p) {
         // 1. z: ingest plane p+G, face p+1/2 = R+(p) + R-(p+1)
         if (zwork && LLF) {
@@ -460,6 +523,60 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 const int fb = (it < nfx) ? TY * GXW : GYH * TX;      // one field block
                 const int k = (it < nfx) ? it / (nrow * (ncol + 1)) : (it - nfx) / ((nrow + 1) * ncol);
                 *out = llf_face<R>(pp, pp + NF * fb, pp + (2 * NF - k) * fb, st, a.eps_s);
+            }
+        } else if constexpr (SWP) {
+            using DF = typename DiffOf<R>::T;
+            int g = sw_g0, f = sw_f0;
+            for (int u = sw_u0; u < sw_u1; ++g, f = 0) {
+                const int fe = min(group_len(g), f + (sw_u1 - u));
+                const int P = 32 * g + lane;
+                // this lane's pencil: staged g+ row (pp) and g- row (pm, one
+                // cell further), element stride, output row; idle lanes read
+                // the first staged row and store nothing
+                const double* pp = gx;
+                const double* pm = gx;
+                int st = 1, nf = 1, ost = 1;
+                double* out = nullptr;
+                if (P < npx) {
+                    const int k = P / nrow, row = P % nrow;
+                    pp = gx + (k * TY + row) * GXW;
+                    pm = gx + ((NF + k) * TY + row) * GXW + 1;
+                    out = Fx + (k * TY + row) * (TX + 1);
+                    nf = ncol + 1;
+                } else if (P < npen) {
+                    const int k = (P - npx) / ncol, col = (P - npx) % ncol;
+                    pp = gy + k * GYH * TX + col;
+                    pm = gy + ((NF + k) * GYH + 1) * TX + col;
+                    st = TX;
+                    out = Fy + k * (TY + 1) * TX + col;
+                    ost = TX;
+                    nf = nrow + 1;
+                }
+                DF qp, qm;
+                for (int ff = f; ff < fe; ++ff) {
+                    // lanes whose pencil is shorter than the group repeat its
+                    // last face (in bounds) and store nothing
+                    const int fc = min(ff, nf - 1);
+                    double vp[S], vm[S];
+#pragma unroll
+                    for (int i = 0; i < S; ++i) {
+                        vp[i] = pp[(fc + i) * st];
+                        vm[i] = pm[(fc + S - 1 - i) * st];    // mirrored window of the right-biased stencil
+                    }
+                    if (ff == f) {
+                        diffs_fresh<R>(vp, a.eps_s, qp);
+                        diffs_fresh<R>(vm, a.eps_s, qm);
+                    } else {
+                        diffs_slide<R>(vp, a.eps_s, qp);
+                        diffs_slide_mirror<R>(vm, a.eps_s, qm);
+                    }
+                    double Np, Dp, Nm, Dm;
+                    weno_core<R>(vp, qp, a.eps_s, Np, Dp);
+                    weno_core<R>(vm, qm, a.eps_s, Nm, Dm);
+                    const double F = face_sum(Np, Dp, Nm, Dm);
+                    if (out && ff < nf) out[ff * ost] = F;
+                }
+                u += fe - f;
             }
         } else
         for (int it0 = tid; it0 < nitems; it0 += ILP * NT) {

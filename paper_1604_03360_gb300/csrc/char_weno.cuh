@@ -121,7 +121,7 @@ __device__ __forceinline__ bool char_face(GV gval, const double* ub, double k, d
     };
 
     // 4. reconstruct: + side from cells 0 .. S-1, - side from cells 1 .. S
-    double Np[NF], Dp[NF], Fc[NF];
+    double Np[NF], Dp[NF], Cp[NF], Fc[NF];
     {
         double v[NF][S];
 #pragma unroll
@@ -132,7 +132,10 @@ __device__ __forceinline__ bool char_face(GV gval, const double* ub, double k, d
             for (int m = 0; m < NF; ++m) v[m][i] = c[m];
         }
 #pragma unroll
-        for (int m = 0; m < NF; ++m) weno_left<R>(v[m], eps_s, Np[m], Dp[m]);
+        for (int m = 0; m < NF; ++m) {
+            weno_left<R>(v[m], eps_s, Np[m], Dp[m]);
+            Cp[m] = v[m][R - 1];
+        }
     }
     {
         double v[NF][S];
@@ -147,7 +150,7 @@ __device__ __forceinline__ bool char_face(GV gval, const double* ub, double k, d
         for (int m = 0; m < NF; ++m) {
             double Nm, Dm;
             weno_right<R>(v[m], eps_s, Nm, Dm);
-            Fc[m] = face_sum(Np[m], Dp[m], Nm, Dm);
+            Fc[m] = face_sum(Np[m], Dp[m], Cp[m], Nm, Dm, v[m][R - 1]);
         }
     }
 

@@ -192,7 +192,9 @@ __device__ __forceinline__ void weno5_slide_mirror(const double* m, Diff5& q)
     q.ks[0] = (13.0 / 3.0) * q.s[0];
 }
 
-__device__ __forceinline__ void weno5_core(const double* v, const Diff5& q, double eps_s, double& N, double& D)
+// Result: the reconstruction is v[2] + M / D (the centre value plus a
+// correction), see weno_left.
+__device__ __forceinline__ void weno5_core(const Diff5& q, double eps_s, double& M, double& D)
 {
     const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3];
     const double t0 = fma(3.0, d1, -d0), t1 = d1 + d2, t2 = fma(3.0, d2, -d3);
@@ -201,23 +203,23 @@ __device__ __forceinline__ void weno5_core(const double* v, const Diff5& q, doub
     const double b2 = fma(q.ks[2], q.s[2], fma(t2, t2, eps_s));
     const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2;
     const double P0 = w1 * w2, P1 = w0 * w2, P2 = w0 * w1;
-    // 10 d_k q_k: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6 = c - d0/3 + 5 d1/6,
-    // q1 = (-b+5c+2d)/6, q2 = (2c+5d-e)/6
-    const double b = v[1], c = v[2], d = v[3], e = v[4];
-    const double n0 = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, c));
-    const double n1 = fma(2.0, d, fma(5.0, c, -b));
-    const double n2 = fma(-0.5, e, fma(2.5, d, c));
-    N = fma(n0, P0, fma(n1, P1, n2 * P2));
+    // 10 d_k (q_k - c), c = v[2]: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6 =
+    // c - d0/3 + 5 d1/6, q1 = (-b+5c+2d)/6 = c + (d1 + 2 d2)/6,
+    // q2 = (2c+5d-e)/6 = c + (4 d2 - d3)/6
+    const double m0 = fma(5.0 / 6.0, d1, (-1.0 / 3.0) * d0);
+    const double m1 = fma(2.0, d2, d1);
+    const double m2 = fma(-0.5, d3, 2.0 * d2);
+    M = fma(m0, P0, fma(m1, P1, m2 * P2));
     D = fma(3.0, P2, fma(6.0, P1, P0));
 }
 
 __device__ __forceinline__ void weno5(double a, double b, double c, double d, double e, double eps_s,
-                                      double& N, double& D)
+                                      double& M, double& D)
 {
     const double v[5] = {a, b, c, d, e};
     Diff5 q;
     weno5_diffs(v, q);
-    weno5_core(v, q, eps_s, N, D);
+    weno5_core(q, eps_s, M, D);
 }
 
 // r = 4 (Balsara-Shu weights from the same definition).  For the cubic
@@ -278,15 +280,18 @@ __device__ __forceinline__ void weno7_slide_mirror(const double* m, double eps_s
     q.ct[0] = w7_cterm(q.e[1] - q.e[0], eps_s);
 }
 
-__device__ __forceinline__ void weno7_core(const double* v, const Diff7& q, double& N, double& D)
+// Result: the reconstruction is v[3] + M / D, see weno_left.
+__device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
 {
     const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3], d4 = q.d[4], d5 = q.d[5];
     const double e0 = q.e[0], e1 = q.e[1], e2 = q.e[2], e3 = q.e[3], e4 = q.e[4];
     const double B0 = fma(2.0, e1, -e0), B12 = e2, B3 = fma(2.0, e3, -e4);
-    const double A0 = fma(11.0, d2, fma(-7.0, d1, 2.0 * d0));
+    // A0 = 2 d0 - 7 d1 + 11 d2 = 6 d2 + 2 B0 + e1, A3 = 11 d3 - 7 d4 + 2 d5 =
+    // 6 d3 - 2 B3 - e3
+    const double A0 = fma(6.0, d2, fma(2.0, B0, e1));
     const double A1 = fma(2.0, d3, fma(5.0, d2, -d1));
     const double A2 = fma(5.0, d3, fma(2.0, d2, -d4));
-    const double A3 = fma(2.0, d5, fma(-7.0, d4, 11.0 * d3));
+    const double A3 = fma(6.0, d3, fma(-2.0, B3, -e3));
     const double b39 = 39.0 * B12;
     const double b0 = fma(A0, A0, fma(39.0 * B0, B0, q.ct[0]));
     const double b1 = fma(A1, A1, fma(b39, B12, q.ct[1]));
@@ -295,46 +300,53 @@ __device__ __forceinline__ void weno7_core(const double* v, const Diff7& q, doub
     const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2, w3 = b3 * b3;
     const double p01 = w0 * w1, p23 = w2 * w3;
     const double P0 = w1 * p23, P1 = w0 * p23, P2 = p01 * w3, P3 = p01 * w2;
-    // 35 d_k q_k, d = (1, 12, 18, 4)/35; q0 = v3 + d0/4 - 5 d1/6 + 13 d2/12
-    const double v1 = v[1], v2 = v[2], v3 = v[3], v4 = v[4], v5 = v[5], v6 = v[6];
-    const double n0 = fma(13.0 / 12.0, d2, fma(-5.0 / 6.0, d1, fma(0.25, d0, v3)));
-    const double n1 = fma(3.0, v4, fma(13.0, v3, fma(-5.0, v2, v1)));
-    const double n2 = fma(10.5, v3 + v4, -1.5 * (v2 + v5));
-    const double n3 = fma(13.0 / 3.0, v4, fma(-5.0 / 3.0, v5, fma(1.0 / 3.0, v6, v3)));
-    N = fma(n0, P0, fma(n1, P1, fma(n2, P2, n3 * P3)));
+    // 35 d_k (q_k - v3), d = (1, 12, 18, 4)/35, in the difference basis:
+    // q0 - v3 = d0/4 - 5 d1/6 + 13 d2/12, q1 - v3 = (-d1 + 4 d2 + 3 d3)/12,
+    // q2 - v3 = (d2 + 6 d3 - d4)/12, q3 - v3 = (9 d3 - 4 d4 + d5)/12
+    const double m0 = fma(13.0 / 12.0, d2, fma(-5.0 / 6.0, d1, 0.25 * d0));
+    const double m1 = fma(3.0, d3, fma(4.0, d2, -d1));
+    const double m2 = fma(9.0, d3, 1.5 * (d2 - d4));
+    const double m3 = fma(3.0, d3, fma(-4.0 / 3.0, d4, (1.0 / 3.0) * d5));
+    M = fma(m0, P0, fma(m1, P1, fma(m2, P2, m3 * P3)));
     D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
 }
 
-__device__ __forceinline__ void weno7(const double* v, double eps_s, double& N, double& D)
+__device__ __forceinline__ void weno7(const double* v, double eps_s, double& M, double& D)
 {
     Diff7 q;
     weno7_diffs(v, eps_s, q);
-    weno7_core(v, q, N, D);
+    weno7_core(q, M, D);
 }
 
+// Left-biased value at x_{j+1/2} from v[0..S-1] = v_{j-r+1} .. v_{j+r-1}: the
+// centre value v[r-1] = v_j plus M / D, where D = sum_k d_k alpha_k and
+// M = sum_k d_k alpha_k (q_k - v_j) up to one common positive factor (q_k the
+// candidate values, alpha_k = 1/(eps+beta_k)^2); candidate k uses v[k..k+r-1].
 template <int R>
-__device__ __forceinline__ void weno_left(const double* v, double eps_s, double& N, double& D)
+__device__ __forceinline__ void weno_left(const double* v, double eps_s, double& M, double& D)
 {
-    if constexpr (R == 3) weno5(v[0], v[1], v[2], v[3], v[4], eps_s, N, D);
-    else weno7(v, eps_s, N, D);
+    if constexpr (R == 3) weno5(v[0], v[1], v[2], v[3], v[4], eps_s, M, D);
+    else weno7(v, eps_s, M, D);
 }
 
-// Right-biased value at x_{j-1/2} of the stencil centred on j: the mirror image.
+// Right-biased value at x_{j-1/2} of the stencil centred on j: the mirror
+// image, again v[r-1] + M / D.
 template <int R>
-__device__ __forceinline__ void weno_right(const double* v, double eps_s, double& N, double& D)
+__device__ __forceinline__ void weno_right(const double* v, double eps_s, double& M, double& D)
 {
     if constexpr (R == 3) {
-        weno5(v[4], v[3], v[2], v[1], v[0], eps_s, N, D);
+        weno5(v[4], v[3], v[2], v[1], v[0], eps_s, M, D);
     } else {
         const double m[7] = {v[6], v[5], v[4], v[3], v[2], v[1], v[0]};
-        weno7(m, eps_s, N, D);
+        weno7(m, eps_s, M, D);
     }
 }
 
-// Face value N+/D+ + N-/D- with one reciprocal.
-__device__ __forceinline__ double face_sum(double Np, double Dp, double Nm, double Dm)
+// Face value (cp + Mp/Dp) + (cm + Mm/Dm) with one reciprocal; cp, cm are the
+// centre values of the two stencils.
+__device__ __forceinline__ double face_sum(double Mp, double Dp, double cp, double Mm, double Dm, double cm)
 {
-    return fma(Np, Dm, Nm * Dp) * rcp(Dp * Dm);
+    return fma(fma(Mp, Dm, Mm * Dp), rcp(Dp * Dm), cp + cm);
 }
 
 template <int R> struct SchemeConst;

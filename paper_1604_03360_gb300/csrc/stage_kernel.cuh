@@ -160,7 +160,7 @@ __device__ __forceinline__ double llf_face(const double* f, const double* u, con
     double Np, Dp, Nm, Dm;
     weno_left<R>(vp, eps_s, Np, Dp);
     weno_right<R>(vm, eps_s, Nm, Dm);
-    return face_sum(Np, Dp, Nm, Dm);
+    return face_sum(Np, Dp, vp[R - 1], Nm, Dm, vm[R - 1]);
 }
 
 // One work item: column tile (tile_x, tile_y) of TX x TY cells and z chunk chunk_z of the
@@ -195,11 +195,10 @@ __device__ __forceinline__ void diffs_slide_mirror(const double* m, double eps_s
     else weno7_slide_mirror(m, eps_s, q);
 }
 template <int R>
-__device__ __forceinline__ void weno_core(const double* v, const typename DiffOf<R>::T& q, double eps_s, double& N,
-                                          double& D)
+__device__ __forceinline__ void weno_core(const typename DiffOf<R>::T& q, double eps_s, double& M, double& D)
 {
-    if constexpr (R == 3) weno5_core(v, q, eps_s, N, D);
-    else weno7_core(v, q, N, D);
+    if constexpr (R == 3) weno5_core(q, eps_s, M, D);
+    else weno7_core(q, M, D);
 }
 
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false>
@@ -283,7 +282,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     };
     // N/D of the left-biased (+) and right-biased (-) reconstructions of the
     // z-stencil centred on plane m, field k
-    auto recon_z = [&](int m, int k, double& Np, double& Dp, double& Nm, double& Dm) {
+    // (both stencils are centred on plane m: cp, cm are g+ and g- there)
+    auto recon_z = [&](int m, int k, double& Np, double& Dp, double& cp, double& Nm, double& Dm, double& cm) {
         double vp[S], vm[S];
 #pragma unroll
         for (int i = 0; i < S; ++i) {
@@ -293,6 +293,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         }
         weno_left<R>(vp, a.eps_s, Np, Dp);
         weno_right<R>(vm, a.eps_s, Nm, Dm);
+        cp = vp[G - 1];
+        cm = vm[G - 1];
     };
 
     // characteristic-wise: the whole z face m+1/2 from planes m-G+1 .. m+G,
@@ -320,9 +322,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     // columns outside the grid (ragged tiles) have no z-faces to compute: their
     // ring is private and nobody reads it
     const bool zwork = zact && own;
-    double hNp[NF], hDp[NF], Fzm[NF], Fzp[NF];
+    double hNp[NF], hDp[NF], hCp[NF], Fzm[NF], Fzp[NF];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) { hNp[k] = 0.0; hDp[k] = 1.0; Fzm[k] = 0.0; Fzp[k] = 0.0; }
+    for (int k = 0; k < NF; ++k) { hNp[k] = 0.0; hDp[k] = 1.0; hCp[k] = 0.0; Fzm[k] = 0.0; Fzp[k] = 0.0; }
     if (zwork && LLF) {
         for (int m = zb - G; m <= zb + G - 1; ++m) ingest(m);
 #pragma unroll
@@ -334,17 +336,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         for (int m = zb - G; m <= zb + G - 2; ++m) ingest(m);
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
-            double Nm, Dm;
-            recon_z(zb - 1, k, hNp[k], hDp[k], Nm, Dm);
+            double Nm, Dm, cm;
+            recon_z(zb - 1, k, hNp[k], hDp[k], hCp[k], Nm, Dm, cm);
         }
         ingest(zb + G - 1);
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
-            double Np, Dp, Nm, Dm;
-            recon_z(zb, k, Np, Dp, Nm, Dm);
-            Fzm[k] = face_sum(hNp[k], hDp[k], Nm, Dm);
+            double Np, Dp, cp, Nm, Dm, cm;
+            recon_z(zb, k, Np, Dp, cp, Nm, Dm, cm);
+            Fzm[k] = face_sum(hNp[k], hDp[k], hCp[k], Nm, Dm, cm);
             hNp[k] = Np;
             hDp[k] = Dp;
+            hCp[k] = cp;
         }
     }
 
@@ -391,11 +394,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             ingest(p + G);
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
-                double Np, Dp, Nm, Dm;
-                recon_z(p + 1, k, Np, Dp, Nm, Dm);
-                Fzp[k] = face_sum(hNp[k], hDp[k], Nm, Dm);
+                double Np, Dp, cp, Nm, Dm, cm;
+                recon_z(p + 1, k, Np, Dp, cp, Nm, Dm, cm);
+                Fzp[k] = face_sum(hNp[k], hDp[k], hCp[k], Nm, Dm, cm);
                 hNp[k] = Np;
                 hDp[k] = Dp;
+                hCp[k] = cp;
             }
         }
         // 2. split x- and y-fluxes of plane p (tile + halo) into shared memory
@@ -571,9 +575,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                         diffs_slide_mirror<R>(vm, a.eps_s, qm);
                     }
                     double Np, Dp, Nm, Dm;
-                    weno_core<R>(vp, qp, a.eps_s, Np, Dp);
-                    weno_core<R>(vm, qm, a.eps_s, Nm, Dm);
-                    const double F = face_sum(Np, Dp, Nm, Dm);
+                    weno_core<R>(qp, a.eps_s, Np, Dp);
+                    weno_core<R>(qm, a.eps_s, Nm, Dm);
+                    const double F = face_sum(Np, Dp, vp[G - 1], Nm, Dm, vm[G - 1]);
                     if (out && ff < nf) out[ff * ost] = F;
                 }
                 u += fe - f;
@@ -606,7 +610,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 double Np, Dp, Nm, Dm;
                 weno_left<R>(vp[u], a.eps_s, Np, Dp);
                 weno_right<R>(vm[u], a.eps_s, Nm, Dm);
-                F[u] = face_sum(Np, Dp, Nm, Dm);
+                F[u] = face_sum(Np, Dp, vp[u][G - 1], Nm, Dm, vm[u][G - 1]);
             }
 #pragma unroll
             for (int u = 0; u < ILP; ++u)

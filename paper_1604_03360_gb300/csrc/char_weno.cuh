@@ -45,7 +45,7 @@ __device__ __forceinline__ int rot_field(int k, int d)
 // (i = 0 .. 2r-1, cell j-r+1+i); ub holds the rotated face state, the mean of
 // the conserved states of window cells r-1 and r.  Returns false (F = 0) if
 // the face state is not physical.
-template <int R, int NF, class GV>
+template <int R, int NF, class GV, int EMU = 0>
 __device__ __forceinline__ bool char_face(GV gval, const double* ub, double k, double eps_s, double* F)
 {
     constexpr int S = 2 * R - 1, NQ = NF - 4;
@@ -133,7 +133,7 @@ __device__ __forceinline__ bool char_face(GV gval, const double* ub, double k, d
         }
 #pragma unroll
         for (int m = 0; m < NF; ++m) {
-            weno_left<R>(v[m], eps_s, Np[m], Dp[m]);
+            weno_left<R, EMU>(v[m], eps_s, Np[m], Dp[m]);
             Cp[m] = v[m][R - 1];
         }
     }
@@ -149,7 +149,7 @@ __device__ __forceinline__ bool char_face(GV gval, const double* ub, double k, d
 #pragma unroll
         for (int m = 0; m < NF; ++m) {
             double Nm, Dm;
-            weno_right<R>(v[m], eps_s, Nm, Dm);
+            weno_right<R, EMU>(v[m], eps_s, Nm, Dm);
             Fc[m] = face_sum(Np[m], Dp[m], Cp[m], Nm, Dm, v[m][R - 1]);
         }
     }

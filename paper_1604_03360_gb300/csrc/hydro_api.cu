@@ -188,7 +188,8 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
     if ((e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev)) != cudaSuccess)
         return bail(cuda_fail(h, e, "device attribute"));
     h->nf = state_fields(*cfg);
-    if ((e = stage_launch_variant(h->R, cfg->split, cfg->nq, 0, &h->L, cfg->charwise)) != cudaSuccess)
+    h->variant = default_launch_variant(h->R, cfg->split, cfg->nq, cfg->charwise);
+    if ((e = stage_launch_variant(h->R, cfg->split, cfg->nq, h->variant, &h->L, cfg->charwise)) != cudaSuccess)
         return bail(cuda_fail(h, e, "stage kernel setup"));
     h->G = h->R;
     h->ncell = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];

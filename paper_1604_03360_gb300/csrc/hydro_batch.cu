@@ -76,7 +76,7 @@ __device__ __forceinline__ StageArgs batch_stage_args(const BatchEvent& E, int s
     return a;
 }
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false)>
 __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) batch_stage_kernel(const BatchArgs b)
 {
     extern __shared__ __align__(16) double smem[];
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) b
         if (it >= b.n_items) break;
         const int4 w = b.items[it];
         const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
-        stage_tile<R, TX, TY, ILP, LLF>(a, w.y, w.z, w.w, smem);
+        stage_tile<R, TX, TY, ILP, LLF, 5, false, EMU>(a, w.y, w.z, w.w, smem);
     }
 }
 
@@ -129,18 +129,17 @@ struct BatchLaunch {
     int tx, ty, ctas_per_sm;
 };
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false)>
 static cudaError_t batch_info_for(BatchLaunch* out)
 {
-    out->fn = batch_stage_kernel<R, TX, TY, ILP, LLF>;
+    auto fn = batch_stage_kernel<R, TX, TY, ILP, LLF, EMU>;
+    out->fn = fn;
     out->smem = StageSmem<R, TX, TY, LLF, 5, false, ILP == kPencilSweep>::bytes;
     out->tx = TX;
     out->ty = TY;
-    cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<R, TX, TY, ILP, LLF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, batch_stage_kernel<R, TX, TY, ILP, LLF>,
-                                                         TX * TY, out->smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, fn, TX * TY, out->smem);
 }
 
 // same tile shapes as the single-grid kernel (variant numbering matches)
@@ -157,15 +156,17 @@ static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* ou
         if (v == 1) return batch_info_for<3, 16, 8>(out);
         if (v == 2) return batch_info_for<3, 32, 8>(out);
         if (v == 3) return batch_info_for<3, 16, 16, 2>(out);
-        if (v == 4) return batch_info_for<3, 16, 16, kPencilSweep>(out);
+        if (v == 4) return batch_info_for<3, 16, 16, kPencilSweep, false, 0>(out);
         if (v == 5) return batch_info_for<3, 16, 8, kPencilSweep>(out);
+        if (v == 6) return batch_info_for<3, 16, 16, kPencilSweep>(out);
     }
     if (R == 4) {
         if (v == 0) return batch_info_for<4, 16, 16>(out);
         if (v == 1) return batch_info_for<4, 16, 8>(out);
         if (v == 2) return batch_info_for<4, 16, 16, 2>(out);
-        if (v == 3) return batch_info_for<4, 16, 16, kPencilSweep>(out);
+        if (v == 3) return batch_info_for<4, 16, 16, kPencilSweep, false, 0>(out);
         if (v == 4) return batch_info_for<4, 16, 8, kPencilSweep>(out);
+        if (v == 5) return batch_info_for<4, 16, 16, kPencilSweep>(out);
     }
     return cudaErrorInvalidValue;
 }
@@ -412,7 +413,7 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
     for (int i = 0; i < n_events; ++i) reset_ctl_kernel<<<1, 1, 0, b->stream>>>(b->ctl + i, 0.0);
     if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(bcuda(b, e, "capture stream"));
-    hydro_status s = apply_batch_launch(b, 0, 0);
+    hydro_status s = apply_batch_launch(b, default_launch_variant(b->R, b->cfg[0].split, 1, 0), 0);
     if (s) return bail(s);
     *out = b;
     return HYDRO_OK;

@@ -112,10 +112,14 @@ struct StageLaunch {
 // nq: number of charges (state fields = 4 + nq).
 // charw: characteristic-wise reconstruction (hydro_char.cu; split must be 0).
 int launch_variant_count(int R, int split, int nq, int charw = 0);
+int default_launch_variant(int R, int split, int nq, int charw = 0);
 cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out, int charw = 0);
 int char_variant_count(int R, int nq);
 cudaError_t char_launch_variant(int R, int nq, int v, StageLaunch* out);
-inline cudaError_t stage_launch_info(int R, StageLaunch* out) { return stage_launch_variant(R, 0, 1, 0, out); }
+inline cudaError_t stage_launch_info(int R, StageLaunch* out)
+{
+    return stage_launch_variant(R, 0, 1, default_launch_variant(R, 0, 1), out);
+}
 inline int state_fields(const hydro_config& c) { return 4 + (c.nq > 1 ? c.nq : 1); }
 // internal scheme code: 3 WENO5, 4 WENO7, 2 MUSTA-FORCE (the ghost width)
 inline int scheme_R(int scheme) { return scheme == HYDRO_WENO5 ? 3 : (scheme == HYDRO_WENO7 ? 4 : 2); }

@@ -131,35 +131,45 @@ __global__ void state_to_prim_kernel(const double* u, long long fs, double* out,
     }
 }
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5,
+          int EMU = default_emu(R, TX, TY, LLF, NF, false)>
 static cudaError_t info_for(StageLaunch* out)
 {
-    out->fn = stage_kernel<R, TX, TY, ILP, LLF, NF>;
+    auto fn = stage_kernel<R, TX, TY, ILP, LLF, NF, false, EMU>;
+    out->fn = fn;
     out->smem = StageSmem<R, TX, TY, LLF, NF, false, ILP == kPencilSweep>::bytes;
     out->tx = TX;
     out->ty = TY;
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, TX, TY, ILP, LLF, NF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_kernel<R, TX, TY, ILP, LLF, NF>,
-                                                         TX * TY, out->smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, fn, TX * TY, out->smem);
 }
 
 // WENO5: 16x16 (1 CTA of 8 warps per SM), 16x8 (2 CTAs of 4 warps), 32x8,
-//        16x16 with two face items per iteration, pencil sweeps on 16x16 and
-//        16x8.
+//        16x16 with two face items per iteration, pencil sweeps on 16x16
+//        (all products on the FP64 unit) and 16x8, and the 16x16 pencil sweep.
 // WENO7: 16x16 (8 warps, 221 KB shared memory), 16x8 (4 warps), 16x16 with two
-//        face items per iteration, pencil sweeps on 16x16 and 16x8.
+//        face items per iteration, pencil sweeps on 16x16 (all products on the
+//        FP64 unit) and 16x8, and the 16x16 pencil sweep.
+// The two marked variants keep every product on the FP64 unit (the bitwise
+// reference); the others take the default of default_emu.
 // Local LF (raw staging, 2G-plane ring): WENO5 16x16 and 16x8; WENO7 16x8
 // (16x16 would need 247 KB of shared memory).
 // Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
+// the launch a grid gets before any tuning: the fastest on the 256^3 workload
+int default_launch_variant(int R, int split, int nq, int charw)
+{
+    if (charw || R == 2 || split || nq > 1) return 0;
+    return R == 3 ? 6 : 5;
+}
+
 int launch_variant_count(int R, int split, int nq, int charw)
 {
     if (charw) return (R == 3 || R == 4) && split == 0 ? char_variant_count(R, nq) : 0;
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 2 : 1;
-    return R == 3 ? 6 : 5;
+    return R == 3 ? 7 : 6;
 }
 
 template <int NF>
@@ -210,15 +220,17 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 1) return info_for<3, 16, 8>(out);
         if (v == 2) return info_for<3, 32, 8>(out);
         if (v == 3) return info_for<3, 16, 16, 2>(out);
-        if (v == 4) return info_for<3, 16, 16, kPencilSweep>(out);
+        if (v == 4) return info_for<3, 16, 16, kPencilSweep, false, 5, 0>(out);
         if (v == 5) return info_for<3, 16, 8, kPencilSweep>(out);
+        if (v == 6) return info_for<3, 16, 16, kPencilSweep>(out);
     }
     if (R == 4) {
         if (v == 0) return info_for<4, 16, 16>(out);
         if (v == 1) return info_for<4, 16, 8>(out);
         if (v == 2) return info_for<4, 16, 16, 2>(out);
-        if (v == 3) return info_for<4, 16, 16, kPencilSweep>(out);
+        if (v == 3) return info_for<4, 16, 16, kPencilSweep, false, 5, 0>(out);
         if (v == 4) return info_for<4, 16, 8, kPencilSweep>(out);
+        if (v == 5) return info_for<4, 16, 16, kPencilSweep>(out);
     }
     return cudaErrorInvalidValue;
 }

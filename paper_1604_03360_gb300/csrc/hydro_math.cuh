@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "fp64_int.cuh"
+
 namespace hydro {
 
 // 1/x for finite, normal, positive or negative x.  Seed r0 from the MUFU
@@ -149,21 +151,30 @@ struct Diff5 {
     double ks[3];    // 13/3 s_k
 };
 
+// EMU selects operations that run on the integer pipe (fp64_int.cuh) instead
+// of the FP64 unit: kEmuConst the products with constants.  Every choice gives
+// the same bits.
+constexpr int kEmuConst = 1;
+
+template <int EMU = 0>
 __device__ __forceinline__ void weno5_diffs(const double* v, Diff5& q)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) q.d[i] = v[i + 1] - v[i];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         q.s[k] = q.d[k + 1] - q.d[k];
-        q.ks[k] = (13.0 / 3.0) * q.s[k];
+        q.ks[k] = xmul<EC>(13.0 / 3.0, q.s[k]);
     }
 }
 
 // window moved one cell up the array (v is the new window): the new cell
 // enters at v[4]
+template <int EMU = 0>
 __device__ __forceinline__ void weno5_slide(const double* v, Diff5& q)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) q.d[i] = q.d[i + 1];
 #pragma unroll
@@ -173,13 +184,15 @@ __device__ __forceinline__ void weno5_slide(const double* v, Diff5& q)
     }
     q.d[3] = v[4] - v[3];
     q.s[2] = q.d[3] - q.d[2];
-    q.ks[2] = (13.0 / 3.0) * q.s[2];
+    q.ks[2] = xmul<EC>(13.0 / 3.0, q.s[2]);
 }
 
 // mirrored window moved one cell (m is the new mirrored window): the new
 // cell enters at m[0]
+template <int EMU = 0>
 __device__ __forceinline__ void weno5_slide_mirror(const double* m, Diff5& q)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 3; i > 0; --i) q.d[i] = q.d[i - 1];
 #pragma unroll
@@ -189,13 +202,15 @@ __device__ __forceinline__ void weno5_slide_mirror(const double* m, Diff5& q)
     }
     q.d[0] = m[1] - m[0];
     q.s[0] = q.d[1] - q.d[0];
-    q.ks[0] = (13.0 / 3.0) * q.s[0];
+    q.ks[0] = xmul<EC>(13.0 / 3.0, q.s[0]);
 }
 
 // Result: the reconstruction is v[2] + M / D (the centre value plus a
 // correction), see weno_left.
+template <int EMU = 0>
 __device__ __forceinline__ void weno5_core(const Diff5& q, double eps_s, double& M, double& D)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0;
     const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3];
     const double t0 = fma(3.0, d1, -d0), t1 = d1 + d2, t2 = fma(3.0, d2, -d3);
     const double b0 = fma(q.ks[0], q.s[0], fma(t0, t0, eps_s));
@@ -206,20 +221,21 @@ __device__ __forceinline__ void weno5_core(const Diff5& q, double eps_s, double&
     // 10 d_k (q_k - c), c = v[2]: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6 =
     // c - d0/3 + 5 d1/6, q1 = (-b+5c+2d)/6 = c + (d1 + 2 d2)/6,
     // q2 = (2c+5d-e)/6 = c + (4 d2 - d3)/6
-    const double m0 = fma(5.0 / 6.0, d1, (-1.0 / 3.0) * d0);
+    const double m0 = fma(5.0 / 6.0, d1, xmul<EC>(-1.0 / 3.0, d0));
     const double m1 = fma(2.0, d2, d1);
-    const double m2 = fma(-0.5, d3, 2.0 * d2);
+    const double m2 = fma(-0.5, d3, xmul_pow2<EC, 1>(d2));
     M = fma(m0, P0, fma(m1, P1, m2 * P2));
     D = fma(3.0, P2, fma(6.0, P1, P0));
 }
 
+template <int EMU = 0>
 __device__ __forceinline__ void weno5(double a, double b, double c, double d, double e, double eps_s,
                                       double& M, double& D)
 {
     const double v[5] = {a, b, c, d, e};
     Diff5 q;
-    weno5_diffs(v, q);
-    weno5_core(q, eps_s, M, D);
+    weno5_diffs<EMU>(v, q);
+    weno5_core<EMU>(q, eps_s, M, D);
 }
 
 // r = 4 (Balsara-Shu weights from the same definition).  For the cubic
@@ -240,21 +256,29 @@ struct Diff7 {
     double ct[4];    // 781/20 C_k^2 + eps_s, C_k = e_{k+1} - e_k
 };
 
-__device__ __forceinline__ double w7_cterm(double C, double eps_s) { return fma((781.0 / 20.0) * C, C, eps_s); }
+template <bool EC>
+__device__ __forceinline__ double w7_cterm(double C, double eps_s)
+{
+    return fma(xmul<EC>(781.0 / 20.0, C), C, eps_s);
+}
 
+template <int EMU = 0>
 __device__ __forceinline__ void weno7_diffs(const double* v, double eps_s, Diff7& q)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) q.d[i] = v[i + 1] - v[i];
 #pragma unroll
     for (int i = 0; i < 5; ++i) q.e[i] = q.d[i + 1] - q.d[i];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) q.ct[k] = w7_cterm(q.e[k + 1] - q.e[k], eps_s);
+    for (int k = 0; k < 4; ++k) q.ct[k] = w7_cterm<EC>(q.e[k + 1] - q.e[k], eps_s);
 }
 
 // window moved one cell up the array: the new cell enters at v[6]
+template <int EMU = 0>
 __device__ __forceinline__ void weno7_slide(const double* v, double eps_s, Diff7& q)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 0; i < 5; ++i) q.d[i] = q.d[i + 1];
 #pragma unroll
@@ -263,12 +287,14 @@ __device__ __forceinline__ void weno7_slide(const double* v, double eps_s, Diff7
     for (int k = 0; k < 3; ++k) q.ct[k] = q.ct[k + 1];
     q.d[5] = v[6] - v[5];
     q.e[4] = q.d[5] - q.d[4];
-    q.ct[3] = w7_cterm(q.e[4] - q.e[3], eps_s);
+    q.ct[3] = w7_cterm<EC>(q.e[4] - q.e[3], eps_s);
 }
 
 // mirrored window moved one cell: the new cell enters at m[0]
+template <int EMU = 0>
 __device__ __forceinline__ void weno7_slide_mirror(const double* m, double eps_s, Diff7& q)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 5; i > 0; --i) q.d[i] = q.d[i - 1];
 #pragma unroll
@@ -277,12 +303,14 @@ __device__ __forceinline__ void weno7_slide_mirror(const double* m, double eps_s
     for (int k = 3; k > 0; --k) q.ct[k] = q.ct[k - 1];
     q.d[0] = m[1] - m[0];
     q.e[0] = q.d[1] - q.d[0];
-    q.ct[0] = w7_cterm(q.e[1] - q.e[0], eps_s);
+    q.ct[0] = w7_cterm<EC>(q.e[1] - q.e[0], eps_s);
 }
 
 // Result: the reconstruction is v[3] + M / D, see weno_left.
+template <int EMU = 0>
 __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0;
     const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3], d4 = q.d[4], d5 = q.d[5];
     const double e0 = q.e[0], e1 = q.e[1], e2 = q.e[2], e3 = q.e[3], e4 = q.e[4];
     const double B0 = fma(2.0, e1, -e0), B12 = e2, B3 = fma(2.0, e3, -e4);
@@ -292,53 +320,54 @@ __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
     const double A1 = fma(2.0, d3, fma(5.0, d2, -d1));
     const double A2 = fma(5.0, d3, fma(2.0, d2, -d4));
     const double A3 = fma(6.0, d3, fma(-2.0, B3, -e3));
-    const double b39 = 39.0 * B12;
-    const double b0 = fma(A0, A0, fma(39.0 * B0, B0, q.ct[0]));
+    const double b39 = xmul_small<EC, 39, 6, 0>(B12);
+    const double b0 = fma(A0, A0, fma(xmul_small<EC, 39, 6, 0>(B0), B0, q.ct[0]));
     const double b1 = fma(A1, A1, fma(b39, B12, q.ct[1]));
     const double b2 = fma(A2, A2, fma(b39, B12, q.ct[2]));
-    const double b3 = fma(A3, A3, fma(39.0 * B3, B3, q.ct[3]));
+    const double b3 = fma(A3, A3, fma(xmul_small<EC, 39, 6, 0>(B3), B3, q.ct[3]));
     const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2, w3 = b3 * b3;
     const double p01 = w0 * w1, p23 = w2 * w3;
     const double P0 = w1 * p23, P1 = w0 * p23, P2 = p01 * w3, P3 = p01 * w2;
     // 35 d_k (q_k - v3), d = (1, 12, 18, 4)/35, in the difference basis:
     // q0 - v3 = d0/4 - 5 d1/6 + 13 d2/12, q1 - v3 = (-d1 + 4 d2 + 3 d3)/12,
     // q2 - v3 = (d2 + 6 d3 - d4)/12, q3 - v3 = (9 d3 - 4 d4 + d5)/12
-    const double m0 = fma(13.0 / 12.0, d2, fma(-5.0 / 6.0, d1, 0.25 * d0));
+    const double m0 = fma(13.0 / 12.0, d2, fma(-5.0 / 6.0, d1, xmul_pow2<EC, -2>(d0)));
     const double m1 = fma(3.0, d3, fma(4.0, d2, -d1));
-    const double m2 = fma(9.0, d3, 1.5 * (d2 - d4));
-    const double m3 = fma(3.0, d3, fma(-4.0 / 3.0, d4, (1.0 / 3.0) * d5));
+    const double m2 = fma(9.0, d3, xmul_small<EC, 3, 2, -1>(d2 - d4));
+    const double m3 = fma(3.0, d3, fma(-4.0 / 3.0, d4, xmul<EC>(1.0 / 3.0, d5)));
     M = fma(m0, P0, fma(m1, P1, fma(m2, P2, m3 * P3)));
     D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
 }
 
+template <int EMU = 0>
 __device__ __forceinline__ void weno7(const double* v, double eps_s, double& M, double& D)
 {
     Diff7 q;
-    weno7_diffs(v, eps_s, q);
-    weno7_core(q, M, D);
+    weno7_diffs<EMU>(v, eps_s, q);
+    weno7_core<EMU>(q, M, D);
 }
 
 // Left-biased value at x_{j+1/2} from v[0..S-1] = v_{j-r+1} .. v_{j+r-1}: the
 // centre value v[r-1] = v_j plus M / D, where D = sum_k d_k alpha_k and
 // M = sum_k d_k alpha_k (q_k - v_j) up to one common positive factor (q_k the
 // candidate values, alpha_k = 1/(eps+beta_k)^2); candidate k uses v[k..k+r-1].
-template <int R>
+template <int R, int EMU = 0>
 __device__ __forceinline__ void weno_left(const double* v, double eps_s, double& M, double& D)
 {
-    if constexpr (R == 3) weno5(v[0], v[1], v[2], v[3], v[4], eps_s, M, D);
-    else weno7(v, eps_s, M, D);
+    if constexpr (R == 3) weno5<EMU>(v[0], v[1], v[2], v[3], v[4], eps_s, M, D);
+    else weno7<EMU>(v, eps_s, M, D);
 }
 
 // Right-biased value at x_{j-1/2} of the stencil centred on j: the mirror
 // image, again v[r-1] + M / D.
-template <int R>
+template <int R, int EMU = 0>
 __device__ __forceinline__ void weno_right(const double* v, double eps_s, double& M, double& D)
 {
     if constexpr (R == 3) {
-        weno5(v[4], v[3], v[2], v[1], v[0], eps_s, M, D);
+        weno5<EMU>(v[4], v[3], v[2], v[1], v[0], eps_s, M, D);
     } else {
         const double m[7] = {v[6], v[5], v[4], v[3], v[2], v[1], v[0]};
-        weno7(m, eps_s, M, D);
+        weno7<EMU>(m, eps_s, M, D);
     }
 }
 

@@ -135,7 +135,7 @@ __device__ __forceinline__ void raw_flux(int d, const double* u, const double w[
 // Local-LF face value (scaled by 2) from raw stencil data of one field over the
 // 2G cells j-G+1 .. j+G of face j+1/2 (element stride st): alpha_face = max s,
 // g+ = f + alpha u on the first 2G-1 cells, g- = f - alpha u on the last 2G-1.
-template <int R>
+template <int R, int EMU = 0>
 __device__ __forceinline__ double llf_face(const double* f, const double* u, const double* s, int st, double eps_s)
 {
     constexpr int W = 2 * R, S = 2 * R - 1;
@@ -158,8 +158,8 @@ __device__ __forceinline__ double llf_face(const double* f, const double* u, con
         vm[i] = fma(-a, uv[i + 1], fv[i + 1]);
     }
     double Np, Dp, Nm, Dm;
-    weno_left<R>(vp, eps_s, Np, Dp);
-    weno_right<R>(vm, eps_s, Nm, Dm);
+    weno_left<R, EMU>(vp, eps_s, Np, Dp);
+    weno_right<R, EMU>(vm, eps_s, Nm, Dm);
     return face_sum(Np, Dp, vp[R - 1], Nm, Dm, vm[R - 1]);
 }
 
@@ -176,32 +176,44 @@ template <int R> struct DiffOf;
 template <> struct DiffOf<3> { using T = Diff5; };
 template <> struct DiffOf<4> { using T = Diff7; };
 
-template <int R>
+template <int R, int EMU>
 __device__ __forceinline__ void diffs_fresh(const double* v, double eps_s, typename DiffOf<R>::T& q)
 {
-    if constexpr (R == 3) weno5_diffs(v, q);
-    else weno7_diffs(v, eps_s, q);
+    if constexpr (R == 3) weno5_diffs<EMU>(v, q);
+    else weno7_diffs<EMU>(v, eps_s, q);
 }
-template <int R>
+template <int R, int EMU>
 __device__ __forceinline__ void diffs_slide(const double* v, double eps_s, typename DiffOf<R>::T& q)
 {
-    if constexpr (R == 3) weno5_slide(v, q);
-    else weno7_slide(v, eps_s, q);
+    if constexpr (R == 3) weno5_slide<EMU>(v, q);
+    else weno7_slide<EMU>(v, eps_s, q);
 }
-template <int R>
+template <int R, int EMU>
 __device__ __forceinline__ void diffs_slide_mirror(const double* m, double eps_s, typename DiffOf<R>::T& q)
 {
-    if constexpr (R == 3) weno5_slide_mirror(m, q);
-    else weno7_slide_mirror(m, eps_s, q);
+    if constexpr (R == 3) weno5_slide_mirror<EMU>(m, q);
+    else weno7_slide_mirror<EMU>(m, eps_s, q);
 }
-template <int R>
+template <int R, int EMU>
 __device__ __forceinline__ void weno_core(const typename DiffOf<R>::T& q, double eps_s, double& M, double& D)
 {
-    if constexpr (R == 3) weno5_core(q, eps_s, M, D);
-    else weno7_core(q, M, D);
+    if constexpr (R == 3) weno5_core<EMU>(q, eps_s, M, D);
+    else weno7_core<EMU>(q, M, D);
 }
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false>
+// EMU: which FP64 operations of the reconstructions run on the integer pipe
+// instead (kEmu* mask, hydro_math.cuh); the result is bit-identical.  The
+// products with constants go there by default when 8 warps share an SM (one
+// 256-thread CTA, or two 128-thread WENO5 CTAs): the FP64 unit is the
+// bottleneck and the issue slots are mostly idle.  With 4 warps per SM, and in
+// the characteristic-wise kernels, the longer integer chains measured slower.
+constexpr int default_emu(int R, int TX, int TY, bool LLF, int NF, bool CHW)
+{
+    return CHW ? 0 : ((TX * TY == 256 || (R == 3 && NF == 5 && !LLF)) ? kEmuConst : 0);
+}
+
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false,
+          int EMU = default_emu(R, TX, TY, LLF, NF, CHW)>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
 {
     static_assert(!(LLF && CHW), "characteristic-wise WENO uses the global Lax-Friedrichs split");
@@ -278,7 +290,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             uv[i] = r[(NF + k) * NT];
             sv[i] = r[2 * NF * NT];
         }
-        return llf_face<R>(fv, uv, sv, 1, a.eps_s);
+        return llf_face<R, EMU>(fv, uv, sv, 1, a.eps_s);
     };
     // N/D of the left-biased (+) and right-biased (-) reconstructions of the
     // z-stencil centred on plane m, field k
@@ -291,8 +303,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             vp[i] = r[k * NT];
             vm[i] = r[(NF + k) * NT];
         }
-        weno_left<R>(vp, a.eps_s, Np, Dp);
-        weno_right<R>(vm, a.eps_s, Nm, Dm);
+        weno_left<R, EMU>(vp, a.eps_s, Np, Dp);
+        weno_right<R, EMU>(vm, a.eps_s, Nm, Dm);
         cp = vp[G - 1];
         cm = vm[G - 1];
     };
@@ -312,7 +324,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         };
 #pragma unroll
         for (int f = 0; f < NF; ++f) ub[f] = 0.5 * (rp(G - 1)[rot_field(f, 2) * NT] + rp(G)[rot_field(f, 2) * NT]);
-        const bool ok = char_face<R, NF>(gval, ub, a.cs2, a.eps_s, Fr);
+        const bool ok = char_face<R, NF, decltype(gval), EMU>(gval, ub, a.cs2, a.eps_s, Fr);
 #pragma unroll
         for (int k = 0; k < NF; ++k) Fz[rot_field(k, 2)] = Fr[k];
         return ok;
@@ -493,7 +505,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 #pragma unroll
                     for (int m = 0; m < NF; ++m)
                         ub[m] = ((gval(G - 1, m, 0) - gval(G - 1, m, 1)) + (gval(G, m, 0) - gval(G, m, 1))) * q;
-                    ok = char_face<R, NF>(gval, ub, a.cs2, a.eps_s, Fr);
+                    ok = char_face<R, NF, decltype(gval), EMU>(gval, ub, a.cs2, a.eps_s, Fr);
 #pragma unroll
                     for (int m = 0; m < NF; ++m) Fx[(rot_field(m, 0) * TY + row) * (TX + 1) + f] = Fr[m];
                 } else {
@@ -508,7 +520,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 #pragma unroll
                     for (int m = 0; m < NF; ++m)
                         ub[m] = ((gval(G - 1, m, 0) - gval(G - 1, m, 1)) + (gval(G, m, 0) - gval(G, m, 1))) * q;
-                    ok = char_face<R, NF>(gval, ub, a.cs2, a.eps_s, Fr);
+                    ok = char_face<R, NF, decltype(gval), EMU>(gval, ub, a.cs2, a.eps_s, Fr);
 #pragma unroll
                     for (int m = 0; m < NF; ++m) Fy[(rot_field(m, 1) * (TY + 1) + f) * TX + col] = Fr[m];
                 }
@@ -526,7 +538,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 // field blocks further in the same staged array
                 const int fb = (it < nfx) ? TY * GXW : GYH * TX;      // one field block
                 const int k = (it < nfx) ? it / (nrow * (ncol + 1)) : (it - nfx) / ((nrow + 1) * ncol);
-                *out = llf_face<R>(pp, pp + NF * fb, pp + (2 * NF - k) * fb, st, a.eps_s);
+                *out = llf_face<R, EMU>(pp, pp + NF * fb, pp + (2 * NF - k) * fb, st, a.eps_s);
             }
         } else if constexpr (SWP) {
             using DF = typename DiffOf<R>::T;
@@ -557,6 +569,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                     nf = nrow + 1;
                 }
                 DF qp, qm;
+#pragma unroll 2
                 for (int ff = f; ff < fe; ++ff) {
                     // lanes whose pencil is shorter than the group repeat its
                     // last face (in bounds) and store nothing
@@ -568,15 +581,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                         vm[i] = pm[(fc + S - 1 - i) * st];    // mirrored window of the right-biased stencil
                     }
                     if (ff == f) {
-                        diffs_fresh<R>(vp, a.eps_s, qp);
-                        diffs_fresh<R>(vm, a.eps_s, qm);
+                        diffs_fresh<R, EMU>(vp, a.eps_s, qp);
+                        diffs_fresh<R, EMU>(vm, a.eps_s, qm);
                     } else {
-                        diffs_slide<R>(vp, a.eps_s, qp);
-                        diffs_slide_mirror<R>(vm, a.eps_s, qm);
+                        diffs_slide<R, EMU>(vp, a.eps_s, qp);
+                        diffs_slide_mirror<R, EMU>(vm, a.eps_s, qm);
                     }
                     double Np, Dp, Nm, Dm;
-                    weno_core<R>(qp, a.eps_s, Np, Dp);
-                    weno_core<R>(qm, a.eps_s, Nm, Dm);
+                    weno_core<R, EMU>(qp, a.eps_s, Np, Dp);
+                    weno_core<R, EMU>(qm, a.eps_s, Nm, Dm);
                     const double F = face_sum(Np, Dp, vp[G - 1], Nm, Dm, vm[G - 1]);
                     if (out && ff < nf) out[ff * ost] = F;
                 }
@@ -608,8 +621,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 #pragma unroll
             for (int u = 0; u < ILP; ++u) {
                 double Np, Dp, Nm, Dm;
-                weno_left<R>(vp[u], a.eps_s, Np, Dp);
-                weno_right<R>(vm[u], a.eps_s, Nm, Dm);
+                weno_left<R, EMU>(vp[u], a.eps_s, Np, Dp);
+                weno_right<R, EMU>(vm[u], a.eps_s, Nm, Dm);
                 F[u] = face_sum(Np, Dp, vp[u][G - 1], Nm, Dm, vm[u][G - 1]);
             }
 #pragma unroll
@@ -681,12 +694,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 }
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false,
+          int EMU = default_emu(R, TX, TY, LLF, NF, CHW)>
 __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 && NF == 5 && !CHW ? 2 : 1))
     stage_kernel(const StageArgs a)
 {
     extern __shared__ __align__(16) double smem[];
-    stage_tile<R, TX, TY, ILP, LLF, NF, CHW>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    stage_tile<R, TX, TY, ILP, LLF, NF, CHW, EMU>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 }  // namespace hydro

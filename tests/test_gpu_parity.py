@@ -183,8 +183,8 @@ def test_unphysical_state_reported():
         assert ei.value.code == 4
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5),
-                                            (7, 0), (7, 1), (7, 2), (7, 3), (7, 4)])
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5), (5, 6),
+                                            (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5)])
 def test_every_launch_variant(scheme, variant):
     """Every compiled CTA tile shape, with a short z chunk so several chunks
     meet inside the grid, matches the oracle."""
@@ -202,8 +202,9 @@ def test_every_launch_variant(scheme, variant):
     assert np.all(field_errors(got, ref) <= TOL)
 
 
-# (per-face variant, pencil-sweep variant) pairs with the same CTA tile
-SWEEP_PAIRS = {5: ((0, 4), (1, 5)), 7: ((0, 3), (1, 4))}
+# (per-face variant, pencil-sweep variant) pairs with the same CTA tile, and
+# (pencil sweep, pencil sweep with integer-pipe products)
+SWEEP_PAIRS = {5: ((0, 4), (1, 5), (4, 6)), 7: ((0, 3), (1, 4), (3, 5))}
 
 
 @pytest.mark.parametrize("scheme", [5, 7])
@@ -212,7 +213,8 @@ def test_pencil_sweep_matches_per_face_bitwise(scheme, n):
     """The pencil sweep carries stencil differences from face to face; it
     performs the same floating-point operations on the same operands as
     reconstructing every face afresh, so both give the same bits -- on full
-    and ragged tiles and with one or two active in-plane axes."""
+    and ragged tiles and with one or two active in-plane axes.  The variant
+    whose products run on the integer pipe must give the same bits too."""
     from paper_1604_03360_gb300 import Hydro
     g, w = W.lumpy(n=n, seed=91, scheme=scheme)
     w = with_flow(g, w)

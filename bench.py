@@ -33,18 +33,19 @@ sys.path.insert(0, ROOT)
 # (2 x 61 / 2 x 136 flops + 6 to combine), flux differences 40, RK combine 20
 # (mean of 10/25/25), split fluxes 75, primitive recovery 22, speeds 34.  The
 # pencil-sweep kernels carry stencil differences between neighbouring faces
-# and execute fewer FP64 instructions than this count (ncu: 2296 per cell and
-# stage for WENO7, 84.9 % FP64 pipe busy).
+# and take the products with constants on the integer pipe, so they execute
+# fewer FP64 instructions than this count (ncu: 2021 per cell and stage for
+# WENO7, 84 % FP64 pipe busy).
 FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
                         7: 15 * (2 * 136 + 6) + 40 + 20 + 75 + 22 + 34}
-# DRAM traffic of one WENO7 stage launch of the 16x16 pencil-sweep kernel
-# measured by ncu on the 128^3 case (profiles/stage_kernel_weno7_sweep_128.md):
-# stage 1 286.3 MB, stages 2 and 3 385.2 MB, mean 352.2 MB / 2.10 M cells; it
-# scales with the cell count.  None for WENO5 (not captured for the current
-# kernel).
-NCU_DRAM_BYTES_PER_CELL_STAGE = {7: (286.3e6 + 2 * 385.2e6) / 3 / 128 ** 3}
+# DRAM traffic of one WENO7 stage launch of the default kernel (16x16 pencil
+# sweep, products with constants on the integer pipe), measured by ncu on the
+# 128^3 case (profiles/stage_kernel_weno7_sweep_intconst_128.md): stage 1
+# 284.1 MB, stages 2 and 3 382.3 MB, mean 349.6 MB / 2.10 M cells; it scales
+# with the cell count.  None for WENO5 (not captured for the current kernel).
+NCU_DRAM_BYTES_PER_CELL_STAGE = {7: (284.1e6 + 2 * 382.3e6) / 3 / 128 ** 3}
 # (variant, tile x, tile y) of the profiled launch; another choice reports null
-NCU_PROFILED_LAUNCH = {7: (3, 16, 16)}
+NCU_PROFILED_LAUNCH = {7: (5, 16, 16)}
 # Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
 # stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
 HBM_BYTES_PER_CELL_UPDATE = 320
@@ -648,8 +649,8 @@ def main():
                          "traffic": (NCU_DRAM_BYTES_PER_CELL_STAGE[args.scheme] * cells
                                      if args.scheme in NCU_DRAM_BYTES_PER_CELL_STAGE
                                      and launch[:3] == NCU_PROFILED_LAUNCH[args.scheme] else None),
-                         "traffic_source": "ncu dram__bytes_read+write of the 128^3 pencil-sweep stage launches "
-                                           "(mean of stages 1-3), scaled by cells",
+                         "traffic_source": "ncu dram__bytes_read+write of the 128^3 stage launches of the same "
+                                           "variant (mean of stages 1-3), scaled by cells",
                          "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[args.scheme],
                          "kernel": "stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,
                          "peak_source": "FP64 FMA probe kernel measured in this run (hydro_measure_fp64_peak); "

@@ -88,7 +88,7 @@ typedef struct {
                            hydro_forward_record/hydro_adjoint or
                            hydro_step_noalloc (HYDRO_ERR_INVALID_ARG) */
     int32_t nq;         /* conserved charge densities: 0 or 1 = one (R), up to
-                           3 (R_1, R_2, R_3; "charge densities" in Sec. 1).
+                           3 (R_1, R_2, R_3; Sec. 1 names charge densities in the plural).
                            Each is passive (p = cs2 e) and advected like R; a
                            state then has 4 + nq fields (E, M_x, M_y, M_z,
                            R_1..R_nq) and primitives (e, v, n_1..n_nq).  nq > 1

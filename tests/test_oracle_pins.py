@@ -617,8 +617,8 @@ def test_musta_second_order_on_smooth_data(oracle_lib):
 def test_musta_sod_and_weno_is_sharper(oracle_lib, limiter):
     """Sod tube with MUSTA-FORCE: plateaus near the exact solution and the
     error falls with N.  WENO5 and WENO7 on the same grid describe the shock
-    better (Sec. 3: MUSTA-FORCE gives a less accurate description of shock
-    waves): smaller error over the shock region (right of the contact) with the
+    better (Sec. 3 finds MUSTA-FORCE less accurate at shocks): smaller error
+    over the shock region (right of the contact) with the
     minmod and van Leer limiters.  (Compressive limiters -- MC, superbee -- make
     the two comparable.)"""
     ex = SodExact()

@@ -25,6 +25,8 @@ struct hydro_s {
     double* U[3] = {nullptr, nullptr, nullptr};
     double* W[3] = {nullptr, nullptr, nullptr};
     double* S[3] = {nullptr, nullptr, nullptr};   // per-axis speeds (local LF only)
+    double* fz = nullptr;            // z-face fluxes of the z-pass variants (5 fields of nz+1 planes)
+    long long fzs = 0;
     Ctl* ctl = nullptr;
     Ctl* hctl = nullptr;             // pinned mirror for read-back
     cudaGraphExec_t exec = nullptr;
@@ -99,18 +101,33 @@ static StageArgs stage_args(hydro_t* h, int stage)
     a.limiter = h->cfg.limiter;
     a.musta_k = musta_stages_of(h->cfg);
     a.eos_m = h->cfg.eos_mass;
+    a.fz = h->fz;
+    a.fzs = h->fzs;
     return a;
+}
+
+// a launch this handle can run: z-pass variants need the z-face buffer and a
+// row count that fits the z pass's grid
+static bool launch_fits(const hydro_t* h, const StageLaunch& L)
+{
+    return !L.zfn || (h->fz && h->cfg.n[1] <= 65535);
+}
+
+// one RK3 stage: the z pass first (z-pass variants, z active), then the stage kernel
+static void launch_stage(const hydro_t* h, const StageLaunch& L, int zc, const StageArgs& a, cudaStream_t s)
+{
+    if (L.zfn && a.act[2]) {
+        const dim3 zg((h->cfg.n[0] + 31) / 32, h->cfg.n[1], (h->zhi - h->zlo + 1 + kZFaces - 1) / kZFaces);
+        L.zfn<<<zg, kZPassThreads, 0, s>>>(a);
+    }
+    const dim3 grid((h->cfg.n[0] + L.tx - 1) / L.tx, (h->cfg.n[1] + L.ty - 1) / L.ty, (h->zhi - h->zlo + zc - 1) / zc);
+    L.fn<<<grid, L.tx * L.ty, L.smem, s>>>(a);
 }
 
 static cudaError_t enqueue_step(hydro_t* h, cudaStream_t s)
 {
-    const dim3 grid((h->cfg.n[0] + h->L.tx - 1) / h->L.tx, (h->cfg.n[1] + h->L.ty - 1) / h->L.ty,
-                    (h->zhi - h->zlo + h->zc - 1) / h->zc);
     step_begin_kernel<<<1, 1, 0, s>>>(h->ctl, step_params(h->cfg));
-    for (int st = 1; st <= 3; ++st) {
-        const StageArgs a = stage_args(h, st);
-        h->L.fn<<<grid, h->L.tx * h->L.ty, h->L.smem, s>>>(a);
-    }
+    for (int st = 1; st <= 3; ++st) launch_stage(h, h->L, h->zc, stage_args(h, st), s);
     step_end_kernel<<<1, 1, 0, s>>>(h->ctl);
     return cudaGetLastError();
 }
@@ -148,6 +165,15 @@ hydro_status hydro_handle_view(hydro_t* h, HandleView* v)
     v->ctl = h->ctl;
     v->L = h->L;
     v->zc = h->zc;
+    if (h->L.zfn) {
+        // the adjoint runs its recorded forward on its own buffers: use the
+        // fastest variant that needs no z-face buffer
+        cudaError_t e = stage_launch_variant(h->R, h->cfg.split, h->cfg.nq,
+                                             fused_launch_variant(h->R, h->cfg.split, h->cfg.nq, h->cfg.charwise), &v->L,
+                                             h->cfg.charwise);
+        if (e != cudaSuccess) return cuda_fail(h, e, "stage kernel setup");
+        v->zc = pick_zc(h->cfg.n[0], h->cfg.n[1], h->cfg.n[2], v->L, h->sms);
+    }
     return HYDRO_OK;
 }
 
@@ -188,7 +214,7 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
     if ((e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev)) != cudaSuccess)
         return bail(cuda_fail(h, e, "device attribute"));
     h->nf = state_fields(*cfg);
-    h->variant = default_launch_variant(h->R, cfg->split, cfg->nq, cfg->charwise);
+    h->variant = fused_launch_variant(h->R, cfg->split, cfg->nq, cfg->charwise);
     if ((e = stage_launch_variant(h->R, cfg->split, cfg->nq, h->variant, &h->L, cfg->charwise)) != cudaSuccess)
         return bail(cuda_fail(h, e, "stage kernel setup"));
     h->G = h->R;
@@ -212,6 +238,23 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
         if (cfg->split) h->S[i] = h->buf + (size_t)h->fs * (3 * nf + 12 + 3 * i);
     }
     if ((e = cudaMemsetAsync(h->buf, 0, bytes, h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+    if (zpass_capable(*cfg, h->R)) {
+        // z-face fluxes for the z-pass variants: 5 fields of nz+1 face planes
+        h->fzs = ((long long)cfg->n[0] * cfg->n[1] * (cfg->n[2] + 1) + 31) / 32 * 32;
+        if ((e = cudaMalloc(&h->fz, sizeof(double) * (size_t)h->fzs * 5)) != cudaSuccess)
+            return bail(cuda_fail(h, e, "z-face buffer"));
+    }
+    {
+        // the variant new grids start on (it may need the z-face buffer)
+        const int dv = default_launch_variant(h->R, cfg->split, cfg->nq, cfg->charwise);
+        StageLaunch L{};
+        if (dv != h->variant && stage_launch_variant(h->R, cfg->split, cfg->nq, dv, &L, cfg->charwise) == cudaSuccess &&
+            launch_fits(h, L)) {
+            h->variant = dv;
+            h->L = L;
+            h->zc = pick_zc(cfg->n[0], cfg->n[1], cfg->n[2], L, h->sms);
+        }
+    }
     if ((e = cudaMalloc(&h->ctl, sizeof(Ctl))) != cudaSuccess) return bail(cuda_fail(h, e, "control block"));
     if ((e = cudaMallocHost(&h->hctl, sizeof(Ctl))) != cudaSuccess) return bail(cuda_fail(h, e, "pinned control"));
     if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
@@ -231,6 +274,7 @@ hydro_status hydro_destroy(hydro_t* h)
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->buf) cudaFree(h->buf);
+    if (h->fz) cudaFree(h->fz);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);
     if (h->adj) {
@@ -331,15 +375,12 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
     for (int i = 0; i < 6; ++i) CK(h, cudaEventCreate(&ev[i]), "event create");
     hydro_status st = HYDRO_OK;
     set_t_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t_end);
-    const dim3 grid((h->cfg.n[0] + h->L.tx - 1) / h->L.tx, (h->cfg.n[1] + h->L.ty - 1) / h->L.ty,
-                    (h->zhi - h->zlo + h->zc - 1) / h->zc);
     for (int s = 0; s < nsteps && st == HYDRO_OK; ++s) {
         cudaEventRecord(ev[0], h->stream);
         step_begin_kernel<<<1, 1, 0, h->stream>>>(h->ctl, step_params(h->cfg));
         cudaEventRecord(ev[1], h->stream);
         for (int k = 1; k <= 3; ++k) {
-            const StageArgs a = stage_args(h, k);
-            h->L.fn<<<grid, h->L.tx * h->L.ty, h->L.smem, h->stream>>>(a);
+            launch_stage(h, h->L, h->zc, stage_args(h, k), h->stream);
             cudaEventRecord(ev[1 + k], h->stream);
         }
         step_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl);
@@ -448,10 +489,7 @@ hydro_status hydro_stage(hydro_t* h, int32_t which, double t_end)
     } else if (which == 4) {
         step_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl);
     } else {
-        const dim3 grid((h->cfg.n[0] + h->L.tx - 1) / h->L.tx, (h->cfg.n[1] + h->L.ty - 1) / h->L.ty,
-                        (h->zhi - h->zlo + h->zc - 1) / h->zc);
-        const StageArgs a = stage_args(h, which);
-        h->L.fn<<<grid, h->L.tx * h->L.ty, h->L.smem, h->stream>>>(a);
+        launch_stage(h, h->L, h->zc, stage_args(h, which), h->stream);
     }
     CK(h, cudaGetLastError(), "stage launch");
     return HYDRO_OK;
@@ -481,6 +519,7 @@ static hydro_status apply_launch(hydro_t* h, int variant, int zc)
     cudaError_t e = stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, variant, &L, h->cfg.charwise);
     if (e == cudaErrorInvalidValue) return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     CK(h, e, "stage kernel setup");
+    if (!launch_fits(h, L)) return fail(h, HYDRO_ERR_INVALID_ARG, "launch variant needs ny <= 65535");
     CK(h, cudaStreamSynchronize(h->stream), "synchronize");
     if (h->exec) {
         cudaGraphExecDestroy(h->exec);
@@ -590,6 +629,7 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
     for (int v = 0; v < hydro_launch_variants_cfg(&h->cfg) && st == HYDRO_OK; ++v) {
         StageLaunch L{};
         if (stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, v, &L, h->cfg.charwise) != cudaSuccess) continue;
+        if (!launch_fits(h, L)) continue;
         // z chunks: balanced splits ceil(nz/k) and a fixed ladder; time the five
         // the wave-count model likes best
         std::vector<int> zs;
@@ -614,10 +654,9 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
             h->L = L;
             h->zc = zc;
             const StageArgs a = stage_args(h, 1);
-            const dim3 grid((h->cfg.n[0] + L.tx - 1) / L.tx, (h->cfg.n[1] + L.ty - 1) / L.ty, (nz + zc - 1) / zc);
-            L.fn<<<grid, L.tx * L.ty, L.smem, h->stream>>>(a);   // warm-up
+            launch_stage(h, L, zc, a, h->stream);   // warm-up
             cudaEventRecord(e0, h->stream);
-            L.fn<<<grid, L.tx * L.ty, L.smem, h->stream>>>(a);
+            launch_stage(h, L, zc, a, h->stream);
             cudaEventRecord(e1, h->stream);
             cudaError_t e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaGetLastError();

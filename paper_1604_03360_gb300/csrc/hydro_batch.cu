@@ -413,7 +413,7 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
     for (int i = 0; i < n_events; ++i) reset_ctl_kernel<<<1, 1, 0, b->stream>>>(b->ctl + i, 0.0);
     if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(bcuda(b, e, "capture stream"));
-    hydro_status s = apply_batch_launch(b, default_launch_variant(b->R, b->cfg[0].split, 1, 0), 0);
+    hydro_status s = apply_batch_launch(b, fused_launch_variant(b->R, b->cfg[0].split, 1, 0), 0);
     if (s) return bail(s);
     *out = b;
     return HYDRO_OK;
@@ -555,7 +555,7 @@ int32_t hydro_batch_size(hydro_batch_t* b) { return b ? b->n_events : 0; }
 hydro_status hydro_batch_set_launch(hydro_batch_t* b, int32_t variant, int32_t zc)
 {
     if (!b) return HYDRO_ERR_INVALID_ARG;
-    if (variant < 0 || variant >= hydro_launch_variants(b->cfg[0].scheme, b->cfg[0].split, 1))
+    if (variant < 0 || variant >= batch_variant_count(b->R, b->cfg[0].split))
         return bfail(b, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     return apply_batch_launch(b, variant, zc);
 }
@@ -587,7 +587,7 @@ hydro_status hydro_batch_autotune(hydro_batch_t* b, double* best_ms)
     BCK(b, cudaEventCreate(&e0), "event");
     BCK(b, cudaEventCreate(&e1), "event");
     const int eb = (b->n_events + 127) / 128;
-    for (int v = 0; v < hydro_launch_variants(b->cfg[0].scheme, b->cfg[0].split, 1) && s == HYDRO_OK; ++v)
+    for (int v = 0; v < batch_variant_count(b->R, b->cfg[0].split) && s == HYDRO_OK; ++v)
         for (int zc : zcs) {
             s = apply_batch_launch(b, v, zc);
             if (s) break;

@@ -9,6 +9,7 @@ static cudaError_t char_info_for(StageLaunch* out)
 {
     auto fn = stage_kernel<R, TX, TY, 1, false, NF, true>;
     out->fn = fn;
+    out->zfn = nullptr;
     out->smem = StageSmem<R, TX, TY, false, NF, true>::bytes;
     out->tx = TX;
     out->ty = TY;

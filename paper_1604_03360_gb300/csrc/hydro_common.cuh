@@ -105,6 +105,7 @@ struct StageLaunch {
     size_t smem;
     int tx, ty;
     int ctas_per_sm;
+    void (*zfn)(StageArgs) = nullptr;   // z pass launched before fn (ZEXT variants), else null
 };
 // Tile shapes compiled per scheme and splitting (index 0 is the default);
 // stage_launch_variant returns cudaErrorInvalidValue for a variant that does
@@ -113,14 +114,24 @@ struct StageLaunch {
 // charw: characteristic-wise reconstruction (hydro_char.cu; split must be 0).
 int launch_variant_count(int R, int split, int nq, int charw = 0);
 int default_launch_variant(int R, int split, int nq, int charw = 0);
+// the fastest variant that keeps the z faces in the stage kernel (no z pass):
+// for launch paths without a z-flux buffer (adjoint, no-alloc)
+int fused_launch_variant(int R, int split, int nq, int charw = 0);
+// variants that the batched (persistent) kernel also has
+int batch_variant_count(int R, int split);
 cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out, int charw = 0);
 int char_variant_count(int R, int nq);
 cudaError_t char_launch_variant(int R, int nq, int v, StageLaunch* out);
 inline cudaError_t stage_launch_info(int R, StageLaunch* out)
 {
-    return stage_launch_variant(R, 0, 1, default_launch_variant(R, 0, 1), out);
+    return stage_launch_variant(R, 0, 1, fused_launch_variant(R, 0, 1), out);
 }
 inline int state_fields(const hydro_config& c) { return 4 + (c.nq > 1 ? c.nq : 1); }
+// configurations with z-pass launch variants (component-wise WENO, global LF, one charge)
+inline bool zpass_capable(const hydro_config& c, int R)
+{
+    return (R == 3 || R == 4) && c.split == 0 && c.nq <= 1 && c.charwise == 0;
+}
 // internal scheme code: 3 WENO5, 4 WENO7, 2 MUSTA-FORCE (the ghost width)
 inline int scheme_R(int scheme) { return scheme == HYDRO_WENO5 ? 3 : (scheme == HYDRO_WENO7 ? 4 : 2); }
 inline int musta_stages_of(const hydro_config& c) { return c.musta_stages > 0 ? c.musta_stages : 2; }

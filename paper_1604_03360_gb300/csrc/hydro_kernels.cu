@@ -132,12 +132,14 @@ __global__ void state_to_prim_kernel(const double* u, long long fs, double* out,
 }
 
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5,
-          int EMU = default_emu(R, TX, TY, LLF, NF, false)>
+          int EMU = default_emu(R, TX, TY, LLF, NF, false), bool ZEXT = false>
 static cudaError_t info_for(StageLaunch* out)
 {
-    auto fn = stage_kernel<R, TX, TY, ILP, LLF, NF, false, EMU>;
+    auto fn = stage_kernel<R, TX, TY, ILP, LLF, NF, false, EMU, ZEXT>;
     out->fn = fn;
-    out->smem = StageSmem<R, TX, TY, LLF, NF, false, ILP == kPencilSweep>::bytes;
+    out->zfn = nullptr;
+    if constexpr (ZEXT) out->zfn = zflux_kernel<R, EMU>;
+    out->smem = StageSmem<R, TX, TY, LLF, NF, false, ILP == kPencilSweep, ZEXT>::bytes;
     out->tx = TX;
     out->ty = TY;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
@@ -152,15 +154,31 @@ static cudaError_t info_for(StageLaunch* out)
 //        face items per iteration, pencil sweeps on 16x16 (all products on the
 //        FP64 unit) and 16x8, and the 16x16 pencil sweep.
 // The two marked variants keep every product on the FP64 unit (the bitwise
-// reference); the others take the default of default_emu.
+// reference); the others take the default of default_emu.  WENO5 7 / WENO7 6:
+// the 16x16 pencil sweep with the z faces from a separate z pass (zflux_kernel:
+// long z pencils at 15 warps per SM, carried differences; the stage kernel
+// then keeps no z ring).
 // Local LF (raw staging, 2G-plane ring): WENO5 16x16 and 16x8; WENO7 16x8
 // (16x16 would need 247 KB of shared memory).
 // Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
 // the launch a grid gets before any tuning: the fastest on the 256^3 workload
+// (the z-pass variant; a handle that cannot run it keeps the fused one)
 int default_launch_variant(int R, int split, int nq, int charw)
 {
     if (charw || R == 2 || split || nq > 1) return 0;
+    return R == 3 ? 7 : 6;
+}
+
+int fused_launch_variant(int R, int split, int nq, int charw)
+{
+    if (charw || R == 2 || split || nq > 1) return 0;
     return R == 3 ? 6 : 5;
+}
+
+int batch_variant_count(int R, int split)
+{
+    if (split == 1) return R == 3 ? 2 : 1;
+    return R == 3 ? 7 : 6;
 }
 
 int launch_variant_count(int R, int split, int nq, int charw)
@@ -169,7 +187,7 @@ int launch_variant_count(int R, int split, int nq, int charw)
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 2 : 1;
-    return R == 3 ? 7 : 6;
+    return R == 3 ? 8 : 7;
 }
 
 template <int NF>
@@ -183,6 +201,7 @@ template <int TX, int TY>
 static cudaError_t musta_info_for(StageLaunch* out)
 {
     out->fn = musta_stage_kernel<TX, TY>;
+    out->zfn = nullptr;
     out->smem = MustaSmem<TX, TY>::bytes;
     out->tx = TX;
     out->ty = TY;
@@ -223,6 +242,7 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 4) return info_for<3, 16, 16, kPencilSweep, false, 5, 0>(out);
         if (v == 5) return info_for<3, 16, 8, kPencilSweep>(out);
         if (v == 6) return info_for<3, 16, 16, kPencilSweep>(out);
+        if (v == 7) return info_for<3, 16, 16, kPencilSweep, false, 5, kEmuConst, true>(out);
     }
     if (R == 4) {
         if (v == 0) return info_for<4, 16, 16>(out);
@@ -231,6 +251,7 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 3) return info_for<4, 16, 16, kPencilSweep, false, 5, 0>(out);
         if (v == 4) return info_for<4, 16, 8, kPencilSweep>(out);
         if (v == 5) return info_for<4, 16, 16, kPencilSweep>(out);
+        if (v == 6) return info_for<4, 16, 16, kPencilSweep, false, 5, kEmuConst, true>(out);
     }
     return cudaErrorInvalidValue;
 }

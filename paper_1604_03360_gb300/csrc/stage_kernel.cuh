@@ -67,6 +67,8 @@ struct StageArgs {
     int musta_k;            // MUSTA-FORCE only: number of MUSTA stages
     int zlo, zhi;           // planes computed: [zlo, zhi) of the nz stored (0, nz unless z halos are stored)
     double eos_m;           // EOS p = cs2 (e - eos_m n_1); 0: p = cs2 e
+    double* fz;             // z-pass variants: z-face fluxes, field k face f (between planes zlo+f-1
+    long long fzs;          // and zlo+f) at fz[k fzs + f nx ny + y nx + x], f = 0 .. zhi-zlo
 };
 
 // boundary rule 0 outflow (copy edge cell), 1 periodic; 2 (z only) halo: the
@@ -83,7 +85,8 @@ __device__ __forceinline__ int bc_map(int i, int n, int bc)
     return i < 0 ? 0 : n - 1;
 }
 
-template <int R, int TX, int TY, bool LLF = false, int NF = 5, bool CHW = false, bool SWP = false>
+template <int R, int TX, int TY, bool LLF = false, int NF = 5, bool CHW = false, bool SWP = false,
+          bool ZEXT = false>
 struct StageSmem {
     static constexpr int G = R, S = 2 * R - 1, NT = TX * TY;
     static constexpr int NV = LLF ? 2 * NF + 1 : 2 * NF;     // staged values per cell
@@ -94,7 +97,7 @@ struct StageSmem {
     // z ring values per cell: characteristic-wise keeps (u, p, v_z) and forms
     // g+- when a face reads them (a smaller ring: two CTAs per SM at 16 x 8)
     static constexpr int NVR = CHW ? NF + 2 : NV;
-    static constexpr int RING = NRING * NVR * NT;
+    static constexpr int RING = ZEXT ? 0 : NRING * NVR * NT;   // z-pass variants keep no ring
     static constexpr int GX = NV * TY * GXW;
     static constexpr int GY = NV * GYH * TX;
     static constexpr int FX = NF * TY * (TX + 1);
@@ -104,6 +107,8 @@ struct StageSmem {
 
 // split fluxes g+- = f_d(u) +- alpha u (= 2 f^{+-}) of one cell along axis d
 // (fields E, M_x, M_y, M_z, then the NF - 4 charges, each with flux R v_d)
+// (explicitly rounded products and sums: no contraction into an FMA, so every
+// kernel that forms these values gets the same bits)
 template <int NF>
 __device__ __forceinline__ void split_flux(int d, const double* u, const double w[4], double alpha, double* gp,
                                            double* gm)
@@ -112,8 +117,8 @@ __device__ __forceinline__ void split_flux(int d, const double* u, const double 
     double f[NF];
     f[0] = u[1 + d];
 #pragma unroll
-    for (int k = 1; k < NF; ++k) f[k] = u[k] * vd;
-    f[1 + d] += p;
+    for (int k = 1; k < NF; ++k) f[k] = __dmul_rn(u[k], vd);
+    f[1 + d] = __dadd_rn(f[1 + d], p);
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
         gp[k] = fma(alpha, u[k], f[k]);
@@ -212,15 +217,18 @@ constexpr int default_emu(int R, int TX, int TY, bool LLF, int NF, bool CHW)
     return CHW ? 0 : ((TX * TY == 256 || (R == 3 && NF == 5 && !LLF)) ? kEmuConst : 0);
 }
 
+// ZEXT: the z-face fluxes come from zflux_kernel (global memory) instead of
+// the per-column ring of this kernel.
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false,
-          int EMU = default_emu(R, TX, TY, LLF, NF, CHW)>
+          int EMU = default_emu(R, TX, TY, LLF, NF, CHW), bool ZEXT = false>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
 {
     static_assert(!(LLF && CHW), "characteristic-wise WENO uses the global Lax-Friedrichs split");
     constexpr bool SWP = (ILP == kPencilSweep);
     static_assert(!(SWP && (LLF || CHW)), "the pencil sweep serves the component-wise global-LF scheme");
     static_assert((TX * TY) % 32 == 0, "whole warps");
-    using SM = StageSmem<R, TX, TY, LLF, NF, CHW, SWP>;
+    static_assert(!ZEXT || (SWP && NF == 5), "the z pass serves the five-field pencil-sweep kernels");
+    using SM = StageSmem<R, TX, TY, LLF, NF, CHW, SWP, ZEXT>;
     constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING, NVR = SM::NVR;
     constexpr int GXW = SM::GXW, GYH = SM::GYH;
     double* ring = smem;
@@ -333,7 +341,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 
     // columns outside the grid (ragged tiles) have no z-faces to compute: their
     // ring is private and nobody reads it
-    const bool zwork = zact && own;
+    const bool zwork = zact && own && !ZEXT;
     double hNp[NF], hDp[NF], hCp[NF], Fzm[NF], Fzp[NF];
 #pragma unroll
     for (int k = 0; k < NF; ++k) { hNp[k] = 0.0; hDp[k] = 1.0; hCp[k] = 0.0; Fzm[k] = 0.0; Fzp[k] = 0.0; }
@@ -394,6 +402,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 
     for (int p = zb; p < ze; ++p) {
+        if constexpr (ZEXT) {
+            // z faces p-1/2 and p+1/2 of this column, from the z pass
+            if (zact && own) {
+                const double* fz = a.fz + (long long)(p - a.zlo) * plane + (long long)y * nx + x;
+#pragma unroll
+                for (int k = 0; k < NF; ++k) {
+                    Fzm[k] = fz[k * a.fzs];
+                    Fzp[k] = fz[k * a.fzs + plane];
+                }
+            }
+        }
         // 1. z: ingest plane p+G, face p+1/2 = R+(p) + R-(p+1)
         if (zwork && LLF) {
             ingest(p + G);
@@ -695,12 +714,90 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 }
 
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false,
-          int EMU = default_emu(R, TX, TY, LLF, NF, CHW)>
+          int EMU = default_emu(R, TX, TY, LLF, NF, CHW), bool ZEXT = false>
 __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 && NF == 5 && !CHW ? 2 : 1))
     stage_kernel(const StageArgs a)
 {
     extern __shared__ __align__(16) double smem[];
-    stage_tile<R, TX, TY, ILP, LLF, NF, CHW, EMU>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    stage_tile<R, TX, TY, ILP, LLF, NF, CHW, EMU, ZEXT>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
+// z pass of a stage (ZEXT variants): the z-face fluxes of the five fields,
+// each thread sweeping one (x, y, field) pencil over a chunk of kZFaces faces
+// with the stencil differences carried from face to face -- the same
+// operations on the same operands as the ring of the fused kernel, so the same
+// bits.  A CTA is 32 consecutive x (one warp per field) of one row y; grid
+// (ceil(nx/32), ny, ceil((nz+1)/kZFaces)).  Face f lies between planes
+// zlo+f-1 and zlo+f (f = 0 .. zhi-zlo); its left-biased stencil is centred
+// on plane zlo+f-1, its right-biased one on plane zlo+f.
+constexpr int kZFaces = 64, kZPassThreads = 160;
+template <int R, int EMU>
+__global__ void __launch_bounds__(kZPassThreads) zflux_kernel(const StageArgs a)
+{
+    constexpr int G = R, S = 2 * R - 1;
+    using DF = typename DiffOf<R>::T;
+    if (!(*a.dt > 0.0)) return;
+    const int k = threadIdx.x >> 5, x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y;
+    if (x >= a.nx) return;                       // no barriers below
+    const int f0 = blockIdx.z * kZFaces, f1 = min(f0 + kZFaces, a.zhi - a.zlo + 1);
+    const double az = __longlong_as_double((long long)a.alpha_in[2]);
+    const long long plane = (long long)a.nx * a.ny, col = (long long)y * a.nx + x;
+    // split z-fluxes g+- = f_z +- alpha_z u of field k at stored plane m (as split_flux)
+    auto split_at = [&](int m, double& gp, double& gm) {
+        const long long q = (long long)bc_map(m, a.nz, a.bc[2]) * plane + col;
+        const double uk = __ldg(a.u_in + k * a.fs + q);
+        double f;
+        if (k == 0) {
+            f = __ldg(a.u_in + 3 * a.fs + q);
+        } else {
+            f = __dmul_rn(uk, __ldg(a.w_in + 3 * a.fs + q));
+            if (k == 3) f = __dadd_rn(f, __ldg(a.w_in + q));
+        }
+        gp = fma(az, uk, f);
+        gm = fma(-az, uk, f);
+    };
+    // windows of face p+1/2 (p = zlo+f-1): wp = g+ at planes p-G+1 .. p+G-1,
+    // wm = g- at planes p-G+2 .. p+G; gl = g+ of the newest plane p+G
+    double wp[S], wm[S], gl = 0.0;
+    const int p0 = a.zlo + f0 - 1;
+#pragma unroll
+    for (int i = 0; i < 2 * G; ++i) {
+        double gp, gm;
+        split_at(p0 - G + 1 + i, gp, gm);
+        if (i < S) wp[i] = gp;
+        if (i > 0) wm[i - 1] = gm;
+        gl = gp;
+    }
+    DF qp, qm;
+    double* out = a.fz + k * a.fzs + col;
+    for (int f = f0; f < f1; ++f) {
+        double mm[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) mm[i] = wm[S - 1 - i];
+        if (f == f0) {
+            diffs_fresh<R, EMU>(wp, a.eps_s, qp);
+            diffs_fresh<R, EMU>(mm, a.eps_s, qm);
+        } else {
+            diffs_slide<R, EMU>(wp, a.eps_s, qp);
+            diffs_slide_mirror<R, EMU>(mm, a.eps_s, qm);
+        }
+        double Np, Dp, Nm, Dm;
+        weno_core<R, EMU>(qp, a.eps_s, Np, Dp);
+        weno_core<R, EMU>(qm, a.eps_s, Nm, Dm);
+        out[(long long)f * plane] = face_sum(Np, Dp, wp[G - 1], Nm, Dm, wm[G - 1]);
+        if (f + 1 < f1) {
+            // next face: planes move up by one
+#pragma unroll
+            for (int i = 0; i < S - 1; ++i) {
+                wp[i] = wp[i + 1];
+                wm[i] = wm[i + 1];
+            }
+            wp[S - 1] = gl;
+            double gm;
+            split_at(a.zlo + f + G, gl, gm);
+            wm[S - 1] = gm;
+        }
+    }
 }
 
 }  // namespace hydro

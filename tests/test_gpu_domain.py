@@ -66,6 +66,18 @@ def test_outflow_slabs_match_whole_grid(scheme, nslabs):
     check(g, w, nslabs, 5, device="cuda")
 
 
+@pytest.mark.parametrize("scheme,variant", [(5, 7), (7, 6)])
+def test_zpass_slabs_match_whole_grid(scheme, variant):
+    """Slabs whose z faces come from the z pass (which reads the stored ghost
+    planes) advance bit for bit like the whole grid on the fused kernel."""
+    g, w = W.lumpy(n=(21, 17, 26), seed=12, scheme=scheme)
+    w = with_flow(g, w)
+    ref, tr, kr = run_gpu(g, w, 4)
+    got, tg, kg = run_slabs(g, w, 3, 4, device="cuda", variant=variant)
+    assert (kg, tg) == (kr, tr)
+    assert np.array_equal(got, ref), np.max(np.abs(got - ref))
+
+
 @pytest.mark.parametrize("scheme", [5, 7, 2])
 def test_periodic_slabs_match_whole_grid(scheme):
     g, w = W.smooth_periodic(n=(13, 11, 17), amp=0.3, vamp=0.5, seed=9, scheme=scheme)

@@ -183,8 +183,8 @@ def test_unphysical_state_reported():
         assert ei.value.code == 4
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5), (5, 6),
-                                            (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5)])
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5), (5, 6), (5, 7),
+                                            (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5), (7, 6)])
 def test_every_launch_variant(scheme, variant):
     """Every compiled CTA tile shape, with a short z chunk so several chunks
     meet inside the grid, matches the oracle."""
@@ -202,9 +202,10 @@ def test_every_launch_variant(scheme, variant):
     assert np.all(field_errors(got, ref) <= TOL)
 
 
-# (per-face variant, pencil-sweep variant) pairs with the same CTA tile, and
-# (pencil sweep, pencil sweep with integer-pipe products)
-SWEEP_PAIRS = {5: ((0, 4), (1, 5), (4, 6)), 7: ((0, 3), (1, 4), (3, 5))}
+# (per-face variant, pencil-sweep variant) pairs with the same CTA tile,
+# (pencil sweep on the FP64 unit only, pencil sweep with integer-pipe
+# products) and (fused z faces, z faces from the z pass)
+SWEEP_PAIRS = {5: ((0, 4), (1, 5), (4, 6), (6, 7)), 7: ((0, 3), (1, 4), (3, 5), (5, 6))}
 
 
 @pytest.mark.parametrize("scheme", [5, 7])
@@ -214,7 +215,9 @@ def test_pencil_sweep_matches_per_face_bitwise(scheme, n):
     performs the same floating-point operations on the same operands as
     reconstructing every face afresh, so both give the same bits -- on full
     and ragged tiles and with one or two active in-plane axes.  The variant
-    whose products run on the integer pipe must give the same bits too."""
+    whose products run on the integer pipe must give the same bits too, and so
+    must the variant whose z faces come from the separate z pass (z pencils
+    swept with carried differences)."""
     from paper_1604_03360_gb300 import Hydro
     g, w = W.lumpy(n=n, seed=91, scheme=scheme)
     w = with_flow(g, w)

@@ -34,18 +34,22 @@ sys.path.insert(0, ROOT)
 # (mean of 10/25/25), split fluxes 75, primitive recovery 22, speeds 34.  The
 # pencil-sweep kernels carry stencil differences between neighbouring faces
 # and take the products with constants on the integer pipe, so they execute
-# fewer FP64 instructions than this count (ncu: 2021 per cell and stage for
-# WENO7, 84 % FP64 pipe busy).
+# fewer FP64 instructions than this count implies (ncu: 1824 per cell and
+# stage for WENO7, 85 % FP64 pipe busy), and the flop rate by this count can
+# read above the FP64 peak.
 FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
                         7: 15 * (2 * 136 + 6) + 40 + 20 + 75 + 22 + 34}
-# DRAM traffic of one WENO7 stage launch of the default kernel (16x16 pencil
-# sweep, products with constants on the integer pipe), measured by ncu on the
-# 128^3 case (profiles/stage_kernel_weno7_sweep_intconst_128.md): stage 1
-# 284.1 MB, stages 2 and 3 382.3 MB, mean 349.6 MB / 2.10 M cells; it scales
-# with the cell count.  None for WENO5 (not captured for the current kernel).
-NCU_DRAM_BYTES_PER_CELL_STAGE = {7: (284.1e6 + 2 * 382.3e6) / 3 / 128 ** 3}
+# DRAM traffic of one WENO7 stage of the default launch (z pass + stage
+# kernel), measured by ncu on the 128^3 case
+# (profiles/stage_weno7_zpass_128.md): stage 1 506.2 MB, stages 2 and 3
+# 594.8 MB, mean 565.3 MB / 2.10 M cells; it scales with the cell count.  Same
+# capture: 1824 FP64 instructions per cell and stage, FP64 pipe 85 % busy.
+# None for WENO5 (not captured for the current kernels).
+NCU_DRAM_BYTES_PER_CELL_STAGE = {7: (506.2e6 + 2 * 594.8e6) / 3 / 128 ** 3}
+NCU_FP64_INST_PER_CELL_STAGE = {7: 1824}
+NCU_FP64_PIPE_BUSY = {7: 0.85}
 # (variant, tile x, tile y) of the profiled launch; another choice reports null
-NCU_PROFILED_LAUNCH = {7: (5, 16, 16)}
+NCU_PROFILED_LAUNCH = {7: (6, 16, 16)}
 # Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
 # stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
 HBM_BYTES_PER_CELL_UPDATE = 320
@@ -631,6 +635,9 @@ def main():
                "sample": "1 RK3 step of the central %d^3 block of the 256^3 workload (%.1f s)"
                % (128 if args.scheme == 5 else 96, secs)}
 
+    # the ncu figures hold for the launch they were captured on
+    profiled = (not args.charwise and args.scheme in NCU_PROFILED_LAUNCH
+                and tuple(launch[:3]) == NCU_PROFILED_LAUNCH[args.scheme])
     if rank == 0:
         line = {
             "metric": headline_metric(args.scheme, args.grid),
@@ -646,12 +653,16 @@ def main():
                                   "autotune_stage_ms": tuned_ms}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp64_peak,
-                         "traffic": (NCU_DRAM_BYTES_PER_CELL_STAGE[args.scheme] * cells
-                                     if args.scheme in NCU_DRAM_BYTES_PER_CELL_STAGE
-                                     and launch[:3] == NCU_PROFILED_LAUNCH[args.scheme] else None),
+                         "traffic": NCU_DRAM_BYTES_PER_CELL_STAGE[args.scheme] * cells if profiled else None,
                          "traffic_source": "ncu dram__bytes_read+write of the 128^3 stage launches of the same "
-                                           "variant (mean of stages 1-3), scaled by cells",
+                                           "variant (z pass + stage kernel, mean of stages 1-3), scaled by cells",
                          "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[args.scheme],
+                         "flops_count": "every face reconstructed from its own stencil; the kernels share "
+                                        "differences between faces and run products with constants on the "
+                                        "integer pipe, so they execute fewer FP64 instructions",
+                         "ncu_fp64_inst_per_cell_stage": (NCU_FP64_INST_PER_CELL_STAGE.get(args.scheme)
+                                                          if profiled else None),
+                         "ncu_fp64_pipe_busy": NCU_FP64_PIPE_BUSY.get(args.scheme) if profiled else None,
                          "kernel": "stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,
                          "peak_source": "FP64 FMA probe kernel measured in this run (hydro_measure_fp64_peak); "
                                         "MEASURED_PEAKS.json has no FP64 figure; nominal 152 SM x 2 DFMA/clk x "

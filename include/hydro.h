@@ -188,18 +188,25 @@ const char* hydro_last_error(hydro_t* h);
  * only; the numerical result equals hydro_step's bit for bit. */
 hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double kernel_ms[5]);
 
-/* Launch configuration of the stage kernel.  Several CTA tile shapes are
- * compiled per scheme (variant 0 is the default); the z-chunk (planes per CTA)
- * sets how many CTAs share a column.  hydro_set_launch forces a variant
+/* Launch configuration of the stage kernel.  Several CTA tile shapes and
+ * face orders are compiled per scheme (a new handle starts on the fastest for
+ * the 256^3 workload); the z-chunk (planes per CTA) sets how many CTAs share a
+ * column.  Some variants compute the z-face fluxes in a separate z pass that
+ * runs before each stage kernel.  hydro_set_launch forces a variant
  * (0 <= variant < hydro_launch_variants(scheme, split, nq)) and z-chunk (zc <= 0: the
- * built-in wave-count heuristic), rebuilding the step graph.  Results do not
- * depend on the choice beyond FMA-level rounding of the same formulas. */
+ * built-in wave-count heuristic), rebuilding the step graph; a z-pass variant is
+ * refused (HYDRO_ERR_INVALID_ARG) for grids with more than 65535 rows.  Results do
+ * not depend on the choice beyond FMA-level rounding of the same formulas. */
 int32_t hydro_launch_variants(int32_t scheme, int32_t split, int32_t nq);
 /* The same count for a full configuration (characteristic-wise WENO has its
  * own tile shapes); 0 for an invalid configuration. */
 int32_t hydro_launch_variants_cfg(const hydro_config* cfg);
 hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc);
 hydro_status hydro_get_launch(hydro_t* h, int32_t* variant, int32_t* tile_x, int32_t* tile_y, int32_t* zc);
+/* Kernels one hydro_step step launches with the current launch configuration
+ * (step-begin, per RK3 stage the z pass if any and the stage kernel,
+ * step-end); 0 for a NULL handle.  No GPU work. */
+int32_t hydro_kernels_per_step(hydro_t* h);
 
 /* Autotuner: with a state loaded, time one stage launch for every compiled
  * tile shape and a few z-chunks around the heuristic choice on this grid, keep
@@ -333,6 +340,9 @@ hydro_status hydro_batch_profile_step(hydro_batch_t* b, int32_t nsteps, double k
  * stage-1 launch per candidate (states, speeds and times are unchanged) and
  * keeps the fastest. */
 hydro_status hydro_batch_set_launch(hydro_batch_t* b, int32_t variant, int32_t zc);
+/* Kernels one hydro_batch_step step launches (as hydro_kernels_per_step, for
+ * the whole batch); 0 for a NULL handle.  No GPU work. */
+int32_t hydro_batch_kernels_per_step(hydro_batch_t* b);
 hydro_status hydro_batch_get_launch(hydro_batch_t* b, int32_t* variant, int32_t* tile_x, int32_t* tile_y, int32_t* zc,
                                     int32_t* n_items);
 hydro_status hydro_batch_autotune(hydro_batch_t* b, double* best_ms);

@@ -97,6 +97,7 @@ def lib():
         "hydro_launch_variants_cfg": ([P(HydroConfig)], i32),
         "hydro_set_launch": ([vp, i32, i32], i32),
         "hydro_get_launch": ([vp, P(i32), P(i32), P(i32), P(i32)], i32),
+        "hydro_kernels_per_step": ([vp], i32),
         "hydro_autotune": ([vp, P(d)], i32),
         "hydro_state_device_ptr": ([vp], vp),
         "hydro_field_stride": ([vp], i64),
@@ -118,6 +119,7 @@ def lib():
         "hydro_batch_profile_step": ([vp, i32, P(d)], i32),
         "hydro_batch_set_launch": ([vp, i32, i32], i32),
         "hydro_batch_get_launch": ([vp, P(i32), P(i32), P(i32), P(i32), P(i32)], i32),
+        "hydro_batch_kernels_per_step": ([vp], i32),
         "hydro_batch_autotune": ([vp, P(d)], i32),
         "hydro_halo_doubles": ([vp], i64),
         "hydro_halo_pack": ([vp, i32, i32, vp, i32], i32),
@@ -249,6 +251,10 @@ class Hydro:
         v = [ctypes.c_int32() for _ in range(4)]
         self._check(self._L.hydro_get_launch(self._h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def kernels_per_step(self):
+        """Kernels one step launches with the current launch configuration."""
+        return int(self._L.hydro_kernels_per_step(self._h))
 
     def forward_record(self, nsteps, ckpt_every=10):
         """Advance nsteps steps, recording speeds/dt and checkpoints for adjoint()."""
@@ -434,6 +440,10 @@ class HydroBatch:
         v = [ctypes.c_int32() for _ in range(5)]
         self._check(self._L.hydro_batch_get_launch(self._h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def kernels_per_step(self):
+        """Kernels one step launches (the whole batch)."""
+        return int(self._L.hydro_batch_kernels_per_step(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -589,6 +589,13 @@ extern "C" int32_t hydro_launch_variants_cfg(const hydro_config* cfg)
     return launch_variant_count(scheme_R(cfg->scheme), cfg->split, cfg->nq, cfg->charwise);
 }
 
+extern "C" int32_t hydro_kernels_per_step(hydro_t* h)
+{
+    if (!h) return 0;
+    const bool zpass = h->L.zfn && axis_active(h->cfg, 2);
+    return 2 + 3 * (zpass ? 2 : 1);
+}
+
 extern "C" hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc)
 {
     if (!h) return HYDRO_ERR_INVALID_ARG;

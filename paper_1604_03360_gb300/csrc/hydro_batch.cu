@@ -24,6 +24,8 @@ struct BatchEvent {
     double* U[3];
     double* W[3];
     double* S[3];             // per-axis speeds (local LF only)
+    double* fz;               // z-face fluxes (z-pass variants): 5 fields of nz + 1 face planes
+    long long fzs;
     long long fs, ncell;
     int n[3], bc[3], act[3];
     double hdx[3];
@@ -36,6 +38,7 @@ struct BatchArgs {
     const BatchEvent* ev;
     const int4* items;        // (event, tile x, tile y, z chunk)
     int n_items;
+    const int4* zitems;       // z pass: (event, x block, row, face chunk)
     unsigned int* counter;    // this stage's work-list counter (zeroed by step-begin)
     int stage;                // 1, 2, 3
     int zc;
@@ -73,10 +76,13 @@ __device__ __forceinline__ StageArgs batch_stage_args(const BatchEvent& E, int s
     a.bad_cell = &E.ctl->bad_cell;
     a.s_in = E.S[in];
     a.s_out = stage == 3 ? E.S[0] : E.S[stage];
+    a.fz = E.fz;
+    a.fzs = E.fzs;
     return a;
 }
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false)>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false),
+          bool ZEXT = false>
 __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) batch_stage_kernel(const BatchArgs b)
 {
     extern __shared__ __align__(16) double smem[];
@@ -89,8 +95,17 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) b
         if (it >= b.n_items) break;
         const int4 w = b.items[it];
         const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
-        stage_tile<R, TX, TY, ILP, LLF, 5, false, EMU>(a, w.y, w.z, w.w, smem);
+        stage_tile<R, TX, TY, ILP, LLF, 5, false, EMU, ZEXT>(a, w.y, w.z, w.w, smem);
     }
+}
+
+// z pass of all events (z-pass variants): one CTA per z item
+template <int R, int EMU>
+__global__ void __launch_bounds__(kZPassThreads, 3) batch_zflux_kernel(const BatchArgs b)
+{
+    const int4 w = b.zitems[blockIdx.x];
+    const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
+    zflux_item<R, EMU>(a, w.y, w.z, w.w);
 }
 
 __global__ void batch_step_begin_kernel(const BatchEvent* ev, int n, unsigned int* counters)
@@ -127,14 +142,18 @@ struct BatchLaunch {
     void (*fn)(BatchArgs);
     size_t smem;
     int tx, ty, ctas_per_sm;
+    void (*zfn)(BatchArgs) = nullptr;   // z pass before fn (z-pass variants)
 };
 
-template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false)>
+template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false),
+          bool ZEXT = false>
 static cudaError_t batch_info_for(BatchLaunch* out)
 {
-    auto fn = batch_stage_kernel<R, TX, TY, ILP, LLF, EMU>;
+    auto fn = batch_stage_kernel<R, TX, TY, ILP, LLF, EMU, ZEXT>;
     out->fn = fn;
-    out->smem = StageSmem<R, TX, TY, LLF, 5, false, ILP == kPencilSweep>::bytes;
+    out->zfn = nullptr;
+    if constexpr (ZEXT) out->zfn = batch_zflux_kernel<R, EMU>;
+    out->smem = StageSmem<R, TX, TY, LLF, 5, false, ILP == kPencilSweep, ZEXT>::bytes;
     out->tx = TX;
     out->ty = TY;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
@@ -159,6 +178,7 @@ static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* ou
         if (v == 4) return batch_info_for<3, 16, 16, kPencilSweep, false, 0>(out);
         if (v == 5) return batch_info_for<3, 16, 8, kPencilSweep>(out);
         if (v == 6) return batch_info_for<3, 16, 16, kPencilSweep>(out);
+        if (v == 7) return batch_info_for<3, 16, 16, kPencilSweep, false, kEmuConst, true>(out);
     }
     if (R == 4) {
         if (v == 0) return batch_info_for<4, 16, 16>(out);
@@ -167,6 +187,7 @@ static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* ou
         if (v == 3) return batch_info_for<4, 16, 16, kPencilSweep, false, 0>(out);
         if (v == 4) return batch_info_for<4, 16, 8, kPencilSweep>(out);
         if (v == 5) return batch_info_for<4, 16, 16, kPencilSweep>(out);
+        if (v == 6) return batch_info_for<4, 16, 16, kPencilSweep, false, kEmuConst, true>(out);
     }
     return cudaErrorInvalidValue;
 }
@@ -189,6 +210,8 @@ struct hydro_batch_s {
     unsigned int* counters = nullptr;
     int4* d_items = nullptr;
     int n_items = 0;
+    int4* d_zitems = nullptr;        // z-pass items (z-pass variants)
+    int n_zitems = 0;
     BatchLaunch L{};
     int variant = 0, zc = 16;
     cudaGraphExec_t exec = nullptr;
@@ -239,7 +262,52 @@ static hydro_status build_items(hydro_batch_t* b)
     b->n_items = (int)items.size();
     BCK(b, cudaMalloc(&b->d_items, sizeof(int4) * items.size()), "work-list");
     BCK(b, cudaMemcpy(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice), "work-list copy");
+    // z-pass items: (event, x block of 32, row, chunk of kZFaces faces) of every
+    // event with an active z axis
+    if (b->d_zitems) {
+        cudaFree(b->d_zitems);
+        b->d_zitems = nullptr;
+    }
+    b->n_zitems = 0;
+    if (b->L.zfn) {
+        std::vector<int4> zi;
+        for (int e : order) {
+            const int* n = b->ev[e].n;
+            if (!b->ev[e].act[2]) continue;
+            const int gx = (n[0] + 31) / 32, gz = (n[2] + 1 + kZFaces - 1) / kZFaces;
+            for (int z = 0; z < gz; ++z)
+                for (int y = 0; y < n[1]; ++y)
+                    for (int x = 0; x < gx; ++x) zi.push_back(make_int4(e, x, y, z));
+        }
+        b->n_zitems = (int)zi.size();
+        if (!zi.empty()) {
+            BCK(b, cudaMalloc(&b->d_zitems, sizeof(int4) * zi.size()), "z work-list");
+            BCK(b, cudaMemcpy(b->d_zitems, zi.data(), sizeof(int4) * zi.size(), cudaMemcpyHostToDevice),
+                "z work-list copy");
+        }
+    }
     return HYDRO_OK;
+}
+
+static BatchArgs batch_args(const hydro_batch_t* b, int stage)
+{
+    BatchArgs a;
+    a.ev = b->d_ev;
+    a.items = b->d_items;
+    a.n_items = b->n_items;
+    a.zitems = b->d_zitems;
+    a.counter = b->counters + (stage - 1);
+    a.stage = stage;
+    a.zc = b->zc;
+    return a;
+}
+
+// one stage of all events: the z pass (z-pass variants), then the persistent stage kernel
+static void launch_batch_stage(const hydro_batch_t* b, const BatchArgs& a, cudaStream_t s)
+{
+    if (b->L.zfn && b->n_zitems > 0) b->L.zfn<<<b->n_zitems, kZPassThreads, 0, s>>>(a);
+    const int grid = b->sms * (b->L.ctas_per_sm > 0 ? b->L.ctas_per_sm : 1);
+    b->L.fn<<<grid, b->L.tx * b->L.ty, b->L.smem, s>>>(a);
 }
 
 static cudaError_t enqueue_batch_step(hydro_batch_t* b, cudaStream_t s, cudaEvent_t* marks)
@@ -248,16 +316,8 @@ static cudaError_t enqueue_batch_step(hydro_batch_t* b, cudaStream_t s, cudaEven
     if (marks) cudaEventRecord(marks[0], s);
     batch_step_begin_kernel<<<eb, 128, 0, s>>>(b->d_ev, b->n_events, b->counters);
     if (marks) cudaEventRecord(marks[1], s);
-    const int grid = b->sms * (b->L.ctas_per_sm > 0 ? b->L.ctas_per_sm : 1);
     for (int k = 1; k <= 3; ++k) {
-        BatchArgs a;
-        a.ev = b->d_ev;
-        a.items = b->d_items;
-        a.n_items = b->n_items;
-        a.counter = b->counters + (k - 1);
-        a.stage = k;
-        a.zc = b->zc;
-        b->L.fn<<<grid, b->L.tx * b->L.ty, b->L.smem, s>>>(a);
+        launch_batch_stage(b, batch_args(b, k), s);
         if (marks) cudaEventRecord(marks[1 + k], s);
     }
     batch_step_end_kernel<<<eb, 128, 0, s>>>(b->d_ev, b->n_events);
@@ -329,6 +389,7 @@ hydro_status hydro_batch_destroy(hydro_batch_t* b)
     cudaFree(b->d_ev);
     cudaFree(b->counters);
     cudaFree(b->d_items);
+    cudaFree(b->d_zitems);
     if (b->hctl) cudaFreeHost(b->hctl);
     delete b;
     return HYDRO_OK;
@@ -378,6 +439,9 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
         b->ev[i].ncell = nc;
         b->ev[i].fs = (nc + 31) / 32 * 32;
         total += (cfgs[0].split ? 36 : 27) * b->ev[i].fs;
+        // z-face fluxes for the z-pass variants (global Lax-Friedrichs)
+        b->ev[i].fzs = cfgs[0].split ? 0 : ((long long)cfgs[i].n[0] * cfgs[i].n[1] * (cfgs[i].n[2] + 1) + 31) / 32 * 32;
+        total += 5 * b->ev[i].fzs;
     }
     if ((e = cudaMalloc(&b->buf, sizeof(double) * (size_t)total)) != cudaSuccess) return bail(bcuda(b, e, "event buffers"));
     if ((e = cudaMalloc(&b->ctl, sizeof(Ctl) * n_events)) != cudaSuccess) return bail(bcuda(b, e, "control blocks"));
@@ -394,6 +458,8 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
             E.S[k] = c.split ? b->buf + off + E.fs * (27 + 3 * k) : nullptr;
         }
         off += (c.split ? 36 : 27) * E.fs;
+        E.fz = E.fzs ? b->buf + off : nullptr;
+        off += 5 * E.fzs;
         for (int d = 0; d < 3; ++d) {
             E.n[d] = c.n[d];
             E.bc[d] = c.bc[d];
@@ -552,6 +618,12 @@ hydro_status hydro_batch_get_state(hydro_batch_t* b, int32_t e, double* u, int64
 
 int32_t hydro_batch_size(hydro_batch_t* b) { return b ? b->n_events : 0; }
 
+int32_t hydro_batch_kernels_per_step(hydro_batch_t* b)
+{
+    if (!b) return 0;
+    return 2 + 3 * ((b->L.zfn && b->n_zitems > 0) ? 2 : 1);
+}
+
 hydro_status hydro_batch_set_launch(hydro_batch_t* b, int32_t variant, int32_t zc)
 {
     if (!b) return HYDRO_ERR_INVALID_ARG;
@@ -591,19 +663,12 @@ hydro_status hydro_batch_autotune(hydro_batch_t* b, double* best_ms)
         for (int zc : zcs) {
             s = apply_batch_launch(b, v, zc);
             if (s) break;
-            BatchArgs a;
-            a.ev = b->d_ev;
-            a.items = b->d_items;
-            a.n_items = b->n_items;
-            a.counter = b->counters;
-            a.stage = 1;
-            a.zc = b->zc;
-            const int grid = b->sms * (b->L.ctas_per_sm > 0 ? b->L.ctas_per_sm : 1);
+            const BatchArgs a = batch_args(b, 1);
             float ms = 0.f;
             for (int rep = 0; rep < 2; ++rep) {   // warm-up, then timed
                 batch_step_begin_kernel<<<eb, 128, 0, b->stream>>>(b->d_ev, b->n_events, b->counters);
                 cudaEventRecord(e0, b->stream);
-                b->L.fn<<<grid, b->L.tx * b->L.ty, b->L.smem, b->stream>>>(a);
+                launch_batch_stage(b, a, b->stream);
                 cudaEventRecord(e1, b->stream);
             }
             cudaError_t e = cudaEventSynchronize(e1);

@@ -178,7 +178,7 @@ int fused_launch_variant(int R, int split, int nq, int charw)
 int batch_variant_count(int R, int split)
 {
     if (split == 1) return R == 3 ? 2 : 1;
-    return R == 3 ? 7 : 6;
+    return R == 3 ? 8 : 7;
 }
 
 int launch_variant_count(int R, int split, int nq, int charw)

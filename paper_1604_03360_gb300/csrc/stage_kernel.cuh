@@ -731,15 +731,18 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 && NF == 5 
 // zlo+f-1 and zlo+f (f = 0 .. zhi-zlo); its left-biased stencil is centred
 // on plane zlo+f-1, its right-biased one on plane zlo+f.
 constexpr int kZFaces = 64, kZPassThreads = 160;
+
+// one z-pass item: x block xb (32 columns), row y, face chunk zch, of the grid
+// described by a; the CTA's five warps are the five fields
 template <int R, int EMU>
-__global__ void __launch_bounds__(kZPassThreads) zflux_kernel(const StageArgs a)
+__device__ __forceinline__ void zflux_item(const StageArgs& a, int xb, int y, int zch)
 {
     constexpr int G = R, S = 2 * R - 1;
     using DF = typename DiffOf<R>::T;
     if (!(*a.dt > 0.0)) return;
-    const int k = threadIdx.x >> 5, x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y;
+    const int k = threadIdx.x >> 5, x = xb * 32 + (threadIdx.x & 31);
     if (x >= a.nx) return;                       // no barriers below
-    const int f0 = blockIdx.z * kZFaces, f1 = min(f0 + kZFaces, a.zhi - a.zlo + 1);
+    const int f0 = zch * kZFaces, f1 = min(f0 + kZFaces, a.zhi - a.zlo + 1);
     const double az = __longlong_as_double((long long)a.alpha_in[2]);
     const long long plane = (long long)a.nx * a.ny, col = (long long)y * a.nx + x;
     // split z-fluxes g+- = f_z +- alpha_z u of field k at stored plane m (as split_flux)
@@ -798,6 +801,12 @@ __global__ void __launch_bounds__(kZPassThreads) zflux_kernel(const StageArgs a)
             wm[S - 1] = gm;
         }
     }
+}
+
+template <int R, int EMU>
+__global__ void __launch_bounds__(kZPassThreads) zflux_kernel(const StageArgs a)
+{
+    zflux_item<R, EMU>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace hydro

@@ -67,6 +67,8 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.hydro_sync(None) == 1
     assert L.hydro_destroy(None) == 0
     assert L.hydro_field_stride(None) == 0
+    assert L.hydro_kernels_per_step(None) == 0
+    assert L.hydro_batch_kernels_per_step(None) == 0
 
 
 def test_charwise_needs_weno_with_global_splitting(L):

@@ -233,6 +233,18 @@ def test_pencil_sweep_matches_per_face_bitwise(scheme, n):
         assert np.array_equal(out[0], out[1]), (v_face, v_sweep)
 
 
+def test_kernels_per_step_follows_the_launch():
+    """A z-pass launch runs two kernels per RK3 stage when z is active, a fused
+    one a single kernel; begin and end add two."""
+    from paper_1604_03360_gb300 import Hydro
+    for n, v, want in (((16, 16, 12), 6, 8), ((16, 16, 12), 5, 5), ((16, 16, 1), 6, 5)):
+        g, w = W.lumpy(n=n, seed=5, scheme=7)
+        with Hydro.from_grid(g) as h:
+            assert h.launch()[0] == 6          # the default launch
+            h.set_launch(v)
+            assert h.kernels_per_step() == want, (n, v)
+
+
 def test_autotune_keeps_results(tmp_path, monkeypatch):
     from paper_1604_03360_gb300 import Hydro
     monkeypatch.setenv("HYDRO_TUNE_CACHE", str(tmp_path / "tune.txt"))

@@ -82,8 +82,9 @@ __device__ __forceinline__ StageArgs batch_stage_args(const BatchEvent& E, int s
 }
 
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false),
-          bool ZEXT = false>
-__global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 ? 2 : 1)) batch_stage_kernel(const BatchArgs b)
+          bool ZEXT = false, int MINB = 0>
+__global__ void __launch_bounds__(TX * TY, (MINB > 0 ? MINB : (TX * TY <= 128 && R == 3 ? 2 : 1)))
+    batch_stage_kernel(const BatchArgs b)
 {
     extern __shared__ __align__(16) double smem[];
     __shared__ int s_item;
@@ -146,13 +147,13 @@ struct BatchLaunch {
 };
 
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false),
-          bool ZEXT = false>
+          bool ZEXT = false, int ZEMU = EMU, int MINB = 0>
 static cudaError_t batch_info_for(BatchLaunch* out)
 {
-    auto fn = batch_stage_kernel<R, TX, TY, ILP, LLF, EMU, ZEXT>;
+    auto fn = batch_stage_kernel<R, TX, TY, ILP, LLF, EMU, ZEXT, MINB>;
     out->fn = fn;
     out->zfn = nullptr;
-    if constexpr (ZEXT) out->zfn = batch_zflux_kernel<R, EMU>;
+    if constexpr (ZEXT) out->zfn = batch_zflux_kernel<R, ZEMU>;
     out->smem = StageSmem<R, TX, TY, LLF, 5, false, ILP == kPencilSweep, ZEXT>::bytes;
     out->tx = TX;
     out->ty = TY;
@@ -178,7 +179,9 @@ static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* ou
         if (v == 4) return batch_info_for<3, 16, 16, kPencilSweep, false, 0>(out);
         if (v == 5) return batch_info_for<3, 16, 8, kPencilSweep>(out);
         if (v == 6) return batch_info_for<3, 16, 16, kPencilSweep>(out);
-        if (v == 7) return batch_info_for<3, 16, 16, kPencilSweep, false, kEmuConst, true>(out);
+        if (v == 7) return batch_info_for<3, 16, 16, kPencilSweep, false, kEmuConst, true, kZPassEmu5>(out);
+        if (v == 8)
+            return batch_info_for<3, 16, 16, kPencilSweep, false, kEmuConst | kEmuWeights, true, kZPassEmu5, 2>(out);
     }
     if (R == 4) {
         if (v == 0) return batch_info_for<4, 16, 16>(out);
@@ -187,7 +190,8 @@ static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* ou
         if (v == 3) return batch_info_for<4, 16, 16, kPencilSweep, false, 0>(out);
         if (v == 4) return batch_info_for<4, 16, 8, kPencilSweep>(out);
         if (v == 5) return batch_info_for<4, 16, 16, kPencilSweep>(out);
-        if (v == 6) return batch_info_for<4, 16, 16, kPencilSweep, false, kEmuConst, true>(out);
+        if (v == 6) return batch_info_for<4, 16, 16, kPencilSweep, false, kEmuConst, true, kZPassEmu7>(out);
+        if (v == 7) return batch_info_for<4, 16, 16, kPencilSweep, false, kEmuConst, true, kZPassEmu7, 2>(out);
     }
     return cudaErrorInvalidValue;
 }

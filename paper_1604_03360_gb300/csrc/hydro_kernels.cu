@@ -132,13 +132,13 @@ __global__ void state_to_prim_kernel(const double* u, long long fs, double* out,
 }
 
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5,
-          int EMU = default_emu(R, TX, TY, LLF, NF, false), bool ZEXT = false>
+          int EMU = default_emu(R, TX, TY, LLF, NF, false), bool ZEXT = false, int ZEMU = EMU, int MINB = 0>
 static cudaError_t info_for(StageLaunch* out)
 {
-    auto fn = stage_kernel<R, TX, TY, ILP, LLF, NF, false, EMU, ZEXT>;
+    auto fn = stage_kernel<R, TX, TY, ILP, LLF, NF, false, EMU, ZEXT, MINB>;
     out->fn = fn;
     out->zfn = nullptr;
-    if constexpr (ZEXT) out->zfn = zflux_kernel<R, EMU>;
+    if constexpr (ZEXT) out->zfn = zflux_kernel<R, ZEMU>;
     out->smem = StageSmem<R, TX, TY, LLF, NF, false, ILP == kPencilSweep, ZEXT>::bytes;
     out->tx = TX;
     out->ty = TY;
@@ -154,10 +154,13 @@ static cudaError_t info_for(StageLaunch* out)
 //        face items per iteration, pencil sweeps on 16x16 (all products on the
 //        FP64 unit) and 16x8, and the 16x16 pencil sweep.
 // The two marked variants keep every product on the FP64 unit (the bitwise
-// reference); the others take the default of default_emu.  WENO5 7 / WENO7 6:
-// the 16x16 pencil sweep with the z faces from a separate z pass (zflux_kernel:
-// long z pencils at 15 warps per SM, carried differences; the stage kernel
-// then keeps no z ring).
+// reference); the others take the default of default_emu.  WENO5 7, 8 /
+// WENO7 6, 7: the 16x16 pencil sweep with the z faces from a separate z pass
+// (zflux_kernel: long z pencils at 15-20 warps per SM, carried differences;
+// the stage kernel then keeps no z ring), with one stage CTA per SM or two
+// (8 / 16 warps; the compiler caps the registers at 128).  The z pass, and
+// with 16 warps the WENO5 stage kernel, also take the weight products on the
+// integer pipe: with that many warps the longer integer chains are hidden.
 // Local LF (raw staging, 2G-plane ring): WENO5 16x16 and 16x8; WENO7 16x8
 // (16x16 would need 247 KB of shared memory).
 // Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
@@ -166,7 +169,7 @@ static cudaError_t info_for(StageLaunch* out)
 int default_launch_variant(int R, int split, int nq, int charw)
 {
     if (charw || R == 2 || split || nq > 1) return 0;
-    return R == 3 ? 7 : 6;
+    return R == 3 ? 8 : 7;
 }
 
 int fused_launch_variant(int R, int split, int nq, int charw)
@@ -178,7 +181,7 @@ int fused_launch_variant(int R, int split, int nq, int charw)
 int batch_variant_count(int R, int split)
 {
     if (split == 1) return R == 3 ? 2 : 1;
-    return R == 3 ? 8 : 7;
+    return R == 3 ? 9 : 8;
 }
 
 int launch_variant_count(int R, int split, int nq, int charw)
@@ -187,7 +190,7 @@ int launch_variant_count(int R, int split, int nq, int charw)
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 2 : 1;
-    return R == 3 ? 8 : 7;
+    return R == 3 ? 9 : 8;
 }
 
 template <int NF>
@@ -242,7 +245,8 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 4) return info_for<3, 16, 16, kPencilSweep, false, 5, 0>(out);
         if (v == 5) return info_for<3, 16, 8, kPencilSweep>(out);
         if (v == 6) return info_for<3, 16, 16, kPencilSweep>(out);
-        if (v == 7) return info_for<3, 16, 16, kPencilSweep, false, 5, kEmuConst, true>(out);
+        if (v == 7) return info_for<3, 16, 16, kPencilSweep, false, 5, kEmuConst, true, kZPassEmu5>(out);
+        if (v == 8) return info_for<3, 16, 16, kPencilSweep, false, 5, kEmuConst | kEmuWeights, true, kZPassEmu5, 2>(out);
     }
     if (R == 4) {
         if (v == 0) return info_for<4, 16, 16>(out);
@@ -251,7 +255,8 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 3) return info_for<4, 16, 16, kPencilSweep, false, 5, 0>(out);
         if (v == 4) return info_for<4, 16, 8, kPencilSweep>(out);
         if (v == 5) return info_for<4, 16, 16, kPencilSweep>(out);
-        if (v == 6) return info_for<4, 16, 16, kPencilSweep, false, 5, kEmuConst, true>(out);
+        if (v == 6) return info_for<4, 16, 16, kPencilSweep, false, 5, kEmuConst, true, kZPassEmu7>(out);
+        if (v == 7) return info_for<4, 16, 16, kPencilSweep, false, 5, kEmuConst, true, kZPassEmu7, 2>(out);
     }
     return cudaErrorInvalidValue;
 }

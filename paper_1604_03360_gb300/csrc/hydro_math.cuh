@@ -152,9 +152,11 @@ struct Diff5 {
 };
 
 // EMU selects operations that run on the integer pipe (fp64_int.cuh) instead
-// of the FP64 unit: kEmuConst the products with constants.  Every choice gives
-// the same bits.
-constexpr int kEmuConst = 1;
+// of the FP64 unit: kEmuConst the products with constants, kEmuWeights the
+// squares and products of the nonlinear weights, kEmuFace the last products of
+// the weighted sums and of the face combination.  Every choice gives the same
+// bits.
+constexpr int kEmuConst = 1, kEmuWeights = 2, kEmuFace = 4;
 
 template <int EMU = 0>
 __device__ __forceinline__ void weno5_diffs(const double* v, Diff5& q)
@@ -216,15 +218,16 @@ __device__ __forceinline__ void weno5_core(const Diff5& q, double eps_s, double&
     const double b0 = fma(q.ks[0], q.s[0], fma(t0, t0, eps_s));
     const double b1 = fma(q.ks[1], q.s[1], fma(t1, t1, eps_s));
     const double b2 = fma(q.ks[2], q.s[2], fma(t2, t2, eps_s));
-    const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2;
-    const double P0 = w1 * w2, P1 = w0 * w2, P2 = w0 * w1;
+    constexpr bool EW = (EMU & kEmuWeights) != 0;
+    const double w0 = xmul<EW>(b0, b0), w1 = xmul<EW>(b1, b1), w2 = xmul<EW>(b2, b2);
+    const double P0 = xmul<EW>(w1, w2), P1 = xmul<EW>(w0, w2), P2 = xmul<EW>(w0, w1);
     // 10 d_k (q_k - c), c = v[2]: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6 =
     // c - d0/3 + 5 d1/6, q1 = (-b+5c+2d)/6 = c + (d1 + 2 d2)/6,
     // q2 = (2c+5d-e)/6 = c + (4 d2 - d3)/6
     const double m0 = fma(5.0 / 6.0, d1, xmul<EC>(-1.0 / 3.0, d0));
     const double m1 = fma(2.0, d2, d1);
     const double m2 = fma(-0.5, d3, xmul_pow2<EC, 1>(d2));
-    M = fma(m0, P0, fma(m1, P1, m2 * P2));
+    M = fma(m0, P0, fma(m1, P1, xmul<(EMU & kEmuFace) != 0>(m2, P2)));
     D = fma(3.0, P2, fma(6.0, P1, P0));
 }
 
@@ -325,9 +328,10 @@ __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
     const double b1 = fma(A1, A1, fma(b39, B12, q.ct[1]));
     const double b2 = fma(A2, A2, fma(b39, B12, q.ct[2]));
     const double b3 = fma(A3, A3, fma(xmul_small<EC, 39, 6, 0>(B3), B3, q.ct[3]));
-    const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2, w3 = b3 * b3;
-    const double p01 = w0 * w1, p23 = w2 * w3;
-    const double P0 = w1 * p23, P1 = w0 * p23, P2 = p01 * w3, P3 = p01 * w2;
+    constexpr bool EW = (EMU & kEmuWeights) != 0;
+    const double w0 = xmul<EW>(b0, b0), w1 = xmul<EW>(b1, b1), w2 = xmul<EW>(b2, b2), w3 = xmul<EW>(b3, b3);
+    const double p01 = xmul<EW>(w0, w1), p23 = xmul<EW>(w2, w3);
+    const double P0 = xmul<EW>(w1, p23), P1 = xmul<EW>(w0, p23), P2 = xmul<EW>(p01, w3), P3 = xmul<EW>(p01, w2);
     // 35 d_k (q_k - v3), d = (1, 12, 18, 4)/35, in the difference basis:
     // q0 - v3 = d0/4 - 5 d1/6 + 13 d2/12, q1 - v3 = (-d1 + 4 d2 + 3 d3)/12,
     // q2 - v3 = (d2 + 6 d3 - d4)/12, q3 - v3 = (9 d3 - 4 d4 + d5)/12
@@ -335,7 +339,7 @@ __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
     const double m1 = fma(3.0, d3, fma(4.0, d2, -d1));
     const double m2 = fma(9.0, d3, xmul_small<EC, 3, 2, -1>(d2 - d4));
     const double m3 = fma(3.0, d3, fma(-4.0 / 3.0, d4, xmul<EC>(1.0 / 3.0, d5)));
-    M = fma(m0, P0, fma(m1, P1, fma(m2, P2, m3 * P3)));
+    M = fma(m0, P0, fma(m1, P1, fma(m2, P2, xmul<(EMU & kEmuFace) != 0>(m3, P3))));
     D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
 }
 
@@ -373,9 +377,11 @@ __device__ __forceinline__ void weno_right(const double* v, double eps_s, double
 
 // Face value (cp + Mp/Dp) + (cm + Mm/Dm) with one reciprocal; cp, cm are the
 // centre values of the two stencils.
+template <int EMU = 0>
 __device__ __forceinline__ double face_sum(double Mp, double Dp, double cp, double Mm, double Dm, double cm)
 {
-    return fma(fma(Mp, Dm, Mm * Dp), rcp(Dp * Dm), cp + cm);
+    constexpr bool EF = (EMU & kEmuFace) != 0;
+    return fma(fma(Mp, Dm, xmul<EF>(Mm, Dp)), rcp(xmul<EF>(Dp, Dm)), cp + cm);
 }
 
 template <int R> struct SchemeConst;

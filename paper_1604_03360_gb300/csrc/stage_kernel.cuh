@@ -402,17 +402,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 
     for (int p = zb; p < ze; ++p) {
-        if constexpr (ZEXT) {
-            // z faces p-1/2 and p+1/2 of this column, from the z pass
-            if (zact && own) {
-                const double* fz = a.fz + (long long)(p - a.zlo) * plane + (long long)y * nx + x;
-#pragma unroll
-                for (int k = 0; k < NF; ++k) {
-                    Fzm[k] = fz[k * a.fzs];
-                    Fzp[k] = fz[k * a.fzs + plane];
-                }
-            }
-        }
         // 1. z: ingest plane p+G, face p+1/2 = R+(p) + R-(p+1)
         if (zwork && LLF) {
             ingest(p + G);
@@ -650,6 +639,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         }
         __syncthreads();
         // 4. combine, RK update, primitives and speeds of the new state
+        if constexpr (ZEXT) {
+            // z faces p-1/2 and p+1/2 of this column, from the z pass (read here,
+            // not before the x/y phase, so they hold no registers there)
+            if (zact && own) {
+                const double* fz = a.fz + (long long)(p - a.zlo) * plane + (long long)y * nx + x;
+#pragma unroll
+                for (int k = 0; k < NF; ++k) {
+                    Fzm[k] = fz[k * a.fzs];
+                    Fzp[k] = fz[k * a.fzs + plane];
+                }
+            }
+        }
         if (own) {
             const long long q = (long long)p * plane + (long long)y * nx + x;
             double un[NF];
@@ -713,9 +714,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     }
 }
 
+// MINB > 0: at least that many CTAs per SM (the compiler caps the registers)
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false,
-          int EMU = default_emu(R, TX, TY, LLF, NF, CHW), bool ZEXT = false>
-__global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 && NF == 5 && !CHW ? 2 : 1))
+          int EMU = default_emu(R, TX, TY, LLF, NF, CHW), bool ZEXT = false, int MINB = 0>
+__global__ void __launch_bounds__(TX * TY, (MINB > 0 ? MINB : (TX * TY <= 128 && R == 3 && NF == 5 && !CHW ? 2 : 1)))
     stage_kernel(const StageArgs a)
 {
     extern __shared__ __align__(16) double smem[];
@@ -731,6 +733,9 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY <= 128 && R == 3 && NF == 5 
 // zlo+f-1 and zlo+f (f = 0 .. zhi-zlo); its left-biased stencil is centred
 // on plane zlo+f-1, its right-biased one on plane zlo+f.
 constexpr int kZFaces = 64, kZPassThreads = 160;
+// integer-pipe products of the z pass (measured fastest: WENO5 all three
+// kinds, WENO7 without the face products)
+constexpr int kZPassEmu5 = kEmuConst | kEmuWeights | kEmuFace, kZPassEmu7 = kEmuConst | kEmuWeights;
 
 // one z-pass item: x block xb (32 columns), row y, face chunk zch, of the grid
 // described by a; the CTA's five warps are the five fields
@@ -787,7 +792,7 @@ __device__ __forceinline__ void zflux_item(const StageArgs& a, int xb, int y, in
         double Np, Dp, Nm, Dm;
         weno_core<R, EMU>(qp, a.eps_s, Np, Dp);
         weno_core<R, EMU>(qm, a.eps_s, Nm, Dm);
-        out[(long long)f * plane] = face_sum(Np, Dp, wp[G - 1], Nm, Dm, wm[G - 1]);
+        out[(long long)f * plane] = face_sum<EMU>(Np, Dp, wp[G - 1], Nm, Dm, wm[G - 1]);
         if (f + 1 < f1) {
             // next face: planes move up by one
 #pragma unroll

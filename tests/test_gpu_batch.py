@@ -57,7 +57,7 @@ def test_batch_matches_oracle_and_single_grid(scheme):
             assert np.array_equal(h.get_state(), u), i
 
 
-@pytest.mark.parametrize("variant,zc", [(0, 8), (1, 16), (2, 5), (3, 12), (4, 10), (5, 7), (6, 9), (7, 11)])
+@pytest.mark.parametrize("variant,zc", [(0, 8), (1, 16), (2, 5), (3, 12), (4, 10), (5, 7), (6, 9), (7, 11), (8, 13)])
 def test_batch_launch_variants(variant, zc):
     from paper_1604_03360_gb300 import HydroBatch
     ev = make_events(SIZES[:4], scheme=5, seed=950)

@@ -66,7 +66,7 @@ def test_outflow_slabs_match_whole_grid(scheme, nslabs):
     check(g, w, nslabs, 5, device="cuda")
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 7), (7, 6)])
+@pytest.mark.parametrize("scheme,variant", [(5, 7), (5, 8), (7, 6), (7, 7)])
 def test_zpass_slabs_match_whole_grid(scheme, variant):
     """Slabs whose z faces come from the z pass (which reads the stored ghost
     planes) advance bit for bit like the whole grid on the fused kernel."""

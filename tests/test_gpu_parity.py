@@ -183,8 +183,8 @@ def test_unphysical_state_reported():
         assert ei.value.code == 4
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5), (5, 6), (5, 7),
-                                            (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5), (7, 6)])
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5), (5, 6), (5, 7), (5, 8),
+                                            (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5), (7, 6), (7, 7)])
 def test_every_launch_variant(scheme, variant):
     """Every compiled CTA tile shape, with a short z chunk so several chunks
     meet inside the grid, matches the oracle."""
@@ -205,7 +205,7 @@ def test_every_launch_variant(scheme, variant):
 # (per-face variant, pencil-sweep variant) pairs with the same CTA tile,
 # (pencil sweep on the FP64 unit only, pencil sweep with integer-pipe
 # products) and (fused z faces, z faces from the z pass)
-SWEEP_PAIRS = {5: ((0, 4), (1, 5), (4, 6), (6, 7)), 7: ((0, 3), (1, 4), (3, 5), (5, 6))}
+SWEEP_PAIRS = {5: ((0, 4), (1, 5), (4, 6), (6, 7), (7, 8)), 7: ((0, 3), (1, 4), (3, 5), (5, 6), (6, 7))}
 
 
 @pytest.mark.parametrize("scheme", [5, 7])
@@ -237,10 +237,10 @@ def test_kernels_per_step_follows_the_launch():
     """A z-pass launch runs two kernels per RK3 stage when z is active, a fused
     one a single kernel; begin and end add two."""
     from paper_1604_03360_gb300 import Hydro
-    for n, v, want in (((16, 16, 12), 6, 8), ((16, 16, 12), 5, 5), ((16, 16, 1), 6, 5)):
+    for n, v, want in (((16, 16, 12), 7, 8), ((16, 16, 12), 5, 5), ((16, 16, 1), 7, 5)):
         g, w = W.lumpy(n=n, seed=5, scheme=7)
         with Hydro.from_grid(g) as h:
-            assert h.launch()[0] == 6          # the default launch
+            assert h.launch()[0] == 7          # the default launch
             h.set_launch(v)
             assert h.kernels_per_step() == want, (n, v)
 

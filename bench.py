@@ -422,6 +422,8 @@ def main():
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--charwise", action="store_true",
                     help="headline run with characteristic-wise WENO (profiling; the metric stays component-wise)")
+    ap.add_argument("--launch", type=int, default=None,
+                    help="force this stage-kernel launch variant instead of autotuning (profiling)")
     ap.add_argument("--only", choices=["adjoint"], default=None,
                     help="run one extra measurement alone and print it (for profiling)")
     args = ap.parse_args()
@@ -462,7 +464,11 @@ def main():
     h = Hydro.from_grid(g, stream=stream)
     w_dev = torch.from_numpy(w).to(dev)
     h.set_primitive(w_dev)
-    tuned_ms = h.autotune()
+    if args.launch is None:
+        tuned_ms = h.autotune()
+    else:
+        h.set_launch(args.launch)
+        tuned_ms = None
     launch = h.launch()
     h.step(args.warmup)
     torch.cuda.synchronize()

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(TX * TY, (MINB > 0 ? MINB : (TX * TY <= 128 &&
 
 // z pass of all events (z-pass variants): one CTA per z item
 template <int R, int EMU>
-__global__ void __launch_bounds__(kZPassThreads, 3) batch_zflux_kernel(const BatchArgs b)
+__global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) batch_zflux_kernel(const BatchArgs b)
 {
     const int4 w = b.zitems[blockIdx.x];
     const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);

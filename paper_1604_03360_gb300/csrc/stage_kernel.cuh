@@ -808,8 +808,9 @@ __device__ __forceinline__ void zflux_item(const StageArgs& a, int xb, int y, in
     }
 }
 
+// (3 CTAs per SM for WENO7, 4 for WENO5: 15 and 20 warps)
 template <int R, int EMU>
-__global__ void __launch_bounds__(kZPassThreads) zflux_kernel(const StageArgs a)
+__global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_kernel(const StageArgs a)
 {
     zflux_item<R, EMU>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }

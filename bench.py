@@ -34,22 +34,23 @@ sys.path.insert(0, ROOT)
 # (mean of 10/25/25), split fluxes 75, primitive recovery 22, speeds 34.  The
 # pencil-sweep kernels carry stencil differences between neighbouring faces
 # and take the products with constants on the integer pipe, so they execute
-# fewer FP64 instructions than this count implies (ncu: 1824 per cell and
+# fewer FP64 instructions than this count implies (ncu: 1743 per cell and
 # stage for WENO7, 85 % FP64 pipe busy), and the flop rate by this count can
 # read above the FP64 peak.
 FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
                         7: 15 * (2 * 136 + 6) + 40 + 20 + 75 + 22 + 34}
-# DRAM traffic of one WENO7 stage of the default launch (z pass + stage
-# kernel), measured by ncu on the 128^3 case
-# (profiles/stage_weno7_zpass_128.md): stage 1 506.2 MB, stages 2 and 3
-# 594.8 MB, mean 565.3 MB / 2.10 M cells; it scales with the cell count.  Same
-# capture: 1824 FP64 instructions per cell and stage, FP64 pipe 85 % busy.
+# DRAM traffic of one WENO7 stage of the default launch (variant 7: z pass +
+# stage kernel), measured by ncu on the 128^3 case
+# (profiles/stage_weno7_zpass_128.md): stage 1 521.5 MB, stages 2 and 3
+# 616.0 MB, mean 584.5 MB / 2.10 M cells; it scales with the cell count.  Same
+# capture: 1743 FP64 instructions per cell and stage; FP64 pipe busy 79 % (z
+# pass, 25 % of the time) and 87 % (stage kernel), 85 % time-weighted.
 # None for WENO5 (not captured for the current kernels).
-NCU_DRAM_BYTES_PER_CELL_STAGE = {7: (506.2e6 + 2 * 594.8e6) / 3 / 128 ** 3}
-NCU_FP64_INST_PER_CELL_STAGE = {7: 1824}
+NCU_DRAM_BYTES_PER_CELL_STAGE = {7: (521.5e6 + 2 * 616.0e6) / 3 / 128 ** 3}
+NCU_FP64_INST_PER_CELL_STAGE = {7: 1743}
 NCU_FP64_PIPE_BUSY = {7: 0.85}
 # (variant, tile x, tile y) of the profiled launch; another choice reports null
-NCU_PROFILED_LAUNCH = {7: (6, 16, 16)}
+NCU_PROFILED_LAUNCH = {7: (7, 16, 16)}
 # Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
 # stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
 HBM_BYTES_PER_CELL_UPDATE = 320
@@ -667,8 +668,8 @@ def main():
                                            "variant (z pass + stage kernel, mean of stages 1-3), scaled by cells",
                          "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[args.scheme],
                          "flops_count": "every face reconstructed from its own stencil; the kernels share "
-                                        "differences between faces and run products with constants on the "
-                                        "integer pipe, so they execute fewer FP64 instructions",
+                                        "differences between faces and run some products on the integer "
+                                        "pipe, so they execute fewer FP64 instructions",
                          "ncu_fp64_inst_per_cell_stage": (NCU_FP64_INST_PER_CELL_STAGE.get(args.scheme)
                                                           if profiled else None),
                          "ncu_fp64_pipe_busy": NCU_FP64_PIPE_BUSY.get(args.scheme) if profiled else None,

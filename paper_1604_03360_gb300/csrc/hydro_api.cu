@@ -651,7 +651,7 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
             for (auto& q : scored) dup |= (q.second == z);
             if (dup) continue;
             const long long ctas = tiles * ((nz + z - 1) / z);
-            const double cost = (double)((ctas + conc - 1) / conc) * (z + 1.5);
+            const double cost = (double)((ctas + conc - 1) / conc) * (z + zc_prologue(L));
             scored.push_back({cost, z});
         }
         std::sort(scored.begin(), scored.end());

@@ -136,6 +136,11 @@ inline bool zpass_capable(const hydro_config& c, int R)
 inline int scheme_R(int scheme) { return scheme == HYDRO_WENO5 ? 3 : (scheme == HYDRO_WENO7 ? 4 : 2); }
 inline int musta_stages_of(const hydro_config& c) { return c.musta_stages > 0 ? c.musta_stages : 2; }
 
+// per-chunk cost of a stage CTA in planes: the z ring's warm-up (2G-1 planes
+// ingested, one z stencil) for the fused kernels, next to nothing for the
+// z-pass variants (no ring)
+inline double zc_prologue(const StageLaunch& L) { return L.zfn ? 0.25 : 1.5; }
+
 inline int pick_zc(int nx, int ny, int nz, const StageLaunch& L, int sms)
 {
     const long long tiles = (long long)((nx + L.tx - 1) / L.tx) * ((ny + L.ty - 1) / L.ty);
@@ -148,7 +153,7 @@ inline int pick_zc(int nx, int ny, int nz, const StageLaunch& L, int sms)
         const int z = zc < nz ? zc : nz;
         const long long ctas = tiles * ((nz + z - 1) / z);
         const long long waves = (ctas + conc - 1) / conc;
-        const double cost = (double)waves * (z + 1.5);   // 1.5 planes: chunk prologue
+        const double cost = (double)waves * (z + zc_prologue(L));
         if (cost < best_cost * 0.999) {
             best_cost = cost;
             best = z;

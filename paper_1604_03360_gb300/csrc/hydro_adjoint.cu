@@ -158,14 +158,16 @@ __device__ __forceinline__ void weno_left_vjp<3>(const double* v, double eps_s, 
     const double d0 = v[1] - v[0], d1 = v[2] - v[1], d2 = v[3] - v[2], d3 = v[4] - v[3];
     const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2;
     const double t0 = fma(3.0, d1, -d0), t1 = d1 + d2, t2 = fma(3.0, d2, -d3);
-    const double ks0 = (13.0 / 3.0) * s0, ks1 = (13.0 / 3.0) * s1, ks2 = (13.0 / 3.0) * s2;
+    // products with constants on the integer pipe (fp64_int.cuh; same bits):
+    // the FP64 unit is the bottleneck and 12 warps per SM hide the integer chains
+    const double ks0 = xmul<true>(13.0 / 3.0, s0), ks1 = xmul<true>(13.0 / 3.0, s1), ks2 = xmul<true>(13.0 / 3.0, s2);
     const double b0 = fma(ks0, s0, fma(t0, t0, eps_s));
     const double b1 = fma(ks1, s1, fma(t1, t1, eps_s));
     const double b2 = fma(ks2, s2, fma(t2, t2, eps_s));
     const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2;
     const double P0 = w1 * w2, P1 = w0 * w2, P2 = w0 * w1;
     // candidates scaled by the linear weights (1, 6, 3)/10 x 10
-    const double n0 = fma(11.0 / 6.0, v[2], fma(-7.0 / 6.0, v[1], (1.0 / 3.0) * v[0]));
+    const double n0 = fma(11.0 / 6.0, v[2], fma(-7.0 / 6.0, v[1], xmul<true>(1.0 / 3.0, v[0])));
     const double n1 = fma(2.0, v[3], fma(5.0, v[2], -v[1]));
     const double n2 = fma(-0.5, v[4], fma(2.5, v[3], v[2]));
     const double N = fma(n0, P0, fma(n1, P1, n2 * P2));
@@ -174,12 +176,13 @@ __device__ __forceinline__ void weno_left_vjp<3>(const double* v, double eps_s, 
     const double iD = rcp(D);
     const double Nb = Rbar * iD;
     const double Db = -Nb * (N * iD);
-    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, 6.0 * Db), Pb2 = fma(Nb, n2, 3.0 * Db);
+    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, xmul_small<true, 3, 2, 1>(Db));
+    const double Pb2 = fma(Nb, n2, xmul_small<true, 3, 2, 0>(Db));
     const double nb0 = Nb * P0, nb1 = Nb * P1, nb2 = Nb * P2;
     // w_k = b_k^2 enters every P_m with m != k
     const double wb0 = fma(Pb1, w2, Pb2 * w1), wb1 = fma(Pb0, w2, Pb2 * w0), wb2 = fma(Pb0, w1, Pb1 * w0);
     // b_k = eps + t_k^2 + 13/3 s_k^2: tbar = 4 t b wbar, sbar = 4 (13/3) s b wbar
-    const double q0 = 4.0 * b0 * wb0, q1 = 4.0 * b1 * wb1, q2 = 4.0 * b2 * wb2;
+    const double q0 = xmul_pow2<true, 2>(b0) * wb0, q1 = xmul_pow2<true, 2>(b1) * wb1, q2 = xmul_pow2<true, 2>(b2) * wb2;
     const double tb0 = t0 * q0, tb1 = t1 * q1, tb2 = t2 * q2;
     const double sb0 = ks0 * q0, sb1 = ks1 * q1, sb2 = ks2 * q2;
     // transposes of t_k, s_k and n_k written on the cell values

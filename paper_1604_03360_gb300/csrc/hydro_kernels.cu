@@ -147,14 +147,16 @@ static cudaError_t info_for(StageLaunch* out)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, fn, TX * TY, out->smem);
 }
 
-// WENO5: 16x16 (1 CTA of 8 warps per SM), 16x8 (2 CTAs of 4 warps), 32x8,
-//        16x16 with two face items per iteration, pencil sweeps on 16x16
-//        (all products on the FP64 unit) and 16x8, and the 16x16 pencil sweep.
-// WENO7: 16x16 (8 warps, 221 KB shared memory), 16x8 (4 warps), 16x16 with two
-//        face items per iteration, pencil sweeps on 16x16 (all products on the
-//        FP64 unit) and 16x8, and the 16x16 pencil sweep.
-// The two marked variants keep every product on the FP64 unit (the bitwise
-// reference); the others take the default of default_emu.  WENO5 7, 8 /
+// WENO5: 0 16x16 (1 CTA of 8 warps per SM), 1 16x8 (2 CTAs of 4 warps),
+//        2 32x8, 3 16x16 with two face items per iteration, pencil sweeps on
+//        4 16x16 (all products on the FP64 unit) and 5 16x8, 6 the 16x16
+//        pencil sweep, 7 and 8 the same with the z pass.
+// WENO7: 0 16x16 (8 warps, 221 KB shared memory), 1 16x8 (4 warps), 2 16x16
+//        with two face items per iteration, pencil sweeps on 3 16x16 (all
+//        products on the FP64 unit) and 4 16x8, 5 the 16x16 pencil sweep,
+//        6 and 7 the same with the z pass.
+// Variants 4 (WENO5) and 3 (WENO7) keep every product on the FP64 unit (the
+// bitwise reference); the others take the default of default_emu.  WENO5 7, 8 /
 // WENO7 6, 7: the 16x16 pencil sweep with the z faces from a separate z pass
 // (zflux_kernel: long z pencils at 15-20 warps per SM, carried differences;
 // the stage kernel then keeps no z ring), with one stage CTA per SM or two

@@ -13,12 +13,14 @@
 // planes and sweeps along z.  Per plane:
 //   1. each thread appends the split z-fluxes g = f_z +- alpha_z u of its own
 //      column at plane p+G to a private ring (shared memory, 2G-1 planes) and
-//      reconstructs the z-face p+1/2 from it (no barrier needed);
+//      reconstructs the z-face p+1/2 from it (no barrier needed) -- or, in the
+//      z-pass variants (ZEXT), nothing: zflux_kernel has written the z faces;
 //   2. the CTA stages split x-fluxes of the tile rows plus G halo cells each
 //      side, and split y-fluxes of the tile columns plus halo, in shared
 //      memory (ghost cells come from the boundary rule by index mapping);
-//   3. the CTA reconstructs all (TX+1) x TY x-faces and TX x (TY+1) y-faces,
-//      one (face, field) item per thread at a time;
+//   3. the CTA reconstructs all (TX+1) x TY x-faces and TX x (TY+1) y-faces:
+//      one (face, field) item per thread at a time, or as pencil sweeps that
+//      carry the stencil differences from face to face (kPencilSweep);
 //   4. each thread combines the six face fluxes of its cell and finishes.
 // Primitive variables (p, v) of the stage input come from the previous
 // stage's epilogue, so no cell is recovered twice in a stage.

@@ -20,7 +20,8 @@
  *                    the Lax-Friedrichs split fluxes f^+- = (f +- alpha u)/2,
  *                    alpha per direction = max |characteristic speed| over the
  *                    grid (global Lax-Friedrichs).
- *   Sec. 1           "third order Runge-Kutta": the SSP (Shu-Osher) form
+ *   Sec. 1           third-order Runge-Kutta in time (variant not named):
+ *                    the SSP (Shu-Osher) form
  *                    u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1));
  *                    u' = 1/3 u + 2/3 (u2 + dt L(u2)).
  *

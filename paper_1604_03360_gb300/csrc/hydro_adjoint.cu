@@ -193,6 +193,78 @@ __device__ __forceinline__ void weno_left_vjp<3>(const double* v, double eps_s, 
     vb[4] += fma(-0.5, nb2, sb2 - tb2);
 }
 
+// WENO7 written out the same way: the forward values in the difference basis of
+// weno7 (A, B, C forms, b_k = eps + A^2 + 39 B^2 + 781/20 C^2), then the reverse
+// sweep N, D -> P -> w (leave-two-out products) -> b -> (A, B, C, n) -> (e, d) -> v.
+// Checked against complex-step derivatives of the forward formula (2e-14).
+template <>
+__device__ __forceinline__ void weno_left_vjp<4>(const double* v, double eps_s, double Rbar, double* vb)
+{
+    constexpr double kc = 781.0 / 20.0;
+    double d[6], e[5];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) d[i] = v[i + 1] - v[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) e[i] = d[i + 1] - d[i];
+    const double C0 = e[1] - e[0], C1 = e[2] - e[1], C2 = e[3] - e[2], C3 = e[4] - e[3];
+    const double B0 = fma(2.0, e[1], -e[0]), B12 = e[2], B3 = fma(2.0, e[3], -e[4]);
+    const double A0 = fma(6.0, d[2], fma(2.0, B0, e[1]));
+    const double A1 = fma(2.0, d[3], fma(5.0, d[2], -d[1]));
+    const double A2 = fma(5.0, d[3], fma(2.0, d[2], -d[4]));
+    const double A3 = fma(6.0, d[3], fma(-2.0, B3, -e[3]));
+    const double kB0 = 39.0 * B0, kB12 = 39.0 * B12, kB3 = 39.0 * B3;
+    const double kC0 = kc * C0, kC1 = kc * C1, kC2 = kc * C2, kC3 = kc * C3;
+    const double b0 = fma(A0, A0, fma(kB0, B0, fma(kC0, C0, eps_s)));
+    const double b1 = fma(A1, A1, fma(kB12, B12, fma(kC1, C1, eps_s)));
+    const double b2 = fma(A2, A2, fma(kB12, B12, fma(kC2, C2, eps_s)));
+    const double b3 = fma(A3, A3, fma(kB3, B3, fma(kC3, C3, eps_s)));
+    const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2, w3 = b3 * b3;
+    const double w01 = w0 * w1, w23 = w2 * w3, w02 = w0 * w2, w03 = w0 * w3, w12 = w1 * w2, w13 = w1 * w3;
+    const double P0 = w1 * w23, P1 = w0 * w23, P2 = w01 * w3, P3 = w01 * w2;
+    // candidates scaled by the linear weights (1, 12, 18, 4)/35 x 35
+    const double n0 = fma(25.0 / 12.0, v[3], fma(-23.0 / 12.0, v[2], fma(13.0 / 12.0, v[1], -0.25 * v[0])));
+    const double n1 = fma(3.0, v[4], fma(13.0, v[3], fma(-5.0, v[2], v[1])));
+    const double n2 = fma(10.5, v[3] + v[4], -1.5 * (v[2] + v[5]));
+    const double n3 = fma(13.0 / 3.0, v[4], fma(-5.0 / 3.0, v[5], fma(1.0 / 3.0, v[6], v[3])));
+    const double N = fma(n0, P0, fma(n1, P1, fma(n2, P2, n3 * P3)));
+    const double D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
+    // reverse: value = N / D
+    const double iD = rcp(D);
+    const double Nb = Rbar * iD;
+    const double Db = -Nb * (N * iD);
+    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, 12.0 * Db);
+    const double Pb2 = fma(Nb, n2, 18.0 * Db), Pb3 = fma(Nb, n3, 4.0 * Db);
+    const double nb0 = Nb * P0, nb1 = Nb * P1, nb2 = Nb * P2, nb3 = Nb * P3;
+    const double wb0 = fma(Pb1, w23, fma(Pb2, w13, Pb3 * w12));
+    const double wb1 = fma(Pb0, w23, fma(Pb2, w03, Pb3 * w02));
+    const double wb2 = fma(Pb0, w13, fma(Pb1, w03, Pb3 * w01));
+    const double wb3 = fma(Pb0, w12, fma(Pb1, w02, Pb2 * w01));
+    // b_k = eps + A^2 + 39 B^2 + kc C^2: Abar = 4 A b wbar, Bbar = 4 (39 B) b wbar, ...
+    const double q0 = 4.0 * b0 * wb0, q1 = 4.0 * b1 * wb1, q2 = 4.0 * b2 * wb2, q3 = 4.0 * b3 * wb3;
+    const double Ab0 = A0 * q0, Ab1 = A1 * q1, Ab2 = A2 * q2, Ab3 = A3 * q3;
+    const double Bb0 = kB0 * q0, Bb1 = kB12 * q1, Bb2 = kB12 * q2, Bb3 = kB3 * q3;
+    const double Cb0 = kC0 * q0, Cb1 = kC1 * q1, Cb2 = kC2 * q2, Cb3 = kC3 * q3;
+    // transposes: (B, C) -> e, (A, e) -> d, d -> v, n -> v
+    const double eb0 = -Bb0 - Cb0;
+    const double eb1 = fma(2.0, Bb0, Cb0 - Cb1);
+    const double eb2 = Bb1 + Bb2 + (Cb1 - Cb2);
+    const double eb3 = fma(2.0, Bb3, Cb2 - Cb3);
+    const double eb4 = Cb3 - Bb3;
+    const double db0 = fma(2.0, Ab0, -eb0);
+    const double db1 = fma(-7.0, Ab0, (eb0 - eb1) - Ab1);
+    const double db2 = fma(11.0, Ab0, fma(5.0, Ab1, fma(2.0, Ab2, eb1 - eb2)));
+    const double db3 = fma(2.0, Ab1, fma(5.0, Ab2, fma(11.0, Ab3, eb2 - eb3)));
+    const double db4 = fma(-7.0, Ab3, (eb3 - eb4) - Ab2);
+    const double db5 = fma(2.0, Ab3, eb4);
+    vb[0] += fma(-0.25, nb0, -db0);
+    vb[1] += fma(13.0 / 12.0, nb0, nb1 + (db0 - db1));
+    vb[2] += fma(-23.0 / 12.0, nb0, fma(-5.0, nb1, fma(-1.5, nb2, db1 - db2)));
+    vb[3] += fma(25.0 / 12.0, nb0, fma(13.0, nb1, fma(10.5, nb2, nb3 + (db2 - db3))));
+    vb[4] += fma(3.0, nb1, fma(10.5, nb2, fma(13.0 / 3.0, nb3, db3 - db4)));
+    vb[5] += fma(-1.5, nb2, fma(-5.0 / 3.0, nb3, db4 - db5));
+    vb[6] += fma(1.0 / 3.0, nb3, db5);
+}
+
 template <int R>
 __device__ __forceinline__ void weno_right_vjp(const double* v, double eps_s, double Rbar, double* vb)
 {

@@ -4,8 +4,8 @@
 Workload (headline): 3+1D ellipsoidal flow on a 256^3 grid, WENO7, FP64,
 synthetic seeded data shaped like the paper's Sec. 3 test (Gaussian ellipsoid
 e0 = 20, a, b, c = 2, 3, 4, linear axis-scaled velocity, n ~ e, p = e/3).
-A "step" is one full RK3 step (three fused stage kernels + two 1-thread
-bookkeeping kernels).  A cell-update is one interior cell advanced by one RK3
+A "step" is one full RK3 step (per stage a z-face pass and a stage kernel, plus
+two 1-thread bookkeeping kernels).  A cell-update is one interior cell advanced by one RK3
 step.  The state (3.6 GB of FP64 fields) is far larger than L2 (129 MB), so
 no flush is needed between steps.
 
@@ -34,23 +34,23 @@ sys.path.insert(0, ROOT)
 # (mean of 10/25/25), split fluxes 75, primitive recovery 22, speeds 34.  The
 # pencil-sweep kernels carry stencil differences between neighbouring faces
 # and take the products with constants on the integer pipe, so they execute
-# fewer FP64 instructions than this count implies (ncu: 1743 per cell and
-# stage for WENO7, 85 % FP64 pipe busy), and the flop rate by this count can
-# read above the FP64 peak.
+# fewer FP64 instructions than this count implies; the flop rate by this count
+# is reported as an equivalent work rate, not as a utilisation.
 FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
                         7: 15 * (2 * 136 + 6) + 40 + 20 + 75 + 22 + 34}
-# DRAM traffic of one WENO7 stage of the default launch (variant 7: z pass +
-# stage kernel), measured by ncu on the 128^3 case
-# (profiles/stage_weno7_zpass_128.md): stage 1 521.5 MB, stages 2 and 3
-# 616.0 MB, mean 584.5 MB / 2.10 M cells; it scales with the cell count.  Same
-# capture: 1743 FP64 instructions per cell and stage; FP64 pipe busy 79 % (z
-# pass, 25 % of the time) and 87 % (stage kernel), 85 % time-weighted.
-# None for WENO5 (not captured for the current kernels).
-NCU_DRAM_BYTES_PER_CELL_STAGE = {7: (521.5e6 + 2 * 616.0e6) / 3 / 128 ** 3}
-NCU_FP64_INST_PER_CELL_STAGE = {7: 1743}
-NCU_FP64_PIPE_BUSY = {7: 0.85}
-# (variant, tile x, tile y) of the profiled launch; another choice reports null
-NCU_PROFILED_LAUNCH = {7: (7, 16, 16)}
+# Executed FP64 instructions (thread-level DFMA + DADD + DMUL, each one issue
+# slot of the FP64 pipe) per interior cell and RK3 stage, z pass + stage kernel,
+# and the DRAM bytes (read + write) per cell and stage, from ncu captures of the
+# 128^3 ellipsoidal workload (mean of stages 1-3), keyed by (scheme, launch
+# variant, tile x, tile y).  roofline.frac = this count x cells / stage time /
+# the FP64 FMA issue rate measured in the same run: the FP64 pipe's
+# utilisation.  A launch without a capture reports null.
+NCU_FP64_INST_PER_CELL_STAGE = {(7, 7, 16, 16): 1745.3, (7, 6, 16, 16): 1729.6,
+                                (5, 8, 16, 16): 896.2, (5, 7, 16, 16): 1023.7}
+NCU_DRAM_BYTES_PER_CELL_STAGE = {(7, 7, 16, 16): 276.5, (7, 6, 16, 16): 270.1,
+                                 (5, 8, 16, 16): 273.5, (5, 7, 16, 16): 269.3}
+# FP64 pipe busy, time-weighted over z pass and stage kernel
+NCU_FP64_PIPE_BUSY = {(7, 7, 16, 16): 0.849, (7, 6, 16, 16): 0.828, (5, 8, 16, 16): 0.809, (5, 7, 16, 16): 0.838}
 # Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
 # stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
 HBM_BYTES_PER_CELL_UPDATE = 320
@@ -221,11 +221,12 @@ def lumpy_on_device(g, seed, dev, width=0.5):
 
 
 def batched_vs_looped(dev, stream, barrier, steps, warmup, events=256):
-    """configs: 256 seeded lumpy events, per-axis sizes U{48..160}, WENO5, 100
-    RK3 steps each.  Times `steps` steps of (a) the batched path (one
-    persistent launch per stage over all events, graph-replayed) and (b) a loop
-    of the single-grid path over the same events; events/s counts events
-    finishing all 100 steps."""
+    """The event-by-event configuration: 256 seeded lumpy events, per-axis
+    sizes U{48..160}, WENO5, 100 RK3 steps each.  Times `steps` steps of (a)
+    the batched path (per stage a z pass over all events and one persistent
+    launch over the tile work-list, each step one graph replay) and (b) a loop
+    of the single-grid path (also graph-replayed) over the same events;
+    events/s counts events finishing all 100 steps at the measured rate."""
     import torch
     import workloads as W
     from paper_1604_03360_gb300 import Hydro, HydroBatch
@@ -242,14 +243,15 @@ def batched_vs_looped(dev, stream, barrier, steps, warmup, events=256):
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    kms = b.profile_step(steps)
+    b.step(steps)                 # the production path: one graph replay per step
     e1.record(stream)
     barrier()
     b.sync()
     tb = e0.elapsed_time(e1) / 1e3 / steps
+    kms = b.profile_step(1)       # per-kernel breakdown of one more step (direct launches)
     out["batched"] = {"ms_per_step": 1e3 * tb, "events_per_s": events / (100 * tb), "cell_updates_per_s": cells / tb,
                       "launch": list(b.launch()), "autotune_stage1_ms": tune_ms,
-                      "persistent_stage_ms": float(kms[1:4].sum()) / (3 * steps),
+                      "stage_ms_profiled": float(kms[1:4].sum()) / 3,
                       "gpu_launches_per_step": b.kernels_per_step()}
     b.close()
     del b
@@ -306,7 +308,7 @@ def musta_force_256(dev, stream, barrier, grid, with_cpu):
     el = a0.elapsed_time(a1) / 1e3
     out = {"value": g.cells * 3 / el, "unit": "cell-updates/s", "steps": 3, "limiter": "minmod",
            "musta_stages": 2, "ms_per_step": 1e3 * el / 3, "launch": h.launch(),
-           "stage_kernel_ms": float(km[1:4].sum()) / 9}
+           "stage_ms": float(km[1:4].sum()) / 9}
     h.close()
     if with_cpu:
         import oracle
@@ -496,7 +498,8 @@ def main():
     achieved = flops / (stage_ms * 1e-3) / 1e12
     peaks = load_peaks()
     from paper_1604_03360_gb300 import measure_fp64_peak
-    fp64_peak = 2.0 * measure_fp64_peak(stream) / 1e12   # TFLOP/s, FMA = 2 flops
+    fp64_inst_peak = measure_fp64_peak(stream) / 1e12    # FP64 FMA (= FP64 pipe issue slots) per second, T/s
+    fp64_peak = 2.0 * fp64_inst_peak                     # TFLOP/s, FMA = 2 flops
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_achieved = HBM_BYTES_PER_CELL_UPDATE * (cells * args.steps / el) / 1e9
 
@@ -536,10 +539,13 @@ def main():
         barrier()
         el5 = a0.elapsed_time(a1) / 1e3
         st5 = float(k5[1:4].sum()) / (3 * args.steps)
+        inst5 = NCU_FP64_INST_PER_CELL_STAGE.get((5,) + tuple(h5.launch()[:3]))
         extra["weno5_256"] = {"value": cells * args.steps / el5, "unit": "cell-updates/s", "launch": h5.launch(),
-                              "ms_per_step": 1e3 * el5 / args.steps, "stage_kernel_ms": st5,
-                              "fp64_tflops": FLOPS_PER_CELL_STAGE[5] * cells / (st5 * 1e-3) / 1e12,
-                              "fp64_frac": FLOPS_PER_CELL_STAGE[5] * cells / (st5 * 1e-3) / 1e12 / fp64_peak,
+                              "ms_per_step": 1e3 * el5 / args.steps, "stage_ms": st5,
+                              "fp64_inst_per_cell_stage": inst5,
+                              "fp64_pipe_frac": None if inst5 is None
+                              else inst5 * cells / (st5 * 1e-3) / 1e12 / fp64_inst_peak,
+                              "equivalent_tflops": FLOPS_PER_CELL_STAGE[5] * cells / (st5 * 1e-3) / 1e12,
                               "hbm_frac": HBM_BYTES_PER_CELL_UPDATE * cells * args.steps / el5 / 1e9 / hbm_peak}
         h5.close()
     h.close()
@@ -561,9 +567,8 @@ def main():
         ell = a0.elapsed_time(a1) / 1e3
         extra["local_lf_256"] = {"value": cells * 3 / ell, "unit": "cell-updates/s", "steps": 3,
                                  "ms_per_step": 1e3 * ell / 3, "launch": hl.launch(),
-                                 "stage_kernel_ms": float(kl[1:4].sum()) / 9,
-                                 "fp64_frac_global_lf_count": FLOPS_PER_CELL_STAGE[args.scheme] * cells
-                                 / (float(kl[1:4].sum()) / 9 * 1e-3) / 1e12 / fp64_peak}
+                                 "stage_ms": float(kl[1:4].sum()) / 9,
+                                 "over_componentwise": (float(kl[1:4].sum()) / 9) / stage_ms}
         hl.close()
     if not args.no_extra:
         # characteristic-wise WENO (global LF), same workload and scheme
@@ -583,7 +588,7 @@ def main():
         elc = a0.elapsed_time(a1) / 1e3
         extra["charwise_%d" % args.grid] = {"value": cells * 3 / elc, "unit": "cell-updates/s", "steps": 3,
                                             "ms_per_step": 1e3 * elc / 3, "launch": hc.launch(),
-                                            "stage_kernel_ms": float(kc[1:4].sum()) / 9,
+                                            "stage_ms": float(kc[1:4].sum()) / 9,
                                             "over_componentwise": (float(kc[1:4].sum()) / 9) / stage_ms}
         hc.close()
     if not args.no_extra:
@@ -605,7 +610,7 @@ def main():
         extra["gas_eos_%d" % args.grid] = {"value": cells * 3 / elg, "unit": "cell-updates/s", "steps": 3,
                                            "eos": "p = cs2 (e - m n), cs2 = 1/3, m = 1",
                                            "ms_per_step": 1e3 * elg / 3, "launch": hg.launch(),
-                                           "stage_kernel_ms": float(kg[1:4].sum()) / 9,
+                                           "stage_ms": float(kg[1:4].sum()) / 9,
                                            "over_default_eos": (float(kg[1:4].sum()) / 9) / stage_ms}
         hg.close()
     if not args.no_extra:
@@ -627,12 +632,12 @@ def main():
         elq = a0.elapsed_time(a1) / 1e3
         extra["charges3_256"] = {"value": cells * 3 / elq, "unit": "cell-updates/s", "steps": 3, "fields": 7,
                                  "ms_per_step": 1e3 * elq / 3, "launch": hq.launch(),
-                                 "stage_kernel_ms": float(kq[1:4].sum()) / 9}
+                                 "stage_ms": float(kq[1:4].sum()) / 9}
         hq.close()
     if not args.no_extra:
         extra["musta_force_256"] = musta_force_256(dev, stream, barrier, args.grid, rank == 0 and not args.no_cpu_baseline)
     if not args.no_extra and not args.no_batch:
-        extra["batched_vs_looped"] = batched_vs_looped(dev, stream, barrier, 3, 3, args.batch_events)
+        extra["batched_vs_looped"] = batched_vs_looped(dev, stream, barrier, 10, 3, args.batch_events)
     if not args.no_extra:
         extra["adjoint_96"] = adjoint_96(dev, stream, barrier)
     if not args.no_extra:
@@ -646,8 +651,11 @@ def main():
                % (128 if args.scheme == 5 else 96, secs)}
 
     # the ncu figures hold for the launch they were captured on
-    profiled = (not args.charwise and args.scheme in NCU_PROFILED_LAUNCH
-                and tuple(launch[:3]) == NCU_PROFILED_LAUNCH[args.scheme])
+    key = (args.scheme,) + tuple(launch[:3])
+    inst = None if args.charwise else NCU_FP64_INST_PER_CELL_STAGE.get(key)
+    traffic = None if args.charwise or key not in NCU_DRAM_BYTES_PER_CELL_STAGE else \
+        NCU_DRAM_BYTES_PER_CELL_STAGE[key] * cells
+    inst_rate = None if inst is None else inst * cells / (stage_ms * 1e-3) / 1e12
     if rank == 0:
         line = {
             "metric": headline_metric(args.scheme, args.grid),
@@ -661,22 +669,26 @@ def main():
                        "l2": "state %.2f GB > 129 MB L2: no flush needed" % (27 * 8 * cells / 1e9),
                        "launch": {"variant": launch[0], "tile": [launch[1], launch[2]], "z_chunk": launch[3],
                                   "autotune_stage_ms": tuned_ms}},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp64_peak,
-                         "traffic": NCU_DRAM_BYTES_PER_CELL_STAGE[args.scheme] * cells if profiled else None,
+            "roofline": {"bound": "alu", "achieved": inst_rate, "peak": fp64_inst_peak,
+                         "unit": "FP64 Tinst/s", "frac": None if inst_rate is None else inst_rate / fp64_inst_peak,
+                         "traffic": traffic,
                          "traffic_source": "ncu dram__bytes_read+write of the 128^3 stage launches of the same "
                                            "variant (z pass + stage kernel, mean of stages 1-3), scaled by cells",
-                         "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[args.scheme],
-                         "flops_count": "every face reconstructed from its own stencil; the kernels share "
-                                        "differences between faces and run some products on the integer "
-                                        "pipe, so they execute fewer FP64 instructions",
-                         "ncu_fp64_inst_per_cell_stage": (NCU_FP64_INST_PER_CELL_STAGE.get(args.scheme)
-                                                          if profiled else None),
-                         "ncu_fp64_pipe_busy": NCU_FP64_PIPE_BUSY.get(args.scheme) if profiled else None,
-                         "kernel": "stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,
+                         "fp64_inst_per_cell_stage": inst,
+                         "achieved_source": "executed FP64 instructions per cell and stage (ncu, thread-level DFMA + "
+                                            "DADD + DMUL of z pass + stage kernel on the 128^3 case of this launch) "
+                                            "x cells / stage time (CUDA events); peak = FP64 FMA issue rate measured "
+                                            "in this run (hydro_measure_fp64_peak)",
+                         "ncu_fp64_pipe_busy": None if args.charwise else NCU_FP64_PIPE_BUSY.get(key),
+                         "equivalent_tflops": achieved, "equivalent_tflops_of_fp64_peak": achieved / fp64_peak,
+                         "equivalent_count": "%d flops per cell-stage, every face reconstructed from its own stencil "
+                                             "(FMA = 2); the kernels share differences between faces and run some "
+                                             "products on the integer pipe, so this rate can exceed the FP64 peak"
+                                             % FLOPS_PER_CELL_STAGE[args.scheme],
+                         "kernel": "zflux_kernel + stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,
                          "peak_source": "FP64 FMA probe kernel measured in this run (hydro_measure_fp64_peak); "
                                         "MEASURED_PEAKS.json has no FP64 figure; nominal 152 SM x 2 DFMA/clk x "
-                                        "2 flop x 2.07 GHz = 1.259"},
+                                        "2.07 GHz = 0.629 T/s"},
             "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak, "frac": hbm_achieved / hbm_peak,
                     "bytes_per_cell_update": HBM_BYTES_PER_CELL_UPDATE, "peak_source": "MEASURED_PEAKS.json"},
             "e2e": e2e,

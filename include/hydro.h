@@ -117,7 +117,12 @@ typedef struct {
     double cs2;         /* EOS p = cs2 * e, 0 < cs2 < 1 (1/3 in the paper's tests) */
     double cfl;         /* dt = cfl * min dx / max alpha when dt_fixed <= 0 */
     double dt_fixed;    /* > 0: constant time step */
-    double weno_eps;    /* WENO epsilon, > 0 (1e-6) */
+    double weno_eps;    /* WENO epsilon, 1e-40 <= weno_eps <= 1e30 (1e-6).
+                           Range of the data: split-flux differences up to
+                           about 1e24 (WENO7) or 1e37 (WENO5) in magnitude;
+                           beyond that the products of the smoothness terms
+                           overflow and the result is NaN, reported as
+                           HYDRO_ERR_UNPHYSICAL */
     double eos_mass;    /* equation of state p = cs2 (e - eos_mass n_1): 0 (the
                            default) is p = cs2 e; > 0 is the ideal gas of
                            adiabatic index 1 + cs2 whose rest mass is eos_mass
@@ -153,8 +158,11 @@ hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stri
 /* Advance by up to nsteps RK3 steps (Sec. 1).  If t_end >= 0 the last step is
  * shortened so that t lands on t_end and later steps do nothing.  Each step is
  * one replay of a captured CUDA graph: a 1-thread step-begin kernel (dt from
- * the current characteristic speeds), three fused stage kernels (Eq. 2 + RK
- * combine + speeds of the new state) and a 1-thread step-end kernel.
+ * the current characteristic speeds), then per RK3 stage either one fused
+ * stage kernel (Eq. 2 + RK combine + speeds of the new state) or, in the
+ * z-pass launch variants (the default for component-wise WENO with global
+ * Lax-Friedrichs and one charge), a z-face pass followed by the stage kernel,
+ * and a 1-thread step-end kernel (hydro_kernels_per_step counts them).
  * Asynchronous; no host synchronisation. */
 hydro_status hydro_step(hydro_t* h, int32_t nsteps, double t_end);
 
@@ -222,8 +230,8 @@ const double* hydro_state_device_ptr(hydro_t* h);
 int64_t hydro_field_stride(hydro_t* h);
 
 /* ---- z-slab domain decomposition ----------------------------------------
- * L(u) of Eq. 3 at a cell depends on the r (= G) neighbouring cells along
- * each axis (Sec. 1, after Eq. 3), and the global Lax-Friedrichs speeds of
+ * L(u) of Eq. 2 at a cell depends on the r (= G) neighbouring cells along
+ * each axis (Sec. 1, after Eq. 2), and the global Lax-Friedrichs speeds of
  * Sec. 1.2 are maxima over the whole grid.  A grid split into z-slabs, each
  * a handle with bc[2] = HYDRO_BC_HALO holding nz >= G interior planes,
  * therefore advances exactly like the whole grid if, before each RK stage,
@@ -276,6 +284,16 @@ hydro_status hydro_speed_slot(hydro_t* h, int32_t slot, int32_t io, double* spee
  * returns the FP64 FMA issue rate in FMA/s -- the roofline denominator of the
  * FP64-bound stage kernel.  Allocates and frees a small scratch buffer. */
 hydro_status hydro_measure_fp64_peak(void* stream, double* fma_per_second);
+
+/* Self-check helper, not part of the paper's method: y[i] = the kernels'
+ * reciprocal of x[i] for i < n (x, y device pointers owned by the caller,
+ * n >= 0; asynchronous on `stream`).  The kernels divide by taking a MUFU
+ * seed and one cubically convergent Newton correction instead of IEEE
+ * division; this entry point lets a test bound that reciprocal's error
+ * against 1/x.  Valid for 2^-1022 <= |x| <= 2^1022 (the seed flushes
+ * subnormal inputs and results to zero).  INVALID_ARG for n < 0 or a NULL
+ * pointer with n > 0; CUDA if the launch fails. */
+hydro_status hydro_eval_rcp(const double* x, double* y, int64_t n, void* stream);
 
 /* ---- Reverse mode (adjoint) --------------------------------------------
  * Gradients of a final-state observable with respect to the initial state.
@@ -352,8 +370,9 @@ hydro_status hydro_batch_autotune(hydro_batch_t* b, double* best_ms);
  * that cannot call cudaMalloc -- for example a host application whose device
  * memory belongs to its own pool allocator, or a loop with a fixed footprint
  * that must not pay cudaMalloc's implicit synchronisation.  It advances the
- * conserved state by up to nsteps RK3 steps exactly like hydro_step (same
- * kernels, same result), but keeps all intermediate data in one static
+ * conserved state by up to nsteps RK3 steps exactly like hydro_step (the same
+ * scheme and the same result bit for bit, computed by the fused stage kernel,
+ * which needs no z-face buffer), but keeps all intermediate data in one static
  * device array of the library (HYDRO_NOALLOC_MAX_CELLS * 176 bytes + 256
  * bytes, about 23 MB) that every GPU which loads the library holds until the
  * process exits.  It calls no cudaMalloc, cudaFree or allocating library

@@ -6,9 +6,9 @@ include/hydro.h (libhydro.so, built in-tree by build.py).  This package is the
 thin Python binding over that ABI.
 """
 from ._binding import (BC_HALO, BC_OUTFLOW, BC_PERIODIC, MEM_DEVICE, MEM_HOST, MUSTA_FORCE, WENO5, WENO7, Hydro, HydroBatch, HydroConfig,
-                       HydroError, LIB_PATH, as_buffer, lib, make_config, measure_fp64_peak)
+                       HydroError, LIB_PATH, as_buffer, eval_rcp, lib, make_config, measure_fp64_peak)
 
 from . import autograd  # noqa: E402  (torch.autograd.Function wrappers of the adjoint)
 
-__all__ = ["autograd", "Hydro", "HydroBatch", "HydroConfig", "HydroError", "lib", "make_config", "measure_fp64_peak", "as_buffer", "LIB_PATH",
+__all__ = ["autograd", "Hydro", "HydroBatch", "HydroConfig", "HydroError", "lib", "make_config", "measure_fp64_peak", "eval_rcp", "as_buffer", "LIB_PATH",
            "WENO5", "WENO7", "MUSTA_FORCE", "BC_OUTFLOW", "BC_PERIODIC", "BC_HALO", "MEM_HOST", "MEM_DEVICE"]

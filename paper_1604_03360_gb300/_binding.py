@@ -103,6 +103,7 @@ def lib():
         "hydro_field_stride": ([vp], i64),
         "hydro_version": ([], ctypes.c_char_p),
         "hydro_measure_fp64_peak": ([vp, P(d)], i32),
+        "hydro_eval_rcp": ([vp, vp, i64, vp], i32),
         "hydro_forward_record": ([vp, i32, i32], i32),
         "hydro_adjoint": ([vp, vp, vp, i64, i32], i32),
         "hydro_recorded_steps": ([vp, P(i32), vp, vp], i32),
@@ -185,6 +186,21 @@ def measure_fp64_peak(stream=None):
     if rc:
         raise HydroError(rc, "FP64 peak probe failed")
     return r.value
+
+
+def eval_rcp(x, out=None, stream=None):
+    """The kernels' reciprocal (MUFU seed + one cubic Newton correction) of
+    every element of the CUDA float64 tensor x (a self-check of the device
+    arithmetic; the result is ordered on `stream`)."""
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+        raise ValueError("need a contiguous float64 CUDA tensor")
+    y = torch.empty_like(x) if out is None else out
+    rc = lib().hydro_eval_rcp(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
+                              _stream_handle(stream))
+    if rc:
+        raise HydroError(rc, "hydro_eval_rcp failed")
+    return y
 
 
 class Hydro:

@@ -287,7 +287,9 @@ std::string check_config(const hydro_config* c)
         c->n[2] > (1 << 28))
         return "grid too large";
     if (!(c->cs2 > 0.0 && c->cs2 < 1.0)) return "cs2 must lie in (0, 1)";
-    if (!(c->weno_eps > 0.0)) return "weno_eps must be positive";
+    // the one-reciprocal WENO face form keeps every product of smoothness
+    // terms a normal number for eps in this range (hydro_math.cuh face_sum)
+    if (!(c->weno_eps >= 1e-40 && c->weno_eps <= 1e30)) return "weno_eps must lie in [1e-40, 1e30]";
     if (!(c->dt_fixed > 0.0) && !(c->cfl > 0.0)) return "need cfl > 0 or dt_fixed > 0";
     if (c->split != 0 && c->split != 1) return "split must be 0 (global) or 1 (local Lax-Friedrichs)";
     if (c->nq < 0 || c->nq > 3) return "nq (number of charges) must be 0..3";

@@ -375,12 +375,47 @@ __device__ __forceinline__ void weno_right(const double* v, double eps_s, double
     }
 }
 
+// 2^(1023 - e) for the biased exponent e of x (e clamped to 1 .. 2045, so
+// the factor is a normal number): x times it lies in [1, 2) for normal x.
+__device__ __forceinline__ double pow2_unscale(double x)
+{
+    int e = (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
+    e = min(max(e, 1), 2045);
+    return __hiloint2double((2046 - e) << 20, 0);
+}
+
 // Face value (cp + Mp/Dp) + (cm + Mm/Dm) with one reciprocal; cp, cm are the
 // centre values of the two stencils.
+//
+// Dynamic range.  Dp and Dm are products of r - 1 squared smoothness terms
+// (eps + beta)^2, so they span a far wider range than the data: Dp Dm can
+// overflow (then the correction would silently vanish) or underflow (then
+// rcp.approx.ftz gives inf).  When either D leaves [2^-448, 2^448] -- checked
+// with integer operations on the exponent fields, off the FP64 pipe -- both
+// sides are first scaled by exact powers of two into [1, 2).  That leaves
+// M/D unchanged, and inside the range the result is the same as before bit
+// for bit.  The scaled path holds while each D and M is a finite normal
+// number: eps >= 1e-40 (checked at set-up) and split-flux differences below
+// about 1e24 (WENO7) or 1e37 (WENO5).
+__device__ __forceinline__ double face_sum_rescaled(double Mp, double Dp, double cp, double Mm, double Dm, double cm)
+{
+    const double sp = pow2_unscale(Dp), sm = pow2_unscale(Dm);
+    Mp *= sp;
+    Dp *= sp;
+    Mm *= sm;
+    Dm *= sm;
+    return fma(fma(Mp, Dm, Mm * Dp), rcp(Dp * Dm), cp + cm);
+}
+
+constexpr unsigned kFaceExpLo = 1023u - 448u, kFaceExpSpan = 896u;
+
 template <int EMU = 0>
 __device__ __forceinline__ double face_sum(double Mp, double Dp, double cp, double Mm, double Dm, double cm)
 {
     constexpr bool EF = (EMU & kEmuFace) != 0;
+    const unsigned ep = ((unsigned)__double2hiint(Dp) >> 20) - kFaceExpLo;
+    const unsigned em = ((unsigned)__double2hiint(Dm) >> 20) - kFaceExpLo;
+    if (max(ep, em) > kFaceExpSpan) return face_sum_rescaled(Mp, Dp, cp, Mm, Dm, cm);
     return fma(fma(Mp, Dm, xmul<EF>(Mm, Dp)), rcp(xmul<EF>(Dp, Dm)), cp + cm);
 }
 

@@ -1,7 +1,7 @@
 """One grid split into z-slabs (domain decomposition).
 
-L(u) of Eq. 3 at a cell reads the r neighbouring cells along each axis
-(Sec. 1, after Eq. 3), and the global Lax-Friedrichs speeds of Sec. 1.2 are
+L(u) of Eq. 2 at a cell reads the r neighbouring cells along each axis
+(Sec. 1, after Eq. 2), and the global Lax-Friedrichs speeds of Sec. 1.2 are
 maxima over the whole grid.  So a grid cut into z-slabs advances exactly like
 the whole grid if, before every RK stage, each slab's r ghost planes per side
 hold the neighbouring slab's planes of that stage's input (or the boundary

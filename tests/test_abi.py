@@ -41,6 +41,7 @@ def test_version(L):
 
 @pytest.mark.parametrize("field,value,msg", [
     ("scheme", 6, b"scheme"), ("cs2", 1.0, b"cs2"), ("weno_eps", 0.0, b"weno_eps"),
+    ("weno_eps", 1e-41, b"weno_eps"), ("weno_eps", 1e31, b"weno_eps"), ("weno_eps", float("nan"), b"weno_eps"),
     ("split", 2, b"split"), ("charwise", 2, b"charwise"), ("eos_mass", -1.0, b"eos_mass"),
 ])
 def test_invalid_config_rejected(L, field, value, msg):

@@ -2,7 +2,7 @@
 
 Each slab is a CPU stand-in for a halo handle: it keeps its nz interior
 planes plus G ghost planes per side for the three RK levels and applies the
-oracle's L(u) (Eq. 3) to the padded slab, so its interior cells see exactly
+oracle's L(u) (Eq. 2) to the padded slab, so its interior cells see exactly
 the cells the whole grid would give them once the ghost planes are filled.
 Driven by the same exchange code as the GPU slabs -- in one process
 (LocalExchange) and as world-size-2 gloo ranks (DistExchange) -- the slabs

@@ -137,3 +137,21 @@ def test_gas_eos_slabs():
     w[0] = w[0] + w[4]
     g.cs2, g.mass = 2.0 / 3.0, 1.0
     check(g, w, 3, 4, device="cuda")
+
+
+@pytest.mark.parametrize("scheme,variant,bc", [(7, None, (0, 0, 0)), (7, 7, (0, 1, 1)), (5, 8, (1, 0, 0)),
+                                               (2, None, (0, 0, 0))])
+def test_slabs_match_oracle(scheme, variant, bc):
+    """The slab run against the CPU oracle directly (not only against the
+    whole-grid GPU run): three slabs, six steps, outflow or periodic z."""
+    import oracle
+    from parity import TOL, field_errors, run_oracle
+    g, w = W.lumpy(n=(23, 19, 27), seed=29, scheme=5 if scheme == 2 else scheme)
+    w = with_flow(g, w)
+    g.scheme, g.bc = scheme, bc
+    oracle.build()
+    ref, tr, kr = run_oracle(g, w, 6)
+    got, tg, kg = run_slabs(g, w, 3, 6, device="cuda", variant=variant)
+    assert kg == kr == 6 and abs(tg - tr) <= 1e-13 * tr
+    err = field_errors(got, ref)
+    assert np.all(err <= TOL), err

@@ -3,6 +3,9 @@ memory (their device memory belongs to their own pool, or their loop must keep
 a fixed footprint).  The entry point keeps its intermediate buffers in a static
 device array of the library; here it is called through the C ABI on two
 consecutive calls and checked against hydro_step, the allocating entry point.
+Both run the same scheme with the same operations (the no-allocation path on
+the fused stage kernel, hydro_step on a z pass plus stage kernel, which agree
+bit for bit), so the results must be identical.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test."""
@@ -13,7 +16,6 @@ import pytest
 
 import oracle
 import workloads as W
-from parity import TOL, field_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -70,13 +72,13 @@ def test_noalloc_matches_hydro_step_on_two_calls(L):
     u1 = oracle.prim2con(w1)
     a1, ta1 = _noalloc(L, g1, u1, 3)
     b1, tb1 = _allocating(g1, u1, 3)
-    assert np.all(field_errors(a1, b1) <= TOL) and abs(ta1 - tb1) <= 1e-14 * tb1
+    assert np.array_equal(a1, b1) and ta1 == tb1
     # call 2: another grid and scheme, in place; the array still holds call 1's data
     g2, w2 = W.hubble(N=40, scheme=7)
     u2 = oracle.prim2con(w2)
     a2, ta2 = _noalloc(L, g2, u2, 4, in_place=True)
     b2, tb2 = _allocating(g2, u2, 4)
-    assert np.all(field_errors(a2, b2) <= TOL) and abs(ta2 - tb2) <= 1e-14 * tb2
+    assert np.array_equal(a2, b2) and ta2 == tb2
     assert np.isfinite(a2).all()
 
 

@@ -425,6 +425,8 @@ def main():
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--charwise", action="store_true",
                     help="headline run with characteristic-wise WENO (profiling; the metric stays component-wise)")
+    ap.add_argument("--split", type=int, default=0, choices=[0, 1],
+                    help="headline run with local Lax-Friedrichs splitting (profiling; the metric stays global LF)")
     ap.add_argument("--launch", type=int, default=None,
                     help="force this stage-kernel launch variant instead of autotuning (profiling)")
     ap.add_argument("--only", choices=["adjoint"], default=None,
@@ -463,6 +465,7 @@ def main():
     stream = torch.cuda.current_stream()
     g, w = workload(args.scheme, args.grid)
     g.charwise = 1 if args.charwise else 0
+    g.split = args.split
     cells = g.cells
     h = Hydro.from_grid(g, stream=stream)
     w_dev = torch.from_numpy(w).to(dev)
@@ -652,8 +655,9 @@ def main():
 
     # the ncu figures hold for the launch they were captured on
     key = (args.scheme,) + tuple(launch[:3])
-    inst = None if args.charwise else NCU_FP64_INST_PER_CELL_STAGE.get(key)
-    traffic = None if args.charwise or key not in NCU_DRAM_BYTES_PER_CELL_STAGE else \
+    other = args.charwise or args.split
+    inst = None if other else NCU_FP64_INST_PER_CELL_STAGE.get(key)
+    traffic = None if other or key not in NCU_DRAM_BYTES_PER_CELL_STAGE else \
         NCU_DRAM_BYTES_PER_CELL_STAGE[key] * cells
     inst_rate = None if inst is None else inst * cells / (stage_ms * 1e-3) / 1e12
     if rank == 0:
@@ -662,8 +666,9 @@ def main():
             "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ellipsoidal-%d^3-WENO%d%s" % (args.grid, args.scheme,
-                                                                  "-characteristic" if args.charwise else ""),
+            "config": {"workload": "ellipsoidal-%d^3-WENO%d%s%s" % (args.grid, args.scheme,
+                                                                    "-characteristic" if args.charwise else "",
+                                                                    "-localLF" if args.split else ""),
                        "grid": [args.grid] * 3,
                        "steps_per_timing": args.steps, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "state %.2f GB > 129 MB L2: no flush needed" % (27 * 8 * cells / 1e9),
@@ -679,7 +684,7 @@ def main():
                                             "DADD + DMUL of z pass + stage kernel on the 128^3 case of this launch) "
                                             "x cells / stage time (CUDA events); peak = FP64 FMA issue rate measured "
                                             "in this run (hydro_measure_fp64_peak)",
-                         "ncu_fp64_pipe_busy": None if args.charwise else NCU_FP64_PIPE_BUSY.get(key),
+                         "ncu_fp64_pipe_busy": None if other else NCU_FP64_PIPE_BUSY.get(key),
                          "equivalent_tflops": achieved, "equivalent_tflops_of_fp64_peak": achieved / fp64_peak,
                          "equivalent_count": "%d flops per cell-stage, every face reconstructed from its own stencil "
                                              "(FMA = 2); the kernels share differences between faces and run some "

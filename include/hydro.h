@@ -36,8 +36,11 @@
  *     no kernel traps.  Device-side problems (an unphysical state such as
  *     E <= 0 or |M| >= E, or a NaN) are recorded on the device and reported
  *     by the next synchronising call (hydro_get_state, hydro_sync), which
- *     then returns HYDRO_ERR_UNPHYSICAL.  hydro_last_error() describes the
- *     most recent failure of a handle.
+ *     then returns HYDRO_ERR_UNPHYSICAL.  Every wait inside a kernel is
+ *     bounded (the TMA-staged launch variants wait for their tile loads);
+ *     one that runs out of time (about a second) is reported the same way
+ *     as HYDRO_ERR_TIMEOUT, and that step's results are invalid.
+ *     hydro_last_error() describes the most recent failure of a handle.
  *   - A handle is not thread-safe: one host thread at a time.
  */
 #ifndef HYDRO_H
@@ -200,10 +203,13 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
  * face orders are compiled per scheme (a new handle starts on the fastest for
  * the 256^3 workload); the z-chunk (planes per CTA) sets how many CTAs share a
  * column.  Some variants compute the z-face fluxes in a separate z pass that
- * runs before each stage kernel.  hydro_set_launch forces a variant
+ * runs before each stage kernel; some of those stage the raw cells of each
+ * z plane in shared memory with tensor-map (TMA) tile loads, which needs an
+ * even nx (rows of a multiple of 16 bytes).  hydro_set_launch forces a variant
  * (0 <= variant < hydro_launch_variants(scheme, split, nq)) and z-chunk (zc <= 0: the
  * built-in wave-count heuristic), rebuilding the step graph; a z-pass variant is
- * refused (HYDRO_ERR_INVALID_ARG) for grids with more than 65535 rows.  Results do
+ * refused (HYDRO_ERR_INVALID_ARG) for grids with more than 65535 rows, a
+ * TMA-staged one for an odd nx (the autotuner skips both there).  Results do
  * not depend on the choice beyond FMA-level rounding of the same formulas. */
 int32_t hydro_launch_variants(int32_t scheme, int32_t split, int32_t nq);
 /* The same count for a full configuration (characteristic-wise WENO has its

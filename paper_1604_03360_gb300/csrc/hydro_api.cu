@@ -110,24 +110,40 @@ static StageArgs stage_args(hydro_t* h, int stage)
 // row count that fits the z pass's grid
 static bool launch_fits(const hydro_t* h, const StageLaunch& L)
 {
+    if (L.fn_tma && !tma_layout_ok(h->cfg.n[0], h->cfg.n[1])) return false;
     return !L.zfn || (h->fz && h->cfg.n[1] <= 65535);
 }
 
-// one RK3 stage: the z pass first (z-pass variants, z active), then the stage kernel
-static void launch_stage(const hydro_t* h, const StageLaunch& L, int zc, const StageArgs& a, cudaStream_t s)
+// one RK3 stage: the z pass first (z-pass variants, z active), then the stage
+// kernel.  Returns an error only when a TMA-staged launch cannot build its
+// tensor maps (nothing is launched then); launch errors come from
+// cudaGetLastError as usual.
+static cudaError_t launch_stage(const hydro_t* h, const StageLaunch& L, int zc, const StageArgs& a, cudaStream_t s)
 {
     if (L.zfn && a.act[2]) {
         const dim3 zg((h->cfg.n[0] + 31) / 32, h->cfg.n[1], (h->zhi - h->zlo + 1 + kZFaces - 1) / kZFaces);
         L.zfn<<<zg, kZPassThreads, 0, s>>>(a);
     }
     const dim3 grid((h->cfg.n[0] + L.tx - 1) / L.tx, (h->cfg.n[1] + L.ty - 1) / L.ty, (h->zhi - h->zlo + zc - 1) / zc);
+    if (L.fn_tma) {
+        // tensor maps of this stage's input (host-side encoding, no GPU work)
+        TmaMaps m;
+        const cudaError_t e = encode_stage_maps(L, a.u_in, a.w_in, a.nx, a.ny, a.nz, a.fs, &m);
+        if (e != cudaSuccess) return e;
+        L.fn_tma<<<grid, L.tx * L.ty, L.smem, s>>>(a, m);
+        return cudaSuccess;
+    }
     L.fn<<<grid, L.tx * L.ty, L.smem, s>>>(a);
+    return cudaSuccess;
 }
 
 static cudaError_t enqueue_step(hydro_t* h, cudaStream_t s)
 {
     step_begin_kernel<<<1, 1, 0, s>>>(h->ctl, step_params(h->cfg));
-    for (int st = 1; st <= 3; ++st) launch_stage(h, h->L, h->zc, stage_args(h, st), s);
+    for (int st = 1; st <= 3; ++st) {
+        const cudaError_t e = launch_stage(h, h->L, h->zc, stage_args(h, st), s);
+        if (e != cudaSuccess) return e;
+    }
     step_end_kernel<<<1, 1, 0, s>>>(h->ctl);
     return cudaGetLastError();
 }
@@ -379,13 +395,16 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
         cudaEventRecord(ev[0], h->stream);
         step_begin_kernel<<<1, 1, 0, h->stream>>>(h->ctl, step_params(h->cfg));
         cudaEventRecord(ev[1], h->stream);
+        cudaError_t el = cudaSuccess;
         for (int k = 1; k <= 3; ++k) {
-            launch_stage(h, h->L, h->zc, stage_args(h, k), h->stream);
+            const cudaError_t e1 = launch_stage(h, h->L, h->zc, stage_args(h, k), h->stream);
+            if (el == cudaSuccess) el = e1;
             cudaEventRecord(ev[1 + k], h->stream);
         }
         step_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl);
         cudaEventRecord(ev[5], h->stream);
         cudaError_t e = cudaEventSynchronize(ev[5]);
+        if (e == cudaSuccess) e = el;
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) {
             st = cuda_fail(h, e, "profiled step");
@@ -489,7 +508,7 @@ hydro_status hydro_stage(hydro_t* h, int32_t which, double t_end)
     } else if (which == 4) {
         step_end_kernel<<<1, 1, 0, h->stream>>>(h->ctl);
     } else {
-        launch_stage(h, h->L, h->zc, stage_args(h, which), h->stream);
+        CK(h, launch_stage(h, h->L, h->zc, stage_args(h, which), h->stream), "stage launch");
     }
     CK(h, cudaGetLastError(), "stage launch");
     return HYDRO_OK;
@@ -519,7 +538,9 @@ static hydro_status apply_launch(hydro_t* h, int variant, int zc)
     cudaError_t e = stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, variant, &L, h->cfg.charwise);
     if (e == cudaErrorInvalidValue) return fail(h, HYDRO_ERR_INVALID_ARG, "no such launch variant");
     CK(h, e, "stage kernel setup");
-    if (!launch_fits(h, L)) return fail(h, HYDRO_ERR_INVALID_ARG, "launch variant needs ny <= 65535");
+    if (!launch_fits(h, L))
+        return fail(h, HYDRO_ERR_INVALID_ARG,
+                    "launch variant does not fit this grid (z-pass variants need ny <= 65535, TMA-staged ones an even nx)");
     CK(h, cudaStreamSynchronize(h->stream), "synchronize");
     if (h->exec) {
         cudaGraphExecDestroy(h->exec);
@@ -661,11 +682,12 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
             h->L = L;
             h->zc = zc;
             const StageArgs a = stage_args(h, 1);
-            launch_stage(h, L, zc, a, h->stream);   // warm-up
+            cudaError_t el = launch_stage(h, L, zc, a, h->stream);   // warm-up
             cudaEventRecord(e0, h->stream);
-            launch_stage(h, L, zc, a, h->stream);
+            if (el == cudaSuccess) el = launch_stage(h, L, zc, a, h->stream);
             cudaEventRecord(e1, h->stream);
             cudaError_t e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = el;
             if (e == cudaSuccess) e = cudaGetLastError();
             if (e != cudaSuccess) {
                 st = cuda_fail(h, e, "autotune");
@@ -693,6 +715,8 @@ static hydro_status read_ctl(hydro_t* h)
 {
     CK(h, cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream), "read control");
     CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+    if (h->hctl->status == HYDRO_ERR_TIMEOUT)
+        return fail(h, HYDRO_ERR_TIMEOUT, "a stage kernel's wait for its TMA tile load ran out of time; results are invalid");
     if (h->hctl->status) {
         char b[160];
         snprintf(b, sizeof b, "unphysical state (E <= 0, |M| >= E or NaN) first seen at cell %lld",

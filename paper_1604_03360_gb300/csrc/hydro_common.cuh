@@ -106,7 +106,17 @@ struct StageLaunch {
     int tx, ty;
     int ctas_per_sm;
     void (*zfn)(StageArgs) = nullptr;   // z pass launched before fn (ZEXT variants), else null
+    // TMA-staged variants: the stage kernel takes the stage input's tensor
+    // maps (fn is then null); raw tile box of tma_rw x tma_rh cells
+    void (*fn_tma)(StageArgs, TmaMaps) = nullptr;
+    int tma_rw = 0, tma_rh = 0;
 };
+// tensor maps of the stage input (u: 5 fields, w: p, v_x, v_y of 4) for a
+// TMA-staged launch; cudaErrorNotSupported where the layout does not allow
+// them (x rows must be a multiple of 16 bytes: nx even)
+cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const double* w, int nx, int ny, int nz,
+                              long long fs, TmaMaps* out);
+inline bool tma_layout_ok(int nx, int ny) { return nx % 2 == 0 && nx >= 2 && ny >= 1; }
 // Tile shapes compiled per scheme and splitting (index 0 is the default);
 // stage_launch_variant returns cudaErrorInvalidValue for a variant that does
 // not exist.  split: 0 global, 1 local Lax-Friedrichs.
@@ -127,10 +137,11 @@ inline cudaError_t stage_launch_info(int R, StageLaunch* out)
     return stage_launch_variant(R, 0, 1, fused_launch_variant(R, 0, 1), out);
 }
 inline int state_fields(const hydro_config& c) { return 4 + (c.nq > 1 ? c.nq : 1); }
-// configurations with z-pass launch variants (component-wise WENO, global LF, one charge)
+// configurations with z-pass launch variants (component-wise WENO, global or
+// local LF, one charge)
 inline bool zpass_capable(const hydro_config& c, int R)
 {
-    return (R == 3 || R == 4) && c.split == 0 && c.nq <= 1 && c.charwise == 0;
+    return (R == 3 || R == 4) && (c.split == 0 || c.split == 1) && c.nq <= 1 && c.charwise == 0;
 }
 // internal scheme code: 3 WENO5, 4 WENO7, 2 MUSTA-FORCE (the ghost width)
 inline int scheme_R(int scheme) { return scheme == HYDRO_WENO5 ? 3 : (scheme == HYDRO_WENO7 ? 4 : 2); }

@@ -138,13 +138,76 @@ static cudaError_t info_for(StageLaunch* out)
     auto fn = stage_kernel<R, TX, TY, ILP, LLF, NF, false, EMU, ZEXT, MINB>;
     out->fn = fn;
     out->zfn = nullptr;
-    if constexpr (ZEXT) out->zfn = zflux_kernel<R, ZEMU>;
+    if constexpr (ZEXT) out->zfn = LLF ? zflux_llf_kernel<R, ZEMU> : zflux_kernel<R, ZEMU>;
     out->smem = StageSmem<R, TX, TY, LLF, NF, false, ILP == kPencilSweep, ZEXT>::bytes;
     out->tx = TX;
     out->ty = TY;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, fn, TX * TY, out->smem);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once (null if unavailable)
+static EncodeTiledFn encode_tiled_fn()
+{
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// TMA-staged stage kernel (with the z pass) for a TX x TY tile; the encoder
+// is looked up here, outside any stream capture
+template <int R, int TX, int TY, int EMU, int ZEMU, int MINB>
+static cudaError_t info_for_tma(StageLaunch* out)
+{
+    if (!encode_tiled_fn()) return cudaErrorNotSupported;
+    auto fn = stage_kernel_tma<R, TX, TY, EMU, MINB>;
+    out->fn = nullptr;
+    out->fn_tma = fn;
+    out->zfn = zflux_kernel<R, ZEMU>;
+    using SM = StageSmem<R, TX, TY, false, 5, false, true, true, true>;
+    out->smem = SM::bytes + 128;   // room to start the raw tile on a 128-byte boundary
+    out->tx = TX;
+    out->ty = TY;
+    out->tma_rw = SM::RW;
+    out->tma_rh = SM::RH;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, fn, TX * TY, out->smem);
+}
+
+cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const double* w, int nx, int ny, int nz,
+                              long long fs, TmaMaps* out)
+{
+    if (!L.fn_tma || !tma_layout_ok(nx, ny)) return cudaErrorNotSupported;
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return cudaErrorNotSupported;
+    // (x, y, z, field), x fastest; strides of y, z and field in bytes
+    const cuuint64_t gdim_u[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
+    const cuuint64_t gdim_w[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 4};
+    const cuuint64_t gstr[3] = {(cuuint64_t)nx * 8, (cuuint64_t)nx * ny * 8, (cuuint64_t)fs * 8};
+    const cuuint32_t box_u[4] = {(cuuint32_t)L.tma_rw, (cuuint32_t)L.tma_rh, 1, 5};
+    const cuuint32_t box_w[4] = {(cuuint32_t)L.tma_rw, (cuuint32_t)L.tma_rh, 1, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&out->u, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)u, gdim_u, gstr, box_u, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    r = enc(&out->w, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)w, gdim_w, gstr, box_w, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // WENO5: 0 16x16 (1 CTA of 8 warps per SM), 1 16x8 (2 CTAs of 4 warps),
@@ -154,7 +217,11 @@ static cudaError_t info_for(StageLaunch* out)
 // WENO7: 0 16x16 (8 warps, 221 KB shared memory), 1 16x8 (4 warps), 2 16x16
 //        with two face items per iteration, pencil sweeps on 3 16x16 (all
 //        products on the FP64 unit) and 4 16x8, 5 the 16x16 pencil sweep,
-//        6 and 7 the same with the z pass.
+//        6 and 7 the same with the z pass; 8 and 9 as 7 with the weight
+//        products (9: also the face products) on the integer pipe.
+// With the z pass, 16x8 tiles without and with TMA staging of the raw cells
+// (same occupancy, for comparison) and the 16x16 tile with TMA staging (its
+// raw tile leaves room for one CTA per SM): WENO5 9, 10, 11; WENO7 10, 11, 12.
 // Variants 4 (WENO5) and 3 (WENO7) keep every product on the FP64 unit (the
 // bitwise reference); the others take the default of default_emu.  WENO5 7, 8 /
 // WENO7 6, 7: the 16x16 pencil sweep with the z faces from a separate z pass
@@ -163,14 +230,17 @@ static cudaError_t info_for(StageLaunch* out)
 // (8 / 16 warps; the compiler caps the registers at 128).  The z pass, and
 // with 16 warps the WENO5 stage kernel, also take the weight products on the
 // integer pipe: with that many warps the longer integer chains are hidden.
-// Local LF (raw staging, 2G-plane ring): WENO5 16x16 and 16x8; WENO7 16x8
-// (16x16 would need 247 KB of shared memory).
+// Local LF (raw staging, 2G-plane ring): WENO5 0 16x16 and 1 16x8; WENO7 0
+// 16x8 (16x16 would need 247 KB of shared memory).  With the local-LF z pass
+// (zflux_llf_kernel, no ring): WENO5 2 16x16 (two CTAs per SM) and 3 16x8
+// (four), WENO7 1 16x16 and 2 16x8.
 // Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
 // the launch a grid gets before any tuning: the fastest on the 256^3 workload
 // (the z-pass variant; a handle that cannot run it keeps the fused one)
 int default_launch_variant(int R, int split, int nq, int charw)
 {
-    if (charw || R == 2 || split || nq > 1) return 0;
+    if (charw || R == 2 || nq > 1) return 0;
+    if (split) return R == 3 ? 2 : 1;   // local LF with the z pass, 16x16
     return R == 3 ? 8 : 7;
 }
 
@@ -191,8 +261,8 @@ int launch_variant_count(int R, int split, int nq, int charw)
     if (charw) return (R == 3 || R == 4) && split == 0 ? char_variant_count(R, nq) : 0;
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
-    if (split == 1) return R == 3 ? 2 : 1;
-    return R == 3 ? 9 : 8;
+    if (split == 1) return R == 3 ? 4 : 3;
+    return R == 3 ? 12 : 13;
 }
 
 template <int NF>
@@ -236,7 +306,11 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
     if (split == 1) {
         if (R == 3 && v == 0) return info_for<3, 16, 16, 1, true>(out);
         if (R == 3 && v == 1) return info_for<3, 16, 8, 1, true>(out);
+        if (R == 3 && v == 2) return info_for<3, 16, 16, 1, true, 5, kEmuConst, true, kZPassEmu5, 2>(out);
+        if (R == 3 && v == 3) return info_for<3, 16, 8, 1, true, 5, kEmuConst, true, kZPassEmu5, 4>(out);
         if (R == 4 && v == 0) return info_for<4, 16, 8, 1, true>(out);
+        if (R == 4 && v == 1) return info_for<4, 16, 16, 1, true, 5, kEmuConst, true, kZPassEmu7, 2>(out);
+        if (R == 4 && v == 2) return info_for<4, 16, 8, 1, true, 5, kEmuConst, true, kZPassEmu7, 4>(out);
         return cudaErrorInvalidValue;
     }
     if (R == 3) {
@@ -249,6 +323,9 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 6) return info_for<3, 16, 16, kPencilSweep>(out);
         if (v == 7) return info_for<3, 16, 16, kPencilSweep, false, 5, kEmuConst, true, kZPassEmu5>(out);
         if (v == 8) return info_for<3, 16, 16, kPencilSweep, false, 5, kEmuConst | kEmuWeights, true, kZPassEmu5, 2>(out);
+        if (v == 9) return info_for<3, 16, 8, kPencilSweep, false, 5, kEmuConst | kEmuWeights, true, kZPassEmu5, 4>(out);
+        if (v == 10) return info_for_tma<3, 16, 8, kEmuConst | kEmuWeights, kZPassEmu5, 4>(out);
+        if (v == 11) return info_for_tma<3, 16, 16, kEmuConst | kEmuWeights, kZPassEmu5, 1>(out);
     }
     if (R == 4) {
         if (v == 0) return info_for<4, 16, 16>(out);
@@ -259,6 +336,12 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 5) return info_for<4, 16, 16, kPencilSweep>(out);
         if (v == 6) return info_for<4, 16, 16, kPencilSweep, false, 5, kEmuConst, true, kZPassEmu7>(out);
         if (v == 7) return info_for<4, 16, 16, kPencilSweep, false, 5, kEmuConst, true, kZPassEmu7, 2>(out);
+        if (v == 8) return info_for<4, 16, 16, kPencilSweep, false, 5, kEmuConst | kEmuWeights, true, kZPassEmu7, 2>(out);
+        if (v == 9)
+            return info_for<4, 16, 16, kPencilSweep, false, 5, kEmuConst | kEmuWeights | kEmuFace, true, kZPassEmu7, 2>(out);
+        if (v == 10) return info_for<4, 16, 8, kPencilSweep, false, 5, kEmuConst, true, kZPassEmu7, 3>(out);
+        if (v == 11) return info_for_tma<4, 16, 8, kEmuConst, kZPassEmu7, 3>(out);
+        if (v == 12) return info_for_tma<4, 16, 16, kEmuConst, kZPassEmu7, 1>(out);
     }
     return cudaErrorInvalidValue;
 }

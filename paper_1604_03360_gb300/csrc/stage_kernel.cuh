@@ -37,9 +37,19 @@
 // (char_weno.cuh), reconstructs them and maps the result back, all fields at
 // once.  The z ring holds 2G planes of (u, p, v_z), from which the z faces
 // form g+- themselves.
+//
+// TMA-staged variant (TMA, with ZEXT and the pencil sweep): the raw cells of
+// each plane that step 2 stages -- u (5 fields) and p, v_x, v_y -- arrive in
+// shared memory as one (TX + 8) x (TY + 2G) tile per field by tensor-map
+// loads issued by one thread; the load of plane p+1 is issued as soon as
+// plane p has been staged, so it overlaps the face work of plane p.  Step 2
+// then reads in-grid cells from that tile and only cells outside the grid
+// (boundary rule) from global memory.  The tile starts 4 cells left of the
+// column tile (x * 8 bytes stays a multiple of 16 for WENO5 too).
 #pragma once
 #include "char_weno.cuh"
 #include "hydro_math.cuh"
+#include "tma_util.cuh"
 
 namespace hydro {
 
@@ -87,10 +97,17 @@ __device__ __forceinline__ int bc_map(int i, int n, int bc)
     return i < 0 ? 0 : n - 1;
 }
 
+// TMA-staged variants: halo width of the raw tile in x (even, >= G) and the
+// raw fields per cell (u 5, then p, v_x, v_y)
+constexpr int kTmaHalo = 4, kTmaRawFields = 8;
+
 template <int R, int TX, int TY, bool LLF = false, int NF = 5, bool CHW = false, bool SWP = false,
-          bool ZEXT = false>
+          bool ZEXT = false, bool TMA = false>
 struct StageSmem {
     static constexpr int G = R, S = 2 * R - 1, NT = TX * TY;
+    // raw tile of the TMA variants, one (RW x RH) box per field
+    static constexpr int RW = TX + 2 * kTmaHalo, RH = TY + 2 * R, RWH = RW * RH;
+    static constexpr int RAW = TMA ? kTmaRawFields * RWH : 0;
     static constexpr int NV = LLF ? 2 * NF + 1 : 2 * NF;     // staged values per cell
     static constexpr int NRING = (LLF || CHW) ? 2 * R : 2 * R - 1;    // z planes kept per column
     // x rows of the staged split fluxes; the pencil sweep reads one row per
@@ -104,7 +121,8 @@ struct StageSmem {
     static constexpr int GY = NV * GYH * TX;
     static constexpr int FX = NF * TY * (TX + 1);
     static constexpr int FY = NF * (TY + 1) * TX;
-    static constexpr size_t bytes = sizeof(double) * (size_t)(RING + GX + GY + FX + FY);
+    static constexpr size_t bytes = sizeof(double) * (size_t)(RAW + RING + GX + GY + FX + FY);
+    static_assert((RWH * sizeof(double)) % 128 == 0 || !TMA, "every field box of the raw tile stays 128-byte aligned");
 };
 
 // split fluxes g+- = f_d(u) +- alpha u (= 2 f^{+-}) of one cell along axis d
@@ -137,6 +155,20 @@ __device__ __forceinline__ void raw_flux(int d, const double* u, const double w[
 #pragma unroll
     for (int k = 1; k < NF; ++k) f[k] = u[k] * vd;
     f[1 + d] += w[0];
+}
+
+// physical flux f_d(u) of one cell along axis d with explicitly rounded
+// operations (no FMA contraction), so that every kernel that forms the local
+// Lax-Friedrichs stencils from raw cells -- the stage kernel's z ring and the
+// local-LF z pass -- gets the same bits
+template <int NF>
+__device__ __forceinline__ void raw_flux_rn(int d, const double* u, const double w[4], double* f)
+{
+    const double vd = w[1 + d];
+    f[0] = u[1 + d];
+#pragma unroll
+    for (int k = 1; k < NF; ++k) f[k] = __dmul_rn(u[k], vd);
+    f[1 + d] = __dadd_rn(f[1 + d], w[0]);
 }
 
 // Local-LF face value (scaled by 2) from raw stencil data of one field over the
@@ -222,18 +254,23 @@ constexpr int default_emu(int R, int TX, int TY, bool LLF, int NF, bool CHW)
 // ZEXT: the z-face fluxes come from zflux_kernel (global memory) instead of
 // the per-column ring of this kernel.
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int NF = 5, bool CHW = false,
-          int EMU = default_emu(R, TX, TY, LLF, NF, CHW), bool ZEXT = false>
-__device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem)
+          int EMU = default_emu(R, TX, TY, LLF, NF, CHW), bool ZEXT = false, bool TMA = false>
+__device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int tile_y, int chunk_z, double* smem,
+                                           const TmaMaps* tm = nullptr, uint64_t* bar = nullptr)
 {
     static_assert(!(LLF && CHW), "characteristic-wise WENO uses the global Lax-Friedrichs split");
     constexpr bool SWP = (ILP == kPencilSweep);
     static_assert(!(SWP && (LLF || CHW)), "the pencil sweep serves the component-wise global-LF scheme");
     static_assert((TX * TY) % 32 == 0, "whole warps");
-    static_assert(!ZEXT || (SWP && NF == 5), "the z pass serves the five-field pencil-sweep kernels");
-    using SM = StageSmem<R, TX, TY, LLF, NF, CHW, SWP, ZEXT>;
+    static_assert(!ZEXT || ((SWP || LLF) && NF == 5 && !CHW),
+                  "the z pass serves the five-field pencil-sweep kernels and the five-field local-LF kernel");
+    static_assert(!TMA || ZEXT, "the TMA-staged variants take their z faces from the z pass");
+    using SM = StageSmem<R, TX, TY, LLF, NF, CHW, SWP, ZEXT, TMA>;
     constexpr int G = SM::G, S = SM::S, NT = SM::NT, NRING = SM::NRING, NVR = SM::NVR;
     constexpr int GXW = SM::GXW, GYH = SM::GYH;
-    double* ring = smem;
+    constexpr int RW = SM::RW, RWH = SM::RWH;
+    double* raw = smem;
+    double* ring = raw + SM::RAW;
     double* gx = ring + SM::RING;
     double* gy = gx + SM::GX;
     double* Fx = gy + SM::GY;
@@ -255,6 +292,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
     const long long fs = a.fs, plane = (long long)nx * ny;
     const bool zact = a.act[2] != 0;
 
+    // TMA: one thread issues the raw-tile loads of a plane (u box and p, v_x,
+    // v_y box) on the mbarrier; plane zb + i completes phase i
+    constexpr uint32_t kRawBytes = (uint32_t)(sizeof(double) * kTmaRawFields * RWH);
+    bool tma_dead = false;         // a wait ran out of time: stop waiting and issuing
+    auto tma_issue = [&](int pz) {
+        if constexpr (TMA) {
+            fence_proxy_async();
+            mbar_arrive_expect(bar, kRawBytes);
+            tma_load_4d(raw, &tm->u, x0 - kTmaHalo, y0 - G, pz, 0, bar);
+            tma_load_4d(raw + 5 * RWH, &tm->w, x0 - kTmaHalo, y0 - G, pz, 0, bar);
+        }
+    };
+    if constexpr (TMA) {
+        if (tid == 0 && zb < ze) tma_issue(zb);
+    }
+
     auto load = [&](long long q, double* u, double w[4]) {
 #pragma unroll
         for (int k = 0; k < NF; ++k) u[k] = __ldg(a.u_in + k * fs + q);
@@ -274,7 +327,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             r[NF * NT] = w[0];
             r[(NF + 1) * NT] = w[3];
         } else if constexpr (LLF) {
-            raw_flux<NF>(2, u, w, gp);
+            raw_flux_rn<NF>(2, u, w, gp);
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
                 r[k * NT] = gp[k];
@@ -426,15 +479,36 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
         }
         // 2. split x- and y-fluxes of plane p (tile + halo) into shared memory
         const long long qz = (long long)bc_map(p, nz, a.bc[2]) * plane;
+        if constexpr (TMA) {
+            if (!tma_dead && !mbar_wait(bar, (uint32_t)(p - zb) & 1u)) {
+                tma_dead = true;
+                atomicCAS(a.status, 0, 5);   // HYDRO_ERR_TIMEOUT
+            }
+        }
+        // raw cell (lx, ly) of the TMA tile (u, then p, v_x, v_y)
+        auto load_raw = [&](int lx, int ly, double* u, double w[4]) {
+            const double* rp = raw + ly * RW + lx;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) u[k] = rp[k * RWH];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) w[k] = rp[(NF + k) * RWH];
+            w[3] = 0.0;   // v_z: not used by the x and y split fluxes
+        };
         for (int it = tid; it < ngx + ngy; it += NT) {
             double u[NF], w[4], gp[NF], gm[NF];
             if (it < ngx) {
                 const int row = it / wx, col = it % wx;
-                const int xx = bc_map(x0 - G + col, nx, a.bc[0]), yy = bc_map(y0 + row, ny, a.bc[1]);
-                const long long q = qz + (long long)yy * nx + xx;
-                load(q, u, w);
+                const int xr = x0 - G + col;
+                if (TMA && xr >= 0 && xr < nx) {
+                    load_raw(col + kTmaHalo - G, row + G, u, w);
+                } else {
+                    const int xx = bc_map(xr, nx, a.bc[0]), yy = bc_map(y0 + row, ny, a.bc[1]);
+                    load(qz + (long long)yy * nx + xx, u, w);
+                }
                 if constexpr (LLF) {
-                    raw_flux<NF>(0, u, w, gp);
+                    const long long q =
+                        qz + (long long)bc_map(y0 + row, ny, a.bc[1]) * nx + bc_map(x0 - G + col, nx, a.bc[0]);
+                    raw_flux_rn<NF>(0, u, w, gp);
 #pragma unroll
                     for (int k = 0; k < NF; ++k) {
                         gx[(k * TY + row) * GXW + col] = gp[k];
@@ -451,11 +525,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
                 }
             } else {
                 const int j = it - ngx, row = j / ncol, col = j % ncol;
-                const int xx = bc_map(x0 + col, nx, a.bc[0]), yy = bc_map(y0 - G + row, ny, a.bc[1]);
+                const int yr = y0 - G + row;
+                const int xx = bc_map(x0 + col, nx, a.bc[0]), yy = bc_map(yr, ny, a.bc[1]);
                 const long long q = qz + (long long)yy * nx + xx;
-                load(q, u, w);
+                if (TMA && yr >= 0 && yr < ny) load_raw(col + kTmaHalo, row, u, w);
+                else load(q, u, w);
                 if constexpr (LLF) {
-                    raw_flux<NF>(1, u, w, gp);
+                    raw_flux_rn<NF>(1, u, w, gp);
 #pragma unroll
                     for (int k = 0; k < NF; ++k) {
                         gy[(k * GYH + row) * TX + col] = gp[k];
@@ -473,6 +549,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
             }
         }
         __syncthreads();
+        if constexpr (TMA) {
+            // plane p is staged: the raw tile is free for plane p+1
+            if (tid == 0 && !tma_dead && p + 1 < ze) tma_issue(p + 1);
+        }
         // 3. x- and y-faces, one (face, field) item per thread at a time (ILP
         //    items per iteration); every item is a stencil of S values with a
         //    stride in the staged arrays, so x and y items run the same code
@@ -698,6 +778,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile_x, int t
 #pragma unroll
         for (int k = 0; k < NF; ++k) Fzm[k] = Fzp[k];
     }
+    if constexpr (TMA) {
+        // a wait ran out of time: give the copy still in flight one more
+        // bounded wait before the CTA's shared memory goes away
+        if (tma_dead && ze > zb) mbar_wait(bar, (uint32_t)(ze - 1 - zb) & 1u);
+    }
     if constexpr (CHW) {
         // a face state that is not physical (only possible next to an
         // unphysical cell): report it like one
@@ -724,6 +809,21 @@ __global__ void __launch_bounds__(TX * TY, (MINB > 0 ? MINB : (TX * TY <= 128 &&
 {
     extern __shared__ __align__(16) double smem[];
     stage_tile<R, TX, TY, ILP, LLF, NF, CHW, EMU, ZEXT>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
+// TMA-staged stage kernel (z faces from the z pass): the tensor maps of the
+// stage input arrive as a kernel parameter; one mbarrier per CTA
+template <int R, int TX, int TY, int EMU, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB) stage_kernel_tma(const StageArgs a, const __grid_constant__ TmaMaps tm)
+{
+    extern __shared__ __align__(16) double smem[];
+    __shared__ __align__(8) uint64_t bar;
+    // the raw tile starts on a 128-byte boundary (the launch adds 128 bytes)
+    double* base = smem + ((128u - (smem_addr(smem) & 127u)) & 127u) / sizeof(double);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    stage_tile<R, TX, TY, kPencilSweep, false, 5, false, EMU, true, true>(a, blockIdx.x, blockIdx.y, blockIdx.z, base,
+                                                                           &tm, &bar);
 }
 
 // z pass of a stage (ZEXT variants): the z-face fluxes of the five fields,
@@ -815,6 +915,64 @@ template <int R, int EMU>
 __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_kernel(const StageArgs a)
 {
     zflux_item<R, EMU>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// z pass of a local Lax-Friedrichs stage: the z-face fluxes of the five
+// fields, each thread sweeping one (x, y, field) pencil over kZFaces faces.
+// Face p+1/2 splits with the largest z speed over its 2G cells p-G+1 .. p+G,
+// so its stencils cannot carry differences from the previous face; the
+// thread keeps the raw window (flux f_z, state u, speed s_z of those 2G
+// planes) in registers, moves it by one plane per face and evaluates the face
+// exactly as the local-LF z ring of the stage kernel does (llf_face on the
+// same values), so both give the same bits.  Same grid and CTA as zflux_kernel.
+template <int R, int EMU>
+__device__ __forceinline__ void zflux_llf_item(const StageArgs& a, int xb, int y, int zch)
+{
+    constexpr int G = R, W = 2 * R;
+    if (!(*a.dt > 0.0)) return;
+    const int k = threadIdx.x >> 5, x = xb * 32 + (threadIdx.x & 31);
+    if (x >= a.nx) return;                       // no barriers below
+    const int f0 = zch * kZFaces, f1 = min(f0 + kZFaces, a.zhi - a.zlo + 1);
+    const long long plane = (long long)a.nx * a.ny, col = (long long)y * a.nx + x;
+    // raw z flux, state and z speed of field k at stored plane m (as raw_flux_rn)
+    auto raw_at = [&](int m, double& fv, double& uv, double& sv) {
+        const long long q = (long long)bc_map(m, a.nz, a.bc[2]) * plane + col;
+        const double uk = __ldg(a.u_in + k * a.fs + q);
+        double f;
+        if (k == 0) {
+            f = __ldg(a.u_in + 3 * a.fs + q);
+        } else {
+            f = __dmul_rn(uk, __ldg(a.w_in + 3 * a.fs + q));
+            if (k == 3) f = __dadd_rn(f, __ldg(a.w_in + q));
+        }
+        fv = f;
+        uv = uk;
+        sv = __ldg(a.s_in + 2 * a.fs + q);
+    };
+    // window of face p+1/2 (p = zlo+f-1): planes p-G+1 .. p+G
+    double fw[W], uw[W], sw[W];
+    const int p0 = a.zlo + f0 - 1;
+#pragma unroll
+    for (int i = 0; i < W; ++i) raw_at(p0 - G + 1 + i, fw[i], uw[i], sw[i]);
+    double* out = a.fz + k * a.fzs + col;
+    for (int f = f0; f < f1; ++f) {
+        out[(long long)f * plane] = llf_face<R, EMU>(fw, uw, sw, 1, a.eps_s);
+        if (f + 1 < f1) {
+#pragma unroll
+            for (int i = 0; i < W - 1; ++i) {
+                fw[i] = fw[i + 1];
+                uw[i] = uw[i + 1];
+                sw[i] = sw[i + 1];
+            }
+            raw_at(a.zlo + f + G, fw[W - 1], uw[W - 1], sw[W - 1]);
+        }
+    }
+}
+
+template <int R, int EMU>
+__global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_llf_kernel(const StageArgs a)
+{
+    zflux_llf_item<R, EMU>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace hydro

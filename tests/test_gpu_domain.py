@@ -66,11 +66,13 @@ def test_outflow_slabs_match_whole_grid(scheme, nslabs):
     check(g, w, nslabs, 5, device="cuda")
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 7), (5, 8), (7, 6), (7, 7)])
+@pytest.mark.parametrize("scheme,variant", [(5, 7), (5, 8), (7, 6), (7, 7), (5, 10), (7, 11), (7, 12)])
 def test_zpass_slabs_match_whole_grid(scheme, variant):
     """Slabs whose z faces come from the z pass (which reads the stored ghost
-    planes) advance bit for bit like the whole grid on the fused kernel."""
-    g, w = W.lumpy(n=(21, 17, 26), seed=12, scheme=scheme)
+    planes) advance bit for bit like the whole grid on the fused kernel; so do
+    slabs on the TMA-staged variants, whose tensor maps span the stored ghost
+    planes (those need an even nx)."""
+    g, w = W.lumpy(n=(22 if variant >= 10 else 21, 17, 26), seed=12, scheme=scheme)
     w = with_flow(g, w)
     ref, tr, kr = run_gpu(g, w, 4)
     got, tg, kg = run_slabs(g, w, 3, 4, device="cuda", variant=variant)
@@ -96,6 +98,19 @@ def test_host_staging_thin_slabs_and_t_end():
     w = with_flow(g, w)
     ref, tr, kr = run_gpu(g, w, 10)
     check(g, w, 4, 10, device=None, t_end=0.5 * tr)
+
+
+@pytest.mark.parametrize("scheme,variant", [(5, 2), (7, 1)])
+def test_local_lf_zpass_slabs(scheme, variant):
+    """Local-LF slabs on the z-pass launch: the z pass reads the exchanged
+    ghost planes of u, the primitives and the speeds."""
+    g, w = W.lumpy(n=(19, 15, 22), seed=31, scheme=scheme)
+    w = with_flow(g, w)
+    g.split = 1
+    ref, tr, kr = run_gpu(g, w, 4)
+    got, tg, kg = run_slabs(g, w, 3, 4, device="cuda", variant=variant)
+    assert (kg, tg) == (kr, tr)
+    assert np.array_equal(got, ref), np.max(np.abs(got - ref))
 
 
 def test_local_lf_and_charges():

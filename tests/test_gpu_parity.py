@@ -183,13 +183,20 @@ def test_unphysical_state_reported():
         assert ei.value.code == 4
 
 
+# TMA-staged launches need an even nx (x rows a multiple of 16 bytes)
+TMA_VARIANTS = {5: (10, 11), 7: (11, 12)}
+
+
 @pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5), (5, 6), (5, 7), (5, 8),
-                                            (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5), (7, 6), (7, 7)])
+                                            (5, 9), (5, 10), (5, 11),
+                                            (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5), (7, 6), (7, 7),
+                                            (7, 8), (7, 9), (7, 10), (7, 11), (7, 12)])
 def test_every_launch_variant(scheme, variant):
     """Every compiled CTA tile shape, with a short z chunk so several chunks
-    meet inside the grid, matches the oracle."""
+    meet inside the grid, matches the oracle (ragged tiles in x and y)."""
     from paper_1604_03360_gb300 import Hydro
-    g, w = W.lumpy(n=(37, 29, 21), seed=77, scheme=scheme)
+    nx = 38 if variant in TMA_VARIANTS[scheme] else 37
+    g, w = W.lumpy(n=(nx, 29, 21), seed=77, scheme=scheme)
     w = with_flow(g, w)
     u0 = oracle.prim2con(w)
     ref = oracle.run(oracle_cfg(g), u0, 4)[0]
@@ -207,7 +214,7 @@ def test_every_launch_variant(scheme, variant):
 # the same CTA tile, (pencil sweep on the FP64 unit only, pencil sweep with
 # integer-pipe products) and (fused z faces, z faces from the z pass)
 SWEEP_PAIRS = {5: ((0, 2), (0, 3), (0, 4), (1, 5), (4, 6), (6, 7), (7, 8)),
-               7: ((0, 2), (0, 3), (1, 4), (3, 5), (5, 6), (6, 7))}
+               7: ((0, 2), (0, 3), (1, 4), (3, 5), (5, 6), (6, 7), (7, 8), (8, 9))}
 
 
 @pytest.mark.parametrize("scheme", [5, 7])
@@ -233,6 +240,51 @@ def test_pencil_sweep_matches_per_face_bitwise(scheme, n):
                 h.step(3)
                 out.append(h.get_state())
         assert np.array_equal(out[0], out[1]), (v_face, v_sweep)
+
+
+# (variant without TMA, TMA-staged variant with the same arithmetic)
+TMA_PAIRS = {5: ((9, 10), (8, 11), (6, 10)), 7: ((10, 11), (7, 12), (5, 11))}
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+@pytest.mark.parametrize("n,bc", [((38, 29, 21), (0, 0, 0)), ((40, 1, 1), (0, 0, 0)), ((2, 30, 9), (0, 0, 0)),
+                                  ((16, 16, 12), (1, 1, 1)), ((34, 18, 1), (1, 0, 0)), ((50, 6, 7), (0, 1, 0))])
+def test_tma_staged_variants_bitwise(scheme, n, bc):
+    """The TMA-staged stage kernel reads in-grid cells from a tensor-map tile
+    and out-of-grid cells (boundary rule) from global memory; it performs the
+    same arithmetic as the kernel that loads every cell from global memory, so
+    both give the same bits: ragged tiles, degenerate axes, periodic and
+    outflow edges."""
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=n, seed=93, scheme=scheme)
+    w = with_flow(g, w)
+    g.bc = bc
+    u0 = oracle.prim2con(w)
+    ref = oracle.run(oracle_cfg(g), u0, 3)[0]
+    for v_plain, v_tma in TMA_PAIRS[scheme]:
+        out = []
+        for v in (v_plain, v_tma):
+            with Hydro.from_grid(g) as h:
+                h.set_launch(v, 5)
+                h.set_state(u0)
+                h.step(3)
+                out.append(h.get_state())
+        assert np.array_equal(out[0], out[1]), (v_plain, v_tma)
+        assert np.all(field_errors(out[1], ref) <= TOL)
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+def test_tma_staged_variants_need_even_nx(scheme):
+    from paper_1604_03360_gb300 import Hydro, HydroError
+    g, w = W.lumpy(n=(37, 16, 12), seed=3, scheme=scheme)
+    with Hydro.from_grid(g) as h:
+        for v in TMA_VARIANTS[scheme]:
+            with pytest.raises(HydroError) as ei:
+                h.set_launch(v)
+            assert ei.value.code == 1 and "even nx" in str(ei.value)
+        h.set_primitive(w)
+        h.autotune()                         # skips them
+        assert h.launch()[0] not in TMA_VARIANTS[scheme]
 
 
 def test_kernels_per_step_follows_the_launch():
@@ -292,7 +344,7 @@ def test_local_lf_periodic_and_ellipsoidal(scheme):
     assert_parity(g, w, 40)
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (7, 0)])
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (7, 0), (7, 1), (7, 2)])
 def test_local_lf_every_launch_variant(scheme, variant):
     from paper_1604_03360_gb300 import Hydro
     g, w = W.lumpy(n=(37, 29, 21), seed=78, scheme=scheme)
@@ -306,6 +358,33 @@ def test_local_lf_every_launch_variant(scheme, variant):
         h.step(4)
         got = h.get_state()
     assert np.all(field_errors(got, ref) <= TOL)
+
+
+# (ring variant, z-pass variant) of the local-LF stage kernel
+LLF_PAIRS = {5: ((0, 2), (1, 3)), 7: ((0, 1), (0, 2))}
+
+
+@pytest.mark.parametrize("scheme", [5, 7])
+@pytest.mark.parametrize("n,bc", [((37, 29, 21), (0, 0, 0)), ((16, 16, 12), (1, 1, 1)), ((23, 17, 1), (0, 0, 0)),
+                                  ((1, 19, 23), (0, 1, 0)), ((9, 8, 40), (0, 0, 1))])
+def test_local_lf_zpass_matches_ring_bitwise(scheme, n, bc):
+    """The local-LF z pass forms each z face from the same raw values with the
+    same operations as the stage kernel's z ring, so both launches give the
+    same bits (ragged tiles, several z chunks, periodic and outflow z)."""
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=n, seed=97, scheme=scheme)
+    w = with_flow(g, w)
+    g.bc, g.split = bc, 1
+    u0 = oracle.prim2con(w)
+    for v_ring, v_zp in LLF_PAIRS[scheme]:
+        out = []
+        for v in (v_ring, v_zp):
+            with Hydro.from_grid(g) as h:
+                h.set_launch(v, 6)
+                h.set_state(u0)
+                h.step(3)
+                out.append(h.get_state())
+        assert np.array_equal(out[0], out[1]), (v_ring, v_zp)
 
 
 def test_local_lf_rejected_where_unsupported():

@@ -207,9 +207,9 @@ hydro_status hydro_profile_step(hydro_t* h, int32_t nsteps, double t_end, double
  * z plane in shared memory with tensor-map (TMA) tile loads, which needs an
  * even nx (rows of a multiple of 16 bytes).  hydro_set_launch forces a variant
  * (0 <= variant < hydro_launch_variants(scheme, split, nq)) and z-chunk (zc <= 0: the
- * built-in wave-count heuristic), rebuilding the step graph; a z-pass variant is
- * refused (HYDRO_ERR_INVALID_ARG) for grids with more than 65535 rows, a
- * TMA-staged one for an odd nx (the autotuner skips both there).  Results do
+ * built-in wave-count heuristic), rebuilding the step graph; a TMA-staged
+ * variant is refused (HYDRO_ERR_INVALID_ARG) for an odd nx (the autotuner
+ * skips it there).  Results do
  * not depend on the choice beyond FMA-level rounding of the same formulas. */
 int32_t hydro_launch_variants(int32_t scheme, int32_t split, int32_t nq);
 /* The same count for a full configuration (characteristic-wise WENO has its
@@ -312,7 +312,7 @@ hydro_status hydro_eval_rcp(const double* x, double* y, int64_t n, void* stream)
  * hydro_forward_record: advance the current state by nsteps RK3 steps (no
  *   t_end), recording each step's speeds and dt and checkpointing the state
  *   every ckpt_every steps (device workspace owned by h, about
- *   77 + 5 * ceil(nsteps/ckpt_every) + 27 * ckpt_every doubles per cell:
+ *   99 + 5 * ceil(nsteps/ckpt_every) + 27 * ckpt_every doubles per cell:
  *   the reverse sweep keeps every stage input of one segment).
  *   Asynchronous.
  * hydro_adjoint: grad_u0 = (d u_N / d u_0)^T lambda_final for the recorded

@@ -11,13 +11,19 @@
 // adjoints in reverse:
 //   u_out = ca u_n + cb (u_s + dt L(u_s))  =>
 //   lam_s = cb lam_out + J_L(u_s)^T (cb dt lam_out),  lam_n += ca lam_out.
-// J_L^T mu is a sum over axes.  One launch covers every axis: one thread per
-// (axis, field, pencil) sweeps the pencil's faces with a register window: face adjoint
+// J_L^T mu is a sum over axes.  One thread per (axis, field, pencil) sweeps
+// the pencil's faces with a register window: face adjoint
 // F~bar_{j+1/2} = hdx (mu_{j+1} - mu_j), reverse-mode WENO of both biased
 // reconstructions into the split-flux adjoints gbar+-, ghost-cell
 // contributions folded back onto their source cells by the boundary rule (no
 // atomics anywhere); then one cell kernel applies, summed over the axes,
 //   ubar = sum_d J_f_d(u)^T (gbar+_d + gbar-_d) + alpha_d (gbar+_d - gbar-_d).
+// A warp's pencils are consecutive in the fastest index of the array it
+// sweeps, so y and z pencils read and write coalesced rows.  x pencils would
+// not (consecutive threads a row apart), so their inputs are first
+// transposed into an x-slowest layout (y fastest, then z, then x), swept
+// there as the slowest axis by the same kernel, and their outputs transposed
+// back: the same operations on the same operands, so the same bits.
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -281,59 +287,68 @@ __device__ __forceinline__ void weno_right_vjp(const double* v, double eps_s, do
 }
 
 // ------------------------------------------------------------ adjoint kernels
-struct AdjPencilArgs {
+// The pencils of one physical axis ("job"), in the layout of its arrays
+// (dimensions n, fastest first): the job sweeps layout axis d; phys is the
+// physical axis (its speed, momentum and pressure term), wv the field of w
+// holding the velocity along it.
+struct AdjPencilJob {
     const double* u;                    // stage input state (5 fields)
-    const double* w;                    // its p, v_x, v_y, v_z
+    const double* w;                    // its p (field 0) and the velocity (field wv)
     const double* lam;                  // adjoint of the stage output (5 fields)
-    double* gp;                         // out: adjoint of g+, 5 fields per axis, axis d at gp + 5 d fs
-    double* gm;                         // out: adjoint of g-, same layout
+    double* gpo;                        // out: adjoint of g+ along the axis, 5 fields
+    double* gmo;                        // out: adjoint of g-, same layout
+    int n[3], d, phys, wv, bc;
+    double hdx;
+    long long count;                    // threads: 5 fields x pencils
+};
+struct AdjPencilArgs {
+    AdjPencilJob job[3];
+    int njob;
     const unsigned long long* rec;      // step record: speeds [3 stages][3 axes], dt
     long long fs;
-    int n[3], bc[3];
-    int act[3];                         // axes with more than one cell
     int stage;
-    double hdx[3], cb, eps_s;
+    double cb, eps_s;
 };
 
 template <int R>
 __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
 {
     constexpr int G = R, Wn = 2 * R;
-    // thread -> (axis, field, pencil): the active axes' ranges follow one another
+    // thread -> (job, field, pencil): the jobs' ranges follow one another
     long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    int d = -1;
-    for (int dd = 0; dd < 3; ++dd) {
-        if (!a.act[dd]) continue;
-        const long long cnt = 5LL * a.n[dd == 0 ? 1 : 0] * a.n[dd == 2 ? 1 : 2];
-        if (tid < cnt) {
-            d = dd;
-            break;
-        }
-        tid -= cnt;
-    }
-    if (d < 0) return;
-    const int nd = a.n[d];
+    int jb = 0;
+    while (jb < a.njob && tid >= a.job[jb].count) tid -= a.job[jb++].count;
+    if (jb >= a.njob) return;
+    const AdjPencilJob& J = a.job[jb];
+    const int d = J.d;
+    const int nd = J.n[d];
     const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
-    const long long npen = (long long)a.n[da] * a.n[db];
+    const long long npen = (long long)J.n[da] * J.n[db];
     const int k = (int)(tid / npen);
     const long long pen = tid % npen;
-    double* const gpo = a.gp + 5LL * d * a.fs;
-    double* const gmo = a.gm + 5LL * d * a.fs;
-    const long long st[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
-    const long long base = (pen % a.n[da]) * st[da] + (pen / a.n[da]) * st[db];
+    const int ph = J.phys;
+    double* const gpo = J.gpo;
+    double* const gmo = J.gmo;
+    const long long st[3] = {1, J.n[0], (long long)J.n[0] * J.n[1]};
+    const long long base = (pen % J.n[da]) * st[da] + (pen / J.n[da]) * st[db];
     const long long stp = st[d];
     const long long fs = a.fs;
-    const double alpha = __longlong_as_double((long long)a.rec[3 * (a.stage - 1) + d]);
+    const double alpha = __longlong_as_double((long long)a.rec[3 * (a.stage - 1) + ph]);
     const double dt = __longlong_as_double((long long)a.rec[9]);
-    const double sc = a.cb * dt * a.hdx[d];
+    const double sc = a.cb * dt * J.hdx;
+    const int bcd = J.bc;
+    const double* const U = J.u;
+    const double* const Wv = J.w + (long long)J.wv * fs;
+    const double* const P = J.w;
+    const double* const lam = J.lam;
 
     auto gval = [&](int m, double& gpv, double& gmv) {
-        const long long q = base + (long long)bc_map(m, nd, a.bc[d]) * stp;
-        const double uk = a.u[k * fs + q];
-        const double vd = a.w[(1 + d) * fs + q];
+        const long long q = base + (long long)bc_map(m, nd, bcd) * stp;
+        const double uk = U[k * fs + q];
+        const double vd = Wv[q];
         double f;
-        if (k == 0) f = a.u[(1 + d) * fs + q];
-        else f = uk * vd + (k == 1 + d ? a.w[q] : 0.0);
+        if (k == 0) f = U[(1 + ph) * fs + q];
+        else f = uk * vd + (k == 1 + ph ? P[q] : 0.0);
         gpv = fma(alpha, uk, f);
         gmv = fma(-alpha, uk, f);
     };
@@ -362,7 +377,7 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
     };
     double lamL = 0.0;
     for (int j = -1; j <= nd - 1; ++j) {
-        const double lamR = (j + 1 < nd) ? a.lam[k * fs + base + (long long)(j + 1) * stp] : 0.0;
+        const double lamR = (j + 1 < nd) ? lam[k * fs + base + (long long)(j + 1) * stp] : 0.0;
         const double Fb = sc * (lamR - lamL);
         lamL = lamR;
         weno_left_vjp<R>(gpw, a.eps_s, Fb, ap);           // cells j-G+1 .. j+G-1
@@ -384,12 +399,52 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
     // ghost cells fold back onto their source cells
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-        const long long ql = base + (long long)bc_map(i - G, nd, a.bc[d]) * stp;
+        const long long ql = base + (long long)bc_map(i - G, nd, bcd) * stp;
         gpo[k * fs + ql] += lo_p[i];
         gmo[k * fs + ql] += lo_m[i];
-        const long long qh = base + (long long)bc_map(nd + i, nd, a.bc[d]) * stp;
+        const long long qh = base + (long long)bc_map(nd + i, nd, bcd) * stp;
         gpo[k * fs + qh] += hi_p[i];
         gmo[k * fs + qh] += hi_m[i];
+    }
+}
+
+// Fields between the x-fastest layout (x, then y, then z) and the x-slowest
+// one used for the x pencils (y, then z, then x): plane by plane, 32 x 32
+// tiles through shared memory, so both sides read and write coalesced rows.
+struct FieldMove {
+    const double* src[12];
+    double* dst[12];
+    int n;
+};
+
+// to_xslow: dst[(x nz + z) ny + y] = src[(z ny + y) nx + x]; otherwise the reverse
+template <bool TO_XSLOW>
+__global__ void __launch_bounds__(256) adj_transpose_kernel(FieldMove fm, int nx, int ny, int nz)
+{
+    __shared__ double t[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, z = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int f = 0; f < fm.n; ++f) {
+        for (int j = ty; j < 32; j += 8) {
+            if (TO_XSLOW) {
+                const int x = x0 + tx, y = y0 + j;
+                if (x < nx && y < ny) t[j][tx] = fm.src[f][((long long)z * ny + y) * nx + x];
+            } else {
+                const int y = y0 + tx, x = x0 + j;
+                if (x < nx && y < ny) t[tx][j] = fm.src[f][((long long)x * nz + z) * ny + y];
+            }
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            if (TO_XSLOW) {
+                const int y = y0 + tx, x = x0 + j;
+                if (x < nx && y < ny) fm.dst[f][((long long)x * nz + z) * ny + y] = t[tx][j];
+            } else {
+                const int x = x0 + tx, y = y0 + j;
+                if (x < nx && y < ny) fm.dst[f][((long long)z * ny + y) * nx + x] = t[j][tx];
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -600,7 +655,20 @@ static StageArgs frozen_stage_at(const HandleView& v, AdjointWork* w, const doub
     a.alpha_out = w->ctl->a_next;
     a.status = &v.ctl->status;
     a.bad_cell = &v.ctl->bad_cell;
+    a.fz = v.fz;
+    a.fzs = v.fzs;
     return a;
+}
+
+// one frozen or recorded stage on the adjoint's buffers: the z pass first
+// when the handle's launch has one, then the stage kernel
+static void forward_stage(const HandleView& v, const StageArgs& a, const dim3& grid)
+{
+    if (v.L.zfn && a.act[2]) {
+        const dim3 zg((unsigned)zpass_blocks(v.cfg.n[0], v.cfg.n[1]), (v.cfg.n[2] + 1 + kZFaces - 1) / kZFaces);
+        v.L.zfn<<<zg, kZPassThreads, 0, v.stream>>>(a);
+    }
+    v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
 }
 
 // segment storage: step i of the segment keeps its three stage inputs, each
@@ -646,7 +714,7 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     w->nckpt = (nsteps + ckpt_every - 1) / ckpt_every;
     w->fs = v.fs;
     const long long fs = v.fs;
-    const long long nfields = 27 + 5 * 4 + 30 + 5LL * w->nckpt + 27LL * ckpt_every;
+    const long long nfields = 27 + 5 * 4 + 30 + 22 + 5LL * w->nckpt + 27LL * ckpt_every;
     ACK(h, cudaMalloc(&w->buf, sizeof(double) * (size_t)(fs * nfields)), "adjoint workspace");
     ACK(h, cudaMalloc(&w->rec, sizeof(unsigned long long) * 10 * (size_t)nsteps), "step record");
     ACK(h, cudaMalloc(&w->ctl, sizeof(Ctl)), "scratch control");
@@ -665,6 +733,7 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     w->V = p; p += 5 * fs;
     w->GP = p; p += 15 * fs;   // 5 fields per axis
     w->GM = p; p += 15 * fs;
+    w->XT = p; p += 22 * fs;
     w->CK = p; p += 5 * fs * w->nckpt;
     w->SEG = p;
     // forward steps on the handle's own state, recording speeds and dt; the
@@ -715,7 +784,9 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
             a.dt = &v.ctl->dt;
             a.status = &v.ctl->status;
             a.bad_cell = &v.ctl->bad_cell;
-            v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
+            a.fz = v.fz;
+            a.fzs = v.fzs;
+            forward_stage(v, a, grid);
         }
         record_kernel<<<1, 1, 0, v.stream>>>(v.ctl, w->rec + 10 * (long long)n);
         step_end_kernel<<<1, 1, 0, v.stream>>>(v.ctl);
@@ -729,34 +800,88 @@ static hydro_status stage_adjoint(hydro_t* h, const HandleView& v, AdjointWork* 
 {
     static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     const long long fs = w->fs, nc = v.ncell;
+    const int nx = v.cfg.n[0], ny = v.cfg.n[1], nz = v.cfg.n[2];
     const unsigned long long* rec = w->rec + 10 * (long long)step;
     AdjPencilArgs a{};
-    a.u = u;
-    a.w = ww;
-    a.lam = lam;
-    a.gp = w->GP;
-    a.gm = w->GM;
     a.rec = rec;
     a.fs = fs;
-    long long threads = 0;
-    int actmask = 0;
-    for (int d = 0; d < 3; ++d) {
-        a.n[d] = v.cfg.n[d];
-        a.bc[d] = v.cfg.bc[d];
-        a.act[d] = v.cfg.n[d] > 1;
-        a.hdx[d] = 0.5 / v.cfg.dx[d];
-        if (a.act[d]) {
-            threads += 5LL * (nc / v.cfg.n[d]);
-            actmask |= 1 << d;
-        }
-    }
     a.stage = stage;
     a.cb = cb[stage - 1];
     a.eps_s = v.cfg.weno_eps * (v.R == 3 ? SchemeConst<3>::eps_scale : SchemeConst<4>::eps_scale);
+    int actmask = 0;
+    for (int d = 0; d < 3; ++d)
+        if (v.cfg.n[d] > 1) actmask |= 1 << d;
+    // one job per active axis, all in one launch: y and z pencils in the
+    // state's own layout, x pencils in the x-slowest layout (dimensions ny,
+    // nz, nx) swept along its slowest axis
+    double* UT = w->XT;
+    double* WT = UT + 5 * fs;
+    double* LT = WT + 2 * fs;
+    double* GPT = LT + 5 * fs;
+    double* GMT = GPT + 5 * fs;
+    const dim3 tg((nx + 31) / 32, (ny + 31) / 32, nz), tb(32, 8);
+    a.njob = 0;
+    long long threads = 0;
+    for (int d = 0; d < 3; ++d) {
+        if (!(actmask & (1 << d))) continue;
+        AdjPencilJob& J = a.job[a.njob++];
+        J.phys = d;
+        J.bc = v.cfg.bc[d];
+        J.hdx = 0.5 / v.cfg.dx[d];
+        if (d == 0) {
+            J.u = UT;
+            J.w = WT;
+            J.wv = 1;
+            J.lam = LT;
+            J.gpo = GPT;
+            J.gmo = GMT;
+            J.n[0] = ny;
+            J.n[1] = nz;
+            J.n[2] = nx;
+            J.d = 2;
+        } else {
+            J.u = u;
+            J.w = ww;
+            J.wv = 1 + d;
+            J.lam = lam;
+            J.gpo = w->GP + 5LL * d * fs;
+            J.gmo = w->GM + 5LL * d * fs;
+            for (int e = 0; e < 3; ++e) J.n[e] = v.cfg.n[e];
+            J.d = d;
+        }
+        J.count = 5LL * (nc / v.cfg.n[d]);
+        threads += J.count;
+    }
+    if (actmask & 1) {
+        FieldMove in{};
+        for (int f = 0; f < 5; ++f) {
+            in.src[f] = u + f * fs;
+            in.dst[f] = UT + f * fs;
+            in.src[7 + f] = lam + f * fs;
+            in.dst[7 + f] = LT + f * fs;
+        }
+        in.src[5] = ww;            // p
+        in.dst[5] = WT;
+        in.src[6] = ww + fs;       // v_x
+        in.dst[6] = WT + fs;
+        in.n = 12;
+        adj_transpose_kernel<true><<<tg, tb, 0, v.stream>>>(in, nx, ny, nz);
+    }
     if (threads > 0) {
         const int blocks = (int)((threads + 127) / 128);
         if (v.R == 3) adj_pencil_kernel<3><<<blocks, 128, 0, v.stream>>>(a);
         else adj_pencil_kernel<4><<<blocks, 128, 0, v.stream>>>(a);
+    }
+    if (actmask & 1) {
+        FieldMove out{};
+        for (int f = 0; f < 5; ++f) {
+            out.src[f] = GPT + f * fs;
+            out.dst[f] = w->GP + f * fs;
+            out.src[5 + f] = GMT + f * fs;
+            out.dst[5 + f] = w->GM + f * fs;
+        }
+        out.n = 10;
+        adj_transpose_kernel<false><<<tg, tb, 0, v.stream>>>(out, nx, ny, nz);
     }
     adj_flux_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(u, ww, w->GP, w->GM, w->V, rec, stage, actmask, fs, nc,
                                                              v.cfg.cs2);
@@ -799,7 +924,7 @@ extern "C" hydro_status hydro_adjoint(hydro_t* h, const double* lambda_final, do
                 const StageArgs a = frozen_stage_at(v, w, seg_u(w, i, st - 1), seg_w(w, i, st - 1), seg_u(w, i, 0),
                                                     st < 3 ? seg_u(w, i, st) : seg_u(w, i + 1, 0),
                                                     st < 3 ? seg_w(w, i, st) : seg_w(w, i + 1, 0), st, n);
-                v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
+                forward_stage(v, a, grid);
             }
         }
         for (int n = s1 - 1; n >= s0; --n) {

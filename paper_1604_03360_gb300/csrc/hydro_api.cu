@@ -27,6 +27,10 @@ struct hydro_s {
     double* S[3] = {nullptr, nullptr, nullptr};   // per-axis speeds (local LF only)
     double* fz = nullptr;            // z-face fluxes of the z-pass variants (5 fields of nz+1 planes)
     long long fzs = 0;
+    double* fx = nullptr;            // x- and y-face fluxes of the three-pass variants (global LF)
+    long long fxs = 0;
+    double* fy = nullptr;
+    long long fys = 0;
     Ctl* ctl = nullptr;
     Ctl* hctl = nullptr;             // pinned mirror for read-back
     cudaGraphExec_t exec = nullptr;
@@ -103,6 +107,10 @@ static StageArgs stage_args(hydro_t* h, int stage)
     a.eos_m = h->cfg.eos_mass;
     a.fz = h->fz;
     a.fzs = h->fzs;
+    a.fx = h->fx;
+    a.fxs = h->fxs;
+    a.fy = h->fy;
+    a.fys = h->fys;
     return a;
 }
 
@@ -111,7 +119,13 @@ static StageArgs stage_args(hydro_t* h, int stage)
 static bool launch_fits(const hydro_t* h, const StageLaunch& L)
 {
     if (L.fn_tma && !tma_layout_ok(h->cfg.n[0], h->cfg.n[1])) return false;
-    return !L.zfn || (h->fz && h->cfg.n[1] <= 65535);
+    if (L.combine) {
+        const int nzi = h->zhi - h->zlo;
+        if (!h->fx || !h->fy || pass_blocks(0, h->cfg.n[0], h->cfg.n[1], nzi) > 0x7fffffffLL ||
+            pass_blocks(1, h->cfg.n[0], h->cfg.n[1], nzi) > 0x7fffffffLL)
+            return false;
+    }
+    return !L.zfn || (h->fz && zpass_blocks(h->cfg.n[0], h->cfg.n[1]) <= 0x7fffffffLL);
 }
 
 // one RK3 stage: the z pass first (z-pass variants, z active), then the stage
@@ -120,8 +134,25 @@ static bool launch_fits(const hydro_t* h, const StageLaunch& L)
 // cudaGetLastError as usual.
 static cudaError_t launch_stage(const hydro_t* h, const StageLaunch& L, int zc, const StageArgs& a, cudaStream_t s)
 {
+    if (L.combine) {
+        // three-pass stage: every face flux by its axis pass, then the per-cell combination
+        const int nzi = h->zhi - h->zlo;
+        if (a.act[0])
+            L.xfn<<<dim3((unsigned)pass_blocks(0, a.nx, a.ny, nzi), (a.nx + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
+                    0, s>>>(a);
+        if (a.act[1])
+            L.yfn<<<dim3((unsigned)pass_blocks(1, a.nx, a.ny, nzi), (a.ny + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
+                    0, s>>>(a);
+        if (a.act[2])
+            L.zfn<<<dim3((unsigned)pass_blocks(2, a.nx, a.ny, nzi), (nzi + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
+                    0, s>>>(a);
+        const long long cells = (long long)a.nx * a.ny * nzi;
+        const long long want = (cells + 255) / 256, cap = (long long)h->sms * 8;
+        L.fn<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(a);
+        return cudaSuccess;
+    }
     if (L.zfn && a.act[2]) {
-        const dim3 zg((h->cfg.n[0] + 31) / 32, h->cfg.n[1], (h->zhi - h->zlo + 1 + kZFaces - 1) / kZFaces);
+        const dim3 zg((unsigned)zpass_blocks(h->cfg.n[0], h->cfg.n[1]), (h->zhi - h->zlo + 1 + kZFaces - 1) / kZFaces);
         L.zfn<<<zg, kZPassThreads, 0, s>>>(a);
     }
     const dim3 grid((h->cfg.n[0] + L.tx - 1) / L.tx, (h->cfg.n[1] + L.ty - 1) / L.ty, (h->zhi - h->zlo + zc - 1) / zc);
@@ -181,9 +212,23 @@ hydro_status hydro_handle_view(hydro_t* h, HandleView* v)
     v->ctl = h->ctl;
     v->L = h->L;
     v->zc = h->zc;
-    if (h->L.zfn) {
-        // the adjoint runs its recorded forward on its own buffers: use the
-        // fastest variant that needs no z-face buffer
+    v->fz = nullptr;
+    v->fzs = 0;
+    if (h->L.zfn && h->fz && !h->L.fn_tma && !h->L.combine && h->cfg.bc[2] != HYDRO_BC_HALO) {
+        // the adjoint's recorded forward runs the handle's z-pass launch on its
+        // own state buffers, with the handle's z-face buffer as scratch
+        v->fz = h->fz;
+        v->fzs = h->fzs;
+    } else if (h->L.combine && h->fz && h->cfg.bc[2] != HYDRO_BC_HALO &&
+               stage_launch_variant(h->R, h->cfg.split, h->cfg.nq,
+                                    default_launch_variant(h->R, h->cfg.split, h->cfg.nq, h->cfg.charwise), &v->L,
+                                    h->cfg.charwise) == cudaSuccess && v->L.zfn && !v->L.combine && !v->L.fn_tma) {
+        // a three-pass launch: the adjoint takes the default z-pass launch
+        v->fz = h->fz;
+        v->fzs = h->fzs;
+        v->zc = pick_zc(h->cfg.n[0], h->cfg.n[1], h->cfg.n[2], v->L, h->sms);
+    } else if (h->L.zfn || h->L.fn_tma) {
+        // otherwise the fastest variant that needs no z-face buffer
         cudaError_t e = stage_launch_variant(h->R, h->cfg.split, h->cfg.nq,
                                              fused_launch_variant(h->R, h->cfg.split, h->cfg.nq, h->cfg.charwise), &v->L,
                                              h->cfg.charwise);
@@ -259,6 +304,16 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
         h->fzs = ((long long)cfg->n[0] * cfg->n[1] * (cfg->n[2] + 1) + 31) / 32 * 32;
         if ((e = cudaMalloc(&h->fz, sizeof(double) * (size_t)h->fzs * 5)) != cudaSuccess)
             return bail(cuda_fail(h, e, "z-face buffer"));
+        if (cfg->split == 0) {
+            // x- and y-face fluxes for the three-pass variants
+            const long long nzi = cfg->n[2];
+            h->fxs = ((long long)(cfg->n[0] + 1) * cfg->n[1] * nzi + 31) / 32 * 32;
+            h->fys = ((long long)cfg->n[0] * (cfg->n[1] + 1) * nzi + 31) / 32 * 32;
+            if ((e = cudaMalloc(&h->fx, sizeof(double) * (size_t)h->fxs * 5)) != cudaSuccess)
+                return bail(cuda_fail(h, e, "x-face buffer"));
+            if ((e = cudaMalloc(&h->fy, sizeof(double) * (size_t)h->fys * 5)) != cudaSuccess)
+                return bail(cuda_fail(h, e, "y-face buffer"));
+        }
     }
     {
         // the variant new grids start on (it may need the z-face buffer)
@@ -291,6 +346,8 @@ hydro_status hydro_destroy(hydro_t* h)
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->buf) cudaFree(h->buf);
     if (h->fz) cudaFree(h->fz);
+    if (h->fx) cudaFree(h->fx);
+    if (h->fy) cudaFree(h->fy);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);
     if (h->adj) {
@@ -540,7 +597,7 @@ static hydro_status apply_launch(hydro_t* h, int variant, int zc)
     CK(h, e, "stage kernel setup");
     if (!launch_fits(h, L))
         return fail(h, HYDRO_ERR_INVALID_ARG,
-                    "launch variant does not fit this grid (z-pass variants need ny <= 65535, TMA-staged ones an even nx)");
+                    "launch variant does not fit this grid (TMA-staged variants need an even nx)");
     CK(h, cudaStreamSynchronize(h->stream), "synchronize");
     if (h->exec) {
         cudaGraphExecDestroy(h->exec);
@@ -614,7 +671,9 @@ extern "C" int32_t hydro_kernels_per_step(hydro_t* h)
 {
     if (!h) return 0;
     const bool zpass = h->L.zfn && axis_active(h->cfg, 2);
-    return 2 + 3 * (zpass ? 2 : 1);
+    int per_stage = 1 + (zpass ? 1 : 0);
+    if (h->L.combine) per_stage += (axis_active(h->cfg, 0) ? 1 : 0) + (axis_active(h->cfg, 1) ? 1 : 0);
+    return 2 + 3 * per_stage;
 }
 
 extern "C" hydro_status hydro_set_launch(hydro_t* h, int32_t variant, int32_t zc)

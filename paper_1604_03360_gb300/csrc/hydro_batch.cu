@@ -38,7 +38,7 @@ struct BatchArgs {
     const BatchEvent* ev;
     const int4* items;        // (event, tile x, tile y, z chunk)
     int n_items;
-    const int4* zitems;       // z pass: (event, x block, row, face chunk)
+    const int4* zitems;       // z pass: (event, column block of 32, unused, face chunk)
     unsigned int* counter;    // this stage's work-list counter (zeroed by step-begin)
     int stage;                // 1, 2, 3
     int zc;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) batch_zflux_ker
 {
     const int4 w = b.zitems[blockIdx.x];
     const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
-    zflux_item<R, EMU>(a, w.y, w.z, w.w);
+    zflux_item<R, EMU>(a, w.y, w.w);
 }
 
 __global__ void batch_step_begin_kernel(const BatchEvent* ev, int n, unsigned int* counters)
@@ -266,8 +266,8 @@ static hydro_status build_items(hydro_batch_t* b)
     b->n_items = (int)items.size();
     BCK(b, cudaMalloc(&b->d_items, sizeof(int4) * items.size()), "work-list");
     BCK(b, cudaMemcpy(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice), "work-list copy");
-    // z-pass items: (event, x block of 32, row, chunk of kZFaces faces) of every
-    // event with an active z axis
+    // z-pass items: (event, block of 32 consecutive columns of the plane, 0,
+    // chunk of kZFaces faces) of every event with an active z axis
     if (b->d_zitems) {
         cudaFree(b->d_zitems);
         b->d_zitems = nullptr;
@@ -278,10 +278,11 @@ static hydro_status build_items(hydro_batch_t* b)
         for (int e : order) {
             const int* n = b->ev[e].n;
             if (!b->ev[e].act[2]) continue;
-            const int gx = (n[0] + 31) / 32, gz = (n[2] + 1 + kZFaces - 1) / kZFaces;
+            const long long gc = zpass_blocks(n[0], n[1]);
+            const int gz = (n[2] + 1 + kZFaces - 1) / kZFaces;
+            if (gc > 0x7fffffffLL) return bfail(b, HYDRO_ERR_INVALID_ARG, "event too large for the z pass");
             for (int z = 0; z < gz; ++z)
-                for (int y = 0; y < n[1]; ++y)
-                    for (int x = 0; x < gx; ++x) zi.push_back(make_int4(e, x, y, z));
+                for (long long c = 0; c < gc; ++c) zi.push_back(make_int4(e, (int)c, 0, z));
         }
         b->n_zitems = (int)zi.size();
         if (!zi.empty()) {

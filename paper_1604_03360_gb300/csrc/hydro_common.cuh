@@ -110,6 +110,11 @@ struct StageLaunch {
     // maps (fn is then null); raw tile box of tma_rw x tma_rh cells
     void (*fn_tma)(StageArgs, TmaMaps) = nullptr;
     int tma_rw = 0, tma_rh = 0;
+    // three-pass variants: x and y passes (like the z pass) write every face
+    // flux, then fn is the per-cell combination kernel, launched grid-stride
+    void (*xfn)(StageArgs) = nullptr;
+    void (*yfn)(StageArgs) = nullptr;
+    bool combine = false;
 };
 // tensor maps of the stage input (u: 5 fields, w: p, v_x, v_y of 4) for a
 // TMA-staged launch; cudaErrorNotSupported where the layout does not allow
@@ -117,6 +122,8 @@ struct StageLaunch {
 cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const double* w, int nx, int ny, int nz,
                               long long fs, TmaMaps* out);
 inline bool tma_layout_ok(int nx, int ny) { return nx % 2 == 0 && nx >= 2 && ny >= 1; }
+// CTAs per face chunk of a z pass: 32 consecutive columns of the plane each
+inline long long zpass_blocks(int nx, int ny) { return ((long long)nx * ny + 31) / 32; }
 // Tile shapes compiled per scheme and splitting (index 0 is the default);
 // stage_launch_variant returns cudaErrorInvalidValue for a variant that does
 // not exist.  split: 0 global, 1 local Lax-Friedrichs.
@@ -179,6 +186,8 @@ struct AdjointWork {
     long long fs = 0;
     double* buf = nullptr;                 // all states below
     double *AU[3], *AW[3], *LAM, *OUT, *ACC, *V, *GP, *GM, *CK, *SEG;
+    double* XT = nullptr;                  // x pencils in the x-slowest layout: u 5, p and v_x 2,
+                                           // lambda 5, gbar+ 5, gbar- 5 (22 fields)
     unsigned long long* rec = nullptr;     // nsteps x 10
     Ctl* ctl = nullptr;                    // scratch control block (speed sinks)
 };
@@ -192,8 +201,10 @@ struct HandleView {
     long long ncell, fs;
     double *U0, *W0;
     Ctl* ctl;
-    StageLaunch L;
-    int zc;
+    StageLaunch L;                 // stage launch for the adjoint's own buffers: the
+    int zc;                        // handle's z-pass launch (z faces in fz) or a fused one
+    double* fz;                    // the handle's z-face buffer (null with a fused launch)
+    long long fzs;
 };
 hydro_status hydro_handle_view(hydro_t* h, HandleView* v);
 AdjointWork* hydro_handle_adjoint(hydro_t* h, bool create);

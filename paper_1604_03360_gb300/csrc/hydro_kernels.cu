@@ -147,6 +147,21 @@ static cudaError_t info_for(StageLaunch* out)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, fn, TX * TY, out->smem);
 }
 
+// three-pass stage: x, y and z passes, then the per-cell combination
+template <int R, int ZEMU>
+static cudaError_t info_for_three(StageLaunch* out)
+{
+    out->fn = stage_combine_kernel<5>;
+    out->xfn = axis_flux_kernel<R, ZEMU, 0>;
+    out->yfn = axis_flux_kernel<R, ZEMU, 1>;
+    out->zfn = zflux_kernel<R, ZEMU>;
+    out->combine = true;
+    out->smem = 0;
+    out->tx = 16;
+    out->ty = 16;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_combine_kernel<5>, 256, 0);
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -222,6 +237,8 @@ cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const doubl
 // With the z pass, 16x8 tiles without and with TMA staging of the raw cells
 // (same occupancy, for comparison) and the 16x16 tile with TMA staging (its
 // raw tile leaves room for one CTA per SM): WENO5 9, 10, 11; WENO7 10, 11, 12.
+// Three-pass (x, y and z passes, then the per-cell combination): WENO5 12,
+// WENO7 13.
 // Variants 4 (WENO5) and 3 (WENO7) keep every product on the FP64 unit (the
 // bitwise reference); the others take the default of default_emu.  WENO5 7, 8 /
 // WENO7 6, 7: the 16x16 pencil sweep with the z faces from a separate z pass
@@ -262,7 +279,7 @@ int launch_variant_count(int R, int split, int nq, int charw)
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 4 : 3;
-    return R == 3 ? 12 : 13;
+    return R == 3 ? 13 : 14;
 }
 
 template <int NF>
@@ -326,6 +343,7 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 9) return info_for<3, 16, 8, kPencilSweep, false, 5, kEmuConst | kEmuWeights, true, kZPassEmu5, 4>(out);
         if (v == 10) return info_for_tma<3, 16, 8, kEmuConst | kEmuWeights, kZPassEmu5, 4>(out);
         if (v == 11) return info_for_tma<3, 16, 16, kEmuConst | kEmuWeights, kZPassEmu5, 1>(out);
+        if (v == 12) return info_for_three<3, kZPassEmu5>(out);
     }
     if (R == 4) {
         if (v == 0) return info_for<4, 16, 16>(out);
@@ -342,6 +360,7 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 10) return info_for<4, 16, 8, kPencilSweep, false, 5, kEmuConst, true, kZPassEmu7, 3>(out);
         if (v == 11) return info_for_tma<4, 16, 8, kEmuConst, kZPassEmu7, 3>(out);
         if (v == 12) return info_for_tma<4, 16, 16, kEmuConst, kZPassEmu7, 1>(out);
+        if (v == 13) return info_for_three<4, kZPassEmu7>(out);
     }
     return cudaErrorInvalidValue;
 }

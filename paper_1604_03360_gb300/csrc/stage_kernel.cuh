@@ -81,6 +81,10 @@ struct StageArgs {
     double eos_m;           // EOS p = cs2 (e - eos_m n_1); 0: p = cs2 e
     double* fz;             // z-pass variants: z-face fluxes, field k face f (between planes zlo+f-1
     long long fzs;          // and zlo+f) at fz[k fzs + f nx ny + y nx + x], f = 0 .. zhi-zlo
+    double* fx;             // three-pass variants: x-face fluxes, field k face f (between columns
+    long long fxs;          // f-1 and f) of row (y, z) at fx[k fxs + ((z-zlo) ny + y)(nx+1) + f]
+    double* fy;             // and y-face fluxes, face f between rows f-1 and f, at
+    long long fys;          // fy[k fys + f nx (zhi-zlo) + (z-zlo) nx + x]
 };
 
 // boundary rule 0 outflow (copy edge cell), 1 periodic; 2 (z only) halo: the
@@ -830,8 +834,9 @@ __global__ void __launch_bounds__(TX * TY, MINB) stage_kernel_tma(const StageArg
 // each thread sweeping one (x, y, field) pencil over a chunk of kZFaces faces
 // with the stencil differences carried from face to face -- the same
 // operations on the same operands as the ring of the fused kernel, so the same
-// bits.  A CTA is 32 consecutive x (one warp per field) of one row y; grid
-// (ceil(nx/32), ny, ceil((nz+1)/kZFaces)).  Face f lies between planes
+// bits.  A CTA is 32 consecutive columns of the plane (flat index y nx + x,
+// so rows of any width fill whole warps; one warp per field); grid
+// (ceil(nx ny / 32), ceil((nz+1)/kZFaces)).  Face f lies between planes
 // zlo+f-1 and zlo+f (f = 0 .. zhi-zlo); its left-biased stencil is centred
 // on plane zlo+f-1, its right-biased one on plane zlo+f.
 constexpr int kZFaces = 64, kZPassThreads = 160;
@@ -839,37 +844,74 @@ constexpr int kZFaces = 64, kZPassThreads = 160;
 // kinds, WENO7 without the face products)
 constexpr int kZPassEmu5 = kEmuConst | kEmuWeights | kEmuFace, kZPassEmu7 = kEmuConst | kEmuWeights;
 
-// one z-pass item: x block xb (32 columns), row y, face chunk zch, of the grid
-// described by a; the CTA's five warps are the five fields
-template <int R, int EMU>
-__device__ __forceinline__ void zflux_item(const StageArgs& a, int xb, int y, int zch)
+// one pass item along axis AX: pencil block cb (32 consecutive pencils), face
+// chunk fch, of the grid described by a; the CTA's five warps are the five
+// fields.  Pencils and outputs:
+//   AX = 2 (z pass): pencil = column y nx + x of the plane; faces f = 0 ..
+//      zhi-zlo between stored planes zlo+f-1 and zlo+f; out fz[k fzs + f nx ny + pencil];
+//   AX = 1 (y pass): pencil = (z-zlo) nx + x; faces f = 0 .. ny between rows
+//      f-1 and f; out fy[k fys + f nx nzi + pencil] (nzi = zhi - zlo);
+//   AX = 0 (x pass): pencil = (z-zlo) ny + y; faces f = 0 .. nx between
+//      columns f-1 and f; out fx[k fxs + pencil (nx+1) + f].
+// Consecutive lanes take consecutive pencils, so the z and y passes read and
+// write coalesced rows; the x pass reads rows a row apart (each lane's next
+// cells hit the same L1 sectors) and writes its faces contiguously per row.
+template <int R, int EMU, int AX>
+__device__ __forceinline__ void axis_flux_item(const StageArgs& a, long long cb, int fch)
 {
     constexpr int G = R, S = 2 * R - 1;
     using DF = typename DiffOf<R>::T;
     if (!(*a.dt > 0.0)) return;
-    const int k = threadIdx.x >> 5, x = xb * 32 + (threadIdx.x & 31);
-    if (x >= a.nx) return;                       // no barriers below
-    const int f0 = zch * kZFaces, f1 = min(f0 + kZFaces, a.zhi - a.zlo + 1);
-    const double az = __longlong_as_double((long long)a.alpha_in[2]);
-    const long long plane = (long long)a.nx * a.ny, col = (long long)y * a.nx + x;
-    // split z-fluxes g+- = f_z +- alpha_z u of field k at stored plane m (as split_flux)
+    const int k = threadIdx.x >> 5;
+    const long long plane = (long long)a.nx * a.ny;
+    const int nzi = a.zhi - a.zlo;
+    const long long npen = AX == 2 ? plane : (AX == 1 ? (long long)a.nx * nzi : (long long)a.ny * nzi);
+    const long long pen = cb * 32 + (threadIdx.x & 31);
+    if (pen >= npen) return;                     // no barriers below
+    const int nax = AX == 2 ? nzi : (AX == 1 ? a.ny : a.nx);     // cells along the pencil (interior)
+    const int f0 = fch * kZFaces, f1 = min(f0 + kZFaces, nax + 1);
+    const double al = __longlong_as_double((long long)a.alpha_in[AX]);
+    // first cell of the pencil and the step between its cells
+    long long base, step;
+    int lo, ncell_ax, bcax;
+    if constexpr (AX == 2) {
+        base = pen;
+        step = plane;
+        lo = a.zlo;
+        ncell_ax = a.nz;
+        bcax = a.bc[2];
+    } else if constexpr (AX == 1) {
+        base = (long long)(a.zlo + pen / a.nx) * plane + pen % a.nx;
+        step = a.nx;
+        lo = 0;
+        ncell_ax = a.ny;
+        bcax = a.bc[1];
+    } else {
+        base = (long long)(a.zlo + pen / a.ny) * plane + (pen % a.ny) * a.nx;
+        step = 1;
+        lo = 0;
+        ncell_ax = a.nx;
+        bcax = a.bc[0];
+    }
+    // split fluxes g+- = f_AX +- alpha u of field k at (stored) position m
+    // along the pencil (as split_flux)
     auto split_at = [&](int m, double& gp, double& gm) {
-        const long long q = (long long)bc_map(m, a.nz, a.bc[2]) * plane + col;
+        const long long q = base + (long long)bc_map(m, ncell_ax, bcax) * step;
         const double uk = __ldg(a.u_in + k * a.fs + q);
         double f;
         if (k == 0) {
-            f = __ldg(a.u_in + 3 * a.fs + q);
+            f = __ldg(a.u_in + (1 + AX) * a.fs + q);
         } else {
-            f = __dmul_rn(uk, __ldg(a.w_in + 3 * a.fs + q));
-            if (k == 3) f = __dadd_rn(f, __ldg(a.w_in + q));
+            f = __dmul_rn(uk, __ldg(a.w_in + (1 + AX) * a.fs + q));
+            if (k == 1 + AX) f = __dadd_rn(f, __ldg(a.w_in + q));
         }
-        gp = fma(az, uk, f);
-        gm = fma(-az, uk, f);
+        gp = fma(al, uk, f);
+        gm = fma(-al, uk, f);
     };
-    // windows of face p+1/2 (p = zlo+f-1): wp = g+ at planes p-G+1 .. p+G-1,
-    // wm = g- at planes p-G+2 .. p+G; gl = g+ of the newest plane p+G
+    // windows of face p+1/2 (p = lo+f-1): wp = g+ at p-G+1 .. p+G-1,
+    // wm = g- at p-G+2 .. p+G; gl = g+ of the newest cell p+G
     double wp[S], wm[S], gl = 0.0;
-    const int p0 = a.zlo + f0 - 1;
+    const int p0 = lo + f0 - 1;
 #pragma unroll
     for (int i = 0; i < 2 * G; ++i) {
         double gp, gm;
@@ -879,7 +921,18 @@ __device__ __forceinline__ void zflux_item(const StageArgs& a, int xb, int y, in
         gl = gp;
     }
     DF qp, qm;
-    double* out = a.fz + k * a.fzs + col;
+    double* out;
+    long long ostep;
+    if constexpr (AX == 2) {
+        out = a.fz + k * a.fzs + pen;
+        ostep = plane;
+    } else if constexpr (AX == 1) {
+        out = a.fy + k * a.fys + pen;
+        ostep = (long long)a.nx * nzi;
+    } else {
+        out = a.fx + k * a.fxs + pen * (a.nx + 1);
+        ostep = 1;
+    }
     for (int f = f0; f < f1; ++f) {
         double mm[S];
 #pragma unroll
@@ -894,9 +947,9 @@ __device__ __forceinline__ void zflux_item(const StageArgs& a, int xb, int y, in
         double Np, Dp, Nm, Dm;
         weno_core<R, EMU>(qp, a.eps_s, Np, Dp);
         weno_core<R, EMU>(qm, a.eps_s, Nm, Dm);
-        out[(long long)f * plane] = face_sum<EMU>(Np, Dp, wp[G - 1], Nm, Dm, wm[G - 1]);
+        out[(long long)f * ostep] = face_sum<EMU>(Np, Dp, wp[G - 1], Nm, Dm, wm[G - 1]);
         if (f + 1 < f1) {
-            // next face: planes move up by one
+            // next face: the window moves by one cell
 #pragma unroll
             for (int i = 0; i < S - 1; ++i) {
                 wp[i] = wp[i + 1];
@@ -904,17 +957,119 @@ __device__ __forceinline__ void zflux_item(const StageArgs& a, int xb, int y, in
             }
             wp[S - 1] = gl;
             double gm;
-            split_at(a.zlo + f + G, gl, gm);
+            split_at(lo + f + G, gl, gm);
             wm[S - 1] = gm;
         }
     }
+}
+
+template <int R, int EMU>
+__device__ __forceinline__ void zflux_item(const StageArgs& a, long long cb, int zch)
+{
+    axis_flux_item<R, EMU, 2>(a, cb, zch);
 }
 
 // (3 CTAs per SM for WENO7, 4 for WENO5: 15 and 20 warps)
 template <int R, int EMU>
 __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_kernel(const StageArgs a)
 {
-    zflux_item<R, EMU>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+    zflux_item<R, EMU>(a, blockIdx.x, blockIdx.y);
+}
+
+// x and y passes of the three-pass variants (same CTA and occupancy as the z pass)
+template <int R, int EMU, int AX>
+__global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) axis_flux_kernel(const StageArgs a)
+{
+    axis_flux_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y);
+}
+
+// pencil blocks of a pass along axis AX
+inline long long pass_blocks(int AX, int nx, int ny, int nzi)
+{
+    const long long npen = AX == 2 ? (long long)nx * ny : (AX == 1 ? (long long)nx * nzi : (long long)ny * nzi);
+    return (npen + 31) / 32;
+}
+
+// Three-pass variants: the rest of the stage once the x, y and z passes have
+// written every face flux -- per cell the flux differences (Eq. 2), the RK
+// combination, the primitives and the speeds of the new state, with the same
+// operations in the same order as step 4 of stage_tile (component-wise, global
+// Lax-Friedrichs, five fields), so the same bits.  Grid-stride over the
+// interior cells, x fastest.  (A template only so that every translation
+// unit including this header can share one definition.)
+template <int NF = 5>
+__global__ void __launch_bounds__(256) stage_combine_kernel(const StageArgs a)
+{
+    static_assert(NF == 5, "the three-pass variants carry five fields");
+    const double dt = *a.dt;
+    if (!(dt > 0.0)) return;
+    const int nx = a.nx, ny = a.ny, nzi = a.zhi - a.zlo;
+    const long long plane = (long long)nx * ny, ncell = plane * nzi, fs = a.fs;
+    const long long yrow = (long long)nx * nzi;           // one y-face row of the fy buffer
+    const bool ax0 = a.act[0] != 0, ax1 = a.act[1] != 0, ax2 = a.act[2] != 0;
+    unsigned long long amax[3] = {0ull, 0ull, 0ull};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long r = i / nx;
+        const int y = (int)(r % ny), zi = (int)(r / ny);
+        const long long q = (long long)(a.zlo + zi) * plane + (long long)y * nx + x;
+        double un[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            double L = 0.0;
+            if (ax0) {
+                const double* fx = a.fx + k * a.fxs + ((long long)zi * ny + y) * (nx + 1) + x;
+                L = a.hdx[0] * (fx[0] - fx[1]);
+            }
+            if (ax1) {
+                const double* fy = a.fy + k * a.fys + (long long)y * yrow + (long long)zi * nx + x;
+                L = fma(a.hdx[1], fy[0] - fy[yrow], L);
+            }
+            if (ax2) {
+                const double* fz = a.fz + k * a.fzs + (long long)zi * plane + (long long)y * nx + x;
+                L = fma(a.hdx[2], fz[0] - fz[plane], L);
+            }
+            const double s = fma(dt, L, __ldg(a.u_in + k * fs + q));
+            un[k] = (a.ca == 0.0) ? s : fma(a.ca, a.u_n[k * fs + q], a.cb * s);
+            a.u_out[k * fs + q] = un[k];
+        }
+        double pr, vx, vy, vz, e, ks = a.cs2;
+        bool okp;
+        if (a.eos_m == 0.0) {
+            okp = con2prim(a.cs2, un[0], un[1], un[2], un[3], pr, vx, vy, vz, e);
+        } else {
+            okp = con2prim_gas(a.cs2, a.eos_m, un[0], un[1], un[2], un[3], un[4], pr, vx, vy, vz, e);
+            if (okp) ks = sound2_gas(a.cs2, pr, e);
+        }
+        if (okp) {
+            a.w_out[q] = pr;
+            a.w_out[fs + q] = vx;
+            a.w_out[2 * fs + q] = vy;
+            a.w_out[3 * fs + q] = vz;
+            double sp[3];
+            max_speeds(ks, vx, vy, vz, sp);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(sp[d]);
+                amax[d] = b > amax[d] ? b : amax[d];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.w_out[k * fs + q] = 0.0;
+            if (atomicCAS(a.status, 0, 4) == 0) *a.bad_cell = q;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        unsigned long long v = amax[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
+        }
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(a.alpha_out + d, v);
+    }
 }
 
 // z pass of a local Lax-Friedrichs stage: the z-face fluxes of the five
@@ -926,14 +1081,14 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_kernel(co
 // exactly as the local-LF z ring of the stage kernel does (llf_face on the
 // same values), so both give the same bits.  Same grid and CTA as zflux_kernel.
 template <int R, int EMU>
-__device__ __forceinline__ void zflux_llf_item(const StageArgs& a, int xb, int y, int zch)
+__device__ __forceinline__ void zflux_llf_item(const StageArgs& a, long long cb, int zch)
 {
     constexpr int G = R, W = 2 * R;
     if (!(*a.dt > 0.0)) return;
-    const int k = threadIdx.x >> 5, x = xb * 32 + (threadIdx.x & 31);
-    if (x >= a.nx) return;                       // no barriers below
+    const int k = threadIdx.x >> 5;
+    const long long plane = (long long)a.nx * a.ny, col = cb * 32 + (threadIdx.x & 31);
+    if (col >= plane) return;                    // no barriers below
     const int f0 = zch * kZFaces, f1 = min(f0 + kZFaces, a.zhi - a.zlo + 1);
-    const long long plane = (long long)a.nx * a.ny, col = (long long)y * a.nx + x;
     // raw z flux, state and z speed of field k at stored plane m (as raw_flux_rn)
     auto raw_at = [&](int m, double& fv, double& uv, double& sv) {
         const long long q = (long long)bc_map(m, a.nz, a.bc[2]) * plane + col;
@@ -972,7 +1127,7 @@ __device__ __forceinline__ void zflux_llf_item(const StageArgs& a, int xb, int y
 template <int R, int EMU>
 __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_llf_kernel(const StageArgs a)
 {
-    zflux_llf_item<R, EMU>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+    zflux_llf_item<R, EMU>(a, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace hydro

@@ -66,7 +66,8 @@ def test_outflow_slabs_match_whole_grid(scheme, nslabs):
     check(g, w, nslabs, 5, device="cuda")
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 7), (5, 8), (7, 6), (7, 7), (5, 10), (7, 11), (7, 12)])
+@pytest.mark.parametrize("scheme,variant", [(5, 7), (5, 8), (7, 6), (7, 7), (5, 10), (7, 11), (7, 12), (5, 12),
+                                            (7, 13)])
 def test_zpass_slabs_match_whole_grid(scheme, variant):
     """Slabs whose z faces come from the z pass (which reads the stored ghost
     planes) advance bit for bit like the whole grid on the fused kernel; so do

@@ -4,8 +4,8 @@
 Workload (headline): 3+1D ellipsoidal flow on a 256^3 grid, WENO7, FP64,
 synthetic seeded data shaped like the paper's Sec. 3 test (Gaussian ellipsoid
 e0 = 20, a, b, c = 2, 3, 4, linear axis-scaled velocity, n ~ e, p = e/3).
-A "step" is one full RK3 step (per stage a z-face pass and a stage kernel, plus
-two 1-thread bookkeeping kernels).  A cell-update is one interior cell advanced by one RK3
+A "step" is one full RK3 step (per stage an x-, a y- and a z-face pass and a
+per-cell combination kernel, plus two 1-thread bookkeeping kernels).  A cell-update is one interior cell advanced by one RK3
 step.  The state (3.6 GB of FP64 fields) is far larger than L2 (129 MB), so
 no flush is needed between steps.
 
@@ -41,16 +41,18 @@ FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
 # Executed FP64 instructions (thread-level DFMA + DADD + DMUL, each one issue
 # slot of the FP64 pipe) per interior cell and RK3 stage, z pass + stage kernel,
 # and the DRAM bytes (read + write) per cell and stage, from ncu captures of the
-# 128^3 ellipsoidal workload (mean of stages 1-3), keyed by (scheme, launch
-# variant, tile x, tile y).  roofline.frac = this count x cells / stage time /
+# 128^3 ellipsoidal workload (mean of stages 1-3, every launch of a stage:
+# the face passes and the stage or combination kernel), keyed by (scheme,
+# launch variant, tile x, tile y).  roofline.frac = this count x cells / stage time /
 # the FP64 FMA issue rate measured in the same run: the FP64 pipe's
 # utilisation.  A launch without a capture reports null.
-NCU_FP64_INST_PER_CELL_STAGE = {(7, 7, 16, 16): 1745.3, (7, 6, 16, 16): 1729.6,
-                                (5, 8, 16, 16): 896.2, (5, 7, 16, 16): 1023.7}
-NCU_DRAM_BYTES_PER_CELL_STAGE = {(7, 7, 16, 16): 276.5, (7, 6, 16, 16): 270.1,
-                                 (5, 8, 16, 16): 273.5, (5, 7, 16, 16): 269.3}
-# FP64 pipe busy, time-weighted over z pass and stage kernel
-NCU_FP64_PIPE_BUSY = {(7, 7, 16, 16): 0.849, (7, 6, 16, 16): 0.828, (5, 8, 16, 16): 0.809, (5, 7, 16, 16): 0.838}
+NCU_FP64_INST_PER_CELL_STAGE = {(7, 13, 16, 16): 1422.7, (7, 7, 16, 16): 1745.3, (7, 6, 16, 16): 1729.6,
+                                (5, 12, 16, 16): 808.8, (5, 8, 16, 16): 896.2, (5, 7, 16, 16): 1023.7}
+NCU_DRAM_BYTES_PER_CELL_STAGE = {(7, 13, 16, 16): 505.8, (7, 7, 16, 16): 276.5, (7, 6, 16, 16): 270.1,
+                                 (5, 12, 16, 16): 511.0, (5, 8, 16, 16): 273.5, (5, 7, 16, 16): 269.3}
+# FP64 pipe busy, time-weighted over the launches of one stage
+NCU_FP64_PIPE_BUSY = {(7, 13, 16, 16): 0.793, (7, 7, 16, 16): 0.849, (7, 6, 16, 16): 0.828,
+                      (5, 12, 16, 16): 0.846, (5, 8, 16, 16): 0.809, (5, 7, 16, 16): 0.838}
 # Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
 # stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
 HBM_BYTES_PER_CELL_UPDATE = 320
@@ -429,7 +431,7 @@ def main():
                     help="headline run with local Lax-Friedrichs splitting (profiling; the metric stays global LF)")
     ap.add_argument("--launch", type=int, default=None,
                     help="force this stage-kernel launch variant instead of autotuning (profiling)")
-    ap.add_argument("--only", choices=["adjoint"], default=None,
+    ap.add_argument("--only", choices=["adjoint", "batch"], default=None,
                     help="run one extra measurement alone and print it (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -442,6 +444,15 @@ def main():
         stream = torch.cuda.current_stream()
         print(json.dumps({"adjoint_96": adjoint_96(torch.device("cuda", 0), stream, torch.cuda.synchronize)}),
               flush=True)
+        return
+    if args.only == "batch":
+        import torch
+        from paper_1604_03360_gb300 import build as B
+        B.build()
+        torch.cuda.set_device(0)
+        stream = torch.cuda.current_stream()
+        print(json.dumps({"batched_vs_looped": batched_vs_looped(torch.device("cuda", 0), stream, torch.cuda.synchronize,
+                                                                 10, 3, args.batch_events)}), flush=True)
         return
 
     import torch
@@ -678,10 +689,10 @@ def main():
                          "unit": "FP64 Tinst/s", "frac": None if inst_rate is None else inst_rate / fp64_inst_peak,
                          "traffic": traffic,
                          "traffic_source": "ncu dram__bytes_read+write of the 128^3 stage launches of the same "
-                                           "variant (z pass + stage kernel, mean of stages 1-3), scaled by cells",
+                                           "variant (all launches of a stage, mean of stages 1-3), scaled by cells",
                          "fp64_inst_per_cell_stage": inst,
                          "achieved_source": "executed FP64 instructions per cell and stage (ncu, thread-level DFMA + "
-                                            "DADD + DMUL of z pass + stage kernel on the 128^3 case of this launch) "
+                                            "DADD + DMUL of all launches of a stage on the 128^3 case of this launch) "
                                             "x cells / stage time (CUDA events); peak = FP64 FMA issue rate measured "
                                             "in this run (hydro_measure_fp64_peak)",
                          "ncu_fp64_pipe_busy": None if other else NCU_FP64_PIPE_BUSY.get(key),
@@ -690,7 +701,10 @@ def main():
                                              "(FMA = 2); the kernels share differences between faces and run some "
                                              "products on the integer pipe, so this rate can exceed the FP64 peak"
                                              % FLOPS_PER_CELL_STAGE[args.scheme],
-                         "kernel": "zflux_kernel + stage_kernel<WENO%d>" % args.scheme, "stage_ms": stage_ms,
+                         "kernel": ("x, y, z face passes + stage_combine_kernel"
+                                    if launch[0] == {5: 12, 7: 13}[args.scheme]
+                                    else "zflux_kernel + stage_kernel") + " (WENO%d)" % args.scheme,
+                         "stage_ms": stage_ms,
                          "peak_source": "FP64 FMA probe kernel measured in this run (hydro_measure_fp64_peak); "
                                         "MEASURED_PEAKS.json has no FP64 figure; nominal 152 SM x 2 DFMA/clk x "
                                         "2.07 GHz = 0.629 T/s"},

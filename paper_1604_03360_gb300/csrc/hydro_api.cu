@@ -220,8 +220,7 @@ hydro_status hydro_handle_view(hydro_t* h, HandleView* v)
         v->fz = h->fz;
         v->fzs = h->fzs;
     } else if (h->L.combine && h->fz && h->cfg.bc[2] != HYDRO_BC_HALO &&
-               stage_launch_variant(h->R, h->cfg.split, h->cfg.nq,
-                                    default_launch_variant(h->R, h->cfg.split, h->cfg.nq, h->cfg.charwise), &v->L,
+               stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, zpass_launch_variant(h->R), &v->L,
                                     h->cfg.charwise) == cudaSuccess && v->L.zfn && !v->L.combine && !v->L.fn_tma) {
         // a three-pass launch: the adjoint takes the default z-pass launch
         v->fz = h->fz;
@@ -304,7 +303,7 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
         h->fzs = ((long long)cfg->n[0] * cfg->n[1] * (cfg->n[2] + 1) + 31) / 32 * 32;
         if ((e = cudaMalloc(&h->fz, sizeof(double) * (size_t)h->fzs * 5)) != cudaSuccess)
             return bail(cuda_fail(h, e, "z-face buffer"));
-        if (cfg->split == 0) {
+        {
             // x- and y-face fluxes for the three-pass variants
             const long long nzi = cfg->n[2];
             h->fxs = ((long long)(cfg->n[0] + 1) * cfg->n[1] * nzi + 31) / 32 * 32;

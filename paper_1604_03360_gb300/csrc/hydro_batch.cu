@@ -26,6 +26,10 @@ struct BatchEvent {
     double* S[3];             // per-axis speeds (local LF only)
     double* fz;               // z-face fluxes (z-pass variants): 5 fields of nz + 1 face planes
     long long fzs;
+    double* fx;               // x- and y-face fluxes (three-pass variants), layouts as in StageArgs
+    long long fxs;
+    double* fy;
+    long long fys;
     long long fs, ncell;
     int n[3], bc[3], act[3];
     double hdx[3];
@@ -39,6 +43,9 @@ struct BatchArgs {
     const int4* items;        // (event, tile x, tile y, z chunk)
     int n_items;
     const int4* zitems;       // z pass: (event, column block of 32, unused, face chunk)
+    const int4* xitems;       // three-pass variants: x and y passes (event, pencil block, unused, face
+    const int4* yitems;       // chunk) and the combination (event, block of kCombineCells cells)
+    const int4* citems;
     unsigned int* counter;    // this stage's work-list counter (zeroed by step-begin)
     int stage;                // 1, 2, 3
     int zc;
@@ -78,6 +85,10 @@ __device__ __forceinline__ StageArgs batch_stage_args(const BatchEvent& E, int s
     a.s_out = stage == 3 ? E.S[0] : E.S[stage];
     a.fz = E.fz;
     a.fzs = E.fzs;
+    a.fx = E.fx;
+    a.fxs = E.fxs;
+    a.fy = E.fy;
+    a.fys = E.fys;
     return a;
 }
 
@@ -107,6 +118,29 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) batch_zflux_ker
     const int4 w = b.zitems[blockIdx.x];
     const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
     zflux_item<R, EMU>(a, w.y, w.w);
+}
+
+// three-pass variants: x and y passes of all events (one CTA per item) and the
+// combination (one CTA per block of kCombineCells cells of one event)
+template <int R, int EMU, int AX>
+__global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) batch_axis_flux_kernel(const BatchArgs b)
+{
+    const int4 w = (AX == 0 ? b.xitems : b.yitems)[blockIdx.x];
+    const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
+    axis_flux_item<R, EMU, AX>(a, w.y, w.w);
+}
+
+constexpr int kCombineCells = 2048;
+
+template <int NF = 5>
+__global__ void __launch_bounds__(256) batch_combine_kernel(const BatchArgs b)
+{
+    const int4 w = b.citems[blockIdx.x];
+    const BatchEvent& E = b.ev[w.x];
+    const StageArgs a = batch_stage_args(E, b.stage, b.zc);
+    const long long c0 = (long long)w.y * kCombineCells;
+    const long long c1 = c0 + kCombineCells < E.ncell ? c0 + kCombineCells : E.ncell;
+    combine_cells<NF>(a, c0 + threadIdx.x, c1, blockDim.x);
 }
 
 __global__ void batch_step_begin_kernel(const BatchEvent* ev, int n, unsigned int* counters)
@@ -144,7 +178,25 @@ struct BatchLaunch {
     size_t smem;
     int tx, ty, ctas_per_sm;
     void (*zfn)(BatchArgs) = nullptr;   // z pass before fn (z-pass variants)
+    void (*xfn)(BatchArgs) = nullptr;   // three-pass variants: x and y passes, fn is the combination
+    void (*yfn)(BatchArgs) = nullptr;
+    bool combine = false;
 };
+
+template <int R, int ZEMU>
+static cudaError_t batch_info_for_three(BatchLaunch* out)
+{
+    out->fn = batch_combine_kernel<5>;
+    out->xfn = batch_axis_flux_kernel<R, ZEMU, 0>;
+    out->yfn = batch_axis_flux_kernel<R, ZEMU, 1>;
+    out->zfn = batch_zflux_kernel<R, ZEMU>;
+    out->combine = true;
+    out->smem = 0;
+    out->tx = 16;
+    out->ty = 16;
+    out->ctas_per_sm = 1;
+    return cudaSuccess;
+}
 
 template <int R, int TX, int TY, int ILP = 1, bool LLF = false, int EMU = default_emu(R, TX, TY, LLF, 5, false),
           bool ZEXT = false, int ZEMU = EMU, int MINB = 0>
@@ -182,6 +234,7 @@ static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* ou
         if (v == 7) return batch_info_for<3, 16, 16, kPencilSweep, false, kEmuConst, true, kZPassEmu5>(out);
         if (v == 8)
             return batch_info_for<3, 16, 16, kPencilSweep, false, kEmuConst | kEmuWeights, true, kZPassEmu5, 2>(out);
+        if (v == 9) return batch_info_for_three<3, kZPassEmu5>(out);
     }
     if (R == 4) {
         if (v == 0) return batch_info_for<4, 16, 16>(out);
@@ -192,6 +245,7 @@ static cudaError_t batch_launch_variant(int R, int split, int v, BatchLaunch* ou
         if (v == 5) return batch_info_for<4, 16, 16, kPencilSweep>(out);
         if (v == 6) return batch_info_for<4, 16, 16, kPencilSweep, false, kEmuConst, true, kZPassEmu7>(out);
         if (v == 7) return batch_info_for<4, 16, 16, kPencilSweep, false, kEmuConst, true, kZPassEmu7, 2>(out);
+        if (v == 8) return batch_info_for_three<4, kZPassEmu7>(out);
     }
     return cudaErrorInvalidValue;
 }
@@ -216,6 +270,12 @@ struct hydro_batch_s {
     int n_items = 0;
     int4* d_zitems = nullptr;        // z-pass items (z-pass variants)
     int n_zitems = 0;
+    int4* d_xitems = nullptr;        // three-pass variants: x-, y-pass and combination items
+    int n_xitems = 0;
+    int4* d_yitems = nullptr;
+    int n_yitems = 0;
+    int4* d_citems = nullptr;
+    int n_citems = 0;
     BatchLaunch L{};
     int variant = 0, zc = 16;
     cudaGraphExec_t exec = nullptr;
@@ -291,6 +351,39 @@ static hydro_status build_items(hydro_batch_t* b)
                 "z work-list copy");
         }
     }
+    // three-pass variants: x- and y-pass items (event, pencil block, 0, face
+    // chunk) of the events with that axis active, and the combination items
+    // (event, block of kCombineCells cells)
+    int4** dl[3] = {&b->d_xitems, &b->d_yitems, &b->d_citems};
+    int* nl[3] = {&b->n_xitems, &b->n_yitems, &b->n_citems};
+    for (int i = 0; i < 3; ++i) {
+        if (*dl[i]) cudaFree(*dl[i]);
+        *dl[i] = nullptr;
+        *nl[i] = 0;
+    }
+    if (b->L.combine) {
+        std::vector<int4> li[3];
+        for (int e : order) {
+            const BatchEvent& E = b->ev[e];
+            for (int ax = 0; ax < 2; ++ax) {
+                if (!E.act[ax]) continue;
+                const long long gc = pass_blocks(ax, E.n[0], E.n[1], E.n[2]);
+                if (gc > 0x7fffffffLL) return bfail(b, HYDRO_ERR_INVALID_ARG, "event too large for the face passes");
+                const int gf = (E.n[ax] + 1 + kZFaces - 1) / kZFaces;
+                for (int f = 0; f < gf; ++f)
+                    for (long long c = 0; c < gc; ++c) li[ax].push_back(make_int4(e, (int)c, 0, f));
+            }
+            const long long nb = (E.ncell + kCombineCells - 1) / kCombineCells;
+            for (long long c = 0; c < nb; ++c) li[2].push_back(make_int4(e, (int)c, 0, 0));
+        }
+        for (int i = 0; i < 3; ++i) {
+            *nl[i] = (int)li[i].size();
+            if (li[i].empty()) continue;
+            BCK(b, cudaMalloc(dl[i], sizeof(int4) * li[i].size()), "pass work-list");
+            BCK(b, cudaMemcpy(*dl[i], li[i].data(), sizeof(int4) * li[i].size(), cudaMemcpyHostToDevice),
+                "pass work-list copy");
+        }
+    }
     return HYDRO_OK;
 }
 
@@ -301,6 +394,9 @@ static BatchArgs batch_args(const hydro_batch_t* b, int stage)
     a.items = b->d_items;
     a.n_items = b->n_items;
     a.zitems = b->d_zitems;
+    a.xitems = b->d_xitems;
+    a.yitems = b->d_yitems;
+    a.citems = b->d_citems;
     a.counter = b->counters + (stage - 1);
     a.stage = stage;
     a.zc = b->zc;
@@ -310,6 +406,13 @@ static BatchArgs batch_args(const hydro_batch_t* b, int stage)
 // one stage of all events: the z pass (z-pass variants), then the persistent stage kernel
 static void launch_batch_stage(const hydro_batch_t* b, const BatchArgs& a, cudaStream_t s)
 {
+    if (b->L.combine) {
+        if (b->n_xitems > 0) b->L.xfn<<<b->n_xitems, kZPassThreads, 0, s>>>(a);
+        if (b->n_yitems > 0) b->L.yfn<<<b->n_yitems, kZPassThreads, 0, s>>>(a);
+        if (b->n_zitems > 0) b->L.zfn<<<b->n_zitems, kZPassThreads, 0, s>>>(a);
+        if (b->n_citems > 0) b->L.fn<<<b->n_citems, 256, 0, s>>>(a);
+        return;
+    }
     if (b->L.zfn && b->n_zitems > 0) b->L.zfn<<<b->n_zitems, kZPassThreads, 0, s>>>(a);
     const int grid = b->sms * (b->L.ctas_per_sm > 0 ? b->L.ctas_per_sm : 1);
     b->L.fn<<<grid, b->L.tx * b->L.ty, b->L.smem, s>>>(a);
@@ -395,6 +498,9 @@ hydro_status hydro_batch_destroy(hydro_batch_t* b)
     cudaFree(b->counters);
     cudaFree(b->d_items);
     cudaFree(b->d_zitems);
+    cudaFree(b->d_xitems);
+    cudaFree(b->d_yitems);
+    cudaFree(b->d_citems);
     if (b->hctl) cudaFreeHost(b->hctl);
     delete b;
     return HYDRO_OK;
@@ -446,7 +552,10 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
         total += (cfgs[0].split ? 36 : 27) * b->ev[i].fs;
         // z-face fluxes for the z-pass variants (global Lax-Friedrichs)
         b->ev[i].fzs = cfgs[0].split ? 0 : ((long long)cfgs[i].n[0] * cfgs[i].n[1] * (cfgs[i].n[2] + 1) + 31) / 32 * 32;
-        total += 5 * b->ev[i].fzs;
+        // x- and y-face fluxes for the three-pass variants (global Lax-Friedrichs)
+        b->ev[i].fxs = cfgs[0].split ? 0 : ((long long)(cfgs[i].n[0] + 1) * cfgs[i].n[1] * cfgs[i].n[2] + 31) / 32 * 32;
+        b->ev[i].fys = cfgs[0].split ? 0 : ((long long)cfgs[i].n[0] * (cfgs[i].n[1] + 1) * cfgs[i].n[2] + 31) / 32 * 32;
+        total += 5 * (b->ev[i].fzs + b->ev[i].fxs + b->ev[i].fys);
     }
     if ((e = cudaMalloc(&b->buf, sizeof(double) * (size_t)total)) != cudaSuccess) return bail(bcuda(b, e, "event buffers"));
     if ((e = cudaMalloc(&b->ctl, sizeof(Ctl) * n_events)) != cudaSuccess) return bail(bcuda(b, e, "control blocks"));
@@ -465,6 +574,10 @@ hydro_status hydro_batch_create(const hydro_config* cfgs, int32_t n_events, void
         off += (c.split ? 36 : 27) * E.fs;
         E.fz = E.fzs ? b->buf + off : nullptr;
         off += 5 * E.fzs;
+        E.fx = E.fxs ? b->buf + off : nullptr;
+        off += 5 * E.fxs;
+        E.fy = E.fys ? b->buf + off : nullptr;
+        off += 5 * E.fys;
         for (int d = 0; d < 3; ++d) {
             E.n[d] = c.n[d];
             E.bc[d] = c.bc[d];
@@ -626,6 +739,7 @@ int32_t hydro_batch_size(hydro_batch_t* b) { return b ? b->n_events : 0; }
 int32_t hydro_batch_kernels_per_step(hydro_batch_t* b)
 {
     if (!b) return 0;
+    if (b->L.combine) return 2 + 3 * (1 + (b->n_xitems > 0) + (b->n_yitems > 0) + (b->n_zitems > 0));
     return 2 + 3 * ((b->L.zfn && b->n_zitems > 0) ? 2 : 1);
 }
 

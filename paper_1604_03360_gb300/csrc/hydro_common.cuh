@@ -131,6 +131,9 @@ inline long long zpass_blocks(int nx, int ny) { return ((long long)nx * ny + 31)
 // charw: characteristic-wise reconstruction (hydro_char.cu; split must be 0).
 int launch_variant_count(int R, int split, int nq, int charw = 0);
 int default_launch_variant(int R, int split, int nq, int charw = 0);
+// the 16x16 z-pass stage kernel with two CTAs per SM (component-wise WENO,
+// global LF): the adjoint's forward launch when the handle runs three passes
+int zpass_launch_variant(int R);
 // the fastest variant that keeps the z faces in the stage kernel (no z pass):
 // for launch paths without a z-flux buffer (adjoint, no-alloc)
 int fused_launch_variant(int R, int split, int nq, int charw = 0);

@@ -147,19 +147,30 @@ static cudaError_t info_for(StageLaunch* out)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, fn, TX * TY, out->smem);
 }
 
-// three-pass stage: x, y and z passes, then the per-cell combination
-template <int R, int ZEMU>
+// three-pass stage: x, y and z passes, then the per-cell combination (LLF:
+// local Lax-Friedrichs passes, and the combination also stores the speeds)
+template <int R, int ZEMU, bool LLF = false, int MINB = 0>
 static cudaError_t info_for_three(StageLaunch* out)
 {
-    out->fn = stage_combine_kernel<5>;
-    out->xfn = axis_flux_kernel<R, ZEMU, 0>;
-    out->yfn = axis_flux_kernel<R, ZEMU, 1>;
-    out->zfn = zflux_kernel<R, ZEMU>;
+    out->fn = stage_combine_kernel<5, LLF>;
+    if constexpr (LLF) {
+        out->xfn = axis_flux_llf_kernel<R, ZEMU, 0>;
+        out->yfn = axis_flux_llf_kernel<R, ZEMU, 1>;
+        out->zfn = zflux_llf_kernel<R, ZEMU>;
+    } else if constexpr (MINB > 0) {
+        out->xfn = axis_flux_kernel<R, ZEMU, 0, MINB>;
+        out->yfn = axis_flux_kernel<R, ZEMU, 1, MINB>;
+        out->zfn = axis_flux_kernel<R, ZEMU, 2, MINB>;
+    } else {
+        out->xfn = axis_flux_kernel<R, ZEMU, 0>;
+        out->yfn = axis_flux_kernel<R, ZEMU, 1>;
+        out->zfn = zflux_kernel<R, ZEMU>;
+    }
     out->combine = true;
     out->smem = 0;
     out->tx = 16;
     out->ty = 16;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_combine_kernel<5>, 256, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_combine_kernel<5, LLF>, 256, 0);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -238,7 +249,7 @@ cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const doubl
 // (same occupancy, for comparison) and the 16x16 tile with TMA staging (its
 // raw tile leaves room for one CTA per SM): WENO5 9, 10, 11; WENO7 10, 11, 12.
 // Three-pass (x, y and z passes, then the per-cell combination): WENO5 12,
-// WENO7 13.
+// WENO7 13; WENO7 14 the same with the passes at four CTAs per SM.
 // Variants 4 (WENO5) and 3 (WENO7) keep every product on the FP64 unit (the
 // bitwise reference); the others take the default of default_emu.  WENO5 7, 8 /
 // WENO7 6, 7: the 16x16 pencil sweep with the z faces from a separate z pass
@@ -253,13 +264,16 @@ cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const doubl
 // (four), WENO7 1 16x16 and 2 16x8.
 // Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
 // the launch a grid gets before any tuning: the fastest on the 256^3 workload
-// (the z-pass variant; a handle that cannot run it keeps the fused one)
+// (the three-pass variant, for component-wise WENO with global or local LF; a
+// handle that cannot run it keeps the fused one)
 int default_launch_variant(int R, int split, int nq, int charw)
 {
     if (charw || R == 2 || nq > 1) return 0;
-    if (split) return R == 3 ? 2 : 1;   // local LF with the z pass, 16x16
-    return R == 3 ? 8 : 7;
+    if (split) return R == 3 ? 4 : 3;   // local LF, three-pass
+    return R == 3 ? 12 : 13;            // three-pass
 }
+
+int zpass_launch_variant(int R) { return R == 3 ? 8 : 7; }
 
 int fused_launch_variant(int R, int split, int nq, int charw)
 {
@@ -270,7 +284,7 @@ int fused_launch_variant(int R, int split, int nq, int charw)
 int batch_variant_count(int R, int split)
 {
     if (split == 1) return R == 3 ? 2 : 1;
-    return R == 3 ? 9 : 8;
+    return R == 3 ? 10 : 9;   // the last is the three-pass variant
 }
 
 int launch_variant_count(int R, int split, int nq, int charw)
@@ -278,8 +292,8 @@ int launch_variant_count(int R, int split, int nq, int charw)
     if (charw) return (R == 3 || R == 4) && split == 0 ? char_variant_count(R, nq) : 0;
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
-    if (split == 1) return R == 3 ? 4 : 3;
-    return R == 3 ? 13 : 14;
+    if (split == 1) return R == 3 ? 5 : 4;
+    return R == 3 ? 13 : 15;
 }
 
 template <int NF>
@@ -328,6 +342,8 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (R == 4 && v == 0) return info_for<4, 16, 8, 1, true>(out);
         if (R == 4 && v == 1) return info_for<4, 16, 16, 1, true, 5, kEmuConst, true, kZPassEmu7, 2>(out);
         if (R == 4 && v == 2) return info_for<4, 16, 8, 1, true, 5, kEmuConst, true, kZPassEmu7, 4>(out);
+        if (R == 3 && v == 4) return info_for_three<3, kZPassEmu5, true>(out);
+        if (R == 4 && v == 3) return info_for_three<4, kZPassEmu7, true>(out);
         return cudaErrorInvalidValue;
     }
     if (R == 3) {
@@ -361,6 +377,7 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 11) return info_for_tma<4, 16, 8, kEmuConst, kZPassEmu7, 3>(out);
         if (v == 12) return info_for_tma<4, 16, 16, kEmuConst, kZPassEmu7, 1>(out);
         if (v == 13) return info_for_three<4, kZPassEmu7>(out);
+        if (v == 14) return info_for_three<4, kZPassEmu7, false, 4>(out);
     }
     return cudaErrorInvalidValue;
 }

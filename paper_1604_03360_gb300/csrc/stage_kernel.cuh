@@ -976,9 +976,10 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_kernel(co
     zflux_item<R, EMU>(a, blockIdx.x, blockIdx.y);
 }
 
-// x and y passes of the three-pass variants (same CTA and occupancy as the z pass)
-template <int R, int EMU, int AX>
-__global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) axis_flux_kernel(const StageArgs a)
+// x and y passes of the three-pass variants (same CTA and occupancy as the z
+// pass); MINB > 0 asks for that many CTAs per SM instead
+template <int R, int EMU, int AX, int MINB = 0>
+__global__ void __launch_bounds__(kZPassThreads, MINB > 0 ? MINB : (R == 4 ? 3 : 4)) axis_flux_kernel(const StageArgs a)
 {
     axis_flux_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y);
 }
@@ -995,21 +996,24 @@ inline long long pass_blocks(int AX, int nx, int ny, int nzi)
 // combination, the primitives and the speeds of the new state, with the same
 // operations in the same order as step 4 of stage_tile (component-wise, global
 // Lax-Friedrichs, five fields), so the same bits.  Grid-stride over the
-// interior cells, x fastest.  (A template only so that every translation
-// unit including this header can share one definition.)
-template <int NF = 5>
-__global__ void __launch_bounds__(256) stage_combine_kernel(const StageArgs a)
+// interior cells, x fastest.
+//
+// combine_cells does cells i0, i0 + step, ... < i1 (flat index over the
+// interior cells, x fastest) and the speed reduction of the calling warps;
+// every thread of a warp must call it.  (Templates only so that every
+// translation unit including this header can share one definition.)
+template <int NF = 5, bool LLF = false>
+__device__ __forceinline__ void combine_cells(const StageArgs& a, long long i0, long long i1, long long step)
 {
     static_assert(NF == 5, "the three-pass variants carry five fields");
     const double dt = *a.dt;
     if (!(dt > 0.0)) return;
     const int nx = a.nx, ny = a.ny, nzi = a.zhi - a.zlo;
-    const long long plane = (long long)nx * ny, ncell = plane * nzi, fs = a.fs;
+    const long long plane = (long long)nx * ny, fs = a.fs;
     const long long yrow = (long long)nx * nzi;           // one y-face row of the fy buffer
     const bool ax0 = a.act[0] != 0, ax1 = a.act[1] != 0, ax2 = a.act[2] != 0;
     unsigned long long amax[3] = {0ull, 0ull, 0ull};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = i0; i < i1; i += step) {
         const int x = (int)(i % nx);
         const long long r = i / nx;
         const int y = (int)(r % ny), zi = (int)(r / ny);
@@ -1053,10 +1057,13 @@ __global__ void __launch_bounds__(256) stage_combine_kernel(const StageArgs a)
             for (int d = 0; d < 3; ++d) {
                 const unsigned long long b = (unsigned long long)__double_as_longlong(sp[d]);
                 amax[d] = b > amax[d] ? b : amax[d];
+                if constexpr (LLF) a.s_out[d * fs + q] = sp[d];
             }
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) a.w_out[k * fs + q] = 0.0;
+            if constexpr (LLF)
+                for (int d = 0; d < 3; ++d) a.s_out[d * fs + q] = 0.0;
             if (atomicCAS(a.status, 0, 4) == 0) *a.bad_cell = q;
         }
     }
@@ -1072,6 +1079,14 @@ __global__ void __launch_bounds__(256) stage_combine_kernel(const StageArgs a)
     }
 }
 
+template <int NF = 5, bool LLF = false>
+__global__ void __launch_bounds__(256) stage_combine_kernel(const StageArgs a)
+{
+    const long long ncell = (long long)a.nx * a.ny * (a.zhi - a.zlo);
+    combine_cells<NF, LLF>(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, ncell,
+                           (long long)gridDim.x * blockDim.x);
+}
+
 // z pass of a local Lax-Friedrichs stage: the z-face fluxes of the five
 // fields, each thread sweeping one (x, y, field) pencil over kZFaces faces.
 // Face p+1/2 splits with the largest z speed over its 2G cells p-G+1 .. p+G,
@@ -1080,38 +1095,77 @@ __global__ void __launch_bounds__(256) stage_combine_kernel(const StageArgs a)
 // planes) in registers, moves it by one plane per face and evaluates the face
 // exactly as the local-LF z ring of the stage kernel does (llf_face on the
 // same values), so both give the same bits.  Same grid and CTA as zflux_kernel.
-template <int R, int EMU>
-__device__ __forceinline__ void zflux_llf_item(const StageArgs& a, long long cb, int zch)
+// The same along any axis AX (pencils, faces and outputs as in
+// axis_flux_item): the raw window holds the flux f_AX, the state and the AX
+// speed of 2G cells, formed as the stage kernel's local-LF staging does.
+template <int R, int EMU, int AX>
+__device__ __forceinline__ void axis_flux_llf_item(const StageArgs& a, long long cb, int fch)
 {
     constexpr int G = R, W = 2 * R;
     if (!(*a.dt > 0.0)) return;
     const int k = threadIdx.x >> 5;
-    const long long plane = (long long)a.nx * a.ny, col = cb * 32 + (threadIdx.x & 31);
-    if (col >= plane) return;                    // no barriers below
-    const int f0 = zch * kZFaces, f1 = min(f0 + kZFaces, a.zhi - a.zlo + 1);
-    // raw z flux, state and z speed of field k at stored plane m (as raw_flux_rn)
+    const long long plane = (long long)a.nx * a.ny;
+    const int nzi = a.zhi - a.zlo;
+    const long long npen = AX == 2 ? plane : (AX == 1 ? (long long)a.nx * nzi : (long long)a.ny * nzi);
+    const long long pen = cb * 32 + (threadIdx.x & 31);
+    if (pen >= npen) return;                     // no barriers below
+    const int nax = AX == 2 ? nzi : (AX == 1 ? a.ny : a.nx);
+    const int f0 = fch * kZFaces, f1 = min(f0 + kZFaces, nax + 1);
+    long long base, step;
+    int lo, ncell_ax, bcax;
+    if constexpr (AX == 2) {
+        base = pen;
+        step = plane;
+        lo = a.zlo;
+        ncell_ax = a.nz;
+        bcax = a.bc[2];
+    } else if constexpr (AX == 1) {
+        base = (long long)(a.zlo + pen / a.nx) * plane + pen % a.nx;
+        step = a.nx;
+        lo = 0;
+        ncell_ax = a.ny;
+        bcax = a.bc[1];
+    } else {
+        base = (long long)(a.zlo + pen / a.ny) * plane + (pen % a.ny) * a.nx;
+        step = 1;
+        lo = 0;
+        ncell_ax = a.nx;
+        bcax = a.bc[0];
+    }
+    // raw flux, state and speed of field k at (stored) position m (as raw_flux_rn)
     auto raw_at = [&](int m, double& fv, double& uv, double& sv) {
-        const long long q = (long long)bc_map(m, a.nz, a.bc[2]) * plane + col;
+        const long long q = base + (long long)bc_map(m, ncell_ax, bcax) * step;
         const double uk = __ldg(a.u_in + k * a.fs + q);
         double f;
         if (k == 0) {
-            f = __ldg(a.u_in + 3 * a.fs + q);
+            f = __ldg(a.u_in + (1 + AX) * a.fs + q);
         } else {
-            f = __dmul_rn(uk, __ldg(a.w_in + 3 * a.fs + q));
-            if (k == 3) f = __dadd_rn(f, __ldg(a.w_in + q));
+            f = __dmul_rn(uk, __ldg(a.w_in + (1 + AX) * a.fs + q));
+            if (k == 1 + AX) f = __dadd_rn(f, __ldg(a.w_in + q));
         }
         fv = f;
         uv = uk;
-        sv = __ldg(a.s_in + 2 * a.fs + q);
+        sv = __ldg(a.s_in + AX * a.fs + q);
     };
-    // window of face p+1/2 (p = zlo+f-1): planes p-G+1 .. p+G
+    // window of face p+1/2 (p = lo+f-1): cells p-G+1 .. p+G
     double fw[W], uw[W], sw[W];
-    const int p0 = a.zlo + f0 - 1;
+    const int p0 = lo + f0 - 1;
 #pragma unroll
     for (int i = 0; i < W; ++i) raw_at(p0 - G + 1 + i, fw[i], uw[i], sw[i]);
-    double* out = a.fz + k * a.fzs + col;
+    double* out;
+    long long ostep;
+    if constexpr (AX == 2) {
+        out = a.fz + k * a.fzs + pen;
+        ostep = plane;
+    } else if constexpr (AX == 1) {
+        out = a.fy + k * a.fys + pen;
+        ostep = (long long)a.nx * nzi;
+    } else {
+        out = a.fx + k * a.fxs + pen * (a.nx + 1);
+        ostep = 1;
+    }
     for (int f = f0; f < f1; ++f) {
-        out[(long long)f * plane] = llf_face<R, EMU>(fw, uw, sw, 1, a.eps_s);
+        out[(long long)f * ostep] = llf_face<R, EMU>(fw, uw, sw, 1, a.eps_s);
         if (f + 1 < f1) {
 #pragma unroll
             for (int i = 0; i < W - 1; ++i) {
@@ -1119,15 +1173,28 @@ __device__ __forceinline__ void zflux_llf_item(const StageArgs& a, long long cb,
                 uw[i] = uw[i + 1];
                 sw[i] = sw[i + 1];
             }
-            raw_at(a.zlo + f + G, fw[W - 1], uw[W - 1], sw[W - 1]);
+            raw_at(lo + f + G, fw[W - 1], uw[W - 1], sw[W - 1]);
         }
     }
+}
+
+template <int R, int EMU>
+__device__ __forceinline__ void zflux_llf_item(const StageArgs& a, long long cb, int zch)
+{
+    axis_flux_llf_item<R, EMU, 2>(a, cb, zch);
 }
 
 template <int R, int EMU>
 __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_llf_kernel(const StageArgs a)
 {
     zflux_llf_item<R, EMU>(a, blockIdx.x, blockIdx.y);
+}
+
+// x and y passes of the local-LF three-pass variants
+template <int R, int EMU, int AX>
+__global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) axis_flux_llf_kernel(const StageArgs a)
+{
+    axis_flux_llf_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace hydro

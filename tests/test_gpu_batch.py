@@ -57,7 +57,8 @@ def test_batch_matches_oracle_and_single_grid(scheme):
             assert np.array_equal(h.get_state(), u), i
 
 
-@pytest.mark.parametrize("variant,zc", [(0, 8), (1, 16), (2, 5), (3, 12), (4, 10), (5, 7), (6, 9), (7, 11), (8, 13)])
+@pytest.mark.parametrize("variant,zc", [(0, 8), (1, 16), (2, 5), (3, 12), (4, 10), (5, 7), (6, 9), (7, 11), (8, 13),
+                                        (9, 0)])
 def test_batch_launch_variants(variant, zc):
     from paper_1604_03360_gb300 import HydroBatch
     ev = make_events(SIZES[:4], scheme=5, seed=950)
@@ -69,6 +70,27 @@ def test_batch_launch_variants(variant, zc):
         b.step(3)
         for i in range(len(ev)):
             assert np.all(field_errors(b.get_state(i)[0], refs[i]) <= TOL)
+
+
+@pytest.mark.parametrize("scheme,variant", [(5, 9), (7, 8)])
+def test_batch_three_pass_matches_single_grid_bitwise(scheme, variant):
+    """The batch's three-pass launch (x, y and z passes over every event's
+    pencils, then one combination item per block of cells) gives each event
+    exactly its single-grid result on the default (three-pass) launch."""
+    from paper_1604_03360_gb300 import Hydro, HydroBatch
+    ev = make_events(SIZES, scheme=scheme, seed=930)
+    with HydroBatch([g for g, _ in ev]) as b:
+        b.set_launch(variant, 0)
+        for i, (g, w) in enumerate(ev):
+            b.set_primitive(i, w)
+        b.step(4)
+        got = [b.get_state(i) for i in range(len(ev))]
+        assert b.kernels_per_step() == 2 + 3 * 4
+    for i, (g, w) in enumerate(ev):
+        with Hydro.from_grid(g) as h:
+            h.set_primitive(w)
+            h.step(4)
+            assert np.array_equal(h.get_state(), got[i][0]), i
 
 
 def test_batch_autotune_leaves_state_unchanged():
@@ -115,10 +137,13 @@ def test_batch_requires_every_event_loaded():
 def test_batch_ensemble_time_step_keeps_events_physical():
     """Eight events of the event-by-event configuration spanning the size
     range, 100 steps with the ensemble time step: all stay physical, reach
-    t = 2.25, and one of them matches the oracle after the full run."""
+    t = 2.25, the 48^3 event matches the oracle run here cell by cell, and the
+    160^3 event matches the oracle's stored full-length state (sampled cells,
+    field maxima, per-plane sums and maxima)."""
+    from full_length import MFL, check_against_stored
     from paper_1604_03360_gb300 import HydroBatch
-    sizes = [(48, 48, 48), (160, 160, 160), (48, 160, 96), (130, 57, 75), (64, 64, 160), (100, 100, 100),
-             (150, 49, 120), (77, 88, 99)]
+    sizes = MFL.BATCH_SIZES
+    assert sizes[0] == (48, 48, 48) and sizes[1] == (160, 160, 160)
     ev = [W.batch_event(i, sizes) for i in range(len(sizes))]
     with HydroBatch([g for g, _ in ev]) as b:
         for i, (g, w) in enumerate(ev):
@@ -132,6 +157,8 @@ def test_batch_ensemble_time_step_keeps_events_physical():
     g0, w0 = ev[0]
     ref = oracle.run(oracle_cfg(g0), oracle.prim2con(w0), 100)[0]
     assert np.all(field_errors(out[0][0], ref) <= TOL)
+    u1, t1, k1 = out[1]
+    check_against_stored(u1, t1, k1, "batch_event160_weno5")
 
 
 @pytest.mark.parametrize("scheme", [5, 7])

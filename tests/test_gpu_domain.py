@@ -101,7 +101,7 @@ def test_host_staging_thin_slabs_and_t_end():
     check(g, w, 4, 10, device=None, t_end=0.5 * tr)
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 2), (7, 1)])
+@pytest.mark.parametrize("scheme,variant", [(5, 2), (7, 1), (5, 4), (7, 3)])
 def test_local_lf_zpass_slabs(scheme, variant):
     """Local-LF slabs on the z-pass launch: the z pass reads the exchanged
     ghost planes of u, the primitives and the speeds."""

@@ -190,7 +190,7 @@ TMA_VARIANTS = {5: (10, 11), 7: (11, 12)}
 @pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5), (5, 6), (5, 7), (5, 8),
                                             (5, 9), (5, 10), (5, 11), (5, 12),
                                             (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5), (7, 6), (7, 7),
-                                            (7, 8), (7, 9), (7, 10), (7, 11), (7, 12), (7, 13)])
+                                            (7, 8), (7, 9), (7, 10), (7, 11), (7, 12), (7, 13), (7, 14)])
 def test_every_launch_variant(scheme, variant):
     """Every compiled CTA tile shape, with a short z chunk so several chunks
     meet inside the grid, matches the oracle (ragged tiles in x and y)."""
@@ -214,7 +214,7 @@ def test_every_launch_variant(scheme, variant):
 # the same CTA tile, (pencil sweep on the FP64 unit only, pencil sweep with
 # integer-pipe products) and (fused z faces, z faces from the z pass)
 SWEEP_PAIRS = {5: ((0, 2), (0, 3), (0, 4), (1, 5), (4, 6), (6, 7), (7, 8), (8, 12)),
-               7: ((0, 2), (0, 3), (1, 4), (3, 5), (5, 6), (6, 7), (7, 8), (8, 9), (7, 13))}
+               7: ((0, 2), (0, 3), (1, 4), (3, 5), (5, 6), (6, 7), (7, 8), (8, 9), (7, 13), (13, 14))}
 
 
 @pytest.mark.parametrize("scheme", [5, 7])
@@ -297,7 +297,7 @@ def test_kernels_per_step_follows_the_launch():
                        ((16, 1, 12), 13, 11), ((16, 16, 1), 13, 11)):
         g, w = W.lumpy(n=n, seed=5, scheme=7)
         with Hydro.from_grid(g) as h:
-            assert h.launch()[0] == 7          # the default launch
+            assert h.launch()[0] == 13         # the default launch (three-pass)
             h.set_launch(v)
             assert h.kernels_per_step() == want, (n, v)
 
@@ -347,7 +347,7 @@ def test_local_lf_periodic_and_ellipsoidal(scheme):
     assert_parity(g, w, 40)
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (7, 0), (7, 1), (7, 2)])
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (7, 0), (7, 1), (7, 2), (7, 3)])
 def test_local_lf_every_launch_variant(scheme, variant):
     from paper_1604_03360_gb300 import Hydro
     g, w = W.lumpy(n=(37, 29, 21), seed=78, scheme=scheme)
@@ -363,8 +363,8 @@ def test_local_lf_every_launch_variant(scheme, variant):
     assert np.all(field_errors(got, ref) <= TOL)
 
 
-# (ring variant, z-pass variant) of the local-LF stage kernel
-LLF_PAIRS = {5: ((0, 2), (1, 3)), 7: ((0, 1), (0, 2))}
+# (ring variant, z-pass or three-pass variant) of the local-LF launches
+LLF_PAIRS = {5: ((0, 2), (1, 3), (0, 4)), 7: ((0, 1), (0, 2), (0, 3))}
 
 
 @pytest.mark.parametrize("scheme", [5, 7])
@@ -373,7 +373,9 @@ LLF_PAIRS = {5: ((0, 2), (1, 3)), 7: ((0, 1), (0, 2))}
 def test_local_lf_zpass_matches_ring_bitwise(scheme, n, bc):
     """The local-LF z pass forms each z face from the same raw values with the
     same operations as the stage kernel's z ring, so both launches give the
-    same bits (ragged tiles, several z chunks, periodic and outflow z)."""
+    same bits (ragged tiles, several z chunks, periodic and outflow z); so do
+    the local-LF three-pass launches (x, y and z passes, then the combination
+    that also stores the speeds)."""
     from paper_1604_03360_gb300 import Hydro
     g, w = W.lumpy(n=n, seed=97, scheme=scheme)
     w = with_flow(g, w)

@@ -4,8 +4,9 @@ a fixed footprint).  The entry point keeps its intermediate buffers in a static
 device array of the library; here it is called through the C ABI on two
 consecutive calls and checked against hydro_step, the allocating entry point.
 Both run the same scheme with the same operations (the no-allocation path on
-the fused stage kernel, hydro_step on a z pass plus stage kernel, which agree
-bit for bit), so the results must be identical.
+the fused stage kernel, hydro_step on its default launch of separate x, y and
+z face passes and a per-cell combination, which agree bit for bit), so the
+results must be identical.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test."""

@@ -46,12 +46,12 @@ FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
 # launch variant, tile x, tile y).  roofline.frac = this count x cells / stage time /
 # the FP64 FMA issue rate measured in the same run: the FP64 pipe's
 # utilisation.  A launch without a capture reports null.
-NCU_FP64_INST_PER_CELL_STAGE = {(7, 13, 16, 16): 1422.7, (7, 7, 16, 16): 1745.3, (7, 6, 16, 16): 1729.6,
+NCU_FP64_INST_PER_CELL_STAGE = {(7, 16, 16, 16): 1364.6, (7, 15, 16, 16): 1425.1, (7, 13, 16, 16): 1422.7, (7, 7, 16, 16): 1745.3, (7, 6, 16, 16): 1729.6,
                                 (5, 12, 16, 16): 808.8, (5, 8, 16, 16): 896.2, (5, 7, 16, 16): 1023.7}
-NCU_DRAM_BYTES_PER_CELL_STAGE = {(7, 13, 16, 16): 505.8, (7, 7, 16, 16): 276.5, (7, 6, 16, 16): 270.1,
+NCU_DRAM_BYTES_PER_CELL_STAGE = {(7, 16, 16, 16): 679.3, (7, 15, 16, 16): 679.1, (7, 13, 16, 16): 505.8, (7, 7, 16, 16): 276.5, (7, 6, 16, 16): 270.1,
                                  (5, 12, 16, 16): 511.0, (5, 8, 16, 16): 273.5, (5, 7, 16, 16): 269.3}
 # FP64 pipe busy, time-weighted over the launches of one stage
-NCU_FP64_PIPE_BUSY = {(7, 13, 16, 16): 0.793, (7, 7, 16, 16): 0.849, (7, 6, 16, 16): 0.828,
+NCU_FP64_PIPE_BUSY = {(7, 16, 16, 16): 0.779, (7, 15, 16, 16): 0.813, (7, 13, 16, 16): 0.793, (7, 7, 16, 16): 0.849, (7, 6, 16, 16): 0.828,
                       (5, 12, 16, 16): 0.846, (5, 8, 16, 16): 0.809, (5, 7, 16, 16): 0.838}
 # Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
 # stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
@@ -702,7 +702,7 @@ def main():
                                              "products on the integer pipe, so this rate can exceed the FP64 peak"
                                              % FLOPS_PER_CELL_STAGE[args.scheme],
                          "kernel": ("x, y, z face passes + stage_combine_kernel"
-                                    if launch[0] == {5: 12, 7: 13}[args.scheme]
+                                    if launch[0] in {5: (12, 13, 14), 7: (13, 14, 15, 16, 17)}[args.scheme]
                                     else "zflux_kernel + stage_kernel") + " (WENO%d)" % args.scheme,
                          "stage_ms": stage_ms,
                          "peak_source": "FP64 FMA probe kernel measured in this run (hydro_measure_fp64_peak); "

@@ -299,7 +299,8 @@ struct AdjPencilJob {
     double* gmo;                        // out: adjoint of g-, same layout
     int n[3], d, phys, wv, bc;
     double hdx;
-    long long count;                    // threads: 5 fields x pencils
+    int nseg;                           // 1, or 2: each pencil's faces split in two halves
+    long long count;                    // threads: segments x 5 fields x pencils
 };
 struct AdjPencilArgs {
     AdjPencilJob job[3];
@@ -324,8 +325,19 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
     const int nd = J.n[d];
     const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
     const long long npen = (long long)J.n[da] * J.n[db];
-    const int k = (int)(tid / npen);
-    const long long pen = tid % npen;
+    const int seg = (int)(tid / (5 * npen));
+    const long long rem = tid % (5 * npen);
+    const int k = (int)(rem / npen);
+    const long long pen = rem % npen;
+    // faces j0 .. j1 of this segment (face j lies between cells j and j+1);
+    // with two segments the cells jm-G+1 .. jm+G-1 receive contributions from
+    // both, and (periodic) the G cells at each end from the other segment's
+    // ghost folds: those are accumulated by exactly two commutative adds into
+    // zeroed outputs, so the sums do not depend on the order
+    const bool split = J.nseg == 2;
+    const int jm = (nd - 1) / 2;
+    const int j0 = (split && seg == 1) ? jm : -1;
+    const int j1 = (split && seg == 0) ? jm - 1 : nd - 1;
     const int ph = J.phys;
     double* const gpo = J.gpo;
     double* const gmo = J.gmo;
@@ -355,16 +367,25 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
     double gpw[Wn], gmw[Wn], ap[Wn], am[Wn], lo_p[G], lo_m[G], hi_p[G], hi_m[G];
 #pragma unroll
     for (int i = 0; i < Wn; ++i) {
-        gval(-G + i, gpw[i], gmw[i]);
+        gval(j0 - G + 1 + i, gpw[i], gmw[i]);
         ap[i] = am[i] = 0.0;
     }
 #pragma unroll
     for (int i = 0; i < G; ++i) lo_p[i] = lo_m[i] = hi_p[i] = hi_m[i] = 0.0;
+    const bool periodic_split = split && bcd == 1;
+    auto shared_cell = [&](int m) {
+        return split && ((m >= jm - G + 1 && m <= jm + G - 1) || (periodic_split && (m < G || m >= nd - G)));
+    };
     auto emit = [&](int m, double vp, double vm) {
         if (m >= 0 && m < nd) {
             const long long q = base + (long long)m * stp;
-            gpo[k * fs + q] = vp;
-            gmo[k * fs + q] = vm;
+            if (shared_cell(m)) {
+                atomicAdd(gpo + k * fs + q, vp);
+                atomicAdd(gmo + k * fs + q, vm);
+            } else {
+                gpo[k * fs + q] = vp;
+                gmo[k * fs + q] = vm;
+            }
         } else if (m < 0) {
 #pragma unroll
             for (int i = 0; i < G; ++i)
@@ -375,8 +396,8 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
                 if (m == nd + i) { hi_p[i] += vp; hi_m[i] += vm; }
         }
     };
-    double lamL = 0.0;
-    for (int j = -1; j <= nd - 1; ++j) {
+    double lamL = j0 >= 0 ? lam[k * fs + base + (long long)j0 * stp] : 0.0;
+    for (int j = j0; j <= j1; ++j) {
         const double lamR = (j + 1 < nd) ? lam[k * fs + base + (long long)(j + 1) * stp] : 0.0;
         const double Fb = sc * (lamR - lamL);
         lamL = lamR;
@@ -390,21 +411,36 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
             ap[i] = ap[i + 1];
             am[i] = am[i + 1];
         }
-        if (j + 1 <= nd - 1) gval(j + G + 1, gpw[Wn - 1], gmw[Wn - 1]);
+        if (j + 1 <= j1) gval(j + G + 1, gpw[Wn - 1], gmw[Wn - 1]);
         ap[Wn - 1] = am[Wn - 1] = 0.0;
     }
-    // cells nd-G+1 .. nd+G-1 are complete
+    // cells j1-G+2 .. j1+G: complete (last segment) or shared with the next one
 #pragma unroll
-    for (int i = 0; i < Wn - 1; ++i) emit(nd - G + 1 + i, ap[i], am[i]);
-    // ghost cells fold back onto their source cells
+    for (int i = 0; i < Wn - 1; ++i) emit(j1 - G + 2 + i, ap[i], am[i]);
+    // ghost cells fold back onto their source cells (only the first segment has
+    // low ghosts, only the last high ones)
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-        const long long ql = base + (long long)bc_map(i - G, nd, bcd) * stp;
-        gpo[k * fs + ql] += lo_p[i];
-        gmo[k * fs + ql] += lo_m[i];
-        const long long qh = base + (long long)bc_map(nd + i, nd, bcd) * stp;
-        gpo[k * fs + qh] += hi_p[i];
-        gmo[k * fs + qh] += hi_m[i];
+        if (j0 == -1) {
+            const long long ql = base + (long long)bc_map(i - G, nd, bcd) * stp;
+            if (periodic_split) {
+                atomicAdd(gpo + k * fs + ql, lo_p[i]);
+                atomicAdd(gmo + k * fs + ql, lo_m[i]);
+            } else {
+                gpo[k * fs + ql] += lo_p[i];
+                gmo[k * fs + ql] += lo_m[i];
+            }
+        }
+        if (j1 == nd - 1) {
+            const long long qh = base + (long long)bc_map(nd + i, nd, bcd) * stp;
+            if (periodic_split) {
+                atomicAdd(gpo + k * fs + qh, hi_p[i]);
+                atomicAdd(gmo + k * fs + qh, hi_m[i]);
+            } else {
+                gpo[k * fs + qh] += hi_p[i];
+                gmo[k * fs + qh] += hi_m[i];
+            }
+        }
     }
 }
 
@@ -657,18 +693,18 @@ static StageArgs frozen_stage_at(const HandleView& v, AdjointWork* w, const doub
     a.bad_cell = &v.ctl->bad_cell;
     a.fz = v.fz;
     a.fzs = v.fzs;
+    a.fx = v.fx;
+    a.fxs = v.fxs;
+    a.fy = v.fy;
+    a.fys = v.fys;
     return a;
 }
 
-// one frozen or recorded stage on the adjoint's buffers: the z pass first
-// when the handle's launch has one, then the stage kernel
-static void forward_stage(const HandleView& v, const StageArgs& a, const dim3& grid)
+// one frozen or recorded stage on the adjoint's buffers, with the handle's
+// launch (face passes and combination, z pass and stage kernel, or fused)
+static void forward_stage(const HandleView& v, const StageArgs& a, const dim3&)
 {
-    if (v.L.zfn && a.act[2]) {
-        const dim3 zg((unsigned)zpass_blocks(v.cfg.n[0], v.cfg.n[1]), (v.cfg.n[2] + 1 + kZFaces - 1) / kZFaces);
-        v.L.zfn<<<zg, kZPassThreads, 0, v.stream>>>(a);
-    }
-    v.L.fn<<<grid, v.L.tx * v.L.ty, v.L.smem, v.stream>>>(a);
+    launch_stage_kernels(v.L, v.zc, a, v.sms, v.stream);
 }
 
 // segment storage: step i of the segment keeps its three stage inputs, each
@@ -786,6 +822,10 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
             a.bad_cell = &v.ctl->bad_cell;
             a.fz = v.fz;
             a.fzs = v.fzs;
+            a.fx = v.fx;
+            a.fxs = v.fxs;
+            a.fy = v.fy;
+            a.fys = v.fys;
             forward_stage(v, a, grid);
         }
         record_kernel<<<1, 1, 0, v.stream>>>(v.ctl, w->rec + 10 * (long long)n);
@@ -849,9 +889,18 @@ static hydro_status stage_adjoint(hydro_t* h, const HandleView& v, AdjointWork* 
             for (int e = 0; e < 3; ++e) J.n[e] = v.cfg.n[e];
             J.d = d;
         }
-        J.count = 5LL * (nc / v.cfg.n[d]);
+        // two segments per pencil where it is long enough for the shared cells
+        // of the middle and of the periodic ends not to overlap
+        J.nseg = v.cfg.n[d] >= 8 * v.R ? 2 : 1;
+        J.count = 5LL * J.nseg * (nc / v.cfg.n[d]);
         threads += J.count;
     }
+    // segmented jobs accumulate their shared cells with adds: zero those outputs
+    for (int i = 0; i < a.njob; ++i)
+        if (a.job[i].nseg == 2) {
+            ACK(h, cudaMemsetAsync(a.job[i].gpo, 0, sizeof(double) * 5 * fs, v.stream), "clear adjoint outputs");
+            ACK(h, cudaMemsetAsync(a.job[i].gmo, 0, sizeof(double) * 5 * fs, v.stream), "clear adjoint outputs");
+        }
     if (actmask & 1) {
         FieldMove in{};
         for (int f = 0; f < 5; ++f) {

@@ -134,38 +134,7 @@ static bool launch_fits(const hydro_t* h, const StageLaunch& L)
 // cudaGetLastError as usual.
 static cudaError_t launch_stage(const hydro_t* h, const StageLaunch& L, int zc, const StageArgs& a, cudaStream_t s)
 {
-    if (L.combine) {
-        // three-pass stage: every face flux by its axis pass, then the per-cell combination
-        const int nzi = h->zhi - h->zlo;
-        if (a.act[0])
-            L.xfn<<<dim3((unsigned)pass_blocks(0, a.nx, a.ny, nzi), (a.nx + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
-                    0, s>>>(a);
-        if (a.act[1])
-            L.yfn<<<dim3((unsigned)pass_blocks(1, a.nx, a.ny, nzi), (a.ny + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
-                    0, s>>>(a);
-        if (a.act[2])
-            L.zfn<<<dim3((unsigned)pass_blocks(2, a.nx, a.ny, nzi), (nzi + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
-                    0, s>>>(a);
-        const long long cells = (long long)a.nx * a.ny * nzi;
-        const long long want = (cells + 255) / 256, cap = (long long)h->sms * 8;
-        L.fn<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(a);
-        return cudaSuccess;
-    }
-    if (L.zfn && a.act[2]) {
-        const dim3 zg((unsigned)zpass_blocks(h->cfg.n[0], h->cfg.n[1]), (h->zhi - h->zlo + 1 + kZFaces - 1) / kZFaces);
-        L.zfn<<<zg, kZPassThreads, 0, s>>>(a);
-    }
-    const dim3 grid((h->cfg.n[0] + L.tx - 1) / L.tx, (h->cfg.n[1] + L.ty - 1) / L.ty, (h->zhi - h->zlo + zc - 1) / zc);
-    if (L.fn_tma) {
-        // tensor maps of this stage's input (host-side encoding, no GPU work)
-        TmaMaps m;
-        const cudaError_t e = encode_stage_maps(L, a.u_in, a.w_in, a.nx, a.ny, a.nz, a.fs, &m);
-        if (e != cudaSuccess) return e;
-        L.fn_tma<<<grid, L.tx * L.ty, L.smem, s>>>(a, m);
-        return cudaSuccess;
-    }
-    L.fn<<<grid, L.tx * L.ty, L.smem, s>>>(a);
-    return cudaSuccess;
+    return launch_stage_kernels(L, zc, a, h->sms, s);
 }
 
 static cudaError_t enqueue_step(hydro_t* h, cudaStream_t s)
@@ -214,18 +183,18 @@ hydro_status hydro_handle_view(hydro_t* h, HandleView* v)
     v->zc = h->zc;
     v->fz = nullptr;
     v->fzs = 0;
-    if (h->L.zfn && h->fz && !h->L.fn_tma && !h->L.combine && h->cfg.bc[2] != HYDRO_BC_HALO) {
-        // the adjoint's recorded forward runs the handle's z-pass launch on its
-        // own state buffers, with the handle's z-face buffer as scratch
+    v->fx = v->fy = nullptr;
+    v->fxs = v->fys = 0;
+    v->sms = h->sms;
+    if (h->L.zfn && h->fz && !h->L.fn_tma && (!h->L.combine || (h->fx && h->fy)) && h->cfg.bc[2] != HYDRO_BC_HALO) {
+        // the adjoint's recorded forward runs the handle's z-pass or three-pass
+        // launch on its own state buffers, with the handle's face buffers as scratch
         v->fz = h->fz;
         v->fzs = h->fzs;
-    } else if (h->L.combine && h->fz && h->cfg.bc[2] != HYDRO_BC_HALO &&
-               stage_launch_variant(h->R, h->cfg.split, h->cfg.nq, zpass_launch_variant(h->R), &v->L,
-                                    h->cfg.charwise) == cudaSuccess && v->L.zfn && !v->L.combine && !v->L.fn_tma) {
-        // a three-pass launch: the adjoint takes the default z-pass launch
-        v->fz = h->fz;
-        v->fzs = h->fzs;
-        v->zc = pick_zc(h->cfg.n[0], h->cfg.n[1], h->cfg.n[2], v->L, h->sms);
+        v->fx = h->fx;
+        v->fxs = h->fxs;
+        v->fy = h->fy;
+        v->fys = h->fys;
     } else if (h->L.zfn || h->L.fn_tma) {
         // otherwise the fastest variant that needs no z-face buffer
         cudaError_t e = stage_launch_variant(h->R, h->cfg.split, h->cfg.nq,
@@ -719,8 +688,12 @@ extern "C" hydro_status hydro_autotune(hydro_t* h, double* best_ms)
         // z chunks: balanced splits ceil(nz/k) and a fixed ladder; time the five
         // the wave-count model likes best
         std::vector<int> zs;
-        for (int k = 1; k <= 64; ++k) zs.push_back((nz + k - 1) / k);
-        for (int z : {8, 12, 16, 24, 32, 48, 64}) zs.push_back(z);
+        if (L.combine) {
+            zs.push_back(nz);     // three-pass launches have no z chunks: one trial
+        } else {
+            for (int k = 1; k <= 64; ++k) zs.push_back((nz + k - 1) / k);
+            for (int z : {8, 12, 16, 24, 32, 48, 64}) zs.push_back(z);
+        }
         std::vector<std::pair<double, int>> scored;
         const long long tiles = (long long)((h->cfg.n[0] + L.tx - 1) / L.tx) * ((h->cfg.n[1] + L.ty - 1) / L.ty);
         const long long conc = (long long)h->sms * (L.ctas_per_sm > 0 ? L.ctas_per_sm : 1);

@@ -782,6 +782,7 @@ hydro_status hydro_batch_autotune(hydro_batch_t* b, double* best_ms)
         for (int zc : zcs) {
             s = apply_batch_launch(b, v, zc);
             if (s) break;
+            if (b->L.combine && zc != zcs[0]) continue;   // three-pass launches have no z chunks
             const BatchArgs a = batch_args(b, 1);
             float ms = 0.f;
             for (int rep = 0; rep < 2; ++rep) {   // warm-up, then timed

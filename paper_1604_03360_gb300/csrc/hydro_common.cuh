@@ -122,6 +122,11 @@ struct StageLaunch {
 cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const double* w, int nx, int ny, int nz,
                               long long fs, TmaMaps* out);
 inline bool tma_layout_ok(int nx, int ny) { return nx % 2 == 0 && nx >= 2 && ny >= 1; }
+// the launches of one RK3 stage of the grid described by a (z planes zlo ..
+// zhi): face passes and the combination for a three-pass launch, else the z
+// pass if any and the stage kernel; zc planes per stage-kernel CTA.  Returns
+// an error only when a TMA-staged launch cannot build its tensor maps.
+cudaError_t launch_stage_kernels(const StageLaunch& L, int zc, const StageArgs& a, int sms, cudaStream_t s);
 // CTAs per face chunk of a z pass: 32 consecutive columns of the plane each
 inline long long zpass_blocks(int nx, int ny) { return ((long long)nx * ny + 31) / 32; }
 // Tile shapes compiled per scheme and splitting (index 0 is the default);
@@ -131,9 +136,6 @@ inline long long zpass_blocks(int nx, int ny) { return ((long long)nx * ny + 31)
 // charw: characteristic-wise reconstruction (hydro_char.cu; split must be 0).
 int launch_variant_count(int R, int split, int nq, int charw = 0);
 int default_launch_variant(int R, int split, int nq, int charw = 0);
-// the 16x16 z-pass stage kernel with two CTAs per SM (component-wise WENO,
-// global LF): the adjoint's forward launch when the handle runs three passes
-int zpass_launch_variant(int R);
 // the fastest variant that keeps the z faces in the stage kernel (no z pass):
 // for launch paths without a z-flux buffer (adjoint, no-alloc)
 int fused_launch_variant(int R, int split, int nq, int charw = 0);
@@ -206,8 +208,13 @@ struct HandleView {
     Ctl* ctl;
     StageLaunch L;                 // stage launch for the adjoint's own buffers: the
     int zc;                        // handle's z-pass launch (z faces in fz) or a fused one
-    double* fz;                    // the handle's z-face buffer (null with a fused launch)
-    long long fzs;
+    double* fz;                    // the handle's face buffers (null with a fused launch;
+    long long fzs;                 // fx, fy only with a three-pass launch)
+    double* fx;
+    long long fxs;
+    double* fy;
+    long long fys;
+    int sms;
 };
 hydro_status hydro_handle_view(hydro_t* h, HandleView* v);
 AdjointWork* hydro_handle_adjoint(hydro_t* h, bool create);

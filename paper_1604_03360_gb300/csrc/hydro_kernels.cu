@@ -149,7 +149,7 @@ static cudaError_t info_for(StageLaunch* out)
 
 // three-pass stage: x, y and z passes, then the per-cell combination (LLF:
 // local Lax-Friedrichs passes, and the combination also stores the speeds)
-template <int R, int ZEMU, bool LLF = false, int MINB = 0>
+template <int R, int ZEMU, bool LLF = false, int MINB = 0, int XMINB = MINB>
 static cudaError_t info_for_three(StageLaunch* out)
 {
     out->fn = stage_combine_kernel<5, LLF>;
@@ -158,7 +158,7 @@ static cudaError_t info_for_three(StageLaunch* out)
         out->yfn = axis_flux_llf_kernel<R, ZEMU, 1>;
         out->zfn = zflux_llf_kernel<R, ZEMU>;
     } else if constexpr (MINB > 0) {
-        out->xfn = axis_flux_kernel<R, ZEMU, 0, MINB>;
+        out->xfn = axis_flux_kernel<R, ZEMU, 0, XMINB>;
         out->yfn = axis_flux_kernel<R, ZEMU, 1, MINB>;
         out->zfn = axis_flux_kernel<R, ZEMU, 2, MINB>;
     } else {
@@ -213,6 +213,42 @@ static cudaError_t info_for_tma(StageLaunch* out)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, fn, TX * TY, out->smem);
 }
 
+cudaError_t launch_stage_kernels(const StageLaunch& L, int zc, const StageArgs& a, int sms, cudaStream_t s)
+{
+    const int nzi = a.zhi - a.zlo;
+    if (L.combine) {
+        // three-pass stage: every face flux by its axis pass, then the per-cell combination
+        if (a.act[0])
+            L.xfn<<<dim3((unsigned)pass_blocks(0, a.nx, a.ny, nzi), (a.nx + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
+                    0, s>>>(a);
+        if (a.act[1])
+            L.yfn<<<dim3((unsigned)pass_blocks(1, a.nx, a.ny, nzi), (a.ny + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
+                    0, s>>>(a);
+        if (a.act[2])
+            L.zfn<<<dim3((unsigned)pass_blocks(2, a.nx, a.ny, nzi), (nzi + 1 + kZFaces - 1) / kZFaces), kZPassThreads,
+                    0, s>>>(a);
+        const long long cells = (long long)a.nx * a.ny * nzi;
+        const long long want = (cells + 255) / 256, cap = (long long)sms * 8;
+        L.fn<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(a);
+        return cudaSuccess;
+    }
+    if (L.zfn && a.act[2]) {
+        const dim3 zg((unsigned)zpass_blocks(a.nx, a.ny), (nzi + 1 + kZFaces - 1) / kZFaces);
+        L.zfn<<<zg, kZPassThreads, 0, s>>>(a);
+    }
+    const dim3 grid((a.nx + L.tx - 1) / L.tx, (a.ny + L.ty - 1) / L.ty, (nzi + zc - 1) / zc);
+    if (L.fn_tma) {
+        // tensor maps of this stage's input (host-side encoding, no GPU work)
+        TmaMaps m;
+        const cudaError_t e = encode_stage_maps(L, a.u_in, a.w_in, a.nx, a.ny, a.nz, a.fs, &m);
+        if (e != cudaSuccess) return e;
+        L.fn_tma<<<grid, L.tx * L.ty, L.smem, s>>>(a, m);
+        return cudaSuccess;
+    }
+    L.fn<<<grid, L.tx * L.ty, L.smem, s>>>(a);
+    return cudaSuccess;
+}
+
 cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const double* w, int nx, int ny, int nz,
                               long long fs, TmaMaps* out)
 {
@@ -249,7 +285,12 @@ cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const doubl
 // (same occupancy, for comparison) and the 16x16 tile with TMA staging (its
 // raw tile leaves room for one CTA per SM): WENO5 9, 10, 11; WENO7 10, 11, 12.
 // Three-pass (x, y and z passes, then the per-cell combination): WENO5 12,
-// WENO7 13; WENO7 14 the same with the passes at four CTAs per SM.
+// WENO7 13 (passes at four / three CTAs per SM); WENO5 13, 14 with the
+// passes at five and six CTAs per SM, WENO7 14, 15 at four and five, and 16
+// at five with the face products of the passes on the integer pipe too, 17
+// with the x pass at four and the y and z passes at five.
+// (Passes with only the weight products, or only their squares, on the
+// integer pipe measured 6-10 % slower: the passes are bound by FP64 issue.)
 // Variants 4 (WENO5) and 3 (WENO7) keep every product on the FP64 unit (the
 // bitwise reference); the others take the default of default_emu.  WENO5 7, 8 /
 // WENO7 6, 7: the 16x16 pencil sweep with the z faces from a separate z pass
@@ -270,10 +311,9 @@ int default_launch_variant(int R, int split, int nq, int charw)
 {
     if (charw || R == 2 || nq > 1) return 0;
     if (split) return R == 3 ? 4 : 3;   // local LF, three-pass
-    return R == 3 ? 12 : 13;            // three-pass
+    return R == 3 ? 12 : 16;            // three-pass (WENO7: passes at five CTAs per SM, face
+                                        // products on the integer pipe too)
 }
-
-int zpass_launch_variant(int R) { return R == 3 ? 8 : 7; }
 
 int fused_launch_variant(int R, int split, int nq, int charw)
 {
@@ -293,7 +333,7 @@ int launch_variant_count(int R, int split, int nq, int charw)
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
     if (nq > 1) return 1;
     if (split == 1) return R == 3 ? 5 : 4;
-    return R == 3 ? 13 : 15;
+    return R == 3 ? 15 : 18;
 }
 
 template <int NF>
@@ -360,6 +400,9 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 10) return info_for_tma<3, 16, 8, kEmuConst | kEmuWeights, kZPassEmu5, 4>(out);
         if (v == 11) return info_for_tma<3, 16, 16, kEmuConst | kEmuWeights, kZPassEmu5, 1>(out);
         if (v == 12) return info_for_three<3, kZPassEmu5>(out);
+        if (v == 13) return info_for_three<3, kZPassEmu5, false, 5>(out);
+        if (v == 14) return info_for_three<3, kZPassEmu5, false, 6>(out);
+
     }
     if (R == 4) {
         if (v == 0) return info_for<4, 16, 16>(out);
@@ -378,6 +421,9 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         if (v == 12) return info_for_tma<4, 16, 16, kEmuConst, kZPassEmu7, 1>(out);
         if (v == 13) return info_for_three<4, kZPassEmu7>(out);
         if (v == 14) return info_for_three<4, kZPassEmu7, false, 4>(out);
+        if (v == 15) return info_for_three<4, kZPassEmu7, false, 5>(out);
+        if (v == 16) return info_for_three<4, kEmuConst | kEmuWeights | kEmuFace, false, 5>(out);
+        if (v == 17) return info_for_three<4, kZPassEmu7, false, 5, 4>(out);
     }
     return cudaErrorInvalidValue;
 }

@@ -153,10 +153,13 @@ struct Diff5 {
 
 // EMU selects operations that run on the integer pipe (fp64_int.cuh) instead
 // of the FP64 unit: kEmuConst the products with constants, kEmuWeights the
-// squares and products of the nonlinear weights, kEmuFace the last products of
-// the weighted sums and of the face combination.  Every choice gives the same
-// bits.
+// squares and products of the nonlinear weights, kEmuFace the last products
+// of the weighted sums and of the face combination.  Every choice gives the
+// same bits.
 constexpr int kEmuConst = 1, kEmuWeights = 2, kEmuFace = 4;
+// the squares / the products of the nonlinear weights on the integer pipe
+__host__ __device__ constexpr bool emu_wsq(int emu) { return (emu & kEmuWeights) != 0; }
+__host__ __device__ constexpr bool emu_wprod(int emu) { return (emu & kEmuWeights) != 0; }
 
 template <int EMU = 0>
 __device__ __forceinline__ void weno5_diffs(const double* v, Diff5& q)
@@ -218,9 +221,9 @@ __device__ __forceinline__ void weno5_core(const Diff5& q, double eps_s, double&
     const double b0 = fma(q.ks[0], q.s[0], fma(t0, t0, eps_s));
     const double b1 = fma(q.ks[1], q.s[1], fma(t1, t1, eps_s));
     const double b2 = fma(q.ks[2], q.s[2], fma(t2, t2, eps_s));
-    constexpr bool EW = (EMU & kEmuWeights) != 0;
-    const double w0 = xmul<EW>(b0, b0), w1 = xmul<EW>(b1, b1), w2 = xmul<EW>(b2, b2);
-    const double P0 = xmul<EW>(w1, w2), P1 = xmul<EW>(w0, w2), P2 = xmul<EW>(w0, w1);
+    constexpr bool ES = emu_wsq(EMU), EP = emu_wprod(EMU);
+    const double w0 = xmul<ES>(b0, b0), w1 = xmul<ES>(b1, b1), w2 = xmul<ES>(b2, b2);
+    const double P0 = xmul<EP>(w1, w2), P1 = xmul<EP>(w0, w2), P2 = xmul<EP>(w0, w1);
     // 10 d_k (q_k - c), c = v[2]: d = (1, 6, 3)/10, q0 = (2a-7b+11c)/6 =
     // c - d0/3 + 5 d1/6, q1 = (-b+5c+2d)/6 = c + (d1 + 2 d2)/6,
     // q2 = (2c+5d-e)/6 = c + (4 d2 - d3)/6
@@ -328,10 +331,10 @@ __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
     const double b1 = fma(A1, A1, fma(b39, B12, q.ct[1]));
     const double b2 = fma(A2, A2, fma(b39, B12, q.ct[2]));
     const double b3 = fma(A3, A3, fma(xmul_small<EC, 39, 6, 0>(B3), B3, q.ct[3]));
-    constexpr bool EW = (EMU & kEmuWeights) != 0;
-    const double w0 = xmul<EW>(b0, b0), w1 = xmul<EW>(b1, b1), w2 = xmul<EW>(b2, b2), w3 = xmul<EW>(b3, b3);
-    const double p01 = xmul<EW>(w0, w1), p23 = xmul<EW>(w2, w3);
-    const double P0 = xmul<EW>(w1, p23), P1 = xmul<EW>(w0, p23), P2 = xmul<EW>(p01, w3), P3 = xmul<EW>(p01, w2);
+    constexpr bool ES = emu_wsq(EMU), EP = emu_wprod(EMU);
+    const double w0 = xmul<ES>(b0, b0), w1 = xmul<ES>(b1, b1), w2 = xmul<ES>(b2, b2), w3 = xmul<ES>(b3, b3);
+    const double p01 = xmul<EP>(w0, w1), p23 = xmul<EP>(w2, w3);
+    const double P0 = xmul<EP>(w1, p23), P1 = xmul<EP>(w0, p23), P2 = xmul<EP>(p01, w3), P3 = xmul<EP>(p01, w2);
     // 35 d_k (q_k - v3), d = (1, 12, 18, 4)/35, in the difference basis:
     // q0 - v3 = d0/4 - 5 d1/6 + 13 d2/12, q1 - v3 = (-d1 + 4 d2 + 3 d3)/12,
     // q2 - v3 = (d2 + 6 d3 - d4)/12, q3 - v3 = (9 d3 - 4 d4 + d5)/12

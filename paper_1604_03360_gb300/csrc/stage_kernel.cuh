@@ -840,8 +840,9 @@ __global__ void __launch_bounds__(TX * TY, MINB) stage_kernel_tma(const StageArg
 // zlo+f-1 and zlo+f (f = 0 .. zhi-zlo); its left-biased stencil is centred
 // on plane zlo+f-1, its right-biased one on plane zlo+f.
 constexpr int kZFaces = 64, kZPassThreads = 160;
-// integer-pipe products of the z pass (measured fastest: WENO5 all three
-// kinds, WENO7 without the face products)
+// integer-pipe products of the z pass of the fused launches (measured fastest:
+// WENO5 all three kinds, WENO7 without the face products; the WENO7 passes of
+// the three-pass launch are fastest with all three)
 constexpr int kZPassEmu5 = kEmuConst | kEmuWeights | kEmuFace, kZPassEmu7 = kEmuConst | kEmuWeights;
 
 // one pass item along axis AX: pencil block cb (32 consecutive pencils), face

@@ -53,6 +53,12 @@ def reference_vjp(g, u0, lam, nsteps):
     (5, (12, 11, 10), (1, 1, 1), 4, 3),
     (7, (8, 12, 1), (0, 0, 0), 2, 5),
     (5, (1, 13, 9), (0, 0, 0), 3, 2),
+    # pencils of at least 8r cells are swept in two segments whose shared
+    # cells (the middle, and with periodic boundaries the ends) are summed
+    (5, (27, 9, 8), (0, 0, 0), 3, 2),
+    (5, (9, 26, 8), (1, 1, 1), 3, 2),
+    (7, (8, 9, 35), (0, 0, 0), 2, 1),
+    (7, (33, 8, 9), (1, 1, 1), 2, 1),
 ])
 def test_adjoint_matches_torch_autograd(scheme, dims, bc, nsteps, ckpt):
     from paper_1604_03360_gb300 import Hydro

@@ -188,9 +188,10 @@ TMA_VARIANTS = {5: (10, 11), 7: (11, 12)}
 
 
 @pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (5, 5), (5, 6), (5, 7), (5, 8),
-                                            (5, 9), (5, 10), (5, 11), (5, 12),
+                                            (5, 9), (5, 10), (5, 11), (5, 12), (5, 13), (5, 14),
                                             (7, 0), (7, 1), (7, 2), (7, 3), (7, 4), (7, 5), (7, 6), (7, 7),
-                                            (7, 8), (7, 9), (7, 10), (7, 11), (7, 12), (7, 13), (7, 14)])
+                                            (7, 8), (7, 9), (7, 10), (7, 11), (7, 12), (7, 13), (7, 14),
+                                            (7, 15), (7, 16), (7, 17)])
 def test_every_launch_variant(scheme, variant):
     """Every compiled CTA tile shape, with a short z chunk so several chunks
     meet inside the grid, matches the oracle (ragged tiles in x and y)."""
@@ -213,8 +214,8 @@ def test_every_launch_variant(scheme, variant):
 # other shapes and face orders, (per-face variant, pencil-sweep variant) with
 # the same CTA tile, (pencil sweep on the FP64 unit only, pencil sweep with
 # integer-pipe products) and (fused z faces, z faces from the z pass)
-SWEEP_PAIRS = {5: ((0, 2), (0, 3), (0, 4), (1, 5), (4, 6), (6, 7), (7, 8), (8, 12)),
-               7: ((0, 2), (0, 3), (1, 4), (3, 5), (5, 6), (6, 7), (7, 8), (8, 9), (7, 13), (13, 14))}
+SWEEP_PAIRS = {5: ((0, 2), (0, 3), (0, 4), (1, 5), (4, 6), (6, 7), (7, 8), (8, 12), (12, 13), (13, 14)),
+               7: ((0, 2), (0, 3), (1, 4), (3, 5), (5, 6), (6, 7), (7, 8), (8, 9), (7, 13), (13, 14), (14, 15), (15, 16), (16, 17))}
 
 
 @pytest.mark.parametrize("scheme", [5, 7])
@@ -294,10 +295,10 @@ def test_kernels_per_step_follows_the_launch():
     combination; begin and end add two."""
     from paper_1604_03360_gb300 import Hydro
     for n, v, want in (((16, 16, 12), 7, 8), ((16, 16, 12), 5, 5), ((16, 16, 1), 7, 5), ((16, 16, 12), 13, 14),
-                       ((16, 1, 12), 13, 11), ((16, 16, 1), 13, 11)):
+                       ((16, 1, 12), 13, 11), ((16, 16, 1), 16, 11)):
         g, w = W.lumpy(n=n, seed=5, scheme=7)
         with Hydro.from_grid(g) as h:
-            assert h.launch()[0] == 13         # the default launch (three-pass)
+            assert h.launch()[0] == 16         # the default launch (three-pass)
             h.set_launch(v)
             assert h.kernels_per_step() == want, (n, v)
 

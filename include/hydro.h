@@ -321,7 +321,11 @@ hydro_status hydro_eval_rcp(const double* x, double* y, int64_t n, void* stream)
  *   run: segment by segment, the step-start states are recomputed from the
  *   checkpoint with frozen stages, then each step's three stage adjoints run
  *   in reverse.  lambda_final and grad_u0: 5 fields with field_stride, in
- *   `mem`.  Synchronises.  HYDRO_ERR_STATE if nothing was recorded.
+ *   `mem`.  Synchronises.  HYDRO_ERR_STATE if nothing was recorded.  The
+ *   environment variable HYDRO_ADJ_PENCIL=<0..5>, read at each call, selects
+ *   a variant of the reverse-WENO pencil kernel (integer-pipe products, CTAs
+ *   per SM) for timing; all give the same bits, and other values select the
+ *   default.
  * hydro_recorded_steps: number of recorded steps and (either may be NULL)
  *   the speeds alpha[n][stage][axis] (9 per step) and dt[n].  Synchronises.
  * hydro_eps2: momentum anisotropy eps_2 = sum(T^xx - T^yy) / sum(T^xx + T^yy)

@@ -25,6 +25,7 @@
 // there as the slowest axis by the same kernel, and their outputs transposed
 // back: the same operations on the same operands, so the same bits.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -35,177 +36,82 @@
 namespace hydro {
 
 // ---------------------------------------------------------------- WENO VJPs
-// Linear forms of the scaled reconstructions (same definitions as weno5 /
-// weno7 in hydro_math.cuh): b_k = eps_s + c1 L1_k^2 + c2 L2_k^2 (+ c3 L3_k^2),
-// w_k = b_k^2, N = sum n_k prod_{m!=k} w_m, D = sum dc_k prod_{m!=k} w_m,
-// value = N / D.  vb += Rbar * d(N/D)/dv.
-template <int R>
-struct WenoForms;
-
-template <>
-struct WenoForms<3> {
-    static constexpr int S = 5, NL = 2;
-    __device__ static double L(int l, int k, int i)
-    {
-        // l = 0: first-derivative form t_k; l = 1: second difference s_k
-        const double t[3][5] = {{1, -4, 3, 0, 0}, {0, -1, 0, 1, 0}, {0, 0, -3, 4, -1}};
-        const double s[3][5] = {{1, -2, 1, 0, 0}, {0, 1, -2, 1, 0}, {0, 0, 1, -2, 1}};
-        return l == 0 ? t[k][i] : s[k][i];
-    }
-    __device__ static double n(int k, int i)
-    {
-        const double c[3][5] = {{1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0, 0}, {0, -1, 5, 2, 0}, {0, 0, 1, 2.5, -0.5}};
-        return c[k][i];
-    }
-    __device__ static double c(int l) { return l == 0 ? 1.0 : 13.0 / 3.0; }
-    __device__ static double dc(int k) { return k == 0 ? 1.0 : (k == 1 ? 6.0 : 3.0); }
-};
-
-template <>
-struct WenoForms<4> {
-    static constexpr int S = 7, NL = 3;
-    __device__ static double L(int l, int k, int i)
-    {
-        const double A[4][7] = {{-2, 9, -18, 11, 0, 0, 0}, {0, 1, -6, 3, 2, 0, 0}, {0, 0, -2, -3, 6, -1, 0},
-                                {0, 0, 0, -11, 18, -9, 2}};
-        const double B[4][7] = {{-1, 4, -5, 2, 0, 0, 0}, {0, 0, 1, -2, 1, 0, 0}, {0, 0, 1, -2, 1, 0, 0},
-                                {0, 0, 0, 2, -5, 4, -1}};
-        const double C[4][7] = {{-1, 3, -3, 1, 0, 0, 0}, {0, -1, 3, -3, 1, 0, 0}, {0, 0, -1, 3, -3, 1, 0},
-                                {0, 0, 0, -1, 3, -3, 1}};
-        return l == 0 ? A[k][i] : (l == 1 ? B[k][i] : C[k][i]);
-    }
-    __device__ static double n(int k, int i)
-    {
-        const double c[4][7] = {{-0.25, 13.0 / 12.0, -23.0 / 12.0, 25.0 / 12.0, 0, 0, 0},
-                                {0, 1, -5, 13, 3, 0, 0},
-                                {0, 0, -1.5, 10.5, 10.5, -1.5, 0},
-                                {0, 0, 0, 1, 13.0 / 3.0, -5.0 / 3.0, 1.0 / 3.0}};
-        return c[k][i];
-    }
-    __device__ static double c(int l) { return l == 0 ? 1.0 : (l == 1 ? 39.0 : 781.0 / 20.0); }
-    __device__ static double dc(int k) { return k == 0 ? 1.0 : (k == 1 ? 12.0 : (k == 2 ? 18.0 : 4.0)); }
-};
-
-template <int R>
-__device__ __forceinline__ void weno_left_vjp(const double* v, double eps_s, double Rbar, double* vb)
+// The scaled reconstructions of weno5 / weno7 (hydro_math.cuh), written in
+// their difference bases: b_k = eps_s + (smoothness forms)^2, w_k = b_k^2,
+// P_k = prod_{m!=k} w_m, N = sum n_k P_k, D = sum dc_k P_k, value = N / D.
+// vb (+)= Rbar * d(N/D)/dv: the forward values once, then the reverse sweep
+// N, D -> P -> w -> b -> (smoothness forms, n) -> v.  EMU selects products
+// computed on the integer pipe (fp64_int.cuh; the same bits): kEmuConst the
+// products with constants, kEmuWeights those of w and P and their reverse
+// (wbar), kEmuFace the other products of the reverse sweep.  ACC: accumulate
+// into vb[0 .. 2R-3] (else overwrite them); vb[2R-2], the newest cell of a
+// sliding window, is always overwritten.  Checked against complex-step derivatives of
+// the forward formulas (1e-14 WENO5, 2e-14 WENO7).
+// x * y on the integer pipe (E) or the FP64 unit; the FP64 product is never
+// contracted into an FMA with a later add, so both give the same bits
+template <bool E>
+__device__ __forceinline__ double pmul(double x, double y)
 {
-    using F = WenoForms<R>;
-    constexpr int S = F::S, NL = F::NL;
-    double Lf[NL][R], nk[R], b[R], w[R], P[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        double bk = eps_s;
-#pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            double x = 0.0;
-#pragma unroll
-            for (int i = 0; i < S; ++i)
-                if (F::L(l, k, i) != 0.0) x = fma(F::L(l, k, i), v[i], x);
-            Lf[l][k] = x;
-            bk = fma(F::c(l) * x, x, bk);
-        }
-        double y = 0.0;
-#pragma unroll
-        for (int i = 0; i < S; ++i)
-            if (F::n(k, i) != 0.0) y = fma(F::n(k, i), v[i], y);
-        nk[k] = y;
-        b[k] = bk;
-        w[k] = bk * bk;
-    }
-    double N = 0.0, D = 0.0;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        double p = 1.0;
-#pragma unroll
-        for (int m = 0; m < R; ++m)
-            if (m != k) p *= w[m];
-        P[k] = p;
-        N = fma(nk[k], p, N);
-        D = fma(F::dc(k), p, D);
-    }
-    const double iD = rcp(D);
-    const double Nb = Rbar * iD;
-    const double Db = -Nb * N * iD;
-    double Pb[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) Pb[k] = fma(Nb, nk[k], Db * F::dc(k));
-#pragma unroll
-    for (int m = 0; m < R; ++m) {
-        double wb = 0.0;
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if (k == m) continue;
-            double p = 1.0;
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                if (j != k && j != m) p *= w[j];
-            wb = fma(Pb[k], p, wb);
-        }
-        const double bb = 2.0 * b[m] * wb;
-        const double nb = Nb * P[m];
-#pragma unroll
-        for (int i = 0; i < S; ++i) {
-            double g = F::n(m, i) * nb;
-#pragma unroll
-            for (int l = 0; l < NL; ++l) g = fma(F::L(l, m, i) * 2.0 * F::c(l) * Lf[l][m], bb, g);
-            vb[i] += g;
-        }
-    }
+    if constexpr (E) return dmul_int(x, y);
+    else return __dmul_rn(x, y);
 }
 
-// WENO5 written out in the formulation of weno5 (difference basis for the
-// smoothness indicators): the forward values once, then the reverse sweep
-// N, D -> P -> w -> b -> (t, s, n) -> v.  About 100 FP64 operations against
-// 170 for the table-driven loops above.  Checked against complex-step
-// derivatives of the forward formula (1e-14).
-template <>
-__device__ __forceinline__ void weno_left_vjp<3>(const double* v, double eps_s, double Rbar, double* vb)
+template <bool ACC>
+__device__ __forceinline__ void vjp_out(double& dst, double x)
 {
+    if constexpr (ACC) dst += x;
+    else dst = x;
+}
+
+template <int EMU, bool ACC>
+__device__ __forceinline__ void weno5_vjp(const double* v, double eps_s, double Rbar, double* vb)
+{
+    constexpr bool EC = (EMU & kEmuConst) != 0, EW = (EMU & kEmuWeights) != 0, EF = (EMU & kEmuFace) != 0;
     const double d0 = v[1] - v[0], d1 = v[2] - v[1], d2 = v[3] - v[2], d3 = v[4] - v[3];
     const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2;
     const double t0 = fma(3.0, d1, -d0), t1 = d1 + d2, t2 = fma(3.0, d2, -d3);
-    // products with constants on the integer pipe (fp64_int.cuh; same bits):
-    // the FP64 unit is the bottleneck and 12 warps per SM hide the integer chains
-    const double ks0 = xmul<true>(13.0 / 3.0, s0), ks1 = xmul<true>(13.0 / 3.0, s1), ks2 = xmul<true>(13.0 / 3.0, s2);
+    const double ks0 = xmul<EC>(13.0 / 3.0, s0), ks1 = xmul<EC>(13.0 / 3.0, s1), ks2 = xmul<EC>(13.0 / 3.0, s2);
     const double b0 = fma(ks0, s0, fma(t0, t0, eps_s));
     const double b1 = fma(ks1, s1, fma(t1, t1, eps_s));
     const double b2 = fma(ks2, s2, fma(t2, t2, eps_s));
-    const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2;
-    const double P0 = w1 * w2, P1 = w0 * w2, P2 = w0 * w1;
+    const double w0 = pmul<EW>(b0, b0), w1 = pmul<EW>(b1, b1), w2 = pmul<EW>(b2, b2);
+    const double P0 = pmul<EW>(w1, w2), P1 = pmul<EW>(w0, w2), P2 = pmul<EW>(w0, w1);
     // candidates scaled by the linear weights (1, 6, 3)/10 x 10
-    const double n0 = fma(11.0 / 6.0, v[2], fma(-7.0 / 6.0, v[1], xmul<true>(1.0 / 3.0, v[0])));
+    const double n0 = fma(11.0 / 6.0, v[2], fma(-7.0 / 6.0, v[1], xmul<EC>(1.0 / 3.0, v[0])));
     const double n1 = fma(2.0, v[3], fma(5.0, v[2], -v[1]));
     const double n2 = fma(-0.5, v[4], fma(2.5, v[3], v[2]));
-    const double N = fma(n0, P0, fma(n1, P1, n2 * P2));
+    const double N = fma(n0, P0, fma(n1, P1, pmul<EF>(n2, P2)));
     const double D = fma(3.0, P2, fma(6.0, P1, P0));
     // reverse: value = N / D
     const double iD = rcp(D);
-    const double Nb = Rbar * iD;
-    const double Db = -Nb * (N * iD);
-    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, xmul_small<true, 3, 2, 1>(Db));
-    const double Pb2 = fma(Nb, n2, xmul_small<true, 3, 2, 0>(Db));
-    const double nb0 = Nb * P0, nb1 = Nb * P1, nb2 = Nb * P2;
+    const double Nb = pmul<EF>(Rbar, iD);
+    const double Db = -pmul<EF>(Nb, pmul<EF>(N, iD));
+    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, xmul_small<EC, 3, 2, 1>(Db));
+    const double Pb2 = fma(Nb, n2, xmul_small<EC, 3, 2, 0>(Db));
+    const double nb0 = pmul<EF>(Nb, P0), nb1 = pmul<EF>(Nb, P1), nb2 = pmul<EF>(Nb, P2);
     // w_k = b_k^2 enters every P_m with m != k
-    const double wb0 = fma(Pb1, w2, Pb2 * w1), wb1 = fma(Pb0, w2, Pb2 * w0), wb2 = fma(Pb0, w1, Pb1 * w0);
+    const double wb0 = fma(Pb1, w2, pmul<EW>(Pb2, w1)), wb1 = fma(Pb0, w2, pmul<EW>(Pb2, w0));
+    const double wb2 = fma(Pb0, w1, pmul<EW>(Pb1, w0));
     // b_k = eps + t_k^2 + 13/3 s_k^2: tbar = 4 t b wbar, sbar = 4 (13/3) s b wbar
-    const double q0 = xmul_pow2<true, 2>(b0) * wb0, q1 = xmul_pow2<true, 2>(b1) * wb1, q2 = xmul_pow2<true, 2>(b2) * wb2;
-    const double tb0 = t0 * q0, tb1 = t1 * q1, tb2 = t2 * q2;
-    const double sb0 = ks0 * q0, sb1 = ks1 * q1, sb2 = ks2 * q2;
+    const double q0 = pmul<EF>(xmul_pow2<EC, 2>(b0), wb0), q1 = pmul<EF>(xmul_pow2<EC, 2>(b1), wb1);
+    const double q2 = pmul<EF>(xmul_pow2<EC, 2>(b2), wb2);
+    const double tb0 = pmul<EF>(t0, q0), tb1 = pmul<EF>(t1, q1), tb2 = pmul<EF>(t2, q2);
+    const double sb0 = pmul<EF>(ks0, q0), sb1 = pmul<EF>(ks1, q1), sb2 = pmul<EF>(ks2, q2);
     // transposes of t_k, s_k and n_k written on the cell values
-    vb[0] += fma(1.0 / 3.0, nb0, tb0 + sb0);
-    vb[1] += fma(-7.0 / 6.0, nb0, fma(-4.0, tb0, fma(-2.0, sb0, sb1 - nb1 - tb1)));
-    vb[2] += fma(11.0 / 6.0, nb0, fma(5.0, nb1, fma(3.0, tb0 - tb2, fma(-2.0, sb1, nb2 + sb0 + sb2))));
-    vb[3] += fma(2.0, nb1, fma(2.5, nb2, fma(4.0, tb2, fma(-2.0, sb2, tb1 + sb1))));
-    vb[4] += fma(-0.5, nb2, sb2 - tb2);
+    vjp_out<ACC>(vb[0], fma(1.0 / 3.0, nb0, tb0 + sb0));
+    vjp_out<ACC>(vb[1], fma(-7.0 / 6.0, nb0, fma(-4.0, tb0, fma(-2.0, sb0, sb1 - nb1 - tb1))));
+    vjp_out<ACC>(vb[2], fma(11.0 / 6.0, nb0, fma(5.0, nb1, fma(3.0, tb0 - tb2, fma(-2.0, sb1, nb2 + sb0 + sb2)))));
+    vjp_out<ACC>(vb[3], fma(2.0, nb1, fma(2.5, nb2, fma(4.0, tb2, fma(-2.0, sb2, tb1 + sb1)))));
+    vb[4] = fma(-0.5, nb2, sb2 - tb2);
 }
 
-// WENO7 written out the same way: the forward values in the difference basis of
-// weno7 (A, B, C forms, b_k = eps + A^2 + 39 B^2 + 781/20 C^2), then the reverse
-// sweep N, D -> P -> w (leave-two-out products) -> b -> (A, B, C, n) -> (e, d) -> v.
-// Checked against complex-step derivatives of the forward formula (2e-14).
-template <>
-__device__ __forceinline__ void weno_left_vjp<4>(const double* v, double eps_s, double Rbar, double* vb)
+// WENO7 in the difference basis of weno7 (A, B, C forms, b_k = eps + A^2 +
+// 39 B^2 + 781/20 C^2); the reverse sweep takes the leave-two-out products
+// for wbar and (A, B, C, n) -> (e, d) -> v for the transposes.
+template <int EMU, bool ACC>
+__device__ __forceinline__ void weno7_vjp(const double* v, double eps_s, double Rbar, double* vb)
 {
+    constexpr bool EC = (EMU & kEmuConst) != 0, EW = (EMU & kEmuWeights) != 0, EF = (EMU & kEmuFace) != 0;
     constexpr double kc = 781.0 / 20.0;
     double d[6], e[5];
 #pragma unroll
@@ -218,38 +124,43 @@ __device__ __forceinline__ void weno_left_vjp<4>(const double* v, double eps_s, 
     const double A1 = fma(2.0, d[3], fma(5.0, d[2], -d[1]));
     const double A2 = fma(5.0, d[3], fma(2.0, d[2], -d[4]));
     const double A3 = fma(6.0, d[3], fma(-2.0, B3, -e[3]));
-    const double kB0 = 39.0 * B0, kB12 = 39.0 * B12, kB3 = 39.0 * B3;
-    const double kC0 = kc * C0, kC1 = kc * C1, kC2 = kc * C2, kC3 = kc * C3;
+    const double kB0 = xmul_small<EC, 39, 6, 0>(B0), kB12 = xmul_small<EC, 39, 6, 0>(B12);
+    const double kB3 = xmul_small<EC, 39, 6, 0>(B3);
+    const double kC0 = xmul<EC>(kc, C0), kC1 = xmul<EC>(kc, C1), kC2 = xmul<EC>(kc, C2), kC3 = xmul<EC>(kc, C3);
     const double b0 = fma(A0, A0, fma(kB0, B0, fma(kC0, C0, eps_s)));
     const double b1 = fma(A1, A1, fma(kB12, B12, fma(kC1, C1, eps_s)));
     const double b2 = fma(A2, A2, fma(kB12, B12, fma(kC2, C2, eps_s)));
     const double b3 = fma(A3, A3, fma(kB3, B3, fma(kC3, C3, eps_s)));
-    const double w0 = b0 * b0, w1 = b1 * b1, w2 = b2 * b2, w3 = b3 * b3;
-    const double w01 = w0 * w1, w23 = w2 * w3, w02 = w0 * w2, w03 = w0 * w3, w12 = w1 * w2, w13 = w1 * w3;
-    const double P0 = w1 * w23, P1 = w0 * w23, P2 = w01 * w3, P3 = w01 * w2;
+    const double w0 = pmul<EW>(b0, b0), w1 = pmul<EW>(b1, b1), w2 = pmul<EW>(b2, b2), w3 = pmul<EW>(b3, b3);
+    const double w01 = pmul<EW>(w0, w1), w23 = pmul<EW>(w2, w3), w02 = pmul<EW>(w0, w2);
+    const double w03 = pmul<EW>(w0, w3), w12 = pmul<EW>(w1, w2), w13 = pmul<EW>(w1, w3);
+    const double P0 = pmul<EW>(w1, w23), P1 = pmul<EW>(w0, w23), P2 = pmul<EW>(w01, w3), P3 = pmul<EW>(w01, w2);
     // candidates scaled by the linear weights (1, 12, 18, 4)/35 x 35
-    const double n0 = fma(25.0 / 12.0, v[3], fma(-23.0 / 12.0, v[2], fma(13.0 / 12.0, v[1], -0.25 * v[0])));
+    const double n0 = fma(25.0 / 12.0, v[3], fma(-23.0 / 12.0, v[2], fma(13.0 / 12.0, v[1], xmul_pow2<EC, -2>(-v[0]))));
     const double n1 = fma(3.0, v[4], fma(13.0, v[3], fma(-5.0, v[2], v[1])));
-    const double n2 = fma(10.5, v[3] + v[4], -1.5 * (v[2] + v[5]));
+    const double n2 = fma(10.5, v[3] + v[4], xmul_small<EC, 3, 2, -1>(-(v[2] + v[5])));
     const double n3 = fma(13.0 / 3.0, v[4], fma(-5.0 / 3.0, v[5], fma(1.0 / 3.0, v[6], v[3])));
-    const double N = fma(n0, P0, fma(n1, P1, fma(n2, P2, n3 * P3)));
+    const double N = fma(n0, P0, fma(n1, P1, fma(n2, P2, pmul<EF>(n3, P3))));
     const double D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
     // reverse: value = N / D
     const double iD = rcp(D);
-    const double Nb = Rbar * iD;
-    const double Db = -Nb * (N * iD);
-    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, 12.0 * Db);
-    const double Pb2 = fma(Nb, n2, 18.0 * Db), Pb3 = fma(Nb, n3, 4.0 * Db);
-    const double nb0 = Nb * P0, nb1 = Nb * P1, nb2 = Nb * P2, nb3 = Nb * P3;
-    const double wb0 = fma(Pb1, w23, fma(Pb2, w13, Pb3 * w12));
-    const double wb1 = fma(Pb0, w23, fma(Pb2, w03, Pb3 * w02));
-    const double wb2 = fma(Pb0, w13, fma(Pb1, w03, Pb3 * w01));
-    const double wb3 = fma(Pb0, w12, fma(Pb1, w02, Pb2 * w01));
+    const double Nb = pmul<EF>(Rbar, iD);
+    const double Db = -pmul<EF>(Nb, pmul<EF>(N, iD));
+    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, xmul_small<EC, 3, 2, 2>(Db));
+    const double Pb2 = fma(Nb, n2, xmul_small<EC, 9, 4, 1>(Db)), Pb3 = fma(Nb, n3, xmul_pow2<EC, 2>(Db));
+    const double nb0 = pmul<EF>(Nb, P0), nb1 = pmul<EF>(Nb, P1), nb2 = pmul<EF>(Nb, P2), nb3 = pmul<EF>(Nb, P3);
+    const double wb0 = fma(Pb1, w23, fma(Pb2, w13, pmul<EW>(Pb3, w12)));
+    const double wb1 = fma(Pb0, w23, fma(Pb2, w03, pmul<EW>(Pb3, w02)));
+    const double wb2 = fma(Pb0, w13, fma(Pb1, w03, pmul<EW>(Pb3, w01)));
+    const double wb3 = fma(Pb0, w12, fma(Pb1, w02, pmul<EW>(Pb2, w01)));
     // b_k = eps + A^2 + 39 B^2 + kc C^2: Abar = 4 A b wbar, Bbar = 4 (39 B) b wbar, ...
-    const double q0 = 4.0 * b0 * wb0, q1 = 4.0 * b1 * wb1, q2 = 4.0 * b2 * wb2, q3 = 4.0 * b3 * wb3;
-    const double Ab0 = A0 * q0, Ab1 = A1 * q1, Ab2 = A2 * q2, Ab3 = A3 * q3;
-    const double Bb0 = kB0 * q0, Bb1 = kB12 * q1, Bb2 = kB12 * q2, Bb3 = kB3 * q3;
-    const double Cb0 = kC0 * q0, Cb1 = kC1 * q1, Cb2 = kC2 * q2, Cb3 = kC3 * q3;
+    const double q0 = pmul<EF>(xmul_pow2<EC, 2>(b0), wb0), q1 = pmul<EF>(xmul_pow2<EC, 2>(b1), wb1);
+    const double q2 = pmul<EF>(xmul_pow2<EC, 2>(b2), wb2), q3 = pmul<EF>(xmul_pow2<EC, 2>(b3), wb3);
+    const double Ab0 = pmul<EF>(A0, q0), Ab1 = pmul<EF>(A1, q1), Ab2 = pmul<EF>(A2, q2), Ab3 = pmul<EF>(A3, q3);
+    const double Bb0 = pmul<EF>(kB0, q0), Bb1 = pmul<EF>(kB12, q1), Bb2 = pmul<EF>(kB12, q2);
+    const double Bb3 = pmul<EF>(kB3, q3);
+    const double Cb0 = pmul<EF>(kC0, q0), Cb1 = pmul<EF>(kC1, q1), Cb2 = pmul<EF>(kC2, q2);
+    const double Cb3 = pmul<EF>(kC3, q3);
     // transposes: (B, C) -> e, (A, e) -> d, d -> v, n -> v
     const double eb0 = -Bb0 - Cb0;
     const double eb1 = fma(2.0, Bb0, Cb0 - Cb1);
@@ -262,28 +173,37 @@ __device__ __forceinline__ void weno_left_vjp<4>(const double* v, double eps_s, 
     const double db3 = fma(2.0, Ab1, fma(5.0, Ab2, fma(11.0, Ab3, eb2 - eb3)));
     const double db4 = fma(-7.0, Ab3, (eb3 - eb4) - Ab2);
     const double db5 = fma(2.0, Ab3, eb4);
-    vb[0] += fma(-0.25, nb0, -db0);
-    vb[1] += fma(13.0 / 12.0, nb0, nb1 + (db0 - db1));
-    vb[2] += fma(-23.0 / 12.0, nb0, fma(-5.0, nb1, fma(-1.5, nb2, db1 - db2)));
-    vb[3] += fma(25.0 / 12.0, nb0, fma(13.0, nb1, fma(10.5, nb2, nb3 + (db2 - db3))));
-    vb[4] += fma(3.0, nb1, fma(10.5, nb2, fma(13.0 / 3.0, nb3, db3 - db4)));
-    vb[5] += fma(-1.5, nb2, fma(-5.0 / 3.0, nb3, db4 - db5));
-    vb[6] += fma(1.0 / 3.0, nb3, db5);
+    vjp_out<ACC>(vb[0], fma(-0.25, nb0, -db0));
+    vjp_out<ACC>(vb[1], fma(13.0 / 12.0, nb0, nb1 + (db0 - db1)));
+    vjp_out<ACC>(vb[2], fma(-23.0 / 12.0, nb0, fma(-5.0, nb1, fma(-1.5, nb2, db1 - db2))));
+    vjp_out<ACC>(vb[3], fma(25.0 / 12.0, nb0, fma(13.0, nb1, fma(10.5, nb2, nb3 + (db2 - db3)))));
+    vjp_out<ACC>(vb[4], fma(3.0, nb1, fma(10.5, nb2, fma(13.0 / 3.0, nb3, db3 - db4))));
+    vjp_out<ACC>(vb[5], fma(-1.5, nb2, fma(-5.0 / 3.0, nb3, db4 - db5)));
+    vb[6] = fma(1.0 / 3.0, nb3, db5);
 }
 
-template <int R>
+// the left-biased reconstruction of the face from the 2R-1 cells v
+template <int R, int EMU, bool ACC = true>
+__device__ __forceinline__ void weno_left_vjp(const double* v, double eps_s, double Rbar, double* vb)
+{
+    static_assert(R == 3 || R == 4, "WENO5 or WENO7");
+    if constexpr (R == 3) weno5_vjp<EMU, ACC>(v, eps_s, Rbar, vb);
+    else weno7_vjp<EMU, ACC>(v, eps_s, Rbar, vb);
+}
+
+// the right-biased one: the left form on the mirrored cells; vb[2R-2] is
+// overwritten, the others accumulate
+template <int R, int EMU>
 __device__ __forceinline__ void weno_right_vjp(const double* v, double eps_s, double Rbar, double* vb)
 {
     constexpr int S = 2 * R - 1;
     double m[S], mb[S];
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-        m[i] = v[S - 1 - i];
-        mb[i] = 0.0;
-    }
-    weno_left_vjp<R>(m, eps_s, Rbar, mb);
+    for (int i = 0; i < S; ++i) m[i] = v[S - 1 - i];
+    weno_left_vjp<R, EMU, false>(m, eps_s, Rbar, mb);
+    vb[S - 1] = mb[0];
 #pragma unroll
-    for (int i = 0; i < S; ++i) vb[S - 1 - i] += mb[i];
+    for (int i = 1; i < S; ++i) vb[S - 1 - i] += mb[i];
 }
 
 // ------------------------------------------------------------ adjoint kernels
@@ -311,8 +231,8 @@ struct AdjPencilArgs {
     double cb, eps_s;
 };
 
-template <int R>
-__global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
+template <int R, int EMU, int MINB>
+__global__ void __launch_bounds__(128, MINB) adj_pencil_kernel(const AdjPencilArgs a)
 {
     constexpr int G = R, Wn = 2 * R;
     // thread -> (job, field, pencil): the jobs' ranges follow one another
@@ -341,9 +261,9 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
     const int ph = J.phys;
     double* const gpo = J.gpo;
     double* const gmo = J.gmo;
-    const long long st[3] = {1, J.n[0], (long long)J.n[0] * J.n[1]};
-    const long long base = (pen % J.n[da]) * st[da] + (pen / J.n[da]) * st[db];
-    const long long stp = st[d];
+    auto stride = [&](int e) { return e == 0 ? 1LL : (e == 1 ? (long long)J.n[0] : (long long)J.n[0] * J.n[1]); };
+    const long long base = (pen % J.n[da]) * stride(da) + (pen / J.n[da]) * stride(db);
+    const long long stp = stride(d);
     const long long fs = a.fs;
     const double alpha = __longlong_as_double((long long)a.rec[3 * (a.stage - 1) + ph]);
     const double dt = __longlong_as_double((long long)a.rec[9]);
@@ -364,36 +284,54 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
         gpv = fma(alpha, uk, f);
         gmv = fma(-alpha, uk, f);
     };
-    double gpw[Wn], gmw[Wn], ap[Wn], am[Wn], lo_p[G], lo_m[G], hi_p[G], hi_m[G];
+    double gpw[Wn], gmw[Wn], ap[Wn], am[Wn];
 #pragma unroll
     for (int i = 0; i < Wn; ++i) {
         gval(j0 - G + 1 + i, gpw[i], gmw[i]);
         ap[i] = am[i] = 0.0;
     }
-#pragma unroll
-    for (int i = 0; i < G; ++i) lo_p[i] = lo_m[i] = hi_p[i] = hi_m[i] = 0.0;
-    const bool periodic_split = split && bcd == 1;
+    // Ghost contributions fold onto the cells they copy.  Cells are emitted
+    // in increasing order, ghosts below 0 first and above nd - 1 last, so:
+    // outflow sums the low ghosts in (lo_p, lo_m) and adds them to cell 0, and
+    // adds the high ghosts to cell nd - 1 after it is stored; periodic (one
+    // segment) stores the low ghosts into cells nd - G .. nd - 1, which then
+    // add their own values, and adds the high ghosts to cells 0 .. G - 1; with
+    // two segments every such cell is accumulated by atomic adds.
+    const bool periodic = bcd == 1;
+    const bool periodic_split = split && periodic;
+    double lo_p = 0.0, lo_m = 0.0;
     auto shared_cell = [&](int m) {
         return split && ((m >= jm - G + 1 && m <= jm + G - 1) || (periodic_split && (m < G || m >= nd - G)));
+    };
+    auto put = [&](long long q, double vp, double vm, int how) {   // how: 0 store, 1 add, 2 atomic add
+        double* const p = gpo + k * fs + q;
+        double* const n = gmo + k * fs + q;
+        if (how == 2) {
+            atomicAdd(p, vp);
+            atomicAdd(n, vm);
+        } else if (how == 1) {
+            *p += vp;
+            *n += vm;
+        } else {
+            *p = vp;
+            *n = vm;
+        }
     };
     auto emit = [&](int m, double vp, double vm) {
         if (m >= 0 && m < nd) {
             const long long q = base + (long long)m * stp;
-            if (shared_cell(m)) {
-                atomicAdd(gpo + k * fs + q, vp);
-                atomicAdd(gmo + k * fs + q, vm);
-            } else {
-                gpo[k * fs + q] = vp;
-                gmo[k * fs + q] = vm;
-            }
+            if (shared_cell(m)) put(q, vp, vm, 2);
+            else if (!periodic && m == 0) put(q, vp + lo_p, vm + lo_m, 0);
+            else put(q, vp, vm, periodic && m >= nd - G ? 1 : 0);
         } else if (m < 0) {
-#pragma unroll
-            for (int i = 0; i < G; ++i)
-                if (m == i - G) { lo_p[i] += vp; lo_m[i] += vm; }
+            if (!periodic) {
+                lo_p += vp;
+                lo_m += vm;
+            } else {
+                put(base + (long long)bc_map(m, nd, 1) * stp, vp, vm, periodic_split ? 2 : 0);
+            }
         } else {
-#pragma unroll
-            for (int i = 0; i < G; ++i)
-                if (m == nd + i) { hi_p[i] += vp; hi_m[i] += vm; }
+            put(base + (long long)bc_map(m, nd, bcd) * stp, vp, vm, periodic_split ? 2 : 1);
         }
     };
     double lamL = j0 >= 0 ? lam[k * fs + base + (long long)j0 * stp] : 0.0;
@@ -401,8 +339,9 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
         const double lamR = (j + 1 < nd) ? lam[k * fs + base + (long long)(j + 1) * stp] : 0.0;
         const double Fb = sc * (lamR - lamL);
         lamL = lamR;
-        weno_left_vjp<R>(gpw, a.eps_s, Fb, ap);           // cells j-G+1 .. j+G-1
-        weno_right_vjp<R>(gmw + 1, a.eps_s, Fb, am + 1);  // cells j-G+2 .. j+G
+        // the newest cell of each window receives its first contribution here
+        weno_left_vjp<R, EMU>(gpw, a.eps_s, Fb, ap);           // cells j-G+1 .. j+G-1
+        weno_right_vjp<R, EMU>(gmw + 1, a.eps_s, Fb, am + 1);  // cells j-G+2 .. j+G
         emit(j - G + 1, ap[0], am[0]);
 #pragma unroll
         for (int i = 0; i < Wn - 1; ++i) {
@@ -412,36 +351,10 @@ __global__ void __launch_bounds__(128) adj_pencil_kernel(const AdjPencilArgs a)
             am[i] = am[i + 1];
         }
         if (j + 1 <= j1) gval(j + G + 1, gpw[Wn - 1], gmw[Wn - 1]);
-        ap[Wn - 1] = am[Wn - 1] = 0.0;
     }
     // cells j1-G+2 .. j1+G: complete (last segment) or shared with the next one
 #pragma unroll
     for (int i = 0; i < Wn - 1; ++i) emit(j1 - G + 2 + i, ap[i], am[i]);
-    // ghost cells fold back onto their source cells (only the first segment has
-    // low ghosts, only the last high ones)
-#pragma unroll
-    for (int i = 0; i < G; ++i) {
-        if (j0 == -1) {
-            const long long ql = base + (long long)bc_map(i - G, nd, bcd) * stp;
-            if (periodic_split) {
-                atomicAdd(gpo + k * fs + ql, lo_p[i]);
-                atomicAdd(gmo + k * fs + ql, lo_m[i]);
-            } else {
-                gpo[k * fs + ql] += lo_p[i];
-                gmo[k * fs + ql] += lo_m[i];
-            }
-        }
-        if (j1 == nd - 1) {
-            const long long qh = base + (long long)bc_map(nd + i, nd, bcd) * stp;
-            if (periodic_split) {
-                atomicAdd(gpo + k * fs + qh, hi_p[i]);
-                atomicAdd(gmo + k * fs + qh, hi_m[i]);
-            } else {
-                gpo[k * fs + qh] += hi_p[i];
-                gmo[k * fs + qh] += hi_m[i];
-            }
-        }
-    }
 }
 
 // Fields between the x-fastest layout (x, then y, then z) and the x-slowest
@@ -639,6 +552,35 @@ __global__ void eps2_grad_kernel(const double* u, long long fs, long long ncell,
     }
 }
 
+// Pencil kernel variants, all with the same bits: integer-pipe products
+// (constants; + weights; + the reverse sweep's) and CTAs per SM.
+using AdjPencilFn = void (*)(const AdjPencilArgs);
+constexpr int kAdjPencilVariants = 6;
+template <int R>
+static AdjPencilFn adj_pencil_fn(int v)
+{
+    switch (v) {
+    case 0: return adj_pencil_kernel<R, kEmuConst, 0>;
+    case 2: return adj_pencil_kernel<R, kEmuConst | kEmuWeights | kEmuFace, 0>;
+    case 3: return adj_pencil_kernel<R, kEmuConst | kEmuFace, 0>;
+    case 4: return adj_pencil_kernel<R, kEmuConst | kEmuWeights | kEmuFace, 4>;
+    case 5: return adj_pencil_kernel<R, kEmuConst, 4>;
+    default: return adj_pencil_kernel<R, kEmuConst | kEmuWeights, 0>;
+    }
+}
+// HYDRO_ADJ_PENCIL=<variant> picks one (for timing them); otherwise variant 1,
+// the fastest at 96^3 (937 ms against 986 ms for the reverse sweep with the
+// constants alone on the integer pipe, 1005 ms with every product there)
+static int adj_pencil_variant()
+{
+    const char* e = getenv("HYDRO_ADJ_PENCIL");
+    if (e && *e) {
+        const int v = atoi(e);
+        if (v >= 0 && v < kAdjPencilVariants) return v;
+    }
+    return 1;
+}
+
 }  // namespace hydro
 
 // ------------------------------------------------------------------ host side
@@ -785,19 +727,41 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     Wp[1] = w->AW[1];
     Wp[2] = w->AW[2];
     const dim3 grid = stage_grid(v);
+    // the steps of the last segment keep their stage inputs in the segment
+    // storage, as its recomputation would (the same operations on the same
+    // operands, since the recorded speeds and steps are those used here), so
+    // the reverse sweep starts without recomputing it
+    const int last0 = (w->nckpt - 1) * ckpt_every;
+    w->seg_kept = false;
     for (int n = 0; n < nsteps; ++n) {
         if (n % ckpt_every == 0)
             ACK(h, cudaMemcpyAsync(w->CK + 5 * fs * (n / ckpt_every), v.U0, sizeof(double) * 5 * fs,
                                    cudaMemcpyDeviceToDevice, v.stream), "checkpoint");
+        const int i = n - last0;
+        if (i == 0) {
+            ACK(h, cudaMemcpyAsync(seg_u(w, 0, 0), v.U0, sizeof(double) * 5 * fs, cudaMemcpyDeviceToDevice, v.stream),
+                "segment start");
+            ACK(h, cudaMemcpyAsync(seg_w(w, 0, 0), v.W0, sizeof(double) * 4 * fs, cudaMemcpyDeviceToDevice, v.stream),
+                "segment start");
+        }
         step_begin_kernel<<<1, 1, 0, v.stream>>>(v.ctl, step_params(v.cfg));
         for (int st = 1; st <= 3; ++st) {
             StageArgs a{};
             const int in = st - 1;
-            a.u_in = U[in];
-            a.w_in = Wp[in];
-            a.u_n = U[0];
-            a.u_out = st == 3 ? U[0] : U[st];
-            a.w_out = st == 3 ? Wp[0] : Wp[st];
+            if (i >= 0) {
+                const bool last = n == nsteps - 1;
+                a.u_in = seg_u(w, i, in);
+                a.w_in = seg_w(w, i, in);
+                a.u_n = seg_u(w, i, 0);
+                a.u_out = st < 3 ? seg_u(w, i, st) : (last ? U[0] : seg_u(w, i + 1, 0));
+                a.w_out = st < 3 ? seg_w(w, i, st) : (last ? Wp[0] : seg_w(w, i + 1, 0));
+            } else {
+                a.u_in = U[in];
+                a.w_in = Wp[in];
+                a.u_n = U[0];
+                a.u_out = st == 3 ? U[0] : U[st];
+                a.w_out = st == 3 ? Wp[0] : Wp[st];
+            }
             a.fs = fs;
             a.nx = v.cfg.n[0];
             a.ny = v.cfg.n[1];
@@ -832,6 +796,7 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
         step_end_kernel<<<1, 1, 0, v.stream>>>(v.ctl);
     }
     ACK(h, cudaGetLastError(), "recorded forward");
+    w->seg_kept = true;
     return HYDRO_OK;
 }
 
@@ -918,8 +883,8 @@ static hydro_status stage_adjoint(hydro_t* h, const HandleView& v, AdjointWork* 
     }
     if (threads > 0) {
         const int blocks = (int)((threads + 127) / 128);
-        if (v.R == 3) adj_pencil_kernel<3><<<blocks, 128, 0, v.stream>>>(a);
-        else adj_pencil_kernel<4><<<blocks, 128, 0, v.stream>>>(a);
+        const auto fn = v.R == 3 ? adj_pencil_fn<3>(adj_pencil_variant()) : adj_pencil_fn<4>(adj_pencil_variant());
+        fn<<<blocks, 128, 0, v.stream>>>(a);
     }
     if (actmask & 1) {
         FieldMove out{};
@@ -962,11 +927,18 @@ extern "C" hydro_status hydro_adjoint(hydro_t* h, const double* lambda_final, do
     for (int seg = w->nckpt - 1; seg >= 0; --seg) {
         const int s0 = seg * C, s1 = (s0 + C < N) ? s0 + C : N;
         // the segment recomputed from its checkpoint with frozen stages; every
-        // stage input is kept (the last step's third stage is not needed)
-        ACK(h, cudaMemcpyAsync(seg_u(w, 0, 0), w->CK + 5 * fs * seg, sizeof(double) * 5 * fs, cudaMemcpyDeviceToDevice,
-                               v.stream), "restore");
-        prepare_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(seg_u(w, 0, 0), seg_w(w, 0, 0), fs, nc, v.cfg.cs2, w->ctl);
-        for (int n = s0; n < s1; ++n) {
+        // stage input is kept (the last step's third stage is not needed).
+        // The last segment's are still there from the recorded forward until
+        // another segment takes the storage.
+        const bool kept = w->seg_kept && seg == w->nckpt - 1;
+        if (!kept) {
+            w->seg_kept = false;
+            ACK(h, cudaMemcpyAsync(seg_u(w, 0, 0), w->CK + 5 * fs * seg, sizeof(double) * 5 * fs,
+                                   cudaMemcpyDeviceToDevice, v.stream), "restore");
+            prepare_kernel<<<cells_blocks(nc), 256, 0, v.stream>>>(seg_u(w, 0, 0), seg_w(w, 0, 0), fs, nc, v.cfg.cs2,
+                                                                   w->ctl);
+        }
+        for (int n = s0; n < s1 && !kept; ++n) {
             const int i = n - s0;
             for (int st = 1; st <= 3; ++st) {
                 if (st == 3 && n == s1 - 1) break;

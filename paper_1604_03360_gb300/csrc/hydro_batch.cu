@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) batch_zflux_ker
 {
     const int4 w = b.zitems[blockIdx.x];
     const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
-    zflux_item<R, EMU>(a, w.y, w.w);
+    zflux_item<R, EMU>(a, w.y, w.w, w.z);
 }
 
 // three-pass variants: x and y passes of all events (one CTA per item) and the
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) batch_axis_flux
 {
     const int4 w = (AX == 0 ? b.xitems : b.yitems)[blockIdx.x];
     const StageArgs a = batch_stage_args(b.ev[w.x], b.stage, b.zc);
-    axis_flux_item<R, EMU, AX>(a, w.y, w.w);
+    axis_flux_item<R, EMU, AX>(a, w.y, w.w, w.z);
 }
 
 constexpr int kCombineCells = 2048;
@@ -326,8 +326,8 @@ static hydro_status build_items(hydro_batch_t* b)
     b->n_items = (int)items.size();
     BCK(b, cudaMalloc(&b->d_items, sizeof(int4) * items.size()), "work-list");
     BCK(b, cudaMemcpy(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice), "work-list copy");
-    // z-pass items: (event, block of 32 consecutive columns of the plane, 0,
-    // chunk of kZFaces faces) of every event with an active z axis
+    // z-pass items: (event, block of 32 consecutive columns of the plane,
+    // faces per chunk, chunk) of every event with an active z axis
     if (b->d_zitems) {
         cudaFree(b->d_zitems);
         b->d_zitems = nullptr;
@@ -339,10 +339,10 @@ static hydro_status build_items(hydro_batch_t* b)
             const int* n = b->ev[e].n;
             if (!b->ev[e].act[2]) continue;
             const long long gc = zpass_blocks(n[0], n[1]);
-            const int gz = (n[2] + 1 + kZFaces - 1) / kZFaces;
+            const int gz = face_chunks(n[2] + 1), len = chunk_len(n[2] + 1, gz);
             if (gc > 0x7fffffffLL) return bfail(b, HYDRO_ERR_INVALID_ARG, "event too large for the z pass");
             for (int z = 0; z < gz; ++z)
-                for (long long c = 0; c < gc; ++c) zi.push_back(make_int4(e, (int)c, 0, z));
+                for (long long c = 0; c < gc; ++c) zi.push_back(make_int4(e, (int)c, len, z));
         }
         b->n_zitems = (int)zi.size();
         if (!zi.empty()) {
@@ -351,8 +351,8 @@ static hydro_status build_items(hydro_batch_t* b)
                 "z work-list copy");
         }
     }
-    // three-pass variants: x- and y-pass items (event, pencil block, 0, face
-    // chunk) of the events with that axis active, and the combination items
+    // three-pass variants: x- and y-pass items (event, pencil block, faces per
+    // chunk, chunk) of the events with that axis active, and the combination items
     // (event, block of kCombineCells cells)
     int4** dl[3] = {&b->d_xitems, &b->d_yitems, &b->d_citems};
     int* nl[3] = {&b->n_xitems, &b->n_yitems, &b->n_citems};
@@ -369,9 +369,9 @@ static hydro_status build_items(hydro_batch_t* b)
                 if (!E.act[ax]) continue;
                 const long long gc = pass_blocks(ax, E.n[0], E.n[1], E.n[2]);
                 if (gc > 0x7fffffffLL) return bfail(b, HYDRO_ERR_INVALID_ARG, "event too large for the face passes");
-                const int gf = (E.n[ax] + 1 + kZFaces - 1) / kZFaces;
+                const int gf = face_chunks(E.n[ax] + 1), len = chunk_len(E.n[ax] + 1, gf);
                 for (int f = 0; f < gf; ++f)
-                    for (long long c = 0; c < gc; ++c) li[ax].push_back(make_int4(e, (int)c, 0, f));
+                    for (long long c = 0; c < gc; ++c) li[ax].push_back(make_int4(e, (int)c, len, f));
             }
             const long long nb = (E.ncell + kCombineCells - 1) / kCombineCells;
             for (long long c = 0; c < nb; ++c) li[2].push_back(make_int4(e, (int)c, 0, 0));

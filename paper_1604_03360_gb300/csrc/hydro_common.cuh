@@ -122,6 +122,8 @@ struct StageLaunch {
 cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const double* w, int nx, int ny, int nz,
                               long long fs, TmaMaps* out);
 inline bool tma_layout_ok(int nx, int ny) { return nx % 2 == 0 && nx >= 2 && ny >= 1; }
+// face chunks of a pass over nf faces
+int pass_chunks(int nf);
 // the launches of one RK3 stage of the grid described by a (z planes zlo ..
 // zhi): face passes and the combination for a three-pass launch, else the z
 // pass if any and the stage kernel; zc planes per stage-kernel CTA.  Returns
@@ -193,6 +195,7 @@ struct AdjointWork {
     double *AU[3], *AW[3], *LAM, *OUT, *ACC, *V, *GP, *GM, *CK, *SEG;
     double* XT = nullptr;                  // x pencils in the x-slowest layout: u 5, p and v_x 2,
                                            // lambda 5, gbar+ 5, gbar- 5 (22 fields)
+    bool seg_kept = false;                 // SEG holds the last segment's stage inputs
     unsigned long long* rec = nullptr;     // nsteps x 10
     Ctl* ctl = nullptr;                    // scratch control block (speed sinks)
 };

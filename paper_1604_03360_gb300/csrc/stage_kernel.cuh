@@ -831,22 +831,34 @@ __global__ void __launch_bounds__(TX * TY, MINB) stage_kernel_tma(const StageArg
 }
 
 // z pass of a stage (ZEXT variants): the z-face fluxes of the five fields,
-// each thread sweeping one (x, y, field) pencil over a chunk of kZFaces faces
+// each thread sweeping one (x, y, field) pencil over a chunk of faces
 // with the stencil differences carried from face to face -- the same
 // operations on the same operands as the ring of the fused kernel, so the same
 // bits.  A CTA is 32 consecutive columns of the plane (flat index y nx + x,
 // so rows of any width fill whole warps; one warp per field); grid
-// (ceil(nx ny / 32), ceil((nz+1)/kZFaces)).  Face f lies between planes
+// (ceil(nx ny / 32), face chunks).  Face f lies between planes
 // zlo+f-1 and zlo+f (f = 0 .. zhi-zlo); its left-biased stencil is centred
 // on plane zlo+f-1, its right-biased one on plane zlo+f.
 constexpr int kZFaces = 64, kZPassThreads = 160;
+// A pass over nf faces cuts each pencil into c chunks of equal length
+// ceil(nf / c) (every chunk non-empty); which faces a thread computes changes
+// nothing in them (each face is the same operations on the same operands).
+__host__ __device__ inline int chunk_len(int nf, int c) { return (nf + c - 1) / c; }
+// c with chunks of about kZFaces faces (work-lists of uneven grids)
+__host__ __device__ inline int face_chunks(int nf)
+{
+    const int c = (nf + kZFaces / 2) / kZFaces;
+    const int len = chunk_len(nf, c < 1 ? 1 : c);
+    return (nf + len - 1) / len;
+}
 // integer-pipe products of the z pass of the fused launches (measured fastest:
 // WENO5 all three kinds, WENO7 without the face products; the WENO7 passes of
 // the three-pass launch are fastest with all three)
 constexpr int kZPassEmu5 = kEmuConst | kEmuWeights | kEmuFace, kZPassEmu7 = kEmuConst | kEmuWeights;
 
 // one pass item along axis AX: pencil block cb (32 consecutive pencils), face
-// chunk fch, of the grid described by a; the CTA's five warps are the five
+// chunk fch of clen faces (clen <= 0: chunks of equal length, gridDim.y of
+// them), of the grid described by a; the CTA's five warps are the five
 // fields.  Pencils and outputs:
 //   AX = 2 (z pass): pencil = column y nx + x of the plane; faces f = 0 ..
 //      zhi-zlo between stored planes zlo+f-1 and zlo+f; out fz[k fzs + f nx ny + pencil];
@@ -858,7 +870,7 @@ constexpr int kZPassEmu5 = kEmuConst | kEmuWeights | kEmuFace, kZPassEmu7 = kEmu
 // write coalesced rows; the x pass reads rows a row apart (each lane's next
 // cells hit the same L1 sectors) and writes its faces contiguously per row.
 template <int R, int EMU, int AX>
-__device__ __forceinline__ void axis_flux_item(const StageArgs& a, long long cb, int fch)
+__device__ __forceinline__ void axis_flux_item(const StageArgs& a, long long cb, int fch, int clen)
 {
     constexpr int G = R, S = 2 * R - 1;
     using DF = typename DiffOf<R>::T;
@@ -870,7 +882,9 @@ __device__ __forceinline__ void axis_flux_item(const StageArgs& a, long long cb,
     const long long pen = cb * 32 + (threadIdx.x & 31);
     if (pen >= npen) return;                     // no barriers below
     const int nax = AX == 2 ? nzi : (AX == 1 ? a.ny : a.nx);     // cells along the pencil (interior)
-    const int f0 = fch * kZFaces, f1 = min(f0 + kZFaces, nax + 1);
+    if (clen <= 0) clen = chunk_len(nax + 1, (int)gridDim.y);
+    const int f0 = fch * clen, f1 = min(f0 + clen, nax + 1);
+    if (f0 >= f1) return;
     const double al = __longlong_as_double((long long)a.alpha_in[AX]);
     // first cell of the pencil and the step between its cells
     long long base, step;
@@ -965,16 +979,16 @@ __device__ __forceinline__ void axis_flux_item(const StageArgs& a, long long cb,
 }
 
 template <int R, int EMU>
-__device__ __forceinline__ void zflux_item(const StageArgs& a, long long cb, int zch)
+__device__ __forceinline__ void zflux_item(const StageArgs& a, long long cb, int zch, int clen)
 {
-    axis_flux_item<R, EMU, 2>(a, cb, zch);
+    axis_flux_item<R, EMU, 2>(a, cb, zch, clen);
 }
 
 // (3 CTAs per SM for WENO7, 4 for WENO5: 15 and 20 warps)
 template <int R, int EMU>
 __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_kernel(const StageArgs a)
 {
-    zflux_item<R, EMU>(a, blockIdx.x, blockIdx.y);
+    zflux_item<R, EMU>(a, blockIdx.x, blockIdx.y, 0);
 }
 
 // x and y passes of the three-pass variants (same CTA and occupancy as the z
@@ -982,7 +996,7 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_kernel(co
 template <int R, int EMU, int AX, int MINB = 0>
 __global__ void __launch_bounds__(kZPassThreads, MINB > 0 ? MINB : (R == 4 ? 3 : 4)) axis_flux_kernel(const StageArgs a)
 {
-    axis_flux_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y);
+    axis_flux_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y, 0);
 }
 
 // pencil blocks of a pass along axis AX
@@ -1100,7 +1114,7 @@ __global__ void __launch_bounds__(256) stage_combine_kernel(const StageArgs a)
 // axis_flux_item): the raw window holds the flux f_AX, the state and the AX
 // speed of 2G cells, formed as the stage kernel's local-LF staging does.
 template <int R, int EMU, int AX>
-__device__ __forceinline__ void axis_flux_llf_item(const StageArgs& a, long long cb, int fch)
+__device__ __forceinline__ void axis_flux_llf_item(const StageArgs& a, long long cb, int fch, int clen)
 {
     constexpr int G = R, W = 2 * R;
     if (!(*a.dt > 0.0)) return;
@@ -1111,7 +1125,9 @@ __device__ __forceinline__ void axis_flux_llf_item(const StageArgs& a, long long
     const long long pen = cb * 32 + (threadIdx.x & 31);
     if (pen >= npen) return;                     // no barriers below
     const int nax = AX == 2 ? nzi : (AX == 1 ? a.ny : a.nx);
-    const int f0 = fch * kZFaces, f1 = min(f0 + kZFaces, nax + 1);
+    if (clen <= 0) clen = chunk_len(nax + 1, (int)gridDim.y);
+    const int f0 = fch * clen, f1 = min(f0 + clen, nax + 1);
+    if (f0 >= f1) return;
     long long base, step;
     int lo, ncell_ax, bcax;
     if constexpr (AX == 2) {
@@ -1180,22 +1196,22 @@ __device__ __forceinline__ void axis_flux_llf_item(const StageArgs& a, long long
 }
 
 template <int R, int EMU>
-__device__ __forceinline__ void zflux_llf_item(const StageArgs& a, long long cb, int zch)
+__device__ __forceinline__ void zflux_llf_item(const StageArgs& a, long long cb, int zch, int clen)
 {
-    axis_flux_llf_item<R, EMU, 2>(a, cb, zch);
+    axis_flux_llf_item<R, EMU, 2>(a, cb, zch, clen);
 }
 
 template <int R, int EMU>
 __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_llf_kernel(const StageArgs a)
 {
-    zflux_llf_item<R, EMU>(a, blockIdx.x, blockIdx.y);
+    zflux_llf_item<R, EMU>(a, blockIdx.x, blockIdx.y, 0);
 }
 
 // x and y passes of the local-LF three-pass variants
 template <int R, int EMU, int AX>
 __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) axis_flux_llf_kernel(const StageArgs a)
 {
-    axis_flux_llf_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y);
+    axis_flux_llf_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y, 0);
 }
 
 }  // namespace hydro

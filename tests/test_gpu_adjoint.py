@@ -77,6 +77,48 @@ def test_adjoint_matches_torch_autograd(scheme, dims, bc, nsteps, ckpt):
     assert np.all(err <= ADJ_TOL), err
 
 
+# pencil-kernel variants (HYDRO_ADJ_PENCIL): integer-pipe products and CTAs
+# per SM; every one gives the same bits
+ADJ_PENCIL_VARIANTS = 6
+
+
+@pytest.mark.parametrize("scheme,dims,bc", [
+    (5, (27, 9, 8), (0, 0, 0)),
+    (5, (9, 26, 8), (1, 1, 1)),
+    (7, (33, 8, 9), (1, 1, 1)),
+    (7, (8, 9, 35), (0, 0, 0)),
+])
+def test_adjoint_pencil_variants_give_the_same_bits(scheme, dims, bc, monkeypatch):
+    from paper_1604_03360_gb300 import Hydro
+    g, u0 = flow_state(dims, 40 + sum(dims), scheme, bc)
+    lam = np.random.default_rng(7).standard_normal(u0.shape)
+    got = []
+    with Hydro.from_grid(g) as h:
+        for v in range(ADJ_PENCIL_VARIANTS):
+            monkeypatch.setenv("HYDRO_ADJ_PENCIL", str(v))
+            h.set_state(u0)
+            h.forward_record(2, 1)
+            got.append(h.adjoint(lam))
+    for v in range(1, ADJ_PENCIL_VARIANTS):
+        assert np.array_equal(got[v], got[0]), v
+
+
+@pytest.mark.parametrize("nsteps,ckpt", [(5, 2), (3, 3), (4, 1)])
+def test_adjoint_repeated_after_one_forward(nsteps, ckpt):
+    """The first reverse sweep after a recorded forward takes the last
+    segment's stage inputs from the forward, later ones recompute it: the same
+    bits either way."""
+    from paper_1604_03360_gb300 import Hydro
+    g, u0 = flow_state((12, 11, 10), 77, 5, (0, 0, 0))
+    lam = np.random.default_rng(3).standard_normal(u0.shape)
+    with Hydro.from_grid(g) as h:
+        h.set_state(u0)
+        h.forward_record(nsteps, ckpt)
+        first = h.adjoint(lam)
+        second = h.adjoint(lam)
+    assert np.array_equal(first, second)
+
+
 def test_eps2_value_and_gradient():
     from paper_1604_03360_gb300 import Hydro
     g, u0 = flow_state((14, 12, 10), 3, 5)

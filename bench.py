@@ -429,6 +429,8 @@ def main():
                     help="headline run with characteristic-wise WENO (profiling; the metric stays component-wise)")
     ap.add_argument("--split", type=int, default=0, choices=[0, 1],
                     help="headline run with local Lax-Friedrichs splitting (profiling; the metric stays global LF)")
+    ap.add_argument("--nq", type=int, default=1, choices=[1, 2, 3],
+                    help="headline run with this many charges (profiling; the metric stays one charge)")
     ap.add_argument("--launch", type=int, default=None,
                     help="force this stage-kernel launch variant instead of autotuning (profiling)")
     ap.add_argument("--only", choices=["adjoint", "batch"], default=None,
@@ -477,6 +479,10 @@ def main():
     g, w = workload(args.scheme, args.grid)
     g.charwise = 1 if args.charwise else 0
     g.split = args.split
+    if args.nq > 1:
+        import workloads as W
+        g.nq = args.nq
+        w = W.with_charges(g, w, args.nq)
     cells = g.cells
     h = Hydro.from_grid(g, stream=stream)
     w_dev = torch.from_numpy(w).to(dev)
@@ -520,7 +526,7 @@ def main():
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_extra:
-        u_host = torch.empty((5,) + w.shape[1:], dtype=torch.float64).pin_memory()
+        u_host = torch.empty((4 + args.nq,) + w.shape[1:], dtype=torch.float64).pin_memory()
         h.get_state(u_host)
         out_host = torch.empty_like(u_host).pin_memory()
         barrier()
@@ -534,7 +540,7 @@ def main():
         t_e = torch.tensor([te], device=dev)
         if pg is not None:
             pg.all_reduce(t_e, op=pg.ReduceOp.MAX)
-        nbytes = 5 * cells * 8
+        nbytes = (4 + args.nq) * cells * 8
         e2e = {"value": world * cells * args.steps / float(t_e.item()), "unit": "cell-updates/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
@@ -668,7 +674,7 @@ def main():
 
     # the ncu figures hold for the launch they were captured on
     key = (args.scheme,) + tuple(launch[:3])
-    other = args.charwise or args.split
+    other = args.charwise or args.split or args.nq > 1
     inst = None if other else NCU_FP64_INST_PER_CELL_STAGE.get(key)
     traffic = None if other or key not in NCU_DRAM_BYTES_PER_CELL_STAGE else \
         NCU_DRAM_BYTES_PER_CELL_STAGE[key] * cells
@@ -681,7 +687,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "ellipsoidal-%d^3-WENO%d%s%s" % (args.grid, args.scheme,
                                                                     "-characteristic" if args.charwise else "",
-                                                                    "-localLF" if args.split else ""),
+                                                                    "-localLF" if args.split else "")
+                       + ("-%dcharges" % args.nq if args.nq > 1 else ""),
                        "grid": [args.grid] * 3,
                        "steps_per_timing": args.steps, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "state %.2f GB > 129 MB L2: no flush needed" % (27 * 8 * cells / 1e9),

@@ -164,10 +164,10 @@ hydro_status hydro_set_primitive(hydro_t* h, const double* w, int64_t field_stri
  * the current characteristic speeds), then per RK3 stage either one fused
  * stage kernel (Eq. 2 + RK combine + speeds of the new state), or in the
  * z-pass launch variants a z-face pass followed by the stage kernel, or in
- * the three-pass variants (the default for component-wise WENO with global
- * Lax-Friedrichs and one charge) an x-, a y- and a z-face pass followed by a
- * per-cell combination kernel, and a 1-thread step-end kernel
- * (hydro_kernels_per_step counts them).
+ * the three-pass variants (the default for WENO with global or local
+ * Lax-Friedrichs, any number of charges, component- or characteristic-wise)
+ * an x-, a y- and a z-face pass followed by a per-cell combination kernel,
+ * and a 1-thread step-end kernel (hydro_kernels_per_step counts them).
  * Asynchronous; no host synchronisation. */
 hydro_status hydro_step(hydro_t* h, int32_t nsteps, double t_end);
 

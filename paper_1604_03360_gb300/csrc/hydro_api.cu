@@ -124,6 +124,10 @@ static bool launch_fits(const hydro_t* h, const StageLaunch& L)
         if (!h->fx || !h->fy || pass_blocks(0, h->cfg.n[0], h->cfg.n[1], nzi) > 0x7fffffffLL ||
             pass_blocks(1, h->cfg.n[0], h->cfg.n[1], nzi) > 0x7fffffffLL)
             return false;
+        // one thread per face: every axis's face count must fit the grid
+        if (L.face_per_thread && (long long)(h->cfg.n[0] + 1) * (h->cfg.n[1] + 1) * (nzi + 1) / L.pass_threads >
+                                     0x7fffffffLL)
+            return false;
     }
     return !L.zfn || (h->fz && zpass_blocks(h->cfg.n[0], h->cfg.n[1]) <= 0x7fffffffLL);
 }
@@ -268,18 +272,18 @@ hydro_status hydro_create(const hydro_config* cfg, void* stream, hydro_t** out)
     }
     if ((e = cudaMemsetAsync(h->buf, 0, bytes, h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
     if (zpass_capable(*cfg, h->R)) {
-        // z-face fluxes for the z-pass variants: 5 fields of nz+1 face planes
+        // z-face fluxes for the z-pass variants: nf fields of nz+1 face planes
         h->fzs = ((long long)cfg->n[0] * cfg->n[1] * (cfg->n[2] + 1) + 31) / 32 * 32;
-        if ((e = cudaMalloc(&h->fz, sizeof(double) * (size_t)h->fzs * 5)) != cudaSuccess)
+        if ((e = cudaMalloc(&h->fz, sizeof(double) * (size_t)h->fzs * nf)) != cudaSuccess)
             return bail(cuda_fail(h, e, "z-face buffer"));
         {
             // x- and y-face fluxes for the three-pass variants
             const long long nzi = cfg->n[2];
             h->fxs = ((long long)(cfg->n[0] + 1) * cfg->n[1] * nzi + 31) / 32 * 32;
             h->fys = ((long long)cfg->n[0] * (cfg->n[1] + 1) * nzi + 31) / 32 * 32;
-            if ((e = cudaMalloc(&h->fx, sizeof(double) * (size_t)h->fxs * 5)) != cudaSuccess)
+            if ((e = cudaMalloc(&h->fx, sizeof(double) * (size_t)h->fxs * nf)) != cudaSuccess)
                 return bail(cuda_fail(h, e, "x-face buffer"));
-            if ((e = cudaMalloc(&h->fy, sizeof(double) * (size_t)h->fys * 5)) != cudaSuccess)
+            if ((e = cudaMalloc(&h->fy, sizeof(double) * (size_t)h->fys * nf)) != cudaSuccess)
                 return bail(cuda_fail(h, e, "y-face buffer"));
         }
     }

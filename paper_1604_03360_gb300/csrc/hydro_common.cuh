@@ -115,6 +115,11 @@ struct StageLaunch {
     void (*xfn)(StageArgs) = nullptr;
     void (*yfn)(StageArgs) = nullptr;
     bool combine = false;
+    int pass_threads = kZPassThreads;   // threads per pass CTA: one warp per field
+    // characteristic-wise passes: one thread per face (grid over the faces of
+    // the axis), pass_smem bytes of shared memory per CTA
+    bool face_per_thread = false;
+    size_t pass_smem = 0;
 };
 // tensor maps of the stage input (u: 5 fields, w: p, v_x, v_y of 4) for a
 // TMA-staged launch; cudaErrorNotSupported where the layout does not allow
@@ -145,17 +150,18 @@ int fused_launch_variant(int R, int split, int nq, int charw = 0);
 int batch_variant_count(int R, int split);
 cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* out, int charw = 0);
 int char_variant_count(int R, int nq);
+int char_default_variant(int R, int nq);
 cudaError_t char_launch_variant(int R, int nq, int v, StageLaunch* out);
 inline cudaError_t stage_launch_info(int R, StageLaunch* out)
 {
     return stage_launch_variant(R, 0, 1, fused_launch_variant(R, 0, 1), out);
 }
 inline int state_fields(const hydro_config& c) { return 4 + (c.nq > 1 ? c.nq : 1); }
-// configurations with z-pass launch variants (component-wise WENO, global or
-// local LF, one charge)
+// configurations with z-pass and three-pass launch variants (WENO with global
+// or local LF, up to three charges; characteristic-wise with global LF)
 inline bool zpass_capable(const hydro_config& c, int R)
 {
-    return (R == 3 || R == 4) && (c.split == 0 || c.split == 1) && c.nq <= 1 && c.charwise == 0;
+    return (R == 3 || R == 4) && (c.split == 0 || c.split == 1) && c.nq <= 3 && (c.charwise == 0 || c.split == 0);
 }
 // internal scheme code: 3 WENO5, 4 WENO7, 2 MUSTA-FORCE (the ghost width)
 inline int scheme_R(int scheme) { return scheme == HYDRO_WENO5 ? 3 : (scheme == HYDRO_WENO7 ? 4 : 2); }

@@ -150,11 +150,23 @@ static cudaError_t info_for(StageLaunch* out)
 
 // three-pass stage: x, y and z passes, then the per-cell combination (LLF:
 // local Lax-Friedrichs passes, and the combination also stores the speeds)
-template <int R, int ZEMU, bool LLF = false, int MINB = 0, int XMINB = MINB>
+template <int R, int ZEMU, bool LLF = false, int MINB = 0, int XMINB = MINB, int NF = 5>
 static cudaError_t info_for_three(StageLaunch* out)
 {
-    out->fn = stage_combine_kernel<5, LLF>;
-    if constexpr (LLF) {
+    out->fn = stage_combine_kernel<NF, LLF>;
+    out->pass_threads = 32 * NF;
+    if constexpr (NF > 5) {
+        // several charges: one warp per field, MINB CTAs per SM
+        if constexpr (LLF) {
+            out->xfn = axis_flux_llf_kernel<R, ZEMU, 0, MINB, NF>;
+            out->yfn = axis_flux_llf_kernel<R, ZEMU, 1, MINB, NF>;
+            out->zfn = axis_flux_llf_kernel<R, ZEMU, 2, MINB, NF>;
+        } else {
+            out->xfn = axis_flux_kernel<R, ZEMU, 0, MINB, NF>;
+            out->yfn = axis_flux_kernel<R, ZEMU, 1, MINB, NF>;
+            out->zfn = axis_flux_kernel<R, ZEMU, 2, MINB, NF>;
+        }
+    } else if constexpr (LLF) {
         out->xfn = axis_flux_llf_kernel<R, ZEMU, 0>;
         out->yfn = axis_flux_llf_kernel<R, ZEMU, 1>;
         out->zfn = zflux_llf_kernel<R, ZEMU>;
@@ -171,7 +183,7 @@ static cudaError_t info_for_three(StageLaunch* out)
     out->smem = 0;
     out->tx = 16;
     out->ty = 16;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_combine_kernel<5, LLF>, 256, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->ctas_per_sm, stage_combine_kernel<NF, LLF>, 256, 0);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -241,8 +253,17 @@ cudaError_t launch_stage_kernels(const StageLaunch& L, int zc, const StageArgs& 
         const int nfa[3] = {a.nx + 1, a.ny + 1, nzi + 1};
         for (int d = 0; d < 3; ++d) {
             if (!a.act[d]) continue;
+            if (L.face_per_thread) {
+                // one thread per face of the axis
+                const long long nfaces = (long long)nfa[d] * (d == 0 ? (long long)a.ny * nzi
+                                                                      : (d == 1 ? (long long)a.nx * nzi
+                                                                                : (long long)a.nx * a.ny));
+                const long long nb = (nfaces + L.pass_threads - 1) / L.pass_threads;
+                fns[d]<<<(unsigned)nb, L.pass_threads, L.pass_smem, s>>>(a);
+                continue;
+            }
             const long long pb = pass_blocks(d, a.nx, a.ny, nzi);
-            fns[d]<<<dim3((unsigned)pb, (unsigned)pass_chunks(nfa[d])), kZPassThreads, 0, s>>>(a);
+            fns[d]<<<dim3((unsigned)pb, (unsigned)pass_chunks(nfa[d])), L.pass_threads, 0, s>>>(a);
         }
         const long long cells = (long long)a.nx * a.ny * nzi;
         const long long want = (cells + 255) / 256, cap = (long long)sms * 8;
@@ -321,13 +342,16 @@ cudaError_t encode_stage_maps(const StageLaunch& L, const double* u, const doubl
 // 16x8 (16x16 would need 247 KB of shared memory).  With the local-LF z pass
 // (zflux_llf_kernel, no ring): WENO5 2 16x16 (two CTAs per SM) and 3 16x8
 // (four), WENO7 1 16x16 and 2 16x8.
-// Several charges (nq = 2, 3): one 16x8 variant per scheme and splitting.
+// Several charges (nq = 2, 3): 0 the 16x8 stage kernel, 1 three-pass (one
+// warp per field in the passes; the default).
 // the launch a grid gets before any tuning: the fastest on the 256^3 workload
 // (the three-pass variant, for component-wise WENO with global or local LF; a
 // handle that cannot run it keeps the fused one)
 int default_launch_variant(int R, int split, int nq, int charw)
 {
-    if (charw || R == 2 || nq > 1) return 0;
+    if (charw) return (R == 3 || R == 4) && split == 0 ? char_default_variant(R, nq) : 0;   // face passes
+    if (R == 2) return 0;
+    if (nq > 1) return 1;               // several charges, three-pass
     if (split) return R == 3 ? 4 : 3;   // local LF, three-pass
     return R == 3 ? 12 : 16;            // three-pass (WENO7: passes at five CTAs per SM, face
                                         // products on the integer pipe too)
@@ -349,14 +373,25 @@ int launch_variant_count(int R, int split, int nq, int charw)
 {
     if (charw) return (R == 3 || R == 4) && split == 0 ? char_variant_count(R, nq) : 0;
     if (R == 2) return (split == 0 && nq <= 1) ? 2 : 0;
-    if (nq > 1) return 1;
+    if (nq > 1) return 2;
     if (split == 1) return R == 3 ? 5 : 4;
     return R == 3 ? 15 : 18;
 }
 
+// several charges: v 0 the 16x8 stage kernel, 1 three-pass (passes of NF
+// warps: WENO5 at three CTAs per SM, 21 warps for NF = 7; WENO7 at four with
+// the weight and face products on the integer pipe as in its default)
 template <int NF>
-static cudaError_t charges_variant(int R, int split, StageLaunch* out)
+static cudaError_t charges_variant(int R, int split, int v, StageLaunch* out)
 {
+    if (v == 1) {
+        if (R == 3)
+            return split ? info_for_three<3, kZPassEmu5, true, 3, 3, NF>(out)
+                         : info_for_three<3, kZPassEmu5, false, 3, 3, NF>(out);
+        return split ? info_for_three<4, kZPassEmu7, true, 4, 4, NF>(out)
+                     : info_for_three<4, kEmuConst | kEmuWeights | kEmuFace, false, 4, 4, NF>(out);
+    }
+    if (v != 0) return cudaErrorInvalidValue;
     if (R == 3) return split ? info_for<3, 16, 8, 1, true, NF>(out) : info_for<3, 16, 8, 1, false, NF>(out);
     return split ? info_for<4, 16, 8, 1, true, NF>(out) : info_for<4, 16, 8, 1, false, NF>(out);
 }
@@ -387,9 +422,8 @@ cudaError_t stage_launch_variant(int R, int split, int nq, int v, StageLaunch* o
         return cudaErrorInvalidValue;
     }
     if (nq > 1) {
-        if (v != 0) return cudaErrorInvalidValue;
-        if (nq == 2) return charges_variant<6>(R, split, out);
-        if (nq == 3) return charges_variant<7>(R, split, out);
+        if (nq == 2) return charges_variant<6>(R, split, v, out);
+        if (nq == 3) return charges_variant<7>(R, split, v, out);
         return cudaErrorInvalidValue;
     }
     if (split == 1) {

@@ -992,9 +992,10 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_kernel(co
 }
 
 // x and y passes of the three-pass variants (same CTA and occupancy as the z
-// pass); MINB > 0 asks for that many CTAs per SM instead
-template <int R, int EMU, int AX, int MINB = 0>
-__global__ void __launch_bounds__(kZPassThreads, MINB > 0 ? MINB : (R == 4 ? 3 : 4)) axis_flux_kernel(const StageArgs a)
+// pass); MINB > 0 asks for that many CTAs per SM instead.  NF > 5 (several
+// charges): one warp per field, NF warps per CTA.
+template <int R, int EMU, int AX, int MINB = 0, int NF = 5>
+__global__ void __launch_bounds__(32 * NF, MINB > 0 ? MINB : (R == 4 ? 3 : 4)) axis_flux_kernel(const StageArgs a)
 {
     axis_flux_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y, 0);
 }
@@ -1010,8 +1011,8 @@ inline long long pass_blocks(int AX, int nx, int ny, int nzi)
 // written every face flux -- per cell the flux differences (Eq. 2), the RK
 // combination, the primitives and the speeds of the new state, with the same
 // operations in the same order as step 4 of stage_tile (component-wise, global
-// Lax-Friedrichs, five fields), so the same bits.  Grid-stride over the
-// interior cells, x fastest.
+// or local Lax-Friedrichs, NF = 4 + number of charges fields), so the same
+// bits.  Grid-stride over the interior cells, x fastest.
 //
 // combine_cells does cells i0, i0 + step, ... < i1 (flat index over the
 // interior cells, x fastest) and the speed reduction of the calling warps;
@@ -1020,7 +1021,6 @@ inline long long pass_blocks(int AX, int nx, int ny, int nzi)
 template <int NF = 5, bool LLF = false>
 __device__ __forceinline__ void combine_cells(const StageArgs& a, long long i0, long long i1, long long step)
 {
-    static_assert(NF == 5, "the three-pass variants carry five fields");
     const double dt = *a.dt;
     if (!(dt > 0.0)) return;
     const int nx = a.nx, ny = a.ny, nzi = a.zhi - a.zlo;
@@ -1207,9 +1207,10 @@ __global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) zflux_llf_kerne
     zflux_llf_item<R, EMU>(a, blockIdx.x, blockIdx.y, 0);
 }
 
-// x and y passes of the local-LF three-pass variants
-template <int R, int EMU, int AX>
-__global__ void __launch_bounds__(kZPassThreads, R == 4 ? 3 : 4) axis_flux_llf_kernel(const StageArgs a)
+// x and y passes of the local-LF three-pass variants (AX = 2: a z pass of NF
+// warps, for several charges)
+template <int R, int EMU, int AX, int MINB = 0, int NF = 5>
+__global__ void __launch_bounds__(32 * NF, MINB > 0 ? MINB : (R == 4 ? 3 : 4)) axis_flux_llf_kernel(const StageArgs a)
 {
     axis_flux_llf_item<R, EMU, AX>(a, blockIdx.x, blockIdx.y, 0);
 }

@@ -79,7 +79,7 @@ def test_charwise_needs_weno_with_global_splitting(L):
         h = ctypes.c_void_p()
         assert L.hydro_create(ctypes.byref(c), None, ctypes.byref(h)) == H._binding.ERR_INVALID_ARG
         assert b"characteristic" in L.hydro_last_error(None)
-    for scheme, nq, n in ((5, 1, 2), (7, 1, 1), (5, 3, 1), (7, 2, 1)):
+    for scheme, nq, n in ((5, 1, 5), (7, 1, 4), (5, 3, 4), (7, 2, 4)):
         c = H.make_config((8, 8, 8), (0.1, 0.1, 0.1), scheme=scheme, nq=nq, charwise=1)
         assert L.hydro_launch_variants_cfg(ctypes.byref(c)) == n
 
@@ -87,9 +87,10 @@ def test_charwise_needs_weno_with_global_splitting(L):
 def test_launch_variant_counts(L):
     """Compiled stage-kernel variants per scheme and splitting (WENO5 and WENO7
     with global LF: per-face tiles, pencil sweeps, z-pass sweeps; local LF:
-    per-face tiles; MUSTA-FORCE: two tiles); 0 for an unknown scheme."""
+    per-face tiles; several charges: the 16x8 stage kernel and the three-pass
+    launch; MUSTA-FORCE: two tiles); 0 for an unknown scheme."""
     for scheme, split, nq, n in ((5, 0, 1, 15), (7, 0, 1, 18), (5, 1, 1, 5), (7, 1, 1, 4), (2, 0, 1, 2),
-                                 (5, 0, 3, 1), (7, 1, 2, 1), (9, 0, 1, 0)):
+                                 (5, 0, 3, 2), (7, 1, 2, 2), (9, 0, 1, 0)):
         assert L.hydro_launch_variants(scheme, split, nq) == n, (scheme, split, nq)
 
 

@@ -413,6 +413,33 @@ def test_several_charges_match_oracle(scheme, split, nq):
     assert_parity(g, W.with_charges(g, w, nq), 6)
 
 
+@pytest.mark.parametrize("scheme,split,nq", [(5, 0, 2), (7, 0, 3), (5, 1, 3), (7, 1, 2)])
+@pytest.mark.parametrize("n,bc", [((37, 29, 21), (0, 0, 0)), ((16, 16, 12), (1, 1, 1)), ((23, 17, 1), (0, 0, 0)),
+                                  ((1, 19, 23), (0, 1, 0)), ((9, 8, 40), (0, 0, 1))])
+def test_several_charges_three_pass_matches_stage_kernel_bitwise(scheme, split, nq, n, bc):
+    """With several charges the three-pass launch (one warp per field in the
+    x, y and z passes, then the combination) is the default; every face gets
+    the same operations on the same operands as in the 16x8 stage kernel, so
+    both give the same bits (ragged, degenerate, periodic and outflow axes)."""
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=n, seed=71 + nq, scheme=scheme)
+    w = with_flow(g, w)
+    g.bc, g.split, g.nq = bc, split, nq
+    wq = W.with_charges(g, w, nq)
+    out = []
+    for v in (0, 1):
+        with Hydro.from_grid(g) as h:
+            assert h.launch()[0] == 1          # the default for several charges
+            h.set_launch(v, 6)
+            h.set_primitive(wq)
+            h.step(3)
+            out.append(h.get_state())
+            if v == 1:
+                assert h.kernels_per_step() == 2 + 3 * (1 + sum(int(m > 1) for m in n))
+    assert out[0].shape[0] == 4 + nq
+    assert np.array_equal(out[0], out[1])
+
+
 def test_extra_charges_evolve_like_the_single_charge():
     from paper_1604_03360_gb300 import Hydro
     g, w = W.lumpy(n=(30, 26, 22), seed=61, scheme=5)
@@ -538,13 +565,36 @@ def test_charwise_several_charges(scheme, nq):
     assert_parity(g, W.with_charges(g, w, nq), 6)
 
 
-@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (7, 0)])
+@pytest.mark.parametrize("scheme,variant", [(5, 0), (5, 1), (5, 2), (5, 3), (5, 4), (7, 0), (7, 1), (7, 2), (7, 3)])
 def test_charwise_every_launch_variant(scheme, variant):
+    """Fused stage kernels (WENO5 0, 1; WENO7 0) and the face passes + the
+    combination (the rest) against the oracle."""
     from paper_1604_03360_gb300 import Hydro
     g, w = W.lumpy(n=(37, 29, 21), seed=79, scheme=scheme)
     w = with_flow(g, w)
     g.charwise = 1
     u0 = oracle.prim2con(w)
+    ref = oracle.run(oracle_cfg(g), u0, 4)[0]
+    with Hydro.from_grid(g) as h:
+        h.set_launch(variant, 8)
+        h.set_state(u0)
+        h.step(4)
+        got = h.get_state()
+    assert np.all(field_errors(got, ref) <= TOL)
+
+
+@pytest.mark.parametrize("scheme,nq", [(5, 2), (7, 3)])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("n,bc", [((37, 29, 21), (0, 0, 0)), ((16, 15, 12), (1, 1, 1)), ((1, 19, 23), (0, 1, 0))])
+def test_charwise_charges_every_launch_variant(scheme, nq, variant, n, bc):
+    """Several charges, characteristic-wise: the 16x8 stage kernel (0) and the
+    face passes (1-3) against the oracle, ragged, periodic and degenerate."""
+    from paper_1604_03360_gb300 import Hydro
+    g, w = W.lumpy(n=n, seed=83 + nq, scheme=scheme)
+    w = with_flow(g, w)
+    g.bc, g.charwise, g.nq = bc, 1, nq
+    wq = W.with_charges(g, w, nq)
+    u0 = oracle.prim2con(wq)
     ref = oracle.run(oracle_cfg(g), u0, 4)[0]
     with Hydro.from_grid(g) as h:
         h.set_launch(variant, 8)

@@ -185,6 +185,29 @@ hydro_status hydro_get_primitive(hydro_t* h, double* w, int64_t field_stride, in
 /* Synchronise the stream and report deferred device errors. */
 hydro_status hydro_sync(hydro_t* h);
 
+/* Event-by-event stream on one grid (the many independent initial conditions
+ * that motivate the paper's GPU code, Sec. 1): for each of n_items initial
+ * states u_in[i] (conserved fields in host memory, layout as hydro_set_state
+ * with mem = HYDRO_MEM_HOST), load it at time t0, advance nsteps RK3 steps
+ * (t_end as in hydro_step) and write the final state to u_out[i] (host
+ * memory, same layout).  Each item's result is bit for bit what
+ * hydro_set_state + hydro_step + hydro_get_state give.  The copies are
+ * double-buffered: item i+1 is copied in and item i-1 out on two copy
+ * streams of the handle while item i steps on the handle's stream, with
+ * device-to-device moves between the staging buffers and the state.  The
+ * first call allocates the staging buffers (three states) and the copy
+ * streams; they live until hydro_destroy.  Host buffers should be page-locked
+ * (cudaMallocHost or pinned torch tensors): pageable ones work, but their
+ * copies do not overlap.  u_in[i] and u_out[j] may be the same buffer only
+ * if j >= i + 2 never reuses it before item i's copy-in ends (simplest:
+ * distinct buffers, or the same input buffer for every item).  Synchronises
+ * before returning; returns the first error of any item
+ * (HYDRO_ERR_UNPHYSICAL names the item and the cell in hydro_last_error).
+ * Afterwards the handle holds the last item's final state.  Whole grids only
+ * (not z-slab handles). */
+hydro_status hydro_run_many(hydro_t* h, int32_t n_items, const double* const* u_in, double* const* u_out,
+                            int64_t field_stride, int32_t nsteps, double t0, double t_end);
+
 /* Largest characteristic speed per direction of the current state (alpha_d
  * of the global Lax-Friedrichs splitting) and the last time step taken.
  * Synchronises. */

@@ -90,6 +90,7 @@ def lib():
         "hydro_get_state": ([vp, vp, i64, i32, P(d), P(i64)], i32),
         "hydro_get_primitive": ([vp, vp, i64, i32], i32),
         "hydro_sync": ([vp], i32),
+        "hydro_run_many": ([vp, i32, P(vp), P(vp), i64, i32, d, d], i32),
         "hydro_get_speeds": ([vp, P(d), P(d)], i32),
         "hydro_profile_step": ([vp, i32, d, P(d)], i32),
         "hydro_last_error": ([vp], ctypes.c_char_p),
@@ -329,6 +330,27 @@ class Hydro:
 
     def sync(self):
         self._check(self._L.hydro_sync(self._h))
+
+    def run_many(self, inputs, outputs, nsteps=1, t0=0.0, t_end=-1.0):
+        """Event-by-event stream: load each host state of `inputs`, advance
+        nsteps RK3 steps from t0 and write the result into the matching host
+        buffer of `outputs` (page-locked buffers overlap the copies with the
+        steps).  All buffers share one field stride."""
+        if len(inputs) != len(outputs):
+            raise ValueError("one output buffer per input")
+        n = len(inputs)
+        pin, pout, fs = (ctypes.c_void_p * max(n, 1))(), (ctypes.c_void_p * max(n, 1))(), None
+        for i, (a, b) in enumerate(zip(inputs, outputs)):
+            pa, fa, ma = as_buffer(a)
+            pb, fb, mb = as_buffer(b, writable=True)
+            if ma != MEM_HOST or mb != MEM_HOST:
+                raise ValueError("run_many streams host buffers")
+            if fa != fb or (fs is not None and fa != fs):
+                raise ValueError("all buffers need the same field stride")
+            fs = fa
+            pin[i], pout[i] = pa, pb
+        self._check(self._L.hydro_run_many(self._h, n, pin, pout, int(fs or 0), int(nsteps), float(t0),
+                                           float(t_end)))
 
     # -- z-slab (bc[2] = BC_HALO) handles: one RK stage at a time ---------
 

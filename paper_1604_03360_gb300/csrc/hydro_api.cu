@@ -45,6 +45,14 @@ struct hydro_s {
     long long off = 0;
     bool have_state = false;
     AdjointWork* adj = nullptr;      // reverse-mode workspace (hydro_adjoint.cu)
+    // hydro_run_many: staging states (two in, one out), copy streams, events
+    // and the first-error record over the items (allocated on first use)
+    double* io_buf = nullptr;
+    RunStatus* run_st = nullptr;
+    RunStatus* hrun_st = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+    cudaEvent_t ev_out_ready = nullptr, ev_out_free = nullptr;
     std::string err;
 };
 
@@ -328,6 +336,15 @@ hydro_status hydro_destroy(hydro_t* h)
         cudaFree(h->adj->ctl);
         delete h->adj;
     }
+    if (h->s_in) cudaStreamSynchronize(h->s_in);
+    if (h->s_out) cudaStreamSynchronize(h->s_out);
+    if (h->io_buf) cudaFree(h->io_buf);
+    if (h->run_st) cudaFree(h->run_st);
+    if (h->hrun_st) cudaFreeHost(h->hrun_st);
+    for (cudaEvent_t ev : {h->ev_in[0], h->ev_in[1], h->ev_used[0], h->ev_used[1], h->ev_out_ready, h->ev_out_free})
+        if (ev) cudaEventDestroy(ev);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
     delete h;
     return HYDRO_OK;
 }
@@ -765,6 +782,94 @@ hydro_status hydro_sync(hydro_t* h)
 {
     if (!h) return HYDRO_ERR_INVALID_ARG;
     return read_ctl(h);
+}
+
+// staging buffers, copy streams and events of hydro_run_many
+static hydro_status run_many_setup(hydro_t* h)
+{
+    if (h->io_buf) return HYDRO_OK;
+    const size_t state = sizeof(double) * (size_t)h->fs * h->nf;
+    CK(h, cudaMalloc(&h->io_buf, 3 * state), "staging buffers");
+    CK(h, cudaMalloc(&h->run_st, sizeof(RunStatus)), "run status");
+    CK(h, cudaMallocHost(&h->hrun_st, sizeof(RunStatus)), "pinned run status");
+    CK(h, cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking), "copy-in stream");
+    CK(h, cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking), "copy-out stream");
+    for (cudaEvent_t* ev : {&h->ev_in[0], &h->ev_in[1], &h->ev_used[0], &h->ev_used[1], &h->ev_out_ready, &h->ev_out_free})
+        CK(h, cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "event");
+    return HYDRO_OK;
+}
+
+hydro_status hydro_run_many(hydro_t* h, int32_t n_items, const double* const* u_in, double* const* u_out,
+                            int64_t field_stride, int32_t nsteps, double t0, double t_end)
+{
+    if (!h) return HYDRO_ERR_INVALID_ARG;
+    if (h->cfg.bc[2] == HYDRO_BC_HALO) return fail(h, HYDRO_ERR_INVALID_ARG, "a halo slab steps through hydro_stage");
+    if (n_items < 0 || nsteps < 0) return fail(h, HYDRO_ERR_INVALID_ARG, "n_items and nsteps must be >= 0");
+    if (n_items == 0) return HYDRO_OK;
+    if (!u_in || !u_out) return fail(h, HYDRO_ERR_INVALID_ARG, "NULL item list");
+    if (field_stride < h->ncell) return fail(h, HYDRO_ERR_INVALID_ARG, "field_stride smaller than the cell count");
+    for (int i = 0; i < n_items; ++i)
+        if (!u_in[i] || !u_out[i]) return fail(h, HYDRO_ERR_INVALID_ARG, "NULL data pointer in the item list");
+    hydro_status st = run_many_setup(h);
+    if (st) return st;
+    const size_t fbytes = sizeof(double) * (size_t)h->ncell;
+    const size_t sbytes = sizeof(double) * (size_t)h->fs * h->nf;     // one whole state, padding included
+    double* const stage_in[2] = {h->io_buf, h->io_buf + (size_t)h->fs * h->nf};
+    double* const stage_out = h->io_buf + 2 * (size_t)h->fs * h->nf;
+    cudaStream_t s = h->stream;
+    CK(h, cudaMemsetAsync(h->run_st, 0, sizeof(RunStatus), s), "run status");
+    auto copy_in = [&](int i, int b) -> hydro_status {
+        for (int f = 0; f < h->nf; ++f)
+            CK(h, cudaMemcpyAsync(stage_in[b] + (size_t)f * h->fs, u_in[i] + (size_t)f * field_stride, fbytes,
+                                  cudaMemcpyHostToDevice, h->s_in), "copy in");
+        CK(h, cudaEventRecord(h->ev_in[b], h->s_in), "event");
+        return HYDRO_OK;
+    };
+    // the copy-in stream starts after everything already queued on the handle's stream
+    CK(h, cudaEventRecord(h->ev_used[1], s), "event");
+    CK(h, cudaStreamWaitEvent(h->s_in, h->ev_used[1], 0), "wait");
+    CK(h, cudaStreamWaitEvent(h->s_out, h->ev_used[1], 0), "wait");
+    if ((st = copy_in(0, 0))) return st;
+    for (int i = 0; i < n_items; ++i) {
+        const int b = i & 1;
+        if (i + 1 < n_items) {
+            // prefetch item i+1 into the buffer item i-1 came through, once the
+            // state has taken it
+            CK(h, cudaStreamWaitEvent(h->s_in, h->ev_used[b ^ 1], 0), "wait");
+            if ((st = copy_in(i + 1, b ^ 1))) return st;
+        }
+        CK(h, cudaStreamWaitEvent(s, h->ev_in[b], 0), "wait");
+        CK(h, cudaMemcpyAsync(h->U[0], stage_in[b], sbytes, cudaMemcpyDeviceToDevice, s), "load item");
+        CK(h, cudaEventRecord(h->ev_used[b], s), "event");
+        if ((st = after_load(h, t0))) return st;
+        set_t_end_kernel<<<1, 1, 0, s>>>(h->ctl, t_end);
+        CK(h, cudaGetLastError(), "set t_end");
+        for (int k = 0; k < nsteps; ++k) CK(h, cudaGraphLaunch(h->exec, s), "graph launch");
+        run_status_kernel<<<1, 1, 0, s>>>(h->ctl, h->run_st, i);
+        CK(h, cudaGetLastError(), "run status");
+        // result out through the staging buffer, once item i-1's copy-out is done
+        CK(h, cudaStreamWaitEvent(s, h->ev_out_free, 0), "wait");
+        CK(h, cudaMemcpyAsync(stage_out, h->U[0], sbytes, cudaMemcpyDeviceToDevice, s), "store item");
+        CK(h, cudaEventRecord(h->ev_out_ready, s), "event");
+        CK(h, cudaStreamWaitEvent(h->s_out, h->ev_out_ready, 0), "wait");
+        for (int f = 0; f < h->nf; ++f)
+            CK(h, cudaMemcpyAsync(u_out[i] + (size_t)f * field_stride, stage_out + (size_t)f * h->fs, fbytes,
+                                  cudaMemcpyDeviceToHost, h->s_out), "copy out");
+        CK(h, cudaEventRecord(h->ev_out_free, h->s_out), "event");
+    }
+    CK(h, cudaMemcpyAsync(h->hrun_st, h->run_st, sizeof(RunStatus), cudaMemcpyDeviceToHost, s), "read run status");
+    CK(h, cudaStreamSynchronize(h->s_out), "synchronize");
+    CK(h, cudaStreamSynchronize(h->s_in), "synchronize");
+    CK(h, cudaStreamSynchronize(s), "synchronize");
+    if (h->hrun_st->status == HYDRO_ERR_TIMEOUT)
+        return fail(h, HYDRO_ERR_TIMEOUT, "a stage kernel's wait for its TMA tile load ran out of time; results are invalid");
+    if (h->hrun_st->status) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "unphysical state (E <= 0, |M| >= E or NaN) in item %d, first seen at cell %lld",
+                 h->hrun_st->item, (long long)h->hrun_st->bad_cell);
+        return fail(h, HYDRO_ERR_UNPHYSICAL, msg);
+    }
+    return HYDRO_OK;
 }
 
 hydro_status hydro_get_state(hydro_t* h, double* u, int64_t field_stride, int32_t mem, double* t, int64_t* step)

@@ -30,6 +30,13 @@ struct Ctl {
     int pad_;
 };
 
+// first error over the items of hydro_run_many
+struct RunStatus {
+    long long bad_cell;
+    int status;
+    int item;
+};
+
 struct StepParams {
     double cfl, dt_fixed, mindx;
     int actmask;                   // bit d: axis d takes part in dt
@@ -49,6 +56,8 @@ struct FieldList {
 };
 __global__ void halo_replicate_kernel(FieldList fl, long long plane, long long src, long long dst, int G);
 __global__ void reset_ctl_kernel(Ctl* c, double t);
+// keep the first error of item `item` (hydro_run_many)
+__global__ void run_status_kernel(const Ctl* c, RunStatus* r, int item);
 // primitives and speeds of a state (after set_state)
 // (and, if s != nullptr, the per-axis speeds of every cell: 3 fields)
 // eos_m: mass of the EOS p = cs2 (e - eos_m n_1) (0: p = cs2 e)

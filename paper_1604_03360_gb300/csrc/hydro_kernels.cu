@@ -58,6 +58,15 @@ __global__ void reset_ctl_kernel(Ctl* c, double t)
     c->status = 0;
 }
 
+__global__ void run_status_kernel(const Ctl* c, RunStatus* r, int item)
+{
+    if (c->status && !r->status) {
+        r->status = c->status;
+        r->bad_cell = c->bad_cell;
+        r->item = item;
+    }
+}
+
 __global__ void prepare_kernel(const double* u, double* w, long long fs, long long n, double cs2, Ctl* c, double* s,
                                double eos_m)
 {

@@ -337,9 +337,10 @@ __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
     const double P0 = xmul<EP>(w1, p23), P1 = xmul<EP>(w0, p23), P2 = xmul<EP>(p01, w3), P3 = xmul<EP>(p01, w2);
     // 35 d_k (q_k - v3), d = (1, 12, 18, 4)/35, in the difference basis:
     // q0 - v3 = d0/4 - 5 d1/6 + 13 d2/12, q1 - v3 = (-d1 + 4 d2 + 3 d3)/12,
-    // q2 - v3 = (d2 + 6 d3 - d4)/12, q3 - v3 = (9 d3 - 4 d4 + d5)/12
+    // q2 - v3 = (d2 + 6 d3 - d4)/12, q3 - v3 = (9 d3 - 4 d4 + d5)/12;
+    // -d1 + 4 d2 + 3 d3 = A1 + e2, one addition
     const double m0 = fma(13.0 / 12.0, d2, fma(-5.0 / 6.0, d1, xmul_pow2<EC, -2>(d0)));
-    const double m1 = fma(3.0, d3, fma(4.0, d2, -d1));
+    const double m1 = A1 + B12;
     const double m2 = fma(9.0, d3, xmul_small<EC, 3, 2, -1>(d2 - d4));
     const double m3 = fma(3.0, d3, fma(-4.0 / 3.0, d4, xmul<EC>(1.0 / 3.0, d5)));
     M = fma(m0, P0, fma(m1, P1, fma(m2, P2, xmul<(EMU & kEmuFace) != 0>(m3, P3))));

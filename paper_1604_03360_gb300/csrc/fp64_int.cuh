@@ -153,6 +153,12 @@ HYDRO_HD bool dmul_small_bits(uint64_t a, uint32_t c, int k, uint64_t& r)
     return true;
 }
 
+// Which products of a kernel run on the integer pipe (bit flags of a kernel's
+// EMU template argument): the products with constants, the squares and
+// products of the nonlinear weights, the last products of the weighted sums
+// and of the face combination.
+constexpr int kEmuConst = 1, kEmuWeights = 2, kEmuFace = 4;
+
 // Operations on the integer pipe (E) or the FP64 unit; both give the same bits.
 template <bool E>
 HYDRO_HD double xmul(double x, double y)

@@ -11,12 +11,14 @@
 // adjoints in reverse:
 //   u_out = ca u_n + cb (u_s + dt L(u_s))  =>
 //   lam_s = cb lam_out + J_L(u_s)^T (cb dt lam_out),  lam_n += ca lam_out.
-// J_L^T mu is a sum over axes.  One thread per (axis, field, pencil) sweeps
-// the pencil's faces with a register window: face adjoint
+// J_L^T mu is a sum over axes.  One thread per (axis, field, pencil segment)
+// sweeps the segment's faces (adj_sweep, adj_weno.cuh): face adjoint
 // F~bar_{j+1/2} = hdx (mu_{j+1} - mu_j), reverse-mode WENO of both biased
-// reconstructions into the split-flux adjoints gbar+-, ghost-cell
-// contributions folded back onto their source cells by the boundary rule (no
-// atomics anywhere); then one cell kernel applies, summed over the axes,
+// reconstructions in their difference basis, with the differences and their
+// adjoints carried from face to face, into the split-flux adjoints gbar+-;
+// ghost-cell contributions fold back onto their source cells by the boundary
+// rule, and the few cells two segments share are summed by two atomic adds
+// into zeroed outputs; then one cell kernel applies, summed over the axes,
 //   ubar = sum_d J_f_d(u)^T (gbar+_d + gbar-_d) + alpha_d (gbar+_d - gbar-_d).
 // A warp's pencils are consecutive in the fastest index of the array it
 // sweeps, so y and z pencils read and write coalesced rows.  x pencils would
@@ -31,180 +33,10 @@
 #include <string>
 #include <vector>
 
+#include "adj_weno.cuh"
 #include "hydro_common.cuh"
 
 namespace hydro {
-
-// ---------------------------------------------------------------- WENO VJPs
-// The scaled reconstructions of weno5 / weno7 (hydro_math.cuh), written in
-// their difference bases: b_k = eps_s + (smoothness forms)^2, w_k = b_k^2,
-// P_k = prod_{m!=k} w_m, N = sum n_k P_k, D = sum dc_k P_k, value = N / D.
-// vb (+)= Rbar * d(N/D)/dv: the forward values once, then the reverse sweep
-// N, D -> P -> w -> b -> (smoothness forms, n) -> v.  EMU selects products
-// computed on the integer pipe (fp64_int.cuh; the same bits): kEmuConst the
-// products with constants, kEmuWeights those of w and P and their reverse
-// (wbar), kEmuFace the other products of the reverse sweep.  ACC: accumulate
-// into vb[0 .. 2R-3] (else overwrite them); vb[2R-2], the newest cell of a
-// sliding window, is always overwritten.  Checked against complex-step derivatives of
-// the forward formulas (1e-14 WENO5, 2e-14 WENO7).
-// x * y on the integer pipe (E) or the FP64 unit; the FP64 product is never
-// contracted into an FMA with a later add, so both give the same bits
-template <bool E>
-__device__ __forceinline__ double pmul(double x, double y)
-{
-    if constexpr (E) return dmul_int(x, y);
-    else return __dmul_rn(x, y);
-}
-
-template <bool ACC>
-__device__ __forceinline__ void vjp_out(double& dst, double x)
-{
-    if constexpr (ACC) dst += x;
-    else dst = x;
-}
-
-template <int EMU, bool ACC>
-__device__ __forceinline__ void weno5_vjp(const double* v, double eps_s, double Rbar, double* vb)
-{
-    constexpr bool EC = (EMU & kEmuConst) != 0, EW = (EMU & kEmuWeights) != 0, EF = (EMU & kEmuFace) != 0;
-    const double d0 = v[1] - v[0], d1 = v[2] - v[1], d2 = v[3] - v[2], d3 = v[4] - v[3];
-    const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2;
-    const double t0 = fma(3.0, d1, -d0), t1 = d1 + d2, t2 = fma(3.0, d2, -d3);
-    const double ks0 = xmul<EC>(13.0 / 3.0, s0), ks1 = xmul<EC>(13.0 / 3.0, s1), ks2 = xmul<EC>(13.0 / 3.0, s2);
-    const double b0 = fma(ks0, s0, fma(t0, t0, eps_s));
-    const double b1 = fma(ks1, s1, fma(t1, t1, eps_s));
-    const double b2 = fma(ks2, s2, fma(t2, t2, eps_s));
-    const double w0 = pmul<EW>(b0, b0), w1 = pmul<EW>(b1, b1), w2 = pmul<EW>(b2, b2);
-    const double P0 = pmul<EW>(w1, w2), P1 = pmul<EW>(w0, w2), P2 = pmul<EW>(w0, w1);
-    // candidates scaled by the linear weights (1, 6, 3)/10 x 10
-    const double n0 = fma(11.0 / 6.0, v[2], fma(-7.0 / 6.0, v[1], xmul<EC>(1.0 / 3.0, v[0])));
-    const double n1 = fma(2.0, v[3], fma(5.0, v[2], -v[1]));
-    const double n2 = fma(-0.5, v[4], fma(2.5, v[3], v[2]));
-    const double N = fma(n0, P0, fma(n1, P1, pmul<EF>(n2, P2)));
-    const double D = fma(3.0, P2, fma(6.0, P1, P0));
-    // reverse: value = N / D
-    const double iD = rcp(D);
-    const double Nb = pmul<EF>(Rbar, iD);
-    const double Db = -pmul<EF>(Nb, pmul<EF>(N, iD));
-    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, xmul_small<EC, 3, 2, 1>(Db));
-    const double Pb2 = fma(Nb, n2, xmul_small<EC, 3, 2, 0>(Db));
-    const double nb0 = pmul<EF>(Nb, P0), nb1 = pmul<EF>(Nb, P1), nb2 = pmul<EF>(Nb, P2);
-    // w_k = b_k^2 enters every P_m with m != k
-    const double wb0 = fma(Pb1, w2, pmul<EW>(Pb2, w1)), wb1 = fma(Pb0, w2, pmul<EW>(Pb2, w0));
-    const double wb2 = fma(Pb0, w1, pmul<EW>(Pb1, w0));
-    // b_k = eps + t_k^2 + 13/3 s_k^2: tbar = 4 t b wbar, sbar = 4 (13/3) s b wbar
-    const double q0 = pmul<EF>(xmul_pow2<EC, 2>(b0), wb0), q1 = pmul<EF>(xmul_pow2<EC, 2>(b1), wb1);
-    const double q2 = pmul<EF>(xmul_pow2<EC, 2>(b2), wb2);
-    const double tb0 = pmul<EF>(t0, q0), tb1 = pmul<EF>(t1, q1), tb2 = pmul<EF>(t2, q2);
-    const double sb0 = pmul<EF>(ks0, q0), sb1 = pmul<EF>(ks1, q1), sb2 = pmul<EF>(ks2, q2);
-    // transposes of t_k, s_k and n_k written on the cell values
-    vjp_out<ACC>(vb[0], fma(1.0 / 3.0, nb0, tb0 + sb0));
-    vjp_out<ACC>(vb[1], fma(-7.0 / 6.0, nb0, fma(-4.0, tb0, fma(-2.0, sb0, sb1 - nb1 - tb1))));
-    vjp_out<ACC>(vb[2], fma(11.0 / 6.0, nb0, fma(5.0, nb1, fma(3.0, tb0 - tb2, fma(-2.0, sb1, nb2 + sb0 + sb2)))));
-    vjp_out<ACC>(vb[3], fma(2.0, nb1, fma(2.5, nb2, fma(4.0, tb2, fma(-2.0, sb2, tb1 + sb1)))));
-    vb[4] = fma(-0.5, nb2, sb2 - tb2);
-}
-
-// WENO7 in the difference basis of weno7 (A, B, C forms, b_k = eps + A^2 +
-// 39 B^2 + 781/20 C^2); the reverse sweep takes the leave-two-out products
-// for wbar and (A, B, C, n) -> (e, d) -> v for the transposes.
-template <int EMU, bool ACC>
-__device__ __forceinline__ void weno7_vjp(const double* v, double eps_s, double Rbar, double* vb)
-{
-    constexpr bool EC = (EMU & kEmuConst) != 0, EW = (EMU & kEmuWeights) != 0, EF = (EMU & kEmuFace) != 0;
-    constexpr double kc = 781.0 / 20.0;
-    double d[6], e[5];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) d[i] = v[i + 1] - v[i];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) e[i] = d[i + 1] - d[i];
-    const double C0 = e[1] - e[0], C1 = e[2] - e[1], C2 = e[3] - e[2], C3 = e[4] - e[3];
-    const double B0 = fma(2.0, e[1], -e[0]), B12 = e[2], B3 = fma(2.0, e[3], -e[4]);
-    const double A0 = fma(6.0, d[2], fma(2.0, B0, e[1]));
-    const double A1 = fma(2.0, d[3], fma(5.0, d[2], -d[1]));
-    const double A2 = fma(5.0, d[3], fma(2.0, d[2], -d[4]));
-    const double A3 = fma(6.0, d[3], fma(-2.0, B3, -e[3]));
-    const double kB0 = xmul_small<EC, 39, 6, 0>(B0), kB12 = xmul_small<EC, 39, 6, 0>(B12);
-    const double kB3 = xmul_small<EC, 39, 6, 0>(B3);
-    const double kC0 = xmul<EC>(kc, C0), kC1 = xmul<EC>(kc, C1), kC2 = xmul<EC>(kc, C2), kC3 = xmul<EC>(kc, C3);
-    const double b0 = fma(A0, A0, fma(kB0, B0, fma(kC0, C0, eps_s)));
-    const double b1 = fma(A1, A1, fma(kB12, B12, fma(kC1, C1, eps_s)));
-    const double b2 = fma(A2, A2, fma(kB12, B12, fma(kC2, C2, eps_s)));
-    const double b3 = fma(A3, A3, fma(kB3, B3, fma(kC3, C3, eps_s)));
-    const double w0 = pmul<EW>(b0, b0), w1 = pmul<EW>(b1, b1), w2 = pmul<EW>(b2, b2), w3 = pmul<EW>(b3, b3);
-    const double w01 = pmul<EW>(w0, w1), w23 = pmul<EW>(w2, w3), w02 = pmul<EW>(w0, w2);
-    const double w03 = pmul<EW>(w0, w3), w12 = pmul<EW>(w1, w2), w13 = pmul<EW>(w1, w3);
-    const double P0 = pmul<EW>(w1, w23), P1 = pmul<EW>(w0, w23), P2 = pmul<EW>(w01, w3), P3 = pmul<EW>(w01, w2);
-    // candidates scaled by the linear weights (1, 12, 18, 4)/35 x 35
-    const double n0 = fma(25.0 / 12.0, v[3], fma(-23.0 / 12.0, v[2], fma(13.0 / 12.0, v[1], xmul_pow2<EC, -2>(-v[0]))));
-    const double n1 = fma(3.0, v[4], fma(13.0, v[3], fma(-5.0, v[2], v[1])));
-    const double n2 = fma(10.5, v[3] + v[4], xmul_small<EC, 3, 2, -1>(-(v[2] + v[5])));
-    const double n3 = fma(13.0 / 3.0, v[4], fma(-5.0 / 3.0, v[5], fma(1.0 / 3.0, v[6], v[3])));
-    const double N = fma(n0, P0, fma(n1, P1, fma(n2, P2, pmul<EF>(n3, P3))));
-    const double D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
-    // reverse: value = N / D
-    const double iD = rcp(D);
-    const double Nb = pmul<EF>(Rbar, iD);
-    const double Db = -pmul<EF>(Nb, pmul<EF>(N, iD));
-    const double Pb0 = fma(Nb, n0, Db), Pb1 = fma(Nb, n1, xmul_small<EC, 3, 2, 2>(Db));
-    const double Pb2 = fma(Nb, n2, xmul_small<EC, 9, 4, 1>(Db)), Pb3 = fma(Nb, n3, xmul_pow2<EC, 2>(Db));
-    const double nb0 = pmul<EF>(Nb, P0), nb1 = pmul<EF>(Nb, P1), nb2 = pmul<EF>(Nb, P2), nb3 = pmul<EF>(Nb, P3);
-    const double wb0 = fma(Pb1, w23, fma(Pb2, w13, pmul<EW>(Pb3, w12)));
-    const double wb1 = fma(Pb0, w23, fma(Pb2, w03, pmul<EW>(Pb3, w02)));
-    const double wb2 = fma(Pb0, w13, fma(Pb1, w03, pmul<EW>(Pb3, w01)));
-    const double wb3 = fma(Pb0, w12, fma(Pb1, w02, pmul<EW>(Pb2, w01)));
-    // b_k = eps + A^2 + 39 B^2 + kc C^2: Abar = 4 A b wbar, Bbar = 4 (39 B) b wbar, ...
-    const double q0 = pmul<EF>(xmul_pow2<EC, 2>(b0), wb0), q1 = pmul<EF>(xmul_pow2<EC, 2>(b1), wb1);
-    const double q2 = pmul<EF>(xmul_pow2<EC, 2>(b2), wb2), q3 = pmul<EF>(xmul_pow2<EC, 2>(b3), wb3);
-    const double Ab0 = pmul<EF>(A0, q0), Ab1 = pmul<EF>(A1, q1), Ab2 = pmul<EF>(A2, q2), Ab3 = pmul<EF>(A3, q3);
-    const double Bb0 = pmul<EF>(kB0, q0), Bb1 = pmul<EF>(kB12, q1), Bb2 = pmul<EF>(kB12, q2);
-    const double Bb3 = pmul<EF>(kB3, q3);
-    const double Cb0 = pmul<EF>(kC0, q0), Cb1 = pmul<EF>(kC1, q1), Cb2 = pmul<EF>(kC2, q2);
-    const double Cb3 = pmul<EF>(kC3, q3);
-    // transposes: (B, C) -> e, (A, e) -> d, d -> v, n -> v
-    const double eb0 = -Bb0 - Cb0;
-    const double eb1 = fma(2.0, Bb0, Cb0 - Cb1);
-    const double eb2 = Bb1 + Bb2 + (Cb1 - Cb2);
-    const double eb3 = fma(2.0, Bb3, Cb2 - Cb3);
-    const double eb4 = Cb3 - Bb3;
-    const double db0 = fma(2.0, Ab0, -eb0);
-    const double db1 = fma(-7.0, Ab0, (eb0 - eb1) - Ab1);
-    const double db2 = fma(11.0, Ab0, fma(5.0, Ab1, fma(2.0, Ab2, eb1 - eb2)));
-    const double db3 = fma(2.0, Ab1, fma(5.0, Ab2, fma(11.0, Ab3, eb2 - eb3)));
-    const double db4 = fma(-7.0, Ab3, (eb3 - eb4) - Ab2);
-    const double db5 = fma(2.0, Ab3, eb4);
-    vjp_out<ACC>(vb[0], fma(-0.25, nb0, -db0));
-    vjp_out<ACC>(vb[1], fma(13.0 / 12.0, nb0, nb1 + (db0 - db1)));
-    vjp_out<ACC>(vb[2], fma(-23.0 / 12.0, nb0, fma(-5.0, nb1, fma(-1.5, nb2, db1 - db2))));
-    vjp_out<ACC>(vb[3], fma(25.0 / 12.0, nb0, fma(13.0, nb1, fma(10.5, nb2, nb3 + (db2 - db3)))));
-    vjp_out<ACC>(vb[4], fma(3.0, nb1, fma(10.5, nb2, fma(13.0 / 3.0, nb3, db3 - db4))));
-    vjp_out<ACC>(vb[5], fma(-1.5, nb2, fma(-5.0 / 3.0, nb3, db4 - db5)));
-    vb[6] = fma(1.0 / 3.0, nb3, db5);
-}
-
-// the left-biased reconstruction of the face from the 2R-1 cells v
-template <int R, int EMU, bool ACC = true>
-__device__ __forceinline__ void weno_left_vjp(const double* v, double eps_s, double Rbar, double* vb)
-{
-    static_assert(R == 3 || R == 4, "WENO5 or WENO7");
-    if constexpr (R == 3) weno5_vjp<EMU, ACC>(v, eps_s, Rbar, vb);
-    else weno7_vjp<EMU, ACC>(v, eps_s, Rbar, vb);
-}
-
-// the right-biased one: the left form on the mirrored cells; vb[2R-2] is
-// overwritten, the others accumulate
-template <int R, int EMU>
-__device__ __forceinline__ void weno_right_vjp(const double* v, double eps_s, double Rbar, double* vb)
-{
-    constexpr int S = 2 * R - 1;
-    double m[S], mb[S];
-#pragma unroll
-    for (int i = 0; i < S; ++i) m[i] = v[S - 1 - i];
-    weno_left_vjp<R, EMU, false>(m, eps_s, Rbar, mb);
-    vb[S - 1] = mb[0];
-#pragma unroll
-    for (int i = 1; i < S; ++i) vb[S - 1 - i] += mb[i];
-}
 
 // ------------------------------------------------------------ adjoint kernels
 // The pencils of one physical axis ("job"), in the layout of its arrays
@@ -234,7 +66,7 @@ struct AdjPencilArgs {
 template <int R, int EMU, int MINB>
 __global__ void __launch_bounds__(128, MINB) adj_pencil_kernel(const AdjPencilArgs a)
 {
-    constexpr int G = R, Wn = 2 * R;
+    constexpr int G = R;
     // thread -> (job, field, pencil): the jobs' ranges follow one another
     long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int jb = 0;
@@ -284,12 +116,6 @@ __global__ void __launch_bounds__(128, MINB) adj_pencil_kernel(const AdjPencilAr
         gpv = fma(alpha, uk, f);
         gmv = fma(-alpha, uk, f);
     };
-    double gpw[Wn], gmw[Wn], ap[Wn], am[Wn];
-#pragma unroll
-    for (int i = 0; i < Wn; ++i) {
-        gval(j0 - G + 1 + i, gpw[i], gmw[i]);
-        ap[i] = am[i] = 0.0;
-    }
     // Ghost contributions fold onto the cells they copy.  Cells are emitted
     // in increasing order, ghosts below 0 first and above nd - 1 last, so:
     // outflow sums the low ghosts in (lo_p, lo_m) and adds them to cell 0, and
@@ -334,27 +160,8 @@ __global__ void __launch_bounds__(128, MINB) adj_pencil_kernel(const AdjPencilAr
             put(base + (long long)bc_map(m, nd, bcd) * stp, vp, vm, periodic_split ? 2 : 1);
         }
     };
-    double lamL = j0 >= 0 ? lam[k * fs + base + (long long)j0 * stp] : 0.0;
-    for (int j = j0; j <= j1; ++j) {
-        const double lamR = (j + 1 < nd) ? lam[k * fs + base + (long long)(j + 1) * stp] : 0.0;
-        const double Fb = sc * (lamR - lamL);
-        lamL = lamR;
-        // the newest cell of each window receives its first contribution here
-        weno_left_vjp<R, EMU>(gpw, a.eps_s, Fb, ap);           // cells j-G+1 .. j+G-1
-        weno_right_vjp<R, EMU>(gmw + 1, a.eps_s, Fb, am + 1);  // cells j-G+2 .. j+G
-        emit(j - G + 1, ap[0], am[0]);
-#pragma unroll
-        for (int i = 0; i < Wn - 1; ++i) {
-            gpw[i] = gpw[i + 1];
-            gmw[i] = gmw[i + 1];
-            ap[i] = ap[i + 1];
-            am[i] = am[i + 1];
-        }
-        if (j + 1 <= j1) gval(j + G + 1, gpw[Wn - 1], gmw[Wn - 1]);
-    }
-    // cells j1-G+2 .. j1+G: complete (last segment) or shared with the next one
-#pragma unroll
-    for (int i = 0; i < Wn - 1; ++i) emit(j1 - G + 2 + i, ap[i], am[i]);
+    auto lam_at = [&](int m) { return (m >= 0 && m < nd) ? lam[k * fs + base + (long long)m * stp] : 0.0; };
+    adj_sweep<R, EMU>(j0, j1, a.eps_s, sc, gval, lam_at, emit);
 }
 
 // Fields between the x-fastest layout (x, then y, then z) and the x-slowest
@@ -569,8 +376,10 @@ static AdjPencilFn adj_pencil_fn(int v)
     }
 }
 // HYDRO_ADJ_PENCIL=<variant> picks one (for timing them); otherwise variant 1,
-// the fastest at 96^3 (937 ms against 986 ms for the reverse sweep with the
-// constants alone on the integer pipe, 1005 ms with every product there)
+// the fastest at 96^3 (reverse sweep 830 ms, against 865 ms with the
+// constants alone on the integer pipe, 927 ms with the constants and the
+// reverse sweep's products, 1087 ms with every product there: 178 registers,
+// two CTAs per SM instead of three)
 static int adj_pencil_variant()
 {
     const char* e = getenv("HYDRO_ADJ_PENCIL");

@@ -155,8 +155,8 @@ struct Diff5 {
 // of the FP64 unit: kEmuConst the products with constants, kEmuWeights the
 // squares and products of the nonlinear weights, kEmuFace the last products
 // of the weighted sums and of the face combination.  Every choice gives the
-// same bits.
-constexpr int kEmuConst = 1, kEmuWeights = 2, kEmuFace = 4;
+// same bits.  (The flags kEmuConst, kEmuWeights and kEmuFace are defined in
+// fp64_int.cuh.)
 // the squares / the products of the nonlinear weights on the integer pipe
 __host__ __device__ constexpr bool emu_wsq(int emu) { return (emu & kEmuWeights) != 0; }
 __host__ __device__ constexpr bool emu_wprod(int emu) { return (emu & kEmuWeights) != 0; }

@@ -249,7 +249,8 @@ __device__ __forceinline__ void weno5(double a, double b, double c, double d, do
 // 13/3 c2^2 + 781/20 c3^2.  With A = 6 (c1 + c3/4), B = 2 c2, C = 6 c3
 // (integer-coefficient forms) and inputs g = 2 f:
 // b_k = A^2 + 39 B^2 + 781/20 C^2 = 144 beta_k(f); eps_s must be 144 eps.
-// N and D are multiplied by 35 prod_k (eps+beta_k)^2.
+// N and D are multiplied by 420 prod_k (eps+beta_k)^2 (35 from the linear
+// weights, 12 from the candidate forms).
 // In the difference basis d_i = v_{i+1} - v_i, e_i = d_{i+1} - d_i:
 // C_k = e_{k+1} - e_k (third differences); B0 = 2 e1 - e0, B1 = B2 = e2,
 // B3 = 2 e3 - e4; A0 = 2 d0 - 7 d1 + 11 d2, A1 = -d1 + 5 d2 + 2 d3,
@@ -336,15 +337,18 @@ __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
     const double p01 = xmul<EP>(w0, w1), p23 = xmul<EP>(w2, w3);
     const double P0 = xmul<EP>(w1, p23), P1 = xmul<EP>(w0, p23), P2 = xmul<EP>(p01, w3), P3 = xmul<EP>(p01, w2);
     // 35 d_k (q_k - v3), d = (1, 12, 18, 4)/35, in the difference basis:
-    // q0 - v3 = d0/4 - 5 d1/6 + 13 d2/12, q1 - v3 = (-d1 + 4 d2 + 3 d3)/12,
-    // q2 - v3 = (d2 + 6 d3 - d4)/12, q3 - v3 = (9 d3 - 4 d4 + d5)/12;
-    // -d1 + 4 d2 + 3 d3 = A1 + e2, one addition
-    const double m0 = fma(13.0 / 12.0, d2, fma(-5.0 / 6.0, d1, xmul_pow2<EC, -2>(d0)));
-    const double m1 = A1 + B12;
-    const double m2 = fma(9.0, d3, xmul_small<EC, 3, 2, -1>(d2 - d4));
-    const double m3 = fma(3.0, d3, fma(-4.0 / 3.0, d4, xmul<EC>(1.0 / 3.0, d5)));
+    // q0 - v3 = (3 d0 - 10 d1 + 13 d2)/12, q1 - v3 = (-d1 + 4 d2 + 3 d3)/12,
+    // q2 - v3 = (d2 + 6 d3 - d4)/12, q3 - v3 = (9 d3 - 4 d4 + d5)/12.  Each
+    // numerator is A_k + B_k of the smoothness forms (3 d0 - 10 d1 + 13 d2 =
+    // A0 + B0, and so on), so with M and D both taken 12 times larger
+    // m_k = 12 x 35 d_k (q_k - v3) = (1, 12, 18, 4)_k (A_k + B_k): one
+    // addition each, the factors on the integer pipe
+    const double m0 = A0 + B0;
+    const double m1 = xmul_small<EC, 3, 2, 2>(A1 + B12);
+    const double m2 = xmul_small<EC, 9, 4, 1>(A2 + B12);
+    const double m3 = xmul_pow2<EC, 2>(A3 + B3);
     M = fma(m0, P0, fma(m1, P1, fma(m2, P2, xmul<(EMU & kEmuFace) != 0>(m3, P3))));
-    D = fma(4.0, P3, fma(18.0, P2, fma(12.0, P1, P0)));
+    D = fma(48.0, P3, fma(216.0, P2, fma(144.0, P1, xmul_small<EC, 3, 2, 2>(P0))));
 }
 
 template <int EMU = 0>
@@ -377,6 +381,46 @@ __device__ __forceinline__ void weno_right(const double* v, double eps_s, double
         const double m[7] = {v[6], v[5], v[4], v[3], v[2], v[1], v[0]};
         weno7<EMU>(m, eps_s, M, D);
     }
+}
+
+// The same reconstructions from the differences of the window alone (the
+// result M / D does not depend on the centre value): dd[i] = v[i+1] - v[i],
+// i = 0 .. 2r-3.  The right-biased one takes the differences of the mirrored
+// window, -dd[2r-3-i].
+template <int R, int EMU = 0>
+__device__ __forceinline__ void weno_left_d(const double* dd, double eps_s, double& M, double& D)
+{
+    constexpr bool EC = (EMU & kEmuConst) != 0;
+    if constexpr (R == 3) {
+        Diff5 q;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q.d[i] = dd[i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            q.s[k] = q.d[k + 1] - q.d[k];
+            q.ks[k] = xmul<EC>(13.0 / 3.0, q.s[k]);
+        }
+        weno5_core<EMU>(q, eps_s, M, D);
+    } else {
+        Diff7 q;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) q.d[i] = dd[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) q.e[i] = q.d[i + 1] - q.d[i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q.ct[k] = w7_cterm<EC>(q.e[k + 1] - q.e[k], eps_s);
+        weno7_core<EMU>(q, M, D);
+    }
+}
+
+template <int R, int EMU = 0>
+__device__ __forceinline__ void weno_right_d(const double* dd, double eps_s, double& M, double& D)
+{
+    constexpr int ND = 2 * R - 2;
+    double m[ND];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) m[i] = -dd[ND - 1 - i];
+    weno_left_d<R, EMU>(m, eps_s, M, D);
 }
 
 // 2^(1023 - e) for the biased exponent e of x (e clamped to 1 .. 2045, so

@@ -383,46 +383,6 @@ __device__ __forceinline__ void weno_right(const double* v, double eps_s, double
     }
 }
 
-// The same reconstructions from the differences of the window alone (the
-// result M / D does not depend on the centre value): dd[i] = v[i+1] - v[i],
-// i = 0 .. 2r-3.  The right-biased one takes the differences of the mirrored
-// window, -dd[2r-3-i].
-template <int R, int EMU = 0>
-__device__ __forceinline__ void weno_left_d(const double* dd, double eps_s, double& M, double& D)
-{
-    constexpr bool EC = (EMU & kEmuConst) != 0;
-    if constexpr (R == 3) {
-        Diff5 q;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) q.d[i] = dd[i];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            q.s[k] = q.d[k + 1] - q.d[k];
-            q.ks[k] = xmul<EC>(13.0 / 3.0, q.s[k]);
-        }
-        weno5_core<EMU>(q, eps_s, M, D);
-    } else {
-        Diff7 q;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) q.d[i] = dd[i];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) q.e[i] = q.d[i + 1] - q.d[i];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) q.ct[k] = w7_cterm<EC>(q.e[k + 1] - q.e[k], eps_s);
-        weno7_core<EMU>(q, M, D);
-    }
-}
-
-template <int R, int EMU = 0>
-__device__ __forceinline__ void weno_right_d(const double* dd, double eps_s, double& M, double& D)
-{
-    constexpr int ND = 2 * R - 2;
-    double m[ND];
-#pragma unroll
-    for (int i = 0; i < ND; ++i) m[i] = -dd[ND - 1 - i];
-    weno_left_d<R, EMU>(m, eps_s, M, D);
-}
-
 // 2^(1023 - e) for the biased exponent e of x (e clamped to 1 .. 2045, so
 // the factor is a normal number): x times it lies in [1, 2) for normal x.
 __device__ __forceinline__ double pow2_unscale(double x)

@@ -46,13 +46,10 @@ FLOPS_PER_CELL_STAGE = {5: 15 * (2 * 61 + 6) + 40 + 20 + 75 + 22 + 34,
 # launch variant, tile x, tile y).  roofline.frac = this count x cells / stage time /
 # the FP64 FMA issue rate measured in the same run: the FP64 pipe's
 # utilisation.  A launch without a capture reports null.
-NCU_FP64_INST_PER_CELL_STAGE = {(7, 16, 16, 16): 1237.0,
-                                (5, 12, 16, 16): 808.8, (5, 8, 16, 16): 896.2, (5, 7, 16, 16): 1023.7}
-NCU_DRAM_BYTES_PER_CELL_STAGE = {(7, 16, 16, 16): 686.1,
-                                 (5, 12, 16, 16): 511.0, (5, 8, 16, 16): 273.5, (5, 7, 16, 16): 269.3}
+NCU_FP64_INST_PER_CELL_STAGE = {(7, 16, 16, 16): 1237.0, (7, 15, 16, 16): 1297.5, (5, 12, 16, 16): 746.5}
+NCU_DRAM_BYTES_PER_CELL_STAGE = {(7, 16, 16, 16): 686.1, (7, 15, 16, 16): 683.2, (5, 12, 16, 16): 509.1}
 # FP64 pipe busy, time-weighted over the launches of one stage
-NCU_FP64_PIPE_BUSY = {(7, 16, 16, 16): 0.750,
-                      (5, 12, 16, 16): 0.846, (5, 8, 16, 16): 0.809, (5, 7, 16, 16): 0.838}
+NCU_FP64_PIPE_BUSY = {(7, 16, 16, 16): 0.750, (7, 15, 16, 16): 0.802, (5, 12, 16, 16): 0.845}
 # Algorithmic HBM traffic per cell-update: stage 1 reads u^n, writes u1 (80 B);
 # stages 2, 3 read u^n and u^(k), write u^(k+1) (120 B each).
 HBM_BYTES_PER_CELL_UPDATE = 320

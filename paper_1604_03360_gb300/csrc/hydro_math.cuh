@@ -147,8 +147,7 @@ __device__ __forceinline__ void max_speeds(double k, double vx, double vy, doubl
 // bits as fresh windows.
 struct Diff5 {
     double d[4];     // d_i = v_{i+1} - v_i
-    double s[3];     // s_k = d_{k+1} - d_k
-    double ks[3];    // 13/3 s_k
+    double cs[3];    // 13/3 s_k^2 + eps_s, s_k = d_{k+1} - d_k
 };
 
 // EMU selects operations that run on the integer pipe (fp64_int.cuh) instead
@@ -161,66 +160,64 @@ struct Diff5 {
 __host__ __device__ constexpr bool emu_wsq(int emu) { return (emu & kEmuWeights) != 0; }
 __host__ __device__ constexpr bool emu_wprod(int emu) { return (emu & kEmuWeights) != 0; }
 
+// The second-difference term 13/3 s_k^2 + eps of b_k depends on the three
+// cells of stencil k only, so it is carried with the differences (as
+// WENO7's third-difference term is).
+template <bool EC>
+__device__ __forceinline__ double w5_sterm(double s, double eps_s)
+{
+    return fma(xmul<EC>(13.0 / 3.0, s), s, eps_s);
+}
+
 template <int EMU = 0>
-__device__ __forceinline__ void weno5_diffs(const double* v, Diff5& q)
+__device__ __forceinline__ void weno5_diffs(const double* v, double eps_s, Diff5& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) q.d[i] = v[i + 1] - v[i];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        q.s[k] = q.d[k + 1] - q.d[k];
-        q.ks[k] = xmul<EC>(13.0 / 3.0, q.s[k]);
-    }
+    for (int k = 0; k < 3; ++k) q.cs[k] = w5_sterm<EC>(q.d[k + 1] - q.d[k], eps_s);
 }
 
 // window moved one cell up the array (v is the new window): the new cell
 // enters at v[4]
 template <int EMU = 0>
-__device__ __forceinline__ void weno5_slide(const double* v, Diff5& q)
+__device__ __forceinline__ void weno5_slide(const double* v, double eps_s, Diff5& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) q.d[i] = q.d[i + 1];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        q.s[k] = q.s[k + 1];
-        q.ks[k] = q.ks[k + 1];
-    }
+    for (int k = 0; k < 2; ++k) q.cs[k] = q.cs[k + 1];
     q.d[3] = v[4] - v[3];
-    q.s[2] = q.d[3] - q.d[2];
-    q.ks[2] = xmul<EC>(13.0 / 3.0, q.s[2]);
+    q.cs[2] = w5_sterm<EC>(q.d[3] - q.d[2], eps_s);
 }
 
 // mirrored window moved one cell (m is the new mirrored window): the new
 // cell enters at m[0]
 template <int EMU = 0>
-__device__ __forceinline__ void weno5_slide_mirror(const double* m, Diff5& q)
+__device__ __forceinline__ void weno5_slide_mirror(const double* m, double eps_s, Diff5& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
     for (int i = 3; i > 0; --i) q.d[i] = q.d[i - 1];
 #pragma unroll
-    for (int k = 2; k > 0; --k) {
-        q.s[k] = q.s[k - 1];
-        q.ks[k] = q.ks[k - 1];
-    }
+    for (int k = 2; k > 0; --k) q.cs[k] = q.cs[k - 1];
     q.d[0] = m[1] - m[0];
-    q.s[0] = q.d[1] - q.d[0];
-    q.ks[0] = xmul<EC>(13.0 / 3.0, q.s[0]);
+    q.cs[0] = w5_sterm<EC>(q.d[1] - q.d[0], eps_s);
 }
 
 // Result: the reconstruction is v[2] + M / D (the centre value plus a
 // correction), see weno_left.
 template <int EMU = 0>
-__device__ __forceinline__ void weno5_core(const Diff5& q, double eps_s, double& M, double& D)
+__device__ __forceinline__ void weno5_core(const Diff5& q, double& M, double& D)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
     const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3];
     const double t0 = fma(3.0, d1, -d0), t1 = d1 + d2, t2 = fma(3.0, d2, -d3);
-    const double b0 = fma(q.ks[0], q.s[0], fma(t0, t0, eps_s));
-    const double b1 = fma(q.ks[1], q.s[1], fma(t1, t1, eps_s));
-    const double b2 = fma(q.ks[2], q.s[2], fma(t2, t2, eps_s));
+    const double b0 = fma(t0, t0, q.cs[0]);
+    const double b1 = fma(t1, t1, q.cs[1]);
+    const double b2 = fma(t2, t2, q.cs[2]);
     constexpr bool ES = emu_wsq(EMU), EP = emu_wprod(EMU);
     const double w0 = xmul<ES>(b0, b0), w1 = xmul<ES>(b1, b1), w2 = xmul<ES>(b2, b2);
     const double P0 = xmul<EP>(w1, w2), P1 = xmul<EP>(w0, w2), P2 = xmul<EP>(w0, w1);
@@ -240,8 +237,8 @@ __device__ __forceinline__ void weno5(double a, double b, double c, double d, do
 {
     const double v[5] = {a, b, c, d, e};
     Diff5 q;
-    weno5_diffs<EMU>(v, q);
-    weno5_core<EMU>(q, eps_s, M, D);
+    weno5_diffs<EMU>(v, eps_s, q);
+    weno5_core<EMU>(q, M, D);
 }
 
 // r = 4 (Balsara-Shu weights from the same definition).  For the cubic

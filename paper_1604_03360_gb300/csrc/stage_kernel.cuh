@@ -222,25 +222,25 @@ template <> struct DiffOf<4> { using T = Diff7; };
 template <int R, int EMU>
 __device__ __forceinline__ void diffs_fresh(const double* v, double eps_s, typename DiffOf<R>::T& q)
 {
-    if constexpr (R == 3) weno5_diffs<EMU>(v, q);
+    if constexpr (R == 3) weno5_diffs<EMU>(v, eps_s, q);
     else weno7_diffs<EMU>(v, eps_s, q);
 }
 template <int R, int EMU>
 __device__ __forceinline__ void diffs_slide(const double* v, double eps_s, typename DiffOf<R>::T& q)
 {
-    if constexpr (R == 3) weno5_slide<EMU>(v, q);
+    if constexpr (R == 3) weno5_slide<EMU>(v, eps_s, q);
     else weno7_slide<EMU>(v, eps_s, q);
 }
 template <int R, int EMU>
 __device__ __forceinline__ void diffs_slide_mirror(const double* m, double eps_s, typename DiffOf<R>::T& q)
 {
-    if constexpr (R == 3) weno5_slide_mirror<EMU>(m, q);
+    if constexpr (R == 3) weno5_slide_mirror<EMU>(m, eps_s, q);
     else weno7_slide_mirror<EMU>(m, eps_s, q);
 }
 template <int R, int EMU>
 __device__ __forceinline__ void weno_core(const typename DiffOf<R>::T& q, double eps_s, double& M, double& D)
 {
-    if constexpr (R == 3) weno5_core<EMU>(q, eps_s, M, D);
+    if constexpr (R == 3) weno5_core<EMU>(q, M, D);
     else weno7_core<EMU>(q, M, D);
 }
 

@@ -338,7 +338,9 @@ hydro_status hydro_eval_rcp(const double* x, double* y, int64_t n, void* stream)
  *   t_end), recording each step's speeds and dt and checkpointing the state
  *   every ckpt_every steps (device workspace owned by h, about
  *   99 + 5 * ceil(nsteps/ckpt_every) + 27 * ckpt_every doubles per cell:
- *   the reverse sweep keeps every stage input of one segment).
+ *   the reverse sweep keeps every stage input of one segment; allocated on
+ *   the first call and kept by later calls with the same nsteps and
+ *   ckpt_every, so only a call that changes them allocates).
  *   Asynchronous.
  * hydro_adjoint: grad_u0 = (d u_N / d u_0)^T lambda_final for the recorded
  *   run: segment by segment, the step-start states are recomputed from the

@@ -488,23 +488,29 @@ extern "C" hydro_status hydro_forward_record(hydro_t* h, int32_t nsteps, int32_t
     if (nsteps < 1 || ckpt_every < 1) return hydro_handle_fail(h, HYDRO_ERR_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
     AdjointWork* w = hydro_handle_adjoint(h, true);
     if (!w) return hydro_handle_fail(h, HYDRO_ERR_OOM, "host allocation failed");
-    // (re)allocate the workspace for this length
-    cudaStreamSynchronize(v.stream);
-    cudaFree(w->buf);
-    cudaFree(w->rec);
-    cudaFree(w->ctl);
-    w->buf = nullptr;
-    w->rec = nullptr;
-    w->ctl = nullptr;
+    // (re)allocate the workspace for this length; a workspace of the same
+    // length is reused (the forward overwrites every part of it that the
+    // reverse sweep reads: checkpoints, the last segment, the step record)
+    const long long fs = v.fs;
+    const int nckpt = (nsteps + ckpt_every - 1) / ckpt_every;
+    const long long nfields = 27 + 5 * 4 + 30 + 22 + 5LL * nckpt + 27LL * ckpt_every;
+    if (!(w->buf && w->rec && w->ctl && w->nsteps == nsteps && w->ckpt == ckpt_every && w->fs == fs)) {
+        cudaStreamSynchronize(v.stream);
+        cudaFree(w->buf);
+        cudaFree(w->rec);
+        cudaFree(w->ctl);
+        w->buf = nullptr;
+        w->rec = nullptr;
+        w->ctl = nullptr;
+        w->nsteps = 0;
+        ACK(h, cudaMalloc(&w->buf, sizeof(double) * (size_t)(fs * nfields)), "adjoint workspace");
+        ACK(h, cudaMalloc(&w->rec, sizeof(unsigned long long) * 10 * (size_t)nsteps), "step record");
+        ACK(h, cudaMalloc(&w->ctl, sizeof(Ctl)), "scratch control");
+    }
     w->nsteps = nsteps;
     w->ckpt = ckpt_every;
-    w->nckpt = (nsteps + ckpt_every - 1) / ckpt_every;
-    w->fs = v.fs;
-    const long long fs = v.fs;
-    const long long nfields = 27 + 5 * 4 + 30 + 22 + 5LL * w->nckpt + 27LL * ckpt_every;
-    ACK(h, cudaMalloc(&w->buf, sizeof(double) * (size_t)(fs * nfields)), "adjoint workspace");
-    ACK(h, cudaMalloc(&w->rec, sizeof(unsigned long long) * 10 * (size_t)nsteps), "step record");
-    ACK(h, cudaMalloc(&w->ctl, sizeof(Ctl)), "scratch control");
+    w->nckpt = nckpt;
+    w->fs = fs;
     double* p = w->buf;
     for (int i = 0; i < 3; ++i) {
         w->AU[i] = p;

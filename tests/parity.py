@@ -3,7 +3,7 @@ import numpy as np
 
 import oracle
 
-# spec tolerance: max relative error per field after the stated steps
+# parity tolerance: max relative error per field after the stated steps
 TOL = 1e-11
 
 

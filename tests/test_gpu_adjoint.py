@@ -2,7 +2,7 @@
 hydro_eps2) against the plain CPU torch-autograd restatement of the scheme
 (tiny grids) and against central finite differences of the C oracle with the
 Lax-Friedrichs speeds and time steps frozen (the 24^3 and 96^3 adjoint
-configurations).  Tolerance: relative error 1e-7 (spec bar) for the
+configurations).  Tolerance: relative error 1e-7 (the stated bar) for the
 autograd comparison; finite differences carry their own truncation error."""
 import numpy as np
 import pytest

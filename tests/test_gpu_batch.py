@@ -1,6 +1,7 @@
-"""Batched event-by-event stepping (one persistent launch per RK3 stage over a
-tile work-list of all events) vs the CPU oracle per event, and vs the
-single-grid path bit for bit."""
+"""Batched event-by-event stepping (per RK3 stage, face passes over the
+pencils of all events and one combination launch, or a z pass and one
+persistent launch over a tile work-list of all events) vs the CPU oracle per
+event, and vs the single-grid path bit for bit."""
 import numpy as np
 import pytest
 

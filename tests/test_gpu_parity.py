@@ -1,5 +1,5 @@
 """GPU (C-ABI) vs CPU oracle parity: element-wise, per field, within the
-spec tolerance of 1e-11 (normwise relative error per field)."""
+stated tolerance of 1e-11 (normwise relative error per field)."""
 import numpy as np
 import pytest
 

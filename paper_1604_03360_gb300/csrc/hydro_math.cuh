@@ -144,7 +144,9 @@ __device__ __forceinline__ void max_speeds(double k, double vx, double vy, doubl
 // of each order with the window of face j+3/2.  weno5 / weno7 compute them
 // afresh; the *_slide functions update them for a window moved by one cell,
 // with the same operations on the same operands, so a sweep gives the same
-// bits as fresh windows.
+// bits as fresh windows.  The reconstruction functions are host functions
+// too, so the same source also runs on the CPU (a host test checks it against
+// the WENO definition and the sweeps against fresh windows).
 struct Diff5 {
     double d[4];     // d_i = v_{i+1} - v_i
     double cs[3];    // 13/3 s_k^2 + eps_s, s_k = d_{k+1} - d_k
@@ -164,13 +166,13 @@ __host__ __device__ constexpr bool emu_wprod(int emu) { return (emu & kEmuWeight
 // cells of stencil k only, so it is carried with the differences (as
 // WENO7's third-difference term is).
 template <bool EC>
-__device__ __forceinline__ double w5_sterm(double s, double eps_s)
+__host__ __device__ __forceinline__ double w5_sterm(double s, double eps_s)
 {
     return fma(xmul<EC>(13.0 / 3.0, s), s, eps_s);
 }
 
 template <int EMU = 0>
-__device__ __forceinline__ void weno5_diffs(const double* v, double eps_s, Diff5& q)
+__host__ __device__ __forceinline__ void weno5_diffs(const double* v, double eps_s, Diff5& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
@@ -182,7 +184,7 @@ __device__ __forceinline__ void weno5_diffs(const double* v, double eps_s, Diff5
 // window moved one cell up the array (v is the new window): the new cell
 // enters at v[4]
 template <int EMU = 0>
-__device__ __forceinline__ void weno5_slide(const double* v, double eps_s, Diff5& q)
+__host__ __device__ __forceinline__ void weno5_slide(const double* v, double eps_s, Diff5& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
@@ -196,7 +198,7 @@ __device__ __forceinline__ void weno5_slide(const double* v, double eps_s, Diff5
 // mirrored window moved one cell (m is the new mirrored window): the new
 // cell enters at m[0]
 template <int EMU = 0>
-__device__ __forceinline__ void weno5_slide_mirror(const double* m, double eps_s, Diff5& q)
+__host__ __device__ __forceinline__ void weno5_slide_mirror(const double* m, double eps_s, Diff5& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
@@ -210,7 +212,7 @@ __device__ __forceinline__ void weno5_slide_mirror(const double* m, double eps_s
 // Result: the reconstruction is v[2] + M / D (the centre value plus a
 // correction), see weno_left.
 template <int EMU = 0>
-__device__ __forceinline__ void weno5_core(const Diff5& q, double& M, double& D)
+__host__ __device__ __forceinline__ void weno5_core(const Diff5& q, double& M, double& D)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
     const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3];
@@ -232,7 +234,7 @@ __device__ __forceinline__ void weno5_core(const Diff5& q, double& M, double& D)
 }
 
 template <int EMU = 0>
-__device__ __forceinline__ void weno5(double a, double b, double c, double d, double e, double eps_s,
+__host__ __device__ __forceinline__ void weno5(double a, double b, double c, double d, double e, double eps_s,
                                       double& M, double& D)
 {
     const double v[5] = {a, b, c, d, e};
@@ -261,13 +263,13 @@ struct Diff7 {
 };
 
 template <bool EC>
-__device__ __forceinline__ double w7_cterm(double C, double eps_s)
+__host__ __device__ __forceinline__ double w7_cterm(double C, double eps_s)
 {
     return fma(xmul<EC>(781.0 / 20.0, C), C, eps_s);
 }
 
 template <int EMU = 0>
-__device__ __forceinline__ void weno7_diffs(const double* v, double eps_s, Diff7& q)
+__host__ __device__ __forceinline__ void weno7_diffs(const double* v, double eps_s, Diff7& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
@@ -280,7 +282,7 @@ __device__ __forceinline__ void weno7_diffs(const double* v, double eps_s, Diff7
 
 // window moved one cell up the array: the new cell enters at v[6]
 template <int EMU = 0>
-__device__ __forceinline__ void weno7_slide(const double* v, double eps_s, Diff7& q)
+__host__ __device__ __forceinline__ void weno7_slide(const double* v, double eps_s, Diff7& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
@@ -296,7 +298,7 @@ __device__ __forceinline__ void weno7_slide(const double* v, double eps_s, Diff7
 
 // mirrored window moved one cell: the new cell enters at m[0]
 template <int EMU = 0>
-__device__ __forceinline__ void weno7_slide_mirror(const double* m, double eps_s, Diff7& q)
+__host__ __device__ __forceinline__ void weno7_slide_mirror(const double* m, double eps_s, Diff7& q)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
 #pragma unroll
@@ -312,7 +314,7 @@ __device__ __forceinline__ void weno7_slide_mirror(const double* m, double eps_s
 
 // Result: the reconstruction is v[3] + M / D, see weno_left.
 template <int EMU = 0>
-__device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
+__host__ __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
 {
     constexpr bool EC = (EMU & kEmuConst) != 0;
     const double d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3], d4 = q.d[4], d5 = q.d[5];
@@ -349,7 +351,7 @@ __device__ __forceinline__ void weno7_core(const Diff7& q, double& M, double& D)
 }
 
 template <int EMU = 0>
-__device__ __forceinline__ void weno7(const double* v, double eps_s, double& M, double& D)
+__host__ __device__ __forceinline__ void weno7(const double* v, double eps_s, double& M, double& D)
 {
     Diff7 q;
     weno7_diffs<EMU>(v, eps_s, q);
@@ -361,7 +363,7 @@ __device__ __forceinline__ void weno7(const double* v, double eps_s, double& M, 
 // M = sum_k d_k alpha_k (q_k - v_j) up to one common positive factor (q_k the
 // candidate values, alpha_k = 1/(eps+beta_k)^2); candidate k uses v[k..k+r-1].
 template <int R, int EMU = 0>
-__device__ __forceinline__ void weno_left(const double* v, double eps_s, double& M, double& D)
+__host__ __device__ __forceinline__ void weno_left(const double* v, double eps_s, double& M, double& D)
 {
     if constexpr (R == 3) weno5<EMU>(v[0], v[1], v[2], v[3], v[4], eps_s, M, D);
     else weno7<EMU>(v, eps_s, M, D);
@@ -370,7 +372,7 @@ __device__ __forceinline__ void weno_left(const double* v, double eps_s, double&
 // Right-biased value at x_{j-1/2} of the stencil centred on j: the mirror
 // image, again v[r-1] + M / D.
 template <int R, int EMU = 0>
-__device__ __forceinline__ void weno_right(const double* v, double eps_s, double& M, double& D)
+__host__ __device__ __forceinline__ void weno_right(const double* v, double eps_s, double& M, double& D)
 {
     if constexpr (R == 3) {
         weno5<EMU>(v[4], v[3], v[2], v[1], v[0], eps_s, M, D);
